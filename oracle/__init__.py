@@ -1,0 +1,216 @@
+"""CPU oracle of the Moss sampling path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never imports it
+and shares no code with it.
+
+Contents
+* ``moss_oracle.c`` (compiled with gcc on first use): exact integer vertex
+  weights and totals (Table 1), alias tables for WeightRandomVertex
+  (Sec. 4.1.3), the Philox4x64-10 word schedule, the per-sample steps of
+  Algorithm 1 (MOSS-4), Algorithm 3 (T-5) and Algorithm 4 (Path-5), the
+  motif classifier (Sec. 4.1.2, Table 2) and ESU exact enumeration.
+* :mod:`oracle.finalize` (numpy, FP64): the estimators and variances of
+  Theorems 3, 7, 9 and 10 and the mix estimator of Sec. 5.1.3.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+from .finalize import finalize_moss4, finalize_moss5, PHI4, PHI5  # noqa: F401
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "moss_oracle.c")
+_LIB = os.path.join(_HERE, "libmoss_oracle.so")
+_lib = None
+
+MOSS4, T5, PATH5 = 0, 1, 2
+
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle library with gcc (portable flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        lib.oracle_new.argtypes = [ctypes.c_uint32, _u64p, _u32p]
+        lib.oracle_new.restype = ctypes.c_void_p
+        lib.oracle_free.argtypes = [ctypes.c_void_p]
+        lib.oracle_totals.argtypes = [ctypes.c_void_p, _u64p]
+        lib.oracle_vertex.argtypes = [ctypes.c_void_p, _u64p, _u64p, _u64p, _u64p]
+        lib.oracle_seed_table.argtypes = [ctypes.c_void_p, ctypes.c_int, _u64p, _u64p, _u32p]
+        lib.oracle_sigma_table.argtypes = [ctypes.c_void_p, _u64p, _u32p, _u64p]
+        lib.oracle_alias_build.argtypes = [ctypes.c_uint64, _u64p, _u64p, _u32p]
+        lib.oracle_alias_build.restype = ctypes.c_int
+        lib.oracle_philox.argtypes = [_u64p, _u64p, _u64p]
+        lib.oracle_classify.argtypes = [ctypes.c_int, ctypes.c_uint32]
+        lib.oracle_classify.restype = ctypes.c_int
+        lib.oracle_sample_words.argtypes = [ctypes.c_void_p, ctypes.c_int, _u64p, _u32p, ctypes.POINTER(ctypes.c_int)]
+        lib.oracle_sample_words.restype = ctypes.c_int
+        lib.oracle_run.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                   _u64p, _u8p, _u32p]
+        lib.oracle_run.restype = ctypes.c_int
+        lib.oracle_esu.argtypes = [ctypes.c_void_p, ctypes.c_int, _u64p]
+        lib.oracle_esu.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def _u128(lohi) -> int:
+    return int(lohi[0]) | (int(lohi[1]) << 64)
+
+
+def philox4x64(ctr, key) -> list[int]:
+    """One Philox4x64-10 block."""
+    c = np.array(ctr, dtype=np.uint64)
+    k = np.array(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    _load().oracle_philox(_p(c, _u64p), _p(k, _u64p), _p(out, _u64p))
+    return [int(x) for x in out]
+
+
+def classify(k: int, mask: int) -> int:
+    """Motif class (1-based) of the k-vertex graph given by a pair bitmask;
+    0 when disconnected."""
+    return _load().oracle_classify(k, mask)
+
+
+def alias_build(weights) -> tuple[list[int], list[int]]:
+    """Alias table (thresholds, aliases) of integer weights, by the sweep."""
+    m = len(weights)
+    w = np.zeros(2 * max(m, 1), dtype=np.uint64)
+    for j, x in enumerate(weights):
+        x = int(x)
+        w[2 * j] = x & ((1 << 64) - 1)
+        w[2 * j + 1] = x >> 64
+    thr = np.zeros(2 * max(m, 1), dtype=np.uint64)
+    alias = np.zeros(max(m, 1), dtype=np.uint32)
+    rc = _load().oracle_alias_build(m, _p(w, _u64p), _p(thr, _u64p), _p(alias, _u32p))
+    if rc:
+        raise MemoryError("oracle_alias_build")
+    return [_u128(thr[2 * j:2 * j + 2]) for j in range(m)], [int(a) for a in alias[:m]]
+
+
+class OracleGraph:
+    """The oracle's view of one graph: weights, tables and the samplers."""
+
+    def __init__(self, row_ptr: np.ndarray, col: np.ndarray):
+        self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.uint64)
+        self.col = np.ascontiguousarray(col, dtype=np.uint32)
+        self.n = len(self.row_ptr) - 1
+        self.nnz = int(self.row_ptr[-1])
+        col_buf = self.col if self.nnz else np.zeros(1, dtype=np.uint32)
+        self._ctx = _load().oracle_new(self.n, _p(self.row_ptr, _u64p), _p(col_buf, _u32p))
+        if not self._ctx:
+            raise MemoryError("oracle_new")
+        t = np.zeros(10, dtype=np.uint64)
+        _load().oracle_totals(self._ctx, _p(t, _u64p))
+        self.Gamma = [_u128(t[0:2]), _u128(t[2:4]), _u128(t[4:6])]
+        self.Lambda3 = _u128(t[6:8])
+        self.Lambda4 = _u128(t[8:10])
+
+    def __del__(self):
+        ctx = getattr(self, "_ctx", None)
+        if ctx:
+            _load().oracle_free(ctx)
+            self._ctx = None
+
+    # -- tables -------------------------------------------------------------
+    def vertex(self):
+        n = max(self.n, 1)
+        deg = np.zeros(n, dtype=np.uint64)
+        S = np.zeros(n, dtype=np.uint64)
+        Q = np.zeros(n, dtype=np.uint64)
+        g = np.zeros(3 * 2 * n, dtype=np.uint64)
+        _load().oracle_vertex(self._ctx, _p(deg, _u64p), _p(S, _u64p), _p(Q, _u64p), _p(g, _u64p))
+        gam = [[_u128(g[(l * 2 * n) + 2 * v:(l * 2 * n) + 2 * v + 2]) for v in range(self.n)] for l in range(3)]
+        return deg[:self.n], S[:self.n], Q[:self.n], gam
+
+    def seed_table(self, which: int):
+        n = max(self.n, 1)
+        thr = np.zeros(2 * n, dtype=np.uint64)
+        T = np.zeros(n, dtype=np.uint64)
+        alias = np.zeros(n, dtype=np.uint32)
+        _load().oracle_seed_table(self._ctx, which, _p(thr, _u64p), _p(T, _u64p), _p(alias, _u32p))
+        return [_u128(thr[2 * v:2 * v + 2]) for v in range(self.n)], T[:self.n], alias[:self.n]
+
+    def sigma_table(self):
+        m = max(self.nnz, 1)
+        thr = np.zeros(m, dtype=np.uint64)
+        alias = np.zeros(m, dtype=np.uint32)
+        acc = np.zeros(m, dtype=np.uint64)
+        _load().oracle_sigma_table(self._ctx, _p(thr, _u64p), _p(alias, _u32p), _p(acc, _u64p))
+        return thr[:self.nnz], alias[:self.nnz], acc[:self.nnz]
+
+    # -- sampling -----------------------------------------------------------
+    def sample_words(self, method: int, words) -> tuple[list[int], int]:
+        x = np.zeros(16, dtype=np.uint64)
+        for i, w in enumerate(words):
+            x[i] = int(w)
+        verts = np.zeros(5, dtype=np.uint32)
+        cls = ctypes.c_int(0)
+        rc = _load().oracle_sample_words(self._ctx, method, _p(x, _u64p), _p(verts, _u32p), ctypes.byref(cls))
+        if rc:
+            raise ValueError("method has zero total weight on this graph")
+        return [int(v) for v in verts], cls.value
+
+    def run(self, method: int, seed: int, count: int, first: int = 0, record: bool = False):
+        """Counts (uint64[22]; [0] = collisions) of samples first..first+count-1.
+        With record=True also per-sample classes (uint8) and vertices (uint32[.,5])."""
+        counts = np.zeros(22, dtype=np.uint64)
+        classes = np.zeros(max(count, 1), dtype=np.uint8) if record else None
+        verts = np.zeros((max(count, 1), 5), dtype=np.uint32) if record else None
+        rc = _load().oracle_run(self._ctx, method, seed, first, count, _p(counts, _u64p),
+                                _p(classes, _u8p) if record else None,
+                                _p(verts, _u32p) if record else None)
+        if rc == -1:
+            raise ValueError("method has zero total weight on this graph")
+        if rc:
+            raise RuntimeError(f"oracle_run failed ({rc})")
+        if record:
+            return counts, classes[:count], verts[:count]
+        return counts
+
+    def esu(self, k: int) -> np.ndarray:
+        """Exact counts of connected induced k-subgraphs per class (index 1..)."""
+        counts = np.zeros(22, dtype=np.uint64)
+        if _load().oracle_esu(self._ctx, k, _p(counts, _u64p)):
+            raise ValueError("k must be 4 or 5")
+        return counts
+
+    # -- the whole path -----------------------------------------------------
+    def estimate(self, k: int, budget: int, seed: int, **kw):
+        """Sample-and-estimate as the library defines it: k=4 runs MOSS-4 with
+        K=budget; k=5 runs T-5 with K1=floor(budget/2) and Path-5 with
+        K2=budget-K1 (K1=K2, Sec. 5.1.5)."""
+        if k == 4:
+            K = budget if self.Gamma[0] > 0 else 0
+            m = self.run(MOSS4, seed, K) if K else np.zeros(22, dtype=np.uint64)
+            return finalize_moss4(m, K, self.Gamma[0], self.Lambda3, **kw)
+        K1 = budget // 2
+        K2 = budget - K1
+        K1 = K1 if self.Gamma[1] > 0 else 0
+        K2 = K2 if self.Gamma[2] > 0 else 0
+        m1 = self.run(T5, seed, K1) if K1 else np.zeros(22, dtype=np.uint64)
+        m2 = self.run(PATH5, seed, K2) if K2 else np.zeros(22, dtype=np.uint64)
+        return finalize_moss5(m1, m2, K1, K2, self.Gamma[1], self.Gamma[2], self.Lambda4, **kw)

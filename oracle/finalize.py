@@ -1,0 +1,137 @@
+"""Estimators and variances (FP64) -- part of the test oracle.
+
+Everything is written as the paper states it, in a fixed evaluation order:
+
+* MOSS-4 (Sec. 4.1.2, Theorem 2, Theorem 3): p_i = 2 phi_i^(1) / Gamma,
+  n_i = m_i / (K p_i) for i in {1,3,4,5,6}; n_2 = Lambda_3 - n_4 - 2 n_5 - 4 n_6
+  (eq. 2); Var(n_i) = n_i/K (1/p_i - n_i); Var(n_2) per Theorem 3.
+  Also the triangle count implied by the collisions r = w: each triangle is
+  produced by 6 ordered (v, u, w) draws of probability 1/Gamma each (the
+  argument of the proof of Theorem 2), so T = m_0 Gamma / (6 K).
+* MOSS-5 (Sec. 5.1, Theorems 6-10): eta^(l)_i = m^(l)_i / (K_l p^(l)_i),
+  p^(l)_i = 2 phi^(l)_i / Gamma^(l); the mix estimator (eq. mixestimator)
+  with lambda from the two variances; eta_2 = Lambda_4 - sum phi^(3)_i eta_i
+  over Omega_3* and its variance from Theorem 10.
+
+The variances contain the unknown eta_i; the plug-in value is the estimate
+itself for a single-source class and the pooled value
+(m1 + m2) / (K1 p1 + K2 p2) for a class of Omega_1 and Omega_2, so that a
+class seen by only one sub-method keeps a positive weight on it.  Passing
+``eta=...`` replaces the plug-in by given values (e.g. the exact counts, with
+which lambda is a constant and Theorem 10 holds exactly).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Sec. 4.1.2: phi^(1) (copies of M_1^(4)) and phi^(2) (copies of M_2^(4)) of M_1..M_6.
+PHI4 = np.array([[1, 0], [0, 1], [4, 0], [2, 1], [6, 2], [12, 4]], dtype=np.float64)
+# Table 2: phi^(1) (forks), phi^(2) (5-paths), phi^(3) (4-stars) of M_1^(5)..M_21^(5).
+PHI5 = np.array([
+    [0, 1, 0], [0, 0, 1], [1, 0, 0], [1, 2, 0], [2, 2, 0], [0, 5, 0], [2, 1, 0],
+    [2, 0, 1], [4, 4, 0], [4, 7, 0], [5, 2, 1], [4, 4, 1], [6, 6, 0], [10, 10, 1],
+    [9, 6, 1], [12, 6, 2], [10, 14, 0], [20, 24, 1], [20, 18, 2], [36, 36, 3], [60, 60, 5]],
+    dtype=np.float64)
+
+
+def finalize_moss4(m, K: int, Gamma: int, Lambda3: int, eta=None) -> dict:
+    """m: counts[22] with m[0] = collisions (triangles), m[i] class i."""
+    m = np.asarray(m, dtype=np.float64)
+    G = float(Gamma)
+    est = np.zeros(7)
+    var = np.zeros(7)
+    p = np.zeros(7)
+    sampled = (1, 3, 4, 5, 6)
+    tri = 0.0
+    tri_var = 0.0
+    if K > 0 and G > 0:
+        for i in sampled:
+            p[i] = 2.0 * PHI4[i - 1, 0] / G                 # Theorem 2
+            est[i] = m[i] / (K * p[i])                       # Sec. 4.1.2
+        plug = est if eta is None else np.asarray(eta, dtype=np.float64)
+        for i in sampled:
+            var[i] = plug[i] / K * (1.0 / p[i] - plug[i])   # Theorem 3
+        var[2] = (plug[4] / p[4] + 4.0 * plug[5] / p[5] + 16.0 * plug[6] / p[6]
+                  - (plug[4] + 2.0 * plug[5] + 4.0 * plug[6]) ** 2) / K
+        tri = m[0] * G / (6.0 * K)
+        tri_var = tri / K * (G / 6.0 - tri)
+    est[2] = float(Lambda3) - est[4] - 2.0 * est[5] - 4.0 * est[6]   # eq. (2)
+    return {"k": 4, "K": (K, 0), "est": est, "var": var, "p": p,
+            "triangles": tri, "triangles_var": tri_var}
+
+
+def finalize_moss5(m1, m2, K1: int, K2: int, Gamma1: int, Gamma2: int, Lambda4: int, eta=None) -> dict:
+    """m1, m2: counts[22] of T-5 and Path-5 ([0] = collisions)."""
+    m1 = np.asarray(m1, dtype=np.float64)
+    m2 = np.asarray(m2, dtype=np.float64)
+    G = (float(Gamma1), float(Gamma2))
+    K = (K1, K2)
+    mm = (m1, m2)
+    avail = (K1 > 0 and G[0] > 0, K2 > 0 and G[1] > 0)
+    p = np.zeros((2, 22))
+    eh = np.zeros((2, 22))
+    for l in range(2):
+        if not avail[l]:
+            continue
+        for i in range(1, 22):
+            if PHI5[i - 1, l] > 0:                                   # i in Omega_l
+                p[l, i] = 2.0 * PHI5[i - 1, l] / G[l]                # Theorems 6, 8
+                eh[l, i] = mm[l][i] / (K[l] * p[l, i])
+    est = np.zeros(22)
+    var = np.zeros(22)
+    lam = np.zeros((2, 22))     # a^(l)_i: lambda^(l)_i, 1 (single source) or 0
+    plug = np.zeros(22)
+    for i in range(1, 22):
+        if i == 2:
+            continue
+        src = [l for l in range(2) if avail[l] and PHI5[i - 1, l] > 0]
+        if not src:
+            continue
+        if len(src) == 1:
+            l = src[0]
+            e = eh[l, i] if eta is None else float(eta[i])
+            plug[i] = e
+            est[i] = eh[l, i]
+            var[i] = e / K[l] * (1.0 / p[l, i] - e)                  # Theorems 7, 9
+            lam[l, i] = 1.0
+            continue
+        if eta is None:
+            e = (m1[i] + m2[i]) / (K1 * p[0, i] + K2 * p[1, i])      # pooled plug-in
+        else:
+            e = float(eta[i])
+        plug[i] = e
+        V1 = max(e / K1 * (1.0 / p[0, i] - e), 0.0)
+        V2 = max(e / K2 * (1.0 / p[1, i] - e), 0.0)
+        if V1 + V2 > 0.0:
+            lam[0, i] = V2 / (V1 + V2)                               # lambda^(1)_i
+            lam[1, i] = V1 / (V1 + V2)                               # lambda^(2)_i
+            var[i] = V1 * V2 / (V1 + V2)                             # Theorem 10
+        else:
+            lam[0, i] = lam[1, i] = 0.5
+            var[i] = 0.0
+        est[i] = lam[0, i] * eh[0, i] + lam[1, i] * eh[1, i]         # eq. (mixestimator)
+    # Cov(eta_i, eta_j) = -plug_i plug_j sum_l a^(l)_i a^(l)_j / K_l  (Theorem 10)
+    cov = np.zeros((22, 22))
+    for l in range(2):
+        if avail[l]:
+            a = lam[l] * plug
+            cov -= np.outer(a, a) / K[l]
+    np.fill_diagonal(cov, 0.0)
+    # eta_2 = Lambda_4 - sum_{Omega_3*} phi^(3)_i eta_i  (Sec. 5.1.3)
+    omega3 = [i for i in range(1, 22) if i != 2 and PHI5[i - 1, 2] > 0]
+    s = 0.0
+    for i in omega3:
+        s += PHI5[i - 1, 2] * est[i]
+    est[2] = float(Lambda4) - s
+    v2 = 0.0
+    for i in omega3:
+        v2 += PHI5[i - 1, 2] ** 2 * var[i]
+    for i in omega3:
+        for j in omega3:
+            if i != j:
+                v2 += PHI5[i - 1, 2] * PHI5[j - 1, 2] * cov[i, j]
+    var[2] = v2
+    for i in range(22):
+        cov[i, i] = var[i]
+    return {"k": 5, "K": (K1, K2), "est": est, "var": var, "lam": lam, "eta1": eh[0], "eta2": eh[1],
+            "p": p, "cov": cov}

@@ -1,0 +1,560 @@
+/*
+ * moss_oracle.c -- plain, slow CPU oracle of the Moss sampling path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this file's library.  It shares
+ * no code with the CUDA library: everything here (weights, alias tables, the
+ * Philox generator, sampling, classification, enumeration) is written out
+ * independently, sequentially and without any blocking or fusion.
+ *
+ * Paper: P. Wang, J. Tao, J. Zhao, X. Guan, "Moss: A Scalable Tool for
+ * Efficiently Sampling and Counting 4- and 5-Node Graphlets" (arXiv 1509.08089).
+ *
+ *  - vertex weights Gamma_v (Sec. 4.1.1), Gamma^(1)_v (Sec. 5.1.1),
+ *    Gamma^(2)_v (Sec. 5.1.2), Lambda_3 (eq. 2), Lambda_4 (Sec. 5.1.3),
+ *    the totals of Table 1;
+ *  - WeightRandomVertex (Sec. 4.1.3) realised with alias tables built by a
+ *    sequential sweep (Walker/Vose alias method, sweeping variant) in exact
+ *    integer arithmetic;
+ *  - RandomVertex(N_v - X) (Sec. 4.1.3): a uniform index over the d_v - |X|
+ *    admissible positions, skipping the excluded positions in list order;
+ *  - MOSS-4 (Algorithm 1), T-5 (Algorithm 3), Path-5 (Algorithm 4);
+ *  - the motif class of a CIS from the counts of spanning subgraphs
+ *    isomorphic to M_1^(4)/M_2^(4) (Sec. 4.1.2) or M_3^(5)/M_1^(5)/M_2^(5)
+ *    (Table 2);
+ *  - ESU enumeration (Wernicke 2006, cited in the paper's introduction) of
+ *    every connected induced k-subgraph, for exact ground truth.
+ *
+ * RNG: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Word i of sample s
+ * of method tag t under seed k is word (i mod 4) of
+ * Philox4x64-10(counter = {s, i div 4, t, 0}, key = {k, 0}).
+ * Word schedule (x_i = word i):
+ *   MOSS-4 : x0,x1 seed draw (column, threshold); x2,x3 sigma draw of u;
+ *            x4 w; x5 r.
+ *   T-5    : x0,x1 seed; x2,x3 sigma of u; x4 w; x5 r; x6 t.
+ *   Path-5 : x0,x1 seed; x2 r; x3 t; attempt a in {0,1}: x(4+4a),x(5+4a)
+ *            sigma draw of u, x(6+4a),x(7+4a) sigma draw of w, accepted when
+ *            the two positions differ; if both attempts collide, x12 draws u
+ *            from tau^(v) and x13 draws w from mu^(v,u) by the prefix-sum
+ *            method of Sec. 5.1.4.
+ * Index from a word: floor(x * m / 2^64).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+
+enum { M_MOSS4 = 0, M_T5 = 1, M_P5 = 2 };
+
+/* ------------------------------------------------------------ Philox ---- */
+/* Philox4x64-10: ten rounds of two 64x64->128 multiplies with a Weyl-sequence
+ * key schedule (Salmon et al. 2011, Sec. 4 and Table 2 of that paper). */
+void oracle_philox(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        u128 p0 = (u128)0xD2E7470EE14C6C93ULL * c0;
+        u128 p1 = (u128)0xCA5A826395121157ULL * c2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += 0x9E3779B97F4A7C15ULL;
+        k1 += 0xBB67AE8584CAA73BULL;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static uint64_t index_of(uint64_t x, uint64_t m) { return (uint64_t)(((u128)x * m) >> 64); }
+
+/* ------------------------------------------------------------ context ---- */
+typedef struct {
+    uint32_t n;
+    uint64_t nnz;
+    uint64_t *off;      /* n+1 */
+    uint32_t *col;      /* nnz, each list sorted */
+    uint64_t *deg;      /* d_v */
+    uint64_t *S, *Q;    /* sum (d_x-1), sum (d_x-1)^2 over x in N_v */
+    u128 *gam[3];       /* Gamma_v, Gamma^(1)_v, Gamma^(2)_v */
+    u128 tot[3];        /* Gamma, Gamma^(1), Gamma^(2) */
+    u128 lam3, lam4;
+    /* seed alias tables over V, one per weight */
+    u128 *sthr[3];      /* threshold in units where a column holds tot */
+    uint64_t *sT[3];    /* floor(thr 2^64 / tot), saturated */
+    uint32_t *salias[3];
+    /* sigma alias tables over each N_v (weights d_x - 1), local positions */
+    uint64_t *gthr;
+    uint32_t *galias;
+    uint64_t *acc;      /* ACC_sigma^(v)[i] exclusive prefix (Sec. 4.1.3) */
+} ctx;
+
+/* ---------------------------------------------------- alias (sweep) ---- */
+/* Alias table for m items with weights w[] (exact integers).  With
+ * q_j = w_j m and total W = sum w, every column holds W: item j keeps
+ * thr_j of its column and the rest W - thr_j belongs to alias_j.  Items with
+ * q_j < W ("light") are filled in index order from the current "heavy" item
+ * (q_j >= W, index order); a heavy item whose residue drops below W is filled
+ * from the next heavy item.  Zero weights are light with thr 0 and are never
+ * an alias.  thr is in [0, W]. */
+static int alias_sweep(uint64_t m, const u128 *w, u128 *thr, uint32_t *alias) {
+    u128 W = 0;
+    for (uint64_t j = 0; j < m; j++) W += w[j];
+    if (W == 0) {
+        for (uint64_t j = 0; j < m; j++) { thr[j] = 0; alias[j] = (uint32_t)j; }
+        return 0;
+    }
+    uint64_t *L = (uint64_t *)malloc(sizeof(uint64_t) * (m ? m : 1));
+    uint64_t *H = (uint64_t *)malloc(sizeof(uint64_t) * (m ? m : 1));
+    if (!L || !H) { free(L); free(H); return -1; }
+    uint64_t nl = 0, nh = 0;
+    for (uint64_t j = 0; j < m; j++) {
+        if (w[j] * m < W) L[nl++] = j; else H[nh++] = j;
+    }
+    uint64_t h = 0;
+    u128 r = w[H[0]] * m;                      /* residue of the current heavy item */
+    for (uint64_t i = 0; i < nl; i++) {
+        uint64_t j = L[i];
+        thr[j] = w[j] * m;
+        alias[j] = (uint32_t)H[h];
+        r -= W - w[j] * m;
+        while (r < W && h + 1 < nh) {          /* the heavy item turned light */
+            thr[H[h]] = r;
+            alias[H[h]] = (uint32_t)H[h + 1];
+            h++;
+            r = w[H[h]] * m - (W - thr[H[h - 1]]);
+        }
+    }
+    for (; h < nh; h++) { thr[H[h]] = W; alias[H[h]] = (uint32_t)H[h]; }
+    free(L);
+    free(H);
+    return 0;
+}
+
+/* floor(thr 2^64 / W) for thr <= W, saturated to 2^64-1 (binary long division) */
+static uint64_t quantize(u128 thr, u128 W) {
+    if (W == 0) return 0;
+    if (thr >= W) return UINT64_MAX;
+    uint64_t q = 0;
+    u128 r = thr;
+    for (int i = 0; i < 64; i++) {
+        int carry = (int)(r >> 127);
+        r <<= 1;
+        q <<= 1;
+        if (carry || r >= W) { r -= W; q |= 1; }
+    }
+    return q;
+}
+
+/* standalone entry for tests: weights as lo/hi u64 pairs */
+int oracle_alias_build(uint64_t m, const uint64_t *w_lohi, uint64_t *thr_lohi, uint32_t *alias) {
+    u128 *w = (u128 *)malloc(sizeof(u128) * (m ? m : 1));
+    u128 *t = (u128 *)malloc(sizeof(u128) * (m ? m : 1));
+    if (!w || !t) { free(w); free(t); return -1; }
+    for (uint64_t j = 0; j < m; j++) w[j] = ((u128)w_lohi[2 * j + 1] << 64) | w_lohi[2 * j];
+    int rc = alias_sweep(m, w, t, alias);
+    for (uint64_t j = 0; j < m; j++) { thr_lohi[2 * j] = (uint64_t)t[j]; thr_lohi[2 * j + 1] = (uint64_t)(t[j] >> 64); }
+    free(w);
+    free(t);
+    return rc;
+}
+
+/* ------------------------------------------------------ construction ---- */
+void oracle_free(ctx *c) {
+    if (!c) return;
+    free(c->off); free(c->col); free(c->deg); free(c->S); free(c->Q);
+    for (int l = 0; l < 3; l++) { free(c->gam[l]); free(c->sthr[l]); free(c->sT[l]); free(c->salias[l]); }
+    free(c->gthr); free(c->galias); free(c->acc);
+    free(c);
+}
+
+static u128 choose(uint64_t d, int k) {
+    if (d < (uint64_t)k) return 0;
+    u128 r = 1;
+    for (int i = 0; i < k; i++) r = r * (u128)(d - (uint64_t)i) / (u128)(i + 1);
+    return r;
+}
+
+ctx *oracle_new(uint32_t n, const uint64_t *row_ptr, const uint32_t *col) {
+    ctx *c = (ctx *)calloc(1, sizeof(ctx));
+    if (!c) return NULL;
+    c->n = n;
+    c->nnz = row_ptr[n];
+    uint64_t nnz1 = c->nnz ? c->nnz : 1;
+    c->off = (uint64_t *)malloc(sizeof(uint64_t) * (n + 1));
+    c->col = (uint32_t *)malloc(sizeof(uint32_t) * nnz1);
+    c->deg = (uint64_t *)malloc(sizeof(uint64_t) * (n ? n : 1));
+    c->S = (uint64_t *)calloc(n ? n : 1, sizeof(uint64_t));
+    c->Q = (uint64_t *)calloc(n ? n : 1, sizeof(uint64_t));
+    c->gthr = (uint64_t *)malloc(sizeof(uint64_t) * nnz1);
+    c->galias = (uint32_t *)malloc(sizeof(uint32_t) * nnz1);
+    c->acc = (uint64_t *)malloc(sizeof(uint64_t) * nnz1);
+    if (!c->off || !c->col || !c->deg || !c->S || !c->Q || !c->gthr || !c->galias || !c->acc) { oracle_free(c); return NULL; }
+    memcpy(c->off, row_ptr, sizeof(uint64_t) * (n + 1));
+    if (c->nnz) memcpy(c->col, col, sizeof(uint32_t) * c->nnz);
+    for (uint32_t v = 0; v < n; v++) c->deg[v] = c->off[v + 1] - c->off[v];
+
+    /* Initialization (Sec. 4.1.3): S_v, Q_v, then the three vertex weights */
+    for (uint32_t v = 0; v < n; v++) {
+        for (uint64_t p = c->off[v]; p < c->off[v + 1]; p++) {
+            uint64_t dx = c->deg[c->col[p]];
+            c->S[v] += dx - 1;
+            c->Q[v] += (dx - 1) * (dx - 1);
+        }
+    }
+    for (int l = 0; l < 3; l++) {
+        c->gam[l] = (u128 *)malloc(sizeof(u128) * (n ? n : 1));
+        c->sthr[l] = (u128 *)malloc(sizeof(u128) * (n ? n : 1));
+        c->sT[l] = (uint64_t *)malloc(sizeof(uint64_t) * (n ? n : 1));
+        c->salias[l] = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+        if (!c->gam[l] || !c->sthr[l] || !c->sT[l] || !c->salias[l]) { oracle_free(c); return NULL; }
+    }
+    for (uint32_t v = 0; v < n; v++) {
+        uint64_t d = c->deg[v];
+        u128 S = c->S[v];
+        /* Gamma_v = (d_v - 1) sum_{x in N_v} (d_x - 1)              (Sec. 4.1.1) */
+        c->gam[0][v] = d >= 1 ? (u128)(d - 1) * S : 0;
+        /* Gamma^(1)_v = (d_v - 1)(d_v - 2) sum (d_x - 1)            (Sec. 5.1.1) */
+        c->gam[1][v] = d >= 2 ? (u128)(d - 1) * (u128)(d - 2) * S : 0;
+        /* Gamma^(2)_v = (sum (d_x - 1))^2 - sum (d_x - 1)^2         (Sec. 5.1.2) */
+        c->gam[2][v] = S * S - (u128)c->Q[v];
+        for (int l = 0; l < 3; l++) c->tot[l] += c->gam[l][v];
+        c->lam3 += choose(d, 3);   /* Lambda_3 = sum C(d_v, 3)  (eq. 2)      */
+        c->lam4 += choose(d, 4);   /* Lambda_4 = sum C(d_v, 4)  (Sec. 5.1.3) */
+    }
+    /* WeightRandomVertex(V, pi), (V, rho^(1)), (V, rho^(2)) tables */
+    for (int l = 0; l < 3; l++) {
+        if (alias_sweep(n, c->gam[l], c->sthr[l], c->salias[l])) { oracle_free(c); return NULL; }
+        for (uint32_t v = 0; v < n; v++) c->sT[l][v] = quantize(c->sthr[l][v], c->tot[l]);
+    }
+    /* WeightRandomVertex(N_v, sigma^(v)) tables and ACC_sigma^(v) */
+    u128 *w = (u128 *)malloc(sizeof(u128) * nnz1), *t = (u128 *)malloc(sizeof(u128) * nnz1);
+    if (!w || !t) { free(w); free(t); oracle_free(c); return NULL; }
+    for (uint32_t v = 0; v < n; v++) {
+        uint64_t o = c->off[v], d = c->deg[v];
+        uint64_t run = 0;
+        for (uint64_t i = 0; i < d; i++) {
+            w[i] = c->deg[c->col[o + i]] - 1;
+            c->acc[o + i] = run;
+            run += (uint64_t)w[i];
+        }
+        if (alias_sweep(d, w, t, c->galias + o)) { free(w); free(t); oracle_free(c); return NULL; }
+        for (uint64_t i = 0; i < d; i++) c->gthr[o + i] = (uint64_t)t[i];
+    }
+    free(w);
+    free(t);
+    return c;
+}
+
+/* --------------------------------------------------------- accessors ---- */
+static void put128(uint64_t *dst, u128 x) { dst[0] = (uint64_t)x; dst[1] = (uint64_t)(x >> 64); }
+
+/* out[10] = lo/hi of Gamma, Gamma^(1), Gamma^(2), Lambda_3, Lambda_4 */
+void oracle_totals(const ctx *c, uint64_t *out) {
+    put128(out + 0, c->tot[0]);
+    put128(out + 2, c->tot[1]);
+    put128(out + 4, c->tot[2]);
+    put128(out + 6, c->lam3);
+    put128(out + 8, c->lam4);
+}
+
+void oracle_vertex(const ctx *c, uint64_t *deg, uint64_t *S, uint64_t *Q, uint64_t *gam_lohi /* 3*2n */) {
+    for (uint32_t v = 0; v < c->n; v++) {
+        deg[v] = c->deg[v];
+        S[v] = c->S[v];
+        Q[v] = c->Q[v];
+        for (int l = 0; l < 3; l++) put128(gam_lohi + (uint64_t)l * 2 * c->n + 2 * (uint64_t)v, c->gam[l][v]);
+    }
+}
+
+void oracle_seed_table(const ctx *c, int l, uint64_t *thr_lohi, uint64_t *T, uint32_t *alias) {
+    for (uint32_t v = 0; v < c->n; v++) {
+        put128(thr_lohi + 2 * (uint64_t)v, c->sthr[l][v]);
+        T[v] = c->sT[l][v];
+        alias[v] = c->salias[l][v];
+    }
+}
+
+void oracle_sigma_table(const ctx *c, uint64_t *thr, uint32_t *alias, uint64_t *acc) {
+    for (uint64_t p = 0; p < c->nnz; p++) { thr[p] = c->gthr[p]; alias[p] = c->galias[p]; acc[p] = c->acc[p]; }
+}
+
+/* --------------------------------------------------- graph primitives ---- */
+/* (a, b) in E: binary search of b in the sorted list N_a */
+static int is_edge(const ctx *c, uint32_t a, uint32_t b) {
+    uint64_t lo = c->off[a], hi = c->off[a + 1];
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (c->col[mid] < b) lo = mid + 1; else hi = mid;
+    }
+    return lo < c->off[a + 1] && c->col[lo] == b;
+}
+
+/* POS_{a,b}: the position of b in N_a (Sec. 4.1.3); b must be a neighbour */
+static uint64_t pos_of(const ctx *c, uint32_t a, uint32_t b) {
+    uint64_t lo = c->off[a], hi = c->off[a + 1];
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (c->col[mid] < b) lo = mid + 1; else hi = mid;
+    }
+    return lo - c->off[a];
+}
+
+/* ----------------------------------------------------- classification ---- */
+/* Table 2 of the paper: (phi^(1), phi^(2), phi^(3)) of M_1^(5)..M_21^(5). */
+static const int PHI5[21][3] = {
+    {0, 1, 0}, {0, 0, 1}, {1, 0, 0}, {1, 2, 0}, {2, 2, 0}, {0, 5, 0}, {2, 1, 0},
+    {2, 0, 1}, {4, 4, 0}, {4, 7, 0}, {5, 2, 1}, {4, 4, 1}, {6, 6, 0}, {10, 10, 1},
+    {9, 6, 1}, {12, 6, 2}, {10, 14, 0}, {20, 24, 1}, {20, 18, 2}, {36, 36, 3}, {60, 60, 5}};
+/* Sec. 4.1.2: (phi^(1), phi^(2)) of M_1^(4)..M_6^(4). */
+static const int PHI4[6][2] = {{1, 0}, {0, 1}, {4, 0}, {2, 1}, {6, 2}, {12, 4}};
+
+static int uf_find(int *p, int x) { while (p[x] != x) x = p[x]; return x; }
+
+/* Class of the graph on k vertices whose pair (i,j), i<j, listed in the order
+ * (0,1),(0,2),...,(k-2,k-1), is an edge iff its bit of mask is set.  The
+ * spanning subgraphs with k-1 edges are enumerated; each is a tree when it is
+ * connected, and its type follows from its degree sequence.  Returns the
+ * class 1..6 / 1..21, or 0 when the graph is not connected. */
+int oracle_classify(int k, uint32_t mask) {
+    int pa[10], pb[10], np = 0;
+    for (int i = 0; i < k; i++)
+        for (int j = i + 1; j < k; j++) { pa[np] = i; pb[np] = j; np++; }
+    int cnt_path = 0, cnt_star = 0, cnt_fork = 0, connected = 0;
+    for (uint32_t sub = 0; sub < (1u << np); sub++) {
+        if ((sub & mask) != sub) continue;
+        if (__builtin_popcount(sub) != k - 1) continue;
+        int deg[5] = {0, 0, 0, 0, 0}, par[5] = {0, 1, 2, 3, 4}, comps = k;
+        for (int e = 0; e < np; e++) {
+            if (!(sub >> e & 1)) continue;
+            deg[pa[e]]++;
+            deg[pb[e]]++;
+            int x = uf_find(par, pa[e]), y = uf_find(par, pb[e]);
+            if (x != y) { par[x] = y; comps--; }
+        }
+        if (comps != 1) continue;           /* not a spanning tree */
+        connected = 1;
+        int maxd = 0, n2 = 0;
+        for (int i = 0; i < k; i++) { if (deg[i] > maxd) maxd = deg[i]; if (deg[i] == 2) n2++; }
+        if (maxd == 2) cnt_path++;                    /* P4 / P5 */
+        else if (maxd == k - 1) cnt_star++;           /* 3-star / 4-star */
+        else if (k == 5 && maxd == 3 && n2 == 1) cnt_fork++; /* fork M_3^(5) */
+    }
+    if (!connected) return 0;
+    if (k == 4) {
+        for (int i = 0; i < 6; i++) if (PHI4[i][0] == cnt_path && PHI4[i][1] == cnt_star) return i + 1;
+    } else {
+        for (int i = 0; i < 21; i++)
+            if (PHI5[i][0] == cnt_fork && PHI5[i][1] == cnt_path && PHI5[i][2] == cnt_star) return i + 1;
+    }
+    return -1; /* unreachable for a connected graph */
+}
+
+static int classify_vertices(const ctx *c, int k, const uint32_t *x) {
+    uint32_t mask = 0;
+    int bit = 0;
+    for (int i = 0; i < k; i++)
+        for (int j = i + 1; j < k; j++, bit++)
+            if (is_edge(c, x[i], x[j])) mask |= 1u << bit;
+    return oracle_classify(k, mask);
+}
+
+/* ----------------------------------------------------------- sampling ---- */
+/* WeightRandomVertex(V, .) with the seed table of weight l */
+static uint32_t draw_seed(const ctx *c, int l, uint64_t xc, uint64_t xt) {
+    uint64_t col = index_of(xc, c->n);
+    return xt < c->sT[l][col] ? (uint32_t)col : c->salias[l][col];
+}
+
+/* WeightRandomVertex(N_v, sigma^(v)): returns the position in N_v */
+static uint64_t draw_sigma(const ctx *c, uint32_t v, uint64_t xc, uint64_t xt) {
+    uint64_t o = c->off[v];
+    uint64_t j = index_of(xc, c->deg[v]);
+    uint64_t y = index_of(xt, c->S[v]);
+    return y < c->gthr[o + j] ? j : c->galias[o + j];
+}
+
+/* RandomVertex(N_v - {positions e1 < e2 ...}): the j-th admissible position */
+static uint64_t skip1(uint64_t j, uint64_t e) { return j < e ? j : j + 1; }
+static uint64_t skip2(uint64_t j, uint64_t e1, uint64_t e2) {
+    uint64_t lo = e1 < e2 ? e1 : e2, hi = e1 < e2 ? e2 : e1;
+    if (j >= lo) j++;
+    if (j >= hi) j++;
+    return j;
+}
+
+/* Path-5 (Sec. 5.1.2): the pair (u, w) with probability tau_u mu_w, given as
+ * positions.  Up to two attempts draw u and w independently from sigma^(v)
+ * and keep the pair when u != w; because sigma_u sigma_w / (1 - sum sigma^2)
+ * equals tau_u mu_w, each accepted attempt has the paper's law.  When both
+ * attempts collide, u is drawn from tau^(v) and then w from mu^(v,u) with the
+ * ACC array and the interval of u removed (Sec. 5.1.4), which has that same
+ * law; the mixture is therefore exact. */
+static void draw_pair(const ctx *c, uint32_t v, const uint64_t *x, uint64_t *pu, uint64_t *pw) {
+    for (int a = 0; a < 2; a++) {
+        uint64_t iu = draw_sigma(c, v, x[4 + 4 * a], x[5 + 4 * a]);
+        uint64_t iw = draw_sigma(c, v, x[6 + 4 * a], x[7 + 4 * a]);
+        if (iu != iw) { *pu = iu; *pw = iw; return; }
+    }
+    uint64_t o = c->off[v], d = c->deg[v], S = c->S[v];
+    /* u from tau^(v): weight (d_u - 1)(S_v - (d_u - 1)), total Gamma^(2)_v */
+    u128 G = c->gam[2][v];
+    uint64_t y = index_of(x[12], (uint64_t)G);
+    u128 run = 0;
+    uint64_t iu = 0;
+    for (uint64_t i = 0; i < d; i++) {
+        uint64_t wi = c->deg[c->col[o + i]] - 1;
+        u128 tw = (u128)wi * (S - wi);
+        if ((u128)y < run + tw) { iu = i; break; }
+        run += tw;
+    }
+    /* w from mu^(v,u): rnd over [0, S_v) minus the interval of u */
+    uint64_t wu = c->deg[c->col[o + iu]] - 1;
+    uint64_t y2 = index_of(x[13], S - wu);
+    if (y2 >= c->acc[o + iu]) y2 += wu;
+    uint64_t iw = 0;
+    for (uint64_t i = 0; i < d; i++)
+        if (c->acc[o + i] <= y2) iw = i;   /* last i with ACC[i] <= rnd */
+    *pu = iu;
+    *pw = iw;
+}
+
+/* One sample from explicit words x[0..13].  Writes the k vertices in role
+ * order (v,u,w,r[,t]) and returns the class (0 = collision, no CIS). */
+static int sample_one(const ctx *c, int method, const uint64_t *x, uint32_t *out) {
+    if (method == M_MOSS4) {
+        /* Algorithm 1 */
+        uint32_t v = draw_seed(c, 0, x[0], x[1]);
+        uint64_t ov = c->off[v], dv = c->deg[v];
+        uint64_t iu = draw_sigma(c, v, x[2], x[3]);
+        uint32_t u = c->col[ov + iu];
+        uint32_t w = c->col[ov + skip1(index_of(x[4], dv - 1), iu)];
+        uint64_t ou = c->off[u], du = c->deg[u];
+        uint32_t r = c->col[ou + skip1(index_of(x[5], du - 1), pos_of(c, u, v))];
+        out[0] = v; out[1] = u; out[2] = w; out[3] = r; out[4] = 0;
+        if (r == u || r == w) return 0;
+        return classify_vertices(c, 4, out);
+    }
+    if (method == M_T5) {
+        /* Algorithm 3 */
+        uint32_t v = draw_seed(c, 1, x[0], x[1]);
+        uint64_t ov = c->off[v], dv = c->deg[v];
+        uint64_t iu = draw_sigma(c, v, x[2], x[3]);
+        uint32_t u = c->col[ov + iu];
+        uint64_t iw = skip1(index_of(x[4], dv - 1), iu);
+        uint32_t w = c->col[ov + iw];
+        uint32_t r = c->col[ov + skip2(index_of(x[5], dv - 2), iu, iw)];
+        uint64_t ou = c->off[u], du = c->deg[u];
+        uint32_t t = c->col[ou + skip1(index_of(x[6], du - 1), pos_of(c, u, v))];
+        out[0] = v; out[1] = u; out[2] = w; out[3] = r; out[4] = t;
+        if (t == w || t == r) return 0;
+        return classify_vertices(c, 5, out);
+    }
+    /* Algorithm 4 */
+    uint32_t v = draw_seed(c, 2, x[0], x[1]);
+    uint64_t ov = c->off[v];
+    uint64_t iu, iw;
+    draw_pair(c, v, x, &iu, &iw);
+    uint32_t u = c->col[ov + iu], w = c->col[ov + iw];
+    uint32_t r = c->col[c->off[u] + skip1(index_of(x[2], c->deg[u] - 1), pos_of(c, u, v))];
+    uint32_t t = c->col[c->off[w] + skip1(index_of(x[3], c->deg[w] - 1), pos_of(c, w, v))];
+    out[0] = v; out[1] = u; out[2] = w; out[3] = r; out[4] = t;
+    if (t == u || r == w || t == r) return 0;
+    return classify_vertices(c, 5, out);
+}
+
+/* validity of a method on this graph: its total weight must be positive */
+static int method_ok(const ctx *c, int method) {
+    if (method < 0 || method > 2) return 0;
+    return c->tot[method] != 0;
+}
+
+int oracle_sample_words(const ctx *c, int method, const uint64_t *words, uint32_t *verts, int *cls) {
+    if (!method_ok(c, method)) return -1;
+    *cls = sample_one(c, method, words, verts);
+    return 0;
+}
+
+/* words of sample s: x[i] = Philox4x64-10({s, i/4, tag, 0}, {seed, 0})[i%4] */
+static void sample_words(int method, uint64_t seed, uint64_t s, uint64_t *x) {
+    for (uint64_t b = 0; b < 4; b++) {
+        uint64_t ctr[4] = {s, b, (uint64_t)method, 0}, key[2] = {seed, 0};
+        oracle_philox(ctr, key, x + 4 * b);
+    }
+}
+
+/* Run samples s in [first, first+count) of one method: counts[0] collisions,
+ * counts[i] class i.  classes/verts (nullable) receive per-sample records. */
+int oracle_run(const ctx *c, int method, uint64_t seed, uint64_t first, uint64_t count,
+               uint64_t *counts, uint8_t *classes, uint32_t *verts) {
+    for (int i = 0; i < 22; i++) counts[i] = 0;
+    if (!method_ok(c, method)) return -1;
+    uint64_t x[16];
+    uint32_t vv[5];
+    for (uint64_t k = 0; k < count; k++) {
+        sample_words(method, seed, first + k, x);
+        int cls = sample_one(c, method, x, vv);
+        if (cls < 0) return -2;
+        counts[cls]++;
+        if (classes) classes[k] = (uint8_t)cls;
+        if (verts) memcpy(verts + 5 * k, vv, sizeof(vv));
+    }
+    return 0;
+}
+
+/* --------------------------------------------------------------- ESU ---- */
+/* Wernicke's ESU: every connected induced k-subgraph is produced once, grown
+ * from its smallest vertex through exclusive neighbourhoods. */
+typedef struct { const ctx *c; int k; uint64_t *counts; } esu_state;
+
+static int in_set(const uint32_t *s, int m, uint32_t x) {
+    for (int i = 0; i < m; i++) if (s[i] == x) return 1;
+    return 0;
+}
+
+static void esu_extend(esu_state *st, uint32_t *sub, int ns, uint32_t *ext, uint64_t next, uint32_t root) {
+    if (ns == st->k) {
+        st->counts[classify_vertices(st->c, st->k, sub)]++;
+        return;
+    }
+    const ctx *c = st->c;
+    uint64_t ne = next;
+    while (ne > 0) {
+        uint32_t w = ext[--ne];
+        /* new extension = rest of ext + exclusive neighbours of w that exceed root */
+        uint64_t cap = ne + c->deg[w];
+        uint32_t *ext2 = (uint32_t *)malloc(sizeof(uint32_t) * (cap ? cap : 1));
+        uint64_t n2 = ne;
+        memcpy(ext2, ext, sizeof(uint32_t) * ne);
+        for (uint64_t p = c->off[w]; p < c->off[w + 1]; p++) {
+            uint32_t u = c->col[p];
+            if (u <= root || in_set(sub, ns, u) || in_set(ext, ne, u) || u == w) continue;
+            int adj = 0;
+            for (int i = 0; i < ns && !adj; i++) adj = is_edge(c, sub[i], u);
+            if (!adj && !in_set(ext2, n2, u)) ext2[n2++] = u;
+        }
+        sub[ns] = w;
+        esu_extend(st, sub, ns + 1, ext2, n2, root);
+        free(ext2);
+    }
+}
+
+/* exact counts of connected induced k-subgraphs by class (counts[1..]) */
+int oracle_esu(const ctx *c, int k, uint64_t *counts) {
+    for (int i = 0; i < 22; i++) counts[i] = 0;
+    if (k != 4 && k != 5) return -1;
+    esu_state st = {c, k, counts};
+    uint32_t sub[5];
+    for (uint32_t v = 0; v < c->n; v++) {
+        uint64_t d = c->deg[v];
+        uint32_t *ext = (uint32_t *)malloc(sizeof(uint32_t) * (d ? d : 1));
+        uint64_t ne = 0;
+        for (uint64_t p = c->off[v]; p < c->off[v + 1]; p++) if (c->col[p] > v) ext[ne++] = c->col[p];
+        sub[0] = v;
+        esu_extend(&st, sub, 1, ext, ne, v);
+        free(ext);
+    }
+    return 0;
+}

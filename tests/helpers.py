@@ -1,0 +1,125 @@
+"""Independent test helpers: motif identification with networkx, brute-force
+subgraph enumeration and the paper's printed phi tables (tests/golden)."""
+from __future__ import annotations
+
+import itertools
+import os
+from functools import lru_cache
+
+import networkx as nx
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _read_table(name: str) -> dict[int, tuple[int, ...]]:
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            vals = [int(x) for x in line.split()]
+            out[vals[0]] = tuple(vals[1:])
+    return out
+
+
+def table2() -> dict[int, tuple[int, int, int]]:
+    """Table 2: class -> (phi1 forks, phi2 5-paths, phi3 4-stars)."""
+    return _read_table("table2_phi5.txt")
+
+
+def phi4() -> dict[int, tuple[int, int]]:
+    """Sec. 4.1.2: class -> (phi1 3-paths, phi2 3-stars)."""
+    return _read_table("phi4.txt")
+
+
+def _count_copies(H: nx.Graph, P: nx.Graph) -> int:
+    """Number of (not necessarily induced) subgraphs of H isomorphic to P."""
+    mono = sum(1 for _ in nx.algorithms.isomorphism.GraphMatcher(H, P).subgraph_monomorphisms_iter())
+    aut = sum(1 for _ in nx.algorithms.isomorphism.GraphMatcher(P, P).isomorphisms_iter())
+    assert mono % aut == 0
+    return mono // aut
+
+
+def _patterns(k: int):
+    if k == 4:
+        return [nx.path_graph(4), nx.star_graph(3)]
+    fork = nx.Graph([(0, 1), (0, 2), (0, 3), (1, 4)])
+    return [fork, nx.path_graph(5), nx.star_graph(4)]
+
+
+@lru_cache(maxsize=None)
+def motif_atlas(k: int):
+    """[(graph, signature, class)] for every connected graph on k vertices;
+    the class is the row of the paper's table carrying that signature."""
+    table = phi4() if k == 4 else table2()
+    by_sig = {v: i for i, v in table.items()}
+    out = []
+    for H in nx.graph_atlas_g():
+        if H.number_of_nodes() != k or not nx.is_connected(H):
+            continue
+        sig = tuple(_count_copies(H, P) for P in _patterns(k))
+        out.append((H, sig, by_sig.get(sig)))
+    return out
+
+
+def nx_class(k: int, edges) -> int:
+    """Class of the graph on vertices 0..k-1 with the given edges (0 if
+    disconnected), identified by isomorphism against the atlas."""
+    G = nx.Graph()
+    G.add_nodes_from(range(k))
+    G.add_edges_from(edges)
+    if not nx.is_connected(G):
+        return 0
+    for H, _sig, cls in motif_atlas(k):
+        if H.number_of_edges() == G.number_of_edges() and nx.is_isomorphic(G, H):
+            return cls
+    raise AssertionError("no atlas match")
+
+
+@lru_cache(maxsize=None)
+def mask_classes(k: int) -> tuple[int, ...]:
+    pairs = [(i, j) for i in range(k) for j in range(i + 1, k)]
+    out = []
+    for mask in range(1 << len(pairs)):
+        out.append(nx_class(k, [pairs[b] for b in range(len(pairs)) if mask >> b & 1]))
+    return tuple(out)
+
+
+def adjacency_sets(row_ptr, col):
+    n = len(row_ptr) - 1
+    return [set(int(x) for x in col[int(row_ptr[v]):int(row_ptr[v + 1])]) for v in range(n)]
+
+
+def induced_class(adj, verts) -> int:
+    """Class of the subgraph induced by verts (ordered), via the mask table."""
+    k = len(verts)
+    mask = 0
+    b = 0
+    for i in range(k):
+        for j in range(i + 1, k):
+            if verts[j] in adj[verts[i]]:
+                mask |= 1 << b
+            b += 1
+    return mask_classes(k)[mask]
+
+
+def brute_force_cis(row_ptr, col, k: int) -> dict[frozenset, int]:
+    """Every connected induced k-subgraph (as a vertex set) with its class,
+    by scanning all k-subsets (tiny graphs only)."""
+    adj = adjacency_sets(row_ptr, col)
+    n = len(adj)
+    out = {}
+    for vs in itertools.combinations(range(n), k):
+        c = induced_class(adj, vs)
+        if c:
+            out[frozenset(vs)] = c
+    return out
+
+
+def class_counts(cis: dict, nclass: int) -> np.ndarray:
+    c = np.zeros(22, dtype=np.int64)
+    for cls in cis.values():
+        c[cls] += 1
+    return c

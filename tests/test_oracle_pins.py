@@ -1,0 +1,215 @@
+"""Pins of the oracle's building blocks against things other than itself (CPU).
+
+* Philox4x64-10 against numpy's independent implementation.
+* Alias tables: exact integer mass identity (each item gets w_j / W).
+* Vertex weights Gamma, Gamma^(1), Gamma^(2), Lambda_3, Lambda_4 against
+  brute-force counts of the draw sequences / subgraphs they stand for
+  (Table 1, Sec. 4.1.1, Sec. 5.1.1, Sec. 5.1.2, eq. (2)).
+* The classifier against networkx isomorphism for all masks (Table 2).
+* The identities Lambda_3 = sum phi^(2) n_i (eq. 2) and Lambda_4 = sum phi^(3)
+  eta_i (Sec. 5.1.3) on exact ESU counts, and ESU against all-subset scans.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import adjacency_sets, brute_force_cis, class_counts, mask_classes, phi4, table2
+
+TWO64 = 1 << 64
+
+
+# ------------------------------------------------------------------ Philox --
+@pytest.mark.parametrize("seed", [0, 1, 42, 2**63 + 5])
+def test_philox_matches_numpy(seed):
+    rng = np.random.default_rng(seed % 1000)
+    for _ in range(20):
+        ctr = [int(x) for x in rng.integers(0, 2**63, size=4, dtype=np.int64)]
+        key = [seed % TWO64, int(rng.integers(0, 2**63))]
+        bg = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=np.array(ctr, dtype=np.uint64))
+        # numpy advances the counter by one before producing a block
+        ref = [int(x) for x in bg.random_raw(4)]
+        nxt = [(ctr[0] + 1) % TWO64] + ctr[1:]
+        if nxt[0] == 0:
+            nxt[1] = (nxt[1] + 1) % TWO64
+        assert oracle.philox4x64(nxt, key) == ref
+
+
+# ------------------------------------------------------------------- alias --
+def alias_mass_ok(w, thr, alias):
+    m = len(w)
+    W = sum(w)
+    mass = [0] * m
+    for j in range(m):
+        assert 0 <= thr[j] <= W
+        mass[j] += thr[j]
+        if alias[j] != j:
+            mass[alias[j]] += W - thr[j]
+        else:
+            assert thr[j] == W or W == 0
+    for j in range(m):
+        assert mass[j] == w[j] * m, (j, mass[j], w[j] * m)
+        if w[j] == 0:
+            assert all(alias[i] != j or i == j for i in range(m))
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_alias_mass_identity(case):
+    rng = np.random.default_rng(case)
+    m = int(rng.integers(1, 300))
+    kind = case % 4
+    if kind == 0:
+        w = [int(x) for x in rng.integers(0, 50, size=m)]
+    elif kind == 1:   # huge 128-bit weights
+        w = [int(rng.integers(0, 2**62)) * int(rng.integers(0, 2**40)) for _ in range(m)]
+    elif kind == 2:   # equal weights: every column full
+        w = [7] * m
+    else:             # one dominant weight and many zeros
+        w = [0] * m
+        w[int(rng.integers(0, m))] = 10**20
+        w[int(rng.integers(0, m))] += 3
+    if sum(w) == 0:
+        w[0] = 1
+    thr, alias = oracle.alias_build(w)
+    alias_mass_ok(w, thr, alias)
+
+
+def test_alias_all_zero_weights():
+    thr, alias = oracle.alias_build([0, 0, 0])
+    assert thr == [0, 0, 0] and alias == [0, 1, 2]
+
+
+def test_seed_threshold_quantisation():
+    rp, col = synth.workload("cl_n2k")
+    g = oracle.OracleGraph(rp, col)
+    for which in range(3):
+        thr, T, alias = g.seed_table(which)
+        W = g.Gamma[which]
+        for v in range(0, g.n, 7):
+            exp = min(thr[v] * TWO64 // W, TWO64 - 1)
+            assert int(T[v]) == exp
+
+
+def test_tables_of_workload_have_exact_mass():
+    rp, col = synth.workload("cl_n2k")
+    g = oracle.OracleGraph(rp, col)
+    deg, S, Q, gam = g.vertex()
+    for which in range(3):
+        thr, _T, alias = g.seed_table(which)
+        alias_mass_ok(gam[which], thr, [int(a) for a in alias])
+    gthr, galias, acc = g.sigma_table()
+    for v in range(0, g.n, 13):
+        o, d = int(rp[v]), int(rp[v + 1] - rp[v])
+        w = [int(deg[int(x)]) - 1 for x in col[o:o + d]]
+        if d:
+            alias_mass_ok(w, [int(x) for x in gthr[o:o + d]], [int(x) for x in galias[o:o + d]])
+            assert [int(x) for x in acc[o:o + d]] == list(itertools.accumulate([0] + w[:-1]))
+
+
+# ----------------------------------------------------------------- weights --
+def brute_weights(rp, col):
+    """Count the draw sequences each weight stands for, by enumeration."""
+    adj = adjacency_sets(rp, col)
+    n = len(adj)
+    G = G1 = G2 = 0
+    for v in range(n):
+        Nv = sorted(adj[v])
+        for u in Nv:
+            for w in Nv:
+                if w == u:
+                    continue
+                for r in adj[u]:
+                    if r != v:
+                        G += 1              # (v, u, w in N_v-{u}, r in N_u-{v})
+                for r in Nv:
+                    if r in (u, w):
+                        continue
+                    for t in adj[u]:
+                        if t != v:
+                            G1 += 1         # T-5 sequences: w, r ordered distinct
+                for r in adj[u]:
+                    if r == v:
+                        continue
+                    for t in adj[w]:
+                        if t != v:
+                            G2 += 1         # Path-5 sequences (u, w ordered, distinct)
+    L3 = sum(1 for v in range(n) for _ in itertools.combinations(adj[v], 3))
+    L4 = sum(1 for v in range(n) for _ in itertools.combinations(adj[v], 4))
+    return G, G1, G2, L3, L4
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_weights_count_draw_sequences(seed):
+    rp, col = synth.gnp(11, 0.4, seed)
+    g = oracle.OracleGraph(rp, col)
+    G, G1, G2, L3, L4 = brute_weights(rp, col)
+    # Gamma counts ordered (v,u,w,r) sequences; Gamma^(1) counts (v,u,w,r,t)
+    # with (w, r) an ordered pair, i.e. 2x the unordered choice the
+    # probability 1/((d_v-1)(d_v-2)) refers to; Gamma^(2) counts ordered (u, w).
+    assert g.Gamma[0] == G
+    assert g.Gamma[1] == G1
+    assert g.Gamma[2] == G2
+    assert g.Lambda3 == L3
+    assert g.Lambda4 == L4
+
+
+def test_weights_on_star_cycle_complete():
+    g = oracle.OracleGraph(*synth.star(6))
+    assert g.Gamma == [0, 0, 0] and g.Lambda3 == 20 and g.Lambda4 == 15
+    g = oracle.OracleGraph(*synth.cycle(9))
+    assert g.Gamma == [18, 0, 18] and g.Lambda3 == 0
+    n = 7
+    g = oracle.OracleGraph(*synth.complete(n))
+    d = n - 1
+    assert g.Gamma[0] == n * (d - 1) * d * (d - 1)
+
+
+# ---------------------------------------------------------------- classify --
+@pytest.mark.parametrize("k", [4, 5])
+def test_classifier_matches_networkx_on_all_masks(k):
+    ref = mask_classes(k)
+    for mask in range(len(ref)):
+        assert oracle.classify(k, mask) == ref[mask], mask
+
+
+def test_table2_signatures_are_unique_and_complete():
+    from helpers import motif_atlas
+    at5 = motif_atlas(5)
+    assert len(at5) == 21
+    assert sorted(c for _, _, c in at5) == list(range(1, 22))
+    at4 = motif_atlas(4)
+    assert sorted(c for _, _, c in at4) == list(range(1, 7))
+
+
+# -------------------------------------------------------------- identities --
+@pytest.mark.parametrize("seed", [5, 6])
+def test_esu_matches_all_subsets_and_identities(seed):
+    rp, col = synth.gnp(12, 0.45, seed)
+    g = oracle.OracleGraph(rp, col)
+    for k in (4, 5):
+        ref = class_counts(brute_force_cis(rp, col, k), 22)
+        got = g.esu(k).astype(np.int64)
+        assert (got == ref).all(), (k, got, ref)
+    n4 = g.esu(4).astype(np.int64)
+    p4 = phi4()
+    # eq. (2): Lambda_3 = sum_i phi^(2)_i n_i
+    assert g.Lambda3 == sum(p4[i][1] * int(n4[i]) for i in range(1, 7))
+    n5 = g.esu(5).astype(np.int64)
+    t2 = table2()
+    # Sec. 5.1.3: Lambda_4 = sum_i phi^(3)_i eta_i
+    assert g.Lambda4 == sum(t2[i][2] * int(n5[i]) for i in range(1, 22))
+
+
+def test_identities_on_power_law_graph():
+    rp, col = synth.chung_lu(300, 2.3, 6.0, 40.0, seed=3)
+    g = oracle.OracleGraph(rp, col)
+    n4 = g.esu(4).astype(np.int64)
+    p4 = phi4()
+    assert g.Lambda3 == sum(p4[i][1] * int(n4[i]) for i in range(1, 7))
+    n5 = g.esu(5).astype(np.int64)
+    t2 = table2()
+    assert g.Lambda4 == sum(t2[i][2] * int(n5[i]) for i in range(1, 22))

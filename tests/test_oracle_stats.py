@@ -1,0 +1,141 @@
+"""Statistical pins of the oracle's estimators against exact ESU counts (CPU).
+
+* Unbiasedness (Theorems 3, 7, 9, 10): the mean over R independent seeds lies
+  within z sigma / sqrt(R) of the exact count, sigma^2 being the paper's
+  variance evaluated at the exact counts.
+* Variances: the empirical variance over R = 1000 seeds, divided by the
+  closed form at the exact counts, lies in the band
+  1 +- z sqrt(2/(R-1) + kappa/R), kappa the excess kurtosis of the scaled
+  binomial count (the chi^2_{R-1}/(R-1) band widened for non-normality).
+z = 4.5 keeps the family-wise false-alarm rate far below 1% over all classes.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle.finalize import PHI4, PHI5
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "esu_counts.json")))
+Z = 4.5
+
+
+def var_moss4(eta, K, G):
+    v = np.zeros(7)
+    p = np.zeros(7)
+    for i in (1, 3, 4, 5, 6):
+        p[i] = 2 * PHI4[i - 1, 0] / G
+        v[i] = eta[i] / K * (1 / p[i] - eta[i])
+    v[2] = (eta[4] / p[4] + 4 * eta[5] / p[5] + 16 * eta[6] / p[6] - (eta[4] + 2 * eta[5] + 4 * eta[6]) ** 2) / K
+    return v, p
+
+
+def kurt(q, K):
+    q = min(max(q, 1e-300), 1 - 1e-16)
+    return (1 - 6 * q * (1 - q)) / (K * q * (1 - q))
+
+
+@pytest.fixture(scope="module")
+def g200():
+    rp, col = synth.chung_lu(200, 2.3, 6.0, 30.0, seed=7)
+    g = oracle.OracleGraph(rp, col)
+    assert str(g.Gamma[0]) == GOLD["cl_n200"]["Gamma"][0]
+    return g
+
+
+def test_moss4_unbiased_on_n2k_workload():
+    rp, col = synth.workload("cl_n2k")
+    g = oracle.OracleGraph(rp, col)
+    eta = np.array(GOLD["cl_n2k"]["esu4"], dtype=np.float64)
+    R, K = 30, 100_000
+    est = np.array([g.estimate(4, K, seed=1000 + s)["est"] for s in range(R)])
+    v, _ = var_moss4(eta, K, float(g.Gamma[0]))
+    for i in range(1, 7):
+        assert abs(est[:, i].mean() - eta[i]) < Z * math.sqrt(v[i] / R), (i, est[:, i].mean(), eta[i])
+
+
+def test_moss4_variance_matches_theorem3(g200):
+    eta = np.array(GOLD["cl_n200"]["esu4"], dtype=np.float64)
+    R, K = 1000, 2000
+    est = np.array([g200.estimate(4, K, seed=s)["est"] for s in range(R)])
+    G = float(g200.Gamma[0])
+    v, p = var_moss4(eta, K, G)
+    for i in range(1, 7):
+        assert abs(est[:, i].mean() - eta[i]) < Z * math.sqrt(v[i] / R), i
+        q = p[i] * eta[i] if i != 2 else None
+        if i != 2 and K * q < 30:
+            continue
+        k = kurt(q, K) if i != 2 else 0.05
+        ratio = est[:, i].var(ddof=1) / v[i]
+        assert abs(ratio - 1) < Z * math.sqrt(2 / (R - 1) + k / R), (i, ratio)
+
+
+def test_moss5_fixed_lambda_matches_theorem10(g200):
+    """With lambda computed from the exact counts (a constant), the mix
+    estimator is exactly unbiased and its variance is Theorem 10's."""
+    eta = np.array(GOLD["cl_n200"]["esu5"], dtype=np.float64)
+    R, B = 1000, 4000
+    runs = [g200.estimate(5, B, seed=s, eta=eta) for s in range(R)]
+    est = np.array([r["est"] for r in runs])
+    ref = runs[0]
+    K1, K2 = ref["K"]
+    p = ref["p"]
+    for i in range(1, 22):
+        v = ref["var"][i]               # closed form at the exact counts
+        assert abs(est[:, i].mean() - eta[i]) < Z * math.sqrt(v / R) + 1e-9, (i, est[:, i].mean(), eta[i])
+        if i == 2:
+            ratio = est[:, i].var(ddof=1) / v
+            assert abs(ratio - 1) < Z * math.sqrt(2 / (R - 1) + 0.05 / R), ratio
+            continue
+        q = [p[l, i] * eta[i] for l in range(2)]
+        hits = [K1 * q[0], K2 * q[1]]
+        if max(hits) < 30:
+            continue
+        k = max(kurt(q[l], (K1, K2)[l]) for l in range(2) if q[l] > 0)
+        ratio = est[:, i].var(ddof=1) / v
+        assert abs(ratio - 1) < Z * math.sqrt(2 / (R - 1) + k / R), (i, ratio)
+    # Cov(eta_i, eta_j) of Theorem 10 on the most correlated pairs; the
+    # sample covariance has variance ~ (V_i V_j + C_ij^2) / R
+    cov = ref["cov"]
+    cand = [i for i in range(1, 22) if i != 2 and ref["var"][i] > 0]
+    pairs = sorted(((abs(cov[i, j]) / math.sqrt(ref["var"][i] * ref["var"][j]), i, j)
+                    for i in cand for j in cand if i < j), reverse=True)[:3]
+    for corr, i, j in pairs:
+        assert corr > 0.1
+        emp = np.cov(est[:, i], est[:, j])[0, 1]
+        se = math.sqrt((ref["var"][i] * ref["var"][j] + cov[i, j] ** 2) / R)
+        assert abs(emp - cov[i, j]) < Z * se, (i, j, emp, cov[i, j])
+
+
+def test_moss5_plugin_lambda_is_nearly_unbiased(g200):
+    """With the plug-in lambda the mix is no longer exactly unbiased
+    (Theorem 10 assumes fixed weights); its bias must stay small."""
+    eta = np.array(GOLD["cl_n200"]["esu5"], dtype=np.float64)
+    R, B = 400, 8000
+    runs = [g200.estimate(5, B, seed=5000 + s) for s in range(R)]
+    est = np.array([r["est"] for r in runs])
+    exact = g200.estimate(5, B, seed=0, eta=eta)
+    for i in range(1, 22):
+        if eta[i] == 0:
+            assert np.all(est[:, i] == 0) or i == 2
+            continue
+        sd = math.sqrt(exact["var"][i])
+        assert abs(est[:, i].mean() - eta[i]) < 6 * sd / math.sqrt(R) + 0.02 * eta[i], i
+
+
+def test_sampled_classes_stay_in_omega(g200):
+    m1 = g200.run(oracle.T5, 3, 50_000)
+    m2 = g200.run(oracle.PATH5, 3, 50_000)
+    for i in range(1, 22):
+        if PHI5[i - 1, 0] == 0:
+            assert m1[i] == 0
+        if PHI5[i - 1, 1] == 0:
+            assert m2[i] == 0
+    m0 = g200.run(oracle.MOSS4, 3, 50_000)
+    assert m0[2] == 0
