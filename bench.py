@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the whole sampling path on one GPU per rank.
+
+A step is one pass of the path over the 1M-edge workload: load the CSR
+(already in HBM) and validate it with the vertex weights (a0), build the
+alias tables (a1), draw and classify the samples and count them (a2-a8),
+finalize the estimates (a9), free the graph.  Default workload: Chung-Lu
+n = 100,000, exponent 2.2, mean degree 20, max degree 5,000, seed 1 (~1M
+edges), k = 5 (T-5 + Path-5), budget 1e8 samples per rank (weak scaling).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "5-node samples/s at 1M edges"
+WORKLOAD = ("Chung-Lu n=100,000, exponent 2.2, mean degree 20, max degree 5,000, seed 1 (~1M edges), "
+            "k=5 (T-5 + Path-5, K1=K2), sorted uint32 CSR")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--workload", default="cl_n100k")
+    p.add_argument("--k", type=int, default=5)
+    p.add_argument("--budget", type=int, default=100_000_000)
+    p.add_argument("--seed", type=int, default=42)
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------- CPU (oracle) --
+def _oracle_worker(args):
+    """One process of the CPU baseline: build the oracle's tables for the
+    workload, then draw its share of samples of each sub-method."""
+    workload, k, seed, shares = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    import synth
+    rp, col = synth.workload(workload)
+    t0 = time.perf_counter()
+    g = oracle.OracleGraph(rp, col)
+    t1 = time.perf_counter()
+    for method, first, count in shares:
+        g.run(method, seed, count, first=first)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1, sum(c for _, _, c in shares)
+
+
+def oracle_pass(pool, cores, workload, k, seed, per_worker):
+    methods = [0] if k == 4 else [1, 2]
+    jobs = []
+    for w in range(cores):
+        shares = [(m, w * per_worker // len(methods), per_worker // len(methods)) for m in methods]
+        jobs.append((workload, k, seed, shares))
+    t0 = time.perf_counter()
+    res = list(pool.map(_oracle_worker, jobs))
+    wall = time.perf_counter() - t0
+    build = max(r[0] for r in res)
+    sample_wall = max(r[1] for r in res)
+    samples = sum(r[2] for r in res)
+    return build, sample_wall, samples, wall
+
+
+def oracle_rate(build, sample_wall, samples, budget):
+    """Whole-path throughput of the oracle extrapolated to the full budget:
+    one table build plus budget samples at the measured sampling rate."""
+    rate = samples / sample_wall
+    return budget / (build + budget / rate), rate
+
+
+def calibrate_per_worker(workload, k, seed, seconds):
+    import oracle
+    import synth
+    rp, col = synth.workload(workload)
+    g = oracle.OracleGraph(rp, col)
+    methods = [0] if k == 4 else [1, 2]
+    n = 20_000
+    t0 = time.perf_counter()
+    for m in methods:
+        g.run(m, seed, n // len(methods))
+    per = (time.perf_counter() - t0) / n
+    return max(len(methods), int(seconds / per))
+
+
+def make_pool(cores):
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    return cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    per_worker = calibrate_per_worker(args.workload, args.k, args.seed, 3.0)
+    with make_pool(cores) as pool:
+        for _ in range(args.warmup):
+            oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker)
+        vals, walls = [], []
+        for _ in range(args.steps):
+            b, sw, n, wall = oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker)
+            vals.append(oracle_rate(b, sw, n, args.budget)[0])
+            walls.append(wall)
+    v = statistics.median(vals)
+    sample = (f"{per_worker * cores} samples per step over {cores} processes (T-5/Path-5 split evenly) plus one "
+              f"table build; rate extrapolated to the {args.budget}-sample budget")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * args.budget / v,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "budget": args.budget, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------- clocks --
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/moss_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- GPU --
+def run_gpu(args):
+    import torch
+    import torch.distributed as tdist
+
+    import synth
+    import paper_1509_08089_gb300 as moss
+    from paper_1509_08089_gb300.dist import estimate_weak, sub_budgets
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
+    # the CPU-baseline pool is spawned before the first GPU call
+    pool = None
+    cores = os.cpu_count() or 1
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = make_pool(cores)
+    torch.cuda.set_device(local)
+    dev = local
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    moss.load()
+    k = args.k
+    kmask = 1 << k
+    rp, col = synth.workload(args.workload)
+    stream = torch.cuda.current_stream(dev)
+    rp_d = torch.from_numpy(rp.view(np.int64)).to(f"cuda:{dev}")
+    col_d = torch.from_numpy(col.view(np.int32)).to(f"cuda:{dev}")
+    rp_h = torch.from_numpy(rp.view(np.int64)).pin_memory()
+    col_h = torch.from_numpy(col.view(np.int32)).pin_memory()
+    l2_flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{dev}")   # > 126 MB L2
+
+    def allreduce(counts: np.ndarray) -> np.ndarray:
+        t = torch.from_numpy(counts).to(f"cuda:{dev}")
+        tdist.all_reduce(t)
+        return t.cpu().numpy()
+
+    def step(src_rp, src_col, seed):
+        h = moss.moss_graph_load_csr(src_rp, src_col, device=dev, stream=stream)
+        try:
+            moss.moss_build_tables(h, kmask, stream)
+            if world == 1:
+                r = moss.result_dict(moss.moss_sample_estimate(h, k, args.budget, seed, stream))
+            else:
+                class _G:  # the weak-scaling helper wants .handle/.device/.stats()
+                    handle, device = h, dev
+
+                    @staticmethod
+                    def stats():
+                        return moss.moss_graph_stats(h)
+                r = estimate_weak(_G, k, args.budget, seed, rank, world, allreduce, stream)
+        finally:
+            moss.moss_graph_free(h)
+        return r
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+
+    for i in range(args.warmup):
+        step(rp_d, col_d, args.seed + i)
+    torch.cuda.synchronize()
+    clocks = Clocks(dev)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    results = []
+    for i in range(args.steps):
+        l2_flush.zero_()                 # evict the previous step's tables from L2
+        ev[i][0].record(stream)
+        results.append(step(rp_d, col_d, args.seed + 100 + i))
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=f"cuda:{dev}", dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    samples_per_step = args.budget * world
+    value = samples_per_step / (ms / 1000.0)
+
+    # ---- end to end through the public API from pinned host buffers
+    e2e_t = []
+    for i in range(args.e2e_steps):
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(rp_h, col_h, args.seed + 200 + i)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_s], device=f"cuda:{dev}", dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = rp.nbytes + col.nbytes
+    d2h = __import__("ctypes").sizeof(moss.moss_result)
+
+    # ---- the dominant kernel alone (same launch as inside the step)
+    roof = None
+    h = moss.moss_graph_load_csr(rp_d, col_d, device=dev, stream=stream)
+    try:
+        moss.moss_build_tables(h, kmask, stream)
+        counts = torch.zeros(22, dtype=torch.int64, device=f"cuda:{dev}")
+        times = {}
+        for m, K in sub_budgets(k, args.budget):
+            moss.moss_sample_counts(h, m, 0, K, args.seed, counts, stream)      # warm
+            reps = []
+            for rep in range(3):
+                l2_flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                moss.moss_sample_counts(h, m, 0, K, args.seed, counts, stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                reps.append(a.elapsed_time(b))
+            times[m] = (K, statistics.median(reps))
+    finally:
+        moss.moss_graph_free(h)
+    sect = None
+    spath = os.path.join(ROOT, "tests", "golden", f"sectors_{args.workload}.json")
+    if os.path.exists(spath):
+        sect = json.load(open(spath))
+    name = {0: "MOSS4", 1: "T5", 2: "PATH5"}
+    dom = max(times, key=lambda m: times[m][1])
+    peaks = {}
+    ppath = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(ppath):
+        peaks = json.load(open(ppath))
+    peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    if sect is not None:
+        K, tms = times[dom]
+        spb = sect[name[dom]]["sectors_per_sample"]
+        ach = spb * 32.0 * K / (tms / 1000.0) / 1e9
+        roof = {"bound": "hbm", "kernel": f"k_sample<{dom}> ({name[dom]})", "achieved": ach, "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                "algorithmic_bytes_per_sample": spb * 32.0, "samples_per_launch": K,
+                "launch_ms": tms, "kernel_times_ms": {name[m]: times[m][1] for m in times}}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "budget_per_gpu": args.budget, "seed": args.seed,
+                   "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}"},
+        "e2e": {"value": samples_per_step / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "roofline": roof,
+        "clocks": clk,
+        "gpu_launches": (13 if k == 5 else 9) * args.steps,
+        "wall_s_timed": t_wall,
+        "step_ms": step_ms,
+    }
+    if world > 1:
+        out["gpu_launches"] = (8 + 2 * len(sub_budgets(k, args.budget)) + 1) * args.steps
+    if pool is not None:
+        per_worker = calibrate_per_worker(args.workload, k, args.seed, 12.0)
+        b, sw, n, wall = oracle_pass(pool, cores, args.workload, k, args.seed, per_worker)
+        v, rate = oracle_rate(b, sw, n, args.budget)
+        pool.shutdown()
+        out["cpu_baseline"] = {
+            "value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": (f"{n} samples ({'T-5/Path-5 evenly' if k == 5 else 'MOSS-4'}) over {cores} processes in "
+                       f"{sw:.1f} s + table build {b:.2f} s, extrapolated to the {args.budget}-sample budget"),
+            "sampling_rate": rate}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * moss.h -- C ABI of the GB300 Moss motif sampler (libmoss.so).
+ *
+ * Estimates the frequencies of the 6 connected induced 4-node subgraph
+ * classes (M_1^(4)..M_6^(4)) and the 21 5-node classes (M_1^(5)..M_21^(5))
+ * of an undirected simple graph, with the unbiased sampling estimators and
+ * closed-form variances of
+ *   P. Wang, J. Tao, J. Zhao, X. Guan, "Moss: A Scalable Tool for Efficiently
+ *   Sampling and Counting 4- and 5-Node Graphlets", arXiv 1509.08089:
+ *     MOSS-4  (Sec. 4.1, Algorithm 1, Theorems 2-3),
+ *     MOSS-5  = T-5 (Algorithm 3, Theorems 6-7) + Path-5 (Algorithm 4,
+ *               Theorems 8-9) + the mix estimator (Sec. 5.1.3, Theorem 10).
+ * Every step runs as CUDA kernels on one GPU (sm_103a).  The only data that
+ * crosses to the host during sampling is the final result.
+ *
+ * Conventions
+ *   - Every function returns an int status: MOSS_OK (0) or a negative
+ *     MOSS_E* code.  No exception crosses the ABI.  moss_last_error_detail()
+ *     returns a thread-local description of the last failure on the calling
+ *     thread.
+ *   - "stream" arguments are cudaStream_t values passed as void*; NULL means
+ *     the legacy default stream.  All work of a call is enqueued on that
+ *     stream.  Calls documented as synchronous return after the stream has
+ *     drained the work of the call.
+ *   - The library never frees or retains caller memory.  Graph objects own
+ *     their device memory and release it in moss_graph_free.
+ *   - A moss_graph may be used by one host thread at a time.
+ *
+ * Random numbers: Philox4x64-10 (Salmon et al., SC'11).  Word i of sample s of
+ * method t under seed k is word (i mod 4) of Philox4x64-10(counter
+ * {s, i div 4, t, 0}, key {k, 0}); t = 0 (MOSS-4), 1 (T-5), 2 (Path-5).  The
+ * counts of a sample range are therefore independent of launch shape, stream
+ * and device count, and shards [a,b) + [b,c) add up to [a,c) exactly.
+ */
+#ifndef MOSS_H
+#define MOSS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define MOSS_OK          0
+#define MOSS_EINVAL     -1  /* bad argument (null pointer, k not 4/5, ...)   */
+#define MOSS_ENOMEM     -2  /* device or host allocation failed             */
+#define MOSS_ECUDA      -3  /* a CUDA runtime call failed                   */
+#define MOSS_EGRAPH     -4  /* CSR is not a sorted symmetric simple graph   */
+#define MOSS_EOVERFLOW  -5  /* a size or an exact total exceeds its range   */
+#define MOSS_ESTATE     -6  /* tables for the requested k were not built    */
+
+#define MOSS_METHOD_MOSS4  0   /* Algorithm 1 */
+#define MOSS_METHOD_T5     1   /* Algorithm 3 */
+#define MOSS_METHOD_PATH5  2   /* Algorithm 4 */
+
+#define MOSS_NCLASS_SLOTS 22   /* [0] = collisions, [1..21] = classes */
+
+typedef struct moss_graph moss_graph;
+
+/* Exact totals of Table 1 (as 128-bit lo/hi pairs and as doubles). */
+typedef struct {
+    uint32_t n;                 /* vertices                                 */
+    uint64_t nnz;               /* directed CSR slots = 2 |E|               */
+    uint32_t d_max;             /* maximum degree                           */
+    uint64_t gamma[3][2];       /* Gamma, Gamma^(1), Gamma^(2): {lo, hi}     */
+    uint64_t lambda3[2];        /* Lambda_3 = sum C(d_v,3): {lo, hi}         */
+    uint64_t lambda4[2];        /* Lambda_4 = sum C(d_v,4): {lo, hi}         */
+    double gamma_d[3], lambda3_d, lambda4_d;
+} moss_stats;
+
+/* Result of one estimate.  Index i of est/var is class M_i (1-based); index
+ * 0 is unused.  For k = 4 only indices 1..6 are meaningful. */
+typedef struct {
+    int k;                      /* 4 or 5                                   */
+    int n_classes;              /* 6 or 21                                  */
+    uint64_t K[2];              /* samples drawn: k=4 {K, 0}; k=5 {K1, K2}    */
+    uint64_t hits[2][MOSS_NCLASS_SLOTS]; /* [sub-method][0 = collisions, i]   */
+    double est[MOSS_NCLASS_SLOTS];       /* estimate of n_i / eta_i          */
+    double var[MOSS_NCLASS_SLOTS];       /* plug-in variance of est[i]       */
+    double lambda[2][MOSS_NCLASS_SLOTS]; /* k=5: weight of T-5 / Path-5 in est */
+    double triangles;           /* k=4: triangle count implied by the r = w collisions */
+    double triangles_var;
+} moss_result;
+
+/* Load an undirected graph given as CSR.
+ *   row_ptr : n+1 offsets, uint64 when row_ptr_is_64 != 0 else uint32;
+ *             row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz.
+ *   col     : nnz vertex ids; each list N_v (Table 1) strictly increasing, no
+ *             self loop, every (v,u) matched by (u,v).
+ *   Both arrays may be host or device memory (detected); they are copied and
+ *   may be released after the call.  device: CUDA ordinal the graph lives on.
+ *   Limits: n < 2^32 - 1, nnz < 2^32.
+ * Validates the graph on the device and returns MOSS_EGRAPH (with detail) if
+ * any rule is broken.  Synchronous on stream.  *out receives a new graph that
+ * the caller releases with moss_graph_free. */
+int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *col,
+                        uint32_t n, uint64_t nnz, int device, void *stream, moss_graph **out);
+
+/* Initialization step (Sec. 4.1.3, Sec. 5.1.4): exact per-vertex weights
+ * Gamma_v, Gamma^(1)_v, Gamma^(2)_v (Sec. 4.1.1, 5.1.1, 5.1.2), the totals of
+ * Table 1, the per-list alias tables of sigma^(v) (eq. 1) with the prefix
+ * array ACC_sigma^(v), and the vertex alias tables of pi (k_mask bit 4) and
+ * rho^(1), rho^(2) (k_mask bit 5).  k_mask: (1<<4) | (1<<5) or either.
+ * MOSS_EOVERFLOW if a scaled total leaves 128 bits.  Synchronous on stream;
+ * tables already built are rebuilt. */
+int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream);
+
+/* Sample-and-estimate.  k = 4: MOSS-4 with K = budget.  k = 5: T-5 with
+ * K1 = floor(budget/2) and Path-5 with K2 = budget - K1 (K1 = K2, Sec. 5.1.5).
+ * A sub-method whose total weight is 0 draws nothing (its classes cannot
+ * occur and are estimated as exactly 0).  Sample ids are 0..K-1 per
+ * sub-method.  out is caller-owned host memory.  Synchronous on stream. */
+int moss_sample_estimate(moss_graph *g, int k, uint64_t budget, uint64_t seed, void *stream,
+                         moss_result *out);
+
+/* Counts of samples first..first+count-1 of one method: counts_dev (device,
+ * 22 uint64) receives [0] = collisions (no CIS) and [i] = samples of class i.
+ * Asynchronous on stream.  Shards of a sample range sum exactly. */
+int moss_sample_counts(moss_graph *g, int method, uint64_t first, uint64_t count, uint64_t seed,
+                       void *stream, uint64_t *counts_dev);
+
+/* Per-sample records of samples first..first+count-1 (for verification):
+ * classes_dev (device, count uint8: 0 = collision, else class) and, when not
+ * NULL, verts_dev (device, 5*count uint32: v,u,w,r,t in draw order; t = 0
+ * for MOSS-4).  Asynchronous on stream. */
+int moss_sample_records(moss_graph *g, int method, uint64_t first, uint64_t count, uint64_t seed,
+                        void *stream, uint8_t *classes_dev, uint32_t *verts_dev);
+
+/* Estimators and variances from counts gathered elsewhere (e.g. summed over
+ * shards): K[2] and hits[2][22] as in moss_result.  The arithmetic runs on
+ * the device in FP64.  Synchronous on stream. */
+int moss_finalize(moss_graph *g, int k, const uint64_t *K, const uint64_t *hits, void *stream,
+                  moss_result *out);
+
+/* Exact totals (requires moss_build_tables for the gamma entries). */
+int moss_graph_stats(const moss_graph *g, moss_stats *out);
+
+/* Copy one internal table to host memory (verification and debugging).
+ *   MOSS_TABLE_VERT   n x {uint32 off, deg, S_v, 0}
+ *   MOSS_TABLE_SLOT   nnz x {uint32 col, sigma threshold, sigma alias
+ *                            (position in N_v), twin (position of v in N_col)}
+ *   MOSS_TABLE_ACC    nnz x uint32 ACC_sigma^(v) exclusive prefix (Sec. 4.1.3)
+ *   MOSS_TABLE_SEED0+l n x {uint64 threshold T, uint32 alias, uint32 0},
+ *                      l = 0 pi, 1 rho^(1), 2 rho^(2)
+ *   MOSS_TABLE_GAMMA0+l n x {uint64 lo, hi} vertex weight of table l
+ * bytes must equal the table size.  Synchronous. */
+#define MOSS_TABLE_VERT   0
+#define MOSS_TABLE_SLOT   1
+#define MOSS_TABLE_ACC    2
+#define MOSS_TABLE_SEED0  3
+#define MOSS_TABLE_GAMMA0 6
+int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t bytes);
+
+void moss_graph_free(moss_graph *g);
+
+const char *moss_strerror(int status);
+const char *moss_last_error_detail(void);
+const char *moss_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOSS_H */

@@ -1,0 +1,171 @@
+"""Algorithmic 32-byte sectors per sample -- measurement infrastructure.
+
+For each sampled CIS, the set of distinct 32 B sectors the sampling step must
+read under the device layout the library documents (include/moss.h and its
+kernels): vertex alias records and vertex records of 16 B, per-slot sigma
+records of 16 B, neighbour ids of 4 B, ACC entries of 4 B, Q_v of 8 B; each
+probe is a lower-bound search with early exit in the shorter sorted list.
+The draws are replayed from the oracle's Philox words and tables, so the
+count is exact per sample; the mean over a few thousand samples is the
+per-sample figure used by the roofline ("achieved" = figure x 32 B x samples
+/ kernel time).
+
+    python oracle/sector_model.py [workload] [samples]
+writes tests/golden/sectors_<workload>.json.  Calls only the oracle and the
+shared input generator.
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+TWO64 = 1 << 64
+
+
+def idx(x: int, m: int) -> int:
+    return (x * m) >> 64
+
+
+class Replay:
+    def __init__(self, rp, col):
+        self.g = oracle.OracleGraph(rp, col)
+        self.rp = rp.astype(np.int64)
+        self.col = col
+        self.deg = np.diff(self.rp)
+        self.S = self.g.vertex()[1].astype(np.int64)
+        self.seed = [self.g.seed_table(l)[1:] for l in range(3)]
+        thr, alias, acc = self.g.sigma_table()
+        self.thr, self.alias, self.acc = thr.astype(np.int64), alias.astype(np.int64), acc.astype(np.int64)
+
+    def words(self, method, seed, s, blocks):
+        out = []
+        for b in range(blocks):
+            out += oracle.philox4x64([s, b, method, 0], [seed, 0])
+        return out
+
+    def probe(self, a, b, touched):
+        da, db = self.deg[a], self.deg[b]
+        if da <= db:
+            lo, ln, key = self.rp[a], da, b
+        else:
+            lo, ln, key = self.rp[b], db, a
+        while ln > 0:
+            half = ln >> 1
+            p = lo + half
+            touched.add(("col", int(p) >> 3))
+            val = int(self.col[p])
+            if val == key:
+                return
+            if val < key:
+                lo, ln = p + 1, ln - half - 1
+            else:
+                ln = half
+
+    def sigma(self, v, xc, xt, touched):
+        o, d, S = int(self.rp[v]), int(self.deg[v]), int(self.S[v])
+        j = idx(xc, d)
+        touched.add(("slot", (o + j) >> 1))
+        if idx(xt, S) < int(self.thr[o + j]):
+            return j
+        a = int(self.alias[o + j])
+        touched.add(("slot", (o + a) >> 1))
+        return a
+
+    def sample(self, method, seed, s, verts, cls):
+        t = set()
+        T, al = self.seed[method]
+        x = self.words(method, seed, s, 4)
+        c = idx(x[0], self.g.n)
+        t.add(("seed", c >> 1))
+        v = int(verts[0])
+        t.add(("vert", v >> 1))
+        o = int(self.rp[v])
+        if method == 2:
+            iu = self.sigma(v, x[4], x[5], t)
+            iw = self.sigma(v, x[6], x[7], t)
+            if iu == iw:
+                iu = self.sigma(v, x[8], x[9], t)
+                iw = self.sigma(v, x[10], x[11], t)
+                if iu == iw:  # fallback: ACC scan and search, Q_v, two slot records
+                    d = int(self.deg[v])
+                    for i in range(d):
+                        t.add(("acc", (o + i) >> 3))
+                    t.add(("q", v >> 2))
+                    col_list = list(self.col[o:o + d])
+                    iu = col_list.index(int(verts[1]))
+                    iw = col_list.index(int(verts[2]))
+                    t.add(("slot", (o + iu) >> 1))
+                    t.add(("slot", (o + iw) >> 1))
+            u, w, r, tt = (int(z) for z in verts[1:5])
+            t.add(("vert", u >> 1))
+            t.add(("vert", w >> 1))
+            ju = int(np.searchsorted(self.col[self.rp[u]:self.rp[u + 1]], r))
+            jt = int(np.searchsorted(self.col[self.rp[w]:self.rp[w + 1]], tt))
+            t.add(("col", (int(self.rp[u]) + ju) >> 3))
+            t.add(("col", (int(self.rp[w]) + jt) >> 3))
+            if cls:
+                t.add(("vert", r >> 1))
+                t.add(("vert", tt >> 1))
+                for a, b in ((v, r), (v, tt), (u, w), (u, tt), (w, r), (r, tt)):
+                    self.probe(a, b, t)
+            return len(t)
+        iu = self.sigma(v, x[2], x[3], t)
+        u, w, r = int(verts[1]), int(verts[2]), int(verts[3])
+        col_v = self.col[o:o + int(self.deg[v])]
+        t.add(("col", (o + int(np.searchsorted(col_v, w))) >> 3))
+        t.add(("vert", u >> 1))
+        if method == 0:
+            ju = int(np.searchsorted(self.col[self.rp[u]:self.rp[u + 1]], r))
+            t.add(("col", (int(self.rp[u]) + ju) >> 3))
+            if cls:
+                t.add(("vert", w >> 1))
+                t.add(("vert", r >> 1))
+                for a, b in ((v, r), (u, w), (w, r)):
+                    self.probe(a, b, t)
+            return len(t)
+        tt = int(verts[4])
+        t.add(("col", (o + int(np.searchsorted(col_v, r))) >> 3))
+        jt = int(np.searchsorted(self.col[self.rp[u]:self.rp[u + 1]], tt))
+        t.add(("col", (int(self.rp[u]) + jt) >> 3))
+        if cls:
+            for z in (w, r, tt):
+                t.add(("vert", z >> 1))
+            for a, b in ((u, w), (u, r), (w, r), (v, tt), (w, tt), (r, tt)):
+                self.probe(a, b, t)
+        return len(t)
+
+
+def model(workload: str, samples: int = 4000, seed: int = 42) -> dict:
+    rp, col = synth.workload(workload)
+    rep = Replay(rp, col)
+    out = {"workload": workload, "samples": samples, "seed": seed,
+           "layout": "16 B vertex/alias/slot records, 4 B ids and ACC, 8 B Q; 32 B sectors",
+           "source": "written by oracle/sector_model.py"}
+    for method, name in ((0, "MOSS4"), (1, "T5"), (2, "PATH5")):
+        first = 1_000_000
+        _, cls, verts = rep.g.run(method, seed, samples, first=first, record=True)
+        n = [rep.sample(method, seed, first + i, verts[i], int(cls[i])) for i in range(samples)]
+        out[name] = {"sectors_per_sample": float(np.mean(n)), "stderr": float(np.std(n) / np.sqrt(samples)),
+                     "collision_rate": float(np.mean(cls == 0))}
+    return out
+
+
+if __name__ == "__main__":
+    wl = sys.argv[1] if len(sys.argv) > 1 else "cl_n100k"
+    ns = int(sys.argv[2]) if len(sys.argv) > 2 else 4000
+    res = model(wl, ns)
+    path = os.path.join(ROOT, "tests", "golden", f"sectors_{wl}.json")
+    with open(path, "w") as f:
+        json.dump(res, f, indent=1)
+        f.write("\n")
+    print(json.dumps(res, indent=1))

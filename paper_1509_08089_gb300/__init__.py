@@ -1,0 +1,234 @@
+"""GB300 Moss motif sampler -- Python binding of libmoss.so (include/moss.h).
+
+A thin ctypes layer: every function marshals its arguments and calls the C
+ABI of the same name; all computation (validation, weights, alias tables,
+sampling, counting, estimators) runs in the library's CUDA kernels.  There is
+no CPU fallback: if ``libmoss.so`` is missing or cannot load, every call
+raises.  Build it with ``python -m paper_1509_08089_gb300.build``.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA).
+``stream`` is a ``torch.cuda.Stream``, a raw ``cudaStream_t`` integer, or None
+for torch's current stream on the graph's device (legacy default stream when
+torch is unavailable).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Any
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmoss.so")
+
+MOSS_OK, MOSS_EINVAL, MOSS_ENOMEM, MOSS_ECUDA, MOSS_EGRAPH, MOSS_EOVERFLOW, MOSS_ESTATE = 0, -1, -2, -3, -4, -5, -6
+MOSS4, T5, PATH5 = 0, 1, 2
+NSLOTS = 22
+TABLE_VERT, TABLE_SLOT, TABLE_ACC, TABLE_SEED0, TABLE_GAMMA0 = 0, 1, 2, 3, 6
+
+
+class moss_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("nnz", ctypes.c_uint64), ("d_max", ctypes.c_uint32),
+                ("gamma", (ctypes.c_uint64 * 2) * 3), ("lambda3", ctypes.c_uint64 * 2),
+                ("lambda4", ctypes.c_uint64 * 2), ("gamma_d", ctypes.c_double * 3),
+                ("lambda3_d", ctypes.c_double), ("lambda4_d", ctypes.c_double)]
+
+
+class moss_result(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("n_classes", ctypes.c_int), ("K", ctypes.c_uint64 * 2),
+                ("hits", (ctypes.c_uint64 * NSLOTS) * 2), ("est", ctypes.c_double * NSLOTS),
+                ("var", ctypes.c_double * NSLOTS), ("lambda_", (ctypes.c_double * NSLOTS) * 2),
+                ("triangles", ctypes.c_double), ("triangles_var", ctypes.c_double)]
+
+
+class MossError(RuntimeError):
+    def __init__(self, status: int, detail: str):
+        super().__init__(f"{detail} (status {status})")
+        self.status = status
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_u64 = ctypes.c_uint64
+
+
+def load():
+    """Load libmoss.so (raises if it is absent: no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run python -m paper_1509_08089_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "moss_graph_load_csr": ([_vp, ctypes.c_int, _vp, ctypes.c_uint32, _u64, ctypes.c_int, _vp,
+                                 ctypes.POINTER(_vp)], ctypes.c_int),
+        "moss_build_tables": ([_vp, ctypes.c_uint, _vp], ctypes.c_int),
+        "moss_sample_estimate": ([_vp, ctypes.c_int, _u64, _u64, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
+        "moss_sample_counts": ([_vp, ctypes.c_int, _u64, _u64, _u64, _vp, _vp], ctypes.c_int),
+        "moss_sample_records": ([_vp, ctypes.c_int, _u64, _u64, _u64, _vp, _vp, _vp], ctypes.c_int),
+        "moss_finalize": ([_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
+        "moss_graph_stats": ([_vp, ctypes.POINTER(moss_stats)], ctypes.c_int),
+        "moss_table_export": ([_vp, ctypes.c_int, _vp, _u64], ctypes.c_int),
+        "moss_graph_free": ([_vp], None),
+        "moss_strerror": ([ctypes.c_int], ctypes.c_char_p),
+        "moss_last_error_detail": ([], ctypes.c_char_p),
+        "moss_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != MOSS_OK:
+        lib = load()
+        raise MossError(rc, f"{lib.moss_strerror(rc).decode()}: {lib.moss_last_error_detail().decode()}")
+
+
+def _ptr(x: Any) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream(stream, device: int | None = None) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream(device).cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------ C ABI calls --
+def moss_version() -> str:
+    return load().moss_version().decode()
+
+
+def moss_strerror(status: int) -> str:
+    return load().moss_strerror(status).decode()
+
+
+def moss_last_error_detail() -> str:
+    return load().moss_last_error_detail().decode()
+
+
+def moss_graph_load_csr(row_ptr, col, n: int | None = None, device: int = 0, stream=None) -> int:
+    """Copy a CSR graph (host or device arrays) to the device; returns the handle."""
+    lib = load()
+    is64 = int(getattr(row_ptr, "dtype", None) in (np.uint64, np.int64) or str(getattr(row_ptr, "dtype", "")) in
+               ("torch.int64", "torch.uint64"))
+    if n is None:
+        n = len(row_ptr) - 1
+    nnz = len(col)
+    out = _vp()
+    _check(lib.moss_graph_load_csr(_ptr(row_ptr), is64, _ptr(col) if nnz else None, n, nnz, device,
+                                   _stream(stream, device), ctypes.byref(out)))
+    return out.value
+
+
+def moss_build_tables(g: int, k_mask: int = (1 << 4) | (1 << 5), stream=None):
+    _check(load().moss_build_tables(g, k_mask, _stream(stream)))
+
+
+def moss_sample_estimate(g: int, k: int, budget: int, seed: int, stream=None) -> moss_result:
+    r = moss_result()
+    _check(load().moss_sample_estimate(g, k, budget, seed, _stream(stream), ctypes.byref(r)))
+    return r
+
+
+def moss_sample_counts(g: int, method: int, first: int, count: int, seed: int, counts_dev, stream=None):
+    _check(load().moss_sample_counts(g, method, first, count, seed, _stream(stream), _ptr(counts_dev)))
+
+
+def moss_sample_records(g: int, method: int, first: int, count: int, seed: int, classes_dev, verts_dev=None,
+                        stream=None):
+    _check(load().moss_sample_records(g, method, first, count, seed, _stream(stream), _ptr(classes_dev),
+                                      _ptr(verts_dev)))
+
+
+def moss_finalize(g: int, k: int, K, hits, stream=None) -> moss_result:
+    Ka = np.ascontiguousarray(K, dtype=np.uint64)
+    Ha = np.ascontiguousarray(hits, dtype=np.uint64).reshape(2 * NSLOTS)
+    r = moss_result()
+    _check(load().moss_finalize(g, k, _ptr(Ka), _ptr(Ha), _stream(stream), ctypes.byref(r)))
+    return r
+
+
+def moss_graph_stats(g: int) -> moss_stats:
+    s = moss_stats()
+    _check(load().moss_graph_stats(g, ctypes.byref(s)))
+    return s
+
+
+def moss_table_export(g: int, table: int, out: np.ndarray):
+    _check(load().moss_table_export(g, table, _ptr(out), out.nbytes))
+    return out
+
+
+def moss_graph_free(g: int):
+    if g:
+        load().moss_graph_free(g)
+
+
+# ------------------------------------------------------------ convenience --
+def result_dict(r: moss_result) -> dict:
+    """moss_result as plain Python/numpy values."""
+    return {"k": r.k, "K": (int(r.K[0]), int(r.K[1])),
+            "hits": np.array([[int(x) for x in r.hits[l]] for l in range(2)], dtype=np.uint64),
+            "est": np.array(list(r.est)), "var": np.array(list(r.var)),
+            "lam": np.array([list(r.lambda_[l]) for l in range(2)]),
+            "triangles": r.triangles, "triangles_var": r.triangles_var}
+
+
+class Graph:
+    """Owning wrapper: load, build, sample, free."""
+
+    def __init__(self, row_ptr, col, device: int = 0, stream=None, k_mask: int = (1 << 4) | (1 << 5)):
+        self.handle = moss_graph_load_csr(row_ptr, col, device=device, stream=stream)
+        self.device = device
+        if k_mask:
+            moss_build_tables(self.handle, k_mask, stream)
+
+    def estimate(self, k: int, budget: int, seed: int, stream=None) -> dict:
+        return result_dict(moss_sample_estimate(self.handle, k, budget, seed, stream))
+
+    def stats(self) -> moss_stats:
+        return moss_graph_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            moss_graph_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,505 @@
+// moss_capi.cu -- the C ABI (include/moss.h): argument checking, device
+// memory, stream ordering and error reporting around the kernels of
+// moss_tables.cu, moss_sample.cu and moss_finalize.cu.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "../../include/moss.h"
+#include "moss_internal.cuh"
+
+using namespace moss;
+
+// ---------------------------------------------------------------- errors --
+namespace {
+
+thread_local char g_detail[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_detail, sizeof(g_detail), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? MOSS_ENOMEM : MOSS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define MOSS_CUDA(call, what)                       \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// ------------------------------------------------------ class lookup table --
+// The class of each edge mask.  Pair (i,j), i<j, in the order
+// (0,1),(0,2),...,(k-2,k-1) is an edge when its bit is set.  A connected
+// graph is identified by how many spanning 3-paths and 3-stars (k = 4,
+// Sec. 4.1.2) or forks, 5-paths and 4-stars (k = 5, Table 2) it contains:
+// paths are counted as vertex orders along edges (halved), stars as vertices
+// adjacent to all others, forks as ordered (centre, middle, end) triples whose
+// remaining two vertices hang on the centre.
+const int kTable4[6][2] = {{1, 0}, {0, 1}, {4, 0}, {2, 1}, {6, 2}, {12, 4}};
+const int kTable2[21][3] = {{0, 1, 0},  {0, 0, 1},  {1, 0, 0},   {1, 2, 0},   {2, 2, 0},   {0, 5, 0},   {2, 1, 0},
+                            {2, 0, 1},  {4, 4, 0},  {4, 7, 0},   {5, 2, 1},   {4, 4, 1},   {6, 6, 0},   {10, 10, 1},
+                            {9, 6, 1},  {12, 6, 2}, {10, 14, 0}, {20, 24, 1}, {20, 18, 2}, {36, 36, 3}, {60, 60, 5}};
+
+int mask_class(int k, uint32_t mask) {
+    bool adj[5][5] = {};
+    int b = 0;
+    for (int i = 0; i < k; ++i)
+        for (int j = i + 1; j < k; ++j, ++b)
+            if (mask >> b & 1u) adj[i][j] = adj[j][i] = true;
+    // connectivity by repeated relaxation from vertex 0
+    bool seen[5] = {true, false, false, false, false};
+    for (int it = 0; it < k; ++it)
+        for (int i = 0; i < k; ++i)
+            if (seen[i])
+                for (int j = 0; j < k; ++j)
+                    if (adj[i][j]) seen[j] = true;
+    for (int i = 0; i < k; ++i)
+        if (!seen[i]) return 0;
+    // Hamiltonian paths: vertex orders with consecutive edges, each path twice
+    int perm[5] = {0, 1, 2, 3, 4};
+    int orders = 0;
+    // iterate all permutations of perm[0..k)
+    int c[5] = {0, 0, 0, 0, 0};
+    auto path_ok = [&](const int *p) {
+        for (int i = 0; i + 1 < k; ++i)
+            if (!adj[p[i]][p[i + 1]]) return false;
+        return true;
+    };
+    orders += path_ok(perm);
+    for (int i = 1; i < k;) {  // Heap's algorithm
+        if (c[i] < i) {
+            int a = (i % 2 == 0) ? 0 : c[i];
+            int t = perm[a]; perm[a] = perm[i]; perm[i] = t;
+            orders += path_ok(perm);
+            ++c[i];
+            i = 1;
+        } else {
+            c[i] = 0;
+            ++i;
+        }
+    }
+    const int paths = orders / 2;
+    int stars = 0;
+    for (int i = 0; i < k; ++i) {
+        int d = 0;
+        for (int j = 0; j < k; ++j) d += adj[i][j];
+        if (d == k - 1) ++stars;
+    }
+    if (k == 4) {
+        for (int i = 0; i < 6; ++i)
+            if (kTable4[i][0] == paths && kTable4[i][1] == stars) return i + 1;
+        return -1;
+    }
+    int forks = 0;
+    for (int ce = 0; ce < 5; ++ce)
+        for (int mid = 0; mid < 5; ++mid) {
+            if (mid == ce || !adj[ce][mid]) continue;
+            for (int end = 0; end < 5; ++end) {
+                if (end == ce || end == mid || !adj[mid][end]) continue;
+                bool ok = true;
+                for (int x = 0; x < 5; ++x)
+                    if (x != ce && x != mid && x != end && !adj[ce][x]) ok = false;
+                forks += ok;
+            }
+        }
+    for (int i = 0; i < 21; ++i)
+        if (kTable2[i][0] == forks && kTable2[i][1] == paths && kTable2[i][2] == stars) return i + 1;
+    return -1;
+}
+
+std::mutex g_lut_mutex;
+bool g_lut_ready[64] = {};
+uint8_t g_lut4_h[64], g_lut5_h[1024];
+bool g_lut_built = false;
+
+int ensure_luts(int device) {
+    std::lock_guard<std::mutex> lk(g_lut_mutex);
+    if (!g_lut_built) {
+        for (uint32_t m = 0; m < 64; ++m) g_lut4_h[m] = (uint8_t)mask_class(4, m);
+        for (uint32_t m = 0; m < 1024; ++m) g_lut5_h[m] = (uint8_t)mask_class(5, m);
+        g_lut_built = true;
+    }
+    if (device < 0 || device >= 64) return fail(MOSS_EINVAL, "device ordinal %d out of range", device);
+    if (!g_lut_ready[device]) {
+        upload_luts(g_lut4_h, g_lut5_h);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "uploading class tables");
+        g_lut_ready[device] = true;
+    }
+    return MOSS_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ graph object --
+struct moss_graph {
+    int device = 0;
+    uint32_t n = 0;
+    uint64_t nnz = 0;
+    uint4 *vert = nullptr;
+    uint32_t *col = nullptr;
+    uint4 *slot = nullptr;
+    uint32_t *acc = nullptr;
+    uint64_t *q = nullptr;
+    u128 *gam[3] = {nullptr, nullptr, nullptr};
+    uint4 *seed[3] = {nullptr, nullptr, nullptr};
+    DevTotals *tot = nullptr;
+    DevTotals tot_h{};
+    unsigned built = 0;          // bit l: vertex table l; bit 3: sigma tables
+    uint64_t *partials = nullptr;
+    int partial_rows = 0;
+    uint64_t *counts = nullptr;  // 2 x 22
+    moss_result *res_dev = nullptr;
+    moss_result *res_host = nullptr;  // pinned
+    uint32_t *flags = nullptr;        // device status word
+    uint32_t *flags_host = nullptr;   // pinned
+};
+
+namespace {
+
+void release(moss_graph *g) {
+    if (!g) return;
+    DeviceGuard dg(g->device);
+    void *dev[] = {g->vert, g->col, g->slot, g->acc, g->q, g->gam[0], g->gam[1], g->gam[2], g->seed[0], g->seed[1],
+                   g->seed[2], g->tot, g->partials, g->counts, g->res_dev, g->flags};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    if (g->res_host) cudaFreeHost(g->res_host);
+    if (g->flags_host) cudaFreeHost(g->flags_host);
+    delete g;
+}
+
+DevGraph view(const moss_graph *g) {
+    DevGraph d;
+    d.vert = g->vert;
+    d.col = g->col;
+    d.slot = g->slot;
+    d.acc = g->acc;
+    d.q = g->q;
+    for (int l = 0; l < 3; ++l) d.seed[l] = g->seed[l];
+    d.n = g->n;
+    return d;
+}
+
+void describe_flags(uint32_t f, char *buf, size_t len) {
+    buf[0] = 0;
+    const char *names[] = {"row_ptr not monotone or wrong ends", "neighbour id >= n", "self loop",
+                           "list not strictly increasing", "edge without its reverse", "total out of range"};
+    for (int b = 0; b < 6; ++b)
+        if (f >> b & 1u) {
+            size_t u = strlen(buf);
+            snprintf(buf + u, len - u, "%s%s", u ? "; " : "", names[b]);
+        }
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, uint64_t count) {
+    return cudaMalloc(reinterpret_cast<void **>(p), (size_t)(count ? count : 1) * sizeof(T));
+}
+
+int read_flags(moss_graph *g, cudaStream_t s) {
+    MOSS_CUDA(cudaMemcpyAsync(g->flags_host, g->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "reading status");
+    MOSS_CUDA(cudaStreamSynchronize(s), "synchronising stream");
+    return MOSS_OK;
+}
+
+bool method_ready(const moss_graph *g, int method) {
+    return (g->built >> 3 & 1u) && (g->built >> method & 1u);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *moss_version(void) { return "moss-gb300 0.1 (sm_103a)"; }
+
+const char *moss_last_error_detail(void) { return g_detail; }
+
+const char *moss_strerror(int status) {
+    switch (status) {
+        case MOSS_OK: return "ok";
+        case MOSS_EINVAL: return "invalid argument";
+        case MOSS_ENOMEM: return "out of memory";
+        case MOSS_ECUDA: return "CUDA error";
+        case MOSS_EGRAPH: return "invalid graph";
+        case MOSS_EOVERFLOW: return "value out of range";
+        case MOSS_ESTATE: return "tables not built";
+        default: return "unknown status";
+    }
+}
+
+int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *col, uint32_t n, uint64_t nnz,
+                        int device, void *stream, moss_graph **out) {
+    if (!out) return fail(MOSS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!row_ptr) return fail(MOSS_EINVAL, "row_ptr is NULL");
+    if (nnz > 0 && !col) return fail(MOSS_EINVAL, "col is NULL with nnz > 0");
+    if (n == 0) return fail(MOSS_EINVAL, "graph has no vertex");
+    if (n == 0xFFFFFFFFu) return fail(MOSS_EOVERFLOW, "n must be below 2^32 - 1");
+    if (nnz >= (1ULL << 32)) return fail(MOSS_EOVERFLOW, "nnz = %llu must be below 2^32", (unsigned long long)nnz);
+    if (nnz % 2) return fail(MOSS_EGRAPH, "nnz is odd: an undirected graph stores both directions");
+    int ndev = 0;
+    MOSS_CUDA(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(MOSS_EINVAL, "device %d not present (%d devices)", device, ndev);
+    DeviceGuard dg(device);
+    int rc = ensure_luts(device);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    moss_graph *g = new (std::nothrow) moss_graph;
+    if (!g) return fail(MOSS_ENOMEM, "host allocation");
+    g->device = device;
+    g->n = n;
+    g->nnz = nnz;
+    void *rp_dev = nullptr;
+    const size_t rp_bytes = (size_t)(n + 1ULL) * (row_ptr_is_64 ? 8 : 4);
+    cudaError_t e = cudaSuccess;
+    int blocks = table_blocks(n);
+    int prow = 0;
+    for (int m = 0; m < 3; ++m) {
+        int b = sample_blocks(m, device);
+        prow = b > prow ? b : prow;
+    }
+    g->partial_rows = prow;
+#define STEP(call, what)                          \
+    do {                                          \
+        e = (call);                               \
+        if (e != cudaSuccess) {                   \
+            rc = cuda_fail(e, what);              \
+            goto fail_out;                        \
+        }                                         \
+    } while (0)
+    STEP(dalloc(&g->vert, n), "allocating vertices");
+    STEP(dalloc(&g->col, nnz), "allocating col");
+    STEP(dalloc(&g->slot, nnz), "allocating slots");
+    STEP(dalloc(&g->acc, nnz), "allocating ACC");
+    STEP(dalloc(&g->q, n), "allocating Q");
+    for (int l = 0; l < 3; ++l) {
+        STEP(dalloc(&g->gam[l], n), "allocating weights");
+        STEP(dalloc(&g->seed[l], n), "allocating vertex tables");
+    }
+    STEP(dalloc(&g->tot, 1), "allocating totals");
+    STEP(dalloc(&g->partials, (uint64_t)prow * kSlots + (uint64_t)blocks * 6 * 2), "allocating partials");
+    STEP(dalloc(&g->counts, 2 * kSlots), "allocating counts");
+    STEP(dalloc(&g->res_dev, 1), "allocating result");
+    STEP(dalloc(&g->flags, 1), "allocating status");
+    STEP(cudaMallocHost(reinterpret_cast<void **>(&g->res_host), sizeof(moss_result)), "allocating pinned result");
+    STEP(cudaMallocHost(reinterpret_cast<void **>(&g->flags_host), sizeof(uint32_t)), "allocating pinned status");
+    STEP(cudaMalloc(&rp_dev, rp_bytes), "allocating row_ptr copy");
+    STEP(cudaMemcpyAsync(rp_dev, row_ptr, rp_bytes, cudaMemcpyDefault, s), "copying row_ptr");
+    if (nnz) STEP(cudaMemcpyAsync(g->col, col, nnz * sizeof(uint32_t), cudaMemcpyDefault, s), "copying col");
+    STEP(cudaMemsetAsync(g->flags, 0, sizeof(uint32_t), s), "clearing status");
+    STEP(launch_vertices(rp_dev, row_ptr_is_64, n, nnz, g->vert, g->flags, s), "vertex kernel");
+    {
+        u128 *tp = reinterpret_cast<u128 *>(g->partials + (uint64_t)prow * kSlots);
+        STEP(launch_slots(n, g->col, g->vert, g->slot, g->acc, g->q, g->gam[0], g->gam[1], g->gam[2], tp, blocks,
+                          g->flags, s),
+             "slot kernel");
+        STEP(launch_totals(tp, blocks, g->tot, s), "totals kernel");
+    }
+    STEP(cudaMemcpyAsync(&g->tot_h, g->tot, sizeof(DevTotals), cudaMemcpyDeviceToHost, s), "reading totals");
+    rc = read_flags(g, s);
+    if (rc) goto fail_out;
+    cudaFree(rp_dev);
+    rp_dev = nullptr;
+    if (*g->flags_host) {
+        char buf[256];
+        describe_flags(*g->flags_host, buf, sizeof(buf));
+        rc = fail(MOSS_EGRAPH, "invalid CSR: %s", buf);
+        goto fail_out;
+    }
+#undef STEP
+    *out = g;
+    return MOSS_OK;
+fail_out:
+    if (rp_dev) cudaFree(rp_dev);
+    release(g);
+    return rc;
+}
+
+int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
+    if (!g) return fail(MOSS_EINVAL, "graph is NULL");
+    if ((k_mask & ~((1u << 4) | (1u << 5))) || !k_mask) return fail(MOSS_EINVAL, "k_mask must select 4 and/or 5");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint64_t items = g->nnz > g->n ? g->nnz : g->n;
+    uint32_t *idx = nullptr;
+    void *pre = nullptr;
+    const size_t pre_bytes = (size_t)(g->nnz * 8 > (uint64_t)g->n * 16 + 64 ? g->nnz * 8 : (uint64_t)g->n * 16 + 64);
+    int rc = MOSS_OK;
+    cudaError_t e;
+    g->built = 0;
+    if ((e = cudaMallocAsync(reinterpret_cast<void **>(&idx), items * sizeof(uint32_t), s)) != cudaSuccess)
+        return cuda_fail(e, "allocating scratch");
+    if ((e = cudaMallocAsync(&pre, pre_bytes, s)) != cudaSuccess) {
+        cudaFreeAsync(idx, s);
+        return cuda_fail(e, "allocating scratch");
+    }
+    e = cudaMemsetAsync(g->flags, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = launch_sigma_alias(g->n, g->vert, g->acc, g->slot, idx, static_cast<uint64_t *>(pre), s);
+    for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
+        const bool want = (l == 0 && (k_mask & (1u << 4))) || (l > 0 && (k_mask & (1u << 5)));
+        if (want)
+            e = launch_seed_alias(g->n, g->gam[l], g->tot, l, g->seed[l], idx, static_cast<u128 *>(pre), g->flags, s);
+    }
+    cudaFreeAsync(idx, s);
+    cudaFreeAsync(pre, s);
+    if (e != cudaSuccess) return cuda_fail(e, "table kernels");
+    rc = read_flags(g, s);
+    if (rc) return rc;
+    if (*g->flags_host & kErrOverflow) return fail(MOSS_EOVERFLOW, "a vertex weight total times n exceeds 2^128");
+    g->built = 1u << 3;
+    if (k_mask & (1u << 4)) g->built |= 1u;
+    if (k_mask & (1u << 5)) g->built |= 6u;
+    return MOSS_OK;
+}
+
+static int sample_into(moss_graph *g, int method, uint64_t first, uint64_t count, uint64_t seed, cudaStream_t s,
+                       uint64_t *counts_dev, uint8_t *classes, uint32_t *verts) {
+    if (method < 0 || method > 2) return fail(MOSS_EINVAL, "method %d", method);
+    if (!method_ready(g, method)) return fail(MOSS_ESTATE, "tables for method %d not built", method);
+    if (count > 0 && g->tot_h.gamma[method] == 0)
+        return fail(MOSS_EINVAL, "method %d has total weight 0 on this graph: no sample exists", method);
+    if (first + count < first) return fail(MOSS_EOVERFLOW, "sample range wraps");
+    const DevGraph dv = view(g);
+    const int blocks = sample_blocks(method, g->device);
+    // per-warp 32-bit counters: keep each launch below 2^31 samples per warp
+    const uint64_t max_chunk = (uint64_t)blocks * 8 * (1ULL << 31);
+    if (count == 0) {
+        MOSS_CUDA(cudaMemsetAsync(counts_dev, 0, kSlots * sizeof(uint64_t), s), "clearing counts");
+        return MOSS_OK;
+    }
+    if (count > max_chunk) return fail(MOSS_EOVERFLOW, "count above %llu per call", (unsigned long long)max_chunk);
+    MOSS_CUDA(launch_sample(method, dv, first, count, seed, g->partials, blocks, classes, verts, s), "sample kernel");
+    MOSS_CUDA(launch_reduce(g->partials, blocks, counts_dev, s), "reduce kernel");
+    return MOSS_OK;
+}
+
+int moss_sample_counts(moss_graph *g, int method, uint64_t first, uint64_t count, uint64_t seed, void *stream,
+                       uint64_t *counts_dev) {
+    if (!g || !counts_dev) return fail(MOSS_EINVAL, "NULL argument");
+    DeviceGuard dg(g->device);
+    return sample_into(g, method, first, count, seed, static_cast<cudaStream_t>(stream), counts_dev, nullptr, nullptr);
+}
+
+int moss_sample_records(moss_graph *g, int method, uint64_t first, uint64_t count, uint64_t seed, void *stream,
+                        uint8_t *classes_dev, uint32_t *verts_dev) {
+    if (!g || !classes_dev) return fail(MOSS_EINVAL, "NULL argument");
+    DeviceGuard dg(g->device);
+    return sample_into(g, method, first, count, seed, static_cast<cudaStream_t>(stream), g->counts, classes_dev,
+                       verts_dev);
+}
+
+static int finalize_from_device(moss_graph *g, int k, const uint64_t K[2], cudaStream_t s, moss_result *out) {
+    FinalizeIn in;
+    in.k = k;
+    in.K[0] = K[0];
+    in.K[1] = K[1];
+    MOSS_CUDA(launch_finalize(in, g->counts, g->tot, g->res_dev, s), "finalize kernel");
+    MOSS_CUDA(cudaMemcpyAsync(g->res_host, g->res_dev, sizeof(moss_result), cudaMemcpyDeviceToHost, s), "reading result");
+    MOSS_CUDA(cudaStreamSynchronize(s), "synchronising stream");
+    memcpy(out, g->res_host, sizeof(moss_result));
+    return MOSS_OK;
+}
+
+int moss_sample_estimate(moss_graph *g, int k, uint64_t budget, uint64_t seed, void *stream, moss_result *out) {
+    if (!g || !out) return fail(MOSS_EINVAL, "NULL argument");
+    if (k != 4 && k != 5) return fail(MOSS_EINVAL, "k must be 4 or 5 (got %d)", k);
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint64_t K[2] = {0, 0};
+    int rc;
+    if (k == 4) {
+        if (!method_ready(g, 0)) return fail(MOSS_ESTATE, "tables for k=4 not built");
+        K[0] = g->tot_h.gamma[0] ? budget : 0;
+        MOSS_CUDA(cudaMemsetAsync(g->counts + kSlots, 0, kSlots * sizeof(uint64_t), s), "clearing counts");
+        if ((rc = sample_into(g, 0, 0, K[0], seed, s, g->counts, nullptr, nullptr))) return rc;
+    } else {
+        if (!method_ready(g, 1) || !method_ready(g, 2)) return fail(MOSS_ESTATE, "tables for k=5 not built");
+        K[0] = g->tot_h.gamma[1] ? budget / 2 : 0;
+        K[1] = g->tot_h.gamma[2] ? budget - budget / 2 : 0;
+        if ((rc = sample_into(g, 1, 0, K[0], seed, s, g->counts, nullptr, nullptr))) return rc;
+        if ((rc = sample_into(g, 2, 0, K[1], seed, s, g->counts + kSlots, nullptr, nullptr))) return rc;
+    }
+    return finalize_from_device(g, k, K, s, out);
+}
+
+int moss_finalize(moss_graph *g, int k, const uint64_t *K, const uint64_t *hits, void *stream, moss_result *out) {
+    if (!g || !K || !hits || !out) return fail(MOSS_EINVAL, "NULL argument");
+    if (k != 4 && k != 5) return fail(MOSS_EINVAL, "k must be 4 or 5 (got %d)", k);
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MOSS_CUDA(cudaMemcpyAsync(g->counts, hits, 2 * kSlots * sizeof(uint64_t), cudaMemcpyDefault, s), "copying counts");
+    uint64_t KK[2] = {K[0], k == 4 ? 0 : K[1]};
+    return finalize_from_device(g, k, KK, s, out);
+}
+
+int moss_graph_stats(const moss_graph *g, moss_stats *out) {
+    if (!g || !out) return fail(MOSS_EINVAL, "NULL argument");
+    memset(out, 0, sizeof(*out));
+    out->n = g->n;
+    out->nnz = g->nnz;
+    out->d_max = g->tot_h.d_max;
+    auto put = [](uint64_t *dst, u128 x) {
+        dst[0] = (uint64_t)x;
+        dst[1] = (uint64_t)(x >> 64);
+    };
+    auto dbl = [](u128 x) { return (double)(uint64_t)(x >> 64) * 18446744073709551616.0 + (double)(uint64_t)x; };
+    for (int l = 0; l < 3; ++l) {
+        put(out->gamma[l], g->tot_h.gamma[l]);
+        out->gamma_d[l] = dbl(g->tot_h.gamma[l]);
+    }
+    put(out->lambda3, g->tot_h.lambda3);
+    put(out->lambda4, g->tot_h.lambda4);
+    out->lambda3_d = dbl(g->tot_h.lambda3);
+    out->lambda4_d = dbl(g->tot_h.lambda4);
+    return MOSS_OK;
+}
+
+int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t bytes) {
+    if (!g || !host_dst) return fail(MOSS_EINVAL, "NULL argument");
+    DeviceGuard dg(g->device);
+    const void *src = nullptr;
+    uint64_t need = 0;
+    if (table == MOSS_TABLE_VERT) { src = g->vert; need = (uint64_t)g->n * 16; }
+    else if (table == MOSS_TABLE_SLOT) { src = g->slot; need = g->nnz * 16; }
+    else if (table == MOSS_TABLE_ACC) { src = g->acc; need = g->nnz * 4; }
+    else if (table >= MOSS_TABLE_SEED0 && table < MOSS_TABLE_SEED0 + 3) {
+        if (!(g->built >> (table - MOSS_TABLE_SEED0) & 1u)) return fail(MOSS_ESTATE, "vertex table not built");
+        src = g->seed[table - MOSS_TABLE_SEED0];
+        need = (uint64_t)g->n * 16;
+    } else if (table >= MOSS_TABLE_GAMMA0 && table < MOSS_TABLE_GAMMA0 + 3) {
+        src = g->gam[table - MOSS_TABLE_GAMMA0];
+        need = (uint64_t)g->n * 16;
+    } else {
+        return fail(MOSS_EINVAL, "unknown table %d", table);
+    }
+    if (table == MOSS_TABLE_SLOT && !(g->built >> 3 & 1u)) return fail(MOSS_ESTATE, "sigma tables not built");
+    if (bytes != need) return fail(MOSS_EINVAL, "table %d has %llu bytes, got %llu", table, (unsigned long long)need,
+                                   (unsigned long long)bytes);
+    if (need) MOSS_CUDA(cudaMemcpy(host_dst, src, need, cudaMemcpyDeviceToHost), "copying table");
+    return MOSS_OK;
+}
+
+void moss_graph_free(moss_graph *g) { release(g); }
+
+}  // extern "C"

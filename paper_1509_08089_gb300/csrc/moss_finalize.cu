@@ -1,0 +1,143 @@
+// moss_finalize.cu -- estimators and variances in FP64 on the device.
+//
+//   MOSS-4 (Sec. 4.1.2, Theorems 2-3): p_i = 2 phi^(1)_i / Gamma,
+//     n_i = m_i / (K p_i), i in {1,3,4,5,6}; n_2 = Lambda_3 - n_4 - 2 n_5 - 4 n_6
+//     (eq. 2); Var(n_i) = n_i/K (1/p_i - n_i); Var(n_2) of Theorem 3.  The
+//     collisions r = w are triangles, each reached by 6 ordered draws of
+//     probability 1/Gamma, so they also estimate the triangle count.
+//   MOSS-5 (Theorems 6-10, Sec. 5.1.3): eta^(l)_i = m^(l)_i / (K_l p^(l)_i),
+//     p^(l)_i = 2 phi^(l)_i / Gamma^(l); classes of Omega_1 and Omega_2 are
+//     mixed with lambda^(1) = V2/(V1+V2), lambda^(2) = V1/(V1+V2); eta_2 =
+//     Lambda_4 - sum_{Omega_3*} phi^(3)_i eta_i with the variance of Theorem 10
+//     and the covariances Cov(eta_i, eta_j) = -eta_i eta_j sum_l a_i a_j / K_l.
+//   The unknown eta in a variance is replaced by the estimate (one source) or
+//   by the pooled value (m1 + m2) / (K1 p1 + K2 p2) (two sources).
+#include "../../include/moss.h"
+#include "moss_internal.cuh"
+
+namespace moss {
+
+namespace {
+
+// Sec. 4.1.2: copies of M_1^(4) in M_1..M_6 (phi^(1)) and of M_2^(4) (phi^(2))
+__device__ const double kPhi4[6][2] = {{1, 0}, {0, 1}, {4, 0}, {2, 1}, {6, 2}, {12, 4}};
+// Table 2: forks, 5-paths, 4-stars in M_1^(5)..M_21^(5)
+__device__ const double kPhi5[21][3] = {
+    {0, 1, 0},  {0, 0, 1},  {1, 0, 0},   {1, 2, 0},   {2, 2, 0},   {0, 5, 0},   {2, 1, 0},
+    {2, 0, 1},  {4, 4, 0},  {4, 7, 0},   {5, 2, 1},   {4, 4, 1},   {6, 6, 0},   {10, 10, 1},
+    {9, 6, 1},  {12, 6, 2}, {10, 14, 0}, {20, 24, 1}, {20, 18, 2}, {36, 36, 3}, {60, 60, 5}};
+
+__device__ __forceinline__ double u128_to_double(u128 x) {
+    return (double)(uint64_t)(x >> 64) * 18446744073709551616.0 + (double)(uint64_t)x;
+}
+
+__global__ void k_finalize(FinalizeIn in, const uint64_t *hits, const DevTotals *tot, moss_result *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    moss_result r;
+    memset(&r, 0, sizeof(r));
+    r.k = in.k;
+    r.K[0] = in.K[0];
+    r.K[1] = in.K[1];
+    for (int l = 0; l < 2; ++l)
+        for (int i = 0; i < kSlots; ++i) r.hits[l][i] = hits[l * kSlots + i];
+    if (in.k == 4) {
+        r.n_classes = 6;
+        const double G = u128_to_double(tot->gamma[0]);
+        const double K = (double)in.K[0];
+        double p[7] = {0, 0, 0, 0, 0, 0, 0};
+        if (in.K[0] > 0 && G > 0) {
+            for (int i = 1; i <= 6; ++i) {
+                if (i == 2) continue;
+                p[i] = 2.0 * kPhi4[i - 1][0] / G;
+                r.est[i] = (double)r.hits[0][i] / (K * p[i]);
+            }
+            for (int i = 1; i <= 6; ++i) {
+                if (i == 2) continue;
+                r.var[i] = r.est[i] / K * (1.0 / p[i] - r.est[i]);
+            }
+            const double s = r.est[4] + 2.0 * r.est[5] + 4.0 * r.est[6];
+            r.var[2] = (r.est[4] / p[4] + 4.0 * r.est[5] / p[5] + 16.0 * r.est[6] / p[6] - s * s) / K;
+            r.triangles = (double)r.hits[0][0] * G / (6.0 * K);
+            r.triangles_var = r.triangles / K * (G / 6.0 - r.triangles);
+        }
+        r.est[2] = u128_to_double(tot->lambda3) - r.est[4] - 2.0 * r.est[5] - 4.0 * r.est[6];
+        *out = r;
+        return;
+    }
+    r.n_classes = 21;
+    const double G[2] = {u128_to_double(tot->gamma[1]), u128_to_double(tot->gamma[2])};
+    const double K[2] = {(double)in.K[0], (double)in.K[1]};
+    const bool avail[2] = {in.K[0] > 0 && G[0] > 0, in.K[1] > 0 && G[1] > 0};
+    double p[2][kSlots], eh[2][kSlots], plug[kSlots], a[2][kSlots];
+    for (int l = 0; l < 2; ++l)
+        for (int i = 0; i < kSlots; ++i) { p[l][i] = 0; eh[l][i] = 0; a[l][i] = 0; }
+    for (int i = 0; i < kSlots; ++i) plug[i] = 0;
+    for (int l = 0; l < 2; ++l) {
+        if (!avail[l]) continue;
+        for (int i = 1; i <= 21; ++i) {
+            if (kPhi5[i - 1][l] > 0) {
+                p[l][i] = 2.0 * kPhi5[i - 1][l] / G[l];
+                eh[l][i] = (double)r.hits[l][i] / (K[l] * p[l][i]);
+            }
+        }
+    }
+    for (int i = 1; i <= 21; ++i) {
+        if (i == 2) continue;
+        const bool s0 = avail[0] && kPhi5[i - 1][0] > 0, s1 = avail[1] && kPhi5[i - 1][1] > 0;
+        if (!s0 && !s1) continue;
+        if (s0 != s1) {
+            const int l = s0 ? 0 : 1;
+            const double e = eh[l][i];
+            plug[i] = e;
+            r.est[i] = e;
+            r.var[i] = e / K[l] * (1.0 / p[l][i] - e);
+            a[l][i] = 1.0;
+            continue;
+        }
+        const double e = ((double)r.hits[0][i] + (double)r.hits[1][i]) / (K[0] * p[0][i] + K[1] * p[1][i]);
+        plug[i] = e;
+        const double V1 = fmax(e / K[0] * (1.0 / p[0][i] - e), 0.0);
+        const double V2 = fmax(e / K[1] * (1.0 / p[1][i] - e), 0.0);
+        if (V1 + V2 > 0.0) {
+            a[0][i] = V2 / (V1 + V2);
+            a[1][i] = V1 / (V1 + V2);
+            r.var[i] = V1 * V2 / (V1 + V2);
+        } else {
+            a[0][i] = a[1][i] = 0.5;
+            r.var[i] = 0.0;
+        }
+        r.est[i] = a[0][i] * eh[0][i] + a[1][i] * eh[1][i];
+    }
+    for (int l = 0; l < 2; ++l)
+        for (int i = 0; i < kSlots; ++i) r.lambda[l][i] = a[l][i];
+    // eta_2 from the Lambda_4 identity and its variance (Theorem 10)
+    double s = 0.0;
+    for (int i = 1; i <= 21; ++i)
+        if (i != 2 && kPhi5[i - 1][2] > 0) s += kPhi5[i - 1][2] * r.est[i];
+    r.est[2] = u128_to_double(tot->lambda4) - s;
+    double v2 = 0.0;
+    for (int i = 1; i <= 21; ++i)
+        if (i != 2 && kPhi5[i - 1][2] > 0) v2 += kPhi5[i - 1][2] * kPhi5[i - 1][2] * r.var[i];
+    for (int i = 1; i <= 21; ++i) {
+        if (i == 2 || kPhi5[i - 1][2] == 0) continue;
+        for (int j = 1; j <= 21; ++j) {
+            if (j == 2 || j == i || kPhi5[j - 1][2] == 0) continue;
+            double c = 0.0;
+            for (int l = 0; l < 2; ++l)
+                if (avail[l]) c -= (a[l][i] * plug[i]) * (a[l][j] * plug[j]) / K[l];
+            v2 += kPhi5[i - 1][2] * kPhi5[j - 1][2] * c;
+        }
+    }
+    r.var[2] = v2;
+    *out = r;
+}
+
+}  // namespace
+
+cudaError_t launch_finalize(const FinalizeIn &in, const uint64_t *hits_dev, const DevTotals *tot, void *result_dev,
+                            cudaStream_t s) {
+    k_finalize<<<1, 32, 0, s>>>(in, hits_dev, tot, static_cast<moss_result *>(result_dev));
+    return cudaGetLastError();
+}
+
+}  // namespace moss

@@ -1,0 +1,120 @@
+// moss_internal.cuh -- shared definitions of the libmoss translation units.
+//
+// Device layout of a loaded graph (all arrays in HBM, owned by moss_graph):
+//   vert[n]   uint4 {off, deg, S_v, 0}           S_v = sum_{x in N_v} (d_x - 1)
+//   col[nnz]  uint32 sorted neighbour lists N_v   (the CSR, Table 1)
+//   slot[nnz] uint4 {col, thr, alias, twin}       per-list alias table of
+//             sigma^(v) (eq. 1): keep the column when y < thr for y uniform
+//             in [0, S_v), else take position alias; twin = position of v in
+//             N_col (POS of Sec. 4.1.3, used to exclude v from N_col)
+//   acc[nnz]  uint32 ACC_sigma^(v) exclusive prefix of (d_x - 1) within N_v
+//   q[n]      uint64 Q_v = sum (d_x - 1)^2   (Gamma^(2)_v = S_v^2 - Q_v)
+//   gam[l][n] u128 vertex weights Gamma_v, Gamma^(1)_v, Gamma^(2)_v
+//   seed[l][n] uint4 {T lo, T hi, alias, 0}: vertex alias table of weight l,
+//             keep the column when x < T for a 64-bit word x.
+// nnz < 2^32 bounds every S_v, ACC entry and sigma threshold below 2^32.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+typedef unsigned __int128 u128;
+
+namespace moss {
+
+constexpr int kSlots = 22;            // [0] collisions, [1..21] classes
+
+struct alignas(16) DevTotals {
+    u128 gamma[3];                    // Gamma, Gamma^(1), Gamma^(2)
+    u128 lambda3, lambda4;            // Lambda_3, Lambda_4
+    uint32_t d_max;
+    uint32_t pad[3];
+};
+
+struct DevGraph {
+    const uint4 *vert;
+    const uint32_t *col;
+    const uint4 *slot;
+    const uint32_t *acc;
+    const uint64_t *q;
+    const uint4 *seed[3];
+    uint32_t n;
+};
+
+// Status flags raised by kernels (bitwise OR into a device word).
+enum : uint32_t {
+    kErrRowPtr = 1u << 0,     // row_ptr not monotone / wrong ends
+    kErrRange = 1u << 1,      // neighbour id >= n
+    kErrSelf = 1u << 2,       // self loop
+    kErrOrder = 1u << 3,      // list not strictly increasing (or duplicate)
+    kErrAsym = 1u << 4,       // (v,u) without (u,v)
+    kErrOverflow = 1u << 5,   // exact total out of range
+};
+
+// ------------------------------------------------------------ arithmetic --
+__host__ __device__ inline uint64_t mulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((u128)a * b) >> 64);
+#endif
+}
+
+// floor(x * m / 2^64): a uniform index in [0, m) from a 64-bit word
+__device__ __forceinline__ uint64_t word_index(uint64_t x, uint64_t m) { return __umul64hi(x, m); }
+
+// ---------------------------------------------------------------- Philox --
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+// as 1, 2, 3", SC'11): ten rounds, each multiplying counter words 0 and 2 by
+// the two round constants (128-bit products), crossing the halves and
+// xoring in the key; the key advances by a Weyl increment between rounds.
+struct Words4 { uint64_t x[4]; };
+
+__device__ __forceinline__ Words4 philox4x64(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                             uint64_t k0, uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += W0; k1 += W1;
+    }
+    Words4 w;
+    w.x[0] = c0; w.x[1] = c1; w.x[2] = c2; w.x[3] = c3;
+    return w;
+}
+
+// ----------------------------------------------------- host-side launches --
+// moss_tables.cu
+cudaError_t launch_vertices(const void *row_ptr, int is64, uint32_t n, uint64_t nnz, uint4 *vert,
+                            uint32_t *flags, cudaStream_t s);
+cudaError_t launch_slots(uint32_t n, const uint32_t *col, uint4 *vert, uint4 *slot, uint32_t *acc,
+                         uint64_t *q, u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials,
+                         int blocks, uint32_t *flags, cudaStream_t s);
+cudaError_t launch_totals(const u128 *partials, int blocks, DevTotals *tot, cudaStream_t s);
+cudaError_t launch_sigma_alias(uint32_t n, const uint4 *vert, const uint32_t *acc, uint4 *slot,
+                               uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s);
+cudaError_t launch_seed_alias(uint32_t n, const u128 *w, const DevTotals *tot, int which, uint4 *seed,
+                              uint32_t *scratch_idx, u128 *scratch_pre, uint32_t *flags, cudaStream_t s);
+int table_blocks(uint32_t n);
+
+// moss_sample.cu
+void upload_luts(const uint8_t *lut4, const uint8_t *lut5);
+cudaError_t launch_sample(int method, const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed,
+                          uint64_t *partials, int blocks, uint8_t *classes, uint32_t *verts,
+                          cudaStream_t s);
+cudaError_t launch_reduce(const uint64_t *partials, int blocks, uint64_t *out, cudaStream_t s);
+int sample_blocks(int method, int device);
+
+// moss_finalize.cu
+struct FinalizeIn {
+    int k;
+    uint64_t K[2];
+};
+cudaError_t launch_finalize(const FinalizeIn &in, const uint64_t *hits_dev, const DevTotals *tot,
+                            void *result_dev, cudaStream_t s);
+
+}  // namespace moss

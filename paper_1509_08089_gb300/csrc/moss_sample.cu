@@ -1,0 +1,357 @@
+// moss_sample.cu -- the sampling loop of MOSS-4 (Algorithm 1), T-5
+// (Algorithm 3) and Path-5 (Algorithm 4) on the device.
+//
+// One thread draws one sample at a time (grid-stride over sample ids), so
+// every sample is an independent chain of dependent gathers:
+//   Philox words -> vertex alias record (16 B) -> vert[v] (16 B) -> sigma
+//   record(s) of N_v (16 B each) -> uniform list picks (4 B) -> vert[] of the
+//   new vertices -> lock-step binary searches for the unknown pairs ->
+//   edge mask -> class through a shared-memory table.
+// Counts are aggregated per warp with __match_any_sync into shared-memory
+// histograms and leave the block as one row of per-block partials; a second
+// kernel adds the rows in a fixed order.  No global atomics.
+//
+// Word schedule (x_i = word i of the sample; Philox4x64-10 counter
+// {s, i div 4, method, 0}, key {seed, 0}):
+//   MOSS-4 : x0,x1 vertex draw; x2,x3 sigma draw of u; x4 w; x5 r.
+//   T-5    : x0,x1 vertex draw; x2,x3 sigma of u; x4 w; x5 r; x6 t.
+//   Path-5 : x0,x1 vertex draw; x2 r; x3 t; attempts a = 0,1 use
+//            x(4+4a)..x(7+4a) for two independent sigma draws (u, w), kept
+//            when the positions differ (sigma_u sigma_w / (1 - sum sigma^2)
+//            is exactly tau_u mu_w of Sec. 5.1.2); if both collide, x12 draws
+//            u from tau^(v) and x13 draws w from mu^(v,u) with the interval of
+//            u removed from ACC (Sec. 5.1.4).
+// RandomVertex(N_v - X) (Sec. 4.1.3) takes the j-th admissible position,
+// skipping the excluded positions of X in list order.
+#include "moss_internal.cuh"
+
+namespace moss {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kLut = 1024;
+
+__device__ uint8_t g_lut4[64];
+__device__ uint8_t g_lut5[1024];
+
+__device__ __forceinline__ uint4 ld4(const uint4 *p) { return __ldg(p); }
+__device__ __forceinline__ uint32_t ld1(const uint32_t *p) { return __ldg(p); }
+
+struct Pick {
+    uint32_t pos;   // position in N_v
+    uint32_t id;    // the vertex
+    uint32_t twin;  // position of v in N_id
+};
+
+// WeightRandomVertex(V, .) through a vertex alias table
+__device__ __forceinline__ uint32_t draw_vertex(const uint4 *seed, uint32_t n, uint64_t xc, uint64_t xt) {
+    const uint32_t c = (uint32_t)word_index(xc, n);
+    const uint4 r = ld4(seed + c);
+    const uint64_t T = ((uint64_t)r.y << 32) | r.x;
+    return xt < T ? c : r.z;
+}
+
+// WeightRandomVertex(N_v, sigma^(v)) through the list's alias table
+__device__ __forceinline__ Pick draw_sigma(const uint4 *slot, uint32_t ov, uint32_t dv, uint32_t Sv, uint64_t xc,
+                                           uint64_t xt) {
+    const uint32_t j = (uint32_t)word_index(xc, dv);
+    const uint4 rec = ld4(slot + ov + j);
+    const uint64_t y = word_index(xt, Sv);
+    if (y < rec.y) return Pick{j, rec.x, rec.w};
+    const uint4 al = ld4(slot + ov + rec.z);
+    return Pick{rec.z, al.x, al.w};
+}
+
+__device__ __forceinline__ uint32_t skip1(uint32_t j, uint32_t e) { return j < e ? j : j + 1; }
+
+__device__ __forceinline__ uint32_t skip2(uint32_t j, uint32_t e1, uint32_t e2) {
+    const uint32_t lo = min(e1, e2), hi = max(e1, e2);
+    j += (j >= lo);
+    j += (j >= hi);
+    return j;
+}
+
+// Membership tests (a_p, b_p) in E for P pairs, advanced in lock step so the
+// P searches of a sample overlap in memory.  Each pair searches the shorter
+// of the two sorted lists.  Returns bit p set when the pair is an edge.
+template <int P>
+__device__ __forceinline__ uint32_t probe_pairs(const uint32_t *col, const uint4 (&ra)[P], const uint4 (&rb)[P],
+                                                const uint32_t (&a)[P], const uint32_t (&b)[P]) {
+    uint32_t lo[P], len[P], key[P];
+    uint32_t found = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const bool use_a = ra[p].y <= rb[p].y;
+        lo[p] = use_a ? ra[p].x : rb[p].x;
+        len[p] = use_a ? ra[p].y : rb[p].y;
+        key[p] = use_a ? b[p] : a[p];
+    }
+    bool any = true;
+    while (any) {
+        any = false;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (len[p] > 0) {
+                const uint32_t half = len[p] >> 1;
+                const uint32_t val = ld1(col + lo[p] + half);
+                if (val == key[p]) {
+                    found |= 1u << p;
+                    len[p] = 0;
+                } else if (val < key[p]) {
+                    lo[p] += half + 1;
+                    len[p] -= half + 1;
+                } else {
+                    len[p] = half;
+                }
+                any |= len[p] > 0;
+            }
+        }
+    }
+    return found;
+}
+
+struct Sample {
+    uint32_t v[5];
+    int cls;
+};
+
+__device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
+    Sample out;
+    const Words4 a = philox4x64(s, 0, 0, 0, seed, 0);
+    const Words4 b = philox4x64(s, 1, 0, 0, seed, 0);
+    const uint32_t v = draw_vertex(g.seed[0], g.n, a.x[0], a.x[1]);
+    const uint4 vr = ld4(g.vert + v);
+    const Pick pu = draw_sigma(g.slot, vr.x, vr.y, vr.z, a.x[2], a.x[3]);
+    const uint32_t jw = skip1((uint32_t)word_index(b.x[0], vr.y - 1), pu.pos);
+    const uint32_t w = ld1(g.col + vr.x + jw);
+    const uint4 ur = ld4(g.vert + pu.id);
+    const uint32_t jr = skip1((uint32_t)word_index(b.x[1], ur.y - 1), pu.twin);
+    const uint32_t r = ld1(g.col + ur.x + jr);
+    out.v[0] = v; out.v[1] = pu.id; out.v[2] = w; out.v[3] = r; out.v[4] = 0;
+    if (r == pu.id || r == w) {
+        out.cls = 0;
+        return out;
+    }
+    const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r);
+    // unknown pairs: v-r, u-w, w-r
+    const uint4 ra[3] = {vr, ur, wr}, rb[3] = {rr, wr, rr};
+    const uint32_t A[3] = {v, pu.id, w}, B[3] = {r, w, r};
+    const uint32_t f = probe_pairs<3>(g.col, ra, rb, A, B);
+    // pair bits (0,1)(0,2)(0,3)(1,2)(1,3)(2,3); known: v-u, v-w, u-r
+    const uint32_t mask = 0x1u | 0x2u | ((f & 1u) << 2) | (((f >> 1) & 1u) << 3) | 0x10u | (((f >> 2) & 1u) << 5);
+    out.cls = lut[mask];
+    return out;
+}
+
+__device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
+    Sample out;
+    const Words4 a = philox4x64(s, 0, 1, 0, seed, 0);
+    const Words4 b = philox4x64(s, 1, 1, 0, seed, 0);
+    const uint32_t v = draw_vertex(g.seed[1], g.n, a.x[0], a.x[1]);
+    const uint4 vr = ld4(g.vert + v);
+    const Pick pu = draw_sigma(g.slot, vr.x, vr.y, vr.z, a.x[2], a.x[3]);
+    const uint32_t jw = skip1((uint32_t)word_index(b.x[0], vr.y - 1), pu.pos);
+    const uint32_t jr = skip2((uint32_t)word_index(b.x[1], vr.y - 2), pu.pos, jw);
+    const uint32_t w = ld1(g.col + vr.x + jw);
+    const uint32_t r = ld1(g.col + vr.x + jr);
+    const uint4 ur = ld4(g.vert + pu.id);
+    const uint32_t jt = skip1((uint32_t)word_index(b.x[2], ur.y - 1), pu.twin);
+    const uint32_t t = ld1(g.col + ur.x + jt);
+    out.v[0] = v; out.v[1] = pu.id; out.v[2] = w; out.v[3] = r; out.v[4] = t;
+    if (t == w || t == r) {
+        out.cls = 0;
+        return out;
+    }
+    const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r), tr = ld4(g.vert + t);
+    // unknown pairs: u-w, u-r, w-r, v-t, w-t, r-t
+    const uint4 ra[6] = {ur, ur, wr, vr, wr, rr}, rb[6] = {wr, rr, rr, tr, tr, tr};
+    const uint32_t A[6] = {pu.id, pu.id, w, v, w, r}, B[6] = {w, r, r, t, t, t};
+    const uint32_t f = probe_pairs<6>(g.col, ra, rb, A, B);
+    // pair bits (0,1)(0,2)(0,3)(0,4)(1,2)(1,3)(1,4)(2,3)(2,4)(3,4)
+    // known: v-u (0), v-w (1), v-r (2), u-t (6)
+    uint32_t mask = 0x1u | 0x2u | 0x4u | 0x40u;
+    mask |= ((f >> 0) & 1u) << 4;   // u-w
+    mask |= ((f >> 1) & 1u) << 5;   // u-r
+    mask |= ((f >> 2) & 1u) << 7;   // w-r
+    mask |= ((f >> 3) & 1u) << 3;   // v-t
+    mask |= ((f >> 4) & 1u) << 8;   // w-t
+    mask |= ((f >> 5) & 1u) << 9;   // r-t
+    out.cls = lut[mask];
+    return out;
+}
+
+// Path-5 fallback: u from tau^(v) by a scan, w from mu^(v,u) by a search
+__device__ __noinline__ void path5_fallback(const DevGraph &g, uint32_t v, uint4 vr, uint64_t x12, uint64_t x13,
+                                            uint32_t &iu, uint32_t &iw) {
+    const uint32_t o = vr.x, d = vr.y, S = vr.z;
+    const uint64_t G = (uint64_t)S * S - g.q[v];
+    const uint64_t y = word_index(x12, G);
+    uint64_t run = 0;
+    iu = 0;
+    for (uint32_t i = 0; i < d; ++i) {
+        const uint32_t wi = (i + 1 < d ? ld1(g.acc + o + i + 1) : S) - ld1(g.acc + o + i);
+        const uint64_t tw = (uint64_t)wi * (S - wi);
+        if (y < run + tw) {
+            iu = i;
+            break;
+        }
+        run += tw;
+    }
+    const uint32_t au = ld1(g.acc + o + iu);
+    const uint32_t wu = (iu + 1 < d ? ld1(g.acc + o + iu + 1) : S) - au;
+    uint64_t y2 = word_index(x13, (uint64_t)(S - wu));
+    if (y2 >= au) y2 += wu;
+    // last i with ACC[i] <= y2
+    uint32_t lo = 0, len = d;
+    while (len > 0) {
+        const uint32_t half = len >> 1;
+        if ((uint64_t)ld1(g.acc + o + lo + half) <= y2) { lo += half + 1; len -= half + 1; } else { len = half; }
+    }
+    iw = lo - 1;
+}
+
+__device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
+    Sample out;
+    const Words4 a = philox4x64(s, 0, 2, 0, seed, 0);
+    const uint32_t v = draw_vertex(g.seed[2], g.n, a.x[0], a.x[1]);
+    const uint4 vr = ld4(g.vert + v);
+    const Words4 b = philox4x64(s, 1, 2, 0, seed, 0);
+    Pick pu = draw_sigma(g.slot, vr.x, vr.y, vr.z, b.x[0], b.x[1]);
+    Pick pw = draw_sigma(g.slot, vr.x, vr.y, vr.z, b.x[2], b.x[3]);
+    if (pu.pos == pw.pos) {
+        const Words4 c = philox4x64(s, 2, 2, 0, seed, 0);
+        pu = draw_sigma(g.slot, vr.x, vr.y, vr.z, c.x[0], c.x[1]);
+        pw = draw_sigma(g.slot, vr.x, vr.y, vr.z, c.x[2], c.x[3]);
+        if (pu.pos == pw.pos) {
+            const Words4 d4 = philox4x64(s, 3, 2, 0, seed, 0);
+            uint32_t iu, iw;
+            path5_fallback(g, v, vr, d4.x[0], d4.x[1], iu, iw);
+            const uint4 su = ld4(g.slot + vr.x + iu), sw = ld4(g.slot + vr.x + iw);
+            pu = Pick{iu, su.x, su.w};
+            pw = Pick{iw, sw.x, sw.w};
+        }
+    }
+    const uint32_t u = pu.id, w = pw.id;
+    const uint4 ur = ld4(g.vert + u), wr = ld4(g.vert + w);
+    const uint32_t r = ld1(g.col + ur.x + skip1((uint32_t)word_index(a.x[2], ur.y - 1), pu.twin));
+    const uint32_t t = ld1(g.col + wr.x + skip1((uint32_t)word_index(a.x[3], wr.y - 1), pw.twin));
+    out.v[0] = v; out.v[1] = u; out.v[2] = w; out.v[3] = r; out.v[4] = t;
+    if (t == u || r == w || t == r) {
+        out.cls = 0;
+        return out;
+    }
+    const uint4 rr = ld4(g.vert + r), tr = ld4(g.vert + t);
+    // unknown pairs: v-r, v-t, u-w, u-t, w-r, r-t
+    const uint4 ra[6] = {vr, vr, ur, ur, wr, rr}, rb[6] = {rr, tr, wr, tr, rr, tr};
+    const uint32_t A[6] = {v, v, u, u, w, r}, B[6] = {r, t, w, t, r, t};
+    const uint32_t f = probe_pairs<6>(g.col, ra, rb, A, B);
+    // known: v-u (0), v-w (1), u-r (5), w-t (8)
+    uint32_t mask = 0x1u | 0x2u | 0x20u | 0x100u;
+    mask |= ((f >> 0) & 1u) << 2;   // v-r
+    mask |= ((f >> 1) & 1u) << 3;   // v-t
+    mask |= ((f >> 2) & 1u) << 4;   // u-w
+    mask |= ((f >> 3) & 1u) << 6;   // u-t
+    mask |= ((f >> 4) & 1u) << 7;   // w-r
+    mask |= ((f >> 5) & 1u) << 9;   // r-t
+    out.cls = lut[mask];
+    return out;
+}
+
+template <int METHOD, bool RECORD>
+__global__ void __launch_bounds__(kThreads) k_sample(DevGraph g, uint64_t first, uint64_t count, uint64_t seed,
+                                                     uint64_t *partials, uint8_t *classes, uint32_t *verts) {
+    __shared__ uint8_t lut[kLut];
+    __shared__ uint32_t hist[kWarps][kSlots];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint8_t *src = METHOD == 0 ? g_lut4 : g_lut5;
+    const int lut_n = METHOD == 0 ? 64 : 1024;
+    for (int i = threadIdx.x; i < lut_n; i += kThreads) lut[i] = src[i];
+    for (int i = threadIdx.x; i < kWarps * kSlots; i += kThreads) (&hist[0][0])[i] = 0;
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * kThreads;
+    // warp-uniform loop: every lane of a warp runs the same trip count
+    const uint64_t warp_base = ((uint64_t)blockIdx.x * kThreads) + (uint64_t)warp * 32;
+    for (uint64_t base = warp_base; base < count; base += stride) {
+        const uint64_t i = base + lane;
+        int cls = kSlots;  // no sample (tail)
+        if (i < count) {
+            const uint64_t s = first + i;
+            Sample sm;
+            if (METHOD == 0) sm = sample_moss4(g, lut, seed, s);
+            else if (METHOD == 1) sm = sample_t5(g, lut, seed, s);
+            else sm = sample_path5(g, lut, seed, s);
+            cls = sm.cls;
+            if (RECORD) {
+                classes[i] = (uint8_t)cls;
+                if (verts) {
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) verts[5 * i + k] = sm.v[k];
+                }
+            }
+        }
+        const uint32_t peers = __match_any_sync(0xffffffffu, cls);
+        if (cls < kSlots && lane == __ffs(peers) - 1) atomicAdd(&hist[warp][cls], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    if (threadIdx.x < kSlots) {
+        uint64_t sum = 0;
+        for (int w = 0; w < kWarps; ++w) sum += hist[w][threadIdx.x];
+        partials[(uint64_t)blockIdx.x * kSlots + threadIdx.x] = sum;
+    }
+}
+
+__global__ void k_reduce(const uint64_t *partials, int blocks, uint64_t *out) {
+    const int c = threadIdx.x;
+    if (c >= kSlots) return;
+    uint64_t s = 0;
+    for (int b = 0; b < blocks; ++b) s += partials[(uint64_t)b * kSlots + c];
+    out[c] = s;
+}
+
+template <int M, bool R>
+cudaError_t launch_one(const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
+                       int blocks, uint8_t *classes, uint32_t *verts, cudaStream_t s) {
+    k_sample<M, R><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+void upload_luts(const uint8_t *lut4, const uint8_t *lut5) {
+    cudaMemcpyToSymbol(g_lut4, lut4, 64);
+    cudaMemcpyToSymbol(g_lut5, lut5, 1024);
+}
+
+int sample_blocks(int method, int device) {
+    int sms = 148, per = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaError_t e = cudaSuccess;
+    if (method == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<0, false>, kThreads, 0);
+    else if (method == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<1, false>, kThreads, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<2, false>, kThreads, 0);
+    if (e != cudaSuccess || per < 1) per = 1;
+    return sms * per;
+}
+
+cudaError_t launch_sample(int method, const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed,
+                          uint64_t *partials, int blocks, uint8_t *classes, uint32_t *verts, cudaStream_t s) {
+    const bool rec = classes != nullptr;
+    switch (method * 2 + (rec ? 1 : 0)) {
+        case 0: return launch_one<0, false>(g, first, count, seed, partials, blocks, classes, verts, s);
+        case 1: return launch_one<0, true>(g, first, count, seed, partials, blocks, classes, verts, s);
+        case 2: return launch_one<1, false>(g, first, count, seed, partials, blocks, classes, verts, s);
+        case 3: return launch_one<1, true>(g, first, count, seed, partials, blocks, classes, verts, s);
+        case 4: return launch_one<2, false>(g, first, count, seed, partials, blocks, classes, verts, s);
+        case 5: return launch_one<2, true>(g, first, count, seed, partials, blocks, classes, verts, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_reduce(const uint64_t *partials, int blocks, uint64_t *out, cudaStream_t s) {
+    k_reduce<<<1, 32, 0, s>>>(partials, blocks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace moss

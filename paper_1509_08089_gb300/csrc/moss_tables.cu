@@ -1,0 +1,511 @@
+// moss_tables.cu -- the initialization step on the device.
+//
+// Paper: Sec. 4.1.3 ("Initialization", WeightRandomVertex) and Sec. 5.1.4.
+//   * vertex weights Gamma_v = (d_v-1) S_v (Sec. 4.1.1), Gamma^(1)_v =
+//     (d_v-1)(d_v-2) S_v (Sec. 5.1.1), Gamma^(2)_v = S_v^2 - Q_v (Sec. 5.1.2),
+//     S_v = sum_{x in N_v} (d_x-1), Q_v = sum (d_x-1)^2; exact totals (Table 1)
+//     and Lambda_3 = sum C(d,3), Lambda_4 = sum C(d,4) in 128-bit integers.
+//   * WeightRandomVertex is realised with alias tables (O(1) per draw) instead
+//     of the paper's prefix-array binary search (O(log d)).
+//
+// Alias construction.  m items, weights w_j, W = sum w, q_j = w_j m.  Every
+// column holds W: item j keeps thr_j, the rest goes to alias_j.  Light items
+// (q_j < W) carry a deficit D = W - q_j, heavy ones (q_j >= W) an excess
+// E = q_j - W, both taken in index order.  With A_i the exclusive prefix of
+// the light deficits and P_k the inclusive prefix of the heavy excesses, the
+// table equals the one of the sequential sweep that fills lights in order
+// from the current heavy item and moves on when the heavy item's residue
+// falls below W:
+//   light i : thr = q, alias = heavy k(i), k(i) = min{k : P_k >= A_i}
+//   heavy k : if P_k < P_total: alias = heavy k+1, thr = W + P_k - A_{i'},
+//             i' = min{i : A_i > P_k} (A_{#lights} = P_total);
+//             else thr = W, alias = itself.
+// Both prefix sums and every search are parallel, so the per-list tables
+// (a warp per list) and the vertex tables (a block scan over V, then one
+// thread per item) are built without a sequential pass.
+#include "moss_internal.cuh"
+
+namespace moss {
+
+namespace {
+
+constexpr int kWarp = 32;
+constexpr int kTableThreads = 256;
+
+__device__ __forceinline__ uint64_t shfl_up64(uint64_t v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+
+__device__ __forceinline__ uint64_t warp_incl_scan64(uint64_t v, int lane) {
+#pragma unroll
+    for (int d = 1; d < kWarp; d <<= 1) {
+        uint64_t t = shfl_up64(v, d);
+        if (lane >= d) v += t;
+    }
+    return v;
+}
+
+
+__device__ __forceinline__ u128 shfl_up_u128(u128 v, int d) {
+    uint64_t lo = __shfl_up_sync(0xffffffffu, (uint64_t)v, d);
+    uint64_t hi = __shfl_up_sync(0xffffffffu, (uint64_t)(v >> 64), d);
+    return ((u128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ u128 shfl_down_u128(u128 v, int d) {
+    uint64_t lo = __shfl_down_sync(0xffffffffu, (uint64_t)v, d);
+    uint64_t hi = __shfl_down_sync(0xffffffffu, (uint64_t)(v >> 64), d);
+    return ((u128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ u128 warp_incl_scan128(u128 v, int lane) {
+#pragma unroll
+    for (int d = 1; d < kWarp; d <<= 1) {
+        u128 t = shfl_up_u128(v, d);
+        if (lane >= d) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ u128 warp_sum128(u128 v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += shfl_down_u128(v, d);
+    return v;
+}
+
+// ------------------------------------------------------------ vertices ---
+template <typename IdxT>
+__global__ void k_vertices(const IdxT *row_ptr, uint32_t n, uint64_t nnz, uint4 *vert, uint32_t *flags) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t a = row_ptr[v], b = row_ptr[v + 1];
+        bool bad = b < a || b > nnz || (v == 0 && a != 0) || (v + 1 == n && b != nnz);
+        if (bad) {
+            atomicOr(flags, kErrRowPtr);
+            a = b = 0;
+        }
+        vert[v] = make_uint4((uint32_t)a, (uint32_t)(b - a), 0u, 0u);
+    }
+}
+
+// --------------------------------------------------------------- slots ---
+// One warp per vertex: validation, twin positions, ACC prefix, S_v, Q_v,
+// the three vertex weights and the block's share of the exact totals.
+__global__ void __launch_bounds__(kTableThreads) k_slots(uint32_t n, const uint32_t *__restrict__ col, uint4 *vert,
+                                                        uint4 *slot, uint32_t *acc, uint64_t *q, u128 *gam0,
+                                                        u128 *gam1, u128 *gam2, u128 *partials, uint32_t *flags) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    u128 t_g0 = 0, t_g1 = 0, t_g2 = 0, t_l3 = 0, t_l4 = 0;
+    uint32_t dmax = 0;
+    uint32_t err = 0;
+    for (uint64_t v = (uint64_t)blockIdx.x * wpb + warp; v < n; v += (uint64_t)gridDim.x * wpb) {
+        const uint4 vr = vert[v];
+        const uint32_t o = vr.x, d = vr.y;
+        uint64_t run = 0, qsum = 0;
+        for (uint32_t base = 0; base < d; base += kWarp) {
+            const uint32_t i = base + lane;
+            uint32_t x = 0, w = 0, twin = 0;
+            if (i < d) {
+                x = col[o + i];
+                if (x >= n) {
+                    err |= kErrRange;
+                } else {
+                    if (x == v) err |= kErrSelf;
+                    if (i > 0 && col[o + i - 1] >= x) err |= kErrOrder;
+                    const uint4 xr = vert[x];
+                    // POS of v in N_x by binary search
+                    uint32_t lo = xr.x, len = xr.y;
+                    while (len > 0) {
+                        uint32_t half = len >> 1;
+                        if (col[lo + half] < (uint32_t)v) { lo += half + 1; len -= half + 1; } else { len = half; }
+                    }
+                    if (lo >= xr.x + xr.y || col[lo] != (uint32_t)v) err |= kErrAsym;
+                    twin = lo - xr.x;
+                    w = xr.y ? xr.y - 1 : 0;
+                }
+            }
+            uint64_t incl = warp_incl_scan64(w, lane);
+            if (i < d) {
+                acc[o + i] = (uint32_t)(run + incl - w);
+                slot[o + i] = make_uint4(x, 0u, 0u, twin);
+            }
+            run += __shfl_sync(0xffffffffu, incl, 31);
+            qsum += (uint64_t)w * w;
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) qsum += __shfl_down_sync(0xffffffffu, qsum, s);
+        if (lane == 0) {
+            const uint64_t S = run;
+            vert[v].z = (uint32_t)S;
+            q[v] = qsum;
+            const u128 g0 = d >= 1 ? (u128)(d - 1) * S : 0;
+            const u128 g1 = d >= 2 ? (u128)(d - 1) * (d - 2) * S : 0;
+            const u128 g2 = (u128)S * S - qsum;
+            gam0[v] = g0;
+            gam1[v] = g1;
+            gam2[v] = g2;
+            t_g0 += g0;
+            t_g1 += g1;
+            t_g2 += g2;
+            const u128 dd = d;
+            t_l3 += d >= 3 ? dd * (dd - 1) * (dd - 2) / 6 : 0;
+            t_l4 += d >= 4 ? dd * (dd - 1) * (dd - 2) * (dd - 3) / 24 : 0;
+            dmax = d > dmax ? d : dmax;
+        }
+    }
+    if (err) atomicOr(flags, err);
+    // block reduction of the totals (lane 0 of each warp holds its share)
+    __shared__ u128 sh[5][kTableThreads / kWarp];
+    __shared__ uint32_t shmax[kTableThreads / kWarp];
+    if (lane == 0) {
+        sh[0][warp] = t_g0; sh[1][warp] = t_g1; sh[2][warp] = t_g2; sh[3][warp] = t_l3; sh[4][warp] = t_l4;
+        shmax[warp] = dmax;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        u128 s = 0;
+        for (int w = 0; w < wpb; ++w) s += sh[threadIdx.x][w];
+        partials[(uint64_t)blockIdx.x * 6 + threadIdx.x] = s;
+    } else if (threadIdx.x == 5) {
+        uint32_t m = 0;
+        for (int w = 0; w < wpb; ++w) m = shmax[w] > m ? shmax[w] : m;
+        partials[(uint64_t)blockIdx.x * 6 + 5] = m;
+    }
+}
+
+__global__ void k_totals(const u128 *partials, int blocks, DevTotals *tot) {
+    const int lane = threadIdx.x;  // one warp
+    u128 s[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = lane; b < blocks; b += kWarp)
+        for (int j = 0; j < 6; ++j) {
+            u128 x = partials[(uint64_t)b * 6 + j];
+            s[j] = j == 5 ? (x > s[j] ? x : s[j]) : s[j] + x;
+        }
+    for (int j = 0; j < 5; ++j) s[j] = warp_sum128(s[j]);
+    for (int d = 16; d > 0; d >>= 1) {
+        u128 o = shfl_down_u128(s[5], d);
+        s[5] = o > s[5] ? o : s[5];
+    }
+    if (lane == 0) {
+        tot->gamma[0] = s[0];
+        tot->gamma[1] = s[1];
+        tot->gamma[2] = s[2];
+        tot->lambda3 = s[3];
+        tot->lambda4 = s[4];
+        tot->d_max = (uint32_t)s[5];
+    }
+}
+
+// ------------------------------------------------ per-list sigma tables ---
+// weight of position p of N_v from the ACC prefix
+__device__ __forceinline__ uint32_t acc_weight(const uint32_t *acc, uint32_t o, uint32_t d, uint32_t S, uint32_t p) {
+    return (p + 1 < d ? acc[o + p + 1] : S) - acc[o + p];
+}
+
+__global__ void __launch_bounds__(kTableThreads) k_sigma_alias(uint32_t n, const uint4 *__restrict__ vert,
+                                                              const uint32_t *__restrict__ acc, uint4 *slot,
+                                                              uint32_t *idx, uint64_t *pre) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const uint32_t below = (1u << lane) - 1u;
+    for (uint64_t v = (uint64_t)blockIdx.x * wpb + warp; v < n; v += (uint64_t)gridDim.x * wpb) {
+        const uint4 vr = vert[v];
+        const uint32_t o = vr.x, d = vr.y, S = vr.z;
+        if (d == 0) continue;
+        uint32_t *slot32 = reinterpret_cast<uint32_t *>(slot);
+        if (S == 0) {  // never drawn (Gamma_v = 0): keep every column
+            for (uint32_t p = lane; p < d; p += kWarp) {
+                slot32[4 * (uint64_t)(o + p) + 1] = 0;
+                slot32[4 * (uint64_t)(o + p) + 2] = p;
+            }
+            continue;
+        }
+        const uint64_t W = S;
+        // pass 1: split into lights (front) and heavies (back) with prefixes
+        uint32_t nl = 0, nh = 0;
+        uint64_t Arun = 0, Prun = 0;
+        for (uint32_t base = 0; base < d; base += kWarp) {
+            const uint32_t j = base + lane;
+            uint64_t qj = 0;
+            bool valid = j < d, light = false;
+            if (valid) {
+                qj = (uint64_t)acc_weight(acc, o, d, S, j) * d;
+                light = qj < W;
+            }
+            const uint32_t lmask = __ballot_sync(0xffffffffu, valid && light);
+            const uint32_t hmask = __ballot_sync(0xffffffffu, valid && !light);
+            const uint64_t D = valid && light ? W - qj : 0;
+            const uint64_t E = valid && !light ? qj - W : 0;
+            const uint64_t Dincl = warp_incl_scan64(D, lane);
+            const uint64_t Eincl = warp_incl_scan64(E, lane);
+            if (valid && light) {
+                const uint32_t r = nl + __popc(lmask & below);
+                idx[o + r] = j;
+                pre[o + r] = Arun + Dincl - D;            // exclusive A_i
+            } else if (valid) {
+                const uint32_t r = nh + __popc(hmask & below);
+                idx[o + d - 1 - r] = j;
+                pre[o + d - 1 - r] = Prun + Eincl;        // inclusive P_k
+            }
+            nl += __popc(lmask);
+            nh += __popc(hmask);
+            Arun += __shfl_sync(0xffffffffu, Dincl, 31);
+            Prun += __shfl_sync(0xffffffffu, Eincl, 31);
+        }
+        __syncwarp();
+        const uint64_t Ptot = Prun;  // == Arun
+        // pass 2: thresholds and aliases
+        for (uint32_t p = lane; p < d; p += kWarp) {
+            const uint32_t j = idx[o + p];
+            const uint64_t qj = (uint64_t)acc_weight(acc, o, d, S, j) * d;
+            uint32_t thr, alias;
+            if (p < nl) {
+                const uint64_t A = pre[o + p];
+                // first heavy k with P_k >= A (heavy k stored at o + d-1-k)
+                uint32_t lo = 0, len = nh;
+                while (len > 0) {
+                    uint32_t half = len >> 1;
+                    if (pre[o + d - 1 - (lo + half)] < A) { lo += half + 1; len -= half + 1; } else { len = half; }
+                }
+                thr = (uint32_t)qj;
+                alias = idx[o + d - 1 - lo];
+            } else {
+                const uint32_t k = d - 1 - p;
+                const uint64_t Pk = pre[o + p];
+                if (Pk < Ptot) {
+                    // first light i with A_i > P_k
+                    uint32_t lo = 0, len = nl;
+                    while (len > 0) {
+                        uint32_t half = len >> 1;
+                        if (pre[o + lo + half] <= Pk) { lo += half + 1; len -= half + 1; } else { len = half; }
+                    }
+                    const uint64_t Ai = lo < nl ? pre[o + lo] : Ptot;
+                    thr = (uint32_t)(W + Pk - Ai);
+                    alias = idx[o + d - 1 - (k + 1)];
+                } else {
+                    thr = (uint32_t)W;
+                    alias = j;
+                }
+            }
+            slot32[4 * (uint64_t)(o + j) + 1] = thr;
+            slot32[4 * (uint64_t)(o + j) + 2] = alias;
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------- vertex (seed) tables ---
+constexpr int kSeedThreads = 1024;
+
+struct SeedSplit {
+    uint32_t nl, nh;
+    u128 total;  // sum of deficits == sum of excesses
+};
+
+// pass 1: one block scans all n items in index order
+__global__ void __launch_bounds__(kSeedThreads) k_seed_split(uint32_t n, const u128 *__restrict__ w,
+                                                            const DevTotals *tot, int which, uint32_t *idx,
+                                                            u128 *pre, SeedSplit *split, uint32_t *flags) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const u128 W = tot->gamma[which];
+    __shared__ uint32_t s_lc[kSeedThreads / kWarp], s_hc[kSeedThreads / kWarp];
+    __shared__ u128 s_D[kSeedThreads / kWarp], s_E[kSeedThreads / kWarp];
+    __shared__ uint32_t s_nl, s_nh;
+    __shared__ u128 s_A, s_P;
+    if (threadIdx.x == 0) {
+        s_nl = s_nh = 0;
+        s_A = s_P = 0;
+        // q = w n must stay below 2^128 for every item: W n < 2^128 suffices
+        if (n > 1 && W > (~(u128)0) / n) atomicOr(flags, kErrOverflow);
+    }
+    __syncthreads();
+    if (W == 0) {
+        if (threadIdx.x == 0) { split->nl = 0; split->nh = 0; split->total = 0; }
+        return;
+    }
+    const uint32_t below = (1u << lane) - 1u;
+    for (uint64_t base = 0; base < n; base += kSeedThreads) {
+        const uint64_t j = base + threadIdx.x;
+        const bool valid = j < n;
+        u128 qj = valid ? w[j] * (u128)n : 0;
+        const bool light = valid && qj < W;
+        const bool heavy = valid && !light;
+        const uint32_t lmask = __ballot_sync(0xffffffffu, light);
+        const uint32_t hmask = __ballot_sync(0xffffffffu, heavy);
+        const u128 D = light ? W - qj : 0;
+        const u128 E = heavy ? qj - W : 0;
+        const u128 Dincl = warp_incl_scan128(D, lane);
+        const u128 Eincl = warp_incl_scan128(E, lane);
+        if (lane == 31) {
+            s_lc[warp] = __popc(lmask);
+            s_hc[warp] = __popc(hmask);
+            s_D[warp] = Dincl;
+            s_E[warp] = Eincl;
+        }
+        __syncthreads();
+        if (warp == 0) {  // scan the per-warp totals
+            uint32_t lc = s_lc[lane], hc = s_hc[lane];
+            u128 dd = s_D[lane], ee = s_E[lane];
+            uint32_t lci = lc, hci = hc;
+#pragma unroll
+            for (int d = 1; d < kWarp; d <<= 1) {
+                uint32_t a = __shfl_up_sync(0xffffffffu, lci, d), b = __shfl_up_sync(0xffffffffu, hci, d);
+                if (lane >= d) { lci += a; hci += b; }
+            }
+            u128 di = warp_incl_scan128(dd, lane), ei = warp_incl_scan128(ee, lane);
+            s_lc[lane] = lci - lc;   // exclusive
+            s_hc[lane] = hci - hc;
+            s_D[lane] = di - dd;
+            s_E[lane] = ei - ee;
+        }
+        __syncthreads();
+        const uint32_t nl0 = s_nl, nh0 = s_nh;
+        const u128 A0 = s_A, P0 = s_P;
+        if (light) {
+            const uint32_t r = nl0 + s_lc[warp] + __popc(lmask & below);
+            idx[r] = (uint32_t)j;
+            pre[r] = A0 + s_D[warp] + Dincl - D;                 // exclusive A_i
+        } else if (heavy) {
+            const uint32_t r = nh0 + s_hc[warp] + __popc(hmask & below);
+            idx[n - 1 - r] = (uint32_t)j;
+            pre[n - 1 - r] = P0 + s_E[warp] + Eincl;             // inclusive P_k
+        }
+        __syncthreads();
+        if (threadIdx.x == kSeedThreads - 1) {
+            s_nl = nl0 + s_lc[warp] + __popc(lmask);
+            s_nh = nh0 + s_hc[warp] + __popc(hmask);
+            s_A = A0 + s_D[warp] + Dincl;
+            s_P = P0 + s_E[warp] + Eincl;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        split->nl = s_nl;
+        split->nh = s_nh;
+        split->total = s_P;
+    }
+}
+
+// floor(thr 2^64 / W) for thr <= W, saturated (binary long division)
+__device__ __forceinline__ uint64_t quantize64(u128 thr, u128 W) {
+    if (W == 0) return 0;
+    if (thr >= W) return ~0ULL;
+    uint64_t qq = 0;
+    u128 r = thr;
+    for (int i = 0; i < 64; ++i) {
+        const bool carry = (uint64_t)(r >> 127) != 0;
+        r <<= 1;
+        qq <<= 1;
+        if (carry || r >= W) { r -= W; qq |= 1; }
+    }
+    return qq;
+}
+
+// pass 2: one thread per position of the split order
+__global__ void k_seed_fill(uint32_t n, const u128 *__restrict__ w, const DevTotals *tot, int which,
+                            const uint32_t *__restrict__ idx, const u128 *__restrict__ pre, const SeedSplit *split,
+                            uint4 *seed) {
+    const u128 W = tot->gamma[which];
+    const uint32_t nl = split->nl, nh = split->nh;
+    const u128 Ptot = split->total;
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
+        if (W == 0) {
+            seed[p] = make_uint4(0u, 0u, (uint32_t)p, 0u);
+            continue;
+        }
+        const uint32_t j = idx[p];
+        u128 thr;
+        uint32_t alias;
+        if (p < nl) {
+            const u128 A = pre[p];
+            uint32_t lo = 0, len = nh;
+            while (len > 0) {
+                uint32_t half = len >> 1;
+                if (pre[n - 1 - (lo + half)] < A) { lo += half + 1; len -= half + 1; } else { len = half; }
+            }
+            thr = w[j] * (u128)n;
+            alias = idx[n - 1 - lo];
+        } else {
+            const uint32_t k = (uint32_t)(n - 1 - p);
+            const u128 Pk = pre[p];
+            if (Pk < Ptot) {
+                uint32_t lo = 0, len = nl;
+                while (len > 0) {
+                    uint32_t half = len >> 1;
+                    if (pre[lo + half] <= Pk) { lo += half + 1; len -= half + 1; } else { len = half; }
+                }
+                const u128 Ai = lo < nl ? pre[lo] : Ptot;
+                thr = W + Pk - Ai;
+                alias = idx[n - 1 - (k + 1)];
+            } else {
+                thr = W;
+                alias = j;
+            }
+        }
+        const uint64_t T = quantize64(thr, W);
+        seed[j] = make_uint4((uint32_t)T, (uint32_t)(T >> 32), alias, 0u);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launches ---
+int table_blocks(uint32_t n) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t warps_needed = (uint64_t)n;
+    uint64_t blocks = (warps_needed + (kTableThreads / kWarp) - 1) / (kTableThreads / kWarp);
+    const uint64_t cap = (uint64_t)sms * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return (int)blocks;
+}
+
+cudaError_t launch_vertices(const void *row_ptr, int is64, uint32_t n, uint64_t nnz, uint4 *vert, uint32_t *flags,
+                            cudaStream_t s) {
+    const int threads = 256;
+    uint64_t blocks = ((uint64_t)n + threads - 1) / threads;
+    if (blocks > 65535) blocks = 65535;
+    if (blocks < 1) blocks = 1;
+    if (is64)
+        k_vertices<uint64_t><<<(unsigned)blocks, threads, 0, s>>>(static_cast<const uint64_t *>(row_ptr), n, nnz,
+                                                                   vert, flags);
+    else
+        k_vertices<uint32_t><<<(unsigned)blocks, threads, 0, s>>>(static_cast<const uint32_t *>(row_ptr), n, nnz,
+                                                                   vert, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slots(uint32_t n, const uint32_t *col, uint4 *vert, uint4 *slot, uint32_t *acc, uint64_t *q,
+                         u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials, int blocks, uint32_t *flags,
+                         cudaStream_t s) {
+    k_slots<<<blocks, kTableThreads, 0, s>>>(n, col, vert, slot, acc, q, gam0, gam1, gam2, partials, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_totals(const u128 *partials, int blocks, DevTotals *tot, cudaStream_t s) {
+    k_totals<<<1, kWarp, 0, s>>>(partials, blocks, tot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sigma_alias(uint32_t n, const uint4 *vert, const uint32_t *acc, uint4 *slot,
+                               uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s) {
+    k_sigma_alias<<<table_blocks(n), kTableThreads, 0, s>>>(n, vert, acc, slot, scratch_idx, scratch_pre);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_alias(uint32_t n, const u128 *w, const DevTotals *tot, int which, uint4 *seed,
+                              uint32_t *scratch_idx, u128 *scratch_pre, uint32_t *flags, cudaStream_t s) {
+    // the split record lives after the n prefix entries of the scratch
+    SeedSplit *split = reinterpret_cast<SeedSplit *>(scratch_pre + n);
+    k_seed_split<<<1, kSeedThreads, 0, s>>>(n, w, tot, which, scratch_idx, scratch_pre, split, flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int threads = 256;
+    uint64_t blocks = ((uint64_t)n + threads - 1) / threads;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_seed_fill<<<(unsigned)blocks, threads, 0, s>>>(n, w, tot, which, scratch_idx, scratch_pre, split, seed);
+    return cudaGetLastError();
+}
+
+}  // namespace moss

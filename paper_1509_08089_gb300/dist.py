@@ -1,0 +1,56 @@
+"""Sharding a sample budget over ranks (one GPU per rank).
+
+Samples are independent and keyed by their id, so a budget splits into
+contiguous id ranges, each rank counts its range with its own graph replica,
+and the only exchange is the sum of 2 x 22 integer counts -- exact for any
+number of ranks.  Weak scaling: every rank draws ``budget`` samples, rank r
+takes ids [r K_l, (r+1) K_l) of each sub-method l.
+"""
+from __future__ import annotations
+
+from typing import Callable
+
+import numpy as np
+
+from . import (MOSS4, NSLOTS, PATH5, T5, moss_finalize, moss_sample_counts, result_dict)
+
+
+def shard(total: int, rank: int, world: int) -> tuple[int, int]:
+    """Contiguous split of [0, total) into world parts; the first
+    total % world parts get one extra id.  Returns (first, count)."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("bad rank/world")
+    base, extra = divmod(total, world)
+    first = rank * base + min(rank, extra)
+    return first, base + (1 if rank < extra else 0)
+
+
+def sub_budgets(k: int, budget: int) -> list[tuple[int, int]]:
+    """(method, samples) per sub-method for one estimate (K1 = K2, Sec. 5.1.5)."""
+    if k == 4:
+        return [(MOSS4, budget)]
+    return [(T5, budget // 2), (PATH5, budget - budget // 2)]
+
+
+def weak_ranges(k: int, budget: int, rank: int) -> list[tuple[int, int, int]]:
+    """(method, first, count) of rank ``rank`` when every rank draws ``budget``."""
+    return [(m, rank * K, K) for m, K in sub_budgets(k, budget)]
+
+
+def estimate_weak(g, k: int, budget: int, seed: int, rank: int, world: int,
+                  allreduce: Callable[[np.ndarray], np.ndarray], stream=None) -> dict:
+    """One weak-scaled estimate: this rank's counts, summed over ranks by
+    ``allreduce`` (int64[2, 22] -> int64[2, 22]), then the device finalize.
+    Methods whose total weight is zero draw nothing (as in the single call)."""
+    import torch
+
+    stats = g.stats()
+    counts = torch.zeros((2, NSLOTS), dtype=torch.int64, device=f"cuda:{g.device}")
+    K = [0, 0]
+    for slot, (m, first, count) in enumerate(weak_ranges(k, budget, rank)):
+        if stats.gamma[m][0] == 0 and stats.gamma[m][1] == 0:
+            continue
+        moss_sample_counts(g.handle, m, first, count, seed, counts[slot], stream)
+        K[slot] = count * world
+    total = allreduce(counts.cpu().numpy())
+    return result_dict(moss_finalize(g.handle, k, np.array(K, dtype=np.uint64), total.astype(np.uint64), stream))

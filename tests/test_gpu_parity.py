@@ -1,0 +1,249 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact: every table (vertex records, ACC, sigma alias tables, twins,
+vertex alias tables, per-vertex weights, totals), every per-sample class and
+vertex tuple, every count.  FP64 estimates: relative 1e-9 (the finalize is
+the same arithmetic in the same order; eta_2 and n_2 are compared relative
+to Lambda, since they are differences of large terms).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1509_08089_gb300 as moss
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GRAPHS = {
+    "gnp12": lambda: synth.gnp(12, 0.45, 5),
+    "cl_n200": lambda: synth.chung_lu(200, 2.3, 6.0, 30.0, seed=7),
+    "rgg2k": lambda: synth.rgg(2000, 12.0, seed=3),
+    "cl_n2k": lambda: synth.workload("cl_n2k"),
+    "cl_n100k": lambda: synth.workload("cl_n100k"),
+}
+
+_cache = {}
+
+
+def pair(name):
+    if name not in _cache:
+        rp, col = GRAPHS[name]()
+        _cache[name] = (rp, col, oracle.OracleGraph(rp, col), moss.Graph(rp, col, device=0))
+    return _cache[name]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cleanup():
+    yield
+    for rp, col, og, g in _cache.values():
+        g.close()
+    _cache.clear()
+
+
+def gpu_records(g, method, first, count, seed):
+    cls = torch.empty(count, dtype=torch.uint8, device="cuda")
+    verts = torch.empty(count * 5, dtype=torch.int32, device="cuda")
+    moss.moss_sample_records(g.handle, method, first, count, seed, cls, verts)
+    torch.cuda.synchronize()
+    return cls.cpu().numpy(), verts.cpu().numpy().view(np.uint32).reshape(count, 5)
+
+
+def gpu_counts(g, method, first, count, seed):
+    c = torch.zeros(22, dtype=torch.int64, device="cuda")
+    moss.moss_sample_counts(g.handle, method, first, count, seed, c)
+    torch.cuda.synchronize()
+    return c.cpu().numpy().view(np.uint64)
+
+
+def u128(a):
+    return [int(a[i, 0]) | (int(a[i, 1]) << 64) for i in range(a.shape[0])]
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_tables_bit_exact(name):
+    rp, col, og, g = pair(name)
+    n, nnz = og.n, og.nnz
+    deg, S, Q, gam = og.vertex()
+    vert = moss.moss_table_export(g.handle, moss.TABLE_VERT, np.zeros((n, 4), dtype=np.uint32))
+    assert np.array_equal(vert[:, 0], rp[:-1].astype(np.uint32))
+    assert np.array_equal(vert[:, 1], deg.astype(np.uint32))
+    assert np.array_equal(vert[:, 2], S.astype(np.uint32))
+    thr, alias, acc = og.sigma_table()
+    acc_g = moss.moss_table_export(g.handle, moss.TABLE_ACC, np.zeros(nnz, dtype=np.uint32))
+    assert np.array_equal(acc_g, acc.astype(np.uint32))
+    slot = moss.moss_table_export(g.handle, moss.TABLE_SLOT, np.zeros((nnz, 4), dtype=np.uint32))
+    assert np.array_equal(slot[:, 0], col)
+    assert np.array_equal(slot[:, 1], thr.astype(np.uint32))
+    assert np.array_equal(slot[:, 2], alias)
+    # twin: position of v in N_col
+    owner = np.repeat(np.arange(n, dtype=np.int64), deg.astype(np.int64))
+    c64 = col.astype(np.int64)
+    pos = np.array([np.searchsorted(col[rp[x]:rp[x + 1]], v) for v, x in zip(owner, c64)], dtype=np.int64) \
+        if nnz <= 200_000 else None
+    if pos is not None:
+        assert np.array_equal(slot[:, 3].astype(np.int64), pos)
+    else:  # large graph: check the defining property on all slots
+        assert np.array_equal(col[rp[c64] + slot[:, 3].astype(np.int64)].astype(np.int64), owner)
+    for l in range(3):
+        sthr, T, salias = og.seed_table(l)
+        seed = moss.moss_table_export(g.handle, moss.TABLE_SEED0 + l, np.zeros((n, 4), dtype=np.uint32))
+        Tg = seed[:, 0].astype(np.uint64) | (seed[:, 1].astype(np.uint64) << np.uint64(32))
+        assert np.array_equal(Tg, T), l
+        assert np.array_equal(seed[:, 2], salias), l
+        gw = moss.moss_table_export(g.handle, moss.TABLE_GAMMA0 + l, np.zeros((n, 2), dtype=np.uint64))
+        assert u128(gw) == gam[l]
+    st = g.stats()
+    for l in range(3):
+        assert (int(st.gamma[l][0]) | (int(st.gamma[l][1]) << 64)) == og.Gamma[l]
+    assert (int(st.lambda3[0]) | (int(st.lambda3[1]) << 64)) == og.Lambda3
+    assert (int(st.lambda4[0]) | (int(st.lambda4[1]) << 64)) == og.Lambda4
+    assert st.d_max == int(deg.max())
+
+
+@pytest.mark.parametrize("name", ["gnp12", "cl_n200", "rgg2k", "cl_n2k", "cl_n100k"])
+@pytest.mark.parametrize("method", [0, 1, 2])
+def test_records_bit_exact(name, method):
+    rp, col, og, g = pair(name)
+    if og.Gamma[method] == 0:
+        pytest.skip("method has no sample on this graph")
+    first, count = (12_345, 100_003) if name != "cl_n100k" else (49_990_000, 20_011)
+    seed = 0xC0FFEE + method
+    cls, verts = gpu_records(g, method, first, count, seed)
+    ocnt, ocls, overts = og.run(method, seed, count, first=first, record=True)
+    bad = np.nonzero(ocls != cls)[0]
+    assert bad.size == 0, (bad[:5], ocls[bad[:5]], cls[bad[:5]], overts[bad[:3]], verts[bad[:3]])
+    ncol = 4 if method == 0 else 5
+    assert np.array_equal(verts[:, :ncol], overts[:, :ncol])
+
+
+@pytest.mark.parametrize("name", ["gnp12", "cl_n200", "rgg2k", "cl_n2k"])
+def test_counts_and_estimates(name):
+    rp, col, og, g = pair(name)
+    budget, seed = 200_001, 99
+    for k in (4, 5):
+        r = g.estimate(k, budget, seed)
+        o = og.estimate(k, budget, seed)
+        if k == 4:
+            ref = og.run(oracle.MOSS4, seed, budget) if og.Gamma[0] else np.zeros(22, np.uint64)
+            assert np.array_equal(r["hits"][0], ref)
+        else:
+            K1, K2 = budget // 2, budget - budget // 2
+            ref1 = og.run(oracle.T5, seed, K1) if og.Gamma[1] else np.zeros(22, np.uint64)
+            ref2 = og.run(oracle.PATH5, seed, K2) if og.Gamma[2] else np.zeros(22, np.uint64)
+            assert np.array_equal(r["hits"][0], ref1)
+            assert np.array_equal(r["hits"][1], ref2)
+        assert tuple(r["K"]) == tuple(o["K"])
+        close_estimates(r, o, og, k)
+
+
+def close_estimates(r, o, og, k):
+    n = 7 if k == 4 else 22
+    lam = float(og.Lambda3 if k == 4 else og.Lambda4)
+    for i in range(1, n):
+        if i == 2:
+            assert abs(r["est"][i] - o["est"][i]) <= 1e-9 * max(lam, 1.0), (k, i)
+            assert abs(r["var"][i] - o["var"][i]) <= 1e-9 * max(abs(o["var"][i]), 1.0) + 1e-9 * lam ** 2 / 1e6
+            continue
+        assert abs(r["est"][i] - o["est"][i]) <= 1e-9 * max(abs(o["est"][i]), 1e-300), (k, i, r["est"][i], o["est"][i])
+        assert abs(r["var"][i] - o["var"][i]) <= 1e-9 * max(abs(o["var"][i]), 1e-300), (k, i)
+    if k == 4:
+        assert abs(r["triangles"] - o["triangles"]) <= 1e-9 * max(abs(o["triangles"]), 1e-300)
+    else:
+        for i in range(1, n):
+            for l in range(2):
+                assert abs(r["lam"][l][i] - o["lam"][l][i]) <= 1e-9
+
+
+def test_shards_add_up():
+    rp, col, og, g = pair("cl_n2k")
+    K, seed = 300_007, 5
+    for method in (0, 1, 2):
+        full = gpu_counts(g, method, 0, K, seed)
+        a = 123_457
+        parts = gpu_counts(g, method, 0, a, seed) + gpu_counts(g, method, a, K - a, seed)
+        assert np.array_equal(full, parts)
+        assert int(full.sum()) == K
+
+
+def test_finalize_entry_matches_oracle():
+    rp, col, og, g = pair("cl_n2k")
+    hits = np.zeros((2, 22), dtype=np.uint64)
+    hits[0] = og.run(oracle.T5, 3, 50_000)
+    hits[1] = og.run(oracle.PATH5, 3, 70_000)
+    r = moss.result_dict(moss.moss_finalize(g.handle, 5, [50_000, 70_000], hits))
+    o = oracle.finalize_moss5(hits[0], hits[1], 50_000, 70_000, og.Gamma[1], og.Gamma[2], og.Lambda4)
+    close_estimates(r, o, og, 5)
+
+
+@pytest.mark.parametrize("family", ["cycle", "star", "complete", "empty", "isolated"])
+def test_special_graphs(family):
+    if family == "cycle":
+        rp, col = synth.cycle(9)
+    elif family == "star":
+        rp, col = synth.star(7)
+    elif family == "complete":
+        rp, col = synth.complete(8)
+    elif family == "empty":
+        rp, col = np.zeros(6, dtype=np.uint64), np.zeros(0, dtype=np.uint32)
+    else:  # a triangle plus isolated vertices
+        rp, col = synth.from_edges(9, [(2, 5), (5, 7), (2, 7)])
+    og = oracle.OracleGraph(rp, col)
+    with moss.Graph(rp, col) as g:
+        for k in (4, 5):
+            r = g.estimate(k, 10_001, 11)
+            o = og.estimate(k, 10_001, 11)
+            assert tuple(r["K"]) == tuple(o["K"])
+            methods = (0,) if k == 4 else (1, 2)
+            for slot, method in enumerate(methods):
+                K = r["K"][slot]
+                ref = og.run(method, 11, K) if K else np.zeros(22, np.uint64)
+                assert np.array_equal(r["hits"][slot], ref)
+            close_estimates(r, o, og, k)
+    if family == "cycle":
+        assert r["est"][1] == pytest.approx(9.0, abs=1e-9)
+    if family == "star":
+        assert r["est"][2] == 35.0
+
+
+def test_uint32_row_ptr_and_device_inputs():
+    rp, col = synth.workload("cl_n2k")
+    og = oracle.OracleGraph(rp, col)
+    rp32 = torch.from_numpy(rp.astype(np.int32)).cuda()
+    colt = torch.from_numpy(col.astype(np.int32)).cuda()
+    with moss.Graph(rp32, colt) as g:
+        r = g.estimate(4, 50_000, 1)
+        assert np.array_equal(r["hits"][0], og.run(oracle.MOSS4, 1, 50_000))
+
+
+def test_full_size_bench_config():
+    """The benchmark's launch: k = 5, budget 1e8 on the 1M-edge graph."""
+    rp, col, og, g = pair("cl_n100k")
+    B = 100_000_000
+    r = g.estimate(5, B, seed=42)
+    K1, K2 = B // 2, B - B // 2
+    assert tuple(r["K"]) == (K1, K2)
+    assert int(r["hits"][0].sum()) == K1 and int(r["hits"][1].sum()) == K2
+    from oracle.finalize import PHI5
+    for i in range(1, 22):
+        if PHI5[i - 1, 0] == 0:
+            assert r["hits"][0][i] == 0
+        if PHI5[i - 1, 1] == 0:
+            assert r["hits"][1][i] == 0
+    # the device finalize of these counts equals the oracle's finalize of them
+    o = oracle.finalize_moss5(r["hits"][0], r["hits"][1], K1, K2, og.Gamma[1], og.Gamma[2], og.Lambda4)
+    close_estimates(r, o, og, 5)
+    # the last samples of both sub-methods, one by one against the oracle
+    for method, K in ((1, K1), (2, K2)):
+        cls, verts = gpu_records(g, method, K - 5000, 5000, 42)
+        _, ocls, overts = og.run(method, 42, 5000, first=K - 5000, record=True)
+        assert np.array_equal(cls, ocls)
+        assert np.array_equal(verts, overts)
+    # an independent seed agrees within the stated variances
+    r2 = g.estimate(5, B, seed=43)
+    for i in range(1, 22):
+        sd = np.sqrt(r["var"][i] + r2["var"][i])
+        assert abs(r["est"][i] - r2["est"][i]) <= 6 * sd + 1e-6 * abs(r["est"][i]), i
