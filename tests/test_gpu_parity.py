@@ -87,7 +87,7 @@ def test_tables_bit_exact(name):
     if pos is not None:
         assert np.array_equal(slot[:, 3].astype(np.int64), pos)
     else:  # large graph: check the defining property on all slots
-        assert np.array_equal(col[rp[c64] + slot[:, 3].astype(np.int64)].astype(np.int64), owner)
+        assert np.array_equal(col[rp.astype(np.int64)[c64] + slot[:, 3].astype(np.int64)].astype(np.int64), owner)
     for l in range(3):
         sthr, T, salias = og.seed_table(l)
         seed = moss.moss_table_export(g.handle, moss.TABLE_SEED0 + l, np.zeros((n, 4), dtype=np.uint32))
