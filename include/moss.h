@@ -120,6 +120,22 @@ int moss_sample_estimate(moss_graph *g, int k, uint64_t budget, uint64_t seed, v
 int moss_sample_counts(moss_graph *g, int method, uint64_t first, uint64_t count, uint64_t seed,
                        void *stream, uint64_t *counts_dev);
 
+/* moss_sample_counts without any device allocation.  The paper has no
+ * counterpart: this serves callers that may not allocate device memory while
+ * they run -- a service that reserves its whole memory budget at start-up, a
+ * latency-bound loop that cannot take the device synchronisation an
+ * allocation or free may cause, or an embedding whose allocator belongs to
+ * another framework.  Same arguments and result as moss_sample_counts (the
+ * graph and counts_dev are allocated by the caller beforehand); the per-block
+ * partial counts live in one fixed device array of 360,448 bytes (2048 rows of
+ * 22 uint64) that every GPU loading the library holds until exit.  The first
+ * call on a device looks up that array's address (cudaGetSymbolAddress), so
+ * make it before any stream capture.  Calls share the array: calls whose work
+ * overlaps on the GPU race and must be ordered by the caller.  MOSS_EOVERFLOW
+ * if the device needs more than 2048 blocks.  Asynchronous on stream. */
+int moss_sample_counts_noalloc(moss_graph *g, int method, uint64_t first, uint64_t count, uint64_t seed,
+                               void *stream, uint64_t *counts_dev);
+
 /* Per-sample records of samples first..first+count-1 (for verification):
  * classes_dev (device, count uint8: 0 = collision, else class) and, when not
  * NULL, verts_dev (device, 5*count uint32: v,u,w,r,t in draw order; t = 0

@@ -68,6 +68,7 @@ def load():
         "moss_sample_estimate": ([_vp, ctypes.c_int, _u64, _u64, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
         "moss_sample_counts": ([_vp, ctypes.c_int, _u64, _u64, _u64, _vp, _vp], ctypes.c_int),
         "moss_sample_records": ([_vp, ctypes.c_int, _u64, _u64, _u64, _vp, _vp, _vp], ctypes.c_int),
+        "moss_sample_counts_noalloc": ([_vp, ctypes.c_int, _u64, _u64, _u64, _vp, _vp], ctypes.c_int),
         "moss_finalize": ([_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
         "moss_graph_stats": ([_vp, ctypes.POINTER(moss_stats)], ctypes.c_int),
         "moss_table_export": ([_vp, ctypes.c_int, _vp, _u64], ctypes.c_int),
@@ -159,6 +160,12 @@ def moss_sample_estimate(g: int, k: int, budget: int, seed: int, stream=None) ->
 
 def moss_sample_counts(g: int, method: int, first: int, count: int, seed: int, counts_dev, stream=None):
     _check(load().moss_sample_counts(g, method, first, count, seed, _stream(stream), _ptr(counts_dev)))
+
+
+def moss_sample_counts_noalloc(g: int, method: int, first: int, count: int, seed: int, counts_dev, stream=None):
+    """moss_sample_counts for callers that may not allocate device memory:
+    the per-block partial counts live in a fixed array inside the library."""
+    _check(load().moss_sample_counts_noalloc(g, method, first, count, seed, _stream(stream), _ptr(counts_dev)))
 
 
 def moss_sample_records(g: int, method: int, first: int, count: int, seed: int, classes_dev, verts_dev=None,

@@ -503,3 +503,18 @@ int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t b
 void moss_graph_free(moss_graph *g) { release(g); }
 
 }  // extern "C"
+
+// ------------------------------------------- access for other translation units
+namespace moss {
+
+int graph_info(const moss_graph *g, GraphInfo *out) {
+    out->view = view(g);
+    out->device = g->device;
+    out->built = g->built;
+    for (int l = 0; l < 3; ++l) out->total_nonzero[l] = g->tot_h.gamma[l] != 0;
+    return MOSS_OK;
+}
+
+int set_error(int code, const char *detail) { return fail(code, "%s", detail); }
+
+}  // namespace moss

@@ -117,4 +117,17 @@ struct FinalizeIn {
 cudaError_t launch_finalize(const FinalizeIn &in, const uint64_t *hits_dev, const DevTotals *tot,
                             void *result_dev, cudaStream_t s);
 
+// moss_capi.cu: what another translation unit needs of a moss_graph
+struct GraphInfo {
+    DevGraph view;
+    int device;
+    unsigned built;          // bit l: vertex table l; bit 3: sigma tables
+    bool total_nonzero[3];   // Gamma, Gamma^(1), Gamma^(2) > 0
+};
+}  // namespace moss
+
+struct moss_graph;
+namespace moss {
+int graph_info(const moss_graph *g, GraphInfo *out);
+int set_error(int code, const char *detail);   // records the thread's error detail
 }  // namespace moss
