@@ -345,7 +345,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": d2h},
         "roofline": roof,
         "clocks": clk,
-        "gpu_launches": (13 if k == 5 else 9) * args.steps,
+        "gpu_launches": (13 if k == 5 else 11) * args.steps,
         "wall_s_timed": t_wall,
         "step_ms": step_ms,
     }

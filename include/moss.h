@@ -56,6 +56,13 @@ extern "C" {
 
 #define MOSS_NCLASS_SLOTS 22   /* [0] = collisions, [1..21] = classes */
 
+/* How the induced-edge tests of CIS() (Algorithms 1, 3, 4) are answered:
+ * SEARCH: binary search in the shorter sorted neighbour list (O(log d) loads);
+ * HASH (default): one lookup in a hashed set of all edges (one 16-byte bucket
+ * load in the common case).  Both give identical results. */
+#define MOSS_PROBE_SEARCH  0
+#define MOSS_PROBE_HASH    1
+
 typedef struct moss_graph moss_graph;
 
 /* Exact totals of Table 1 (as 128-bit lo/hi pairs and as doubles). */
@@ -83,7 +90,9 @@ typedef struct {
     double triangles_var;
 } moss_result;
 
-/* Load an undirected graph given as CSR.
+/* Load an undirected graph given as CSR and run the initialization pass
+ * (Sec. 4.1.3): exact per-vertex weights Gamma_v, Gamma^(1)_v, Gamma^(2)_v
+ * (Sec. 4.1.1, 5.1.1, 5.1.2), the totals of Table 1 and the ACC prefix arrays.
  *   row_ptr : n+1 offsets, uint64 when row_ptr_is_64 != 0 else uint32;
  *             row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz.
  *   col     : nnz vertex ids; each list N_v (Table 1) strictly increasing, no
@@ -97,14 +106,18 @@ typedef struct {
 int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *col,
                         uint32_t n, uint64_t nnz, int device, void *stream, moss_graph **out);
 
-/* Initialization step (Sec. 4.1.3, Sec. 5.1.4): exact per-vertex weights
- * Gamma_v, Gamma^(1)_v, Gamma^(2)_v (Sec. 4.1.1, 5.1.1, 5.1.2), the totals of
- * Table 1, the per-list alias tables of sigma^(v) (eq. 1) with the prefix
- * array ACC_sigma^(v), and the vertex alias tables of pi (k_mask bit 4) and
- * rho^(1), rho^(2) (k_mask bit 5).  k_mask: (1<<4) | (1<<5) or either.
- * MOSS_EOVERFLOW if a scaled total leaves 128 bits.  Synchronous on stream;
- * tables already built are rebuilt. */
+/* Sampling tables (Sec. 4.1.3 WeightRandomVertex, Sec. 5.1.4): the per-list
+ * alias tables of sigma^(v) (eq. 1), the vertex alias tables of pi (k_mask
+ * bit 4) and rho^(1), rho^(2) (k_mask bit 5) from the exact weights computed
+ * at load, and, under MOSS_PROBE_HASH, the hashed edge set.  k_mask:
+ * (1<<4) | (1<<5) or either.  MOSS_EOVERFLOW if a scaled total leaves 128
+ * bits.  Synchronous on stream; tables already built are rebuilt. */
 int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream);
+
+/* Select the probe strategy (MOSS_PROBE_*) for later samples.  Switching to
+ * MOSS_PROBE_HASH requires moss_build_tables afterwards (MOSS_ESTATE until
+ * then). */
+int moss_set_probe(moss_graph *g, int strategy);
 
 /* Sample-and-estimate.  k = 4: MOSS-4 with K = budget.  k = 5: T-5 with
  * K1 = floor(budget/2) and Path-5 with K2 = budget - K1 (K1 = K2, Sec. 5.1.5).

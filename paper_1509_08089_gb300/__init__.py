@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libmoss.so")
 
 MOSS_OK, MOSS_EINVAL, MOSS_ENOMEM, MOSS_ECUDA, MOSS_EGRAPH, MOSS_EOVERFLOW, MOSS_ESTATE = 0, -1, -2, -3, -4, -5, -6
 MOSS4, T5, PATH5 = 0, 1, 2
+PROBE_SEARCH, PROBE_HASH = 0, 1
 NSLOTS = 22
 TABLE_VERT, TABLE_SLOT, TABLE_ACC, TABLE_SEED0, TABLE_GAMMA0 = 0, 1, 2, 3, 6
 
@@ -65,6 +66,7 @@ def load():
         "moss_graph_load_csr": ([_vp, ctypes.c_int, _vp, ctypes.c_uint32, _u64, ctypes.c_int, _vp,
                                  ctypes.POINTER(_vp)], ctypes.c_int),
         "moss_build_tables": ([_vp, ctypes.c_uint, _vp], ctypes.c_int),
+        "moss_set_probe": ([_vp, ctypes.c_int], ctypes.c_int),
         "moss_sample_estimate": ([_vp, ctypes.c_int, _u64, _u64, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
         "moss_sample_counts": ([_vp, ctypes.c_int, _u64, _u64, _u64, _vp, _vp], ctypes.c_int),
         "moss_sample_records": ([_vp, ctypes.c_int, _u64, _u64, _u64, _vp, _vp, _vp], ctypes.c_int),
@@ -152,6 +154,10 @@ def moss_build_tables(g: int, k_mask: int = (1 << 4) | (1 << 5), stream=None):
     _check(load().moss_build_tables(g, k_mask, _stream(stream)))
 
 
+def moss_set_probe(g: int, strategy: int):
+    _check(load().moss_set_probe(g, strategy))
+
+
 def moss_sample_estimate(g: int, k: int, budget: int, seed: int, stream=None) -> moss_result:
     r = moss_result()
     _check(load().moss_sample_estimate(g, k, budget, seed, _stream(stream), ctypes.byref(r)))
@@ -211,9 +217,11 @@ def result_dict(r: moss_result) -> dict:
 class Graph:
     """Owning wrapper: load, build, sample, free."""
 
-    def __init__(self, row_ptr, col, device: int = 0, stream=None, k_mask: int = (1 << 4) | (1 << 5)):
+    def __init__(self, row_ptr, col, device: int = 0, stream=None, k_mask: int = (1 << 4) | (1 << 5),
+                 probe: int = PROBE_HASH):
         self.handle = moss_graph_load_csr(row_ptr, col, device=device, stream=stream)
         self.device = device
+        moss_set_probe(self.handle, probe)
         if k_mask:
             moss_build_tables(self.handle, k_mask, stream)
 

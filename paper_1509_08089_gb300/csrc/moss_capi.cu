@@ -170,9 +170,13 @@ struct moss_graph {
     int partial_rows = 0;
     uint64_t *counts = nullptr;  // 2 x 22
     moss_result *res_dev = nullptr;
-    moss_result *res_host = nullptr;  // pinned
-    uint32_t *flags = nullptr;        // device status word
-    uint32_t *flags_host = nullptr;   // pinned
+    uint32_t *flags = nullptr;   // device status word
+    void *arena = nullptr;       // every device array above lives in this one allocation
+    int probe = MOSS_PROBE_HASH; // membership tests: hashed edge set or list search
+    unsigned long long *hash = nullptr;  // 2 keys per bucket
+    uint64_t hash_buckets = 0;
+    moss_result res_host{};      // host staging of the result
+    uint32_t flags_host = 0;
 };
 
 namespace {
@@ -180,12 +184,9 @@ namespace {
 void release(moss_graph *g) {
     if (!g) return;
     DeviceGuard dg(g->device);
-    void *dev[] = {g->vert, g->col, g->slot, g->acc, g->q, g->gam[0], g->gam[1], g->gam[2], g->seed[0], g->seed[1],
-                   g->seed[2], g->tot, g->partials, g->counts, g->res_dev, g->flags};
-    for (void *p : dev)
-        if (p) cudaFree(p);
-    if (g->res_host) cudaFreeHost(g->res_host);
-    if (g->flags_host) cudaFreeHost(g->flags_host);
+    // ordered on the legacy default stream, i.e. after the work of blocking streams
+    if (g->arena) cudaFreeAsync(g->arena, 0);
+    if (g->hash) cudaFreeAsync(g->hash, 0);
     delete g;
 }
 
@@ -198,6 +199,12 @@ DevGraph view(const moss_graph *g) {
     d.q = g->q;
     for (int l = 0; l < 3; ++l) d.seed[l] = g->seed[l];
     d.n = g->n;
+    const bool use_hash = g->probe == MOSS_PROBE_HASH && (g->built >> 4 & 1u);
+    d.hash = use_hash ? reinterpret_cast<const uint4 *>(g->hash) : nullptr;
+    uint32_t lg = 0;
+    while ((1ULL << lg) < g->hash_buckets) ++lg;
+    d.hash_mask = use_hash ? (uint32_t)(g->hash_buckets - 1) : 0;
+    d.hash_shift = 64 - lg;
     return d;
 }
 
@@ -212,19 +219,57 @@ void describe_flags(uint32_t f, char *buf, size_t len) {
         }
 }
 
-template <typename T>
-cudaError_t dalloc(T **p, uint64_t count) {
-    return cudaMalloc(reinterpret_cast<void **>(p), (size_t)(count ? count : 1) * sizeof(T));
+// A stream-ordered memory pool per device, owned by the library, that keeps
+// freed memory for reuse (so repeated load/build/free cycles do not return to
+// the driver).
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pool[64];
+bool g_pool_ok[64] = {};
+
+cudaError_t pool_alloc(int device, void **p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mutex);
+        if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+        if (!g_pool_ok[device]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = device;
+            cudaError_t e = cudaMemPoolCreate(&g_pool[device], &props);
+            if (e != cudaSuccess) return e;
+            uint64_t keep = ~0ULL;
+            e = cudaMemPoolSetAttribute(g_pool[device], cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) return e;
+            g_pool_ok[device] = true;
+        }
+        pool = g_pool[device];
+    }
+    return cudaMallocFromPoolAsync(p, bytes ? bytes : 1, pool, s);
 }
 
+// Carves 256-byte aligned arrays out of one allocation (first pass: size).
+struct Carver {
+    uint8_t *base = nullptr;
+    size_t off = 0;
+    template <typename T>
+    T *take(uint64_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = reinterpret_cast<T *>(base + off);
+        off += (size_t)(count ? count : 1) * sizeof(T);
+        return p;
+    }
+};
+
 int read_flags(moss_graph *g, cudaStream_t s) {
-    MOSS_CUDA(cudaMemcpyAsync(g->flags_host, g->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "reading status");
+    MOSS_CUDA(cudaMemcpyAsync(&g->flags_host, g->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "reading status");
     MOSS_CUDA(cudaStreamSynchronize(s), "synchronising stream");
     return MOSS_OK;
 }
 
 bool method_ready(const moss_graph *g, int method) {
-    return (g->built >> 3 & 1u) && (g->built >> method & 1u);
+    const bool probes = g->probe != MOSS_PROBE_HASH || (g->built >> 4 & 1u);
+    return (g->built >> 3 & 1u) && (g->built >> method & 1u) && probes;
 }
 
 }  // namespace
@@ -288,23 +333,31 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
             goto fail_out;                        \
         }                                         \
     } while (0)
-    STEP(dalloc(&g->vert, n), "allocating vertices");
-    STEP(dalloc(&g->col, nnz), "allocating col");
-    STEP(dalloc(&g->slot, nnz), "allocating slots");
-    STEP(dalloc(&g->acc, nnz), "allocating ACC");
-    STEP(dalloc(&g->q, n), "allocating Q");
-    for (int l = 0; l < 3; ++l) {
-        STEP(dalloc(&g->gam[l], n), "allocating weights");
-        STEP(dalloc(&g->seed[l], n), "allocating vertex tables");
+    {
+        Carver c;
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1) {
+                STEP(pool_alloc(device, &g->arena, c.off, s), "allocating graph memory");
+                c.base = static_cast<uint8_t *>(g->arena);
+                c.off = 0;
+            }
+            g->vert = c.take<uint4>(n);
+            g->col = c.take<uint32_t>(nnz);
+            g->slot = c.take<uint4>(nnz);
+            g->acc = c.take<uint32_t>(nnz);
+            g->q = c.take<uint64_t>(n);
+            for (int l = 0; l < 3; ++l) {
+                g->gam[l] = c.take<u128>(n);
+                g->seed[l] = c.take<uint4>(n);
+            }
+            g->tot = c.take<DevTotals>(1);
+            g->partials = c.take<uint64_t>((uint64_t)prow * kSlots + (uint64_t)blocks * 6 * 2);
+            g->counts = c.take<uint64_t>(2 * kSlots);
+            g->res_dev = c.take<moss_result>(1);
+            g->flags = c.take<uint32_t>(1);
+            rp_dev = c.take<uint8_t>(rp_bytes);
+        }
     }
-    STEP(dalloc(&g->tot, 1), "allocating totals");
-    STEP(dalloc(&g->partials, (uint64_t)prow * kSlots + (uint64_t)blocks * 6 * 2), "allocating partials");
-    STEP(dalloc(&g->counts, 2 * kSlots), "allocating counts");
-    STEP(dalloc(&g->res_dev, 1), "allocating result");
-    STEP(dalloc(&g->flags, 1), "allocating status");
-    STEP(cudaMallocHost(reinterpret_cast<void **>(&g->res_host), sizeof(moss_result)), "allocating pinned result");
-    STEP(cudaMallocHost(reinterpret_cast<void **>(&g->flags_host), sizeof(uint32_t)), "allocating pinned status");
-    STEP(cudaMalloc(&rp_dev, rp_bytes), "allocating row_ptr copy");
     STEP(cudaMemcpyAsync(rp_dev, row_ptr, rp_bytes, cudaMemcpyDefault, s), "copying row_ptr");
     if (nnz) STEP(cudaMemcpyAsync(g->col, col, nnz * sizeof(uint32_t), cudaMemcpyDefault, s), "copying col");
     STEP(cudaMemsetAsync(g->flags, 0, sizeof(uint32_t), s), "clearing status");
@@ -319,11 +372,9 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
     STEP(cudaMemcpyAsync(&g->tot_h, g->tot, sizeof(DevTotals), cudaMemcpyDeviceToHost, s), "reading totals");
     rc = read_flags(g, s);
     if (rc) goto fail_out;
-    cudaFree(rp_dev);
-    rp_dev = nullptr;
-    if (*g->flags_host) {
+    if (g->flags_host) {
         char buf[256];
-        describe_flags(*g->flags_host, buf, sizeof(buf));
+        describe_flags(g->flags_host, buf, sizeof(buf));
         rc = fail(MOSS_EGRAPH, "invalid CSR: %s", buf);
         goto fail_out;
     }
@@ -331,7 +382,6 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
     *out = g;
     return MOSS_OK;
 fail_out:
-    if (rp_dev) cudaFree(rp_dev);
     release(g);
     return rc;
 }
@@ -341,35 +391,72 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
     if ((k_mask & ~((1u << 4) | (1u << 5))) || !k_mask) return fail(MOSS_EINVAL, "k_mask must select 4 and/or 5");
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const uint64_t items = g->nnz > g->n ? g->nnz : g->n;
-    uint32_t *idx = nullptr;
-    void *pre = nullptr;
-    const size_t pre_bytes = (size_t)(g->nnz * 8 > (uint64_t)g->n * 16 + 64 ? g->nnz * 8 : (uint64_t)g->n * 16 + 64);
+    // one scratch buffer, used first by the per-list tables then by the vertex tables
+    const uint64_t sigma_bytes = ((g->nnz * 4 + 255) & ~255ULL) + g->nnz * 8;
+    const uint64_t seed_bytes = seed_scratch_bytes(g->n);
+    const uint64_t scratch_bytes = sigma_bytes > seed_bytes ? sigma_bytes : seed_bytes;
+    void *scratch = nullptr;
     int rc = MOSS_OK;
     cudaError_t e;
     g->built = 0;
-    if ((e = cudaMallocAsync(reinterpret_cast<void **>(&idx), items * sizeof(uint32_t), s)) != cudaSuccess)
+    if ((e = pool_alloc(g->device, &scratch, scratch_bytes, s)) != cudaSuccess)
         return cuda_fail(e, "allocating scratch");
-    if ((e = cudaMallocAsync(&pre, pre_bytes, s)) != cudaSuccess) {
-        cudaFreeAsync(idx, s);
-        return cuda_fail(e, "allocating scratch");
-    }
+    uint32_t *idx = static_cast<uint32_t *>(scratch);
+    uint64_t *pre = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(scratch) + ((g->nnz * 4 + 255) & ~255ULL));
     e = cudaMemsetAsync(g->flags, 0, sizeof(uint32_t), s);
-    if (e == cudaSuccess) e = launch_sigma_alias(g->n, g->vert, g->acc, g->slot, idx, static_cast<uint64_t *>(pre), s);
-    for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
+    if (e == cudaSuccess) e = launch_sigma_alias(g->n, g->vert, g->acc, g->slot, idx, pre, s);
+    int which[3], nt = 0;
+    u128 *w[3];
+    uint4 *seed[3];
+    for (int l = 0; l < 3; ++l) {
         const bool want = (l == 0 && (k_mask & (1u << 4))) || (l > 0 && (k_mask & (1u << 5)));
-        if (want)
-            e = launch_seed_alias(g->n, g->gam[l], g->tot, l, g->seed[l], idx, static_cast<u128 *>(pre), g->flags, s);
+        if (want) {
+            which[nt] = l;
+            w[nt] = g->gam[l];
+            seed[nt] = g->seed[l];
+            ++nt;
+        }
     }
-    cudaFreeAsync(idx, s);
-    cudaFreeAsync(pre, s);
+    if (e == cudaSuccess) e = launch_seed_alias(g->n, g->tot, nt, which, w, seed, scratch, g->flags, s);
+    cudaFreeAsync(scratch, s);
+    bool hashed = false;
+    if (e == cudaSuccess && g->probe == MOSS_PROBE_HASH) {
+        // at least 4 slots per undirected edge: buckets = next power of two >= nnz
+        uint64_t buckets = 2;
+        while (buckets < g->nnz) buckets <<= 1;
+        if (buckets > (1ULL << 32)) return fail(MOSS_EOVERFLOW, "edge hash above 2^32 buckets");
+        if (g->hash && g->hash_buckets != buckets) {
+            cudaFreeAsync(g->hash, s);
+            g->hash = nullptr;
+        }
+        if (!g->hash) {
+            e = pool_alloc(g->device, reinterpret_cast<void **>(&g->hash), buckets * 16, s);
+            if (e != cudaSuccess) return cuda_fail(e, "allocating edge hash");
+            g->hash_buckets = buckets;
+        }
+        uint32_t lg = 0;
+        while ((1ULL << lg) < buckets) ++lg;
+        e = cudaMemsetAsync(g->hash, 0xFF, buckets * 16, s);
+        if (e == cudaSuccess)
+            e = launch_edge_hash(g->n, g->vert, g->col, g->hash, (uint32_t)(buckets - 1), 64 - lg, s);
+        hashed = e == cudaSuccess;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "table kernels");
     rc = read_flags(g, s);
     if (rc) return rc;
-    if (*g->flags_host & kErrOverflow) return fail(MOSS_EOVERFLOW, "a vertex weight total times n exceeds 2^128");
+    if (g->flags_host & kErrOverflow) return fail(MOSS_EOVERFLOW, "a vertex weight total times n exceeds 2^128");
     g->built = 1u << 3;
     if (k_mask & (1u << 4)) g->built |= 1u;
     if (k_mask & (1u << 5)) g->built |= 6u;
+    if (hashed) g->built |= 1u << 4;
+    return MOSS_OK;
+}
+
+int moss_set_probe(moss_graph *g, int strategy) {
+    if (!g) return fail(MOSS_EINVAL, "graph is NULL");
+    if (strategy != MOSS_PROBE_SEARCH && strategy != MOSS_PROBE_HASH)
+        return fail(MOSS_EINVAL, "unknown probe strategy %d", strategy);
+    g->probe = strategy;
     return MOSS_OK;
 }
 
@@ -415,9 +502,9 @@ static int finalize_from_device(moss_graph *g, int k, const uint64_t K[2], cudaS
     in.K[0] = K[0];
     in.K[1] = K[1];
     MOSS_CUDA(launch_finalize(in, g->counts, g->tot, g->res_dev, s), "finalize kernel");
-    MOSS_CUDA(cudaMemcpyAsync(g->res_host, g->res_dev, sizeof(moss_result), cudaMemcpyDeviceToHost, s), "reading result");
+    MOSS_CUDA(cudaMemcpyAsync(&g->res_host, g->res_dev, sizeof(moss_result), cudaMemcpyDeviceToHost, s), "reading result");
     MOSS_CUDA(cudaStreamSynchronize(s), "synchronising stream");
-    memcpy(out, g->res_host, sizeof(moss_result));
+    memcpy(out, &g->res_host, sizeof(moss_result));
     return MOSS_OK;
 }
 

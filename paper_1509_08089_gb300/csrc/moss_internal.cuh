@@ -38,8 +38,32 @@ struct DevGraph {
     const uint32_t *acc;
     const uint64_t *q;
     const uint4 *seed[3];
+    const uint4 *hash;      // hashed edge set (2 keys per 16 B bucket), or null: probe by search
+    uint32_t hash_mask;     // buckets - 1
+    uint32_t hash_shift;    // 64 - log2(buckets)
     uint32_t n;
 };
+
+// ------------------------------------------------------- hashed edge set --
+// Key of the undirected edge {a, b}: (min << 32) | max; empty slot: ~0.
+// Buckets hold two keys (16 B); a bucket's second slot is filled only after
+// its first, and keys are never removed, so a lookup walking from the home
+// bucket can stop at the first bucket whose second slot is empty.
+constexpr uint64_t kEmptyKey = ~0ULL;
+
+__host__ __device__ inline uint64_t edge_key(uint32_t a, uint32_t b) {
+    return a < b ? ((uint64_t)a << 32) | b : ((uint64_t)b << 32) | a;
+}
+
+// home bucket: the top bits of a 64-bit finaliser (MurmurHash3 fmix64 steps)
+__host__ __device__ inline uint32_t edge_bucket(uint64_t k, uint32_t shift) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdULL;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ULL;
+    k ^= k >> 33;
+    return (uint32_t)(k >> shift);
+}
 
 // Status flags raised by kernels (bitwise OR into a device word).
 enum : uint32_t {
@@ -95,10 +119,15 @@ cudaError_t launch_slots(uint32_t n, const uint32_t *col, uint4 *vert, uint4 *sl
                          uint64_t *q, u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials,
                          int blocks, uint32_t *flags, cudaStream_t s);
 cudaError_t launch_totals(const u128 *partials, int blocks, DevTotals *tot, cudaStream_t s);
+cudaError_t launch_edge_hash(uint32_t n, const uint4 *vert, const uint32_t *col, unsigned long long *table,
+                             uint32_t mask, uint32_t shift, cudaStream_t s);
 cudaError_t launch_sigma_alias(uint32_t n, const uint4 *vert, const uint32_t *acc, uint4 *slot,
                                uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s);
-cudaError_t launch_seed_alias(uint32_t n, const u128 *w, const DevTotals *tot, int which, uint4 *seed,
-                              uint32_t *scratch_idx, u128 *scratch_pre, uint32_t *flags, cudaStream_t s);
+// vertex alias tables of up to 3 weights in the same launches; scratch of
+// seed_scratch_bytes(n) bytes
+cudaError_t launch_seed_alias(uint32_t n, const DevTotals *tot, int ntables, const int *which, u128 *const *w,
+                              uint4 *const *seed, void *scratch, uint32_t *flags, cudaStream_t s);
+uint64_t seed_scratch_bytes(uint32_t n);
 int table_blocks(uint32_t n);
 
 // moss_sample.cu

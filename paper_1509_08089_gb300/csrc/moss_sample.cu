@@ -112,11 +112,44 @@ __device__ __forceinline__ uint32_t probe_pairs(const uint32_t *col, const uint4
     return found;
 }
 
+// Membership tests through the hashed edge set: one 16-byte bucket load per
+// pair in the common case, all P loads issued together.
+template <int P>
+__device__ __forceinline__ uint32_t probe_hash(const DevGraph &g, const uint32_t (&a)[P], const uint32_t (&b)[P]) {
+    uint64_t key[P];
+    uint32_t bk[P];
+    uint32_t found = 0, pending = (1u << P) - 1u;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        key[p] = edge_key(a[p], b[p]);
+        bk[p] = edge_bucket(key[p], g.hash_shift);
+    }
+    for (uint32_t it = 0; pending != 0 && it <= g.hash_mask; ++it) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (pending >> p & 1u) {
+                const uint4 e = ld4(g.hash + bk[p]);
+                const uint64_t k0 = ((uint64_t)e.y << 32) | e.x, k1 = ((uint64_t)e.w << 32) | e.z;
+                if (k0 == key[p] || k1 == key[p]) {
+                    found |= 1u << p;
+                    pending &= ~(1u << p);
+                } else if (k1 == kEmptyKey) {
+                    pending &= ~(1u << p);
+                } else {
+                    bk[p] = (bk[p] + 1) & g.hash_mask;
+                }
+            }
+        }
+    }
+    return found;
+}
+
 struct Sample {
     uint32_t v[5];
     int cls;
 };
 
+template <bool HASH>
 __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
     const Words4 a = philox4x64(s, 0, 0, 0, seed, 0);
@@ -134,17 +167,23 @@ __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t 
         out.cls = 0;
         return out;
     }
-    const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r);
     // unknown pairs: v-r, u-w, w-r
-    const uint4 ra[3] = {vr, ur, wr}, rb[3] = {rr, wr, rr};
     const uint32_t A[3] = {v, pu.id, w}, B[3] = {r, w, r};
-    const uint32_t f = probe_pairs<3>(g.col, ra, rb, A, B);
+    uint32_t f;
+    if (HASH) {
+        f = probe_hash<3>(g, A, B);
+    } else {
+        const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r);
+        const uint4 ra[3] = {vr, ur, wr}, rb[3] = {rr, wr, rr};
+        f = probe_pairs<3>(g.col, ra, rb, A, B);
+    }
     // pair bits (0,1)(0,2)(0,3)(1,2)(1,3)(2,3); known: v-u, v-w, u-r
     const uint32_t mask = 0x1u | 0x2u | ((f & 1u) << 2) | (((f >> 1) & 1u) << 3) | 0x10u | (((f >> 2) & 1u) << 5);
     out.cls = lut[mask];
     return out;
 }
 
+template <bool HASH>
 __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
     const Words4 a = philox4x64(s, 0, 1, 0, seed, 0);
@@ -164,11 +203,16 @@ __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lu
         out.cls = 0;
         return out;
     }
-    const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r), tr = ld4(g.vert + t);
     // unknown pairs: u-w, u-r, w-r, v-t, w-t, r-t
-    const uint4 ra[6] = {ur, ur, wr, vr, wr, rr}, rb[6] = {wr, rr, rr, tr, tr, tr};
     const uint32_t A[6] = {pu.id, pu.id, w, v, w, r}, B[6] = {w, r, r, t, t, t};
-    const uint32_t f = probe_pairs<6>(g.col, ra, rb, A, B);
+    uint32_t f;
+    if (HASH) {
+        f = probe_hash<6>(g, A, B);
+    } else {
+        const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r), tr = ld4(g.vert + t);
+        const uint4 ra[6] = {ur, ur, wr, vr, wr, rr}, rb[6] = {wr, rr, rr, tr, tr, tr};
+        f = probe_pairs<6>(g.col, ra, rb, A, B);
+    }
     // pair bits (0,1)(0,2)(0,3)(0,4)(1,2)(1,3)(1,4)(2,3)(2,4)(3,4)
     // known: v-u (0), v-w (1), v-r (2), u-t (6)
     uint32_t mask = 0x1u | 0x2u | 0x4u | 0x40u;
@@ -212,6 +256,7 @@ __device__ __noinline__ void path5_fallback(const DevGraph &g, uint32_t v, uint4
     iw = lo - 1;
 }
 
+template <bool HASH>
 __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
     const Words4 a = philox4x64(s, 0, 2, 0, seed, 0);
@@ -242,11 +287,16 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
         out.cls = 0;
         return out;
     }
-    const uint4 rr = ld4(g.vert + r), tr = ld4(g.vert + t);
     // unknown pairs: v-r, v-t, u-w, u-t, w-r, r-t
-    const uint4 ra[6] = {vr, vr, ur, ur, wr, rr}, rb[6] = {rr, tr, wr, tr, rr, tr};
     const uint32_t A[6] = {v, v, u, u, w, r}, B[6] = {r, t, w, t, r, t};
-    const uint32_t f = probe_pairs<6>(g.col, ra, rb, A, B);
+    uint32_t f;
+    if (HASH) {
+        f = probe_hash<6>(g, A, B);
+    } else {
+        const uint4 rr = ld4(g.vert + r), tr = ld4(g.vert + t);
+        const uint4 ra[6] = {vr, vr, ur, ur, wr, rr}, rb[6] = {rr, tr, wr, tr, rr, tr};
+        f = probe_pairs<6>(g.col, ra, rb, A, B);
+    }
     // known: v-u (0), v-w (1), u-r (5), w-t (8)
     uint32_t mask = 0x1u | 0x2u | 0x20u | 0x100u;
     mask |= ((f >> 0) & 1u) << 2;   // v-r
@@ -259,7 +309,7 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
     return out;
 }
 
-template <int METHOD, bool RECORD>
+template <int METHOD, bool RECORD, bool HASH>
 __global__ void __launch_bounds__(kThreads) k_sample(DevGraph g, uint64_t first, uint64_t count, uint64_t seed,
                                                      uint64_t *partials, uint8_t *classes, uint32_t *verts) {
     __shared__ uint8_t lut[kLut];
@@ -279,9 +329,9 @@ __global__ void __launch_bounds__(kThreads) k_sample(DevGraph g, uint64_t first,
         if (i < count) {
             const uint64_t s = first + i;
             Sample sm;
-            if (METHOD == 0) sm = sample_moss4(g, lut, seed, s);
-            else if (METHOD == 1) sm = sample_t5(g, lut, seed, s);
-            else sm = sample_path5(g, lut, seed, s);
+            if (METHOD == 0) sm = sample_moss4<HASH>(g, lut, seed, s);
+            else if (METHOD == 1) sm = sample_t5<HASH>(g, lut, seed, s);
+            else sm = sample_path5<HASH>(g, lut, seed, s);
             cls = sm.cls;
             if (RECORD) {
                 classes[i] = (uint8_t)cls;
@@ -313,7 +363,10 @@ __global__ void k_reduce(const uint64_t *partials, int blocks, uint64_t *out) {
 template <int M, bool R>
 cudaError_t launch_one(const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
                        int blocks, uint8_t *classes, uint32_t *verts, cudaStream_t s) {
-    k_sample<M, R><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    if (g.hash)
+        k_sample<M, R, true><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    else
+        k_sample<M, R, false><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
     return cudaGetLastError();
 }
 
@@ -328,10 +381,19 @@ int sample_blocks(int method, int device) {
     int sms = 148, per = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     cudaError_t e = cudaSuccess;
-    if (method == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<0, false>, kThreads, 0);
-    else if (method == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<1, false>, kThreads, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<2, false>, kThreads, 0);
+    int per_h = 1;
+    if (method == 0) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<0, false, false>, kThreads, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_sample<0, false, true>, kThreads, 0);
+    } else if (method == 1) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<1, false, false>, kThreads, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_sample<1, false, true>, kThreads, 0);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<2, false, false>, kThreads, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_sample<2, false, true>, kThreads, 0);
+    }
     if (e != cudaSuccess || per < 1) per = 1;
+    if (per_h > per) per = per_h;   // grid sized for the faster (hash) variant
     return sms * per;
 }
 

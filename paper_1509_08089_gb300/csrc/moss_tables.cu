@@ -194,6 +194,35 @@ __global__ void k_totals(const u128 *partials, int blocks, DevTotals *tot) {
     }
 }
 
+// ----------------------------------------------------- hashed edge set ---
+// One warp per vertex inserts the edges {v, x} with x > v by compare-and-swap
+// into the first free slot from the home bucket on.  The table has at least
+// four slots per edge, so a free slot always exists and the walk is bounded
+// by the bucket count.
+__global__ void __launch_bounds__(kTableThreads) k_edge_hash(uint32_t n, const uint4 *__restrict__ vert,
+                                                            const uint32_t *__restrict__ col,
+                                                            unsigned long long *table, uint32_t mask,
+                                                            uint32_t shift) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    for (uint64_t v = (uint64_t)blockIdx.x * wpb + warp; v < n; v += (uint64_t)gridDim.x * wpb) {
+        const uint4 vr = vert[v];
+        for (uint32_t i = lane; i < vr.y; i += kWarp) {
+            const uint32_t x = col[vr.x + i];
+            if (x <= (uint32_t)v) continue;
+            const unsigned long long key = edge_key((uint32_t)v, x);
+            uint32_t b = edge_bucket(key, shift);
+            for (uint64_t it = 0; it <= mask; ++it) {
+                unsigned long long old = atomicCAS(table + 2ull * b, (unsigned long long)kEmptyKey, key);
+                if (old == kEmptyKey || old == key) break;
+                old = atomicCAS(table + 2ull * b + 1, (unsigned long long)kEmptyKey, key);
+                if (old == kEmptyKey || old == key) break;
+                b = (b + 1) & mask;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------ per-list sigma tables ---
 // weight of position p of N_v from the ACC prefix
 __device__ __forceinline__ uint32_t acc_weight(const uint32_t *acc, uint32_t o, uint32_t d, uint32_t S, uint32_t p) {
@@ -293,94 +322,195 @@ __global__ void __launch_bounds__(kTableThreads) k_sigma_alias(uint32_t n, const
 }
 
 // ---------------------------------------------------- vertex (seed) tables ---
-constexpr int kSeedThreads = 1024;
+constexpr int kSeedThreads = 256;
+constexpr int kSeedRounds = 16;                              // items per thread per block
+constexpr uint32_t kSeedChunk = kSeedThreads * kSeedRounds;  // items per block
 
 struct SeedSplit {
     uint32_t nl, nh;
     u128 total;  // sum of deficits == sum of excesses
 };
 
-// pass 1: one block scans all n items in index order
-__global__ void __launch_bounds__(kSeedThreads) k_seed_split(uint32_t n, const u128 *__restrict__ w,
-                                                            const DevTotals *tot, int which, uint32_t *idx,
-                                                            u128 *pre, SeedSplit *split, uint32_t *flags) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const u128 W = tot->gamma[which];
-    __shared__ uint32_t s_lc[kSeedThreads / kWarp], s_hc[kSeedThreads / kWarp];
+// per-block aggregate of one contiguous chunk: lights, heavies, sum D, sum E
+struct alignas(16) SeedAgg {
+    u128 D, E;
+    uint32_t nl, nh, pad0, pad1;
+};
+
+// One vertex table being built: weights, output, and its scratch.
+struct SeedTask {
+    const u128 *w;
+    uint4 *seed;
+    uint32_t *idx;     // n: lights from the front, heavies from the back
+    u128 *pre;         // n: A_i (lights) / P_k (heavies)
+    SeedSplit *split;
+    SeedAgg *agg;      // one per chunk
+    int which;         // 0 Gamma, 1 Gamma^(1), 2 Gamma^(2)
+};
+struct SeedTasks {
+    SeedTask t[3];
+};
+
+__device__ __forceinline__ void seed_item(const SeedTask &T, uint64_t j, uint32_t n, u128 W, bool &light,
+                                          bool &heavy, u128 &D, u128 &E) {
+    light = heavy = false;
+    D = E = 0;
+    if (j < n) {
+        const u128 q = T.w[j] * (u128)n;
+        light = q < W;
+        heavy = !light;
+        if (light) D = W - q; else E = q - W;
+    }
+}
+
+// exclusive block scan of (lights, heavies, D, E); returns the block totals
+__device__ __forceinline__ void block_scan4(bool light, bool heavy, u128 D, u128 E, uint32_t &xl, uint32_t &xh,
+                                            u128 &xD, u128 &xE, SeedAgg &tot) {
+    __shared__ uint32_t s_l[kSeedThreads / kWarp], s_h[kSeedThreads / kWarp];
     __shared__ u128 s_D[kSeedThreads / kWarp], s_E[kSeedThreads / kWarp];
-    __shared__ uint32_t s_nl, s_nh;
-    __shared__ u128 s_A, s_P;
-    if (threadIdx.x == 0) {
-        s_nl = s_nh = 0;
-        s_A = s_P = 0;
-        // q = w n must stay below 2^128 for every item: W n < 2^128 suffices
-        if (n > 1 && W > (~(u128)0) / n) atomicOr(flags, kErrOverflow);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t lm = __ballot_sync(0xffffffffu, light), hm = __ballot_sync(0xffffffffu, heavy);
+    const u128 Di = warp_incl_scan128(D, lane), Ei = warp_incl_scan128(E, lane);
+    if (lane == 31) {
+        s_l[warp] = __popc(lm);
+        s_h[warp] = __popc(hm);
+        s_D[warp] = Di;
+        s_E[warp] = Ei;
     }
     __syncthreads();
-    if (W == 0) {
-        if (threadIdx.x == 0) { split->nl = 0; split->nh = 0; split->total = 0; }
+    uint32_t wl = 0, wh = 0;
+    u128 wD = 0, wE = 0;
+    for (int k = 0; k < warp; ++k) {
+        wl += s_l[k];
+        wh += s_h[k];
+        wD += s_D[k];
+        wE += s_E[k];
+    }
+    tot.nl = tot.nh = 0;
+    tot.D = tot.E = 0;
+    for (int k = 0; k < kSeedThreads / kWarp; ++k) {
+        tot.nl += s_l[k];
+        tot.nh += s_h[k];
+        tot.D += s_D[k];
+        tot.E += s_E[k];
+    }
+    xl = wl + __popc(lm & below);
+    xh = wh + __popc(hm & below);
+    xD = wD + Di - D;
+    xE = wE + Ei - E;
+    __syncthreads();
+}
+
+// phase 1: per-chunk aggregates
+__global__ void __launch_bounds__(kSeedThreads) k_seed_count(uint32_t n, const DevTotals *tot, SeedTasks tasks,
+                                                            uint32_t *flags) {
+    const SeedTask &T = tasks.t[blockIdx.y];
+    const u128 W = tot->gamma[T.which];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && n > 1 && W > (~(u128)0) / n) atomicOr(flags, kErrOverflow);
+    if (W == 0) return;
+    const uint64_t base = (uint64_t)blockIdx.x * kSeedChunk;
+    SeedAgg acc;
+    acc.nl = acc.nh = 0;
+    acc.D = acc.E = 0;
+    for (int r = 0; r < kSeedRounds; ++r) {
+        bool light, heavy;
+        u128 D, E;
+        seed_item(T, base + (uint64_t)r * kSeedThreads + threadIdx.x, n, W, light, heavy, D, E);
+        uint32_t xl, xh;
+        u128 xD, xE;
+        SeedAgg t;
+        block_scan4(light, heavy, D, E, xl, xh, xD, xE, t);
+        acc.nl += t.nl;
+        acc.nh += t.nh;
+        acc.D += t.D;
+        acc.E += t.E;
+    }
+    if (threadIdx.x == 0) T.agg[blockIdx.x] = acc;
+}
+
+// phase 2: exclusive scan of the chunk aggregates (one block per table)
+__global__ void __launch_bounds__(kSeedThreads) k_seed_offsets(uint32_t chunks, const DevTotals *tot,
+                                                              SeedTasks tasks) {
+    const SeedTask &T = tasks.t[blockIdx.x];
+    if (tot->gamma[T.which] == 0) {
+        if (threadIdx.x == 0) { T.split->nl = 0; T.split->nh = 0; T.split->total = 0; }
         return;
     }
-    const uint32_t below = (1u << lane) - 1u;
-    for (uint64_t base = 0; base < n; base += kSeedThreads) {
-        const uint64_t j = base + threadIdx.x;
-        const bool valid = j < n;
-        u128 qj = valid ? w[j] * (u128)n : 0;
-        const bool light = valid && qj < W;
-        const bool heavy = valid && !light;
-        const uint32_t lmask = __ballot_sync(0xffffffffu, light);
-        const uint32_t hmask = __ballot_sync(0xffffffffu, heavy);
-        const u128 D = light ? W - qj : 0;
-        const u128 E = heavy ? qj - W : 0;
-        const u128 Dincl = warp_incl_scan128(D, lane);
-        const u128 Eincl = warp_incl_scan128(E, lane);
-        if (lane == 31) {
-            s_lc[warp] = __popc(lmask);
-            s_hc[warp] = __popc(hmask);
-            s_D[warp] = Dincl;
-            s_E[warp] = Eincl;
-        }
+    __shared__ SeedAgg run;
+    if (threadIdx.x == 0) { run.nl = run.nh = 0; run.D = run.E = 0; }
+    __syncthreads();
+    for (uint32_t b0 = 0; b0 < chunks; b0 += kSeedThreads) {
+        const uint32_t b = b0 + threadIdx.x;
+        SeedAgg a;
+        a.nl = a.nh = 0;
+        a.D = a.E = 0;
+        if (b < chunks) a = T.agg[b];
+        // inclusive scan of the four fields through shared memory (Hillis-Steele)
+        __shared__ uint32_t sl[kSeedThreads], sh[kSeedThreads];
+        __shared__ u128 sD[kSeedThreads], sE[kSeedThreads];
+        sl[threadIdx.x] = a.nl; sh[threadIdx.x] = a.nh; sD[threadIdx.x] = a.D; sE[threadIdx.x] = a.E;
         __syncthreads();
-        if (warp == 0) {  // scan the per-warp totals
-            uint32_t lc = s_lc[lane], hc = s_hc[lane];
-            u128 dd = s_D[lane], ee = s_E[lane];
-            uint32_t lci = lc, hci = hc;
-#pragma unroll
-            for (int d = 1; d < kWarp; d <<= 1) {
-                uint32_t a = __shfl_up_sync(0xffffffffu, lci, d), b = __shfl_up_sync(0xffffffffu, hci, d);
-                if (lane >= d) { lci += a; hci += b; }
+        for (int d = 1; d < kSeedThreads; d <<= 1) {
+            uint32_t l2 = 0, h2 = 0;
+            u128 D2 = 0, E2 = 0;
+            if ((int)threadIdx.x >= d) {
+                l2 = sl[threadIdx.x - d]; h2 = sh[threadIdx.x - d]; D2 = sD[threadIdx.x - d]; E2 = sE[threadIdx.x - d];
             }
-            u128 di = warp_incl_scan128(dd, lane), ei = warp_incl_scan128(ee, lane);
-            s_lc[lane] = lci - lc;   // exclusive
-            s_hc[lane] = hci - hc;
-            s_D[lane] = di - dd;
-            s_E[lane] = ei - ee;
+            __syncthreads();
+            sl[threadIdx.x] += l2; sh[threadIdx.x] += h2; sD[threadIdx.x] += D2; sE[threadIdx.x] += E2;
+            __syncthreads();
         }
-        __syncthreads();
-        const uint32_t nl0 = s_nl, nh0 = s_nh;
-        const u128 A0 = s_A, P0 = s_P;
-        if (light) {
-            const uint32_t r = nl0 + s_lc[warp] + __popc(lmask & below);
-            idx[r] = (uint32_t)j;
-            pre[r] = A0 + s_D[warp] + Dincl - D;                 // exclusive A_i
-        } else if (heavy) {
-            const uint32_t r = nh0 + s_hc[warp] + __popc(hmask & below);
-            idx[n - 1 - r] = (uint32_t)j;
-            pre[n - 1 - r] = P0 + s_E[warp] + Eincl;             // inclusive P_k
+        if (b < chunks) {
+            SeedAgg ex;
+            ex.nl = run.nl + sl[threadIdx.x] - a.nl;
+            ex.nh = run.nh + sh[threadIdx.x] - a.nh;
+            ex.D = run.D + sD[threadIdx.x] - a.D;
+            ex.E = run.E + sE[threadIdx.x] - a.E;
+            T.agg[b] = ex;   // now the chunk's exclusive offsets
         }
         __syncthreads();
         if (threadIdx.x == kSeedThreads - 1) {
-            s_nl = nl0 + s_lc[warp] + __popc(lmask);
-            s_nh = nh0 + s_hc[warp] + __popc(hmask);
-            s_A = A0 + s_D[warp] + Dincl;
-            s_P = P0 + s_E[warp] + Eincl;
+            run.nl += sl[threadIdx.x]; run.nh += sh[threadIdx.x]; run.D += sD[threadIdx.x]; run.E += sE[threadIdx.x];
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        split->nl = s_nl;
-        split->nh = s_nh;
-        split->total = s_P;
+        T.split->nl = run.nl;
+        T.split->nh = run.nh;
+        T.split->total = run.E;
+    }
+}
+
+// phase 3: place every item at its split position with its prefix
+__global__ void __launch_bounds__(kSeedThreads) k_seed_place(uint32_t n, const DevTotals *tot, SeedTasks tasks) {
+    const SeedTask &T = tasks.t[blockIdx.y];
+    const u128 W = tot->gamma[T.which];
+    if (W == 0) return;
+    const uint64_t base = (uint64_t)blockIdx.x * kSeedChunk;
+    SeedAgg off = T.agg[blockIdx.x];
+    for (int r = 0; r < kSeedRounds; ++r) {
+        const uint64_t j = base + (uint64_t)r * kSeedThreads + threadIdx.x;
+        bool light, heavy;
+        u128 D, E;
+        seed_item(T, j, n, W, light, heavy, D, E);
+        uint32_t xl, xh;
+        u128 xD, xE;
+        SeedAgg t;
+        block_scan4(light, heavy, D, E, xl, xh, xD, xE, t);
+        if (light) {
+            const uint32_t rnk = off.nl + xl;
+            T.idx[rnk] = (uint32_t)j;
+            T.pre[rnk] = off.D + xD;                       // exclusive A_i
+        } else if (heavy) {
+            const uint32_t rnk = off.nh + xh;
+            T.idx[n - 1 - rnk] = (uint32_t)j;
+            T.pre[n - 1 - rnk] = off.E + xE + E;           // inclusive P_k
+        }
+        off.nl += t.nl;
+        off.nh += t.nh;
+        off.D += t.D;
+        off.E += t.E;
     }
 }
 
@@ -399,16 +529,17 @@ __device__ __forceinline__ uint64_t quantize64(u128 thr, u128 W) {
     return qq;
 }
 
-// pass 2: one thread per position of the split order
-__global__ void k_seed_fill(uint32_t n, const u128 *__restrict__ w, const DevTotals *tot, int which,
-                            const uint32_t *__restrict__ idx, const u128 *__restrict__ pre, const SeedSplit *split,
-                            uint4 *seed) {
-    const u128 W = tot->gamma[which];
-    const uint32_t nl = split->nl, nh = split->nh;
-    const u128 Ptot = split->total;
+// phase 4: thresholds and aliases, one thread per position of the split order
+__global__ void k_seed_fill(uint32_t n, const DevTotals *tot, SeedTasks tasks) {
+    const SeedTask &T = tasks.t[blockIdx.y];
+    const u128 W = tot->gamma[T.which];
+    const uint32_t *idx = T.idx;
+    const u128 *pre = T.pre;
+    const uint32_t nl = T.split->nl, nh = T.split->nh;
+    const u128 Ptot = T.split->total;
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
         if (W == 0) {
-            seed[p] = make_uint4(0u, 0u, (uint32_t)p, 0u);
+            T.seed[p] = make_uint4(0u, 0u, (uint32_t)p, 0u);
             continue;
         }
         const uint32_t j = idx[p];
@@ -421,7 +552,7 @@ __global__ void k_seed_fill(uint32_t n, const u128 *__restrict__ w, const DevTot
                 uint32_t half = len >> 1;
                 if (pre[n - 1 - (lo + half)] < A) { lo += half + 1; len -= half + 1; } else { len = half; }
             }
-            thr = w[j] * (u128)n;
+            thr = T.w[j] * (u128)n;
             alias = idx[n - 1 - lo];
         } else {
             const uint32_t k = (uint32_t)(n - 1 - p);
@@ -440,8 +571,8 @@ __global__ void k_seed_fill(uint32_t n, const u128 *__restrict__ w, const DevTot
                 alias = j;
             }
         }
-        const uint64_t T = quantize64(thr, W);
-        seed[j] = make_uint4((uint32_t)T, (uint32_t)(T >> 32), alias, 0u);
+        const uint64_t Tq = quantize64(thr, W);
+        T.seed[j] = make_uint4((uint32_t)Tq, (uint32_t)(Tq >> 32), alias, 0u);
     }
 }
 
@@ -487,24 +618,58 @@ cudaError_t launch_totals(const u128 *partials, int blocks, DevTotals *tot, cuda
     return cudaGetLastError();
 }
 
+cudaError_t launch_edge_hash(uint32_t n, const uint4 *vert, const uint32_t *col, unsigned long long *table,
+                             uint32_t mask, uint32_t shift, cudaStream_t s) {
+    k_edge_hash<<<table_blocks(n), kTableThreads, 0, s>>>(n, vert, col, table, mask, shift);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sigma_alias(uint32_t n, const uint4 *vert, const uint32_t *acc, uint4 *slot,
                                uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s) {
     k_sigma_alias<<<table_blocks(n), kTableThreads, 0, s>>>(n, vert, acc, slot, scratch_idx, scratch_pre);
     return cudaGetLastError();
 }
 
-cudaError_t launch_seed_alias(uint32_t n, const u128 *w, const DevTotals *tot, int which, uint4 *seed,
-                              uint32_t *scratch_idx, u128 *scratch_pre, uint32_t *flags, cudaStream_t s) {
-    // the split record lives after the n prefix entries of the scratch
-    SeedSplit *split = reinterpret_cast<SeedSplit *>(scratch_pre + n);
-    k_seed_split<<<1, kSeedThreads, 0, s>>>(n, w, tot, which, scratch_idx, scratch_pre, split, flags);
+uint64_t seed_scratch_bytes(uint32_t n) {
+    const uint64_t chunks = ((uint64_t)n + kSeedChunk - 1) / kSeedChunk;
+    const uint64_t per = (uint64_t)n * 4 + 256 + (uint64_t)n * 16 + 256 + sizeof(SeedSplit) + 256 +
+                         chunks * sizeof(SeedAgg) + 256;
+    return 3 * per;
+}
+
+cudaError_t launch_seed_alias(uint32_t n, const DevTotals *tot, int ntables, const int *which, u128 *const *w,
+                              uint4 *const *seed, void *scratch, uint32_t *flags, cudaStream_t s) {
+    if (ntables < 1 || ntables > 3) return cudaErrorInvalidValue;
+    const uint32_t chunks = (uint32_t)(((uint64_t)n + kSeedChunk - 1) / kSeedChunk);
+    SeedTasks tasks = {};
+    uint8_t *p = static_cast<uint8_t *>(scratch);
+    auto take = [&](uint64_t bytes) {
+        uint8_t *r = p;
+        p += (bytes + 255) & ~(uint64_t)255;
+        return r;
+    };
+    for (int t = 0; t < ntables; ++t) {
+        SeedTask &T = tasks.t[t];
+        T.w = w[t];
+        T.seed = seed[t];
+        T.which = which[t];
+        T.idx = reinterpret_cast<uint32_t *>(take((uint64_t)n * 4));
+        T.pre = reinterpret_cast<u128 *>(take((uint64_t)n * 16));
+        T.split = reinterpret_cast<SeedSplit *>(take(sizeof(SeedSplit)));
+        T.agg = reinterpret_cast<SeedAgg *>(take((uint64_t)chunks * sizeof(SeedAgg)));
+    }
+    k_seed_count<<<dim3(chunks, ntables), kSeedThreads, 0, s>>>(n, tot, tasks, flags);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    k_seed_offsets<<<ntables, kSeedThreads, 0, s>>>(chunks, tot, tasks);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_seed_place<<<dim3(chunks, ntables), kSeedThreads, 0, s>>>(n, tot, tasks);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int threads = 256;
     uint64_t blocks = ((uint64_t)n + threads - 1) / threads;
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    k_seed_fill<<<(unsigned)blocks, threads, 0, s>>>(n, w, tot, which, scratch_idx, scratch_pre, split, seed);
+    k_seed_fill<<<dim3((unsigned)blocks, ntables), threads, 0, s>>>(n, tot, tasks);
     return cudaGetLastError();
 }
 

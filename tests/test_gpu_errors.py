@@ -63,6 +63,14 @@ def test_state_and_argument_errors():
         assert ei.value.status == moss.MOSS_EINVAL
         r = g.estimate(4, 100, 1)          # still usable; Gamma = 0 gives n_2 = Lambda_3
         assert r["est"][2] == 10.0 and r["K"] == (0, 0)
+    with moss.Graph(rp, col, probe=moss.PROBE_SEARCH) as g:
+        moss.moss_set_probe(g.handle, moss.PROBE_HASH)       # hash not built yet
+        with pytest.raises(moss.MossError) as ei:
+            moss.moss_sample_estimate(g.handle, 5, 100, 1)
+        assert ei.value.status == moss.MOSS_ESTATE
+        with pytest.raises(moss.MossError) as ei:
+            moss.moss_set_probe(g.handle, 7)
+        assert ei.value.status == moss.MOSS_EINVAL
     with pytest.raises(moss.MossError) as ei:
         moss.moss_graph_load_csr(rp, col, device=99)
     assert ei.value.status == moss.MOSS_EINVAL

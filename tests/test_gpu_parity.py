@@ -112,19 +112,23 @@ def test_records_bit_exact(name, method):
         pytest.skip("method has no sample on this graph")
     first, count = (12_345, 100_003) if name != "cl_n100k" else (49_990_000, 20_011)
     seed = 0xC0FFEE + method
-    cls, verts = gpu_records(g, method, first, count, seed)
     ocnt, ocls, overts = og.run(method, seed, count, first=first, record=True)
-    bad = np.nonzero(ocls != cls)[0]
-    assert bad.size == 0, (bad[:5], ocls[bad[:5]], cls[bad[:5]], overts[bad[:3]], verts[bad[:3]])
     ncol = 4 if method == 0 else 5
-    assert np.array_equal(verts[:, :ncol], overts[:, :ncol])
+    for probe in (moss.PROBE_SEARCH, moss.PROBE_HASH):
+        moss.moss_set_probe(g.handle, probe)
+        cls, verts = gpu_records(g, method, first, count, seed)
+        bad = np.nonzero(ocls != cls)[0]
+        assert bad.size == 0, (probe, bad[:5], ocls[bad[:5]], cls[bad[:5]], overts[bad[:3]], verts[bad[:3]])
+        assert np.array_equal(verts[:, :ncol], overts[:, :ncol])
+    moss.moss_set_probe(g.handle, moss.PROBE_HASH)
 
 
 @pytest.mark.parametrize("name", ["gnp12", "cl_n200", "rgg2k", "cl_n2k"])
 def test_counts_and_estimates(name):
     rp, col, og, g = pair(name)
     budget, seed = 200_001, 99
-    for k in (4, 5):
+    for k, probe in ((4, moss.PROBE_SEARCH), (4, moss.PROBE_HASH), (5, moss.PROBE_SEARCH), (5, moss.PROBE_HASH)):
+        moss.moss_set_probe(g.handle, probe)
         r = g.estimate(k, budget, seed)
         o = og.estimate(k, budget, seed)
         if k == 4:
@@ -138,6 +142,7 @@ def test_counts_and_estimates(name):
             assert np.array_equal(r["hits"][1], ref2)
         assert tuple(r["K"]) == tuple(o["K"])
         close_estimates(r, o, og, k)
+    moss.moss_set_probe(g.handle, moss.PROBE_HASH)
 
 
 def close_estimates(r, o, og, k):
