@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--seed", type=int, default=42)
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--probe", default="hash", choices=["hash", "search"],
+                   help="induced-edge tests: hashed edge set (default) or sorted-list search")
     return p.parse_args()
 
 
@@ -225,9 +227,12 @@ def run_gpu(args):
         tdist.all_reduce(t)
         return t.cpu().numpy()
 
+    probe = moss.PROBE_HASH if args.probe == "hash" else moss.PROBE_SEARCH
+
     def step(src_rp, src_col, seed):
         h = moss.moss_graph_load_csr(src_rp, src_col, device=dev, stream=stream)
         try:
+            moss.moss_set_probe(h, probe)
             moss.moss_build_tables(h, kmask, stream)
             if world == 1:
                 r = moss.result_dict(moss.moss_sample_estimate(h, k, args.budget, seed, stream))
@@ -297,6 +302,7 @@ def run_gpu(args):
     roof = None
     h = moss.moss_graph_load_csr(rp_d, col_d, device=dev, stream=stream)
     try:
+        moss.moss_set_probe(h, probe)
         moss.moss_build_tables(h, kmask, stream)
         counts = torch.zeros(22, dtype=torch.int64, device=f"cuda:{dev}")
         times = {}
@@ -326,11 +332,13 @@ def run_gpu(args):
         peaks = json.load(open(ppath))
     peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    probe_name = "hash" if args.probe == "hash" else "search"
     if sect is not None:
         K, tms = times[dom]
-        spb = sect[name[dom]]["sectors_per_sample"]
+        spb = sect[f"{name[dom]}_{probe_name}"]["sectors_per_sample"]
         ach = spb * 32.0 * K / (tms / 1000.0) / 1e9
-        roof = {"bound": "hbm", "kernel": f"k_sample<{dom}> ({name[dom]})", "achieved": ach, "peak": peak,
+        roof = {"bound": "hbm", "kernel": f"k_sample<{dom}> ({name[dom]}, {probe_name} probes)", "achieved": ach,
+                "peak": peak,
                 "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak, "traffic": None,
                 "algorithmic_bytes_per_sample": spb * 32.0, "samples_per_launch": K,
                 "launch_ms": tms, "kernel_times_ms": {name[m]: times[m][1] for m in times}}
@@ -339,7 +347,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "budget_per_gpu": args.budget, "seed": args.seed,
+        "config": {"workload": WORKLOAD, "budget_per_gpu": args.budget, "seed": args.seed, "probe": args.probe,
                    "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}"},
         "e2e": {"value": samples_per_step / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

@@ -3,8 +3,11 @@
 For each sampled CIS, the set of distinct 32 B sectors the sampling step must
 read under the device layout the library documents (include/moss.h and its
 kernels): vertex alias records and vertex records of 16 B, per-slot sigma
-records of 16 B, neighbour ids of 4 B, ACC entries of 4 B, Q_v of 8 B; each
-probe is a lower-bound search with early exit in the shorter sorted list.
+records of 16 B, neighbour ids of 4 B, ACC entries of 4 B, Q_v of 8 B.  Each
+probe is either a lower-bound search with early exit in the shorter sorted
+list (MOSS_PROBE_SEARCH, which also reads the two vertex records) or the home
+bucket of the hashed edge set (MOSS_PROBE_HASH, 16 B buckets; the rare
+continuation into the next bucket is not counted).
 The draws are replayed from the oracle's Philox words and tables, so the
 count is exact per sample; the mean over a few thousand samples is the
 per-sample figure used by the roofline ("achieved" = figure x 32 B x samples
@@ -36,8 +39,23 @@ def idx(x: int, m: int) -> int:
     return (x * m) >> 64
 
 
+M64 = (1 << 64) - 1
+
+
+def edge_bucket(a: int, b: int, shift: int) -> int:
+    """Home bucket of edge {a, b} in the library's hashed edge set (key
+    (min << 32) | max through three xor-shift-multiply steps, top bits)."""
+    k = (min(a, b) << 32) | max(a, b)
+    k ^= k >> 33
+    k = (k * 0xff51afd7ed558ccd) & M64
+    k ^= k >> 33
+    k = (k * 0xc4ceb9fe1a85ec53) & M64
+    k ^= k >> 33
+    return k >> shift
+
+
 class Replay:
-    def __init__(self, rp, col):
+    def __init__(self, rp, col, probe="search"):
         self.g = oracle.OracleGraph(rp, col)
         self.rp = rp.astype(np.int64)
         self.col = col
@@ -46,6 +64,11 @@ class Replay:
         self.seed = [self.g.seed_table(l)[1:] for l in range(3)]
         thr, alias, acc = self.g.sigma_table()
         self.thr, self.alias, self.acc = thr.astype(np.int64), alias.astype(np.int64), acc.astype(np.int64)
+        self.probe_kind = probe
+        buckets = 2
+        while buckets < len(col):
+            buckets <<= 1
+        self.shift = 64 - (buckets.bit_length() - 1)
 
     def words(self, method, seed, s, blocks):
         out = []
@@ -54,6 +77,9 @@ class Replay:
         return out
 
     def probe(self, a, b, touched):
+        if self.probe_kind == "hash":   # home bucket of 16 B: two per sector
+            touched.add(("hash", edge_bucket(int(a), int(b), self.shift) >> 1))
+            return
         da, db = self.deg[a], self.deg[b]
         if da <= db:
             lo, ln, key = self.rp[a], da, b
@@ -114,8 +140,9 @@ class Replay:
             t.add(("col", (int(self.rp[u]) + ju) >> 3))
             t.add(("col", (int(self.rp[w]) + jt) >> 3))
             if cls:
-                t.add(("vert", r >> 1))
-                t.add(("vert", tt >> 1))
+                if self.probe_kind == "search":
+                    t.add(("vert", r >> 1))
+                    t.add(("vert", tt >> 1))
                 for a, b in ((v, r), (v, tt), (u, w), (u, tt), (w, r), (r, tt)):
                     self.probe(a, b, t)
             return len(t)
@@ -128,8 +155,9 @@ class Replay:
             ju = int(np.searchsorted(self.col[self.rp[u]:self.rp[u + 1]], r))
             t.add(("col", (int(self.rp[u]) + ju) >> 3))
             if cls:
-                t.add(("vert", w >> 1))
-                t.add(("vert", r >> 1))
+                if self.probe_kind == "search":
+                    t.add(("vert", w >> 1))
+                    t.add(("vert", r >> 1))
                 for a, b in ((v, r), (u, w), (w, r)):
                     self.probe(a, b, t)
             return len(t)
@@ -138,8 +166,9 @@ class Replay:
         jt = int(np.searchsorted(self.col[self.rp[u]:self.rp[u + 1]], tt))
         t.add(("col", (int(self.rp[u]) + jt) >> 3))
         if cls:
-            for z in (w, r, tt):
-                t.add(("vert", z >> 1))
+            if self.probe_kind == "search":
+                for z in (w, r, tt):
+                    t.add(("vert", z >> 1))
             for a, b in ((u, w), (u, r), (w, r), (v, tt), (w, tt), (r, tt)):
                 self.probe(a, b, t)
         return len(t)
@@ -147,16 +176,19 @@ class Replay:
 
 def model(workload: str, samples: int = 4000, seed: int = 42) -> dict:
     rp, col = synth.workload(workload)
-    rep = Replay(rp, col)
     out = {"workload": workload, "samples": samples, "seed": seed,
-           "layout": "16 B vertex/alias/slot records, 4 B ids and ACC, 8 B Q; 32 B sectors",
+           "layout": ("16 B vertex/alias/slot records, 4 B ids and ACC, 8 B Q, 16 B edge-hash buckets "
+                      "(home bucket counted); 32 B sectors"),
            "source": "written by oracle/sector_model.py"}
-    for method, name in ((0, "MOSS4"), (1, "T5"), (2, "PATH5")):
-        first = 1_000_000
-        _, cls, verts = rep.g.run(method, seed, samples, first=first, record=True)
-        n = [rep.sample(method, seed, first + i, verts[i], int(cls[i])) for i in range(samples)]
-        out[name] = {"sectors_per_sample": float(np.mean(n)), "stderr": float(np.std(n) / np.sqrt(samples)),
-                     "collision_rate": float(np.mean(cls == 0))}
+    for probe, suffix in (("search", "_search"), ("hash", "_hash")):
+        rep = Replay(rp, col, probe)
+        for method, name in ((0, "MOSS4"), (1, "T5"), (2, "PATH5")):
+            first = 1_000_000
+            _, cls, verts = rep.g.run(method, seed, samples, first=first, record=True)
+            n = [rep.sample(method, seed, first + i, verts[i], int(cls[i])) for i in range(samples)]
+            out[name + suffix] = {"sectors_per_sample": float(np.mean(n)),
+                                  "stderr": float(np.std(n) / np.sqrt(samples)),
+                                  "collision_rate": float(np.mean(cls == 0))}
     return out
 
 
