@@ -309,8 +309,15 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
     return out;
 }
 
+// Resident blocks per SM each sampler is compiled for: the loop is bound by
+// memory latency, so more warps in flight help until register spills cost
+// more than they hide (measured: MOSS-4 and T-5 fastest at 6 blocks of 256
+// threads, Path-5, with its larger live state, at 4).
+template <int METHOD>
+constexpr int min_blocks() { return METHOD == 2 ? 4 : 6; }
+
 template <int METHOD, bool RECORD, bool HASH>
-__global__ void __launch_bounds__(kThreads) k_sample(DevGraph g, uint64_t first, uint64_t count, uint64_t seed,
+__global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGraph g, uint64_t first, uint64_t count, uint64_t seed,
                                                      uint64_t *partials, uint8_t *classes, uint32_t *verts) {
     __shared__ uint8_t lut[kLut];
     __shared__ uint32_t hist[kWarps][kSlots];
