@@ -160,6 +160,7 @@ struct moss_graph {
     uint32_t *col = nullptr;
     uint4 *slot = nullptr;
     uint32_t *acc = nullptr;
+    uint32_t *owner = nullptr;   // vertex of each CSR slot (flat per-slot passes)
     uint64_t *q = nullptr;
     u128 *gam[3] = {nullptr, nullptr, nullptr};
     uint4 *seed[3] = {nullptr, nullptr, nullptr};
@@ -170,13 +171,13 @@ struct moss_graph {
     int partial_rows = 0;
     uint64_t *counts = nullptr;  // 2 x 22
     moss_result *res_dev = nullptr;
-    uint32_t *flags = nullptr;   // device status word
+    uint32_t *flags = nullptr;   // device status: [0] error bits, [1] matched twins
     void *arena = nullptr;       // every device array above lives in this one allocation
     int probe = MOSS_PROBE_HASH; // membership tests: hashed edge set or list search
     unsigned long long *hash = nullptr;  // 2 keys per bucket
     uint64_t hash_buckets = 0;
     moss_result res_host{};      // host staging of the result
-    uint32_t flags_host = 0;
+    uint32_t flags_host[2] = {0, 0};
 };
 
 namespace {
@@ -262,7 +263,8 @@ struct Carver {
 };
 
 int read_flags(moss_graph *g, cudaStream_t s) {
-    MOSS_CUDA(cudaMemcpyAsync(&g->flags_host, g->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "reading status");
+    MOSS_CUDA(cudaMemcpyAsync(g->flags_host, g->flags, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s),
+              "reading status");
     MOSS_CUDA(cudaStreamSynchronize(s), "synchronising stream");
     return MOSS_OK;
 }
@@ -345,6 +347,7 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
             g->col = c.take<uint32_t>(nnz);
             g->slot = c.take<uint4>(nnz);
             g->acc = c.take<uint32_t>(nnz);
+            g->owner = c.take<uint32_t>(nnz);
             g->q = c.take<uint64_t>(n);
             for (int l = 0; l < 3; ++l) {
                 g->gam[l] = c.take<u128>(n);
@@ -354,27 +357,28 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
             g->partials = c.take<uint64_t>((uint64_t)prow * kSlots + (uint64_t)blocks * 6 * 2);
             g->counts = c.take<uint64_t>(2 * kSlots);
             g->res_dev = c.take<moss_result>(1);
-            g->flags = c.take<uint32_t>(1);
+            g->flags = c.take<uint32_t>(2);
             rp_dev = c.take<uint8_t>(rp_bytes);
         }
     }
     STEP(cudaMemcpyAsync(rp_dev, row_ptr, rp_bytes, cudaMemcpyDefault, s), "copying row_ptr");
     if (nnz) STEP(cudaMemcpyAsync(g->col, col, nnz * sizeof(uint32_t), cudaMemcpyDefault, s), "copying col");
-    STEP(cudaMemsetAsync(g->flags, 0, sizeof(uint32_t), s), "clearing status");
+    STEP(cudaMemsetAsync(g->flags, 0, 2 * sizeof(uint32_t), s), "clearing status");
     STEP(launch_vertices(rp_dev, row_ptr_is_64, n, nnz, g->vert, g->flags, s), "vertex kernel");
     {
         u128 *tp = reinterpret_cast<u128 *>(g->partials + (uint64_t)prow * kSlots);
-        STEP(launch_slots(n, g->col, g->vert, g->slot, g->acc, g->q, g->gam[0], g->gam[1], g->gam[2], tp, blocks,
-                          g->flags, s),
-             "slot kernel");
+        STEP(launch_slots(n, nnz, g->col, g->vert, g->slot, g->acc, g->owner, g->q, g->gam[0], g->gam[1], g->gam[2],
+                          tp, blocks, g->flags, s),
+             "slot kernels");
         STEP(launch_totals(tp, blocks, g->tot, s), "totals kernel");
     }
     STEP(cudaMemcpyAsync(&g->tot_h, g->tot, sizeof(DevTotals), cudaMemcpyDeviceToHost, s), "reading totals");
     rc = read_flags(g, s);
     if (rc) goto fail_out;
-    if (g->flags_host) {
+    if (!g->flags_host[0] && g->flags_host[1] != nnz) g->flags_host[0] |= kErrAsym;
+    if (g->flags_host[0]) {
         char buf[256];
-        describe_flags(g->flags_host, buf, sizeof(buf));
+        describe_flags(g->flags_host[0], buf, sizeof(buf));
         rc = fail(MOSS_EGRAPH, "invalid CSR: %s", buf);
         goto fail_out;
     }
@@ -403,7 +407,7 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
         return cuda_fail(e, "allocating scratch");
     uint32_t *idx = static_cast<uint32_t *>(scratch);
     uint64_t *pre = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(scratch) + ((g->nnz * 4 + 255) & ~255ULL));
-    e = cudaMemsetAsync(g->flags, 0, sizeof(uint32_t), s);
+    e = cudaMemsetAsync(g->flags, 0, 2 * sizeof(uint32_t), s);
     if (e == cudaSuccess) e = launch_sigma_alias(g->n, g->vert, g->acc, g->slot, idx, pre, s);
     int which[3], nt = 0;
     u128 *w[3];
@@ -438,13 +442,13 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
         while ((1ULL << lg) < buckets) ++lg;
         e = cudaMemsetAsync(g->hash, 0xFF, buckets * 16, s);
         if (e == cudaSuccess)
-            e = launch_edge_hash(g->n, g->vert, g->col, g->hash, (uint32_t)(buckets - 1), 64 - lg, s);
+            e = launch_edge_hash(g->nnz, g->col, g->owner, g->hash, (uint32_t)(buckets - 1), 64 - lg, s);
         hashed = e == cudaSuccess;
     }
     if (e != cudaSuccess) return cuda_fail(e, "table kernels");
     rc = read_flags(g, s);
     if (rc) return rc;
-    if (g->flags_host & kErrOverflow) return fail(MOSS_EOVERFLOW, "a vertex weight total times n exceeds 2^128");
+    if (g->flags_host[0] & kErrOverflow) return fail(MOSS_EOVERFLOW, "a vertex weight total times n exceeds 2^128");
     g->built = 1u << 3;
     if (k_mask & (1u << 4)) g->built |= 1u;
     if (k_mask & (1u << 5)) g->built |= 6u;

@@ -118,15 +118,18 @@ __global__ void k_finalize(FinalizeIn in, const uint64_t *hits, const DevTotals 
     double v2 = 0.0;
     for (int i = 1; i <= 21; ++i)
         if (i != 2 && kPhi5[i - 1][2] > 0) v2 += kPhi5[i - 1][2] * kPhi5[i - 1][2] * r.var[i];
-    for (int i = 1; i <= 21; ++i) {
-        if (i == 2 || kPhi5[i - 1][2] == 0) continue;
-        for (int j = 1; j <= 21; ++j) {
-            if (j == 2 || j == i || kPhi5[j - 1][2] == 0) continue;
-            double c = 0.0;
-            for (int l = 0; l < 2; ++l)
-                if (avail[l]) c -= (a[l][i] * plug[i]) * (a[l][j] * plug[j]) / K[l];
-            v2 += kPhi5[i - 1][2] * kPhi5[j - 1][2] * c;
+    // sum_{i != j} phi_i phi_j Cov(i, j) with Cov = -sum_l b_i b_j / K_l,
+    // b_i = phi_i a^(l)_i plug_i: the pair sum is (sum b)^2 - sum b^2 per l
+    for (int l = 0; l < 2; ++l) {
+        if (!avail[l]) continue;
+        double sb = 0.0, sbb = 0.0;
+        for (int i = 1; i <= 21; ++i) {
+            if (i == 2 || kPhi5[i - 1][2] == 0) continue;
+            const double b = kPhi5[i - 1][2] * (a[l][i] * plug[i]);
+            sb += b;
+            sbb += b * b;
         }
+        v2 -= (sb * sb - sbb) / K[l];
     }
     r.var[2] = v2;
     *out = r;

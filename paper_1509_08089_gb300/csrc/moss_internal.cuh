@@ -115,11 +115,12 @@ __device__ __forceinline__ Words4 philox4x64(uint64_t c0, uint64_t c1, uint64_t 
 // moss_tables.cu
 cudaError_t launch_vertices(const void *row_ptr, int is64, uint32_t n, uint64_t nnz, uint4 *vert,
                             uint32_t *flags, cudaStream_t s);
-cudaError_t launch_slots(uint32_t n, const uint32_t *col, uint4 *vert, uint4 *slot, uint32_t *acc,
-                         uint64_t *q, u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials,
+// flags[0]: kErr* bits; flags[1]: slots whose twin was matched (must reach nnz)
+cudaError_t launch_slots(uint32_t n, uint64_t nnz, const uint32_t *col, uint4 *vert, uint4 *slot, uint32_t *acc,
+                         uint32_t *owner, uint64_t *q, u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials,
                          int blocks, uint32_t *flags, cudaStream_t s);
 cudaError_t launch_totals(const u128 *partials, int blocks, DevTotals *tot, cudaStream_t s);
-cudaError_t launch_edge_hash(uint32_t n, const uint4 *vert, const uint32_t *col, unsigned long long *table,
+cudaError_t launch_edge_hash(uint64_t nnz, const uint32_t *col, const uint32_t *owner, unsigned long long *table,
                              uint32_t mask, uint32_t shift, cudaStream_t s);
 cudaError_t launch_sigma_alias(uint32_t n, const uint4 *vert, const uint32_t *acc, uint4 *slot,
                                uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s);

@@ -359,12 +359,14 @@ __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGr
     }
 }
 
+// one warp per class slot: lanes stride over the block rows, then a warp sum
 __global__ void k_reduce(const uint64_t *partials, int blocks, uint64_t *out) {
-    const int c = threadIdx.x;
-    if (c >= kSlots) return;
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint64_t s = 0;
-    for (int b = 0; b < blocks; ++b) s += partials[(uint64_t)b * kSlots + c];
-    out[c] = s;
+    for (int b = lane; b < blocks; b += 32) s += partials[(uint64_t)b * kSlots + c];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
+    if (lane == 0) out[c] = s;
 }
 
 template <int M, bool R>
@@ -419,7 +421,7 @@ cudaError_t launch_sample(int method, const DevGraph &g, uint64_t first, uint64_
 }
 
 cudaError_t launch_reduce(const uint64_t *partials, int blocks, uint64_t *out, cudaStream_t s) {
-    k_reduce<<<1, 32, 0, s>>>(partials, blocks, out);
+    k_reduce<<<1, 32 * kSlots, 0, s>>>(partials, blocks, out);
     return cudaGetLastError();
 }
 

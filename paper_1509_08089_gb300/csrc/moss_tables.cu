@@ -86,11 +86,12 @@ __global__ void k_vertices(const IdxT *row_ptr, uint32_t n, uint64_t nnz, uint4 
 }
 
 // --------------------------------------------------------------- slots ---
-// One warp per vertex: validation, twin positions, ACC prefix, S_v, Q_v,
-// the three vertex weights and the block's share of the exact totals.
+// One warp per vertex: validation, the owner of each slot, ACC prefix, S_v,
+// Q_v, the three vertex weights and the block's share of the exact totals.
 __global__ void __launch_bounds__(kTableThreads) k_slots(uint32_t n, const uint32_t *__restrict__ col, uint4 *vert,
-                                                        uint4 *slot, uint32_t *acc, uint64_t *q, u128 *gam0,
-                                                        u128 *gam1, u128 *gam2, u128 *partials, uint32_t *flags) {
+                                                        uint4 *slot, uint32_t *acc, uint32_t *owner, uint64_t *q,
+                                                        u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials,
+                                                        uint32_t *flags) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     u128 t_g0 = 0, t_g1 = 0, t_g2 = 0, t_l3 = 0, t_l4 = 0;
@@ -102,7 +103,7 @@ __global__ void __launch_bounds__(kTableThreads) k_slots(uint32_t n, const uint3
         uint64_t run = 0, qsum = 0;
         for (uint32_t base = 0; base < d; base += kWarp) {
             const uint32_t i = base + lane;
-            uint32_t x = 0, w = 0, twin = 0;
+            uint32_t x = 0, w = 0;
             if (i < d) {
                 x = col[o + i];
                 if (x >= n) {
@@ -110,22 +111,15 @@ __global__ void __launch_bounds__(kTableThreads) k_slots(uint32_t n, const uint3
                 } else {
                     if (x == v) err |= kErrSelf;
                     if (i > 0 && col[o + i - 1] >= x) err |= kErrOrder;
-                    const uint4 xr = vert[x];
-                    // POS of v in N_x by binary search
-                    uint32_t lo = xr.x, len = xr.y;
-                    while (len > 0) {
-                        uint32_t half = len >> 1;
-                        if (col[lo + half] < (uint32_t)v) { lo += half + 1; len -= half + 1; } else { len = half; }
-                    }
-                    if (lo >= xr.x + xr.y || col[lo] != (uint32_t)v) err |= kErrAsym;
-                    twin = lo - xr.x;
-                    w = xr.y ? xr.y - 1 : 0;
+                    const uint32_t dx = vert[x].y;
+                    w = dx ? dx - 1 : 0;
                 }
             }
             uint64_t incl = warp_incl_scan64(w, lane);
             if (i < d) {
                 acc[o + i] = (uint32_t)(run + incl - w);
-                slot[o + i] = make_uint4(x, 0u, 0u, twin);
+                slot[o + i] = make_uint4(x, 0u, 0u, 0u);
+                owner[o + i] = (uint32_t)v;
             }
             run += __shfl_sync(0xffffffffu, incl, 31);
             qsum += (uint64_t)w * w;
@@ -194,31 +188,61 @@ __global__ void k_totals(const u128 *partials, int blocks, DevTotals *tot) {
     }
 }
 
+// --------------------------------------------------------------- twins ---
+// One thread per slot.  Each undirected edge {v, x} is handled once, by the
+// endpoint with the larger degree (the smaller id on ties), which searches
+// itself in the other endpoint's (shorter) sorted list and writes both
+// twins: twin(v->x) = POS of v in N_x and twin(x->v) = POS of x in N_v.  For
+// a symmetric graph every edge is matched once, so the matched slots add up
+// to nnz; a reverse that is missing leaves the sum short.
+__global__ void k_twin(uint32_t n, uint64_t nnz, const uint4 *__restrict__ vert, const uint32_t *__restrict__ col,
+                       const uint32_t *__restrict__ owner, uint4 *slot, uint32_t *flags) {
+    uint32_t matched = 0, err = 0;
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = owner[p], x = col[p];
+        if (x >= n || x == v) continue;  // flagged by the slot pass
+        const uint4 vr = vert[v], xr = vert[x];
+        const bool mine = vr.y > xr.y || (vr.y == xr.y && v < x);
+        if (!mine) continue;
+        uint32_t lo = xr.x, len = xr.y;
+        while (len > 0) {
+            const uint32_t half = len >> 1;
+            if (col[lo + half] < v) { lo += half + 1; len -= half + 1; } else { len = half; }
+        }
+        if (lo >= xr.x + xr.y || col[lo] != v) {
+            err |= kErrAsym;
+            continue;
+        }
+        uint32_t *s32 = reinterpret_cast<uint32_t *>(slot);
+        s32[4 * p + 3] = lo - xr.x;                           // POS of v in N_x
+        s32[4 * (uint64_t)lo + 3] = (uint32_t)(p - vr.x);     // POS of x in N_v
+        matched += 2;
+    }
+    if (err) atomicOr(flags, err);
+    // warp sum of the matched slots, one atomic per warp
+#pragma unroll
+    for (int sft = 16; sft > 0; sft >>= 1) matched += __shfl_down_sync(0xffffffffu, matched, sft);
+    if ((threadIdx.x & 31) == 0 && matched) atomicAdd(flags + 1, matched);
+}
+
 // ----------------------------------------------------- hashed edge set ---
-// One warp per vertex inserts the edges {v, x} with x > v by compare-and-swap
+// One thread per slot inserts the edge {v, x} with v < x by compare-and-swap
 // into the first free slot from the home bucket on.  The table has at least
 // four slots per edge, so a free slot always exists and the walk is bounded
 // by the bucket count.
-__global__ void __launch_bounds__(kTableThreads) k_edge_hash(uint32_t n, const uint4 *__restrict__ vert,
-                                                            const uint32_t *__restrict__ col,
-                                                            unsigned long long *table, uint32_t mask,
-                                                            uint32_t shift) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
-    for (uint64_t v = (uint64_t)blockIdx.x * wpb + warp; v < n; v += (uint64_t)gridDim.x * wpb) {
-        const uint4 vr = vert[v];
-        for (uint32_t i = lane; i < vr.y; i += kWarp) {
-            const uint32_t x = col[vr.x + i];
-            if (x <= (uint32_t)v) continue;
-            const unsigned long long key = edge_key((uint32_t)v, x);
-            uint32_t b = edge_bucket(key, shift);
-            for (uint64_t it = 0; it <= mask; ++it) {
-                unsigned long long old = atomicCAS(table + 2ull * b, (unsigned long long)kEmptyKey, key);
-                if (old == kEmptyKey || old == key) break;
-                old = atomicCAS(table + 2ull * b + 1, (unsigned long long)kEmptyKey, key);
-                if (old == kEmptyKey || old == key) break;
-                b = (b + 1) & mask;
-            }
+__global__ void k_edge_hash(uint64_t nnz, const uint32_t *__restrict__ col, const uint32_t *__restrict__ owner,
+                            unsigned long long *table, uint32_t mask, uint32_t shift) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = owner[p], x = col[p];
+        if (x <= v) continue;
+        const unsigned long long key = edge_key(v, x);
+        uint32_t b = edge_bucket(key, shift);
+        for (uint64_t it = 0; it <= mask; ++it) {
+            unsigned long long old = atomicCAS(table + 2ull * b, (unsigned long long)kEmptyKey, key);
+            if (old == kEmptyKey || old == key) break;
+            old = atomicCAS(table + 2ull * b + 1, (unsigned long long)kEmptyKey, key);
+            if (old == kEmptyKey || old == key) break;
+            b = (b + 1) & mask;
         }
     }
 }
@@ -281,41 +305,56 @@ __global__ void __launch_bounds__(kTableThreads) k_sigma_alias(uint32_t n, const
         }
         __syncwarp();
         const uint64_t Ptot = Prun;  // == Arun
-        // pass 2: thresholds and aliases
-        for (uint32_t p = lane; p < d; p += kWarp) {
-            const uint32_t j = idx[o + p];
-            const uint64_t qj = (uint64_t)acc_weight(acc, o, d, S, j) * d;
-            uint32_t thr, alias;
-            if (p < nl) {
-                const uint64_t A = pre[o + p];
-                // first heavy k with P_k >= A (heavy k stored at o + d-1-k)
-                uint32_t lo = 0, len = nh;
+        // pass 2: thresholds and aliases.  Lights take the first heavy whose
+        // inclusive excess reaches their exclusive deficit, heavies the first
+        // light whose deficit exceeds their excess; both sequences are sorted,
+        // so each lane merges a contiguous run after one binary search.
+        {
+            const uint32_t cl = (nl + kWarp - 1) / kWarp;
+            const uint32_t i0 = lane * cl, i1 = min(nl, i0 + cl);
+            if (i0 < i1) {
+                const uint64_t A0 = pre[o + i0];
+                uint32_t k = 0, len = nh;           // first heavy k with P_k >= A
                 while (len > 0) {
-                    uint32_t half = len >> 1;
-                    if (pre[o + d - 1 - (lo + half)] < A) { lo += half + 1; len -= half + 1; } else { len = half; }
+                    const uint32_t half = len >> 1;
+                    if (pre[o + d - 1 - (k + half)] < A0) { k += half + 1; len -= half + 1; } else { len = half; }
                 }
-                thr = (uint32_t)qj;
-                alias = idx[o + d - 1 - lo];
-            } else {
-                const uint32_t k = d - 1 - p;
-                const uint64_t Pk = pre[o + p];
-                if (Pk < Ptot) {
-                    // first light i with A_i > P_k
-                    uint32_t lo = 0, len = nl;
-                    while (len > 0) {
-                        uint32_t half = len >> 1;
-                        if (pre[o + lo + half] <= Pk) { lo += half + 1; len -= half + 1; } else { len = half; }
-                    }
-                    const uint64_t Ai = lo < nl ? pre[o + lo] : Ptot;
-                    thr = (uint32_t)(W + Pk - Ai);
-                    alias = idx[o + d - 1 - (k + 1)];
-                } else {
-                    thr = (uint32_t)W;
-                    alias = j;
+                for (uint32_t i = i0; i < i1; ++i) {
+                    const uint64_t A = pre[o + i];
+                    while (pre[o + d - 1 - k] < A) ++k;
+                    const uint32_t j = idx[o + i];
+                    slot32[4 * (uint64_t)(o + j) + 1] = acc_weight(acc, o, d, S, j) * d;
+                    slot32[4 * (uint64_t)(o + j) + 2] = idx[o + d - 1 - k];
                 }
             }
-            slot32[4 * (uint64_t)(o + j) + 1] = thr;
-            slot32[4 * (uint64_t)(o + j) + 2] = alias;
+        }
+        {
+            const uint32_t ch = (nh + kWarp - 1) / kWarp;
+            const uint32_t k0 = lane * ch, k1 = min(nh, k0 + ch);
+            if (k0 < k1) {
+                const uint64_t P0 = pre[o + d - 1 - k0];
+                uint32_t i = 0, len = nl;           // first light i with A_i > P_k
+                while (len > 0) {
+                    const uint32_t half = len >> 1;
+                    if (pre[o + i + half] <= P0) { i += half + 1; len -= half + 1; } else { len = half; }
+                }
+                for (uint32_t k = k0; k < k1; ++k) {
+                    const uint64_t Pk = pre[o + d - 1 - k];
+                    while (i < nl && pre[o + i] <= Pk) ++i;
+                    const uint32_t j = idx[o + d - 1 - k];
+                    uint32_t thr, alias;
+                    if (Pk < Ptot) {
+                        const uint64_t Ai = i < nl ? pre[o + i] : Ptot;
+                        thr = (uint32_t)(W + Pk - Ai);
+                        alias = idx[o + d - 1 - (k + 1)];
+                    } else {
+                        thr = (uint32_t)W;
+                        alias = j;
+                    }
+                    slot32[4 * (uint64_t)(o + j) + 1] = thr;
+                    slot32[4 * (uint64_t)(o + j) + 2] = alias;
+                }
+            }
         }
         __syncwarp();
     }
@@ -606,10 +645,23 @@ cudaError_t launch_vertices(const void *row_ptr, int is64, uint32_t n, uint64_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_slots(uint32_t n, const uint32_t *col, uint4 *vert, uint4 *slot, uint32_t *acc, uint64_t *q,
-                         u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials, int blocks, uint32_t *flags,
-                         cudaStream_t s) {
-    k_slots<<<blocks, kTableThreads, 0, s>>>(n, col, vert, slot, acc, q, gam0, gam1, gam2, partials, flags);
+static unsigned flat_blocks(uint64_t items) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint64_t b = (items + 255) / 256;
+    const uint64_t cap = (uint64_t)sms * 16;
+    if (b > cap) b = cap;
+    return (unsigned)(b ? b : 1);
+}
+
+cudaError_t launch_slots(uint32_t n, uint64_t nnz, const uint32_t *col, uint4 *vert, uint4 *slot, uint32_t *acc,
+                         uint32_t *owner, uint64_t *q, u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials,
+                         int blocks, uint32_t *flags, cudaStream_t s) {
+    k_slots<<<blocks, kTableThreads, 0, s>>>(n, col, vert, slot, acc, owner, q, gam0, gam1, gam2, partials, flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || nnz == 0) return e;
+    k_twin<<<flat_blocks(nnz), 256, 0, s>>>(n, nnz, vert, col, owner, slot, flags);
     return cudaGetLastError();
 }
 
@@ -618,9 +670,10 @@ cudaError_t launch_totals(const u128 *partials, int blocks, DevTotals *tot, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_edge_hash(uint32_t n, const uint4 *vert, const uint32_t *col, unsigned long long *table,
+cudaError_t launch_edge_hash(uint64_t nnz, const uint32_t *col, const uint32_t *owner, unsigned long long *table,
                              uint32_t mask, uint32_t shift, cudaStream_t s) {
-    k_edge_hash<<<table_blocks(n), kTableThreads, 0, s>>>(n, vert, col, table, mask, shift);
+    if (nnz == 0) return cudaSuccess;
+    k_edge_hash<<<flat_blocks(nnz), 256, 0, s>>>(nnz, col, owner, table, mask, shift);
     return cudaGetLastError();
 }
 
