@@ -29,9 +29,20 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-METRIC = "5-node samples/s at 1M edges"
-WORKLOAD = ("Chung-Lu n=100,000, exponent 2.2, mean degree 20, max degree 5,000, seed 1 (~1M edges), "
-            "k=5 (T-5 + Path-5, K1=K2), sorted uint32 CSR")
+GRAPHS = {
+    "cl_n2k": ("Chung-Lu n=2,000, exponent 2.5, mean degree 8, max degree 200, seed 1 (7,886 edges)", "8k edges"),
+    "cl_n100k": ("Chung-Lu n=100,000, exponent 2.2, mean degree 20, max degree 5,000, seed 1 (~1M edges)",
+                 "1M edges"),
+    "cl_n4m": ("Chung-Lu n=4,000,000, exponent 2.1, mean degree 17, max degree 20,000, seed 1 (~34M edges)",
+               "34M edges"),
+}
+
+
+def describe(workload: str, k: int) -> tuple[str, str]:
+    """(metric, workload description) of a run."""
+    graph, size = GRAPHS[workload]
+    method = "k=5 (T-5 + Path-5, K1=K2)" if k == 5 else "k=4 (MOSS-4)"
+    return f"{k}-node samples/s at {size}", f"{graph}, {method}, sorted uint32 CSR"
 
 
 def parse():
@@ -115,6 +126,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    METRIC, WORKLOAD = describe(args.workload, args.k)
     cores = os.cpu_count() or 1
     per_worker = calibrate_per_worker(args.workload, args.k, args.seed, 3.0)
     with make_pool(cores) as pool:
@@ -200,6 +212,7 @@ def run_gpu(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    METRIC, WORKLOAD = describe(args.workload, args.k)
     if world != args.gpus:
         raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
     # the CPU-baseline pool is spawned before the first GPU call
@@ -333,13 +346,30 @@ def run_gpu(args):
     peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     probe_name = "hash" if args.probe == "hash" else "search"
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", f"dram_traffic_{args.workload}.txt")
+    if os.path.exists(tpath):
+        import hashlib
+        rec = {}
+        for line in open(tpath):
+            if line.strip() and not line.startswith("#"):
+                key, val = line.split()[:2]
+                rec[key] = val
+        src = b"".join(open(os.path.join(ROOT, "paper_1509_08089_gb300", "csrc", f), "rb").read()
+                       for f in ("moss_sample.cu", "moss_internal.cuh"))
+        # counters describe the kernel only while its source is unchanged
+        if hashlib.sha256(src).hexdigest()[:16] == rec.get("source_sha"):
+            traffic = rec
     if sect is not None:
         K, tms = times[dom]
         spb = sect[f"{name[dom]}_{probe_name}"]["sectors_per_sample"]
         ach = spb * 32.0 * K / (tms / 1000.0) / 1e9
+        tb = None
+        if traffic is not None and f"{name[dom]}_{probe_name}" in traffic:
+            tb = float(traffic[f"{name[dom]}_{probe_name}"]) * K / float(traffic["samples_per_launch"])
         roof = {"bound": "hbm", "kernel": f"k_sample<{dom}> ({name[dom]}, {probe_name} probes)", "achieved": ach,
                 "peak": peak,
-                "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak, "traffic": tb,
                 "algorithmic_bytes_per_sample": spb * 32.0, "samples_per_launch": K,
                 "launch_ms": tms, "kernel_times_ms": {name[m]: times[m][1] for m in times}}
 
