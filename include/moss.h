@@ -162,6 +162,35 @@ int moss_sample_records(moss_graph *g, int method, uint64_t first, uint64_t coun
 int moss_finalize(moss_graph *g, int k, const uint64_t *K, const uint64_t *hits, void *stream,
                   moss_result *out);
 
+/* ----------------------------------------------------------------- batches
+ * Many sample-and-estimate requests, on many loaded graphs, in one persistent
+ * launch.  Each request (graph, k, budget, seed) is exactly one
+ * moss_sample_estimate (MOSS-4, Sec. 4.1; MOSS-5 with K1 = floor(B/2),
+ * K2 = B - K1, Sec. 5.1) and yields the same counts and estimates; the batch
+ * only changes how the work is scheduled: every sub-method's sample ids are
+ * cut into tiles that one kernel drains from a device counter, per-tile
+ * counts are summed per request in tile order, and the finalize runs per
+ * request on the device.  The launch sequence is captured into a CUDA graph
+ * on the batch's own stream and replayed until the request list or the tile
+ * size changes.  Graphs must stay alive, built and unchanged while they are
+ * in a batch. */
+typedef struct moss_batch moss_batch;
+int moss_batch_create(int device, moss_batch **out);
+/* Append a request; *index (nullable) receives its position in the results. */
+int moss_batch_add(moss_batch *b, moss_graph *g, int k, uint64_t budget, uint64_t seed, int *index);
+int moss_batch_size(const moss_batch *b);
+int moss_batch_clear(moss_batch *b);
+/* Samples per tile (32 .. 2^30; default 8192). */
+int moss_batch_set_tile(moss_batch *b, uint32_t tile_samples);
+uint32_t moss_batch_tile(const moss_batch *b);
+/* Run every request: results[i] (caller-owned host array of moss_batch_size
+ * entries) receives request i.  Ordered after prior work on `stream`;
+ * synchronous. */
+int moss_batch_run(moss_batch *b, void *stream, moss_result *results);
+/* Time the batch under a few tile sizes and keep the fastest (*chosen). */
+int moss_batch_tune(moss_batch *b, void *stream, uint32_t *chosen);
+void moss_batch_free(moss_batch *b);
+
 /* Exact totals (requires moss_build_tables for the gamma entries). */
 int moss_graph_stats(const moss_graph *g, moss_stats *out);
 

@@ -78,6 +78,15 @@ def load():
         "moss_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "moss_last_error_detail": ([], ctypes.c_char_p),
         "moss_version": ([], ctypes.c_char_p),
+        "moss_batch_create": ([ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
+        "moss_batch_add": ([_vp, _vp, ctypes.c_int, _u64, _u64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "moss_batch_size": ([_vp], ctypes.c_int),
+        "moss_batch_clear": ([_vp], ctypes.c_int),
+        "moss_batch_set_tile": ([_vp, ctypes.c_uint32], ctypes.c_int),
+        "moss_batch_tile": ([_vp], ctypes.c_uint32),
+        "moss_batch_run": ([_vp, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
+        "moss_batch_tune": ([_vp, _vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+        "moss_batch_free": ([_vp], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -204,6 +213,52 @@ def moss_graph_free(g: int):
         load().moss_graph_free(g)
 
 
+def moss_batch_create(device: int = 0) -> int:
+    out = _vp()
+    _check(load().moss_batch_create(device, ctypes.byref(out)))
+    return out.value
+
+
+def moss_batch_add(b: int, g: int, k: int, budget: int, seed: int) -> int:
+    idx = ctypes.c_int(-1)
+    _check(load().moss_batch_add(b, g, k, budget, seed, ctypes.byref(idx)))
+    return idx.value
+
+
+def moss_batch_size(b: int) -> int:
+    return load().moss_batch_size(b)
+
+
+def moss_batch_clear(b: int):
+    _check(load().moss_batch_clear(b))
+
+
+def moss_batch_set_tile(b: int, tile_samples: int):
+    _check(load().moss_batch_set_tile(b, tile_samples))
+
+
+def moss_batch_tile(b: int) -> int:
+    return load().moss_batch_tile(b)
+
+
+def moss_batch_run(b: int, stream=None) -> list:
+    n = load().moss_batch_size(b)
+    arr = (moss_result * max(n, 1))()
+    _check(load().moss_batch_run(b, _stream(stream), arr))
+    return [arr[i] for i in range(n)]
+
+
+def moss_batch_tune(b: int, stream=None) -> int:
+    c = ctypes.c_uint32(0)
+    _check(load().moss_batch_tune(b, _stream(stream), ctypes.byref(c)))
+    return c.value
+
+
+def moss_batch_free(b: int):
+    if b:
+        load().moss_batch_free(b)
+
+
 # ------------------------------------------------------------ convenience --
 def result_dict(r: moss_result) -> dict:
     """moss_result as plain Python/numpy values."""
@@ -212,6 +267,48 @@ def result_dict(r: moss_result) -> dict:
             "est": np.array(list(r.est)), "var": np.array(list(r.var)),
             "lam": np.array([list(r.lambda_[l]) for l in range(2)]),
             "triangles": r.triangles, "triangles_var": r.triangles_var}
+
+
+class Batch:
+    """Owning wrapper of a request batch (see moss_batch_* in include/moss.h)."""
+
+    def __init__(self, device: int = 0):
+        self.handle = moss_batch_create(device)
+
+    def add(self, graph: "Graph", k: int, budget: int, seed: int) -> int:
+        return moss_batch_add(self.handle, graph.handle, k, budget, seed)
+
+    def run(self, stream=None) -> list[dict]:
+        return [result_dict(r) for r in moss_batch_run(self.handle, stream)]
+
+    def tune(self, stream=None) -> int:
+        return moss_batch_tune(self.handle, stream)
+
+    def set_tile(self, tile_samples: int):
+        moss_batch_set_tile(self.handle, tile_samples)
+
+    def clear(self):
+        moss_batch_clear(self.handle)
+
+    def __len__(self):
+        return moss_batch_size(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            moss_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Graph:

@@ -600,6 +600,7 @@ namespace moss {
 
 int graph_info(const moss_graph *g, GraphInfo *out) {
     out->view = view(g);
+    out->tot = g->tot;
     out->device = g->device;
     out->built = g->built;
     for (int l = 0; l < 3; ++l) out->total_nonzero[l] = g->tot_h.gamma[l] != 0;

@@ -31,15 +31,18 @@ __device__ __forceinline__ double u128_to_double(u128 x) {
     return (double)(uint64_t)(x >> 64) * 18446744073709551616.0 + (double)(uint64_t)x;
 }
 
-__global__ void k_finalize(FinalizeIn in, const uint64_t *hits, const DevTotals *tot, moss_result *out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// hits0/hits1: counts of the first and second sub-method (hits1 may be null)
+__device__ void finalize_one(const FinalizeIn &in, const uint64_t *hits0, const uint64_t *hits1,
+                             const DevTotals *tot, moss_result *out) {
     moss_result r;
     memset(&r, 0, sizeof(r));
     r.k = in.k;
     r.K[0] = in.K[0];
     r.K[1] = in.K[1];
-    for (int l = 0; l < 2; ++l)
-        for (int i = 0; i < kSlots; ++i) r.hits[l][i] = hits[l * kSlots + i];
+    for (int i = 0; i < kSlots; ++i) {
+        r.hits[0][i] = hits0 ? hits0[i] : 0;
+        r.hits[1][i] = hits1 ? hits1[i] : 0;
+    }
     if (in.k == 4) {
         r.n_classes = 6;
         const double G = u128_to_double(tot->gamma[0]);
@@ -135,11 +138,34 @@ __global__ void k_finalize(FinalizeIn in, const uint64_t *hits, const DevTotals 
     *out = r;
 }
 
+__global__ void k_finalize(FinalizeIn in, const uint64_t *hits, const DevTotals *tot, moss_result *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    finalize_one(in, hits, hits + kSlots, tot, out);
+}
+
+// one thread per request of a batch
+__global__ void k_finalize_batch(const BatchRequest *reqs, int nreq, const uint64_t *task_counts,
+                                 moss_result *out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nreq) return;
+    const BatchRequest q = reqs[r];
+    const uint64_t *h0 = q.task[0] >= 0 ? task_counts + (uint64_t)q.task[0] * kSlots : nullptr;
+    const uint64_t *h1 = q.task[1] >= 0 ? task_counts + (uint64_t)q.task[1] * kSlots : nullptr;
+    finalize_one(q.in, h0, h1, q.tot, out + r);
+}
+
 }  // namespace
 
 cudaError_t launch_finalize(const FinalizeIn &in, const uint64_t *hits_dev, const DevTotals *tot, void *result_dev,
                             cudaStream_t s) {
     k_finalize<<<1, 32, 0, s>>>(in, hits_dev, tot, static_cast<moss_result *>(result_dev));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batch(const BatchRequest *reqs, int nreq, const uint64_t *task_counts, void *results,
+                                  cudaStream_t s) {
+    if (nreq <= 0) return cudaSuccess;
+    k_finalize_batch<<<(nreq + 63) / 64, 64, 0, s>>>(reqs, nreq, task_counts, static_cast<moss_result *>(results));
     return cudaGetLastError();
 }
 

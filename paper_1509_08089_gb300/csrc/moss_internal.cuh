@@ -147,9 +147,38 @@ struct FinalizeIn {
 cudaError_t launch_finalize(const FinalizeIn &in, const uint64_t *hits_dev, const DevTotals *tot,
                             void *result_dev, cudaStream_t s);
 
+// ---------------------------------------------------------------- batches --
+// One task = one sub-method of one request: sample ids [first, first+count)
+// of `method` on graph `graph`, cut into tiles of the batch's tile size,
+// starting at tile `tile0` of the batch.
+struct BatchTask {
+    uint64_t seed;
+    uint64_t first;
+    uint64_t count;
+    uint64_t tile0;
+    uint32_t graph;
+    uint32_t method;
+};
+struct BatchRequest {
+    FinalizeIn in;
+    const DevTotals *tot;
+    int task[2];      // task index per sub-method, -1 when it draws nothing
+};
+// persistent sampler over a batch: tile_counts[t][22] per tile
+cudaError_t launch_sample_batch(const DevGraph *graphs, const BatchTask *tasks, int ntasks, uint64_t ntiles,
+                                uint32_t tile_samples, unsigned long long *next_tile, uint32_t *tile_counts,
+                                int blocks, cudaStream_t s);
+// task_counts[task][22] = sum of the task's tile rows, in tile order
+cudaError_t launch_batch_reduce(const BatchTask *tasks, int ntasks, uint32_t tile_samples,
+                                const uint32_t *tile_counts, uint64_t *task_counts, cudaStream_t s);
+int batch_blocks(int device);
+cudaError_t launch_finalize_batch(const BatchRequest *reqs, int nreq, const uint64_t *task_counts, void *results,
+                                  cudaStream_t s);
+
 // moss_capi.cu: what another translation unit needs of a moss_graph
 struct GraphInfo {
     DevGraph view;
+    const DevTotals *tot;
     int device;
     unsigned built;          // bit l: vertex table l; bit 3: sigma tables
     bool total_nonzero[3];   // Gamma, Gamma^(1), Gamma^(2) > 0

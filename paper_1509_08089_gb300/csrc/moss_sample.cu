@@ -360,6 +360,83 @@ __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGr
 }
 
 // one warp per class slot: lanes stride over the block rows, then a warp sum
+// ---------------------------------------------------------------- batches --
+// Many requests on many graphs in one persistent launch.  Warps take tiles
+// (fixed-size runs of sample ids of one task) from a global counter -- one
+// atomic per tile, none per sample -- and write each tile's class counts to
+// the tile's own row, so a task's counts are the sum of its rows whatever
+// warp ran which tile, and equal the counts of a solo launch of the task.
+constexpr int kBatchBlocks = 4;   // resident blocks per SM (Path-5 bound)
+
+template <bool HASH>
+__device__ __forceinline__ int sample_any(const DevGraph &g, const uint8_t *lut4, const uint8_t *lut5, uint32_t method,
+                                          uint64_t seed, uint64_t s) {
+    if (method == 0) return sample_moss4<HASH>(g, lut4, seed, s).cls;
+    if (method == 1) return sample_t5<HASH>(g, lut5, seed, s).cls;
+    return sample_path5<HASH>(g, lut5, seed, s).cls;
+}
+
+__global__ void __launch_bounds__(kThreads, kBatchBlocks)
+    k_sample_batch(const DevGraph *graphs, const BatchTask *tasks, int ntasks, uint64_t ntiles, uint32_t tile_samples,
+                   unsigned long long *next_tile, uint32_t *tile_counts) {
+    __shared__ uint8_t lut4[64];
+    __shared__ uint8_t lut5[kLut];
+    __shared__ uint32_t hist[kWarps][kSlots];
+    __shared__ DevGraph gsh[kWarps];
+    static_assert(sizeof(DevGraph) % 4 == 0 && sizeof(DevGraph) / 4 <= 32, "graph descriptor staging");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 64; i += kThreads) lut4[i] = g_lut4[i];
+    for (int i = threadIdx.x; i < kLut; i += kThreads) lut5[i] = g_lut5[i];
+    __syncthreads();
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(next_tile, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= ntiles) break;
+        // the task of tile t: the last task whose first tile is <= t
+        int lo = 0, len = ntasks;
+        while (len > 0) {
+            const int half = len >> 1;
+            if (tasks[lo + half].tile0 <= t) { lo += half + 1; len -= half + 1; } else { len = half; }
+        }
+        const BatchTask tk = tasks[lo - 1];
+        if (lane < (int)(sizeof(DevGraph) / 4))
+            reinterpret_cast<uint32_t *>(&gsh[warp])[lane] = reinterpret_cast<const uint32_t *>(graphs + tk.graph)[lane];
+        if (lane < kSlots) hist[warp][lane] = 0;
+        __syncwarp();
+        const DevGraph &g = gsh[warp];
+        const uint64_t f = tk.first + (t - tk.tile0) * tile_samples;
+        const uint64_t left = tk.first + tk.count - f;
+        const uint32_t cnt = (uint32_t)(left < tile_samples ? left : tile_samples);
+        const bool hashed = g.hash != nullptr;
+        for (uint32_t base = 0; base < cnt; base += 32) {
+            const uint32_t i = base + lane;
+            int cls = kSlots;
+            if (i < cnt)
+                cls = hashed ? sample_any<true>(g, lut4, lut5, tk.method, tk.seed, f + i)
+                             : sample_any<false>(g, lut4, lut5, tk.method, tk.seed, f + i);
+            const uint32_t peers = __match_any_sync(0xffffffffu, cls);
+            if (cls < kSlots && lane == __ffs(peers) - 1) atomicAdd(&hist[warp][cls], (uint32_t)__popc(peers));
+        }
+        __syncwarp();
+        if (lane < kSlots) tile_counts[t * kSlots + lane] = hist[warp][lane];
+        __syncwarp();
+    }
+}
+
+// block per task, warp per class slot: sum the task's tile rows
+__global__ void k_batch_reduce(const BatchTask *tasks, uint32_t tile_samples, const uint32_t *tile_counts,
+                               uint64_t *task_counts) {
+    const BatchTask tk = tasks[blockIdx.x];
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t nt = (tk.count + tile_samples - 1) / tile_samples;
+    uint64_t s = 0;
+    for (uint64_t j = lane; j < nt; j += 32) s += tile_counts[(tk.tile0 + j) * kSlots + c];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
+    if (lane == 0) task_counts[(uint64_t)blockIdx.x * kSlots + c] = s;
+}
+
 __global__ void k_reduce(const uint64_t *partials, int blocks, uint64_t *out) {
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint64_t s = 0;
@@ -418,6 +495,29 @@ cudaError_t launch_sample(int method, const DevGraph &g, uint64_t first, uint64_
         case 5: return launch_one<2, true>(g, first, count, seed, partials, blocks, classes, verts, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+int batch_blocks(int device) {
+    int sms = 148, per = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample_batch, kThreads, 0) != cudaSuccess || per < 1)
+        per = 1;
+    return sms * per;
+}
+
+cudaError_t launch_sample_batch(const DevGraph *graphs, const BatchTask *tasks, int ntasks, uint64_t ntiles,
+                                uint32_t tile_samples, unsigned long long *next_tile, uint32_t *tile_counts,
+                                int blocks, cudaStream_t s) {
+    if (ntasks <= 0 || ntiles == 0) return cudaSuccess;
+    k_sample_batch<<<blocks, kThreads, 0, s>>>(graphs, tasks, ntasks, ntiles, tile_samples, next_tile, tile_counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_reduce(const BatchTask *tasks, int ntasks, uint32_t tile_samples,
+                                const uint32_t *tile_counts, uint64_t *task_counts, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    k_batch_reduce<<<ntasks, 32 * kSlots, 0, s>>>(tasks, tile_samples, tile_counts, task_counts);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const uint64_t *partials, int blocks, uint64_t *out, cudaStream_t s) {

@@ -1,0 +1,118 @@
+"""Batched persistent launch: many requests on many graphs in one kernel.
+
+Each request must give exactly the counts and estimates of its solo
+moss_sample_estimate (same sample ids, same finalize), whatever the tile size
+and however often the captured launch is replayed; a few are also checked
+against the oracle."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1509_08089_gb300 as moss
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def uneven_graphs(count: int, seed: int):
+    """Half Chung-Lu (exponent 2.0-3.0), half 2-D RGG (mean degree 6-30),
+    n from 500 to 5,000 -- a scaled-down version of the batched workload."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(500, 5000))
+        if i % 2 == 0:
+            gamma = float(rng.uniform(2.0, 3.0))
+            dbar = float(rng.uniform(4.0, 12.0))
+            out.append(synth.chung_lu(n, gamma, dbar, min(0.2 * n, 40 * dbar), seed=1000 + i))
+        else:
+            out.append(synth.rgg(n, float(rng.uniform(6.0, 30.0)), seed=2000 + i))
+    return out
+
+
+@pytest.fixture(scope="module")
+def fleet():
+    csrs = uneven_graphs(14, 3) + [synth.star(6), synth.cycle(9)]
+    graphs = [moss.Graph(rp, col) for rp, col in csrs]
+    yield csrs, graphs
+    for g in graphs:
+        g.close()
+
+
+def requests(n_graphs: int, seed: int):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_graphs):
+        for _ in range(2):
+            k = int(rng.choice([4, 5]))
+            budget = int(rng.integers(10_000, 300_000))
+            out.append((i, k, budget, int(rng.integers(1, 2**62))))
+    return out
+
+
+def same(a: dict, b: dict):
+    assert tuple(a["K"]) == tuple(b["K"])
+    assert np.array_equal(a["hits"], b["hits"])
+    assert np.array_equal(a["est"], b["est"])
+    assert np.array_equal(a["var"], b["var"])
+
+
+def test_batch_equals_solo_runs(fleet):
+    csrs, graphs = fleet
+    reqs = requests(len(graphs), 11)
+    with moss.Batch() as batch:
+        for gi, k, budget, seed in reqs:
+            batch.add(graphs[gi], k, budget, seed)
+        assert len(batch) == len(reqs)
+        res = batch.run()
+        for (gi, k, budget, seed), r in zip(reqs, res):
+            same(r, graphs[gi].estimate(k, budget, seed))
+        # replay of the captured launch
+        again = batch.run()
+        for a, b in zip(res, again):
+            same(a, b)
+        # other tile sizes (ragged tiles everywhere) give the same results
+        for tile in (32, 1000, 65536):
+            batch.set_tile(tile)
+            for a, b in zip(res, batch.run()):
+                same(a, b)
+        chosen = batch.tune()
+        assert chosen in (1024, 4096, 16384, 65536)
+        for a, b in zip(res, batch.run()):
+            same(a, b)
+
+
+def test_batch_against_oracle(fleet):
+    csrs, graphs = fleet
+    with moss.Batch() as batch:
+        picks = [(0, 4, 40_001, 5), (1, 5, 30_003, 6), (14, 4, 1000, 7), (15, 5, 2000, 8)]
+        for gi, k, budget, seed in picks:
+            batch.add(graphs[gi], k, budget, seed)
+        res = batch.run()
+    for (gi, k, budget, seed), r in zip(picks, res):
+        og = oracle.OracleGraph(*csrs[gi])
+        if k == 4:
+            ref = og.run(oracle.MOSS4, seed, budget) if og.Gamma[0] else np.zeros(22, np.uint64)
+            assert np.array_equal(r["hits"][0], ref)
+        else:
+            K1, K2 = budget // 2, budget - budget // 2
+            r1 = og.run(oracle.T5, seed, K1) if og.Gamma[1] else np.zeros(22, np.uint64)
+            r2 = og.run(oracle.PATH5, seed, K2) if og.Gamma[2] else np.zeros(22, np.uint64)
+            assert np.array_equal(r["hits"][0], r1)
+            assert np.array_equal(r["hits"][1], r2)
+    assert res[2]["est"][2] == 20.0          # star K_{1,6}: Gamma = 0, n_2 = C(6,3)
+    assert res[3]["est"][1] == pytest.approx(9.0)   # cycle C_9: eta_1 = 9 exactly
+
+
+def test_batch_rejects_unbuilt_graph_and_handles_empty():
+    rp, col = synth.cycle(10)
+    with moss.Graph(rp, col, k_mask=1 << 4) as g, moss.Batch() as batch:
+        assert batch.run() == []
+        with pytest.raises(moss.MossError) as ei:
+            batch.add(g, 5, 100, 1)
+        assert ei.value.status == moss.MOSS_ESTATE
+        batch.add(g, 4, 100, 1)
+        assert batch.run()[0]["est"][1] == pytest.approx(10.0)
