@@ -49,6 +49,7 @@ extern "C" {
 #define MOSS_EGRAPH     -4  /* CSR is not a sorted symmetric simple graph   */
 #define MOSS_EOVERFLOW  -5  /* a size or an exact total exceeds its range   */
 #define MOSS_ESTATE     -6  /* tables for the requested k were not built    */
+#define MOSS_EBUSY      -7  /* a request did not finish before a timeout     */
 
 #define MOSS_METHOD_MOSS4  0   /* Algorithm 1 */
 #define MOSS_METHOD_T5     1   /* Algorithm 3 */
@@ -190,6 +191,62 @@ int moss_batch_run(moss_batch *b, void *stream, moss_result *results);
 /* Time the batch under a few tile sizes and keep the fastest (*chosen). */
 int moss_batch_tune(moss_batch *b, void *stream, uint32_t *chosen);
 void moss_batch_free(moss_batch *b);
+
+/* ----------------------------------------------------------------- serving
+ * A continuous-batching server over resident graphs.  Requests (graph, k,
+ * and either a budget or a target relative standard error) may be submitted
+ * from any thread.  A scheduler thread admits them into at most max_active
+ * slots while at least reserve_bytes of device memory stay free, and runs
+ * ticks: one persistent launch over the next chunk of sample ids of every
+ * active request, about tick_samples samples shared fairly, so requests that
+ * arrive while a tick runs are sampled in the next one.  A result equals
+ * moss_sample_estimate(graph, k, final budget, seed) exactly, alone or in any
+ * mix.  With a target eps instead of a budget, the first pilot_samples set
+ * the budget: for each class with at least 10 pilot hits, hit fraction f,
+ * the samples at which the relative standard error of Theorems 3, 7, 9
+ * (sqrt((1/f - 1)/K)) reaches eps, the largest over classes (doubled at k=5,
+ * K1 = K2), clamped to [min_budget, max_budget]. */
+typedef struct {
+    int max_active;            /* requests sampled concurrently (slots)           */
+    uint64_t tick_samples;     /* samples per launch over all active requests    */
+    uint32_t tile_samples;     /* tile of the persistent launch                   */
+    uint64_t pilot_samples;    /* first chunk of a target-error request           */
+    uint64_t min_budget;       /* clamp of a budget derived from a target         */
+    uint64_t max_budget;
+    uint64_t reserve_bytes;    /* admission keeps this much device memory free    */
+} moss_server_config;
+
+typedef struct {
+    uint64_t budget;           /* samples the request used                         */
+    double latency_s;          /* submit to result                                 */
+    double queue_s;            /* submit to admission                              */
+    uint64_t ticks;            /* launches the request took part in                */
+} moss_request_stats;
+
+typedef struct {
+    uint64_t ticks, samples, completed, pending, active;
+    double busy_s;             /* time inside launches                             */
+    double span_s;             /* first submit to last completion                  */
+} moss_server_info;
+
+typedef struct moss_server moss_server;
+void moss_server_default_config(moss_server_config *cfg);
+int moss_server_create(int device, const moss_server_config *cfg /* nullable */, moss_server **out);
+/* Register a graph built for k = 4 and 5 (before the first request). */
+int moss_server_add_graph(moss_server *s, moss_graph *g, int *graph_id);
+/* budget > 0: fixed budget; budget == 0: derive it from target_rse. */
+int moss_server_submit(moss_server *s, int graph_id, int k, uint64_t budget, double target_rse, uint64_t seed,
+                       uint64_t *request_id);
+/* Block until the request finishes (MOSS_EBUSY after timeout_s); out and
+ * stats are nullable.  A request can be waited for once. */
+int moss_server_wait(moss_server *s, uint64_t request_id, double timeout_s, moss_result *out,
+                     moss_request_stats *stats);
+int moss_server_stats(moss_server *s, moss_server_info *out);
+/* Stops the scheduler (unfinished requests are abandoned) and frees it. */
+void moss_server_free(moss_server *s);
+/* The budget rule above, from pilot counts K[2], hits[2][22] (host only). */
+uint64_t moss_budget_for_target(int k, const uint64_t *K, const uint64_t *hits, double target,
+                                uint64_t min_budget, uint64_t max_budget);
 
 /* Exact totals (requires moss_build_tables for the gamma entries). */
 int moss_graph_stats(const moss_graph *g, moss_stats *out);

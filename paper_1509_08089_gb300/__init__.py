@@ -23,6 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmoss.so")
 
 MOSS_OK, MOSS_EINVAL, MOSS_ENOMEM, MOSS_ECUDA, MOSS_EGRAPH, MOSS_EOVERFLOW, MOSS_ESTATE = 0, -1, -2, -3, -4, -5, -6
+MOSS_EBUSY = -7
 MOSS4, T5, PATH5 = 0, 1, 2
 PROBE_SEARCH, PROBE_HASH = 0, 1
 NSLOTS = 22
@@ -41,6 +42,23 @@ class moss_result(ctypes.Structure):
                 ("hits", (ctypes.c_uint64 * NSLOTS) * 2), ("est", ctypes.c_double * NSLOTS),
                 ("var", ctypes.c_double * NSLOTS), ("lambda_", (ctypes.c_double * NSLOTS) * 2),
                 ("triangles", ctypes.c_double), ("triangles_var", ctypes.c_double)]
+
+
+class moss_server_config(ctypes.Structure):
+    _fields_ = [("max_active", ctypes.c_int), ("tick_samples", ctypes.c_uint64), ("tile_samples", ctypes.c_uint32),
+                ("pilot_samples", ctypes.c_uint64), ("min_budget", ctypes.c_uint64), ("max_budget", ctypes.c_uint64),
+                ("reserve_bytes", ctypes.c_uint64)]
+
+
+class moss_request_stats(ctypes.Structure):
+    _fields_ = [("budget", ctypes.c_uint64), ("latency_s", ctypes.c_double), ("queue_s", ctypes.c_double),
+                ("ticks", ctypes.c_uint64)]
+
+
+class moss_server_info(ctypes.Structure):
+    _fields_ = [("ticks", ctypes.c_uint64), ("samples", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("pending", ctypes.c_uint64), ("active", ctypes.c_uint64), ("busy_s", ctypes.c_double),
+                ("span_s", ctypes.c_double)]
 
 
 class MossError(RuntimeError):
@@ -87,6 +105,16 @@ def load():
         "moss_batch_run": ([_vp, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
         "moss_batch_tune": ([_vp, _vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
         "moss_batch_free": ([_vp], None),
+        "moss_server_default_config": ([ctypes.POINTER(moss_server_config)], None),
+        "moss_server_create": ([ctypes.c_int, ctypes.POINTER(moss_server_config), ctypes.POINTER(_vp)], ctypes.c_int),
+        "moss_server_add_graph": ([_vp, _vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "moss_server_submit": ([_vp, ctypes.c_int, ctypes.c_int, _u64, ctypes.c_double, _u64,
+                                ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "moss_server_wait": ([_vp, _u64, ctypes.c_double, ctypes.POINTER(moss_result),
+                              ctypes.POINTER(moss_request_stats)], ctypes.c_int),
+        "moss_server_stats": ([_vp, ctypes.POINTER(moss_server_info)], ctypes.c_int),
+        "moss_server_free": ([_vp], None),
+        "moss_budget_for_target": ([ctypes.c_int, _vp, _vp, ctypes.c_double, _u64, _u64], ctypes.c_uint64),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -257,6 +285,96 @@ def moss_batch_tune(b: int, stream=None) -> int:
 def moss_batch_free(b: int):
     if b:
         load().moss_batch_free(b)
+
+
+def moss_server_default_config() -> moss_server_config:
+    c = moss_server_config()
+    load().moss_server_default_config(ctypes.byref(c))
+    return c
+
+
+def moss_server_create(device: int = 0, config: moss_server_config | None = None) -> int:
+    out = _vp()
+    _check(load().moss_server_create(device, ctypes.byref(config) if config is not None else None, ctypes.byref(out)))
+    return out.value
+
+
+def moss_server_add_graph(s: int, g: int) -> int:
+    gid = ctypes.c_int(-1)
+    _check(load().moss_server_add_graph(s, g, ctypes.byref(gid)))
+    return gid.value
+
+
+def moss_server_submit(s: int, graph_id: int, k: int, budget: int = 0, target_rse: float = 0.0, seed: int = 1) -> int:
+    rid = ctypes.c_uint64(0)
+    _check(load().moss_server_submit(s, graph_id, k, budget, target_rse, seed, ctypes.byref(rid)))
+    return rid.value
+
+
+def moss_server_wait(s: int, request_id: int, timeout_s: float = 600.0):
+    r = moss_result()
+    st = moss_request_stats()
+    _check(load().moss_server_wait(s, request_id, timeout_s, ctypes.byref(r), ctypes.byref(st)))
+    return r, st
+
+
+def moss_server_stats(s: int) -> moss_server_info:
+    i = moss_server_info()
+    _check(load().moss_server_stats(s, ctypes.byref(i)))
+    return i
+
+
+def moss_server_free(s: int):
+    if s:
+        load().moss_server_free(s)
+
+
+def moss_budget_for_target(k: int, K, hits, target: float, min_budget: int, max_budget: int) -> int:
+    Ka = np.ascontiguousarray(K, dtype=np.uint64)
+    Ha = np.ascontiguousarray(hits, dtype=np.uint64).reshape(2 * NSLOTS)
+    return int(load().moss_budget_for_target(k, _ptr(Ka), _ptr(Ha), target, min_budget, max_budget))
+
+
+class Server:
+    """Owning wrapper of a request server (see moss_server_* in include/moss.h)."""
+
+    def __init__(self, device: int = 0, **config):
+        cfg = moss_server_default_config()
+        for key, val in config.items():
+            setattr(cfg, key, val)
+        self.handle = moss_server_create(device, cfg)
+
+    def add_graph(self, graph: "Graph") -> int:
+        return moss_server_add_graph(self.handle, graph.handle)
+
+    def submit(self, graph_id: int, k: int, budget: int = 0, target_rse: float = 0.0, seed: int = 1) -> int:
+        return moss_server_submit(self.handle, graph_id, k, budget, target_rse, seed)
+
+    def wait(self, request_id: int, timeout_s: float = 600.0):
+        r, st = moss_server_wait(self.handle, request_id, timeout_s)
+        return result_dict(r), {"budget": st.budget, "latency_s": st.latency_s, "queue_s": st.queue_s,
+                                "ticks": st.ticks}
+
+    def stats(self) -> dict:
+        i = moss_server_stats(self.handle)
+        return {f: getattr(i, f) for f, _ in moss_server_info._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            moss_server_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 # ------------------------------------------------------------ convenience --

@@ -291,6 +291,7 @@ const char *moss_strerror(int status) {
         case MOSS_EGRAPH: return "invalid graph";
         case MOSS_EOVERFLOW: return "value out of range";
         case MOSS_ESTATE: return "tables not built";
+        case MOSS_EBUSY: return "not finished";
         default: return "unknown status";
     }
 }

@@ -1,0 +1,86 @@
+"""The maximum-size workload: Chung-Lu n=4M, exponent 2.1, mean degree 17,
+max degree 20,000 (~35M edges, ~1.4 GB of device tables), 1e9 samples per
+motif size.  Tables are compared with the oracle's bit for bit, samples one
+by one at the end of the 1e9 range, and the full-budget counts by their
+invariants and by the finalize of the same counts."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1509_08089_gb300 as moss
+from oracle.finalize import PHI5
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def big():
+    rp, col = synth.workload("cl_n4m")
+    og = oracle.OracleGraph(rp, col)
+    g = moss.Graph(rp, col)
+    yield rp, col, og, g
+    g.close()
+
+
+def test_large_tables_bit_exact(big):
+    rp, col, og, g = big
+    n, nnz = og.n, og.nnz
+    deg, S, Q, gam = og.vertex()
+    vert = moss.moss_table_export(g.handle, moss.TABLE_VERT, np.zeros((n, 4), dtype=np.uint32))
+    assert np.array_equal(vert[:, 1], deg.astype(np.uint32))
+    assert np.array_equal(vert[:, 2], S.astype(np.uint32))
+    thr, alias, acc = og.sigma_table()
+    slot = moss.moss_table_export(g.handle, moss.TABLE_SLOT, np.zeros((nnz, 4), dtype=np.uint32))
+    assert np.array_equal(slot[:, 1], thr.astype(np.uint32))
+    assert np.array_equal(slot[:, 2], alias)
+    owner = np.repeat(np.arange(n, dtype=np.int64), deg.astype(np.int64))
+    assert np.array_equal(col[rp.astype(np.int64)[col.astype(np.int64)] + slot[:, 3].astype(np.int64)], owner)
+    for l in range(3):
+        _, T, salias = og.seed_table(l)
+        seed = moss.moss_table_export(g.handle, moss.TABLE_SEED0 + l, np.zeros((n, 4), dtype=np.uint32))
+        Tg = seed[:, 0].astype(np.uint64) | (seed[:, 1].astype(np.uint64) << np.uint64(32))
+        assert np.array_equal(Tg, T), l
+        assert np.array_equal(seed[:, 2], salias), l
+    st = g.stats()
+    for l in range(3):
+        assert (int(st.gamma[l][0]) | (int(st.gamma[l][1]) << 64)) == og.Gamma[l]
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_large_full_budget(big, k):
+    rp, col, og, g = big
+    B = 1_000_000_000
+    r = g.estimate(k, B, seed=42)
+    if k == 4:
+        assert tuple(r["K"]) == (B, 0) and int(r["hits"][0].sum()) == B
+        o = oracle.finalize_moss4(r["hits"][0], B, og.Gamma[0], og.Lambda3)
+        methods = [(0, B)]
+    else:
+        K1, K2 = B // 2, B - B // 2
+        assert tuple(r["K"]) == (K1, K2)
+        assert int(r["hits"][0].sum()) == K1 and int(r["hits"][1].sum()) == K2
+        for i in range(1, 22):
+            if PHI5[i - 1, 0] == 0:
+                assert r["hits"][0][i] == 0
+            if PHI5[i - 1, 1] == 0:
+                assert r["hits"][1][i] == 0
+        o = oracle.finalize_moss5(r["hits"][0], r["hits"][1], K1, K2, og.Gamma[1], og.Gamma[2], og.Lambda4)
+        methods = [(1, K1), (2, K2)]
+    n = 7 if k == 4 else 22
+    lam = float(og.Lambda3 if k == 4 else og.Lambda4)
+    for i in range(1, n):
+        tol = 1e-9 * (max(lam, 1.0) if i == 2 else max(abs(o["est"][i]), 1e-300))
+        assert abs(r["est"][i] - o["est"][i]) <= tol, (k, i)
+    for method, K in methods:
+        cls = torch.empty(4000, dtype=torch.uint8, device="cuda")
+        verts = torch.empty(4000 * 5, dtype=torch.int32, device="cuda")
+        moss.moss_sample_records(g.handle, method, K - 4000, 4000, 42, cls, verts)
+        torch.cuda.synchronize()
+        _, ocls, overts = og.run(method, 42, 4000, first=K - 4000, record=True)
+        assert np.array_equal(cls.cpu().numpy(), ocls)
+        ncol = 4 if method == 0 else 5
+        assert np.array_equal(verts.cpu().numpy().view(np.uint32).reshape(4000, 5)[:, :ncol], overts[:, :ncol])

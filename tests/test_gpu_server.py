@@ -1,0 +1,97 @@
+"""The continuous-batching server: results are the same alone and in the mix.
+
+Requests from several submitting threads (fixed budgets and target errors,
+k = 4 and 5, several graphs) are served concurrently; each result must equal
+moss_sample_estimate on the same graph with the request's final budget and
+seed -- counts bit for bit, estimates exactly (same device finalize)."""
+from __future__ import annotations
+
+import threading
+
+import numpy as np
+import pytest
+
+import synth
+import paper_1509_08089_gb300 as moss
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pool():
+    csrs = [synth.chung_lu(n, g, d, 60.0, seed=s)
+            for n, g, d, s in ((800, 2.3, 6.0, 1), (3000, 2.6, 8.0, 2), (6000, 2.2, 10.0, 3))]
+    csrs.append(synth.rgg(4000, 14.0, seed=4))
+    graphs = [moss.Graph(rp, col) for rp, col in csrs]
+    yield graphs
+    for g in graphs:
+        g.close()
+
+
+def submit_all(server, gids, plan, out, lock):
+    for gi, k, budget, eps, seed in plan:
+        rid = server.submit(gids[gi], k, budget=budget, target_rse=eps, seed=seed)
+        with lock:
+            out.append((rid, gi, k, seed))
+
+
+@pytest.mark.parametrize("cfg", [dict(max_active=64, tick_samples=2_000_000, tile_samples=1024),
+                                 dict(max_active=3, tick_samples=200_000, tile_samples=4096)])
+def test_server_results_equal_solo_runs(pool, cfg):
+    rng = np.random.default_rng(9)
+    plans = []
+    for t in range(4):
+        plan = []
+        for _ in range(10):
+            gi = int(rng.integers(0, len(pool)))
+            k = int(rng.choice([4, 5]))
+            if rng.random() < 0.5:
+                plan.append((gi, k, int(rng.integers(1_000, 500_000)), 0.0, int(rng.integers(1, 2**62))))
+            else:
+                plan.append((gi, k, 0, float(rng.uniform(0.02, 0.05)), int(rng.integers(1, 2**62))))
+        plans.append(plan)
+    subs, lock = [], threading.Lock()
+    with moss.Server(min_budget=10_000, max_budget=2_000_000, pilot_samples=20_000, **cfg) as server:
+        gids = [server.add_graph(g) for g in pool]
+        threads = [threading.Thread(target=submit_all, args=(server, gids, p, subs, lock)) for p in plans]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        results = [(server.wait(rid, 300.0), gi, k, seed) for rid, gi, k, seed in subs]
+        stats = server.stats()
+    assert stats["completed"] == len(subs)
+    for (r, st), gi, k, seed in results:
+        solo = pool[gi].estimate(k, st["budget"], seed)
+        assert tuple(r["K"]) == tuple(solo["K"])
+        assert np.array_equal(r["hits"], solo["hits"])
+        assert np.array_equal(r["est"], solo["est"])
+        assert np.array_equal(r["var"], solo["var"])
+        assert st["latency_s"] >= st["queue_s"] >= 0.0
+
+
+def test_target_budget_meets_target(pool):
+    with moss.Server(min_budget=1_000, max_budget=50_000_000, pilot_samples=50_000) as server:
+        gid = server.add_graph(pool[2])
+        rid = server.submit(gid, 4, target_rse=0.02, seed=3)
+        r, st = server.wait(rid)
+    # every class seen at least 10 times in the pilot now has relative SE <= ~2%
+    for i in (1, 3, 4, 5):
+        if r["hits"][0][i] >= 200 and r["est"][i] > 0:
+            assert np.sqrt(r["var"][i]) / r["est"][i] <= 0.025, i
+
+
+def test_server_rejects_bad_requests(pool):
+    with moss.Server() as server:
+        gid = server.add_graph(pool[0])
+        with pytest.raises(moss.MossError):
+            server.submit(gid, 3, budget=100)
+        with pytest.raises(moss.MossError):
+            server.submit(gid + 5, 4, budget=100)
+        with pytest.raises(moss.MossError):
+            server.submit(gid, 4)          # neither budget nor target
+        rid = server.submit(gid, 4, budget=10_000, seed=1)
+        server.wait(rid)
+        with pytest.raises(moss.MossError):
+            server.wait(rid)               # a request is waited for once
