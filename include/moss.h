@@ -89,6 +89,7 @@ typedef struct {
     double lambda[2][MOSS_NCLASS_SLOTS]; /* k=5: weight of T-5 / Path-5 in est */
     double triangles;           /* k=4: triangle count implied by the r = w collisions */
     double triangles_var;
+    double conc[MOSS_NCLASS_SLOTS];      /* concentration est[i] / sum_j est[j] (Sec. 6.3) */
 } moss_result;
 
 /* Load an undirected graph given as CSR and run the initialization pass
@@ -247,6 +248,16 @@ void moss_server_free(moss_server *s);
 /* The budget rule above, from pilot counts K[2], hits[2][22] (host only). */
 uint64_t moss_budget_for_target(int k, const uint64_t *K, const uint64_t *hits, double target,
                                 uint64_t min_budget, uint64_t max_budget);
+
+/* The covariance matrix of the estimates of moss_finalize's inputs: cov_host
+ * (22 x 22 doubles, row-major, host) receives Cov(est_i, est_j) for classes
+ * 1..n_classes -- -n_i n_j / K between sampled MOSS-4 classes (proof of
+ * Theorem 3), Theorem 10's covariances for MOSS-5 -- with the plug-in values
+ * of the variances, the variances on the diagonal, and the row of class 2
+ * (n_2, eta_2) from its identity (eq. 2, Sec. 5.1.3).  out (nullable)
+ * receives the result as moss_finalize would.  Synchronous on stream. */
+int moss_covariance(moss_graph *g, int k, const uint64_t *K, const uint64_t *hits, void *stream, double *cov_host,
+                    moss_result *out);
 
 /* Exact totals (requires moss_build_tables for the gamma entries). */
 int moss_graph_stats(const moss_graph *g, moss_stats *out);

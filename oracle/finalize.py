@@ -56,8 +56,33 @@ def finalize_moss4(m, K: int, Gamma: int, Lambda3: int, eta=None) -> dict:
         tri = m[0] * G / (6.0 * K)
         tri_var = tri / K * (G / 6.0 - tri)
     est[2] = float(Lambda3) - est[4] - 2.0 * est[5] - 4.0 * est[6]   # eq. (2)
+    # covariance matrix: Cov(n_i, n_j) = -n_i n_j / K for sampled i != j
+    # (proof of Theorem 3); n_2 = Lambda_3 - n_4 - 2 n_5 - 4 n_6 is linear in them
+    cov = np.zeros((22, 22))
+    if K > 0 and G > 0:
+        plug = est if eta is None else np.asarray(eta, dtype=np.float64)
+        for i in sampled:
+            for j in sampled:
+                cov[i, j] = var[i] if i == j else -plug[i] * plug[j] / K
+        c = {4: 1.0, 5: 2.0, 6: 4.0}
+        for j in range(1, 7):
+            if j != 2:
+                cov[2, j] = cov[j, 2] = -sum(c[i] * cov[i, j] for i in (4, 5, 6))
+        cov[2, 2] = var[2]
     return {"k": 4, "K": (K, 0), "est": est, "var": var, "p": p,
-            "triangles": tri, "triangles_var": tri_var}
+            "triangles": tri, "triangles_var": tri_var, "cov": cov, "conc": concentrations(est, 6)}
+
+
+def concentrations(est, n_classes: int) -> np.ndarray:
+    """omega_i = eta_i / sum_j eta_j over the classes (Sec. 6.3)."""
+    out = np.zeros(22)
+    tot = 0.0
+    for i in range(1, n_classes + 1):
+        tot += est[i]
+    if tot != 0.0:
+        for i in range(1, n_classes + 1):
+            out[i] = est[i] / tot
+    return out
 
 
 def finalize_moss5(m1, m2, K1: int, K2: int, Gamma1: int, Gamma2: int, Lambda4: int, eta=None) -> dict:
@@ -133,5 +158,12 @@ def finalize_moss5(m1, m2, K1: int, K2: int, Gamma1: int, Gamma2: int, Lambda4: 
     var[2] = v2
     for i in range(22):
         cov[i, i] = var[i]
+    # eta_2 is linear in the others: Cov(eta_2, eta_j) = -sum phi^(3)_i Cov(eta_i, eta_j)
+    for j in range(1, 22):
+        if j != 2:
+            c2 = 0.0
+            for i in omega3:
+                c2 -= PHI5[i - 1, 2] * cov[i, j]
+            cov[2, j] = cov[j, 2] = c2
     return {"k": 5, "K": (K1, K2), "est": est, "var": var, "lam": lam, "eta1": eh[0], "eta2": eh[1],
-            "p": p, "cov": cov}
+            "p": p, "cov": cov, "conc": concentrations(est, 21)}

@@ -41,7 +41,8 @@ class moss_result(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("n_classes", ctypes.c_int), ("K", ctypes.c_uint64 * 2),
                 ("hits", (ctypes.c_uint64 * NSLOTS) * 2), ("est", ctypes.c_double * NSLOTS),
                 ("var", ctypes.c_double * NSLOTS), ("lambda_", (ctypes.c_double * NSLOTS) * 2),
-                ("triangles", ctypes.c_double), ("triangles_var", ctypes.c_double)]
+                ("triangles", ctypes.c_double), ("triangles_var", ctypes.c_double),
+                ("conc", ctypes.c_double * NSLOTS)]
 
 
 class moss_server_config(ctypes.Structure):
@@ -91,6 +92,7 @@ def load():
         "moss_sample_counts_noalloc": ([_vp, ctypes.c_int, _u64, _u64, _u64, _vp, _vp], ctypes.c_int),
         "moss_finalize": ([_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
         "moss_graph_stats": ([_vp, ctypes.POINTER(moss_stats)], ctypes.c_int),
+        "moss_covariance": ([_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
         "moss_table_export": ([_vp, ctypes.c_int, _vp, _u64], ctypes.c_int),
         "moss_graph_free": ([_vp], None),
         "moss_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -223,6 +225,16 @@ def moss_finalize(g: int, k: int, K, hits, stream=None) -> moss_result:
     r = moss_result()
     _check(load().moss_finalize(g, k, _ptr(Ka), _ptr(Ha), _stream(stream), ctypes.byref(r)))
     return r
+
+
+def moss_covariance(g: int, k: int, K, hits, stream=None):
+    """(22 x 22 covariance matrix, result) of the estimates of these counts."""
+    Ka = np.ascontiguousarray(K, dtype=np.uint64)
+    Ha = np.ascontiguousarray(hits, dtype=np.uint64).reshape(2 * NSLOTS)
+    cov = np.zeros((NSLOTS, NSLOTS), dtype=np.float64)
+    r = moss_result()
+    _check(load().moss_covariance(g, k, _ptr(Ka), _ptr(Ha), _stream(stream), _ptr(cov), ctypes.byref(r)))
+    return cov, result_dict(r)
 
 
 def moss_graph_stats(g: int) -> moss_stats:
@@ -384,7 +396,7 @@ def result_dict(r: moss_result) -> dict:
             "hits": np.array([[int(x) for x in r.hits[l]] for l in range(2)], dtype=np.uint64),
             "est": np.array(list(r.est)), "var": np.array(list(r.var)),
             "lam": np.array([list(r.lambda_[l]) for l in range(2)]),
-            "triangles": r.triangles, "triangles_var": r.triangles_var}
+            "triangles": r.triangles, "triangles_var": r.triangles_var, "conc": np.array(list(r.conc))}
 
 
 class Batch:

@@ -171,6 +171,7 @@ struct moss_graph {
     int partial_rows = 0;
     uint64_t *counts = nullptr;  // 2 x 22
     moss_result *res_dev = nullptr;
+    double *cov_dev = nullptr;   // 22 x 22 covariance matrix
     uint32_t *flags = nullptr;   // device status: [0] error bits, [1] matched twins
     void *arena = nullptr;       // every device array above lives in this one allocation
     int probe = MOSS_PROBE_HASH; // membership tests: hashed edge set or list search
@@ -358,6 +359,7 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
             g->partials = c.take<uint64_t>((uint64_t)prow * kSlots + (uint64_t)blocks * 6 * 2);
             g->counts = c.take<uint64_t>(2 * kSlots);
             g->res_dev = c.take<moss_result>(1);
+            g->cov_dev = c.take<double>(kSlots * kSlots);
             g->flags = c.take<uint32_t>(2);
             rp_dev = c.take<uint8_t>(rp_bytes);
         }
@@ -543,6 +545,27 @@ int moss_finalize(moss_graph *g, int k, const uint64_t *K, const uint64_t *hits,
     MOSS_CUDA(cudaMemcpyAsync(g->counts, hits, 2 * kSlots * sizeof(uint64_t), cudaMemcpyDefault, s), "copying counts");
     uint64_t KK[2] = {K[0], k == 4 ? 0 : K[1]};
     return finalize_from_device(g, k, KK, s, out);
+}
+
+int moss_covariance(moss_graph *g, int k, const uint64_t *K, const uint64_t *hits, void *stream, double *cov_host,
+                    moss_result *out) {
+    if (!g || !K || !hits || !cov_host) return fail(MOSS_EINVAL, "NULL argument");
+    if (k != 4 && k != 5) return fail(MOSS_EINVAL, "k must be 4 or 5 (got %d)", k);
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MOSS_CUDA(cudaMemcpyAsync(g->counts, hits, 2 * kSlots * sizeof(uint64_t), cudaMemcpyDefault, s), "copying counts");
+    FinalizeIn in;
+    in.k = k;
+    in.K[0] = K[0];
+    in.K[1] = k == 4 ? 0 : K[1];
+    MOSS_CUDA(launch_covariance(in, g->counts, g->tot, g->res_dev, g->cov_dev, s), "covariance kernel");
+    MOSS_CUDA(cudaMemcpyAsync(cov_host, g->cov_dev, kSlots * kSlots * sizeof(double), cudaMemcpyDeviceToHost, s),
+              "reading covariance");
+    MOSS_CUDA(cudaMemcpyAsync(&g->res_host, g->res_dev, sizeof(moss_result), cudaMemcpyDeviceToHost, s),
+              "reading result");
+    MOSS_CUDA(cudaStreamSynchronize(s), "synchronising stream");
+    if (out) memcpy(out, &g->res_host, sizeof(moss_result));
+    return MOSS_OK;
 }
 
 int moss_graph_stats(const moss_graph *g, moss_stats *out) {

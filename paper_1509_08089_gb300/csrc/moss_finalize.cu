@@ -31,9 +31,19 @@ __device__ __forceinline__ double u128_to_double(u128 x) {
     return (double)(uint64_t)(x >> 64) * 18446744073709551616.0 + (double)(uint64_t)x;
 }
 
-// hits0/hits1: counts of the first and second sub-method (hits1 may be null)
+// omega_i = eta_i / sum_j eta_j over the classes (Sec. 6.3)
+__device__ void concentrations(moss_result &r) {
+    double t = 0.0;
+    for (int i = 1; i <= r.n_classes; ++i) t += r.est[i];
+    for (int i = 0; i < kSlots; ++i) r.conc[i] = 0.0;
+    if (t != 0.0)
+        for (int i = 1; i <= r.n_classes; ++i) r.conc[i] = r.est[i] / t;
+}
+
+// hits0/hits1: counts of the first and second sub-method (hits1 may be null);
+// cov (nullable, 22 x 22 row-major) receives the covariance matrix
 __device__ void finalize_one(const FinalizeIn &in, const uint64_t *hits0, const uint64_t *hits1,
-                             const DevTotals *tot, moss_result *out) {
+                             const DevTotals *tot, moss_result *out, double *cov = nullptr) {
     moss_result r;
     memset(&r, 0, sizeof(r));
     r.k = in.k;
@@ -64,6 +74,26 @@ __device__ void finalize_one(const FinalizeIn &in, const uint64_t *hits0, const 
             r.triangles_var = r.triangles / K * (G / 6.0 - r.triangles);
         }
         r.est[2] = u128_to_double(tot->lambda3) - r.est[4] - 2.0 * r.est[5] - 4.0 * r.est[6];
+        concentrations(r);
+        if (cov) {
+            // Cov(n_i, n_j) = -n_i n_j / K (proof of Theorem 3); n_2 is linear in n_4, n_5, n_6
+            for (int i = 0; i < kSlots * kSlots; ++i) cov[i] = 0.0;
+            if (in.K[0] > 0 && G > 0) {
+                const int sm[5] = {1, 3, 4, 5, 6};
+                for (int a = 0; a < 5; ++a)
+                    for (int b = 0; b < 5; ++b) {
+                        const int i = sm[a], j = sm[b];
+                        cov[i * kSlots + j] = i == j ? r.var[i] : -r.est[i] * r.est[j] / K;
+                    }
+                for (int j = 1; j <= 6; ++j) {
+                    if (j == 2) continue;
+                    const double c = -(cov[4 * kSlots + j] + 2.0 * cov[5 * kSlots + j] + 4.0 * cov[6 * kSlots + j]);
+                    cov[2 * kSlots + j] = c;
+                    cov[j * kSlots + 2] = c;
+                }
+                cov[2 * kSlots + 2] = r.var[2];
+            }
+        }
         *out = r;
         return;
     }
@@ -135,7 +165,42 @@ __device__ void finalize_one(const FinalizeIn &in, const uint64_t *hits0, const 
         v2 -= (sb * sb - sbb) / K[l];
     }
     r.var[2] = v2;
+    concentrations(r);
+    if (cov) {
+        // Cov(eta_i, eta_j) = -plug_i plug_j sum_l a_i a_j / K_l (Theorem 10);
+        // eta_2 = Lambda_4 - sum phi^(3)_i eta_i is linear in the others
+        for (int i = 0; i < kSlots * kSlots; ++i) cov[i] = 0.0;
+        for (int i = 1; i <= 21; ++i) {
+            if (i == 2) continue;
+            for (int j = 1; j <= 21; ++j) {
+                if (j == 2) continue;
+                double c = 0.0;
+                if (i == j) {
+                    c = r.var[i];
+                } else {
+                    for (int l = 0; l < 2; ++l)
+                        if (avail[l]) c -= (a[l][i] * plug[i]) * (a[l][j] * plug[j]) / K[l];
+                }
+                cov[i * kSlots + j] = c;
+            }
+        }
+        for (int j = 1; j <= 21; ++j) {
+            if (j == 2) continue;
+            double c2 = 0.0;
+            for (int i = 1; i <= 21; ++i)
+                if (i != 2 && kPhi5[i - 1][2] > 0) c2 -= kPhi5[i - 1][2] * cov[i * kSlots + j];
+            cov[2 * kSlots + j] = c2;
+            cov[j * kSlots + 2] = c2;
+        }
+        cov[2 * kSlots + 2] = r.var[2];
+    }
     *out = r;
+}
+
+__global__ void k_covariance(FinalizeIn in, const uint64_t *hits, const DevTotals *tot, moss_result *out,
+                             double *cov) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    finalize_one(in, hits, hits + kSlots, tot, out, cov);
 }
 
 __global__ void k_finalize(FinalizeIn in, const uint64_t *hits, const DevTotals *tot, moss_result *out) {
@@ -159,6 +224,12 @@ __global__ void k_finalize_batch(const BatchRequest *reqs, int nreq, const uint6
 cudaError_t launch_finalize(const FinalizeIn &in, const uint64_t *hits_dev, const DevTotals *tot, void *result_dev,
                             cudaStream_t s) {
     k_finalize<<<1, 32, 0, s>>>(in, hits_dev, tot, static_cast<moss_result *>(result_dev));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_covariance(const FinalizeIn &in, const uint64_t *hits_dev, const DevTotals *tot, void *result_dev,
+                              double *cov_dev, cudaStream_t s) {
+    k_covariance<<<1, 32, 0, s>>>(in, hits_dev, tot, static_cast<moss_result *>(result_dev), cov_dev);
     return cudaGetLastError();
 }
 

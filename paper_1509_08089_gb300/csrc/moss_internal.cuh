@@ -146,6 +146,8 @@ struct FinalizeIn {
 };
 cudaError_t launch_finalize(const FinalizeIn &in, const uint64_t *hits_dev, const DevTotals *tot,
                             void *result_dev, cudaStream_t s);
+cudaError_t launch_covariance(const FinalizeIn &in, const uint64_t *hits_dev, const DevTotals *tot,
+                              void *result_dev, double *cov_dev, cudaStream_t s);
 
 // ---------------------------------------------------------------- batches --
 // One task = one sub-method of one request: sample ids [first, first+count)

@@ -155,12 +155,33 @@ def close_estimates(r, o, og, k):
             continue
         assert abs(r["est"][i] - o["est"][i]) <= 1e-9 * max(abs(o["est"][i]), 1e-300), (k, i, r["est"][i], o["est"][i])
         assert abs(r["var"][i] - o["var"][i]) <= 1e-9 * max(abs(o["var"][i]), 1e-300), (k, i)
+    for i in range(1, n):
+        assert abs(r["conc"][i] - o["conc"][i]) <= 1e-9 * max(abs(o["conc"][i]), 1e-300) + 1e-12, (k, i)
     if k == 4:
         assert abs(r["triangles"] - o["triangles"]) <= 1e-9 * max(abs(o["triangles"]), 1e-300)
     else:
         for i in range(1, n):
             for l in range(2):
                 assert abs(r["lam"][l][i] - o["lam"][l][i]) <= 1e-9
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_covariance_entry_matches_oracle(k):
+    rp, col, og, g = pair("cl_n2k")
+    hits = np.zeros((2, 22), dtype=np.uint64)
+    if k == 4:
+        hits[0] = og.run(oracle.MOSS4, 3, 80_000)
+        K = [80_000, 0]
+        o = oracle.finalize_moss4(hits[0], 80_000, og.Gamma[0], og.Lambda3)
+    else:
+        hits[0] = og.run(oracle.T5, 3, 50_000)
+        hits[1] = og.run(oracle.PATH5, 3, 70_000)
+        K = [50_000, 70_000]
+        o = oracle.finalize_moss5(hits[0], hits[1], 50_000, 70_000, og.Gamma[1], og.Gamma[2], og.Lambda4)
+    cov, r = moss.moss_covariance(g.handle, k, K, hits)
+    close_estimates(r, o, og, k)
+    scale = np.abs(o["cov"]).max()
+    assert np.allclose(cov, o["cov"], rtol=1e-9, atol=1e-9 * scale)
 
 
 def test_shards_add_up():

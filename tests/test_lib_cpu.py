@@ -73,5 +73,5 @@ def test_fails_loudly_without_gpu():
 
 def test_result_struct_layout_matches_header():
     # doubles after uint64 arrays: no padding surprises between C and ctypes
-    assert ctypes.sizeof(moss.moss_result) == 4 + 4 + 16 + 2 * 22 * 8 + 22 * 8 * 2 + 2 * 22 * 8 + 16
+    assert ctypes.sizeof(moss.moss_result) == 4 + 4 + 16 + 2 * 22 * 8 + 22 * 8 * 2 + 2 * 22 * 8 + 16 + 22 * 8
     assert ctypes.sizeof(moss.moss_stats) == 8 + 8 + 8 + 48 + 16 + 16 + 24 + 16

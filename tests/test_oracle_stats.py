@@ -139,3 +139,40 @@ def test_sampled_classes_stay_in_omega(g200):
             assert m2[i] == 0
     m0 = g200.run(oracle.MOSS4, 3, 50_000)
     assert m0[2] == 0
+
+
+def test_covariance_matrix_is_consistent(g200):
+    """The class-2 entries of the covariance matrix follow from the identities:
+    Var(n_2) of Theorem 3 equals Var(n_4 + 2 n_5 + 4 n_6) built from the
+    pairwise covariances, and for k = 5 Var(eta_2) equals the quadratic form
+    of the phi^(3) weights; the matrix is symmetric positive semi-definite on
+    the sampled classes; concentrations sum to 1."""
+    r4 = g200.estimate(4, 200_000, seed=3)
+    c = np.zeros(22)
+    c[4], c[5], c[6] = 1.0, 2.0, 4.0
+    assert abs(c @ r4["cov"] @ c - r4["var"][2]) <= 1e-9 * abs(r4["var"][2])
+    assert np.allclose(r4["cov"], r4["cov"].T)
+    assert abs(r4["conc"][1:7].sum() - 1.0) < 1e-12
+    r5 = g200.estimate(5, 200_000, seed=3)
+    phi = np.zeros(22)
+    for i in range(1, 22):
+        if i != 2:
+            phi[i] = PHI5[i - 1, 2]
+    assert abs(phi @ r5["cov"] @ phi - r5["var"][2]) <= 1e-9 * abs(r5["var"][2])
+    sub = [i for i in range(1, 22) if i != 2]
+    ev = np.linalg.eigvalsh(r5["cov"][np.ix_(sub, sub)])
+    assert ev.min() > -1e-9 * ev.max()
+    assert abs(r5["conc"][1:22].sum() - 1.0) < 1e-12
+
+
+def test_covariance_matches_sampling(g200):
+    """Off-diagonal covariances of the MOSS-4 estimates against the sample
+    covariance over 1,000 seeds at the exact counts (proof of Theorem 3)."""
+    eta = np.array(GOLD["cl_n200"]["esu4"], dtype=np.float64)
+    R, K = 1000, 2000
+    est = np.array([g200.estimate(4, K, seed=s)["est"] for s in range(R)])
+    ref = g200.estimate(4, K, seed=0, eta=eta)["cov"]
+    for i, j in ((1, 3), (1, 4), (3, 4), (1, 2), (2, 4)):
+        emp = np.cov(est[:, i], est[:, j])[0, 1]
+        se = math.sqrt((ref[i, i] * ref[j, j] + ref[i, j] ** 2) / R)
+        assert abs(emp - ref[i, j]) < Z * se, (i, j, emp, ref[i, j])
