@@ -227,15 +227,15 @@ __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lu
 }
 
 // Path-5 fallback: u from tau^(v) by a scan, w from mu^(v,u) by a search
-__device__ __noinline__ void path5_fallback(const DevGraph &g, uint32_t v, uint4 vr, uint64_t x12, uint64_t x13,
-                                            uint32_t &iu, uint32_t &iw) {
+__device__ __noinline__ void path5_fallback(const uint32_t *acc, const uint64_t *q, uint32_t v, uint4 vr, uint64_t x12,
+                                            uint64_t x13, uint32_t &iu, uint32_t &iw) {
     const uint32_t o = vr.x, d = vr.y, S = vr.z;
-    const uint64_t G = (uint64_t)S * S - g.q[v];
+    const uint64_t G = (uint64_t)S * S - q[v];
     const uint64_t y = word_index(x12, G);
     uint64_t run = 0;
     iu = 0;
     for (uint32_t i = 0; i < d; ++i) {
-        const uint32_t wi = (i + 1 < d ? ld1(g.acc + o + i + 1) : S) - ld1(g.acc + o + i);
+        const uint32_t wi = (i + 1 < d ? ld1(acc + o + i + 1) : S) - ld1(acc + o + i);
         const uint64_t tw = (uint64_t)wi * (S - wi);
         if (y < run + tw) {
             iu = i;
@@ -243,15 +243,15 @@ __device__ __noinline__ void path5_fallback(const DevGraph &g, uint32_t v, uint4
         }
         run += tw;
     }
-    const uint32_t au = ld1(g.acc + o + iu);
-    const uint32_t wu = (iu + 1 < d ? ld1(g.acc + o + iu + 1) : S) - au;
+    const uint32_t au = ld1(acc + o + iu);
+    const uint32_t wu = (iu + 1 < d ? ld1(acc + o + iu + 1) : S) - au;
     uint64_t y2 = word_index(x13, (uint64_t)(S - wu));
     if (y2 >= au) y2 += wu;
     // last i with ACC[i] <= y2
     uint32_t lo = 0, len = d;
     while (len > 0) {
         const uint32_t half = len >> 1;
-        if ((uint64_t)ld1(g.acc + o + lo + half) <= y2) { lo += half + 1; len -= half + 1; } else { len = half; }
+        if ((uint64_t)ld1(acc + o + lo + half) <= y2) { lo += half + 1; len -= half + 1; } else { len = half; }
     }
     iw = lo - 1;
 }
@@ -272,7 +272,7 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
         if (pu.pos == pw.pos) {
             const Words4 d4 = philox4x64(s, 3, 2, 0, seed, 0);
             uint32_t iu, iw;
-            path5_fallback(g, v, vr, d4.x[0], d4.x[1], iu, iw);
+            path5_fallback(g.acc, g.q, v, vr, d4.x[0], d4.x[1], iu, iw);
             const uint4 su = ld4(g.slot + vr.x + iu), sw = ld4(g.slot + vr.x + iw);
             pu = Pick{iu, su.x, su.w};
             pw = Pick{iw, sw.x, sw.w};
