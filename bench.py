@@ -388,12 +388,12 @@ def run_gpu(args):
                 "d2h_bytes_per_step": d2h},
         "roofline": roof,
         "clocks": clk,
-        "gpu_launches": (13 if k == 5 else 11) * args.steps,
+        # load 4 (vertices, slots, twins, totals) + build 6 (sigma alias, 4 vertex-table
+        # phases, edge hash) + per sub-method sampler and reduce + finalize
+        "gpu_launches": (4 + 6 + 2 * len(sub_budgets(k, args.budget)) + 1) * args.steps,
         "wall_s_timed": t_wall,
         "step_ms": step_ms,
     }
-    if world > 1:
-        out["gpu_launches"] = (8 + 2 * len(sub_budgets(k, args.budget)) + 1) * args.steps
     if pool is not None:
         per_worker = calibrate_per_worker(args.workload, k, args.seed, 12.0)
         b, sw, n, wall = oracle_pass(pool, cores, args.workload, k, args.seed, per_worker)
