@@ -8,10 +8,14 @@ Contents
 * ``moss_oracle.c`` (compiled with gcc on first use): exact integer vertex
   weights and totals (Table 1), alias tables for WeightRandomVertex
   (Sec. 4.1.3), the Philox4x64-10 word schedule, the per-sample steps of
-  Algorithm 1 (MOSS-4), Algorithm 3 (T-5) and Algorithm 4 (Path-5), the
-  motif classifier (Sec. 4.1.2, Table 2) and ESU exact enumeration.
+  Algorithm 1 (MOSS-4), Algorithm 2 (MOSS-4Min, Sec. 4.2: the total order,
+  N_{u,v}, the weights Gamma-check_v and sigma-check, and c(s), the number
+  of 3-paths of a CIS that the method can draw), Algorithm 3 (T-5) and
+  Algorithm 4 (Path-5), the motif classifier (Sec. 4.1.2, Table 2) and ESU
+  exact enumeration.
 * :mod:`oracle.finalize` (numpy, FP64): the estimators and variances of
-  Theorems 3, 7, 9 and 10 and the mix estimator of Sec. 5.1.3.
+  Theorems 3, 5, 7, 9 and 10 and the mix estimator (Theorem 1) of MOSS-4
+  with MOSS-4Min and of T-5 with Path-5 (Sec. 5.1.3).
 """
 from __future__ import annotations
 
@@ -21,14 +25,14 @@ import subprocess
 
 import numpy as np
 
-from .finalize import finalize_moss4, finalize_moss5, PHI4, PHI5  # noqa: F401
+from .finalize import finalize_moss4, finalize_moss4min, finalize_moss5, min_slot, PHI4, PHI5  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "moss_oracle.c")
 _LIB = os.path.join(_HERE, "libmoss_oracle.so")
 _lib = None
 
-MOSS4, T5, PATH5 = 0, 1, 2
+MOSS4, T5, PATH5, MOSS4MIN = 0, 1, 2, 3
 
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -68,6 +72,10 @@ def _load():
         lib.oracle_run.restype = ctypes.c_int
         lib.oracle_esu.argtypes = [ctypes.c_void_p, ctypes.c_int, _u64p]
         lib.oracle_esu.restype = ctypes.c_int
+        lib.oracle_build_min.argtypes = [ctypes.c_void_p]
+        lib.oracle_build_min.restype = ctypes.c_int
+        lib.oracle_min_total.argtypes = [ctypes.c_void_p, _u64p]
+        lib.oracle_min_tables.argtypes = [ctypes.c_void_p, _u32p, _u64p, _u64p, _u32p, _u64p, _u64p, _u32p]
         _lib = lib
     return _lib
 
@@ -162,8 +170,36 @@ class OracleGraph:
         _load().oracle_sigma_table(self._ctx, _p(thr, _u64p), _p(alias, _u32p), _p(acc, _u64p))
         return thr[:self.nnz], alias[:self.nnz], acc[:self.nnz]
 
+    def build_min(self) -> int:
+        """Build the MOSS-4Min tables (Sec. 4.2); returns Gamma-check."""
+        if _load().oracle_build_min(self._ctx):
+            raise MemoryError("oracle_build_min")
+        t = np.zeros(2, dtype=np.uint64)
+        _load().oracle_min_total(self._ctx, _p(t, _u64p))
+        self.Gamma_min = _u128(t)
+        return self.Gamma_min
+
+    def min_tables(self):
+        """(ordered lists, d_{v,u} per slot, sigma-check thresholds and
+        aliases per slot, Gamma-check_v, vertex thresholds T, vertex aliases)."""
+        self.build_min()
+        m, n = max(self.nnz, 1), max(self.n, 1)
+        rl = np.zeros(m, dtype=np.uint32)
+        rk = np.zeros(m, dtype=np.uint64)
+        ct = np.zeros(m, dtype=np.uint64)
+        ca = np.zeros(m, dtype=np.uint32)
+        g = np.zeros(2 * n, dtype=np.uint64)
+        T = np.zeros(n, dtype=np.uint64)
+        al = np.zeros(n, dtype=np.uint32)
+        _load().oracle_min_tables(self._ctx, _p(rl, _u32p), _p(rk, _u64p), _p(ct, _u64p), _p(ca, _u32p),
+                                  _p(g, _u64p), _p(T, _u64p), _p(al, _u32p))
+        gam = [_u128(g[2 * v:2 * v + 2]) for v in range(self.n)]
+        return (rl[:self.nnz], rk[:self.nnz], ct[:self.nnz], ca[:self.nnz], gam, T[:self.n], al[:self.n])
+
     # -- sampling -----------------------------------------------------------
     def sample_words(self, method: int, words) -> tuple[list[int], int]:
+        if method == MOSS4MIN:
+            self.build_min()
         x = np.zeros(16, dtype=np.uint64)
         for i, w in enumerate(words):
             x[i] = int(w)
@@ -176,7 +212,11 @@ class OracleGraph:
 
     def run(self, method: int, seed: int, count: int, first: int = 0, record: bool = False):
         """Counts (uint64[22]; [0] = collisions) of samples first..first+count-1.
-        With record=True also per-sample classes (uint8) and vertices (uint32[.,5])."""
+        With record=True also per-sample classes (uint8) and vertices (uint32[.,5]).
+        MOSS-4Min (method 3) counts by (class, c) slot (:func:`min_slot`) and
+        records c(s) as the fifth vertex entry."""
+        if method == MOSS4MIN:
+            self.build_min()
         counts = np.zeros(22, dtype=np.uint64)
         classes = np.zeros(max(count, 1), dtype=np.uint8) if record else None
         verts = np.zeros((max(count, 1), 5), dtype=np.uint32) if record else None
@@ -214,3 +254,13 @@ class OracleGraph:
         m1 = self.run(T5, seed, K1) if K1 else np.zeros(22, dtype=np.uint64)
         m2 = self.run(PATH5, seed, K2) if K2 else np.zeros(22, dtype=np.uint64)
         return finalize_moss5(m1, m2, K1, K2, self.Gamma[1], self.Gamma[2], self.Lambda4, **kw)
+
+    def estimate_min(self, budget: int, budget_min: int, seed: int, **kw):
+        """MOSS-4 with K = budget and MOSS-4Min with K-check = budget_min on
+        the same seed, mixed by Theorem 1 (Sec. 4.2)."""
+        Gm = self.build_min()
+        K = budget if self.Gamma[0] > 0 else 0
+        Km = budget_min if Gm > 0 else 0
+        m = self.run(MOSS4, seed, K) if K else np.zeros(22, dtype=np.uint64)
+        mm = self.run(MOSS4MIN, seed, Km) if Km else np.zeros(22, dtype=np.uint64)
+        return finalize_moss4min(m, mm, K, Km, self.Gamma[0], Gm, self.Lambda3, **kw)

@@ -8,6 +8,15 @@ Everything is written as the paper states it, in a fixed evaluation order:
   Also the triangle count implied by the collisions r = w: each triangle is
   produced by 6 ordered (v, u, w) draws of probability 1/Gamma each (the
   argument of the proof of Theorem 2), so T = m_0 Gamma / (6 K).
+* MOSS-4Min (Sec. 4.2, Algorithm 2, Theorem 5) with one correction: a CIS
+  s of class 3, 5 or 6 is drawn with probability 2 c(s) / Gamma-check, where
+  c(s) counts the 3-paths p0-p1-p2-p3 of s with p0 > p2 and p3 > p1 in the
+  total order (each drawn from both of its orientations).  c is 1 for every
+  4-cycle and 3 for every 4-clique, as Theorem 4 states, but 1, 2 or 3 for a
+  diamond, so counts are kept per (class, c) slot and each hit has the
+  Horvitz-Thompson weight Gamma-check / (2 c).  Theorem 5 becomes
+  Var = (sum_s 1/P(s) - n_i^2) / K-check; the mix with MOSS-4 follows
+  Theorem 1.
 * MOSS-5 (Sec. 5.1, Theorems 6-10): eta^(l)_i = m^(l)_i / (K_l p^(l)_i),
   p^(l)_i = 2 phi^(l)_i / Gamma^(l); the mix estimator (eq. mixestimator)
   with lambda from the two variances; eta_2 = Lambda_4 - sum phi^(3)_i eta_i
@@ -71,6 +80,126 @@ def finalize_moss4(m, K: int, Gamma: int, Lambda3: int, eta=None) -> dict:
         cov[2, 2] = var[2]
     return {"k": 4, "K": (K, 0), "est": est, "var": var, "p": p,
             "triangles": tri, "triangles_var": tri_var, "cov": cov, "conc": concentrations(est, 6)}
+
+
+def min_slot(cls: int, c: int) -> int:
+    """Count slot of a MOSS-4Min hit of class cls with c(s) = c: 4-cycles
+    use slots 0-3 (c = 1..4), diamonds 4-9 (c = 1..6), 4-cliques 10-21
+    (c = 1..12); -1 for anything not counted."""
+    if cls == 3 and 1 <= c <= 4:
+        return c - 1
+    if cls == 5 and 1 <= c <= 6:
+        return 4 + c - 1
+    if cls == 6 and 1 <= c <= 12:
+        return 10 + c - 1
+    return -1
+
+
+MIN_CLASSES = {3: (0, 4), 5: (4, 6), 6: (10, 12)}    # class -> (first slot, slots)
+# 1/c of every CIS of the class as Theorem 4 states it (4-cycles c = 1, diamonds
+# c = 1, 4-cliques c = 3): the plug-in mean of 1/c for a class MOSS-4Min did not hit
+THM4_INV_C = {3: 1.0, 5: 1.0, 6: 1.0 / 3.0}
+
+
+def finalize_moss4min(m, mm, K: int, Kmin: int, Gamma: int, Gamma_min: int, Lambda3: int, eta=None) -> dict:
+    """m: MOSS-4 counts[22]; mm: MOSS-4Min slot counts[22] (:func:`min_slot`).
+
+    MOSS-4Min estimate of class i in {3, 5, 6} (Algorithm 2 with the weight
+    Gamma-check / (2 c)): n-check_i = Gamma-check / (2 K-check) sum_c m_{i,c} / c.
+    Its variance (Theorem 5 with per-CIS probabilities) is
+    (S_i - n_i^2) / K-check with S_i = sum_s 1/P(s) = n_i Gamma-check h_i / 2,
+    h_i the mean of 1/c(s) over the class, estimated by
+    sum_c m_{i,c}/c^2 / sum_c m_{i,c}/c (THM4_INV_C when the class has no hit).
+    n_i in both variances is the plug-in e_i = (K n-hat_i + K-check n-check_i)
+    / (K + K-check) (or eta).  The two estimates of a class are mixed with
+    weights proportional to the inverse variances (Theorem 1); classes 1 and 4
+    come from MOSS-4 alone and n_2 from eq. (2)."""
+    m = np.asarray(m, dtype=np.float64)
+    mm = np.asarray(mm, dtype=np.float64)
+    G, Gm = float(Gamma), float(Gamma_min)
+    avail = (K > 0 and G > 0, Kmin > 0 and Gm > 0)
+    sampled = (1, 3, 4, 5, 6)
+    p = np.zeros(22)
+    e4 = np.zeros(22)                     # n-hat (MOSS-4)
+    em = np.zeros(22)                     # n-check (MOSS-4Min)
+    h = np.zeros(22)
+    if avail[0]:
+        for i in sampled:
+            p[i] = 2.0 * PHI4[i - 1, 0] / G                 # Theorem 2
+            e4[i] = m[i] / (K * p[i])
+    if avail[1]:
+        for i, (s0, ns) in MIN_CLASSES.items():
+            a = 0.0
+            b = 0.0
+            for c in range(1, ns + 1):
+                a += mm[s0 + c - 1] / c
+                b += mm[s0 + c - 1] / (c * c)
+            em[i] = Gm / (2.0 * Kmin) * a
+            h[i] = b / a if a > 0 else THM4_INV_C[i]
+    est = np.zeros(22)
+    var = np.zeros(22)
+    lam = np.zeros((2, 22))
+    plug = np.zeros(22)
+    for i in sampled:
+        src = [l for l in range(2) if avail[l] and (l == 0 or i in MIN_CLASSES)]
+        if not src:
+            continue
+        if len(src) == 1:
+            l = src[0]
+            e = (e4[i] if l == 0 else em[i]) if eta is None else float(eta[i])
+            plug[i] = e
+            if l == 0:
+                var[i] = e / K * (1.0 / p[i] - e)                    # Theorem 3
+                est[i] = e4[i]
+            else:
+                var[i] = (e * Gm * h[i] / 2.0 - e * e) / Kmin        # Theorem 5, per-CIS P(s)
+                est[i] = em[i]
+            lam[l, i] = 1.0
+            continue
+        e = (K * e4[i] + Kmin * em[i]) / (K + Kmin) if eta is None else float(eta[i])
+        plug[i] = e
+        V1 = max(e / K * (1.0 / p[i] - e), 0.0)
+        V2 = max((e * Gm * h[i] / 2.0 - e * e) / Kmin, 0.0)
+        if V1 + V2 > 0.0:
+            lam[0, i] = V2 / (V1 + V2)
+            lam[1, i] = V1 / (V1 + V2)
+            var[i] = V1 * V2 / (V1 + V2)                             # Theorem 1
+        else:
+            lam[0, i] = lam[1, i] = 0.5
+            var[i] = 0.0
+        est[i] = lam[0, i] * e4[i] + lam[1, i] * em[i]
+    # a sample lands in one class: Cov = -sum_l a^(l)_i a^(l)_j n_i n_j / K_l
+    cov = np.zeros((22, 22))
+    Ks = (K, Kmin)
+    for l in range(2):
+        if avail[l]:
+            a = lam[l] * plug
+            cov -= np.outer(a, a) / Ks[l]
+    np.fill_diagonal(cov, 0.0)
+    for i in range(22):
+        cov[i, i] = var[i]
+    coef = {4: 1.0, 5: 2.0, 6: 4.0}
+    est[2] = float(Lambda3) - est[4] - 2.0 * est[5] - 4.0 * est[6]   # eq. (2)
+    v2 = 0.0
+    for i in coef:
+        for j in coef:
+            v2 += coef[i] * coef[j] * cov[i, j]
+    for j in range(1, 7):
+        if j != 2:
+            c2 = 0.0
+            for i in coef:
+                c2 -= coef[i] * cov[i, j]
+            cov[2, j] = cov[j, 2] = c2
+    var[2] = v2 if avail[0] or avail[1] else 0.0
+    cov[2, 2] = var[2]
+    tri = 0.0
+    tri_var = 0.0
+    if avail[0]:
+        tri = m[0] * G / (6.0 * K)
+        tri_var = tri / K * (G / 6.0 - tri)
+    return {"k": 4, "K": (K if avail[0] else 0, Kmin if avail[1] else 0), "est": est, "var": var, "lam": lam,
+            "eta1": e4, "eta2": em, "h": h, "p": p, "cov": cov, "triangles": tri, "triangles_var": tri_var,
+            "conc": concentrations(est, 6)}
 
 
 def concentrations(est, n_classes: int) -> np.ndarray:

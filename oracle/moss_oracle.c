@@ -89,6 +89,17 @@ typedef struct {
     uint64_t *gthr;
     uint32_t *galias;
     uint64_t *acc;      /* ACC_sigma^(v)[i] exclusive prefix (Sec. 4.1.3) */
+    /* MOSS-4Min (Sec. 4.2), built on request by oracle_build_min */
+    int has_min;
+    uint32_t *rlist;    /* N_v ordered by the total order, highest first */
+    uint64_t *rank;     /* slot (v->u): d_{v,u} = |{x in N_v : x > u}| */
+    u128 *gmin;         /* Gamma-check_v = sum_{x in N_v} d_{v,x} d_{x,v} */
+    u128 tmin;          /* Gamma-check */
+    u128 *mthr;         /* vertex alias table of Gamma-check */
+    uint64_t *mT;
+    uint32_t *malias;
+    uint64_t *cthr;     /* per-list alias tables of sigma-check (eq. 3) */
+    uint32_t *calias;
 } ctx;
 
 /* ---------------------------------------------------- alias (sweep) ---- */
@@ -167,6 +178,8 @@ void oracle_free(ctx *c) {
     free(c->off); free(c->col); free(c->deg); free(c->S); free(c->Q);
     for (int l = 0; l < 3; l++) { free(c->gam[l]); free(c->sthr[l]); free(c->sT[l]); free(c->salias[l]); }
     free(c->gthr); free(c->galias); free(c->acc);
+    free(c->rlist); free(c->rank); free(c->gmin); free(c->mthr); free(c->mT); free(c->malias);
+    free(c->cthr); free(c->calias);
     free(c);
 }
 
@@ -467,13 +480,23 @@ static int sample_one(const ctx *c, int method, const uint64_t *x, uint32_t *out
 
 /* validity of a method on this graph: its total weight must be positive */
 static int method_ok(const ctx *c, int method) {
+    if (method == 3) return c->has_min && c->tmin != 0;
     if (method < 0 || method > 2) return 0;
     return c->tot[method] != 0;
 }
 
+static int sample_min(const ctx *c, const uint64_t *x, uint32_t *out, int *cp);
+static int min_slot(int cls, int cp);
+
+/* One sample from explicit words.  Method 3 (MOSS-4Min) puts c(s) in verts[4]. */
 int oracle_sample_words(const ctx *c, int method, const uint64_t *words, uint32_t *verts, int *cls) {
     if (!method_ok(c, method)) return -1;
-    *cls = sample_one(c, method, words, verts);
+    if (method == 3) {
+        int cp;
+        *cls = sample_min(c, words, verts, &cp);
+    } else {
+        *cls = sample_one(c, method, words, verts);
+    }
     return 0;
 }
 
@@ -486,7 +509,8 @@ static void sample_words(int method, uint64_t seed, uint64_t s, uint64_t *x) {
 }
 
 /* Run samples s in [first, first+count) of one method: counts[0] collisions,
- * counts[i] class i.  classes/verts (nullable) receive per-sample records. */
+ * counts[i] class i; for MOSS-4Min (method 3) counts[min_slot(class, c)]
+ * instead.  classes/verts (nullable) receive per-sample records. */
 int oracle_run(const ctx *c, int method, uint64_t seed, uint64_t first, uint64_t count,
                uint64_t *counts, uint8_t *classes, uint32_t *verts) {
     for (int i = 0; i < 22; i++) counts[i] = 0;
@@ -495,13 +519,181 @@ int oracle_run(const ctx *c, int method, uint64_t seed, uint64_t first, uint64_t
     uint32_t vv[5];
     for (uint64_t k = 0; k < count; k++) {
         sample_words(method, seed, first + k, x);
-        int cls = sample_one(c, method, x, vv);
-        if (cls < 0) return -2;
-        counts[cls]++;
+        int cls;
+        if (method == 3) {
+            /* Algorithm 2: counts by (class, c(s)) slot */
+            int cp;
+            cls = sample_min(c, x, vv, &cp);
+            int sl = min_slot(cls, cp);
+            if (sl >= 0) counts[sl]++;
+        } else {
+            cls = sample_one(c, method, x, vv);
+            if (cls < 0) return -2;
+            counts[cls]++;
+        }
         if (classes) classes[k] = (uint8_t)cls;
         if (verts) memcpy(verts + 5 * k, vv, sizeof(vv));
     }
     return 0;
+}
+
+/* --------------------------------------------------------- MOSS-4Min ---- */
+/* The total order of Sec. 3.2: a > b iff d_a > d_b, or d_a = d_b and a > b. */
+static int order_gt(const ctx *c, uint32_t a, uint32_t b) {
+    return c->deg[a] > c->deg[b] || (c->deg[a] == c->deg[b] && a > b);
+}
+
+static uint64_t order_key(const ctx *c, uint32_t x) { return (c->deg[x] << 32) | x; }
+
+static int cmp_desc_u64(const void *a, const void *b) {
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x < y) - (x > y);
+}
+
+/* Tables of Sec. 4.2: the ordered lists, d_{v,u}, Gamma-check and the alias
+ * tables of the vertex distribution pi-check and of sigma-check^(v) (eq. 3). */
+int oracle_build_min(ctx *c) {
+    if (c->has_min) return 0;
+    uint64_t nnz1 = c->nnz ? c->nnz : 1, n1 = c->n ? c->n : 1;
+    c->rlist = (uint32_t *)malloc(sizeof(uint32_t) * nnz1);
+    c->rank = (uint64_t *)malloc(sizeof(uint64_t) * nnz1);
+    c->gmin = (u128 *)calloc(n1, sizeof(u128));
+    c->mthr = (u128 *)malloc(sizeof(u128) * n1);
+    c->mT = (uint64_t *)malloc(sizeof(uint64_t) * n1);
+    c->malias = (uint32_t *)malloc(sizeof(uint32_t) * n1);
+    c->cthr = (uint64_t *)malloc(sizeof(uint64_t) * nnz1);
+    c->calias = (uint32_t *)malloc(sizeof(uint32_t) * nnz1);
+    uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * nnz1);
+    if (!c->rlist || !c->rank || !c->gmin || !c->mthr || !c->mT || !c->malias || !c->cthr || !c->calias || !keys) {
+        free(keys);
+        return -1;
+    }
+    /* ordered lists; d_{v,u} is u's position in the ordered N_v */
+    for (uint32_t v = 0; v < c->n; v++) {
+        uint64_t o = c->off[v], d = c->deg[v];
+        for (uint64_t i = 0; i < d; i++) keys[o + i] = order_key(c, c->col[o + i]);
+        qsort(keys + o, d, sizeof(uint64_t), cmp_desc_u64);
+        for (uint64_t i = 0; i < d; i++) c->rlist[o + i] = (uint32_t)keys[o + i];
+        for (uint64_t i = 0; i < d; i++) {
+            uint64_t k = order_key(c, c->col[o + i]);
+            uint64_t lo = 0, hi = d;          /* position of k in the descending keys */
+            while (lo < hi) {
+                uint64_t mid = (lo + hi) / 2;
+                if (keys[o + mid] > k) lo = mid + 1; else hi = mid;
+            }
+            c->rank[o + i] = lo;
+        }
+    }
+    /* Gamma-check_v and the sigma-check weights d_{v,u} d_{u,v} */
+    u128 *w = (u128 *)malloc(sizeof(u128) * nnz1), *t = (u128 *)malloc(sizeof(u128) * nnz1);
+    if (!w || !t) { free(keys); free(w); free(t); return -1; }
+    c->tmin = 0;
+    for (uint32_t v = 0; v < c->n; v++) {
+        uint64_t o = c->off[v], d = c->deg[v];
+        for (uint64_t i = 0; i < d; i++) {
+            uint32_t u = c->col[o + i];
+            uint64_t dvu = c->rank[o + i];
+            uint64_t duv = c->rank[c->off[u] + pos_of(c, u, v)];
+            w[i] = (u128)dvu * duv;
+            c->gmin[v] += w[i];
+        }
+        c->tmin += c->gmin[v];
+        if (alias_sweep(d, w, t, c->calias + o)) { free(keys); free(w); free(t); return -1; }
+        for (uint64_t i = 0; i < d; i++) c->cthr[o + i] = (uint64_t)t[i];
+    }
+    if (alias_sweep(c->n, c->gmin, c->mthr, c->malias)) { free(keys); free(w); free(t); return -1; }
+    for (uint32_t v = 0; v < c->n; v++) c->mT[v] = quantize(c->mthr[v], c->tmin);
+    free(keys);
+    free(w);
+    free(t);
+    c->has_min = 1;
+    return 0;
+}
+
+/* c(s): the 3-paths p0-p1-p2-p3 of the CIS whose ends satisfy p0 > p2 and
+ * p3 > p1 -- the paths MOSS-4Min can draw, each from both of its orientations,
+ * so the CIS is drawn with probability 2 c(s) / Gamma-check.  Vertices in role
+ * order, mask over the pairs (0,1),(0,2),(0,3),(1,2),(1,3),(2,3). */
+static int centered_paths(const ctx *c, const uint32_t *x, uint32_t mask) {
+    int pair[4][4];
+    int b = 0;
+    for (int i = 0; i < 4; i++)
+        for (int j = i + 1; j < 4; j++, b++) pair[i][j] = pair[j][i] = (mask >> b) & 1;
+    int count = 0;
+    int p[4];
+    for (p[0] = 0; p[0] < 4; p[0]++)
+        for (p[1] = 0; p[1] < 4; p[1]++)
+            for (p[2] = 0; p[2] < 4; p[2]++)
+                for (p[3] = 0; p[3] < 4; p[3]++) {
+                    if (p[0] == p[1] || p[0] == p[2] || p[0] == p[3] || p[1] == p[2] || p[1] == p[3] ||
+                        p[2] == p[3])
+                        continue;
+                    if (!pair[p[0]][p[1]] || !pair[p[1]][p[2]] || !pair[p[2]][p[3]]) continue;
+                    if (order_gt(c, x[p[0]], x[p[2]]) && order_gt(c, x[p[3]], x[p[1]])) count++;
+                }
+    return count / 2;
+}
+
+/* count slot of (class, c): C4 c=1..4 -> 0..3, diamond c=1..6 -> 4..9,
+ * K4 c=1..12 -> 10..21; other outcomes are not counted (-1) */
+static int min_slot(int cls, int cp) {
+    if (cls == 3 && cp >= 1 && cp <= 4) return cp - 1;
+    if (cls == 5 && cp >= 1 && cp <= 6) return 4 + cp - 1;
+    if (cls == 6 && cp >= 1 && cp <= 12) return 10 + cp - 1;
+    return -1;
+}
+
+/* Algorithm 2 from explicit words: x0,x1 vertex draw, x2,x3 sigma-check draw
+ * of u, x4 w (uniform in N_{v,u}), x5 r (uniform in N_{u,v}).  Returns the
+ * class (0 = collision) and *cp = c(s) for classes 3, 5, 6 (else 0). */
+static int sample_min(const ctx *c, const uint64_t *x, uint32_t *out, int *cp) {
+    uint64_t col = index_of(x[0], c->n);
+    uint32_t v = x[1] < c->mT[col] ? (uint32_t)col : c->malias[col];
+    uint64_t ov = c->off[v];
+    uint64_t j = index_of(x[2], c->deg[v]);
+    uint64_t y = index_of(x[3], (uint64_t)c->gmin[v]);
+    uint64_t iu = y < c->cthr[ov + j] ? j : c->calias[ov + j];
+    uint32_t u = c->col[ov + iu];
+    uint64_t dvu = c->rank[ov + iu];                       /* |N_{v,u}| */
+    uint64_t duv = c->rank[c->off[u] + pos_of(c, u, v)];    /* |N_{u,v}| */
+    uint32_t w = c->rlist[ov + index_of(x[4], dvu)];
+    uint32_t r = c->rlist[c->off[u] + index_of(x[5], duv)];
+    out[0] = v; out[1] = u; out[2] = w; out[3] = r; out[4] = 0;
+    *cp = 0;
+    if (r == u || r == w) return 0;
+    uint32_t mask = 0;
+    int bit = 0;
+    for (int i = 0; i < 4; i++)
+        for (int k = i + 1; k < 4; k++, bit++)
+            if (is_edge(c, out[i], out[k])) mask |= 1u << bit;
+    int cls = oracle_classify(4, mask);
+    if (cls == 3 || cls == 5 || cls == 6) *cp = centered_paths(c, out, mask);
+    out[4] = (uint32_t)*cp;
+    return cls;
+}
+
+int oracle_min_words(const ctx *c, const uint64_t *words, uint32_t *verts, int *cls, int *cp) {
+    if (!c->has_min || c->tmin == 0) return -1;
+    *cls = sample_min(c, words, verts, cp);
+    return 0;
+}
+
+/* out[2] = Gamma-check lo/hi */
+void oracle_min_total(const ctx *c, uint64_t *out) { put128(out, c->tmin); }
+
+void oracle_min_tables(const ctx *c, uint32_t *rlist, uint64_t *rank, uint64_t *cthr, uint32_t *calias,
+                       uint64_t *gmin_lohi, uint64_t *mT, uint32_t *malias) {
+    for (uint64_t p = 0; p < c->nnz; p++) {
+        rlist[p] = c->rlist[p];
+        rank[p] = c->rank[p];
+        cthr[p] = c->cthr[p];
+        calias[p] = c->calias[p];
+    }
+    for (uint32_t v = 0; v < c->n; v++) {
+        put128(gmin_lohi + 2 * (uint64_t)v, c->gmin[v]);
+        mT[v] = c->mT[v];
+        malias[v] = c->malias[v];
+    }
 }
 
 /* --------------------------------------------------------------- ESU ---- */
