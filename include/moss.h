@@ -9,7 +9,10 @@
  *   Sampling and Counting 4- and 5-Node Graphlets", arXiv 1509.08089:
  *     MOSS-4  (Sec. 4.1, Algorithm 1, Theorems 2-3),
  *     MOSS-5  = T-5 (Algorithm 3, Theorems 6-7) + Path-5 (Algorithm 4,
- *               Theorems 8-9) + the mix estimator (Sec. 5.1.3, Theorem 10).
+ *               Theorems 8-9) + the mix estimator (Sec. 5.1.3, Theorem 10),
+ *     MOSS-4Min (Sec. 4.2, Algorithm 2, Theorem 5) and its mix with MOSS-4
+ *               (Theorem 1), with the per-CIS sampling probability
+ *               2 c(s) / Gamma-check described at MOSS_METHOD_MOSS4MIN.
  * Every step runs as CUDA kernels on one GPU (sm_103a).  The only data that
  * crosses to the host during sampling is the final result.
  *
@@ -28,7 +31,8 @@
  *
  * Random numbers: Philox4x64-10 (Salmon et al., SC'11).  Word i of sample s of
  * method t under seed k is word (i mod 4) of Philox4x64-10(counter
- * {s, i div 4, t, 0}, key {k, 0}); t = 0 (MOSS-4), 1 (T-5), 2 (Path-5).  The
+ * {s, i div 4, t, 0}, key {k, 0}); t = 0 (MOSS-4), 1 (T-5), 2 (Path-5),
+ * 3 (MOSS-4Min).  The
  * counts of a sample range are therefore independent of launch shape, stream
  * and device count, and shards [a,b) + [b,c) add up to [a,c) exactly.
  */
@@ -54,6 +58,20 @@ extern "C" {
 #define MOSS_METHOD_MOSS4  0   /* Algorithm 1 */
 #define MOSS_METHOD_T5     1   /* Algorithm 3 */
 #define MOSS_METHOD_PATH5  2   /* Algorithm 4 */
+/* Algorithm 2 (Sec. 4.2).  v from pi-check (weight Gamma-check_v =
+ * sum_{x in N_v} d_{v,x} d_{x,v}), u from sigma-check^(v) (eq. 3), w uniform
+ * in N_{v,u}, r uniform in N_{u,v}, where N_{u,v} holds the neighbours of u
+ * above v in the total order of Sec. 3.2 (higher degree, ties by the larger
+ * id) and d_{u,v} = |N_{u,v}|.  Every admissible (v, u, w, r) has probability
+ * 1 / Gamma-check, so a CIS s is drawn with probability 2 c(s) / Gamma-check,
+ * c(s) being the number of 3-paths p0-p1-p2-p3 of s with p0 above p2 and p3
+ * above p1.  c(s) is 1 for a 4-cycle and 3 for a 4-clique (Theorem 4), but
+ * 1, 2 or 3 for a diamond (Theorem 4 states 1), so the counts of this method
+ * are kept per (class, c) slot: 4-cycles with c = 1..4 in slots 0..3,
+ * diamonds with c = 1..6 in slots 4..9, 4-cliques with c = 1..12 in slots
+ * 10..21; collisions (r = w) and the other classes are not counted.  Word
+ * schedule: x0,x1 vertex draw, x2,x3 sigma-check draw, x4 w, x5 r. */
+#define MOSS_METHOD_MOSS4MIN 3
 
 #define MOSS_NCLASS_SLOTS 22   /* [0] = collisions, [1..21] = classes */
 
@@ -71,10 +89,11 @@ typedef struct {
     uint32_t n;                 /* vertices                                 */
     uint64_t nnz;               /* directed CSR slots = 2 |E|               */
     uint32_t d_max;             /* maximum degree                           */
-    uint64_t gamma[3][2];       /* Gamma, Gamma^(1), Gamma^(2): {lo, hi}     */
+    uint64_t gamma[4][2];       /* Gamma, Gamma^(1), Gamma^(2), Gamma-check  */
+                                /* (0 until the MOSS-4Min tables are built): {lo, hi} */
     uint64_t lambda3[2];        /* Lambda_3 = sum C(d_v,3): {lo, hi}         */
     uint64_t lambda4[2];        /* Lambda_4 = sum C(d_v,4): {lo, hi}         */
-    double gamma_d[3], lambda3_d, lambda4_d;
+    double gamma_d[4], lambda3_d, lambda4_d;
 } moss_stats;
 
 /* Result of one estimate.  Index i of est/var is class M_i (1-based); index
@@ -82,11 +101,14 @@ typedef struct {
 typedef struct {
     int k;                      /* 4 or 5                                   */
     int n_classes;              /* 6 or 21                                  */
-    uint64_t K[2];              /* samples drawn: k=4 {K, 0}; k=5 {K1, K2}    */
-    uint64_t hits[2][MOSS_NCLASS_SLOTS]; /* [sub-method][0 = collisions, i]   */
+    uint64_t K[2];              /* samples drawn: k=4 {K, 0} (with MOSS-4Min  */
+                                /* {K, K-check}); k=5 {K1, K2}                */
+    uint64_t hits[2][MOSS_NCLASS_SLOTS]; /* [sub-method][0 = collisions, i];  */
+                                /* MOSS-4Min: its (class, c) slots           */
     double est[MOSS_NCLASS_SLOTS];       /* estimate of n_i / eta_i          */
     double var[MOSS_NCLASS_SLOTS];       /* plug-in variance of est[i]       */
-    double lambda[2][MOSS_NCLASS_SLOTS]; /* k=5: weight of T-5 / Path-5 in est */
+    double lambda[2][MOSS_NCLASS_SLOTS]; /* weight of each sub-method in est */
+                                /* (k=5: T-5 / Path-5; mix: MOSS-4 / 4Min)   */
     double triangles;           /* k=4: triangle count implied by the r = w collisions */
     double triangles_var;
     double conc[MOSS_NCLASS_SLOTS];      /* concentration est[i] / sum_j est[j] (Sec. 6.3) */
@@ -111,9 +133,15 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
 /* Sampling tables (Sec. 4.1.3 WeightRandomVertex, Sec. 5.1.4): the per-list
  * alias tables of sigma^(v) (eq. 1), the vertex alias tables of pi (k_mask
  * bit 4) and rho^(1), rho^(2) (k_mask bit 5) from the exact weights computed
- * at load, and, under MOSS_PROBE_HASH, the hashed edge set.  k_mask:
- * (1<<4) | (1<<5) or either.  MOSS_EOVERFLOW if a scaled total leaves 128
- * bits.  Synchronous on stream; tables already built are rebuilt. */
+ * at load, and, under MOSS_PROBE_HASH, the hashed edge set.  k_mask: any
+ * non-empty combination of (1<<4), (1<<5) and MOSS_TABLES_4MIN, which adds
+ * the MOSS-4Min tables (Sec. 4.2): every N_v ordered by the total order,
+ * d_{v,u} per slot, Gamma-check_v, the alias tables of sigma-check^(v)
+ * (eq. 3) and of pi-check, and the exact total Gamma-check -- about
+ * 40 bytes per CSR slot plus 48 per vertex, held until moss_graph_free.
+ * MOSS_EOVERFLOW if a scaled total leaves 128 bits.  Synchronous on stream;
+ * the tables of k_mask are rebuilt and only those stay usable. */
+#define MOSS_TABLES_4MIN (1u << 6)
 int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream);
 
 /* Select the probe strategy (MOSS_PROBE_*) for later samples.  Switching to
@@ -130,8 +158,9 @@ int moss_sample_estimate(moss_graph *g, int k, uint64_t budget, uint64_t seed, v
                          moss_result *out);
 
 /* Counts of samples first..first+count-1 of one method: counts_dev (device,
- * 22 uint64) receives [0] = collisions (no CIS) and [i] = samples of class i.
- * Asynchronous on stream.  Shards of a sample range sum exactly. */
+ * 22 uint64) receives [0] = collisions (no CIS) and [i] = samples of class i
+ * (MOSS_METHOD_MOSS4MIN: its (class, c) slots).  Asynchronous on stream.
+ * Shards of a sample range sum exactly. */
 int moss_sample_counts(moss_graph *g, int method, uint64_t first, uint64_t count, uint64_t seed,
                        void *stream, uint64_t *counts_dev);
 
@@ -154,7 +183,8 @@ int moss_sample_counts_noalloc(moss_graph *g, int method, uint64_t first, uint64
 /* Per-sample records of samples first..first+count-1 (for verification):
  * classes_dev (device, count uint8: 0 = collision, else class) and, when not
  * NULL, verts_dev (device, 5*count uint32: v,u,w,r,t in draw order; t = 0
- * for MOSS-4).  Asynchronous on stream. */
+ * for MOSS-4; MOSS-4Min: v,u,w,r,c(s), c(s) = 0 outside classes 3, 5, 6).
+ * Asynchronous on stream. */
 int moss_sample_records(moss_graph *g, int method, uint64_t first, uint64_t count, uint64_t seed,
                         void *stream, uint8_t *classes_dev, uint32_t *verts_dev);
 
@@ -163,6 +193,32 @@ int moss_sample_records(moss_graph *g, int method, uint64_t first, uint64_t coun
  * the device in FP64.  Synchronous on stream. */
 int moss_finalize(moss_graph *g, int k, const uint64_t *K, const uint64_t *hits, void *stream,
                   moss_result *out);
+
+/* MOSS-4 with K = budget and MOSS-4Min with K-check = budget_min (sample ids
+ * 0.. of each, same seed), mixed class by class (Theorem 1): requires the
+ * tables of (1<<4) | MOSS_TABLES_4MIN.  Classes 3, 5, 6 have both estimates
+ * n-hat_i (Theorem 2) and n-check_i = Gamma-check / (2 K-check) sum_c
+ * m_{i,c} / c (each hit weighted by its inverse probability); Var(n-check_i)
+ * is (S_i - n_i^2) / K-check with S_i = sum_s 1/P(s) = n_i Gamma-check h_i / 2,
+ * h_i the mean of 1/c(s) over the class, estimated from the hits as
+ * sum_c m_{i,c}/c^2 / sum_c m_{i,c}/c (1, 1, 1/3 for classes 3, 5, 6 when
+ * there is none).  Both variances use the plug-in n_i = (K n-hat_i +
+ * K-check n-check_i) / (K + K-check); the weights are lambda = V_other /
+ * (V_1 + V_2) and the mixed variance V_1 V_2 / (V_1 + V_2).  Classes 1 and 4
+ * come from MOSS-4 alone, n_2 from eq. (2).  Result: k = 4, K = {K, K-check},
+ * hits[0] MOSS-4 counts, hits[1] MOSS-4Min slots, lambda[0] / lambda[1]
+ * the weights.  Synchronous on stream. */
+int moss_sample_estimate_min(moss_graph *g, uint64_t budget, uint64_t budget_min, uint64_t seed, void *stream,
+                             moss_result *out);
+
+/* The estimate above from counts gathered elsewhere: K[2] = {K, K-check},
+ * hits[2][22] = {MOSS-4 counts, MOSS-4Min slots}.  cov_host (nullable, 22 x 22
+ * doubles, host) receives the covariance matrix: -n_i n_j sum_l a_i a_j / K_l
+ * between classes (a = the weights, a sample lands in one class), the
+ * variances on the diagonal, the row of class 2 from eq. (2).  Synchronous on
+ * stream. */
+int moss_finalize_min(moss_graph *g, const uint64_t *K, const uint64_t *hits, void *stream, double *cov_host,
+                      moss_result *out);
 
 /* ----------------------------------------------------------------- batches
  * Many sample-and-estimate requests, on many loaded graphs, in one persistent
@@ -270,12 +326,24 @@ int moss_graph_stats(const moss_graph *g, moss_stats *out);
  *   MOSS_TABLE_SEED0+l n x {uint64 threshold T, uint32 alias, uint32 0},
  *                      l = 0 pi, 1 rho^(1), 2 rho^(2)
  *   MOSS_TABLE_GAMMA0+l n x {uint64 lo, hi} vertex weight of table l
+ * and, after a build with MOSS_TABLES_4MIN (Sec. 4.2):
+ *   MOSS_TABLE_MIN_SEED  n x {uint64 threshold T, uint32 alias, uint32 0} of pi-check
+ *   MOSS_TABLE_MIN_GAMMA n x {uint64 lo, hi} Gamma-check_v
+ *   MOSS_TABLE_MIN_VERT  n x {uint32 off, deg, Gamma-check_v lo, hi}
+ *   MOSS_TABLE_MIN_SLOT  nnz x {uint64 sigma-check threshold, uint32 alias
+ *                        (position in N_v), u, off_u, d_u, d_{v,u}, d_{u,v}}
+ *   MOSS_TABLE_MIN_LIST  nnz x {uint32 x, d_x}: each N_v highest first
  * bytes must equal the table size.  Synchronous. */
 #define MOSS_TABLE_VERT   0
 #define MOSS_TABLE_SLOT   1
 #define MOSS_TABLE_ACC    2
 #define MOSS_TABLE_SEED0  3
 #define MOSS_TABLE_GAMMA0 6
+#define MOSS_TABLE_MIN_SEED  9
+#define MOSS_TABLE_MIN_GAMMA 10
+#define MOSS_TABLE_MIN_VERT  11
+#define MOSS_TABLE_MIN_SLOT  12
+#define MOSS_TABLE_MIN_LIST  13
 int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t bytes);
 
 void moss_graph_free(moss_graph *g);

@@ -24,16 +24,18 @@ LIB_PATH = os.path.join(_HERE, "libmoss.so")
 
 MOSS_OK, MOSS_EINVAL, MOSS_ENOMEM, MOSS_ECUDA, MOSS_EGRAPH, MOSS_EOVERFLOW, MOSS_ESTATE = 0, -1, -2, -3, -4, -5, -6
 MOSS_EBUSY = -7
-MOSS4, T5, PATH5 = 0, 1, 2
+MOSS4, T5, PATH5, MOSS4MIN = 0, 1, 2, 3
 PROBE_SEARCH, PROBE_HASH = 0, 1
 NSLOTS = 22
+TABLES_4MIN = 1 << 6
 TABLE_VERT, TABLE_SLOT, TABLE_ACC, TABLE_SEED0, TABLE_GAMMA0 = 0, 1, 2, 3, 6
+TABLE_MIN_SEED, TABLE_MIN_GAMMA, TABLE_MIN_VERT, TABLE_MIN_SLOT, TABLE_MIN_LIST = 9, 10, 11, 12, 13
 
 
 class moss_stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint32), ("nnz", ctypes.c_uint64), ("d_max", ctypes.c_uint32),
-                ("gamma", (ctypes.c_uint64 * 2) * 3), ("lambda3", ctypes.c_uint64 * 2),
-                ("lambda4", ctypes.c_uint64 * 2), ("gamma_d", ctypes.c_double * 3),
+                ("gamma", (ctypes.c_uint64 * 2) * 4), ("lambda3", ctypes.c_uint64 * 2),
+                ("lambda4", ctypes.c_uint64 * 2), ("gamma_d", ctypes.c_double * 4),
                 ("lambda3_d", ctypes.c_double), ("lambda4_d", ctypes.c_double)]
 
 
@@ -91,6 +93,8 @@ def load():
         "moss_sample_records": ([_vp, ctypes.c_int, _u64, _u64, _u64, _vp, _vp, _vp], ctypes.c_int),
         "moss_sample_counts_noalloc": ([_vp, ctypes.c_int, _u64, _u64, _u64, _vp, _vp], ctypes.c_int),
         "moss_finalize": ([_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
+        "moss_sample_estimate_min": ([_vp, _u64, _u64, _u64, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
+        "moss_finalize_min": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
         "moss_graph_stats": ([_vp, ctypes.POINTER(moss_stats)], ctypes.c_int),
         "moss_covariance": ([_vp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
         "moss_table_export": ([_vp, ctypes.c_int, _vp, _u64], ctypes.c_int),
@@ -225,6 +229,24 @@ def moss_finalize(g: int, k: int, K, hits, stream=None) -> moss_result:
     r = moss_result()
     _check(load().moss_finalize(g, k, _ptr(Ka), _ptr(Ha), _stream(stream), ctypes.byref(r)))
     return r
+
+
+def moss_sample_estimate_min(g: int, budget: int, budget_min: int, seed: int, stream=None) -> moss_result:
+    """MOSS-4 (K = budget) mixed with MOSS-4Min (K-check = budget_min)."""
+    r = moss_result()
+    _check(load().moss_sample_estimate_min(g, budget, budget_min, seed, _stream(stream), ctypes.byref(r)))
+    return r
+
+
+def moss_finalize_min(g: int, K, hits, stream=None, covariance: bool = False):
+    """The MOSS-4 + MOSS-4Min mix from counts; with covariance=True returns
+    (22 x 22 covariance matrix, result)."""
+    Ka = np.ascontiguousarray(K, dtype=np.uint64)
+    Ha = np.ascontiguousarray(hits, dtype=np.uint64).reshape(2 * NSLOTS)
+    cov = np.zeros((NSLOTS, NSLOTS), dtype=np.float64) if covariance else None
+    r = moss_result()
+    _check(load().moss_finalize_min(g, _ptr(Ka), _ptr(Ha), _stream(stream), _ptr(cov), ctypes.byref(r)))
+    return (cov, r) if covariance else r
 
 
 def moss_covariance(g: int, k: int, K, hits, stream=None):
@@ -454,6 +476,10 @@ class Graph:
 
     def estimate(self, k: int, budget: int, seed: int, stream=None) -> dict:
         return result_dict(moss_sample_estimate(self.handle, k, budget, seed, stream))
+
+    def estimate_min(self, budget: int, budget_min: int, seed: int, stream=None) -> dict:
+        """MOSS-4 with MOSS-4Min (needs k_mask with (1 << 4) | TABLES_4MIN)."""
+        return result_dict(moss_sample_estimate_min(self.handle, budget, budget_min, seed, stream))
 
     def stats(self) -> moss_stats:
         return moss_graph_stats(self.handle)

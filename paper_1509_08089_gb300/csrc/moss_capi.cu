@@ -162,11 +162,15 @@ struct moss_graph {
     uint32_t *acc = nullptr;
     uint32_t *owner = nullptr;   // vertex of each CSR slot (flat per-slot passes)
     uint64_t *q = nullptr;
-    u128 *gam[3] = {nullptr, nullptr, nullptr};
-    uint4 *seed[3] = {nullptr, nullptr, nullptr};
+    u128 *gam[kMethods] = {nullptr, nullptr, nullptr, nullptr};    // [3]: Gamma-check_v (min arena)
+    uint4 *seed[kMethods] = {nullptr, nullptr, nullptr, nullptr};
+    uint4 *mvert = nullptr;      // MOSS-4Min tables, in min_arena
+    uint4 *mslot = nullptr;
+    uint2 *rlist = nullptr;
+    void *min_arena = nullptr;
     DevTotals *tot = nullptr;
     DevTotals tot_h{};
-    unsigned built = 0;          // bit l: vertex table l; bit 3: sigma tables
+    unsigned built = 0;          // bit l: vertex table l; bit 3: sigma tables; bit 4: edge hash; bit 5: MOSS-4Min
     uint64_t *partials = nullptr;
     int partial_rows = 0;
     uint64_t *counts = nullptr;  // 2 x 22
@@ -189,6 +193,7 @@ void release(moss_graph *g) {
     // ordered on the legacy default stream, i.e. after the work of blocking streams
     if (g->arena) cudaFreeAsync(g->arena, 0);
     if (g->hash) cudaFreeAsync(g->hash, 0);
+    if (g->min_arena) cudaFreeAsync(g->min_arena, 0);
     delete g;
 }
 
@@ -199,7 +204,10 @@ DevGraph view(const moss_graph *g) {
     d.slot = g->slot;
     d.acc = g->acc;
     d.q = g->q;
-    for (int l = 0; l < 3; ++l) d.seed[l] = g->seed[l];
+    for (int l = 0; l < kMethods; ++l) d.seed[l] = g->seed[l];
+    d.mvert = g->mvert;
+    d.mslot = g->mslot;
+    d.rlist = g->rlist;
     d.n = g->n;
     const bool use_hash = g->probe == MOSS_PROBE_HASH && (g->built >> 4 & 1u);
     d.hash = use_hash ? reinterpret_cast<const uint4 *>(g->hash) : nullptr;
@@ -272,6 +280,7 @@ int read_flags(moss_graph *g, cudaStream_t s) {
 
 bool method_ready(const moss_graph *g, int method) {
     const bool probes = g->probe != MOSS_PROBE_HASH || (g->built >> 4 & 1u);
+    if (method == MOSS_METHOD_MOSS4MIN) return (g->built >> 5 & 1u) && probes;
     return (g->built >> 3 & 1u) && (g->built >> method & 1u) && probes;
 }
 
@@ -393,9 +402,39 @@ fail_out:
     return rc;
 }
 
+// The MOSS-4Min tables in their own allocation (made once per graph).
+static int build_min_tables(moss_graph *g, cudaStream_t s) {
+    cudaError_t e;
+    if (!g->min_arena) {
+        Carver c;
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1) {
+                if ((e = pool_alloc(g->device, &g->min_arena, c.off, s)) != cudaSuccess)
+                    return cuda_fail(e, "allocating MOSS-4Min tables");
+                c.base = static_cast<uint8_t *>(g->min_arena);
+                c.off = 0;
+            }
+            g->mvert = c.take<uint4>(g->n);
+            g->mslot = c.take<uint4>(2 * g->nnz);
+            g->rlist = c.take<uint2>(g->nnz);
+            g->gam[3] = c.take<u128>(g->n);
+            g->seed[3] = c.take<uint4>(g->n);
+        }
+    }
+    void *scratch = nullptr;
+    if ((e = pool_alloc(g->device, &scratch, min_scratch_bytes(g->n, g->nnz), s)) != cudaSuccess)
+        return cuda_fail(e, "allocating scratch");
+    e = launch_min_tables(g->n, g->nnz, g->vert, g->col, g->owner, g->slot, g->mvert, g->mslot, g->rlist, g->gam[3],
+                          g->seed[3], g->tot, scratch, g->flags, s);
+    cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "MOSS-4Min table kernels");
+    return MOSS_OK;
+}
+
 int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
     if (!g) return fail(MOSS_EINVAL, "graph is NULL");
-    if ((k_mask & ~((1u << 4) | (1u << 5))) || !k_mask) return fail(MOSS_EINVAL, "k_mask must select 4 and/or 5");
+    if ((k_mask & ~((1u << 4) | (1u << 5) | MOSS_TABLES_4MIN)) || !k_mask)
+        return fail(MOSS_EINVAL, "k_mask must combine (1<<4), (1<<5) and MOSS_TABLES_4MIN");
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // one scratch buffer, used first by the per-list tables then by the vertex tables
@@ -424,7 +463,7 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
             ++nt;
         }
     }
-    if (e == cudaSuccess) e = launch_seed_alias(g->n, g->tot, nt, which, w, seed, scratch, g->flags, s);
+    if (e == cudaSuccess && nt > 0) e = launch_seed_alias(g->n, g->tot, nt, which, w, seed, scratch, g->flags, s);
     cudaFreeAsync(scratch, s);
     bool hashed = false;
     if (e == cudaSuccess && g->probe == MOSS_PROBE_HASH) {
@@ -449,6 +488,12 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
         hashed = e == cudaSuccess;
     }
     if (e != cudaSuccess) return cuda_fail(e, "table kernels");
+    bool min_built = false;
+    if (k_mask & MOSS_TABLES_4MIN) {
+        if ((rc = build_min_tables(g, s))) return rc;
+        min_built = true;
+    }
+    MOSS_CUDA(cudaMemcpyAsync(&g->tot_h, g->tot, sizeof(DevTotals), cudaMemcpyDeviceToHost, s), "reading totals");
     rc = read_flags(g, s);
     if (rc) return rc;
     if (g->flags_host[0] & kErrOverflow) return fail(MOSS_EOVERFLOW, "a vertex weight total times n exceeds 2^128");
@@ -456,6 +501,7 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
     if (k_mask & (1u << 4)) g->built |= 1u;
     if (k_mask & (1u << 5)) g->built |= 6u;
     if (hashed) g->built |= 1u << 4;
+    if (min_built) g->built |= 1u << 5;
     return MOSS_OK;
 }
 
@@ -469,7 +515,7 @@ int moss_set_probe(moss_graph *g, int strategy) {
 
 static int sample_into(moss_graph *g, int method, uint64_t first, uint64_t count, uint64_t seed, cudaStream_t s,
                        uint64_t *counts_dev, uint8_t *classes, uint32_t *verts) {
-    if (method < 0 || method > 2) return fail(MOSS_EINVAL, "method %d", method);
+    if (method < 0 || method >= kMethods) return fail(MOSS_EINVAL, "method %d", method);
     if (!method_ready(g, method)) return fail(MOSS_ESTATE, "tables for method %d not built", method);
     if (count > 0 && g->tot_h.gamma[method] == 0)
         return fail(MOSS_EINVAL, "method %d has total weight 0 on this graph: no sample exists", method);
@@ -568,6 +614,55 @@ int moss_covariance(moss_graph *g, int k, const uint64_t *K, const uint64_t *hit
     return MOSS_OK;
 }
 
+int moss_sample_estimate_min(moss_graph *g, uint64_t budget, uint64_t budget_min, uint64_t seed, void *stream,
+                             moss_result *out) {
+    if (!g || !out) return fail(MOSS_EINVAL, "NULL argument");
+    if (!method_ready(g, MOSS_METHOD_MOSS4) || !method_ready(g, MOSS_METHOD_MOSS4MIN))
+        return fail(MOSS_ESTATE, "tables for k=4 and MOSS-4Min not built");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FinalizeIn in;
+    in.k = 4;
+    in.mix = 1;
+    in.K[0] = g->tot_h.gamma[0] ? budget : 0;
+    in.K[1] = g->tot_h.gamma[3] ? budget_min : 0;
+    int rc;
+    if ((rc = sample_into(g, MOSS_METHOD_MOSS4, 0, in.K[0], seed, s, g->counts, nullptr, nullptr))) return rc;
+    if ((rc = sample_into(g, MOSS_METHOD_MOSS4MIN, 0, in.K[1], seed, s, g->counts + kSlots, nullptr, nullptr)))
+        return rc;
+    MOSS_CUDA(launch_finalize(in, g->counts, g->tot, g->res_dev, s), "finalize kernel");
+    MOSS_CUDA(cudaMemcpyAsync(&g->res_host, g->res_dev, sizeof(moss_result), cudaMemcpyDeviceToHost, s), "reading result");
+    MOSS_CUDA(cudaStreamSynchronize(s), "synchronising stream");
+    memcpy(out, &g->res_host, sizeof(moss_result));
+    return MOSS_OK;
+}
+
+int moss_finalize_min(moss_graph *g, const uint64_t *K, const uint64_t *hits, void *stream, double *cov_host,
+                      moss_result *out) {
+    if (!g || !K || !hits || !out) return fail(MOSS_EINVAL, "NULL argument");
+    if (!(g->built >> 5 & 1u)) return fail(MOSS_ESTATE, "MOSS-4Min tables not built (Gamma-check unknown)");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MOSS_CUDA(cudaMemcpyAsync(g->counts, hits, 2 * kSlots * sizeof(uint64_t), cudaMemcpyDefault, s), "copying counts");
+    FinalizeIn in;
+    in.k = 4;
+    in.mix = 1;
+    in.K[0] = K[0];
+    in.K[1] = K[1];
+    if (cov_host) {
+        MOSS_CUDA(launch_covariance(in, g->counts, g->tot, g->res_dev, g->cov_dev, s), "covariance kernel");
+        MOSS_CUDA(cudaMemcpyAsync(cov_host, g->cov_dev, kSlots * kSlots * sizeof(double), cudaMemcpyDeviceToHost, s),
+                  "reading covariance");
+    } else {
+        MOSS_CUDA(launch_finalize(in, g->counts, g->tot, g->res_dev, s), "finalize kernel");
+    }
+    MOSS_CUDA(cudaMemcpyAsync(&g->res_host, g->res_dev, sizeof(moss_result), cudaMemcpyDeviceToHost, s),
+              "reading result");
+    MOSS_CUDA(cudaStreamSynchronize(s), "synchronising stream");
+    memcpy(out, &g->res_host, sizeof(moss_result));
+    return MOSS_OK;
+}
+
 int moss_graph_stats(const moss_graph *g, moss_stats *out) {
     if (!g || !out) return fail(MOSS_EINVAL, "NULL argument");
     memset(out, 0, sizeof(*out));
@@ -579,7 +674,7 @@ int moss_graph_stats(const moss_graph *g, moss_stats *out) {
         dst[1] = (uint64_t)(x >> 64);
     };
     auto dbl = [](u128 x) { return (double)(uint64_t)(x >> 64) * 18446744073709551616.0 + (double)(uint64_t)x; };
-    for (int l = 0; l < 3; ++l) {
+    for (int l = 0; l < kMethods; ++l) {
         put(out->gamma[l], g->tot_h.gamma[l]);
         out->gamma_d[l] = dbl(g->tot_h.gamma[l]);
     }
@@ -605,6 +700,15 @@ int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t b
     } else if (table >= MOSS_TABLE_GAMMA0 && table < MOSS_TABLE_GAMMA0 + 3) {
         src = g->gam[table - MOSS_TABLE_GAMMA0];
         need = (uint64_t)g->n * 16;
+    } else if (table >= MOSS_TABLE_MIN_SEED && table <= MOSS_TABLE_MIN_LIST) {
+        if (!(g->built >> 5 & 1u)) return fail(MOSS_ESTATE, "MOSS-4Min tables not built");
+        switch (table) {
+            case MOSS_TABLE_MIN_SEED: src = g->seed[3]; need = (uint64_t)g->n * 16; break;
+            case MOSS_TABLE_MIN_GAMMA: src = g->gam[3]; need = (uint64_t)g->n * 16; break;
+            case MOSS_TABLE_MIN_VERT: src = g->mvert; need = (uint64_t)g->n * 16; break;
+            case MOSS_TABLE_MIN_SLOT: src = g->mslot; need = g->nnz * 32; break;
+            default: src = g->rlist; need = g->nnz * 8; break;
+        }
     } else {
         return fail(MOSS_EINVAL, "unknown table %d", table);
     }
@@ -627,7 +731,7 @@ int graph_info(const moss_graph *g, GraphInfo *out) {
     out->tot = g->tot;
     out->device = g->device;
     out->built = g->built;
-    for (int l = 0; l < 3; ++l) out->total_nonzero[l] = g->tot_h.gamma[l] != 0;
+    for (int l = 0; l < kMethods; ++l) out->total_nonzero[l] = g->tot_h.gamma[l] != 0;
     return MOSS_OK;
 }
 

@@ -12,6 +12,15 @@
 //     and the covariances Cov(eta_i, eta_j) = -eta_i eta_j sum_l a_i a_j / K_l.
 //   The unknown eta in a variance is replaced by the estimate (one source) or
 //   by the pooled value (m1 + m2) / (K1 p1 + K2 p2) (two sources).
+//   MOSS-4 with MOSS-4Min (Sec. 4.2, Theorems 1 and 5): a MOSS-4Min hit of
+//     class i in {3, 5, 6} whose CIS has c centred 3-paths was drawn with
+//     probability 2 c / Gamma-check, so n-check_i = Gamma-check / (2 K-check)
+//     sum_c m_{i,c} / c; Var(n-check_i) = (S_i - n_i^2) / K-check with
+//     S_i = n_i Gamma-check h_i / 2, h_i the mean of 1/c over the class
+//     (sum_c m_{i,c}/c^2 over sum_c m_{i,c}/c; 1, 1, 1/3 without hits, the
+//     values of Theorem 4).  Both variances take the plug-in
+//     n_i = (K n-hat_i + K-check n-check_i) / (K + K-check), the weights are
+//     V_other / (V_1 + V_2) (Theorem 1), n_2 follows eq. (2).
 #include "../../include/moss.h"
 #include "moss_internal.cuh"
 
@@ -197,15 +206,138 @@ __device__ void finalize_one(const FinalizeIn &in, const uint64_t *hits0, const 
     *out = r;
 }
 
+// MOSS-4 (hits0, K[0]) mixed with MOSS-4Min (hits1 = (class, c) slots, K[1])
+__device__ void finalize_mix(const FinalizeIn &in, const uint64_t *hits0, const uint64_t *hits1, const DevTotals *tot,
+                             moss_result *out, double *cov) {
+    moss_result r;
+    memset(&r, 0, sizeof(r));
+    r.k = 4;
+    r.n_classes = 6;
+    for (int i = 0; i < kSlots; ++i) {
+        r.hits[0][i] = hits0 ? hits0[i] : 0;
+        r.hits[1][i] = hits1 ? hits1[i] : 0;
+    }
+    const double G = u128_to_double(tot->gamma[0]), Gm = u128_to_double(tot->gamma[3]);
+    const double K = (double)in.K[0], Km = (double)in.K[1];
+    const bool avail0 = in.K[0] > 0 && G > 0, avail1 = in.K[1] > 0 && Gm > 0;
+    r.K[0] = avail0 ? in.K[0] : 0;
+    r.K[1] = avail1 ? in.K[1] : 0;
+    const int first[7] = {0, 0, 0, 0, 0, 4, 10}, nslot[7] = {0, 0, 0, 4, 0, 6, 12};
+    const double thm4_inv_c[7] = {0, 0, 0, 1.0, 0, 1.0, 1.0 / 3.0};
+    double p[7], e4[7], em[7], h[7], plug[7], a[2][7];
+    for (int i = 0; i < 7; ++i) { p[i] = e4[i] = em[i] = h[i] = plug[i] = a[0][i] = a[1][i] = 0.0; }
+    if (avail0) {
+        for (int i = 1; i <= 6; ++i) {
+            if (i == 2) continue;
+            p[i] = 2.0 * kPhi4[i - 1][0] / G;                  // Theorem 2
+            e4[i] = (double)r.hits[0][i] / (K * p[i]);
+        }
+    }
+    if (avail1) {
+        for (int i = 3; i <= 6; ++i) {
+            if (nslot[i] == 0) continue;
+            double sa = 0.0, sb = 0.0;
+            for (int c = 1; c <= nslot[i]; ++c) {
+                const double m = (double)r.hits[1][first[i] + c - 1];
+                sa += m / c;
+                sb += m / (c * c);
+            }
+            em[i] = Gm / (2.0 * Km) * sa;
+            h[i] = sa > 0 ? sb / sa : thm4_inv_c[i];
+        }
+    }
+    for (int i = 1; i <= 6; ++i) {
+        if (i == 2) continue;
+        const bool s0 = avail0, s1 = avail1 && nslot[i] > 0;
+        if (!s0 && !s1) continue;
+        if (s0 != s1) {
+            if (s0) {
+                const double e = e4[i];
+                plug[i] = e;
+                r.var[i] = e / K * (1.0 / p[i] - e);           // Theorem 3
+                r.est[i] = e;
+                a[0][i] = 1.0;
+            } else {
+                const double e = em[i];
+                plug[i] = e;
+                r.var[i] = (e * Gm * h[i] / 2.0 - e * e) / Km;  // Theorem 5, per-CIS probabilities
+                r.est[i] = e;
+                a[1][i] = 1.0;
+            }
+            continue;
+        }
+        const double e = (K * e4[i] + Km * em[i]) / (K + Km);
+        plug[i] = e;
+        const double V1 = fmax(e / K * (1.0 / p[i] - e), 0.0);
+        const double V2 = fmax((e * Gm * h[i] / 2.0 - e * e) / Km, 0.0);
+        if (V1 + V2 > 0.0) {
+            a[0][i] = V2 / (V1 + V2);
+            a[1][i] = V1 / (V1 + V2);
+            r.var[i] = V1 * V2 / (V1 + V2);                      // Theorem 1
+        } else {
+            a[0][i] = a[1][i] = 0.5;
+            r.var[i] = 0.0;
+        }
+        r.est[i] = a[0][i] * e4[i] + a[1][i] * em[i];
+    }
+    for (int i = 0; i < 7; ++i) {
+        r.lambda[0][i] = a[0][i];
+        r.lambda[1][i] = a[1][i];
+    }
+    // Cov(i, j) = -plug_i plug_j sum_l a_i a_j / K_l for i != j (a sample lands in one class)
+    double cv[7][7];
+    for (int i = 0; i < 7; ++i)
+        for (int j = 0; j < 7; ++j) {
+            double c = 0.0;
+            if (i == j) {
+                c = r.var[i];
+            } else {
+                if (avail0) c -= (a[0][i] * plug[i]) * (a[0][j] * plug[j]) / K;
+                if (avail1) c -= (a[1][i] * plug[i]) * (a[1][j] * plug[j]) / Km;
+            }
+            cv[i][j] = c;
+        }
+    const double coef[7] = {0, 0, 0, 0, 1.0, 2.0, 4.0};
+    r.est[2] = u128_to_double(tot->lambda3) - r.est[4] - 2.0 * r.est[5] - 4.0 * r.est[6];   // eq. (2)
+    double v2 = 0.0;
+    for (int i = 4; i <= 6; ++i)
+        for (int j = 4; j <= 6; ++j) v2 += coef[i] * coef[j] * cv[i][j];
+    for (int j = 1; j <= 6; ++j) {
+        if (j == 2) continue;
+        double c2 = 0.0;
+        for (int i = 4; i <= 6; ++i) c2 -= coef[i] * cv[i][j];
+        cv[2][j] = cv[j][2] = c2;
+    }
+    r.var[2] = (avail0 || avail1) ? v2 : 0.0;
+    cv[2][2] = r.var[2];
+    if (avail0) {
+        r.triangles = (double)r.hits[0][0] * G / (6.0 * K);
+        r.triangles_var = r.triangles / K * (G / 6.0 - r.triangles);
+    }
+    concentrations(r);
+    if (cov) {
+        for (int i = 0; i < kSlots * kSlots; ++i) cov[i] = 0.0;
+        for (int i = 1; i <= 6; ++i)
+            for (int j = 1; j <= 6; ++j) cov[i * kSlots + j] = cv[i][j];
+    }
+    *out = r;
+}
+
+__device__ void finalize_any(const FinalizeIn &in, const uint64_t *hits0, const uint64_t *hits1,
+                             const DevTotals *tot, moss_result *out, double *cov = nullptr) {
+    if (in.mix) finalize_mix(in, hits0, hits1, tot, out, cov);
+    else finalize_one(in, hits0, hits1, tot, out, cov);
+}
+
 __global__ void k_covariance(FinalizeIn in, const uint64_t *hits, const DevTotals *tot, moss_result *out,
                              double *cov) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    finalize_one(in, hits, hits + kSlots, tot, out, cov);
+    finalize_any(in, hits, hits + kSlots, tot, out, cov);
 }
 
 __global__ void k_finalize(FinalizeIn in, const uint64_t *hits, const DevTotals *tot, moss_result *out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    finalize_one(in, hits, hits + kSlots, tot, out);
+    finalize_any(in, hits, hits + kSlots, tot, out);
 }
 
 // one thread per request of a batch
@@ -216,7 +348,7 @@ __global__ void k_finalize_batch(const BatchRequest *reqs, int nreq, const uint6
     const BatchRequest q = reqs[r];
     const uint64_t *h0 = q.task[0] >= 0 ? task_counts + (uint64_t)q.task[0] * kSlots : nullptr;
     const uint64_t *h1 = q.task[1] >= 0 ? task_counts + (uint64_t)q.task[1] * kSlots : nullptr;
-    finalize_one(q.in, h0, h1, q.tot, out + r);
+    finalize_any(q.in, h0, h1, q.tot, out + r);
 }
 
 }  // namespace

@@ -12,7 +12,19 @@
 //   gam[l][n] u128 vertex weights Gamma_v, Gamma^(1)_v, Gamma^(2)_v
 //   seed[l][n] uint4 {T lo, T hi, alias, 0}: vertex alias table of weight l,
 //             keep the column when x < T for a 64-bit word x.
-// nnz < 2^32 bounds every S_v, ACC entry and sigma threshold below 2^32.
+// MOSS-4Min (Sec. 4.2), built on request:
+//   mvert[n]  uint4 {off, deg, Gamma-check_v lo, hi}
+//   mslot[2 nnz] two uint4 per slot (v -> u), one 32-byte sector:
+//             {thr lo, thr hi, alias, u} -- per-list alias table of
+//             sigma-check^(v) (eq. 3): keep the column when y < thr for y
+//             uniform in [0, Gamma-check_v), else take position alias --
+//             and {off_u, d_u, d_{v,u}, d_{u,v}}
+//   rlist[nnz] uint2 {x, d_x}: N_v ordered by the total order (degree, then
+//             id; Sec. 3.2), highest first, so N_{v,u} is its first d_{v,u}
+//             entries
+//   gam[3], seed[3]: Gamma-check_v and its vertex alias table
+// nnz < 2^32 bounds every S_v, ACC entry and sigma threshold below 2^32, and
+// every Gamma-check_v = sum d_{v,x} d_{x,v} <= d_v * nnz below 2^64.
 #pragma once
 
 #include <cstdint>
@@ -24,8 +36,10 @@ namespace moss {
 
 constexpr int kSlots = 22;            // [0] collisions, [1..21] classes
 
+constexpr int kMethods = 4;          // MOSS-4, T-5, Path-5, MOSS-4Min
+
 struct alignas(16) DevTotals {
-    u128 gamma[3];                    // Gamma, Gamma^(1), Gamma^(2)
+    u128 gamma[kMethods];             // Gamma, Gamma^(1), Gamma^(2), Gamma-check
     u128 lambda3, lambda4;            // Lambda_3, Lambda_4
     uint32_t d_max;
     uint32_t pad[3];
@@ -37,7 +51,10 @@ struct DevGraph {
     const uint4 *slot;
     const uint32_t *acc;
     const uint64_t *q;
-    const uint4 *seed[3];
+    const uint4 *seed[kMethods];
+    const uint4 *mvert;     // MOSS-4Min tables (null until built)
+    const uint4 *mslot;
+    const uint2 *rlist;
     const uint4 *hash;      // hashed edge set (2 keys per 16 B bucket), or null: probe by search
     uint32_t hash_mask;     // buckets - 1
     uint32_t hash_shift;    // 64 - log2(buckets)
@@ -87,6 +104,51 @@ __host__ __device__ inline uint64_t mulhi64(uint64_t a, uint64_t b) {
 // floor(x * m / 2^64): a uniform index in [0, m) from a 64-bit word
 __device__ __forceinline__ uint64_t word_index(uint64_t x, uint64_t m) { return __umul64hi(x, m); }
 
+// ------------------------------------------------------------ warp scans --
+__device__ __forceinline__ uint64_t shfl_up64(uint64_t v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+
+__device__ __forceinline__ uint64_t warp_incl_scan64(uint64_t v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t t = shfl_up64(v, d);
+        if (lane >= d) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ u128 shfl_up_u128(u128 v, int d) {
+    uint64_t lo = __shfl_up_sync(0xffffffffu, (uint64_t)v, d);
+    uint64_t hi = __shfl_up_sync(0xffffffffu, (uint64_t)(v >> 64), d);
+    return ((u128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ u128 shfl_down_u128(u128 v, int d) {
+    uint64_t lo = __shfl_down_sync(0xffffffffu, (uint64_t)v, d);
+    uint64_t hi = __shfl_down_sync(0xffffffffu, (uint64_t)(v >> 64), d);
+    return ((u128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ u128 shfl_idx_u128(u128 v, int src) {
+    uint64_t lo = __shfl_sync(0xffffffffu, (uint64_t)v, src);
+    uint64_t hi = __shfl_sync(0xffffffffu, (uint64_t)(v >> 64), src);
+    return ((u128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ u128 warp_incl_scan128(u128 v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        u128 t = shfl_up_u128(v, d);
+        if (lane >= d) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ u128 warp_sum128(u128 v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += shfl_down_u128(v, d);
+    return v;
+}
+
 // ---------------------------------------------------------------- Philox --
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
 // as 1, 2, 3", SC'11): ten rounds, each multiplying counter words 0 and 2 by
@@ -131,6 +193,14 @@ cudaError_t launch_seed_alias(uint32_t n, const DevTotals *tot, int ntables, con
 uint64_t seed_scratch_bytes(uint32_t n);
 int table_blocks(uint32_t n);
 
+// moss_min.cu: the MOSS-4Min tables (ordered lists, d_{v,u}, Gamma-check_v,
+// the sigma-check alias tables, tot->gamma[3] and its vertex alias table)
+uint64_t min_scratch_bytes(uint32_t n, uint64_t nnz);
+cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const uint32_t *col,
+                              const uint32_t *owner, const uint4 *slot, uint4 *mvert, uint4 *mslot, uint2 *rlist,
+                              u128 *gmin, uint4 *seed_min, DevTotals *tot, void *scratch, uint32_t *flags,
+                              cudaStream_t s);
+
 // moss_sample.cu
 void upload_luts(const uint8_t *lut4, const uint8_t *lut5);
 cudaError_t launch_sample(int method, const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed,
@@ -142,6 +212,7 @@ int sample_blocks(int method, int device);
 // moss_finalize.cu
 struct FinalizeIn {
     int k;
+    int mix = 0;      // k = 4 only: MOSS-4 (K[0], hits[0]) with MOSS-4Min (K[1], hits[1])
     uint64_t K[2];
 };
 cudaError_t launch_finalize(const FinalizeIn &in, const uint64_t *hits_dev, const DevTotals *tot,
@@ -182,8 +253,8 @@ struct GraphInfo {
     DevGraph view;
     const DevTotals *tot;
     int device;
-    unsigned built;          // bit l: vertex table l; bit 3: sigma tables
-    bool total_nonzero[3];   // Gamma, Gamma^(1), Gamma^(2) > 0
+    unsigned built;          // bit l: vertex table l; bit 3: sigma tables; bit 4: edge hash; bit 5: MOSS-4Min
+    bool total_nonzero[kMethods];   // Gamma, Gamma^(1), Gamma^(2), Gamma-check > 0
 };
 }  // namespace moss
 

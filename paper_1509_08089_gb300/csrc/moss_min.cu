@@ -1,0 +1,424 @@
+// moss_min.cu -- the MOSS-4Min tables (Sec. 4.2) on the device.
+//
+// The total order of Sec. 3.2 puts x above y when d_x > d_y, or d_x = d_y and
+// x > y; the 64-bit key (d_x << 32) | x orders vertices exactly that way.
+// N_{u,v} = {x in N_u : x above v}, d_{u,v} = |N_{u,v}|.  Every list N_v is
+// stored sorted by that key, highest first (rlist), so N_{v,u} is its first
+// d_{v,u} entries and d_{v,u} is the position of u in it:
+//   * lists of at most 32 entries: a warp per list, each lane counts the keys
+//     above its own;
+//   * lists of at most kTile entries: a block per list, bitonic sort in
+//     shared memory;
+//   * longer lists: a block per list sorts tiles of kTile keys in shared
+//     memory, then merges runs pairwise in global memory, each key placed by
+//     one binary search in the partner run (keys are distinct).
+// Then per slot (v -> u): u, d_u, off_u, d_{v,u} and d_{u,v} (the rank of the
+// twin slot); per list: Gamma-check_v = sum_u d_{v,u} d_{u,v} and the alias
+// table of sigma-check^(v) (eq. 3) -- the parallel closed form of the sweep
+// used for sigma^(v) in moss_tables.cu, here in 128-bit arithmetic since
+// q_j = w_j d_v can exceed 2^64; the exact total Gamma-check; and the vertex
+// alias table of pi-check through the seed-table kernels.
+#include "moss_internal.cuh"
+
+namespace moss {
+
+namespace {
+
+constexpr int kWarp = 32;
+constexpr uint32_t kTile = 4096;      // keys sorted per shared-memory pass (32 KB)
+constexpr int kSortThreads = 512;
+constexpr int kListThreads = 256;
+
+__device__ __forceinline__ uint64_t order_key(uint32_t x, uint32_t dx) { return ((uint64_t)dx << 32) | x; }
+
+// position of x in the increasing list col[o, o + d)
+__device__ __forceinline__ uint32_t find_pos(const uint32_t *col, uint32_t o, uint32_t d, uint32_t x) {
+    uint32_t lo = 0, len = d;
+    while (len > 0) {
+        const uint32_t half = len >> 1;
+        if (col[o + lo + half] < x) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo;
+}
+
+// position q of the sorted list holds key: record the entry and u's rank
+__device__ __forceinline__ void emit(const uint32_t *col, uint32_t o, uint32_t d, uint32_t q, uint64_t key,
+                                     uint2 *rlist, uint32_t *rank) {
+    const uint32_t x = (uint32_t)key, dx = (uint32_t)(key >> 32);
+    rlist[o + q] = make_uint2(x, dx);
+    rank[o + find_pos(col, o, d, x)] = q;
+}
+
+__global__ void __launch_bounds__(kListThreads) k_rank_warp(uint32_t n, const uint4 *__restrict__ vert,
+                                                           const uint32_t *__restrict__ col, uint2 *rlist,
+                                                           uint32_t *rank) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    for (uint64_t v = (uint64_t)blockIdx.x * wpb + warp; v < n; v += (uint64_t)gridDim.x * wpb) {
+        const uint4 vr = vert[v];
+        const uint32_t o = vr.x, d = vr.y;
+        if (d == 0 || d > (uint32_t)kWarp) continue;   // warp-uniform
+        uint32_t x = 0, dx = 0;
+        uint64_t key = 0;                               // below every real key (d_x >= 1)
+        if ((uint32_t)lane < d) {
+            x = col[o + lane];
+            dx = vert[x].y;
+            key = order_key(x, dx);
+        }
+        uint32_t r = 0;
+#pragma unroll
+        for (int j = 0; j < kWarp; ++j) r += __shfl_sync(0xffffffffu, key, j) > key;
+        if ((uint32_t)lane < d) {
+            rlist[o + r] = make_uint2(x, dx);
+            rank[o + lane] = r;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t pow2_at_least(uint32_t x) {
+    uint32_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// keys of col[o + base, o + base + len) into k[0, P), zero padded (zero sorts last)
+__device__ void load_keys(const uint4 *vert, const uint32_t *col, uint32_t o, uint32_t base, uint32_t len,
+                          uint32_t P, uint64_t *k) {
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+        uint64_t key = 0;
+        if (i < len) {
+            const uint32_t x = col[o + base + i];
+            key = order_key(x, vert[x].y);
+        }
+        k[i] = key;
+    }
+    __syncthreads();
+}
+
+// block-wide bitonic sort of k[0, P), P a power of two, highest first
+__device__ void bitonic_desc(uint64_t *k, uint32_t P) {
+    for (uint32_t size = 2; size <= P; size <<= 1)
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (uint32_t t = threadIdx.x; t < P / 2; t += blockDim.x) {
+                const uint32_t i = 2 * t - (t & (stride - 1)), j = i + stride;
+                const uint64_t a = k[i], b = k[j];
+                const bool down = (i & size) == 0;   // this run ends highest first
+                if ((a < b) == down) {
+                    k[i] = b;
+                    k[j] = a;
+                }
+            }
+            __syncthreads();
+        }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_rank_block(uint32_t n, const uint4 *__restrict__ vert,
+                                                            const uint32_t *__restrict__ col, uint2 *rlist,
+                                                            uint32_t *rank) {
+    __shared__ uint64_t k[kTile];
+    for (uint64_t v = blockIdx.x; v < n; v += gridDim.x) {
+        const uint4 vr = vert[v];
+        const uint32_t o = vr.x, d = vr.y;
+        if (d <= (uint32_t)kWarp || d > kTile) continue;   // block-uniform
+        const uint32_t P = pow2_at_least(d);
+        load_keys(vert, col, o, 0, d, P, k);
+        bitonic_desc(k, P);
+        for (uint32_t q = threadIdx.x; q < d; q += blockDim.x) emit(col, o, d, q, k[q], rlist, rank);
+        __syncthreads();   // k is refilled for the next list
+    }
+}
+
+// lists longer than kTile: tiles sorted in shared memory into a[], then runs
+// of length L merged pairwise between a[] and b[] until one run is left
+__global__ void __launch_bounds__(kSortThreads) k_rank_long(uint32_t n, const uint4 *__restrict__ vert,
+                                                           const uint32_t *__restrict__ col, uint64_t *a,
+                                                           uint64_t *b, uint2 *rlist, uint32_t *rank) {
+    __shared__ uint64_t k[kTile];
+    for (uint64_t v = blockIdx.x; v < n; v += gridDim.x) {
+        const uint4 vr = vert[v];
+        const uint32_t o = vr.x, d = vr.y;
+        if (d <= kTile) continue;   // block-uniform
+        for (uint32_t base = 0; base < d; base += kTile) {
+            const uint32_t len = min(kTile, d - base);
+            const uint32_t P = pow2_at_least(len);
+            load_keys(vert, col, o, base, len, P, k);
+            bitonic_desc(k, P);
+            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) a[(uint64_t)o + base + i] = k[i];
+            __syncthreads();
+        }
+        uint64_t *src = a, *dst = b;
+        for (uint64_t L = kTile; L < d; L <<= 1) {
+            for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
+                const uint64_t run = i / L, start = run * L;
+                const uint64_t ps = (run ^ 1) * L;               // the partner run
+                const uint64_t ms = (run & ~1ull) * L;           // where the pair's merge starts
+                const uint64_t key = src[(uint64_t)o + i];
+                // partner keys above key (the partner run is sorted highest first)
+                uint64_t lo = ps, len = ps < d ? min(ps + L, (uint64_t)d) - ps : 0;
+                while (len > 0) {
+                    const uint64_t half = len >> 1;
+                    if (src[(uint64_t)o + lo + half] > key) {
+                        lo += half + 1;
+                        len -= half + 1;
+                    } else {
+                        len = half;
+                    }
+                }
+                const uint64_t above = ps < d ? lo - ps : 0;
+                dst[(uint64_t)o + ms + (i - start) + above] = key;
+            }
+            __syncthreads();
+            uint64_t *t = src;
+            src = dst;
+            dst = t;
+        }
+        for (uint32_t q = threadIdx.x; q < d; q += blockDim.x) emit(col, o, d, q, src[(uint64_t)o + q], rlist, rank);
+        __syncthreads();
+    }
+}
+
+// per slot p (v -> u): {0, 0, 0, u} and {off_u, d_u, d_{v,u}, d_{u,v}}
+__global__ void k_min_slots(uint64_t nnz, const uint4 *__restrict__ vert, const uint32_t *__restrict__ col,
+                            const uint4 *__restrict__ slot, const uint32_t *__restrict__ rank, uint4 *mslot) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = col[p];
+        const uint4 ur = vert[u];
+        const uint32_t twin = slot[p].w;
+        mslot[2 * p] = make_uint4(0u, 0u, 0u, u);
+        mslot[2 * p + 1] = make_uint4(ur.x, ur.y, rank[p], rank[(uint64_t)ur.x + twin]);
+    }
+}
+
+__device__ __forceinline__ uint64_t min_weight(const uint4 *mslot, uint64_t p) {
+    const uint4 r = mslot[2 * p + 1];
+    return (uint64_t)r.z * r.w;   // d_{v,u} d_{u,v}
+}
+
+// warp per list: Gamma-check_v, mvert, and the alias table of sigma-check^(v)
+// over capacity W = Gamma-check_v.  Lights (q_j = w_j d < W) carry the deficit
+// W - q_j, heavies the excess q_j - W, both in list order; with A_i the
+// exclusive prefix of the light deficits and P_k the inclusive prefix of the
+// heavy excesses: light i keeps q_i and aliases heavy min{k : P_k >= A_i};
+// heavy k keeps W + P_k - A_{i'} (i' = min{i : A_i > P_k}) and aliases heavy
+// k+1, or keeps W when P_k is the total.
+__global__ void __launch_bounds__(kListThreads) k_min_alias(uint32_t n, const uint4 *__restrict__ vert, uint4 *mslot,
+                                                           uint4 *mvert, u128 *gmin, uint32_t *idx, u128 *pre,
+                                                           u128 *partials) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const uint32_t below = (1u << lane) - 1u;
+    uint32_t *m32 = reinterpret_cast<uint32_t *>(mslot);
+    u128 total = 0;
+    for (uint64_t v = (uint64_t)blockIdx.x * wpb + warp; v < n; v += (uint64_t)gridDim.x * wpb) {
+        const uint4 vr = vert[v];
+        const uint32_t o = vr.x, d = vr.y;
+        uint64_t W = 0;
+        for (uint32_t j = lane; j < d; j += kWarp) W += min_weight(mslot, (uint64_t)o + j);
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) W += __shfl_down_sync(0xffffffffu, W, s);
+        W = __shfl_sync(0xffffffffu, W, 0);
+        if (lane == 0) {
+            mvert[v] = make_uint4(o, d, (uint32_t)W, (uint32_t)(W >> 32));
+            gmin[v] = W;
+            total += W;
+        }
+        if (d == 0) continue;
+        if (W == 0) {   // never drawn: keep every column
+            for (uint32_t j = lane; j < d; j += kWarp) {
+                m32[8 * ((uint64_t)o + j) + 0] = 0;
+                m32[8 * ((uint64_t)o + j) + 1] = 0;
+                m32[8 * ((uint64_t)o + j) + 2] = j;
+            }
+            continue;
+        }
+        // pass 1: lights to the front, heavies to the back, with their prefixes
+        uint32_t nl = 0, nh = 0;
+        u128 Arun = 0, Prun = 0;
+        for (uint32_t base = 0; base < d; base += kWarp) {
+            const uint32_t j = base + lane;
+            const bool valid = j < d;
+            const u128 q = valid ? (u128)min_weight(mslot, (uint64_t)o + j) * d : 0;
+            const bool light = valid && q < W;
+            const uint32_t lmask = __ballot_sync(0xffffffffu, light);
+            const uint32_t hmask = __ballot_sync(0xffffffffu, valid && !light);
+            const u128 D = light ? (u128)W - q : 0;
+            const u128 E = valid && !light ? q - W : 0;
+            const u128 Dincl = warp_incl_scan128(D, lane);
+            const u128 Eincl = warp_incl_scan128(E, lane);
+            if (light) {
+                const uint32_t r = nl + __popc(lmask & below);
+                idx[(uint64_t)o + r] = j;
+                pre[(uint64_t)o + r] = Arun + Dincl - D;          // exclusive A_i
+            } else if (valid) {
+                const uint32_t r = nh + __popc(hmask & below);
+                idx[(uint64_t)o + d - 1 - r] = j;
+                pre[(uint64_t)o + d - 1 - r] = Prun + Eincl;      // inclusive P_k
+            }
+            nl += __popc(lmask);
+            nh += __popc(hmask);
+            Arun += shfl_idx_u128(Dincl, 31);
+            Prun += shfl_idx_u128(Eincl, 31);
+        }
+        __syncwarp();
+        const u128 Ptot = Prun;   // == Arun
+        const uint64_t ob = o;
+        // pass 2: each lane merges a contiguous run of lights, then of heavies
+        {
+            const uint32_t cl = (nl + kWarp - 1) / kWarp;
+            const uint32_t i0 = lane * cl, i1 = min(nl, i0 + cl);
+            if (i0 < i1) {
+                const u128 A0 = pre[ob + i0];
+                uint32_t k = 0, len = nh;   // first heavy with P_k >= A
+                while (len > 0) {
+                    const uint32_t half = len >> 1;
+                    if (pre[ob + d - 1 - (k + half)] < A0) {
+                        k += half + 1;
+                        len -= half + 1;
+                    } else {
+                        len = half;
+                    }
+                }
+                for (uint32_t i = i0; i < i1; ++i) {
+                    const u128 A = pre[ob + i];
+                    while (pre[ob + d - 1 - k] < A) ++k;
+                    const uint32_t j = idx[ob + i];
+                    const uint64_t thr = min_weight(mslot, ob + j) * (uint64_t)d;   // q_j < W < 2^64
+                    m32[8 * (ob + j) + 0] = (uint32_t)thr;
+                    m32[8 * (ob + j) + 1] = (uint32_t)(thr >> 32);
+                    m32[8 * (ob + j) + 2] = idx[ob + d - 1 - k];
+                }
+            }
+        }
+        {
+            const uint32_t ch = (nh + kWarp - 1) / kWarp;
+            const uint32_t k0 = lane * ch, k1 = min(nh, k0 + ch);
+            if (k0 < k1) {
+                const u128 P0 = pre[ob + d - 1 - k0];
+                uint32_t i = 0, len = nl;   // first light with A_i > P_k
+                while (len > 0) {
+                    const uint32_t half = len >> 1;
+                    if (pre[ob + i + half] <= P0) {
+                        i += half + 1;
+                        len -= half + 1;
+                    } else {
+                        len = half;
+                    }
+                }
+                for (uint32_t k = k0; k < k1; ++k) {
+                    const u128 Pk = pre[ob + d - 1 - k];
+                    while (i < nl && pre[ob + i] <= Pk) ++i;
+                    const uint32_t j = idx[ob + d - 1 - k];
+                    uint64_t thr;
+                    uint32_t alias;
+                    if (Pk < Ptot) {
+                        const u128 Ai = i < nl ? pre[ob + i] : Ptot;
+                        thr = (uint64_t)((u128)W + Pk - Ai);
+                        alias = idx[ob + d - 1 - (k + 1)];
+                    } else {
+                        thr = W;
+                        alias = j;
+                    }
+                    m32[8 * (ob + j) + 0] = (uint32_t)thr;
+                    m32[8 * (ob + j) + 1] = (uint32_t)(thr >> 32);
+                    m32[8 * (ob + j) + 2] = alias;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // block share of Gamma-check (lane 0 of each warp holds its warp's)
+    __shared__ u128 sh[kListThreads / kWarp];
+    if (lane == 0) sh[warp] = total;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u128 s = 0;
+        for (int w = 0; w < wpb; ++w) s += sh[w];
+        partials[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_min_total(const u128 *partials, int blocks, DevTotals *tot) {
+    const int lane = threadIdx.x;   // one warp
+    u128 s = 0;
+    for (int b = lane; b < blocks; b += kWarp) s += partials[b];
+    s = warp_sum128(s);
+    if (lane == 0) tot->gamma[3] = s;
+}
+
+unsigned grid_for(uint64_t items, int per_block, int cap_per_sm) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint64_t b = (items + per_block - 1) / per_block;
+    const uint64_t cap = (uint64_t)sms * cap_per_sm;
+    if (b > cap) b = cap;
+    return (unsigned)(b ? b : 1);
+}
+
+struct MinScratch {
+    uint32_t *rank;   // nnz, then reused as the alias split order
+    uint64_t *a, *b;  // nnz each (long-list merges), then reused as u128 prefixes
+    u128 *partials;
+    void *seed;       // vertex alias scratch
+    uint64_t bytes;
+};
+
+MinScratch carve(void *base, uint32_t n, uint64_t nnz) {
+    MinScratch m{};
+    uint8_t *p = static_cast<uint8_t *>(base);
+    uint64_t off = 0;
+    auto take = [&](uint64_t bytes) {
+        off = (off + 255) & ~255ULL;
+        uint8_t *r = p ? p + off : nullptr;
+        off += bytes ? bytes : 1;
+        return r;
+    };
+    const unsigned alias_blocks = grid_for((uint64_t)n, kListThreads / kWarp, 8);
+    m.rank = reinterpret_cast<uint32_t *>(take(nnz * 4));
+    m.a = reinterpret_cast<uint64_t *>(take(nnz * 16));
+    m.b = m.a ? m.a + nnz : nullptr;
+    m.partials = reinterpret_cast<u128 *>(take((uint64_t)alias_blocks * 16));
+    m.seed = take(seed_scratch_bytes(n));
+    m.bytes = off;
+    return m;
+}
+
+}  // namespace
+
+uint64_t min_scratch_bytes(uint32_t n, uint64_t nnz) { return carve(nullptr, n, nnz).bytes; }
+
+cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const uint32_t *col,
+                              const uint32_t *owner, const uint4 *slot, uint4 *mvert, uint4 *mslot, uint2 *rlist,
+                              u128 *gmin, uint4 *seed_min, DevTotals *tot, void *scratch, uint32_t *flags,
+                              cudaStream_t s) {
+    (void)owner;
+    const MinScratch m = carve(scratch, n, nnz);
+    cudaError_t e;
+    if (nnz) {
+        k_rank_warp<<<grid_for((uint64_t)n, kListThreads / kWarp, 8), kListThreads, 0, s>>>(n, vert, col, rlist,
+                                                                                             m.rank);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_rank_block<<<grid_for((uint64_t)n, 1, 4), kSortThreads, 0, s>>>(n, vert, col, rlist, m.rank);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_rank_long<<<grid_for((uint64_t)n, 1, 1), kSortThreads, 0, s>>>(n, vert, col, m.a, m.b, rlist, m.rank);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_min_slots<<<grid_for(nnz, 256, 16), 256, 0, s>>>(nnz, vert, col, slot, m.rank, mslot);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const unsigned ab = grid_for((uint64_t)n, kListThreads / kWarp, 8);
+    // the rank array is dead now: it holds the split order, a[]/b[] the prefixes
+    k_min_alias<<<ab, kListThreads, 0, s>>>(n, vert, mslot, mvert, gmin, m.rank, reinterpret_cast<u128 *>(m.a),
+                                             m.partials);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_min_total<<<1, kWarp, 0, s>>>(m.partials, (int)ab, tot);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int which[1] = {3};
+    u128 *w[1] = {gmin};
+    uint4 *sd[1] = {seed_min};
+    return launch_seed_alias(n, tot, 1, which, w, sd, m.seed, flags, s);
+}
+
+}  // namespace moss

@@ -62,11 +62,12 @@ using namespace moss;
 extern "C" int moss_sample_counts_noalloc(moss_graph *g, int method, uint64_t first, uint64_t count, uint64_t seed,
                                           void *stream, uint64_t *counts_dev) {
     if (!g || !counts_dev) return set_error(MOSS_EINVAL, "NULL argument");
-    if (method < 0 || method > 2) return set_error(MOSS_EINVAL, "method must be 0, 1 or 2");
+    if (method < 0 || method >= kMethods) return set_error(MOSS_EINVAL, "method must be 0, 1, 2 or 3");
     GraphInfo gi;
     graph_info(g, &gi);
-    if (!((gi.built >> 3) & 1u) || !((gi.built >> method) & 1u))
-        return set_error(MOSS_ESTATE, "tables for this method are not built");
+    const bool ready = method == MOSS_METHOD_MOSS4MIN ? ((gi.built >> 5) & 1u) != 0
+                                                     : ((gi.built >> 3) & 1u) && ((gi.built >> method) & 1u);
+    if (!ready) return set_error(MOSS_ESTATE, "tables for this method are not built");
     if (count > 0 && !gi.total_nonzero[method])
         return set_error(MOSS_EINVAL, "method has total weight 0 on this graph: no sample exists");
     if (first + count < first) return set_error(MOSS_EOVERFLOW, "sample range wraps");

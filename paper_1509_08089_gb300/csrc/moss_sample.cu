@@ -1,5 +1,5 @@
-// moss_sample.cu -- the sampling loop of MOSS-4 (Algorithm 1), T-5
-// (Algorithm 3) and Path-5 (Algorithm 4) on the device.
+// moss_sample.cu -- the sampling loop of MOSS-4 (Algorithm 1), MOSS-4Min
+// (Algorithm 2), T-5 (Algorithm 3) and Path-5 (Algorithm 4) on the device.
 //
 // One thread draws one sample at a time (grid-stride over sample ids), so
 // every sample is an independent chain of dependent gathers:
@@ -15,6 +15,8 @@
 // {s, i div 4, method, 0}, key {seed, 0}):
 //   MOSS-4 : x0,x1 vertex draw; x2,x3 sigma draw of u; x4 w; x5 r.
 //   T-5    : x0,x1 vertex draw; x2,x3 sigma of u; x4 w; x5 r; x6 t.
+//   MOSS-4Min: x0,x1 vertex draw (pi-check); x2,x3 sigma-check draw of u;
+//            x4 w (uniform in N_{v,u}); x5 r (uniform in N_{u,v}).
 //   Path-5 : x0,x1 vertex draw; x2 r; x3 t; attempts a = 0,1 use
 //            x(4+4a)..x(7+4a) for two independent sigma draws (u, w), kept
 //            when the positions differ (sigma_u sigma_w / (1 - sum sigma^2)
@@ -37,6 +39,7 @@ __device__ uint8_t g_lut4[64];
 __device__ uint8_t g_lut5[1024];
 
 __device__ __forceinline__ uint4 ld4(const uint4 *p) { return __ldg(p); }
+__device__ __forceinline__ uint2 ld2(const uint2 *p) { return __ldg(p); }
 __device__ __forceinline__ uint32_t ld1(const uint32_t *p) { return __ldg(p); }
 
 struct Pick {
@@ -226,6 +229,93 @@ __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lu
     return out;
 }
 
+// ------------------------------------------------------------- MOSS-4Min --
+// Bit of the pair (a, b) in the order (0,1),(0,2),(0,3),(1,2),(1,3),(2,3).
+__device__ __forceinline__ constexpr int pair_bit4(int a, int b) {
+    return a > b ? pair_bit4(b, a) : (a == 0 ? b - 1 : (a == 1 ? b + 1 : 5));
+}
+
+// c(s): 3-paths p0-p1-p2-p3 of the CIS with p0 above p2 and p3 above p1 in the
+// total order.  mask holds the CIS's edges over the roles 0..3, key[] the
+// order keys (d_x << 32) | x; each unordered path is visited once, as the
+// vertex order whose end roles satisfy p0 < p3.
+__device__ __forceinline__ uint32_t centred_paths(uint32_t mask, const uint64_t (&key)[4]) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int e0 = 0; e0 < 4; ++e0) {
+#pragma unroll
+        for (int e3 = e0 + 1; e3 < 4; ++e3) {
+            const int m0 = (e0 != 0 && e3 != 0) ? 0 : ((e0 != 1 && e3 != 1) ? 1 : 2);
+            const int m1 = 6 - e0 - e3 - m0;
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                const int p1 = o ? m1 : m0, p2 = o ? m0 : m1;
+                const bool path = (mask >> pair_bit4(e0, p1) & 1u) && (mask >> pair_bit4(p1, p2) & 1u) &&
+                                  (mask >> pair_bit4(p2, e3) & 1u);
+                c += path && key[e0] > key[p2] && key[e3] > key[p1];
+            }
+        }
+    }
+    return c;
+}
+
+// count slot of a MOSS-4Min hit: 4-cycles 0..3, diamonds 4..9, 4-cliques
+// 10..21 by c; kSlots (not counted) for collisions and the other classes
+__device__ __forceinline__ int min_slot(int cls, uint32_t c) {
+    if (cls == 3 && c >= 1 && c <= 4) return (int)c - 1;
+    if (cls == 5 && c >= 1 && c <= 6) return 4 + (int)c - 1;
+    if (cls == 6 && c >= 1 && c <= 12) return 10 + (int)c - 1;
+    return kSlots;
+}
+
+template <bool HASH>
+__device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
+    Sample out;
+    const Words4 a = philox4x64(s, 0, 3, 0, seed, 0);
+    const Words4 b = philox4x64(s, 1, 3, 0, seed, 0);
+    const uint32_t v = draw_vertex(g.seed[3], g.n, a.x[0], a.x[1]);
+    const uint4 mv = ld4(g.mvert + v);                 // {off, d_v, Gamma-check_v}
+    const uint64_t Gv = ((uint64_t)mv.w << 32) | mv.z;
+    // WeightRandomVertex(N_v, sigma-check^(v)): 32-byte slot records
+    uint32_t j = (uint32_t)word_index(a.x[2], mv.y);
+    uint4 sa = ld4(g.mslot + 2 * (uint64_t)(mv.x + j));
+    const uint64_t y = word_index(a.x[3], Gv);
+    if (!(y < (((uint64_t)sa.y << 32) | sa.x))) {
+        j = sa.z;
+        sa = ld4(g.mslot + 2 * (uint64_t)(mv.x + j));
+    }
+    const uint4 sb = ld4(g.mslot + 2 * (uint64_t)(mv.x + j) + 1);   // {off_u, d_u, d_{v,u}, d_{u,v}}
+    const uint32_t u = sa.w;
+    const uint2 we = ld2(g.rlist + mv.x + (uint32_t)word_index(b.x[0], sb.z));   // w in N_{v,u}
+    const uint2 re = ld2(g.rlist + sb.x + (uint32_t)word_index(b.x[1], sb.w));   // r in N_{u,v}
+    const uint32_t w = we.x, r = re.x;
+    out.v[0] = v; out.v[1] = u; out.v[2] = w; out.v[3] = r; out.v[4] = 0;
+    if (r == u || r == w) {
+        out.cls = 0;
+        return out;
+    }
+    // unknown pairs: v-r, u-w, w-r
+    const uint32_t A[3] = {v, u, w}, B[3] = {r, w, r};
+    uint32_t f;
+    if (HASH) {
+        f = probe_hash<3>(g, A, B);
+    } else {
+        const uint4 vr = make_uint4(mv.x, mv.y, 0u, 0u), ur = make_uint4(sb.x, sb.y, 0u, 0u);
+        const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r);
+        const uint4 ra[3] = {vr, ur, wr}, rb[3] = {rr, wr, rr};
+        f = probe_pairs<3>(g.col, ra, rb, A, B);
+    }
+    // known: v-u, v-w, u-r
+    const uint32_t mask = 0x1u | 0x2u | ((f & 1u) << 2) | (((f >> 1) & 1u) << 3) | 0x10u | (((f >> 2) & 1u) << 5);
+    out.cls = lut[mask];
+    if (out.cls == 3 || out.cls == 5 || out.cls == 6) {
+        const uint64_t key[4] = {((uint64_t)mv.y << 32) | v, ((uint64_t)sb.y << 32) | u, ((uint64_t)we.y << 32) | w,
+                                 ((uint64_t)re.y << 32) | r};
+        out.v[4] = centred_paths(mask, key);
+    }
+    return out;
+}
+
 // Path-5 fallback: u from tau^(v) by a scan, w from mu^(v,u) by a search
 __device__ __noinline__ void path5_fallback(const uint32_t *acc, const uint64_t *q, uint32_t v, uint4 vr, uint64_t x12,
                                             uint64_t x13, uint32_t &iu, uint32_t &iw) {
@@ -322,8 +412,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGr
     __shared__ uint8_t lut[kLut];
     __shared__ uint32_t hist[kWarps][kSlots];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint8_t *src = METHOD == 0 ? g_lut4 : g_lut5;
-    const int lut_n = METHOD == 0 ? 64 : 1024;
+    const uint8_t *src = (METHOD == 0 || METHOD == 3) ? g_lut4 : g_lut5;
+    const int lut_n = (METHOD == 0 || METHOD == 3) ? 64 : 1024;
     for (int i = threadIdx.x; i < lut_n; i += kThreads) lut[i] = src[i];
     for (int i = threadIdx.x; i < kWarps * kSlots; i += kThreads) (&hist[0][0])[i] = 0;
     __syncthreads();
@@ -338,10 +428,11 @@ __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGr
             Sample sm;
             if (METHOD == 0) sm = sample_moss4<HASH>(g, lut, seed, s);
             else if (METHOD == 1) sm = sample_t5<HASH>(g, lut, seed, s);
-            else sm = sample_path5<HASH>(g, lut, seed, s);
-            cls = sm.cls;
+            else if (METHOD == 2) sm = sample_path5<HASH>(g, lut, seed, s);
+            else sm = sample_min<HASH>(g, lut, seed, s);
+            cls = METHOD == 3 ? min_slot(sm.cls, sm.v[4]) : sm.cls;
             if (RECORD) {
-                classes[i] = (uint8_t)cls;
+                classes[i] = (uint8_t)sm.cls;
                 if (verts) {
 #pragma unroll
                     for (int k = 0; k < 5; ++k) verts[5 * i + k] = sm.v[k];
@@ -474,9 +565,12 @@ int sample_blocks(int method, int device) {
     } else if (method == 1) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<1, false, false>, kThreads, 0);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_sample<1, false, true>, kThreads, 0);
-    } else {
+    } else if (method == 2) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<2, false, false>, kThreads, 0);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_sample<2, false, true>, kThreads, 0);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<3, false, false>, kThreads, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_sample<3, false, true>, kThreads, 0);
     }
     if (e != cudaSuccess || per < 1) per = 1;
     if (per_h > per) per = per_h;   // grid sized for the faster (hash) variant
@@ -493,6 +587,8 @@ cudaError_t launch_sample(int method, const DevGraph &g, uint64_t first, uint64_
         case 3: return launch_one<1, true>(g, first, count, seed, partials, blocks, classes, verts, s);
         case 4: return launch_one<2, false>(g, first, count, seed, partials, blocks, classes, verts, s);
         case 5: return launch_one<2, true>(g, first, count, seed, partials, blocks, classes, verts, s);
+        case 6: return launch_one<3, false>(g, first, count, seed, partials, blocks, classes, verts, s);
+        case 7: return launch_one<3, true>(g, first, count, seed, partials, blocks, classes, verts, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -32,45 +32,6 @@ namespace {
 constexpr int kWarp = 32;
 constexpr int kTableThreads = 256;
 
-__device__ __forceinline__ uint64_t shfl_up64(uint64_t v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
-
-__device__ __forceinline__ uint64_t warp_incl_scan64(uint64_t v, int lane) {
-#pragma unroll
-    for (int d = 1; d < kWarp; d <<= 1) {
-        uint64_t t = shfl_up64(v, d);
-        if (lane >= d) v += t;
-    }
-    return v;
-}
-
-
-__device__ __forceinline__ u128 shfl_up_u128(u128 v, int d) {
-    uint64_t lo = __shfl_up_sync(0xffffffffu, (uint64_t)v, d);
-    uint64_t hi = __shfl_up_sync(0xffffffffu, (uint64_t)(v >> 64), d);
-    return ((u128)hi << 64) | lo;
-}
-
-__device__ __forceinline__ u128 shfl_down_u128(u128 v, int d) {
-    uint64_t lo = __shfl_down_sync(0xffffffffu, (uint64_t)v, d);
-    uint64_t hi = __shfl_down_sync(0xffffffffu, (uint64_t)(v >> 64), d);
-    return ((u128)hi << 64) | lo;
-}
-
-__device__ __forceinline__ u128 warp_incl_scan128(u128 v, int lane) {
-#pragma unroll
-    for (int d = 1; d < kWarp; d <<= 1) {
-        u128 t = shfl_up_u128(v, d);
-        if (lane >= d) v += t;
-    }
-    return v;
-}
-
-__device__ __forceinline__ u128 warp_sum128(u128 v) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += shfl_down_u128(v, d);
-    return v;
-}
-
 // ------------------------------------------------------------ vertices ---
 template <typename IdxT>
 __global__ void k_vertices(const IdxT *row_ptr, uint32_t n, uint64_t nnz, uint4 *vert, uint32_t *flags) {
@@ -182,6 +143,7 @@ __global__ void k_totals(const u128 *partials, int blocks, DevTotals *tot) {
         tot->gamma[0] = s[0];
         tot->gamma[1] = s[1];
         tot->gamma[2] = s[2];
+        tot->gamma[3] = 0;    // Gamma-check: set when the MOSS-4Min tables are built
         tot->lambda3 = s[3];
         tot->lambda4 = s[4];
         tot->d_max = (uint32_t)s[5];

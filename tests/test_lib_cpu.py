@@ -59,6 +59,10 @@ def test_argument_checks_before_device():
     assert lib.moss_sample_estimate(None, 4, 10, 1, None, ctypes.byref(r)) == moss.MOSS_EINVAL
     assert lib.moss_build_tables(None, 16, None) == moss.MOSS_EINVAL
     assert lib.moss_sample_counts(None, 0, 0, 1, 1, None, None) == moss.MOSS_EINVAL
+    assert lib.moss_sample_estimate_min(None, 10, 10, 1, None, ctypes.byref(r)) == moss.MOSS_EINVAL
+    K = np.zeros(2, dtype=np.uint64)
+    H = np.zeros(44, dtype=np.uint64)
+    assert lib.moss_finalize_min(None, K.ctypes.data, H.ctypes.data, None, None, ctypes.byref(r)) == moss.MOSS_EINVAL
     lib.moss_graph_free(None)
 
 
@@ -74,4 +78,4 @@ def test_fails_loudly_without_gpu():
 def test_result_struct_layout_matches_header():
     # doubles after uint64 arrays: no padding surprises between C and ctypes
     assert ctypes.sizeof(moss.moss_result) == 4 + 4 + 16 + 2 * 22 * 8 + 22 * 8 * 2 + 2 * 22 * 8 + 16 + 22 * 8
-    assert ctypes.sizeof(moss.moss_stats) == 8 + 8 + 8 + 48 + 16 + 16 + 24 + 16
+    assert ctypes.sizeof(moss.moss_stats) == 8 + 8 + 8 + 64 + 16 + 16 + 32 + 16
