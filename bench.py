@@ -38,9 +38,12 @@ GRAPHS = {
 }
 
 
-def describe(workload: str, k: int) -> tuple[str, str]:
+def describe(workload: str, k: int, mix: bool = False) -> tuple[str, str]:
     """(metric, workload description) of a run."""
     graph, size = GRAPHS[workload]
+    if mix:
+        return (f"4-node samples/s at {size} (MOSS-4 + MOSS-4Min)",
+                f"{graph}, k=4 MOSS-4 and MOSS-4Min with K = K-check, sorted uint32 CSR")
     method = "k=5 (T-5 + Path-5, K1=K2)" if k == 5 else "k=4 (MOSS-4)"
     return f"{k}-node samples/s at {size}", f"{graph}, {method}, sorted uint32 CSR"
 
@@ -57,8 +60,9 @@ def parse():
     p.add_argument("--seed", type=int, default=42)
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
-                   help="single: the one-graph step; batch: many graphs in one persistent launch")
+    p.add_argument("--mode", default="single", choices=["single", "batch", "serve", "min"],
+                   help="single: the one-graph step; batch: many graphs in one persistent launch; serve: "
+                        "the request server; min: the one-graph step of MOSS-4 + MOSS-4Min (k=4)")
     p.add_argument("--graphs", type=int, default=512, help="batch mode: number of graphs")
     p.add_argument("--rate", type=float, default=2000.0, help="serve mode: mean arrivals per second")
     p.add_argument("--duration", type=float, default=2.0, help="serve mode: seconds of arrivals")
@@ -78,6 +82,8 @@ def _oracle_worker(args):
     rp, col = synth.workload(workload)
     t0 = time.perf_counter()
     g = oracle.OracleGraph(rp, col)
+    if any(m == oracle.MOSS4MIN for m, _, _ in shares):
+        g.build_min()
     t1 = time.perf_counter()
     for method, first, count in shares:
         g.run(method, seed, count, first=first)
@@ -85,8 +91,12 @@ def _oracle_worker(args):
     return t1 - t0, t2 - t1, sum(c for _, _, c in shares)
 
 
-def oracle_pass(pool, cores, workload, k, seed, per_worker):
-    methods = [0] if k == 4 else [1, 2]
+def sub_methods(k, mix=False):
+    return ([0, 3] if mix else [0]) if k == 4 else [1, 2]
+
+
+def oracle_pass(pool, cores, workload, k, seed, per_worker, mix=False):
+    methods = sub_methods(k, mix)
     jobs = []
     for w in range(cores):
         shares = [(m, w * per_worker // len(methods), per_worker // len(methods)) for m in methods]
@@ -107,12 +117,14 @@ def oracle_rate(build, sample_wall, samples, budget):
     return budget / (build + budget / rate), rate
 
 
-def calibrate_per_worker(workload, k, seed, seconds):
+def calibrate_per_worker(workload, k, seed, seconds, mix=False):
     import oracle
     import synth
     rp, col = synth.workload(workload)
     g = oracle.OracleGraph(rp, col)
-    methods = [0] if k == 4 else [1, 2]
+    methods = sub_methods(k, mix)
+    if mix:
+        g.build_min()
     n = 20_000
     t0 = time.perf_counter()
     for m in methods:
@@ -131,19 +143,23 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    METRIC, WORKLOAD = describe(args.workload, args.k)
+    mix = args.mode == "min"
+    if mix:
+        args.k = 4
+    METRIC, WORKLOAD = describe(args.workload, args.k, mix)
     cores = os.cpu_count() or 1
-    per_worker = calibrate_per_worker(args.workload, args.k, args.seed, 3.0)
+    per_worker = calibrate_per_worker(args.workload, args.k, args.seed, 3.0, mix)
     with make_pool(cores) as pool:
         for _ in range(args.warmup):
-            oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker)
+            oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker, mix)
         vals, walls = [], []
         for _ in range(args.steps):
-            b, sw, n, wall = oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker)
+            b, sw, n, wall = oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker, mix)
             vals.append(oracle_rate(b, sw, n, args.budget)[0])
             walls.append(wall)
     v = statistics.median(vals)
-    sample = (f"{per_worker * cores} samples per step over {cores} processes (T-5/Path-5 split evenly) plus one "
+    split = "T-5/Path-5" if args.k == 5 else ("MOSS-4/MOSS-4Min" if mix else "MOSS-4")
+    sample = (f"{per_worker * cores} samples per step over {cores} processes ({split} split evenly) plus one "
               f"table build; rate extrapolated to the {args.budget}-sample budget")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": args.gpus,
@@ -217,7 +233,10 @@ def run_gpu(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    METRIC, WORKLOAD = describe(args.workload, args.k)
+    mix = args.mode == "min"
+    if mix:
+        args.k = 4
+    METRIC, WORKLOAD = describe(args.workload, args.k, mix)
     if world != args.gpus:
         raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
     # the CPU-baseline pool is spawned before the first GPU call
@@ -231,7 +250,7 @@ def run_gpu(args):
         tdist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     moss.load()
     k = args.k
-    kmask = 1 << k
+    kmask = (1 << k) | (moss.TABLES_4MIN if mix else 0)
     rp, col = synth.workload(args.workload)
     stream = torch.cuda.current_stream(dev)
     rp_d = torch.from_numpy(rp.view(np.int64)).to(f"cuda:{dev}")
@@ -252,7 +271,10 @@ def run_gpu(args):
         try:
             moss.moss_set_probe(h, probe)
             moss.moss_build_tables(h, kmask, stream)
-            if world == 1:
+            if world == 1 and mix:
+                K4, Km = (K for _, K in sub_budgets(k, args.budget, True))
+                r = moss.result_dict(moss.moss_sample_estimate_min(h, K4, Km, seed, stream))
+            elif world == 1:
                 r = moss.result_dict(moss.moss_sample_estimate(h, k, args.budget, seed, stream))
             else:
                 class _G:  # the weak-scaling helper wants .handle/.device/.stats()
@@ -261,7 +283,7 @@ def run_gpu(args):
                     @staticmethod
                     def stats():
                         return moss.moss_graph_stats(h)
-                r = estimate_weak(_G, k, args.budget, seed, rank, world, allreduce, stream)
+                r = estimate_weak(_G, k, args.budget, seed, rank, world, allreduce, stream, mix)
         finally:
             moss.moss_graph_free(h)
         return r
@@ -324,7 +346,7 @@ def run_gpu(args):
         moss.moss_build_tables(h, kmask, stream)
         counts = torch.zeros(22, dtype=torch.int64, device=f"cuda:{dev}")
         times = {}
-        for m, K in sub_budgets(k, args.budget):
+        for m, K in sub_budgets(k, args.budget, mix):
             moss.moss_sample_counts(h, m, 0, K, args.seed, counts, stream)      # warm
             reps = []
             for rep in range(3):
@@ -342,7 +364,7 @@ def run_gpu(args):
     spath = os.path.join(ROOT, "tests", "golden", f"sectors_{args.workload}.json")
     if os.path.exists(spath):
         sect = json.load(open(spath))
-    name = {0: "MOSS4", 1: "T5", 2: "PATH5"}
+    name = {0: "MOSS4", 1: "T5", 2: "PATH5", 3: "MOSS4MIN"}
     dom = max(times, key=lambda m: times[m][1])
     peaks = {}
     ppath = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -390,18 +412,19 @@ def run_gpu(args):
         "clocks": clk,
         # load 4 (vertices, slots, twins, totals) + build 6 (sigma alias, 4 vertex-table
         # phases, edge hash) + per sub-method sampler and reduce + finalize
-        "gpu_launches": (4 + 6 + 2 * len(sub_budgets(k, args.budget)) + 1) * args.steps,
+        # (+ MOSS-4Min build: 3 sort tiers, slot records, alias tables, total, 4 vertex-table phases)
+        "gpu_launches": (4 + 6 + (10 if mix else 0) + 2 * len(sub_budgets(k, args.budget, mix)) + 1) * args.steps,
         "wall_s_timed": t_wall,
         "step_ms": step_ms,
     }
     if pool is not None:
-        per_worker = calibrate_per_worker(args.workload, k, args.seed, 12.0)
-        b, sw, n, wall = oracle_pass(pool, cores, args.workload, k, args.seed, per_worker)
+        per_worker = calibrate_per_worker(args.workload, k, args.seed, 12.0, mix)
+        b, sw, n, wall = oracle_pass(pool, cores, args.workload, k, args.seed, per_worker, mix)
         v, rate = oracle_rate(b, sw, n, args.budget)
         pool.shutdown()
         out["cpu_baseline"] = {
             "value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
-            "sample": (f"{n} samples ({'T-5/Path-5 evenly' if k == 5 else 'MOSS-4'}) over {cores} processes in "
+            "sample": (f"{n} samples ({'T-5/Path-5 evenly' if k == 5 else ('MOSS-4/MOSS-4Min evenly' if mix else 'MOSS-4')}) over {cores} processes in "
                        f"{sw:.1f} s + table build {b:.2f} s, extrapolated to the {args.budget}-sample budget"),
             "sampling_rate": rate}
     if rank == 0:
@@ -602,7 +625,7 @@ def main():
     elif args.mode == "serve":
         run_serve(args)
     else:
-        run_gpu(args)
+        run_gpu(args)   # single and min
 
 
 if __name__ == "__main__":

@@ -3,7 +3,9 @@
 For each sampled CIS, the set of distinct 32 B sectors the sampling step must
 read under the device layout the library documents (include/moss.h and its
 kernels): vertex alias records and vertex records of 16 B, per-slot sigma
-records of 16 B, neighbour ids of 4 B, ACC entries of 4 B, Q_v of 8 B.  Each
+records of 16 B, neighbour ids of 4 B, ACC entries of 4 B, Q_v of 8 B; for
+MOSS-4Min its vertex records of 16 B, per-slot records of 32 B (one sector)
+and ordered-list entries of 8 B.  Each
 probe is either a lower-bound search with early exit in the shorter sorted
 list (MOSS_PROBE_SEARCH, which also reads the two vertex records) or the home
 bucket of the hashed edge set (MOSS_PROBE_HASH, 16 B buckets; the rare
@@ -69,6 +71,41 @@ class Replay:
         while buckets < len(col):
             buckets <<= 1
         self.shift = 64 - (buckets.bit_length() - 1)
+
+    def min_tables(self):
+        if not hasattr(self, "rank"):
+            rl, rk, cthr, calias, gam, T, al = self.g.min_tables()
+            self.rank, self.cthr_m, self.calias_m = rk.astype(np.int64), cthr, calias.astype(np.int64)
+            self.gam_m = gam
+
+    def sample_min(self, seed, s, verts, cls):
+        """Sectors of one MOSS-4Min sample (Algorithm 2)."""
+        self.min_tables()
+        t = set()
+        x = self.words(3, seed, s, 2)
+        t.add(("seedm", idx(x[0], self.g.n) >> 1))
+        v = int(verts[0])
+        t.add(("mvert", v >> 1))
+        o, d = int(self.rp[v]), int(self.deg[v])
+        j = idx(x[2], d)
+        t.add(("mslot", o + j))
+        if idx(x[3], self.gam_m[v]) >= int(self.cthr_m[o + j]):
+            j = int(self.calias_m[o + j])
+            t.add(("mslot", o + j))
+        u = int(self.col[o + j])
+        dvu = int(self.rank[o + j])
+        ou = int(self.rp[u])
+        duv = int(self.rank[ou + int(np.searchsorted(self.col[ou:self.rp[u + 1]], v))])
+        t.add(("rlist", (o + idx(x[4], dvu)) >> 2))
+        t.add(("rlist", (ou + idx(x[5], duv)) >> 2))
+        w, r = int(verts[2]), int(verts[3])
+        if cls:
+            if self.probe_kind == "search":
+                t.add(("vert", w >> 1))
+                t.add(("vert", r >> 1))
+            for a, b in ((v, r), (u, w), (w, r)):
+                self.probe(a, b, t)
+        return len(t)
 
     def words(self, method, seed, s, blocks):
         out = []
@@ -189,6 +226,12 @@ def model(workload: str, samples: int = 4000, seed: int = 42) -> dict:
             out[name + suffix] = {"sectors_per_sample": float(np.mean(n)),
                                   "stderr": float(np.std(n) / np.sqrt(samples)),
                                   "collision_rate": float(np.mean(cls == 0))}
+        first = 1_000_000
+        _, cls, verts = rep.g.run(oracle.MOSS4MIN, seed, samples, first=first, record=True)
+        n = [rep.sample_min(seed, first + i, verts[i], int(cls[i])) for i in range(samples)]
+        out["MOSS4MIN" + suffix] = {"sectors_per_sample": float(np.mean(n)),
+                                    "stderr": float(np.std(n) / np.sqrt(samples)),
+                                    "collision_rate": float(np.mean(cls == 0))}
     return out
 
 

@@ -12,7 +12,8 @@ from typing import Callable
 
 import numpy as np
 
-from . import (MOSS4, NSLOTS, PATH5, T5, moss_finalize, moss_sample_counts, result_dict)
+from . import (MOSS4, MOSS4MIN, NSLOTS, PATH5, T5, moss_finalize, moss_finalize_min, moss_sample_counts,
+               result_dict)
 
 
 def shard(total: int, rank: int, world: int) -> tuple[int, int]:
@@ -25,20 +26,24 @@ def shard(total: int, rank: int, world: int) -> tuple[int, int]:
     return first, base + (1 if rank < extra else 0)
 
 
-def sub_budgets(k: int, budget: int) -> list[tuple[int, int]]:
-    """(method, samples) per sub-method for one estimate (K1 = K2, Sec. 5.1.5)."""
+def sub_budgets(k: int, budget: int, mix: bool = False) -> list[tuple[int, int]]:
+    """(method, samples) per sub-method for one estimate: K1 = K2 for k = 5
+    (Sec. 5.1.5); with mix (k = 4), MOSS-4 and MOSS-4Min share the budget
+    evenly (Sec. 4.2)."""
+    if k == 4 and mix:
+        return [(MOSS4, budget // 2), (MOSS4MIN, budget - budget // 2)]
     if k == 4:
         return [(MOSS4, budget)]
     return [(T5, budget // 2), (PATH5, budget - budget // 2)]
 
 
-def weak_ranges(k: int, budget: int, rank: int) -> list[tuple[int, int, int]]:
+def weak_ranges(k: int, budget: int, rank: int, mix: bool = False) -> list[tuple[int, int, int]]:
     """(method, first, count) of rank ``rank`` when every rank draws ``budget``."""
-    return [(m, rank * K, K) for m, K in sub_budgets(k, budget)]
+    return [(m, rank * K, K) for m, K in sub_budgets(k, budget, mix)]
 
 
 def estimate_weak(g, k: int, budget: int, seed: int, rank: int, world: int,
-                  allreduce: Callable[[np.ndarray], np.ndarray], stream=None) -> dict:
+                  allreduce: Callable[[np.ndarray], np.ndarray], stream=None, mix: bool = False) -> dict:
     """One weak-scaled estimate: this rank's counts, summed over ranks by
     ``allreduce`` (int64[2, 22] -> int64[2, 22]), then the device finalize.
     Methods whose total weight is zero draw nothing (as in the single call)."""
@@ -47,10 +52,13 @@ def estimate_weak(g, k: int, budget: int, seed: int, rank: int, world: int,
     stats = g.stats()
     counts = torch.zeros((2, NSLOTS), dtype=torch.int64, device=f"cuda:{g.device}")
     K = [0, 0]
-    for slot, (m, first, count) in enumerate(weak_ranges(k, budget, rank)):
+    for slot, (m, first, count) in enumerate(weak_ranges(k, budget, rank, mix)):
         if stats.gamma[m][0] == 0 and stats.gamma[m][1] == 0:
             continue
         moss_sample_counts(g.handle, m, first, count, seed, counts[slot], stream)
         K[slot] = count * world
     total = allreduce(counts.cpu().numpy())
-    return result_dict(moss_finalize(g.handle, k, np.array(K, dtype=np.uint64), total.astype(np.uint64), stream))
+    Ka, Ha = np.array(K, dtype=np.uint64), total.astype(np.uint64)
+    if mix:
+        return result_dict(moss_finalize_min(g.handle, Ka, Ha, stream))
+    return result_dict(moss_finalize(g.handle, k, Ka, Ha, stream))
