@@ -323,11 +323,13 @@ int moss_graph_stats(const moss_graph *g, moss_stats *out);
  *   MOSS_TABLE_SLOT   nnz x {uint32 col, sigma threshold, sigma alias
  *                            (position in N_v), twin (position of v in N_col)}
  *   MOSS_TABLE_ACC    nnz x uint32 ACC_sigma^(v) exclusive prefix (Sec. 4.1.3)
- *   MOSS_TABLE_SEED0+l n x {uint64 threshold T, uint32 alias, uint32 0},
+ *   MOSS_TABLE_SEED0+l n x {uint64 threshold T, uint32 alias, uint32 0,
+ *                      then the alias's MOSS_TABLE_VERT record} (32 bytes),
  *                      l = 0 pi, 1 rho^(1), 2 rho^(2)
  *   MOSS_TABLE_GAMMA0+l n x {uint64 lo, hi} vertex weight of table l
  * and, after a build with MOSS_TABLES_4MIN (Sec. 4.2):
- *   MOSS_TABLE_MIN_SEED  n x {uint64 threshold T, uint32 alias, uint32 0} of pi-check
+ *   MOSS_TABLE_MIN_SEED  n x {uint64 threshold T, uint32 alias, uint32 0, then
+ *                        the alias's MOSS_TABLE_MIN_VERT record} of pi-check
  *   MOSS_TABLE_MIN_GAMMA n x {uint64 lo, hi} Gamma-check_v
  *   MOSS_TABLE_MIN_VERT  n x {uint32 off, deg, Gamma-check_v lo, hi}
  *   MOSS_TABLE_MIN_SLOT  nnz x {uint64 sigma-check threshold, uint32 alias

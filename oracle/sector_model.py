@@ -2,10 +2,12 @@
 
 For each sampled CIS, the set of distinct 32 B sectors the sampling step must
 read under the device layout the library documents (include/moss.h and its
-kernels): vertex alias records and vertex records of 16 B, per-slot sigma
-records of 16 B, neighbour ids of 4 B, ACC entries of 4 B, Q_v of 8 B; for
-MOSS-4Min its vertex records of 16 B, per-slot records of 32 B (one sector)
-and ordered-list entries of 8 B.  Each
+kernels): vertex alias records of 32 B (one sector, carrying the alias's
+vertex record, so the drawn vertex's own 16 B record is read only when the
+column keeps the draw), per-slot sigma records of 16 B, vertex records of
+16 B, neighbour ids of 4 B, ACC entries of 4 B, Q_v of 8 B; for MOSS-4Min its
+vertex records of 16 B, per-slot records of 32 B (one sector) and
+ordered-list entries of 8 B.  Each
 probe is either a lower-bound search with early exit in the shorter sorted
 list (MOSS_PROBE_SEARCH, which also reads the two vertex records) or the home
 bucket of the hashed edge set (MOSS_PROBE_HASH, 16 B buckets; the rare
@@ -77,15 +79,18 @@ class Replay:
             rl, rk, cthr, calias, gam, T, al = self.g.min_tables()
             self.rank, self.cthr_m, self.calias_m = rk.astype(np.int64), cthr, calias.astype(np.int64)
             self.gam_m = gam
+            self.seed_m = T
 
     def sample_min(self, seed, s, verts, cls):
         """Sectors of one MOSS-4Min sample (Algorithm 2)."""
         self.min_tables()
         t = set()
         x = self.words(3, seed, s, 2)
-        t.add(("seedm", idx(x[0], self.g.n) >> 1))
+        c = idx(x[0], self.g.n)
+        t.add(("seedm", c))
         v = int(verts[0])
-        t.add(("mvert", v >> 1))
+        if x[1] < int(self.seed_m[c]):   # the column keeps the draw: its own record
+            t.add(("mvert", v >> 1))
         o, d = int(self.rp[v]), int(self.deg[v])
         j = idx(x[2], d)
         t.add(("mslot", o + j))
@@ -149,9 +154,10 @@ class Replay:
         T, al = self.seed[method]
         x = self.words(method, seed, s, 4)
         c = idx(x[0], self.g.n)
-        t.add(("seed", c >> 1))
+        t.add(("seed", c))
         v = int(verts[0])
-        t.add(("vert", v >> 1))
+        if x[1] < int(T[c]):   # the column keeps the draw: its own vertex record
+            t.add(("vert", v >> 1))
         o = int(self.rp[v])
         if method == 2:
             iu = self.sigma(v, x[4], x[5], t)
@@ -214,8 +220,9 @@ class Replay:
 def model(workload: str, samples: int = 4000, seed: int = 42) -> dict:
     rp, col = synth.workload(workload)
     out = {"workload": workload, "samples": samples, "seed": seed,
-           "layout": ("16 B vertex/alias/slot records, 4 B ids and ACC, 8 B Q, 16 B edge-hash buckets "
-                      "(home bucket counted); 32 B sectors"),
+           "layout": ("32 B vertex alias records with the alias's vertex record, 16 B vertex/slot records, "
+                      "4 B ids and ACC, 8 B Q, 16 B edge-hash buckets (home bucket counted); MOSS-4Min: 16 B "
+                      "vertex, 32 B slot, 8 B list records; 32 B sectors"),
            "source": "written by oracle/sector_model.py"}
     for probe, suffix in (("search", "_search"), ("hash", "_hash")):
         rep = Replay(rp, col, probe)

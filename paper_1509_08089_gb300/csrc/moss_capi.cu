@@ -362,7 +362,7 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
             g->q = c.take<uint64_t>(n);
             for (int l = 0; l < 3; ++l) {
                 g->gam[l] = c.take<u128>(n);
-                g->seed[l] = c.take<uint4>(n);
+                g->seed[l] = c.take<uint4>(2 * (uint64_t)n);
             }
             g->tot = c.take<DevTotals>(1);
             g->partials = c.take<uint64_t>((uint64_t)prow * kSlots + (uint64_t)blocks * 6 * 2);
@@ -418,7 +418,7 @@ static int build_min_tables(moss_graph *g, cudaStream_t s) {
             g->mslot = c.take<uint4>(2 * g->nnz);
             g->rlist = c.take<uint2>(g->nnz);
             g->gam[3] = c.take<u128>(g->n);
-            g->seed[3] = c.take<uint4>(g->n);
+            g->seed[3] = c.take<uint4>(2 * (uint64_t)g->n);
         }
     }
     void *scratch = nullptr;
@@ -454,6 +454,7 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
     int which[3], nt = 0;
     u128 *w[3];
     uint4 *seed[3];
+    const uint4 *vrec[3] = {g->vert, g->vert, g->vert};
     for (int l = 0; l < 3; ++l) {
         const bool want = (l == 0 && (k_mask & (1u << 4))) || (l > 0 && (k_mask & (1u << 5)));
         if (want) {
@@ -463,7 +464,8 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
             ++nt;
         }
     }
-    if (e == cudaSuccess && nt > 0) e = launch_seed_alias(g->n, g->tot, nt, which, w, seed, scratch, g->flags, s);
+    if (e == cudaSuccess && nt > 0)
+        e = launch_seed_alias(g->n, g->tot, nt, which, w, seed, vrec, scratch, g->flags, s);
     cudaFreeAsync(scratch, s);
     bool hashed = false;
     if (e == cudaSuccess && g->probe == MOSS_PROBE_HASH) {
@@ -696,14 +698,14 @@ int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t b
     else if (table >= MOSS_TABLE_SEED0 && table < MOSS_TABLE_SEED0 + 3) {
         if (!(g->built >> (table - MOSS_TABLE_SEED0) & 1u)) return fail(MOSS_ESTATE, "vertex table not built");
         src = g->seed[table - MOSS_TABLE_SEED0];
-        need = (uint64_t)g->n * 16;
+        need = (uint64_t)g->n * 32;
     } else if (table >= MOSS_TABLE_GAMMA0 && table < MOSS_TABLE_GAMMA0 + 3) {
         src = g->gam[table - MOSS_TABLE_GAMMA0];
         need = (uint64_t)g->n * 16;
     } else if (table >= MOSS_TABLE_MIN_SEED && table <= MOSS_TABLE_MIN_LIST) {
         if (!(g->built >> 5 & 1u)) return fail(MOSS_ESTATE, "MOSS-4Min tables not built");
         switch (table) {
-            case MOSS_TABLE_MIN_SEED: src = g->seed[3]; need = (uint64_t)g->n * 16; break;
+            case MOSS_TABLE_MIN_SEED: src = g->seed[3]; need = (uint64_t)g->n * 32; break;
             case MOSS_TABLE_MIN_GAMMA: src = g->gam[3]; need = (uint64_t)g->n * 16; break;
             case MOSS_TABLE_MIN_VERT: src = g->mvert; need = (uint64_t)g->n * 16; break;
             case MOSS_TABLE_MIN_SLOT: src = g->mslot; need = g->nnz * 32; break;

@@ -10,8 +10,11 @@
 //   acc[nnz]  uint32 ACC_sigma^(v) exclusive prefix of (d_x - 1) within N_v
 //   q[n]      uint64 Q_v = sum (d_x - 1)^2   (Gamma^(2)_v = S_v^2 - Q_v)
 //   gam[l][n] u128 vertex weights Gamma_v, Gamma^(1)_v, Gamma^(2)_v
-//   seed[l][n] uint4 {T lo, T hi, alias, 0}: vertex alias table of weight l,
-//             keep the column when x < T for a 64-bit word x.
+//   seed[l][2n] two uint4 per column c, one 32-byte sector: {T lo, T hi,
+//             alias, 0} -- vertex alias table of weight l, keep the column when
+//             x < T for a 64-bit word x -- and a copy of the alias's vertex
+//             record (vert, or mvert for MOSS-4Min), so that a draw that takes
+//             the alias (most draws for skewed weights) needs no second load.
 // MOSS-4Min (Sec. 4.2), built on request:
 //   mvert[n]  uint4 {off, deg, Gamma-check_v lo, hi}
 //   mslot[2 nnz] two uint4 per slot (v -> u), one 32-byte sector:
@@ -186,10 +189,12 @@ cudaError_t launch_edge_hash(uint64_t nnz, const uint32_t *col, const uint32_t *
                              uint32_t mask, uint32_t shift, cudaStream_t s);
 cudaError_t launch_sigma_alias(uint32_t n, const uint4 *vert, const uint32_t *acc, uint4 *slot,
                                uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s);
-// vertex alias tables of up to 3 weights in the same launches; scratch of
+// vertex alias tables of up to 3 weights in the same launches (seed[t]: 2n
+// uint4, vrec[t]: the n vertex records copied beside each alias); scratch of
 // seed_scratch_bytes(n) bytes
 cudaError_t launch_seed_alias(uint32_t n, const DevTotals *tot, int ntables, const int *which, u128 *const *w,
-                              uint4 *const *seed, void *scratch, uint32_t *flags, cudaStream_t s);
+                              uint4 *const *seed, const uint4 *const *vrec, void *scratch, uint32_t *flags,
+                              cudaStream_t s);
 uint64_t seed_scratch_bytes(uint32_t n);
 int table_blocks(uint32_t n);
 

@@ -18,6 +18,7 @@
 // used for sigma^(v) in moss_tables.cu, here in 128-bit arithmetic since
 // q_j = w_j d_v can exceed 2^64; the exact total Gamma-check; and the vertex
 // alias table of pi-check through the seed-table kernels.
+#include "moss_alias.cuh"
 #include "moss_internal.cuh"
 
 namespace moss {
@@ -28,6 +29,7 @@ constexpr int kWarp = 32;
 constexpr uint32_t kTile = 4096;      // keys sorted per shared-memory pass (32 KB)
 constexpr int kSortThreads = 512;
 constexpr int kListThreads = 256;
+constexpr uint32_t kLongList = 256;   // longer lists: k_min_alias_long, a block per list
 
 __device__ __forceinline__ uint64_t order_key(uint32_t x, uint32_t dx) { return ((uint64_t)dx << 32) | x; }
 
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(kListThreads) k_min_alias(uint32_t n, const ui
             gmin[v] = W;
             total += W;
         }
-        if (d == 0) continue;
+        if (d == 0 || (d > kLongList && W != 0)) continue;
         if (W == 0) {   // never drawn: keep every column
             for (uint32_t j = lane; j < d; j += kWarp) {
                 m32[8 * ((uint64_t)o + j) + 0] = 0;
@@ -340,6 +342,27 @@ __global__ void __launch_bounds__(kListThreads) k_min_alias(uint32_t n, const ui
     }
 }
 
+// the alias tables of lists longer than kLongList, a block per list, after
+// k_min_alias has written Gamma-check_v into mvert
+__global__ void __launch_bounds__(kListThreads) k_min_alias_long(uint32_t n, const uint4 *__restrict__ vert,
+                                                                const uint4 *__restrict__ mvert, uint4 *mslot,
+                                                                uint32_t *idx, u128 *pre) {
+    uint32_t *m32 = reinterpret_cast<uint32_t *>(mslot);
+    for (uint64_t v = blockIdx.x; v < n; v += gridDim.x) {
+        const uint4 mv = mvert[v];
+        const uint32_t o = mv.x, d = mv.y;
+        const uint64_t W = ((uint64_t)mv.w << 32) | mv.z;
+        if (d <= kLongList || W == 0) continue;   // block-uniform
+        block_alias<u128, kListThreads>(
+            d, (u128)W, [&](uint32_t j) { return (u128)min_weight(mslot, (uint64_t)o + j); }, idx + o, pre + o,
+            [&](uint32_t j, u128 thr, uint32_t alias) {
+                m32[8 * ((uint64_t)o + j) + 0] = (uint32_t)thr;
+                m32[8 * ((uint64_t)o + j) + 1] = (uint32_t)((uint64_t)thr >> 32);
+                m32[8 * ((uint64_t)o + j) + 2] = alias;
+            });
+    }
+}
+
 __global__ void k_min_total(const u128 *partials, int blocks, DevTotals *tot) {
     const int lane = threadIdx.x;   // one warp
     u128 s = 0;
@@ -413,12 +436,16 @@ cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const
     k_min_alias<<<ab, kListThreads, 0, s>>>(n, vert, mslot, mvert, gmin, m.rank, reinterpret_cast<u128 *>(m.a),
                                              m.partials);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_min_alias_long<<<grid_for((uint64_t)n, 1, 4), kListThreads, 0, s>>>(n, vert, mvert, mslot, m.rank,
+                                                                          reinterpret_cast<u128 *>(m.a));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_min_total<<<1, kWarp, 0, s>>>(m.partials, (int)ab, tot);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int which[1] = {3};
     u128 *w[1] = {gmin};
     uint4 *sd[1] = {seed_min};
-    return launch_seed_alias(n, tot, 1, which, w, sd, m.seed, flags, s);
+    const uint4 *vr[1] = {mvert};
+    return launch_seed_alias(n, tot, 1, which, w, sd, vr, m.seed, flags, s);
 }
 
 }  // namespace moss

@@ -23,6 +23,7 @@
 // Both prefix sums and every search are parallel, so the per-list tables
 // (a warp per list) and the vertex tables (a block scan over V, then one
 // thread per item) are built without a sequential pass.
+#include "moss_alias.cuh"
 #include "moss_internal.cuh"
 
 namespace moss {
@@ -31,6 +32,9 @@ namespace {
 
 constexpr int kWarp = 32;
 constexpr int kTableThreads = 256;
+constexpr uint32_t kLongList = 256;   // longer lists get a block each in the alias passes
+constexpr int kUnroll = 4;            // chunks of 32 slots per round in k_slots
+constexpr int kLongThreads = 256;
 
 // ------------------------------------------------------------ vertices ---
 template <typename IdxT>
@@ -62,28 +66,40 @@ __global__ void __launch_bounds__(kTableThreads) k_slots(uint32_t n, const uint3
         const uint4 vr = vert[v];
         const uint32_t o = vr.x, d = vr.y;
         uint64_t run = 0, qsum = 0;
-        for (uint32_t base = 0; base < d; base += kWarp) {
-            const uint32_t i = base + lane;
-            uint32_t x = 0, w = 0;
-            if (i < d) {
-                x = col[o + i];
-                if (x >= n) {
-                    err |= kErrRange;
-                } else {
-                    if (x == v) err |= kErrSelf;
-                    if (i > 0 && col[o + i - 1] >= x) err |= kErrOrder;
-                    const uint32_t dx = vert[x].y;
-                    w = dx ? dx - 1 : 0;
+        // kUnroll chunks of 32 per round: their gathers of d_x are issued
+        // together, so a hub's list costs d / (32 kUnroll) round trips
+        for (uint32_t base = 0; base < d; base += kWarp * kUnroll) {
+            uint32_t x[kUnroll], w[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const uint32_t i = base + u * kWarp + lane;
+                x[u] = 0;
+                w[u] = 0;
+                if (i < d) {
+                    x[u] = col[o + i];
+                    if (x[u] >= n) {
+                        err |= kErrRange;
+                    } else {
+                        if (x[u] == v) err |= kErrSelf;
+                        if (i > 0 && col[o + i - 1] >= x[u]) err |= kErrOrder;
+                        const uint32_t dx = vert[x[u]].y;
+                        w[u] = dx ? dx - 1 : 0;
+                    }
                 }
             }
-            uint64_t incl = warp_incl_scan64(w, lane);
-            if (i < d) {
-                acc[o + i] = (uint32_t)(run + incl - w);
-                slot[o + i] = make_uint4(x, 0u, 0u, 0u);
-                owner[o + i] = (uint32_t)v;
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                if (base + u * kWarp >= d) break;   // warp-uniform
+                const uint32_t i = base + u * kWarp + lane;
+                const uint64_t incl = warp_incl_scan64(w[u], lane);
+                if (i < d) {
+                    acc[o + i] = (uint32_t)(run + incl - w[u]);
+                    slot[o + i] = make_uint4(x[u], 0u, 0u, 0u);
+                    owner[o + i] = (uint32_t)v;
+                }
+                run += __shfl_sync(0xffffffffu, incl, 31);
+                qsum += (uint64_t)w[u] * w[u];
             }
-            run += __shfl_sync(0xffffffffu, incl, 31);
-            qsum += (uint64_t)w * w;
         }
 #pragma unroll
         for (int s = 16; s > 0; s >>= 1) qsum += __shfl_down_sync(0xffffffffu, qsum, s);
@@ -224,7 +240,7 @@ __global__ void __launch_bounds__(kTableThreads) k_sigma_alias(uint32_t n, const
     for (uint64_t v = (uint64_t)blockIdx.x * wpb + warp; v < n; v += (uint64_t)gridDim.x * wpb) {
         const uint4 vr = vert[v];
         const uint32_t o = vr.x, d = vr.y, S = vr.z;
-        if (d == 0) continue;
+        if (d == 0 || (d > kLongList && S != 0)) continue;   // long lists: k_sigma_alias_long
         uint32_t *slot32 = reinterpret_cast<uint32_t *>(slot);
         if (S == 0) {  // never drawn (Gamma_v = 0): keep every column
             for (uint32_t p = lane; p < d; p += kWarp) {
@@ -322,6 +338,24 @@ __global__ void __launch_bounds__(kTableThreads) k_sigma_alias(uint32_t n, const
     }
 }
 
+// lists longer than kLongList: a block per list (moss_alias.cuh)
+__global__ void __launch_bounds__(kLongThreads) k_sigma_alias_long(uint32_t n, const uint4 *__restrict__ vert,
+                                                                  const uint32_t *__restrict__ acc, uint4 *slot,
+                                                                  uint32_t *idx, uint64_t *pre) {
+    uint32_t *slot32 = reinterpret_cast<uint32_t *>(slot);
+    for (uint64_t v = blockIdx.x; v < n; v += gridDim.x) {
+        const uint4 vr = vert[v];
+        const uint32_t o = vr.x, d = vr.y, S = vr.z;
+        if (d <= kLongList || S == 0) continue;   // block-uniform
+        block_alias<uint64_t, kLongThreads>(
+            d, (uint64_t)S, [&](uint32_t j) { return (uint64_t)acc_weight(acc, o, d, S, j); }, idx + o, pre + o,
+            [&](uint32_t j, uint64_t thr, uint32_t alias) {
+                slot32[4 * (uint64_t)(o + j) + 1] = (uint32_t)thr;
+                slot32[4 * (uint64_t)(o + j) + 2] = alias;
+            });
+    }
+}
+
 // ---------------------------------------------------- vertex (seed) tables ---
 constexpr int kSeedThreads = 256;
 constexpr int kSeedRounds = 16;                              // items per thread per block
@@ -341,7 +375,8 @@ struct alignas(16) SeedAgg {
 // One vertex table being built: weights, output, and its scratch.
 struct SeedTask {
     const u128 *w;
-    uint4 *seed;
+    uint4 *seed;       // 2 per column: {T, alias, 0} and the alias's vertex record
+    const uint4 *vrec; // vertex records copied into seed
     uint32_t *idx;     // n: lights from the front, heavies from the back
     u128 *pre;         // n: A_i (lights) / P_k (heavies)
     SeedSplit *split;
@@ -540,7 +575,8 @@ __global__ void k_seed_fill(uint32_t n, const DevTotals *tot, SeedTasks tasks) {
     const u128 Ptot = T.split->total;
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
         if (W == 0) {
-            T.seed[p] = make_uint4(0u, 0u, (uint32_t)p, 0u);
+            T.seed[2 * p] = make_uint4(0u, 0u, (uint32_t)p, 0u);
+            T.seed[2 * p + 1] = T.vrec[p];
             continue;
         }
         const uint32_t j = idx[p];
@@ -573,7 +609,8 @@ __global__ void k_seed_fill(uint32_t n, const DevTotals *tot, SeedTasks tasks) {
             }
         }
         const uint64_t Tq = quantize64(thr, W);
-        T.seed[j] = make_uint4((uint32_t)Tq, (uint32_t)(Tq >> 32), alias, 0u);
+        T.seed[2 * (uint64_t)j] = make_uint4((uint32_t)Tq, (uint32_t)(Tq >> 32), alias, 0u);
+        T.seed[2 * (uint64_t)j + 1] = T.vrec[alias];
     }
 }
 
@@ -605,6 +642,14 @@ cudaError_t launch_vertices(const void *row_ptr, int is64, uint32_t n, uint64_t 
         k_vertices<uint32_t><<<(unsigned)blocks, threads, 0, s>>>(static_cast<const uint32_t *>(row_ptr), n, nnz,
                                                                    vert, flags);
     return cudaGetLastError();
+}
+
+static unsigned long_blocks(uint32_t n) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t cap = (uint64_t)sms * 4;
+    return (unsigned)(n < cap ? (n ? n : 1) : cap);
 }
 
 static unsigned flat_blocks(uint64_t items) {
@@ -642,6 +687,9 @@ cudaError_t launch_edge_hash(uint64_t nnz, const uint32_t *col, const uint32_t *
 cudaError_t launch_sigma_alias(uint32_t n, const uint4 *vert, const uint32_t *acc, uint4 *slot,
                                uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s) {
     k_sigma_alias<<<table_blocks(n), kTableThreads, 0, s>>>(n, vert, acc, slot, scratch_idx, scratch_pre);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sigma_alias_long<<<long_blocks(n), kLongThreads, 0, s>>>(n, vert, acc, slot, scratch_idx, scratch_pre);
     return cudaGetLastError();
 }
 
@@ -653,7 +701,8 @@ uint64_t seed_scratch_bytes(uint32_t n) {
 }
 
 cudaError_t launch_seed_alias(uint32_t n, const DevTotals *tot, int ntables, const int *which, u128 *const *w,
-                              uint4 *const *seed, void *scratch, uint32_t *flags, cudaStream_t s) {
+                              uint4 *const *seed, const uint4 *const *vrec, void *scratch, uint32_t *flags,
+                              cudaStream_t s) {
     if (ntables < 1 || ntables > 3) return cudaErrorInvalidValue;
     const uint32_t chunks = (uint32_t)(((uint64_t)n + kSeedChunk - 1) / kSeedChunk);
     SeedTasks tasks = {};
@@ -667,6 +716,7 @@ cudaError_t launch_seed_alias(uint32_t n, const DevTotals *tot, int ntables, con
         SeedTask &T = tasks.t[t];
         T.w = w[t];
         T.seed = seed[t];
+        T.vrec = vrec[t];
         T.which = which[t];
         T.idx = reinterpret_cast<uint32_t *>(take((uint64_t)n * 4));
         T.pre = reinterpret_cast<u128 *>(take((uint64_t)n * 16));

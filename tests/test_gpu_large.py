@@ -41,10 +41,11 @@ def test_large_tables_bit_exact(big):
     assert np.array_equal(col[rp.astype(np.int64)[col.astype(np.int64)] + slot[:, 3].astype(np.int64)], owner)
     for l in range(3):
         _, T, salias = og.seed_table(l)
-        seed = moss.moss_table_export(g.handle, moss.TABLE_SEED0 + l, np.zeros((n, 4), dtype=np.uint32))
+        seed = moss.moss_table_export(g.handle, moss.TABLE_SEED0 + l, np.zeros((n, 8), dtype=np.uint32))
         Tg = seed[:, 0].astype(np.uint64) | (seed[:, 1].astype(np.uint64) << np.uint64(32))
         assert np.array_equal(Tg, T), l
         assert np.array_equal(seed[:, 2], salias), l
+        assert np.array_equal(seed[:, 4:8], vert[salias.astype(np.int64)]), l
     st = g.stats()
     for l in range(3):
         assert (int(st.gamma[l][0]) | (int(st.gamma[l][1]) << 64)) == og.Gamma[l]

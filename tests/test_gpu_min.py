@@ -114,9 +114,10 @@ def test_min_tables_bit_exact(name):
     assert [int(x) for x in gv] == gam
     gw = moss.moss_table_export(g.handle, moss.TABLE_MIN_GAMMA, np.zeros((n, 2), dtype=np.uint64))
     assert [int(a) | (int(b) << 64) for a, b in gw] == gam
-    seed = moss.moss_table_export(g.handle, moss.TABLE_MIN_SEED, np.zeros((n, 4), dtype=np.uint32))
+    seed = moss.moss_table_export(g.handle, moss.TABLE_MIN_SEED, np.zeros((n, 8), dtype=np.uint32))
     assert np.array_equal(u64(seed[:, 0], seed[:, 1]), T)
     assert np.array_equal(seed[:, 2], alias)
+    assert np.array_equal(seed[:, 4:8], mv[alias.astype(np.int64)])
     st = g.stats()
     assert (int(st.gamma[3][0]) | (int(st.gamma[3][1]) << 64)) == og.Gamma_min
 

@@ -90,10 +90,12 @@ def test_tables_bit_exact(name):
         assert np.array_equal(col[rp.astype(np.int64)[c64] + slot[:, 3].astype(np.int64)].astype(np.int64), owner)
     for l in range(3):
         sthr, T, salias = og.seed_table(l)
-        seed = moss.moss_table_export(g.handle, moss.TABLE_SEED0 + l, np.zeros((n, 4), dtype=np.uint32))
+        seed = moss.moss_table_export(g.handle, moss.TABLE_SEED0 + l, np.zeros((n, 8), dtype=np.uint32))
         Tg = seed[:, 0].astype(np.uint64) | (seed[:, 1].astype(np.uint64) << np.uint64(32))
         assert np.array_equal(Tg, T), l
         assert np.array_equal(seed[:, 2], salias), l
+        # the alias's vertex record rides in the second half of the column record
+        assert np.array_equal(seed[:, 4:8], vert[salias.astype(np.int64)]), l
         gw = moss.moss_table_export(g.handle, moss.TABLE_GAMMA0 + l, np.zeros((n, 2), dtype=np.uint64))
         assert u128(gw) == gam[l]
     st = g.stats()
