@@ -206,6 +206,125 @@ __device__ void finalize_one(const FinalizeIn &in, const uint64_t *hits0, const 
     *out = r;
 }
 
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// MOSS-5 with one warp: lane i is class i (1..21); the sums over classes
+// (the eta_2 identity, its variance, the concentrations) are warp sums.  Same
+// arithmetic as the k = 5 branch of finalize_one, which it replaces on the
+// launch paths; only the order of those sums differs.
+__device__ void finalize5_warp(const FinalizeIn &in, const uint64_t *hits0, const uint64_t *hits1,
+                               const DevTotals *tot, moss_result *out, double *cov) {
+    const int i = threadIdx.x & 31;
+    const bool cls = i >= 1 && i <= 21;
+    const double G0 = u128_to_double(tot->gamma[1]), G1 = u128_to_double(tot->gamma[2]);
+    const double K0 = (double)in.K[0], K1 = (double)in.K[1];
+    const bool av0 = in.K[0] > 0 && G0 > 0, av1 = in.K[1] > 0 && G1 > 0;
+    const uint64_t h0 = (i < kSlots && hits0) ? hits0[i] : 0, h1 = (i < kSlots && hits1) ? hits1[i] : 0;
+    const double f0 = cls ? kPhi5[i - 1][0] : 0.0, f1 = cls ? kPhi5[i - 1][1] : 0.0, f3 = cls ? kPhi5[i - 1][2] : 0.0;
+    const bool s0 = av0 && f0 > 0, s1 = av1 && f1 > 0;
+    double p0 = 0.0, p1 = 0.0, e0 = 0.0, e1 = 0.0;
+    if (s0) {
+        p0 = 2.0 * f0 / G0;                               // Theorem 6
+        e0 = (double)h0 / (K0 * p0);
+    }
+    if (s1) {
+        p1 = 2.0 * f1 / G1;                               // Theorem 8
+        e1 = (double)h1 / (K1 * p1);
+    }
+    double est = 0.0, var = 0.0, plug = 0.0, a0 = 0.0, a1 = 0.0;
+    if (cls && i != 2 && (s0 || s1)) {
+        if (s0 != s1) {
+            const double e = s0 ? e0 : e1, K = s0 ? K0 : K1, p = s0 ? p0 : p1;
+            plug = e;
+            est = e;
+            var = e / K * (1.0 / p - e);                  // Theorems 7, 9
+            if (s0) a0 = 1.0; else a1 = 1.0;
+        } else {
+            const double e = ((double)h0 + (double)h1) / (K0 * p0 + K1 * p1);
+            plug = e;
+            const double V1 = fmax(e / K0 * (1.0 / p0 - e), 0.0);
+            const double V2 = fmax(e / K1 * (1.0 / p1 - e), 0.0);
+            if (V1 + V2 > 0.0) {
+                a0 = V2 / (V1 + V2);
+                a1 = V1 / (V1 + V2);
+                var = V1 * V2 / (V1 + V2);                // Theorem 10
+            } else {
+                a0 = a1 = 0.5;
+                var = 0.0;
+            }
+            est = a0 * e0 + a1 * e1;
+        }
+    }
+    // eta_2 = Lambda_4 - sum_{Omega_3*} phi^(3)_i eta_i and its variance
+    const bool om3 = cls && i != 2 && f3 > 0;
+    const double s = warp_sum_d(om3 ? f3 * est : 0.0);
+    double v2 = warp_sum_d(om3 ? f3 * f3 * var : 0.0);
+    // sum_{i != j} phi_i phi_j Cov(i, j), Cov = -sum_l b_i b_j / K_l with
+    // b_i = phi_i a^(l)_i plug_i: per l, (sum b)^2 - sum b^2
+    const double b0 = om3 ? f3 * (a0 * plug) : 0.0, b1 = om3 ? f3 * (a1 * plug) : 0.0;
+    const double sb0 = warp_sum_d(b0), sbb0 = warp_sum_d(b0 * b0);
+    const double sb1 = warp_sum_d(b1), sbb1 = warp_sum_d(b1 * b1);
+    if (av0) v2 -= (sb0 * sb0 - sbb0) / K0;
+    if (av1) v2 -= (sb1 * sb1 - sbb1) / K1;
+    if (i == 2) {
+        est = u128_to_double(tot->lambda4) - s;
+        var = v2;
+    }
+    const double t = warp_sum_d(cls ? est : 0.0);         // concentrations (Sec. 6.3)
+    if (i < kSlots) {
+        out->hits[0][i] = h0;
+        out->hits[1][i] = h1;
+        out->est[i] = est;
+        out->var[i] = var;
+        out->lambda[0][i] = a0;
+        out->lambda[1][i] = a1;
+        out->conc[i] = (cls && t != 0.0) ? est / t : 0.0;
+    }
+    if (i == 0) {
+        out->k = 5;
+        out->n_classes = 21;
+        out->K[0] = in.K[0];
+        out->K[1] = in.K[1];
+        out->triangles = 0.0;
+        out->triangles_var = 0.0;
+    }
+    if (cov) {
+        // lane j fills column j; Cov(eta_i, eta_j) = -plug_i plug_j sum_l a_i a_j / K_l
+        // off the diagonal, and row/column 2 from the linear identity
+        const bool colj = cls && i != 2;
+        const double c0 = a0 * plug, c1 = a1 * plug;
+        double c2 = 0.0;
+        for (int r = 0; r < kSlots; ++r) {
+            const double c0r = __shfl_sync(0xffffffffu, c0, r), c1r = __shfl_sync(0xffffffffu, c1, r);
+            const bool rowr = r >= 1 && r <= 21 && r != 2;
+            double c = 0.0;
+            if (rowr && colj) {
+                if (r == i) {
+                    c = var;
+                } else {
+                    if (av0) c -= c0r * c0 / K0;
+                    if (av1) c -= c1r * c1 / K1;
+                }
+            }
+            if (i < kSlots && r != 2) cov[r * kSlots + i] = c;
+            if (rowr && kPhi5[r - 1][2] > 0) c2 -= kPhi5[r - 1][2] * c;
+        }
+        __syncwarp();
+        if (colj) {
+            cov[2 * kSlots + i] = c2;
+            cov[i * kSlots + 2] = c2;
+        } else if (i == 2) {
+            cov[2 * kSlots + 2] = var;
+        } else if (i < kSlots) {
+            cov[2 * kSlots + i] = 0.0;
+        }
+    }
+}
+
 // MOSS-4 (hits0, K[0]) mixed with MOSS-4Min (hits1 = (class, c) slots, K[1])
 __device__ void finalize_mix(const FinalizeIn &in, const uint64_t *hits0, const uint64_t *hits1, const DevTotals *tot,
                              moss_result *out, double *cov) {
@@ -323,28 +442,35 @@ __device__ void finalize_mix(const FinalizeIn &in, const uint64_t *hits0, const 
     *out = r;
 }
 
+// called by a whole warp: MOSS-5 uses every lane, the k = 4 paths lane 0
 __device__ void finalize_any(const FinalizeIn &in, const uint64_t *hits0, const uint64_t *hits1,
                              const DevTotals *tot, moss_result *out, double *cov = nullptr) {
+    if (in.k == 5 && !in.mix) {
+        finalize5_warp(in, hits0, hits1, tot, out, cov);
+        return;
+    }
+    if ((threadIdx.x & 31) != 0) return;
     if (in.mix) finalize_mix(in, hits0, hits1, tot, out, cov);
     else finalize_one(in, hits0, hits1, tot, out, cov);
 }
 
+// one warp
 __global__ void k_covariance(FinalizeIn in, const uint64_t *hits, const DevTotals *tot, moss_result *out,
                              double *cov) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     finalize_any(in, hits, hits + kSlots, tot, out, cov);
 }
 
+// one warp
 __global__ void k_finalize(FinalizeIn in, const uint64_t *hits, const DevTotals *tot, moss_result *out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     finalize_any(in, hits, hits + kSlots, tot, out);
 }
 
-// one thread per request of a batch
+// one warp per request of a batch
+constexpr int kFinalizeWarps = 4;
 __global__ void k_finalize_batch(const BatchRequest *reqs, int nreq, const uint64_t *task_counts,
                                  moss_result *out) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nreq) return;
+    const int r = blockIdx.x * kFinalizeWarps + (threadIdx.x >> 5);
+    if (r >= nreq) return;   // warp-uniform
     const BatchRequest q = reqs[r];
     const uint64_t *h0 = q.task[0] >= 0 ? task_counts + (uint64_t)q.task[0] * kSlots : nullptr;
     const uint64_t *h1 = q.task[1] >= 0 ? task_counts + (uint64_t)q.task[1] * kSlots : nullptr;
@@ -368,7 +494,8 @@ cudaError_t launch_covariance(const FinalizeIn &in, const uint64_t *hits_dev, co
 cudaError_t launch_finalize_batch(const BatchRequest *reqs, int nreq, const uint64_t *task_counts, void *results,
                                   cudaStream_t s) {
     if (nreq <= 0) return cudaSuccess;
-    k_finalize_batch<<<(nreq + 63) / 64, 64, 0, s>>>(reqs, nreq, task_counts, static_cast<moss_result *>(results));
+    k_finalize_batch<<<(nreq + kFinalizeWarps - 1) / kFinalizeWarps, 32 * kFinalizeWarps, 0, s>>>(
+        reqs, nreq, task_counts, static_cast<moss_result *>(results));
     return cudaGetLastError();
 }
 

@@ -3,7 +3,8 @@
 //
 // One thread draws one sample at a time (grid-stride over sample ids), so
 // every sample is an independent chain of dependent gathers:
-//   Philox words -> vertex alias record (16 B) -> vert[v] (16 B) -> sigma
+//   Philox words -> vertex alias record (32 B, with the alias's vertex record;
+//   vert[v] (16 B) only when the column keeps the draw) -> sigma
 //   record(s) of N_v (16 B each) -> uniform list picks (4 B) -> vert[] of the
 //   new vertices -> lock-step binary searches for the unknown pairs ->
 //   edge mask -> class through a shared-memory table.
@@ -48,12 +49,34 @@ struct Pick {
     uint32_t twin;  // position of v in N_id
 };
 
-// WeightRandomVertex(V, .) through a vertex alias table
-__device__ __forceinline__ uint32_t draw_vertex(const uint4 *seed, uint32_t n, uint64_t xc, uint64_t xt) {
+// one 32-byte sector in a single 256-bit load (32-byte aligned)
+struct alignas(32) Sector {
+    uint4 lo, hi;
+};
+__device__ __forceinline__ Sector ld8(const uint4 *p) {
+    Sector r;
+    asm("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r.lo.x), "=r"(r.lo.y), "=r"(r.lo.z), "=r"(r.lo.w), "=r"(r.hi.x), "=r"(r.hi.y), "=r"(r.hi.z),
+          "=r"(r.hi.w)
+        : "l"(p));
+    return r;
+}
+
+struct VertexPick {
+    uint32_t v;
+    uint4 rec;      // v's vertex record (vert, or mvert for MOSS-4Min)
+};
+
+// WeightRandomVertex(V, .) through a vertex alias table whose 32-byte column
+// records carry the alias's vertex record: one load, plus the column's own
+// record only when the column keeps the draw
+__device__ __forceinline__ VertexPick draw_vertex(const uint4 *seed, const uint4 *vrec, uint32_t n, uint64_t xc,
+                                                  uint64_t xt) {
     const uint32_t c = (uint32_t)word_index(xc, n);
-    const uint4 r = ld4(seed + c);
-    const uint64_t T = ((uint64_t)r.y << 32) | r.x;
-    return xt < T ? c : r.z;
+    const Sector r = ld8(seed + 2 * (uint64_t)c);
+    const uint64_t T = ((uint64_t)r.lo.y << 32) | r.lo.x;
+    if (xt < T) return VertexPick{c, ld4(vrec + c)};
+    return VertexPick{r.lo.z, r.hi};
 }
 
 // WeightRandomVertex(N_v, sigma^(v)) through the list's alias table
@@ -157,8 +180,9 @@ __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t 
     Sample out;
     const Words4 a = philox4x64(s, 0, 0, 0, seed, 0);
     const Words4 b = philox4x64(s, 1, 0, 0, seed, 0);
-    const uint32_t v = draw_vertex(g.seed[0], g.n, a.x[0], a.x[1]);
-    const uint4 vr = ld4(g.vert + v);
+    const VertexPick pv = draw_vertex(g.seed[0], g.vert, g.n, a.x[0], a.x[1]);
+    const uint32_t v = pv.v;
+    const uint4 vr = pv.rec;
     const Pick pu = draw_sigma(g.slot, vr.x, vr.y, vr.z, a.x[2], a.x[3]);
     const uint32_t jw = skip1((uint32_t)word_index(b.x[0], vr.y - 1), pu.pos);
     const uint32_t w = ld1(g.col + vr.x + jw);
@@ -191,8 +215,9 @@ __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lu
     Sample out;
     const Words4 a = philox4x64(s, 0, 1, 0, seed, 0);
     const Words4 b = philox4x64(s, 1, 1, 0, seed, 0);
-    const uint32_t v = draw_vertex(g.seed[1], g.n, a.x[0], a.x[1]);
-    const uint4 vr = ld4(g.vert + v);
+    const VertexPick pv = draw_vertex(g.seed[1], g.vert, g.n, a.x[0], a.x[1]);
+    const uint32_t v = pv.v;
+    const uint4 vr = pv.rec;
     const Pick pu = draw_sigma(g.slot, vr.x, vr.y, vr.z, a.x[2], a.x[3]);
     const uint32_t jw = skip1((uint32_t)word_index(b.x[0], vr.y - 1), pu.pos);
     const uint32_t jr = skip2((uint32_t)word_index(b.x[1], vr.y - 2), pu.pos, jw);
@@ -273,8 +298,9 @@ __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *l
     Sample out;
     const Words4 a = philox4x64(s, 0, 3, 0, seed, 0);
     const Words4 b = philox4x64(s, 1, 3, 0, seed, 0);
-    const uint32_t v = draw_vertex(g.seed[3], g.n, a.x[0], a.x[1]);
-    const uint4 mv = ld4(g.mvert + v);                 // {off, d_v, Gamma-check_v}
+    const VertexPick pv = draw_vertex(g.seed[3], g.mvert, g.n, a.x[0], a.x[1]);
+    const uint32_t v = pv.v;
+    const uint4 mv = pv.rec;                           // {off, d_v, Gamma-check_v}
     const uint64_t Gv = ((uint64_t)mv.w << 32) | mv.z;
     // WeightRandomVertex(N_v, sigma-check^(v)): 32-byte slot records
     uint32_t j = (uint32_t)word_index(a.x[2], mv.y);
@@ -350,8 +376,9 @@ template <bool HASH>
 __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
     const Words4 a = philox4x64(s, 0, 2, 0, seed, 0);
-    const uint32_t v = draw_vertex(g.seed[2], g.n, a.x[0], a.x[1]);
-    const uint4 vr = ld4(g.vert + v);
+    const VertexPick pv = draw_vertex(g.seed[2], g.vert, g.n, a.x[0], a.x[1]);
+    const uint32_t v = pv.v;
+    const uint4 vr = pv.rec;
     const Words4 b = philox4x64(s, 1, 2, 0, seed, 0);
     Pick pu = draw_sigma(g.slot, vr.x, vr.y, vr.z, b.x[0], b.x[1]);
     Pick pw = draw_sigma(g.slot, vr.x, vr.y, vr.z, b.x[2], b.x[3]);

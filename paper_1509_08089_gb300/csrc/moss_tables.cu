@@ -116,9 +116,14 @@ __global__ void __launch_bounds__(kTableThreads) k_slots(uint32_t n, const uint3
             t_g0 += g0;
             t_g1 += g1;
             t_g2 += g2;
-            const u128 dd = d;
-            t_l3 += d >= 3 ? dd * (dd - 1) * (dd - 2) / 6 : 0;
-            t_l4 += d >= 4 ? dd * (dd - 1) * (dd - 2) * (dd - 3) / 24 : 0;
+            if (d >= 3) {
+                // C(d,3) and C(d,4) without a 128-bit division: d(d-1)/2 is
+                // exact in 64 bits, 3 divides it or d-2, and 4 C(d,4) = C(d,3)(d-3)
+                const uint64_t h = (uint64_t)d * (d - 1) / 2;
+                const u128 c3 = (d - 2) % 3 == 0 ? (u128)h * ((d - 2) / 3) : (u128)(h / 3) * (d - 2);
+                t_l3 += c3;
+                if (d >= 4) t_l4 += (c3 * (d - 3)) >> 2;
+            }
             dmax = d > dmax ? d : dmax;
         }
     }
