@@ -161,7 +161,7 @@ struct moss_graph {
     uint4 *slot = nullptr;
     uint32_t *acc = nullptr;
     uint32_t *owner = nullptr;   // vertex of each CSR slot (flat per-slot passes)
-    uint64_t *q = nullptr;
+    uint64_t *sq = nullptr;      // prefix of (d_x - 1)^2 within each list
     u128 *gam[kMethods] = {nullptr, nullptr, nullptr, nullptr};    // [3]: Gamma-check_v (min arena)
     uint4 *seed[kMethods] = {nullptr, nullptr, nullptr, nullptr};
     uint4 *mvert = nullptr;      // MOSS-4Min tables, in min_arena
@@ -177,6 +177,7 @@ struct moss_graph {
     moss_result *res_dev = nullptr;
     double *cov_dev = nullptr;   // 22 x 22 covariance matrix
     uint32_t *flags = nullptr;   // device status: [0] error bits, [1] matched twins
+    uint32_t *defer = nullptr;   // Path-5 deferral bitmap (kDeferChunk bits)
     void *arena = nullptr;       // every device array above lives in this one allocation
     int probe = MOSS_PROBE_HASH; // membership tests: hashed edge set or list search
     unsigned long long *hash = nullptr;  // 2 keys per bucket
@@ -203,11 +204,12 @@ DevGraph view(const moss_graph *g) {
     d.col = g->col;
     d.slot = g->slot;
     d.acc = g->acc;
-    d.q = g->q;
+    d.sq = g->sq;
     for (int l = 0; l < kMethods; ++l) d.seed[l] = g->seed[l];
     d.mvert = g->mvert;
     d.mslot = g->mslot;
     d.rlist = g->rlist;
+    d.defer = g->defer;
     d.n = g->n;
     const bool use_hash = g->probe == MOSS_PROBE_HASH && (g->built >> 4 & 1u);
     d.hash = use_hash ? reinterpret_cast<const uint4 *>(g->hash) : nullptr;
@@ -333,8 +335,8 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
     cudaError_t e = cudaSuccess;
     int blocks = table_blocks(n);
     int prow = 0;
-    for (int m = 0; m < 3; ++m) {
-        int b = sample_blocks(m, device);
+    for (int m = 0; m < kMethods; ++m) {
+        int b = sample_rows(m, device);
         prow = b > prow ? b : prow;
     }
     g->partial_rows = prow;
@@ -359,7 +361,7 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
             g->slot = c.take<uint4>(nnz);
             g->acc = c.take<uint32_t>(nnz);
             g->owner = c.take<uint32_t>(nnz);
-            g->q = c.take<uint64_t>(n);
+            g->sq = c.take<uint64_t>(nnz);
             for (int l = 0; l < 3; ++l) {
                 g->gam[l] = c.take<u128>(n);
                 g->seed[l] = c.take<uint4>(2 * (uint64_t)n);
@@ -370,6 +372,7 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
             g->res_dev = c.take<moss_result>(1);
             g->cov_dev = c.take<double>(kSlots * kSlots);
             g->flags = c.take<uint32_t>(2);
+            g->defer = c.take<uint32_t>(kDeferChunk / 32);
             rp_dev = c.take<uint8_t>(rp_bytes);
         }
     }
@@ -379,7 +382,7 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
     STEP(launch_vertices(rp_dev, row_ptr_is_64, n, nnz, g->vert, g->flags, s), "vertex kernel");
     {
         u128 *tp = reinterpret_cast<u128 *>(g->partials + (uint64_t)prow * kSlots);
-        STEP(launch_slots(n, nnz, g->col, g->vert, g->slot, g->acc, g->owner, g->q, g->gam[0], g->gam[1], g->gam[2],
+        STEP(launch_slots(n, nnz, g->col, g->vert, g->slot, g->acc, g->owner, g->sq, g->gam[0], g->gam[1], g->gam[2],
                           tp, blocks, g->flags, s),
              "slot kernels");
         STEP(launch_totals(tp, blocks, g->tot, s), "totals kernel");
@@ -531,8 +534,8 @@ static int sample_into(moss_graph *g, int method, uint64_t first, uint64_t count
         return MOSS_OK;
     }
     if (count > max_chunk) return fail(MOSS_EOVERFLOW, "count above %llu per call", (unsigned long long)max_chunk);
-    MOSS_CUDA(launch_sample(method, dv, first, count, seed, g->partials, blocks, classes, verts, s), "sample kernel");
-    MOSS_CUDA(launch_reduce(g->partials, blocks, counts_dev, s), "reduce kernel");
+    MOSS_CUDA(launch_counts(method, dv, first, count, seed, g->partials, classes, verts, counts_dev, s),
+              "sample kernels");
     return MOSS_OK;
 }
 

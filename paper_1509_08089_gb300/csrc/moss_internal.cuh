@@ -8,7 +8,10 @@
 //             in [0, S_v), else take position alias; twin = position of v in
 //             N_col (POS of Sec. 4.1.3, used to exclude v from N_col)
 //   acc[nnz]  uint32 ACC_sigma^(v) exclusive prefix of (d_x - 1) within N_v
-//   q[n]      uint64 Q_v = sum (d_x - 1)^2   (Gamma^(2)_v = S_v^2 - Q_v)
+//   sq[nnz]   uint64 exclusive prefix of (d_x - 1)^2 within N_v: with ACC it
+//             gives the prefix of tau^(v) weights (d_x - 1)(S_v - d_x + 1) as
+//             S_v ACC - sq, so the Path-5 fallback draws u by binary search;
+//             Q_v = sum (d_x - 1)^2 is the list's total (Gamma^(2)_v = S_v^2 - Q_v)
 //   gam[l][n] u128 vertex weights Gamma_v, Gamma^(1)_v, Gamma^(2)_v
 //   seed[l][2n] two uint4 per column c, one 32-byte sector: {T lo, T hi,
 //             alias, 0} -- vertex alias table of weight l, keep the column when
@@ -40,6 +43,9 @@ namespace moss {
 constexpr int kSlots = 22;            // [0] collisions, [1..21] classes
 
 constexpr int kMethods = 4;          // MOSS-4, T-5, Path-5, MOSS-4Min
+// Path-5 samples run in chunks of kDeferChunk ids; a sample whose first pair
+// of sigma draws collides is flagged in a bitmap and redone by a second launch
+constexpr uint64_t kDeferChunk = 1ull << 25;
 
 struct alignas(16) DevTotals {
     u128 gamma[kMethods];             // Gamma, Gamma^(1), Gamma^(2), Gamma-check
@@ -53,12 +59,13 @@ struct DevGraph {
     const uint32_t *col;
     const uint4 *slot;
     const uint32_t *acc;
-    const uint64_t *q;
+    const uint64_t *sq;
     const uint4 *seed[kMethods];
     const uint4 *mvert;     // MOSS-4Min tables (null until built)
     const uint4 *mslot;
     const uint2 *rlist;
     const uint4 *hash;      // hashed edge set (2 keys per 16 B bucket), or null: probe by search
+    uint32_t *defer;        // Path-5 deferral bitmap, kDeferChunk bits
     uint32_t hash_mask;     // buckets - 1
     uint32_t hash_shift;    // 64 - log2(buckets)
     uint32_t n;
@@ -182,7 +189,7 @@ cudaError_t launch_vertices(const void *row_ptr, int is64, uint32_t n, uint64_t 
                             uint32_t *flags, cudaStream_t s);
 // flags[0]: kErr* bits; flags[1]: slots whose twin was matched (must reach nnz)
 cudaError_t launch_slots(uint32_t n, uint64_t nnz, const uint32_t *col, uint4 *vert, uint4 *slot, uint32_t *acc,
-                         uint32_t *owner, uint64_t *q, u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials,
+                         uint32_t *owner, uint64_t *sq, u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials,
                          int blocks, uint32_t *flags, cudaStream_t s);
 cudaError_t launch_totals(const u128 *partials, int blocks, DevTotals *tot, cudaStream_t s);
 cudaError_t launch_edge_hash(uint64_t nnz, const uint32_t *col, const uint32_t *owner, unsigned long long *table,
@@ -208,11 +215,16 @@ cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const
 
 // moss_sample.cu
 void upload_luts(const uint8_t *lut4, const uint8_t *lut5);
-cudaError_t launch_sample(int method, const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed,
-                          uint64_t *partials, int blocks, uint8_t *classes, uint32_t *verts,
+// Counts (22 uint64 at counts_dev) of samples [first, first+count) of one
+// method, with optional per-sample records (classes, verts: count and 5*count
+// entries); partials holds sample_rows(method) rows of 22 uint64.  Path-5 runs
+// in chunks of kDeferChunk ids: a launch that defers the samples whose first
+// sigma attempt collides, one that redoes them, and a reduce that accumulates.
+cudaError_t launch_counts(int method, const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed,
+                          uint64_t *partials, uint8_t *classes, uint32_t *verts, uint64_t *counts_dev,
                           cudaStream_t s);
-cudaError_t launch_reduce(const uint64_t *partials, int blocks, uint64_t *out, cudaStream_t s);
-int sample_blocks(int method, int device);
+int sample_blocks(int method, int device);   // blocks of one sampler launch
+int sample_rows(int method, int device);     // partial-count rows launch_counts needs
 
 // moss_finalize.cu
 struct FinalizeIn {

@@ -80,7 +80,7 @@ extern "C" int moss_sample_counts_noalloc(moss_graph *g, int method, uint64_t fi
     uint64_t *partials = nullptr;
     const int blocks = sample_blocks(method, gi.device);
     const uint64_t max_chunk = (uint64_t)blocks * 8 * (1ULL << 31);
-    if (blocks > kNoAllocMaxBlocks) {
+    if (sample_rows(method, gi.device) > kNoAllocMaxBlocks) {
         rc = set_error(MOSS_EOVERFLOW, "this GPU needs more than 2048 blocks of partial counts, the fixed maximum");
     } else if (count > max_chunk) {
         rc = set_error(MOSS_EOVERFLOW, "count above the per-call maximum of 2^31 samples per warp");
@@ -89,8 +89,7 @@ extern "C" int moss_sample_counts_noalloc(moss_graph *g, int method, uint64_t fi
         if (count == 0) {
             e = cudaMemsetAsync(counts_dev, 0, kSlots * sizeof(uint64_t), s);
         } else {
-            e = launch_sample(method, gi.view, first, count, seed, partials, blocks, nullptr, nullptr, s);
-            if (e == cudaSuccess) e = launch_reduce(partials, blocks, counts_dev, s);
+            e = launch_counts(method, gi.view, first, count, seed, partials, nullptr, nullptr, counts_dev, s);
         }
         if (e != cudaSuccess) rc = set_error(MOSS_ECUDA, cudaGetErrorString(e));
     }

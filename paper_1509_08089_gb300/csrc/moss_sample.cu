@@ -342,22 +342,31 @@ __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *l
     return out;
 }
 
-// Path-5 fallback: u from tau^(v) by a scan, w from mu^(v,u) by a search
-__device__ __noinline__ void path5_fallback(const uint32_t *acc, const uint64_t *q, uint32_t v, uint4 vr, uint64_t x12,
-                                            uint64_t x13, uint32_t &iu, uint32_t &iw) {
+// Path-5 fallback: u from tau^(v), w from mu^(v,u) (Sec. 5.1.4).  The
+// prefix of the tau weights w_i (S - w_i), w_i = d_x - 1, is S ACC[p] - sq[p],
+// so u is the last position whose prefix is <= y, found by binary search
+// (the same position a scan of the running sum gives); w by the search of
+// ACC with u's interval removed.
+__device__ __noinline__ void path5_fallback(const uint32_t *acc, const uint64_t *sq, uint32_t v, uint4 vr,
+                                            uint64_t x12, uint64_t x13, uint32_t &iu, uint32_t &iw) {
     const uint32_t o = vr.x, d = vr.y, S = vr.z;
-    const uint64_t G = (uint64_t)S * S - q[v];
+    const uint32_t wl = S - ld1(acc + o + d - 1);
+    const uint64_t Q = __ldg(sq + o + d - 1) + (uint64_t)wl * wl;
+    const uint64_t G = (uint64_t)S * S - Q;
     const uint64_t y = word_index(x12, G);
-    uint64_t run = 0;
-    iu = 0;
-    for (uint32_t i = 0; i < d; ++i) {
-        const uint32_t wi = (i + 1 < d ? ld1(acc + o + i + 1) : S) - ld1(acc + o + i);
-        const uint64_t tw = (uint64_t)wi * (S - wi);
-        if (y < run + tw) {
-            iu = i;
-            break;
+    {
+        uint32_t lo = 0, len = d;   // first p with prefix(p) > y
+        while (len > 0) {
+            const uint32_t half = len >> 1, p = lo + half;
+            const uint64_t f = (uint64_t)S * ld1(acc + o + p) - __ldg(sq + o + p);
+            if (f <= y) {
+                lo = p + 1;
+                len -= half + 1;
+            } else {
+                len = half;
+            }
         }
-        run += tw;
+        iu = lo - 1;
     }
     const uint32_t au = ld1(acc + o + iu);
     const uint32_t wu = (iu + 1 < d ? ld1(acc + o + iu + 1) : S) - au;
@@ -372,7 +381,13 @@ __device__ __noinline__ void path5_fallback(const uint32_t *acc, const uint64_t 
     iw = lo - 1;
 }
 
-template <bool HASH>
+// DEFER: a sample whose first attempt collides returns kDeferred at once (the
+// retry and the fallback are left to k_sample_deferred, which calls this with
+// DEFER = false), so that their live state does not set the register budget
+// of the main launch.
+constexpr int kDeferred = 254;
+
+template <bool HASH, bool DEFER>
 __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
     const Words4 a = philox4x64(s, 0, 2, 0, seed, 0);
@@ -383,13 +398,17 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
     Pick pu = draw_sigma(g.slot, vr.x, vr.y, vr.z, b.x[0], b.x[1]);
     Pick pw = draw_sigma(g.slot, vr.x, vr.y, vr.z, b.x[2], b.x[3]);
     if (pu.pos == pw.pos) {
+        if (DEFER) {
+            out.cls = kDeferred;
+            return out;
+        }
         const Words4 c = philox4x64(s, 2, 2, 0, seed, 0);
         pu = draw_sigma(g.slot, vr.x, vr.y, vr.z, c.x[0], c.x[1]);
         pw = draw_sigma(g.slot, vr.x, vr.y, vr.z, c.x[2], c.x[3]);
         if (pu.pos == pw.pos) {
             const Words4 d4 = philox4x64(s, 3, 2, 0, seed, 0);
             uint32_t iu, iw;
-            path5_fallback(g.acc, g.q, v, vr, d4.x[0], d4.x[1], iu, iw);
+            path5_fallback(g.acc, g.sq, v, vr, d4.x[0], d4.x[1], iu, iw);
             const uint4 su = ld4(g.slot + vr.x + iu), sw = ld4(g.slot + vr.x + iw);
             pu = Pick{iu, su.x, su.w};
             pw = Pick{iw, sw.x, sw.w};
@@ -428,10 +447,12 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
 
 // Resident blocks per SM each sampler is compiled for: the loop is bound by
 // memory latency, so more warps in flight help until register spills cost
-// more than they hide (measured: MOSS-4 and T-5 fastest at 6 blocks of 256
-// threads, Path-5, with its larger live state, at 4).
+// more than they hide (measured: 6 blocks of 256 threads for every main
+// sampler; Path-5 reaches it only with its retry path deferred, whose own
+// launch runs at 4).
 template <int METHOD>
-constexpr int min_blocks() { return METHOD == 2 ? 4 : 6; }
+constexpr int min_blocks() { return 6; }
+constexpr int kDeferBlocks = 4;
 
 template <int METHOD, bool RECORD, bool HASH>
 __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGraph g, uint64_t first, uint64_t count, uint64_t seed,
@@ -450,24 +471,95 @@ __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGr
     for (uint64_t base = warp_base; base < count; base += stride) {
         const uint64_t i = base + lane;
         int cls = kSlots;  // no sample (tail)
+        bool deferred = false;
         if (i < count) {
             const uint64_t s = first + i;
             Sample sm;
             if (METHOD == 0) sm = sample_moss4<HASH>(g, lut, seed, s);
             else if (METHOD == 1) sm = sample_t5<HASH>(g, lut, seed, s);
-            else if (METHOD == 2) sm = sample_path5<HASH>(g, lut, seed, s);
+            else if (METHOD == 2) sm = sample_path5<HASH, true>(g, lut, seed, s);
             else sm = sample_min<HASH>(g, lut, seed, s);
-            cls = METHOD == 3 ? min_slot(sm.cls, sm.v[4]) : sm.cls;
-            if (RECORD) {
-                classes[i] = (uint8_t)sm.cls;
-                if (verts) {
+            deferred = METHOD == 2 && sm.cls == kDeferred;
+            if (!deferred) {
+                cls = METHOD == 3 ? min_slot(sm.cls, sm.v[4]) : sm.cls;
+                if (RECORD) {
+                    classes[i] = (uint8_t)sm.cls;
+                    if (verts) {
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) verts[5 * i + k] = sm.v[k];
+                        for (int k = 0; k < 5; ++k) verts[5 * i + k] = sm.v[k];
+                    }
                 }
             }
         }
+        if (METHOD == 2) {   // one bitmap word per 32 sample ids, written by the warp that drew them
+            const uint32_t bits = __ballot_sync(0xffffffffu, deferred);
+            if (lane == 0) g.defer[base >> 5] = bits;
+        }
         const uint32_t peers = __match_any_sync(0xffffffffu, cls);
         if (cls < kSlots && lane == __ffs(peers) - 1) atomicAdd(&hist[warp][cls], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    if (threadIdx.x < kSlots) {
+        uint64_t sum = 0;
+        for (int w = 0; w < kWarps; ++w) sum += hist[w][threadIdx.x];
+        partials[(uint64_t)blockIdx.x * kSlots + threadIdx.x] = sum;
+    }
+}
+
+// The Path-5 samples a main launch deferred.  A warp takes 32 bitmap words
+// (1,024 ids), lists their flagged ids in shared memory (a warp scan of the
+// words' popcounts places them), then draws them 32 at a time, one per lane,
+// in full (second attempt, fallback); counts are aggregated as in k_sample and
+// written to this launch's own partial rows.
+template <bool RECORD, bool HASH>
+__global__ void __launch_bounds__(kThreads, kDeferBlocks)
+    k_sample_deferred(DevGraph g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
+                      uint8_t *classes, uint32_t *verts) {
+    __shared__ uint8_t lut[kLut];
+    __shared__ uint32_t hist[kWarps][kSlots];
+    __shared__ uint32_t list[kWarps][32 * 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kLut; i += kThreads) lut[i] = g_lut5[i];
+    for (int i = threadIdx.x; i < kWarps * kSlots; i += kThreads) (&hist[0][0])[i] = 0;
+    __syncthreads();
+    const uint64_t words = (count + 31) / 32;
+    const uint64_t stride = (uint64_t)gridDim.x * kWarps * 32;
+    for (uint64_t w0 = ((uint64_t)blockIdx.x * kWarps + warp) * 32; w0 < words; w0 += stride) {
+        const uint64_t w = w0 + lane;
+        uint32_t bits = w < words ? g.defer[w] : 0u;
+        // exclusive prefix of the popcounts: where this word's ids go in the list
+        const uint32_t c = __popc(bits);
+        uint32_t incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t at = incl - c;
+        while (bits) {
+            list[warp][at++] = (uint32_t)(lane * 32 + __ffs(bits) - 1);   // id - 32 w0
+            bits &= bits - 1;
+        }
+        __syncwarp();
+        for (uint32_t j0 = 0; j0 < total; j0 += 32) {
+            int cls = kSlots;
+            if (j0 + lane < total) {
+                const uint64_t i = w0 * 32 + list[warp][j0 + lane];   // < count: only drawn ids are flagged
+                const Sample sm = sample_path5<HASH, false>(g, lut, seed, first + i);
+                cls = sm.cls;
+                if (RECORD) {
+                    classes[i] = (uint8_t)sm.cls;
+                    if (verts) {
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) verts[5 * i + k] = sm.v[k];
+                    }
+                }
+            }
+            const uint32_t peers = __match_any_sync(0xffffffffu, cls);
+            if (cls < kSlots && lane == __ffs(peers) - 1) atomicAdd(&hist[warp][cls], (uint32_t)__popc(peers));
+        }
+        __syncwarp();   // the list is refilled for the next 32 words
     }
     __syncthreads();
     if (threadIdx.x < kSlots) {
@@ -491,7 +583,7 @@ __device__ __forceinline__ int sample_any(const DevGraph &g, const uint8_t *lut4
                                           uint64_t seed, uint64_t s) {
     if (method == 0) return sample_moss4<HASH>(g, lut4, seed, s).cls;
     if (method == 1) return sample_t5<HASH>(g, lut5, seed, s).cls;
-    return sample_path5<HASH>(g, lut5, seed, s).cls;
+    return sample_path5<HASH, false>(g, lut5, seed, s).cls;
 }
 
 __global__ void __launch_bounds__(kThreads, kBatchBlocks)
@@ -555,13 +647,14 @@ __global__ void k_batch_reduce(const BatchTask *tasks, uint32_t tile_samples, co
     if (lane == 0) task_counts[(uint64_t)blockIdx.x * kSlots + c] = s;
 }
 
-__global__ void k_reduce(const uint64_t *partials, int blocks, uint64_t *out) {
+// accumulate: add to out (later chunks of one count) instead of overwriting
+__global__ void k_reduce(const uint64_t *partials, int blocks, uint64_t *out, int accumulate) {
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint64_t s = 0;
     for (int b = lane; b < blocks; b += 32) s += partials[(uint64_t)b * kSlots + c];
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
-    if (lane == 0) out[c] = s;
+    if (lane == 0) out[c] = accumulate ? out[c] + s : s;
 }
 
 template <int M, bool R>
@@ -604,6 +697,8 @@ int sample_blocks(int method, int device) {
     return sms * per;
 }
 
+namespace {
+
 cudaError_t launch_sample(int method, const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed,
                           uint64_t *partials, int blocks, uint8_t *classes, uint32_t *verts, cudaStream_t s) {
     const bool rec = classes != nullptr;
@@ -618,6 +713,59 @@ cudaError_t launch_sample(int method, const DevGraph &g, uint64_t first, uint64_
         case 7: return launch_one<3, true>(g, first, count, seed, partials, blocks, classes, verts, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_deferred(const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
+                            int blocks, uint8_t *classes, uint32_t *verts, cudaStream_t s) {
+    const bool rec = classes != nullptr;
+    if (g.hash) {
+        if (rec) k_sample_deferred<true, true><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+        else k_sample_deferred<false, true><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    } else {
+        if (rec) k_sample_deferred<true, false><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+        else k_sample_deferred<false, false><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    }
+    return cudaGetLastError();
+}
+
+int defer_blocks(int device) {
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    return sms * kDeferBlocks;
+}
+
+}  // namespace
+
+int sample_rows(int method, int device) {
+    return sample_blocks(method, device) + (method == 2 ? defer_blocks(device) : 0);
+}
+
+cudaError_t launch_counts(int method, const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed,
+                          uint64_t *partials, uint8_t *classes, uint32_t *verts, uint64_t *counts_dev,
+                          cudaStream_t s) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int blocks = sample_blocks(method, dev);
+    cudaError_t e;
+    if (method != 2) {
+        if ((e = launch_sample(method, g, first, count, seed, partials, blocks, classes, verts, s)) != cudaSuccess)
+            return e;
+        k_reduce<<<1, 32 * kSlots, 0, s>>>(partials, blocks, counts_dev, 0);
+        return cudaGetLastError();
+    }
+    const int dblocks = defer_blocks(dev);
+    for (uint64_t c0 = 0; c0 < count; c0 += kDeferChunk) {
+        const uint64_t len = count - c0 < kDeferChunk ? count - c0 : kDeferChunk;
+        uint8_t *cl = classes ? classes + c0 : nullptr;
+        uint32_t *vt = verts ? verts + 5 * c0 : nullptr;
+        if ((e = launch_sample(2, g, first + c0, len, seed, partials, blocks, cl, vt, s)) != cudaSuccess) return e;
+        if ((e = launch_deferred(g, first + c0, len, seed, partials + (uint64_t)blocks * kSlots, dblocks, cl, vt, s)) !=
+            cudaSuccess)
+            return e;
+        k_reduce<<<1, 32 * kSlots, 0, s>>>(partials, blocks + dblocks, counts_dev, c0 > 0 ? 1 : 0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 int batch_blocks(int device) {
@@ -640,11 +788,6 @@ cudaError_t launch_batch_reduce(const BatchTask *tasks, int ntasks, uint32_t til
                                 const uint32_t *tile_counts, uint64_t *task_counts, cudaStream_t s) {
     if (ntasks <= 0) return cudaSuccess;
     k_batch_reduce<<<ntasks, 32 * kSlots, 0, s>>>(tasks, tile_samples, tile_counts, task_counts);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_reduce(const uint64_t *partials, int blocks, uint64_t *out, cudaStream_t s) {
-    k_reduce<<<1, 32 * kSlots, 0, s>>>(partials, blocks, out);
     return cudaGetLastError();
 }
 

@@ -54,7 +54,7 @@ __global__ void k_vertices(const IdxT *row_ptr, uint32_t n, uint64_t nnz, uint4 
 // One warp per vertex: validation, the owner of each slot, ACC prefix, S_v,
 // Q_v, the three vertex weights and the block's share of the exact totals.
 __global__ void __launch_bounds__(kTableThreads) k_slots(uint32_t n, const uint32_t *__restrict__ col, uint4 *vert,
-                                                        uint4 *slot, uint32_t *acc, uint32_t *owner, uint64_t *q,
+                                                        uint4 *slot, uint32_t *acc, uint32_t *owner, uint64_t *sq,
                                                         u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials,
                                                         uint32_t *flags) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -91,22 +91,22 @@ __global__ void __launch_bounds__(kTableThreads) k_slots(uint32_t n, const uint3
             for (int u = 0; u < kUnroll; ++u) {
                 if (base + u * kWarp >= d) break;   // warp-uniform
                 const uint32_t i = base + u * kWarp + lane;
+                const uint64_t w2 = (uint64_t)w[u] * w[u];
                 const uint64_t incl = warp_incl_scan64(w[u], lane);
+                const uint64_t incl2 = warp_incl_scan64(w2, lane);
                 if (i < d) {
                     acc[o + i] = (uint32_t)(run + incl - w[u]);
+                    sq[o + i] = qsum + incl2 - w2;
                     slot[o + i] = make_uint4(x[u], 0u, 0u, 0u);
                     owner[o + i] = (uint32_t)v;
                 }
                 run += __shfl_sync(0xffffffffu, incl, 31);
-                qsum += (uint64_t)w[u] * w[u];
+                qsum += __shfl_sync(0xffffffffu, incl2, 31);
             }
         }
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) qsum += __shfl_down_sync(0xffffffffu, qsum, s);
         if (lane == 0) {
             const uint64_t S = run;
             vert[v].z = (uint32_t)S;
-            q[v] = qsum;
             const u128 g0 = d >= 1 ? (u128)(d - 1) * S : 0;
             const u128 g1 = d >= 2 ? (u128)(d - 1) * (d - 2) * S : 0;
             const u128 g2 = (u128)S * S - qsum;
@@ -668,9 +668,9 @@ static unsigned flat_blocks(uint64_t items) {
 }
 
 cudaError_t launch_slots(uint32_t n, uint64_t nnz, const uint32_t *col, uint4 *vert, uint4 *slot, uint32_t *acc,
-                         uint32_t *owner, uint64_t *q, u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials,
+                         uint32_t *owner, uint64_t *sq, u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials,
                          int blocks, uint32_t *flags, cudaStream_t s) {
-    k_slots<<<blocks, kTableThreads, 0, s>>>(n, col, vert, slot, acc, owner, q, gam0, gam1, gam2, partials, flags);
+    k_slots<<<blocks, kTableThreads, 0, s>>>(n, col, vert, slot, acc, owner, sq, gam0, gam1, gam2, partials, flags);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || nnz == 0) return e;
     k_twin<<<flat_blocks(nnz), 256, 0, s>>>(n, nnz, vert, col, owner, slot, flags);
