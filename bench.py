@@ -222,6 +222,24 @@ class Clocks:
 
 
 # ------------------------------------------------------------------- GPU --
+DEFER_CHUNK = 1 << 25   # Path-5 sample ids per main/deferred launch pair
+
+
+def launches_per_step(k: int, budget: int, mix: bool) -> int:
+    """Kernels of one step: load 6 (vertices, owners, slot weights, slot scans,
+    twins, totals); build 7
+    (two sigma alias passes, four vertex-table phases, edge hash); MOSS-4Min
+    build 11 (three sort tiers, slot records, two alias passes, total, four
+    vertex-table phases); per sub-method a sampler and a reduce, Path-5 per
+    chunk of DEFER_CHUNK ids a main launch, a deferred launch and a reduce;
+    one finalize."""
+    from paper_1509_08089_gb300.dist import sub_budgets
+    n = 6 + 7 + (11 if mix else 0) + 1
+    for m, K in sub_budgets(k, budget, mix):
+        n += 3 * -(-K // DEFER_CHUNK) if m == 2 else 2
+    return n
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as tdist
@@ -410,10 +428,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": d2h},
         "roofline": roof,
         "clocks": clk,
-        # load 4 (vertices, slots, twins, totals) + build 6 (sigma alias, 4 vertex-table
-        # phases, edge hash) + per sub-method sampler and reduce + finalize
-        # (+ MOSS-4Min build: 3 sort tiers, slot records, alias tables, total, 4 vertex-table phases)
-        "gpu_launches": (4 + 6 + (10 if mix else 0) + 2 * len(sub_budgets(k, args.budget, mix)) + 1) * args.steps,
+        "gpu_launches": launches_per_step(k, args.budget, mix) * args.steps,
         "wall_s_timed": t_wall,
         "step_ms": step_ms,
     }

@@ -367,7 +367,7 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
                 g->seed[l] = c.take<uint4>(2 * (uint64_t)n);
             }
             g->tot = c.take<DevTotals>(1);
-            g->partials = c.take<uint64_t>((uint64_t)prow * kSlots + (uint64_t)blocks * 6 * 2);
+            g->partials = c.take<uint64_t>((uint64_t)prow * kSlots + (uint64_t)slot_partial_rows(n) * 6 * 2);
             g->counts = c.take<uint64_t>(2 * kSlots);
             g->res_dev = c.take<moss_result>(1);
             g->cov_dev = c.take<double>(kSlots * kSlots);
@@ -385,7 +385,7 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
         STEP(launch_slots(n, nnz, g->col, g->vert, g->slot, g->acc, g->owner, g->sq, g->gam[0], g->gam[1], g->gam[2],
                           tp, blocks, g->flags, s),
              "slot kernels");
-        STEP(launch_totals(tp, blocks, g->tot, s), "totals kernel");
+        STEP(launch_totals(tp, slot_partial_rows(n), g->tot, s), "totals kernel");
     }
     STEP(cudaMemcpyAsync(&g->tot_h, g->tot, sizeof(DevTotals), cudaMemcpyDeviceToHost, s), "reading totals");
     rc = read_flags(g, s);

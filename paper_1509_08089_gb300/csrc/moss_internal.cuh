@@ -204,6 +204,7 @@ cudaError_t launch_seed_alias(uint32_t n, const DevTotals *tot, int ntables, con
                               cudaStream_t s);
 uint64_t seed_scratch_bytes(uint32_t n);
 int table_blocks(uint32_t n);
+int slot_partial_rows(uint32_t n);   // rows of 6 u128 totals launch_slots writes (launch_totals sums them)
 
 // moss_min.cu: the MOSS-4Min tables (ordered lists, d_{v,u}, Gamma-check_v,
 // the sigma-check alias tables, tot->gamma[3] and its vertex alias table)

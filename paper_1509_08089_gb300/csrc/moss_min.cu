@@ -122,16 +122,17 @@ __global__ void __launch_bounds__(kSortThreads) k_rank_block(uint32_t n, const u
                                                             const uint32_t *__restrict__ col, uint2 *rlist,
                                                             uint32_t *rank) {
     __shared__ uint64_t k[kTile];
-    for (uint64_t v = blockIdx.x; v < n; v += gridDim.x) {
-        const uint4 vr = vert[v];
-        const uint32_t o = vr.x, d = vr.y;
-        if (d <= (uint32_t)kWarp || d > kTile) continue;   // block-uniform
-        const uint32_t P = pow2_at_least(d);
-        load_keys(vert, col, o, 0, d, P, k);
-        bitonic_desc(k, P);
-        for (uint32_t q = threadIdx.x; q < d; q += blockDim.x) emit(col, o, d, q, k[q], rlist, rank);
-        __syncthreads();   // k is refilled for the next list
-    }
+    for_each_vertex<kSortThreads>(
+        n, vert, [](uint4 vr) { return vr.y > (uint32_t)kWarp && vr.y <= kTile; },
+        [&](uint32_t v) {
+            const uint4 vr = vert[v];
+            const uint32_t o = vr.x, d = vr.y;
+            const uint32_t P = pow2_at_least(d);
+            load_keys(vert, col, o, 0, d, P, k);
+            bitonic_desc(k, P);
+            for (uint32_t q = threadIdx.x; q < d; q += blockDim.x) emit(col, o, d, q, k[q], rlist, rank);
+            __syncthreads();   // k is refilled for the next list
+        });
 }
 
 // lists longer than kTile: tiles sorted in shared memory into a[], then runs
@@ -140,10 +141,9 @@ __global__ void __launch_bounds__(kSortThreads) k_rank_long(uint32_t n, const ui
                                                            const uint32_t *__restrict__ col, uint64_t *a,
                                                            uint64_t *b, uint2 *rlist, uint32_t *rank) {
     __shared__ uint64_t k[kTile];
-    for (uint64_t v = blockIdx.x; v < n; v += gridDim.x) {
+    for_each_vertex<kSortThreads>(n, vert, [](uint4 vr) { return vr.y > kTile; }, [&](uint32_t v) {
         const uint4 vr = vert[v];
         const uint32_t o = vr.x, d = vr.y;
-        if (d <= kTile) continue;   // block-uniform
         for (uint32_t base = 0; base < d; base += kTile) {
             const uint32_t len = min(kTile, d - base);
             const uint32_t P = pow2_at_least(len);
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rank_long(uint32_t n, const ui
         }
         for (uint32_t q = threadIdx.x; q < d; q += blockDim.x) emit(col, o, d, q, src[(uint64_t)o + q], rlist, rank);
         __syncthreads();
-    }
+    });
 }
 
 // per slot p (v -> u): {0, 0, 0, u} and {off_u, d_u, d_{v,u}, d_{u,v}}
@@ -348,19 +348,20 @@ __global__ void __launch_bounds__(kListThreads) k_min_alias_long(uint32_t n, con
                                                                 const uint4 *__restrict__ mvert, uint4 *mslot,
                                                                 uint32_t *idx, u128 *pre) {
     uint32_t *m32 = reinterpret_cast<uint32_t *>(mslot);
-    for (uint64_t v = blockIdx.x; v < n; v += gridDim.x) {
-        const uint4 mv = mvert[v];
-        const uint32_t o = mv.x, d = mv.y;
-        const uint64_t W = ((uint64_t)mv.w << 32) | mv.z;
-        if (d <= kLongList || W == 0) continue;   // block-uniform
-        block_alias<u128, kListThreads>(
-            d, (u128)W, [&](uint32_t j) { return (u128)min_weight(mslot, (uint64_t)o + j); }, idx + o, pre + o,
-            [&](uint32_t j, u128 thr, uint32_t alias) {
-                m32[8 * ((uint64_t)o + j) + 0] = (uint32_t)thr;
-                m32[8 * ((uint64_t)o + j) + 1] = (uint32_t)((uint64_t)thr >> 32);
-                m32[8 * ((uint64_t)o + j) + 2] = alias;
-            });
-    }
+    for_each_vertex<kListThreads>(
+        n, mvert, [](uint4 mv) { return mv.y > kLongList && (mv.z | mv.w) != 0; },
+        [&](uint32_t v) {
+            const uint4 mv = mvert[v];
+            const uint32_t o = mv.x, d = mv.y;
+            const uint64_t W = ((uint64_t)mv.w << 32) | mv.z;
+            block_alias<u128, kListThreads>(
+                d, (u128)W, [&](uint32_t j) { return (u128)min_weight(mslot, (uint64_t)o + j); }, idx + o, pre + o,
+                [&](uint32_t j, u128 thr, uint32_t alias) {
+                    m32[8 * ((uint64_t)o + j) + 0] = (uint32_t)thr;
+                    m32[8 * ((uint64_t)o + j) + 1] = (uint32_t)((uint64_t)thr >> 32);
+                    m32[8 * ((uint64_t)o + j) + 2] = alias;
+                });
+        });
 }
 
 __global__ void k_min_total(const u128 *partials, int blocks, DevTotals *tot) {
@@ -424,9 +425,10 @@ cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const
         k_rank_warp<<<grid_for((uint64_t)n, kListThreads / kWarp, 8), kListThreads, 0, s>>>(n, vert, col, rlist,
                                                                                              m.rank);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_rank_block<<<grid_for((uint64_t)n, 1, 4), kSortThreads, 0, s>>>(n, vert, col, rlist, m.rank);
+        k_rank_block<<<grid_for((uint64_t)n, kSortThreads, 4), kSortThreads, 0, s>>>(n, vert, col, rlist, m.rank);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_rank_long<<<grid_for((uint64_t)n, 1, 1), kSortThreads, 0, s>>>(n, vert, col, m.a, m.b, rlist, m.rank);
+        k_rank_long<<<grid_for((uint64_t)n, kSortThreads, 1), kSortThreads, 0, s>>>(n, vert, col, m.a, m.b, rlist,
+                                                                                    m.rank);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         k_min_slots<<<grid_for(nnz, 256, 16), 256, 0, s>>>(nnz, vert, col, slot, m.rank, mslot);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -436,7 +438,7 @@ cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const
     k_min_alias<<<ab, kListThreads, 0, s>>>(n, vert, mslot, mvert, gmin, m.rank, reinterpret_cast<u128 *>(m.a),
                                              m.partials);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_min_alias_long<<<grid_for((uint64_t)n, 1, 4), kListThreads, 0, s>>>(n, vert, mvert, mslot, m.rank,
+    k_min_alias_long<<<grid_for((uint64_t)n, kListThreads, 4), kListThreads, 0, s>>>(n, vert, mvert, mslot, m.rank,
                                                                           reinterpret_cast<u128 *>(m.a));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_min_total<<<1, kWarp, 0, s>>>(m.partials, (int)ab, tot);

@@ -51,41 +51,98 @@ __global__ void k_vertices(const IdxT *row_ptr, uint32_t n, uint64_t nnz, uint4 
 }
 
 // --------------------------------------------------------------- slots ---
-// One warp per vertex: validation, the owner of each slot, ACC prefix, S_v,
-// Q_v, the three vertex weights and the block's share of the exact totals.
-__global__ void __launch_bounds__(kTableThreads) k_slots(uint32_t n, const uint32_t *__restrict__ col, uint4 *vert,
-                                                        uint4 *slot, uint32_t *acc, uint32_t *owner, uint64_t *sq,
-                                                        u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials,
-                                                        uint32_t *flags) {
+// Three passes.  k_owner: the vertex of each slot (warp per vertex, stores
+// only).  k_slot_weights: one thread per slot validates the neighbour id and
+// order and gathers w = d_x - 1 into acc -- every gather of the graph in
+// flight at once.  k_slots: one warp per vertex scans its w (coalesced
+// loads) into the ACC prefix and the prefix of squares, then S_v, Q_v, the
+// three vertex weights and the block's share of the exact totals.
+__global__ void k_owner(uint32_t n, const uint4 *__restrict__ vert, uint32_t *owner) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    u128 t_g0 = 0, t_g1 = 0, t_g2 = 0, t_l3 = 0, t_l4 = 0;
-    uint32_t dmax = 0;
+    for (uint64_t v = (uint64_t)blockIdx.x * wpb + warp; v < n; v += (uint64_t)gridDim.x * wpb) {
+        const uint4 vr = vert[v];
+        for (uint32_t i = lane; i < vr.y; i += kWarp) owner[vr.x + i] = (uint32_t)v;
+    }
+}
+
+__global__ void k_slot_weights(uint32_t n, uint64_t nnz, const uint32_t *__restrict__ col,
+                               const uint4 *__restrict__ vert, const uint32_t *__restrict__ owner, uint4 *slot,
+                               uint32_t *acc, uint32_t *flags) {
     uint32_t err = 0;
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = owner[p], x = col[p];
+        uint32_t w = 0;
+        if (x >= n) {
+            err |= kErrRange;
+        } else {
+            if (x == v) err |= kErrSelf;
+            if (p > 0 && owner[p - 1] == v && col[p - 1] >= x) err |= kErrOrder;
+            const uint32_t dx = vert[x].y;
+            w = dx ? dx - 1 : 0;
+        }
+        acc[p] = w;    // turned into the prefix by k_slots
+        slot[p] = make_uint4(x, 0u, 0u, 0u);
+    }
+    if (err) atomicOr(flags, err);
+}
+
+// exact totals of a share of the vertices: Gamma, Gamma^(1), Gamma^(2),
+// Lambda_3, Lambda_4 and the maximum degree
+struct Totals {
+    u128 g0, g1, g2, l3, l4;
+    uint32_t dmax;
+    __device__ void add(const Totals &o) {
+        g0 += o.g0; g1 += o.g1; g2 += o.g2; l3 += o.l3; l4 += o.l4;
+        dmax = o.dmax > dmax ? o.dmax : dmax;
+    }
+    __device__ void store(u128 *row) const {
+        row[0] = g0; row[1] = g1; row[2] = g2; row[3] = l3; row[4] = l4; row[5] = dmax;
+    }
+};
+
+// S_v, the vertex weights Gamma_v = (d-1) S_v, Gamma^(1)_v = (d-1)(d-2) S_v,
+// Gamma^(2)_v = S_v^2 - Q_v, and v's share of the totals
+__device__ __forceinline__ void vertex_weights(uint64_t v, uint32_t d, uint64_t S, uint64_t Q, uint4 *vert,
+                                               u128 *gam0, u128 *gam1, u128 *gam2, Totals &t) {
+    vert[v].z = (uint32_t)S;
+    const u128 g0 = d >= 1 ? (u128)(d - 1) * S : 0;
+    const u128 g1 = d >= 2 ? (u128)(d - 1) * (d - 2) * S : 0;
+    const u128 g2 = (u128)S * S - Q;
+    gam0[v] = g0;
+    gam1[v] = g1;
+    gam2[v] = g2;
+    t.g0 += g0;
+    t.g1 += g1;
+    t.g2 += g2;
+    if (d >= 3) {
+        // C(d,3) and C(d,4) without a 128-bit division: d(d-1)/2 is exact in
+        // 64 bits, 3 divides it or d-2, and 4 C(d,4) = C(d,3)(d-3)
+        const uint64_t h = (uint64_t)d * (d - 1) / 2;
+        const u128 c3 = (d - 2) % 3 == 0 ? (u128)h * ((d - 2) / 3) : (u128)(h / 3) * (d - 2);
+        t.l3 += c3;
+        if (d >= 4) t.l4 += (c3 * (d - 3)) >> 2;
+    }
+    t.dmax = d > t.dmax ? d : t.dmax;
+}
+
+__global__ void __launch_bounds__(kTableThreads) k_slots(uint32_t n, uint4 *vert, uint32_t *acc, uint64_t *sq,
+                                                        u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    Totals t = {};
     for (uint64_t v = (uint64_t)blockIdx.x * wpb + warp; v < n; v += (uint64_t)gridDim.x * wpb) {
         const uint4 vr = vert[v];
         const uint32_t o = vr.x, d = vr.y;
+        if (d > kLongList) continue;   // k_slots_long
         uint64_t run = 0, qsum = 0;
-        // kUnroll chunks of 32 per round: their gathers of d_x are issued
-        // together, so a hub's list costs d / (32 kUnroll) round trips
+        // kUnroll chunks of 32 per round, their loads issued together
         for (uint32_t base = 0; base < d; base += kWarp * kUnroll) {
-            uint32_t x[kUnroll], w[kUnroll];
+            uint32_t w[kUnroll];
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
                 const uint32_t i = base + u * kWarp + lane;
-                x[u] = 0;
-                w[u] = 0;
-                if (i < d) {
-                    x[u] = col[o + i];
-                    if (x[u] >= n) {
-                        err |= kErrRange;
-                    } else {
-                        if (x[u] == v) err |= kErrSelf;
-                        if (i > 0 && col[o + i - 1] >= x[u]) err |= kErrOrder;
-                        const uint32_t dx = vert[x[u]].y;
-                        w[u] = dx ? dx - 1 : 0;
-                    }
-                }
+                w[u] = i < d ? acc[o + i] : 0u;
             }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
@@ -97,54 +154,64 @@ __global__ void __launch_bounds__(kTableThreads) k_slots(uint32_t n, const uint3
                 if (i < d) {
                     acc[o + i] = (uint32_t)(run + incl - w[u]);
                     sq[o + i] = qsum + incl2 - w2;
-                    slot[o + i] = make_uint4(x[u], 0u, 0u, 0u);
-                    owner[o + i] = (uint32_t)v;
                 }
                 run += __shfl_sync(0xffffffffu, incl, 31);
                 qsum += __shfl_sync(0xffffffffu, incl2, 31);
             }
         }
-        if (lane == 0) {
-            const uint64_t S = run;
-            vert[v].z = (uint32_t)S;
-            const u128 g0 = d >= 1 ? (u128)(d - 1) * S : 0;
-            const u128 g1 = d >= 2 ? (u128)(d - 1) * (d - 2) * S : 0;
-            const u128 g2 = (u128)S * S - qsum;
-            gam0[v] = g0;
-            gam1[v] = g1;
-            gam2[v] = g2;
-            t_g0 += g0;
-            t_g1 += g1;
-            t_g2 += g2;
-            if (d >= 3) {
-                // C(d,3) and C(d,4) without a 128-bit division: d(d-1)/2 is
-                // exact in 64 bits, 3 divides it or d-2, and 4 C(d,4) = C(d,3)(d-3)
-                const uint64_t h = (uint64_t)d * (d - 1) / 2;
-                const u128 c3 = (d - 2) % 3 == 0 ? (u128)h * ((d - 2) / 3) : (u128)(h / 3) * (d - 2);
-                t_l3 += c3;
-                if (d >= 4) t_l4 += (c3 * (d - 3)) >> 2;
-            }
-            dmax = d > dmax ? d : dmax;
-        }
+        if (lane == 0) vertex_weights(v, d, run, qsum, vert, gam0, gam1, gam2, t);
     }
-    if (err) atomicOr(flags, err);
     // block reduction of the totals (lane 0 of each warp holds its share)
-    __shared__ u128 sh[5][kTableThreads / kWarp];
-    __shared__ uint32_t shmax[kTableThreads / kWarp];
-    if (lane == 0) {
-        sh[0][warp] = t_g0; sh[1][warp] = t_g1; sh[2][warp] = t_g2; sh[3][warp] = t_l3; sh[4][warp] = t_l4;
-        shmax[warp] = dmax;
-    }
+    __shared__ Totals sh[kTableThreads / kWarp];
+    if (lane == 0) sh[warp] = t;
     __syncthreads();
-    if (threadIdx.x < 5) {
-        u128 s = 0;
-        for (int w = 0; w < wpb; ++w) s += sh[threadIdx.x][w];
-        partials[(uint64_t)blockIdx.x * 6 + threadIdx.x] = s;
-    } else if (threadIdx.x == 5) {
-        uint32_t m = 0;
-        for (int w = 0; w < wpb; ++w) m = shmax[w] > m ? shmax[w] : m;
-        partials[(uint64_t)blockIdx.x * 6 + 5] = m;
+    if (threadIdx.x == 0) {
+        Totals b = {};
+        for (int w = 0; w < wpb; ++w) b.add(sh[w]);
+        b.store(partials + (uint64_t)blockIdx.x * 6);
     }
+}
+
+// lists longer than kLongList: a block per list scans NT x 4 entries a round
+// (each thread 4 consecutive ones, then a block scan of the thread sums)
+__global__ void __launch_bounds__(kLongThreads) k_slots_long(uint32_t n, uint4 *vert, uint32_t *acc, uint64_t *sq,
+                                                            u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials) {
+    __shared__ uint64_t s_w[kLongThreads / kWarp], s_q[kLongThreads / kWarp];
+    Totals t = {};
+    for_each_vertex<kLongThreads>(n, vert, [](uint4 vr) { return vr.y > kLongList; }, [&](uint32_t v) {
+        const uint4 vr = vert[v];
+        const uint32_t o = vr.x, d = vr.y;
+        uint64_t run = 0, qsum = 0;
+        for (uint32_t base = 0; base < d; base += kLongThreads * 4) {
+            const uint32_t i0 = base + 4 * threadIdx.x;
+            uint32_t w[4];
+            uint64_t lw = 0, lq = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                w[k] = i0 + k < d ? acc[o + i0 + k] : 0u;
+                lw += w[k];
+                lq += (uint64_t)w[k] * w[k];
+            }
+            uint64_t tw, tq;
+            const uint64_t iw = block_incl_scan<uint64_t, kLongThreads>(lw, tw, s_w);
+            const uint64_t iq = block_incl_scan<uint64_t, kLongThreads>(lq, tq, s_q);
+            uint64_t ew = run + iw - lw, eq = qsum + iq - lq;   // exclusive prefixes at i0
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (i0 + k < d) {
+                    acc[o + i0 + k] = (uint32_t)ew;
+                    sq[o + i0 + k] = eq;
+                }
+                ew += w[k];
+                eq += (uint64_t)w[k] * w[k];
+            }
+            run += tw;
+            qsum += tq;
+        }
+        if (threadIdx.x == 0) vertex_weights(v, d, run, qsum, vert, gam0, gam1, gam2, t);
+        __syncthreads();
+    });
+    if (threadIdx.x == 0) t.store(partials + (uint64_t)blockIdx.x * 6);
 }
 
 __global__ void k_totals(const u128 *partials, int blocks, DevTotals *tot) {
@@ -348,17 +415,18 @@ __global__ void __launch_bounds__(kLongThreads) k_sigma_alias_long(uint32_t n, c
                                                                   const uint32_t *__restrict__ acc, uint4 *slot,
                                                                   uint32_t *idx, uint64_t *pre) {
     uint32_t *slot32 = reinterpret_cast<uint32_t *>(slot);
-    for (uint64_t v = blockIdx.x; v < n; v += gridDim.x) {
-        const uint4 vr = vert[v];
-        const uint32_t o = vr.x, d = vr.y, S = vr.z;
-        if (d <= kLongList || S == 0) continue;   // block-uniform
-        block_alias<uint64_t, kLongThreads>(
-            d, (uint64_t)S, [&](uint32_t j) { return (uint64_t)acc_weight(acc, o, d, S, j); }, idx + o, pre + o,
-            [&](uint32_t j, uint64_t thr, uint32_t alias) {
-                slot32[4 * (uint64_t)(o + j) + 1] = (uint32_t)thr;
-                slot32[4 * (uint64_t)(o + j) + 2] = alias;
-            });
-    }
+    for_each_vertex<kLongThreads>(
+        n, vert, [](uint4 vr) { return vr.y > kLongList && vr.z != 0; },
+        [&](uint32_t v) {
+            const uint4 vr = vert[v];
+            const uint32_t o = vr.x, d = vr.y, S = vr.z;
+            block_alias<uint64_t, kLongThreads>(
+                d, (uint64_t)S, [&](uint32_t j) { return (uint64_t)acc_weight(acc, o, d, S, j); }, idx + o, pre + o,
+                [&](uint32_t j, uint64_t thr, uint32_t alias) {
+                    slot32[4 * (uint64_t)(o + j) + 1] = (uint32_t)thr;
+                    slot32[4 * (uint64_t)(o + j) + 2] = alias;
+                });
+        });
 }
 
 // ---------------------------------------------------- vertex (seed) tables ---
@@ -649,12 +717,15 @@ cudaError_t launch_vertices(const void *row_ptr, int is64, uint32_t n, uint64_t 
     return cudaGetLastError();
 }
 
+static unsigned long_blocks(uint32_t n);
+int slot_partial_rows(uint32_t n) { return table_blocks(n) + (int)long_blocks(n); }
+
 static unsigned long_blocks(uint32_t n) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint64_t cap = (uint64_t)sms * 4;
-    return (unsigned)(n < cap ? (n ? n : 1) : cap);
+    const uint64_t cap = (uint64_t)sms * 4, chunks = ((uint64_t)n + kLongThreads - 1) / kLongThreads;
+    return (unsigned)(chunks < cap ? (chunks ? chunks : 1) : cap);
 }
 
 static unsigned flat_blocks(uint64_t items) {
@@ -670,8 +741,18 @@ static unsigned flat_blocks(uint64_t items) {
 cudaError_t launch_slots(uint32_t n, uint64_t nnz, const uint32_t *col, uint4 *vert, uint4 *slot, uint32_t *acc,
                          uint32_t *owner, uint64_t *sq, u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials,
                          int blocks, uint32_t *flags, cudaStream_t s) {
-    k_slots<<<blocks, kTableThreads, 0, s>>>(n, col, vert, slot, acc, owner, sq, gam0, gam1, gam2, partials, flags);
+    k_owner<<<blocks, kTableThreads, 0, s>>>(n, vert, owner);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (nnz) {
+        k_slot_weights<<<flat_blocks(nnz), 256, 0, s>>>(n, nnz, col, vert, owner, slot, acc, flags);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_slots<<<blocks, kTableThreads, 0, s>>>(n, vert, acc, sq, gam0, gam1, gam2, partials);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_slots_long<<<long_blocks(n), kLongThreads, 0, s>>>(n, vert, acc, sq, gam0, gam1, gam2,
+                                                         partials + (uint64_t)blocks * 6);
+    e = cudaGetLastError();
     if (e != cudaSuccess || nnz == 0) return e;
     k_twin<<<flat_blocks(nnz), 256, 0, s>>>(n, nnz, vert, col, owner, slot, flags);
     return cudaGetLastError();
