@@ -150,17 +150,19 @@ __device__ void block_alias(uint32_t d, T W, Weight weight, uint32_t *idx, T *pr
 
 // Calls body(v) for every vertex v < n whose record passes pred, one vertex at
 // a time for the whole block (body is block-cooperative).  Blocks take chunks
-// of NT vertices and test a chunk's records in parallel, so a block touches
-// n / gridDim records in NT-wide coalesced loads rather than one by one.
-template <int NT, typename Pred, typename Body>
+// of CH <= NT vertices and test a chunk's records in parallel, so a block
+// touches n / gridDim records in coalesced loads rather than one by one; a
+// small CH spreads frequent qualifying vertices over more blocks.
+template <int NT, int CH = NT, typename Pred, typename Body>
 __device__ void for_each_vertex(uint32_t n, const uint4 *rec, Pred pred, Body body) {
-    __shared__ uint32_t found[NT];
+    static_assert(CH <= NT, "chunk larger than the block");
+    __shared__ uint32_t found[CH];
     __shared__ uint32_t nfound;
-    for (uint64_t v0 = (uint64_t)blockIdx.x * NT; v0 < n; v0 += (uint64_t)gridDim.x * NT) {
+    for (uint64_t v0 = (uint64_t)blockIdx.x * CH; v0 < n; v0 += (uint64_t)gridDim.x * CH) {
         if (threadIdx.x == 0) nfound = 0;
         __syncthreads();
         const uint64_t v = v0 + threadIdx.x;
-        if (v < n && pred(rec[v])) found[atomicAdd(&nfound, 1u)] = (uint32_t)v;
+        if (threadIdx.x < CH && v < n && pred(rec[v])) found[atomicAdd(&nfound, 1u)] = (uint32_t)v;
         __syncthreads();
         const uint32_t cnt = nfound;
         for (uint32_t k = 0; k < cnt; ++k) body(found[k]);

@@ -5,8 +5,8 @@
 // N_{u,v} = {x in N_u : x above v}, d_{u,v} = |N_{u,v}|.  Every list N_v is
 // stored sorted by that key, highest first (rlist), so N_{v,u} is its first
 // d_{v,u} entries and d_{v,u} is the position of u in it:
-//   * lists of at most 32 entries: a warp per list, each lane counts the keys
-//     above its own;
+//   * lists of at most 128 entries: a warp per list, each entry's rank is the
+//     count of keys above its own;
 //   * lists of at most kTile entries: a block per list, bitonic sort in
 //     shared memory;
 //   * longer lists: a block per list sorts tiles of kTile keys in shared
@@ -29,6 +29,7 @@ constexpr int kWarp = 32;
 constexpr uint32_t kTile = 4096;      // keys sorted per shared-memory pass (32 KB)
 constexpr int kSortThreads = 512;
 constexpr int kListThreads = 256;
+constexpr uint32_t kWarpKeys = 4;     // k_rank_warp: lists up to 128 entries
 constexpr uint32_t kLongList = 256;   // longer lists: k_min_alias_long, a block per list
 
 __device__ __forceinline__ uint64_t order_key(uint32_t x, uint32_t dx) { return ((uint64_t)dx << 32) | x; }
@@ -56,6 +57,9 @@ __device__ __forceinline__ void emit(const uint32_t *col, uint32_t o, uint32_t d
     rank[o + find_pos(col, o, d, x)] = q;
 }
 
+// lists of at most kWarpKeys * 32 entries: lane l holds entries l, l + 32, ...;
+// an entry's rank is the number of keys above its own, counted against every
+// key of the list broadcast by shuffles
 __global__ void __launch_bounds__(kListThreads) k_rank_warp(uint32_t n, const uint4 *__restrict__ vert,
                                                            const uint32_t *__restrict__ col, uint2 *rlist,
                                                            uint32_t *rank) {
@@ -63,20 +67,37 @@ __global__ void __launch_bounds__(kListThreads) k_rank_warp(uint32_t n, const ui
     for (uint64_t v = (uint64_t)blockIdx.x * wpb + warp; v < n; v += (uint64_t)gridDim.x * wpb) {
         const uint4 vr = vert[v];
         const uint32_t o = vr.x, d = vr.y;
-        if (d == 0 || d > (uint32_t)kWarp) continue;   // warp-uniform
-        uint32_t x = 0, dx = 0;
-        uint64_t key = 0;                               // below every real key (d_x >= 1)
-        if ((uint32_t)lane < d) {
-            x = col[o + lane];
-            dx = vert[x].y;
-            key = order_key(x, dx);
-        }
-        uint32_t r = 0;
+        if (d == 0 || d > kWarpKeys * (uint32_t)kWarp) continue;   // warp-uniform
+        const int rounds = (int)((d + kWarp - 1) / kWarp);
+        uint32_t x[kWarpKeys], dx[kWarpKeys], r[kWarpKeys];
+        uint64_t key[kWarpKeys];
 #pragma unroll
-        for (int j = 0; j < kWarp; ++j) r += __shfl_sync(0xffffffffu, key, j) > key;
-        if ((uint32_t)lane < d) {
-            rlist[o + r] = make_uint2(x, dx);
-            rank[o + lane] = r;
+        for (int k = 0; k < kWarpKeys; ++k) {
+            const uint32_t i = k * kWarp + lane;
+            x[k] = dx[k] = r[k] = 0;
+            key[k] = 0;                               // below every real key (d_x >= 1)
+            if (i < d) {
+                x[k] = col[o + i];
+                dx[k] = vert[x[k]].y;
+                key[k] = order_key(x[k], dx[k]);
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < kWarpKeys; ++kk) {
+            if (kk >= rounds) break;                  // warp-uniform
+            for (int j = 0; j < kWarp; ++j) {
+                const uint64_t other = __shfl_sync(0xffffffffu, key[kk], j);
+#pragma unroll
+                for (int k = 0; k < kWarpKeys; ++k) r[k] += other > key[k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kWarpKeys; ++k) {
+            const uint32_t i = k * kWarp + lane;
+            if (i < d) {
+                rlist[o + r[k]] = make_uint2(x[k], dx[k]);
+                rank[o + i] = r[k];
+            }
         }
     }
 }
@@ -122,8 +143,8 @@ __global__ void __launch_bounds__(kSortThreads) k_rank_block(uint32_t n, const u
                                                             const uint32_t *__restrict__ col, uint2 *rlist,
                                                             uint32_t *rank) {
     __shared__ uint64_t k[kTile];
-    for_each_vertex<kSortThreads>(
-        n, vert, [](uint4 vr) { return vr.y > (uint32_t)kWarp && vr.y <= kTile; },
+    for_each_vertex<kSortThreads, kWarp>(
+        n, vert, [](uint4 vr) { return vr.y > kWarpKeys * (uint32_t)kWarp && vr.y <= kTile; },
         [&](uint32_t v) {
             const uint4 vr = vert[v];
             const uint32_t o = vr.x, d = vr.y;
@@ -425,7 +446,7 @@ cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const
         k_rank_warp<<<grid_for((uint64_t)n, kListThreads / kWarp, 8), kListThreads, 0, s>>>(n, vert, col, rlist,
                                                                                              m.rank);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_rank_block<<<grid_for((uint64_t)n, kSortThreads, 4), kSortThreads, 0, s>>>(n, vert, col, rlist, m.rank);
+        k_rank_block<<<grid_for((uint64_t)n, kWarp, 4), kSortThreads, 0, s>>>(n, vert, col, rlist, m.rank);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         k_rank_long<<<grid_for((uint64_t)n, kSortThreads, 1), kSortThreads, 0, s>>>(n, vert, col, m.a, m.b, rlist,
                                                                                     m.rank);

@@ -3,7 +3,7 @@
 Bit-exact: the ordered lists, d_{v,u}, Gamma-check_v and its total, the
 alias tables of sigma-check^(v) and pi-check, every per-sample tuple with its
 class and c(s), every (class, c) count, for both probe strategies; the lists
-cover the three sort tiers (at most 32 entries, at most 4096, longer -- the
+cover the three sort tiers (at most 128 entries, at most 4096, longer -- the
 hub graph's centre has 11,999 neighbours and needs two merge rounds).  FP64
 estimates of the MOSS-4 + MOSS-4Min mix: relative 1e-9 (same arithmetic,
 same order).
