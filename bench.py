@@ -66,8 +66,9 @@ def parse():
     p.add_argument("--graphs", type=int, default=512, help="batch mode: number of graphs")
     p.add_argument("--rate", type=float, default=2000.0, help="serve mode: mean arrivals per second")
     p.add_argument("--duration", type=float, default=2.0, help="serve mode: seconds of arrivals")
-    p.add_argument("--probe", default="hash", choices=["hash", "search"],
-                   help="induced-edge tests: hashed edge set (default) or sorted-list search")
+    p.add_argument("--probe", default="auto", choices=["auto", "hash", "filter", "search"],
+                   help="induced-edge tests: auto (filtered set when the set exceeds 64 MiB, else the set), "
+                        "hashed edge set, set behind a Bloom filter, or sorted-list search")
     return p.parse_args()
 
 
@@ -225,7 +226,18 @@ class Clocks:
 DEFER_CHUNK = 1 << 25   # Path-5 sample ids per main/deferred launch pair
 
 
-def launches_per_step(k: int, budget: int, mix: bool) -> int:
+def resolved_probe(name: str, row_ptr) -> str:
+    """The strategy the library picks for --probe auto: the filtered set when
+    the hashed set (next power of two >= nnz buckets of 16 B) exceeds 64 MiB."""
+    if name != "auto":
+        return name
+    nnz, b = int(row_ptr[-1]), 2
+    while b < nnz:
+        b <<= 1
+    return "filter" if b * 16 > (64 << 20) else "hash"
+
+
+def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False) -> int:
     """Kernels of one step: load 6 (vertices, owners, slot weights, slot scans,
     twins, totals); build 7
     (two sigma alias passes, four vertex-table phases, edge hash); MOSS-4Min
@@ -234,7 +246,7 @@ def launches_per_step(k: int, budget: int, mix: bool) -> int:
     chunk of DEFER_CHUNK ids a main launch, a deferred launch and a reduce;
     one finalize."""
     from paper_1509_08089_gb300.dist import sub_budgets
-    n = 6 + 7 + (11 if mix else 0) + 1
+    n = 6 + 7 + (1 if filtered else 0) + (11 if mix else 0) + 1
     for m, K in sub_budgets(k, budget, mix):
         n += 3 * -(-K // DEFER_CHUNK) if m == 2 else 2
     return n
@@ -282,7 +294,8 @@ def run_gpu(args):
         tdist.all_reduce(t)
         return t.cpu().numpy()
 
-    probe = moss.PROBE_HASH if args.probe == "hash" else moss.PROBE_SEARCH
+    probe = {"auto": moss.PROBE_AUTO, "hash": moss.PROBE_HASH, "filter": moss.PROBE_FILTER,
+             "search": moss.PROBE_SEARCH}[args.probe]
 
     def step(src_rp, src_col, seed):
         h = moss.moss_graph_load_csr(src_rp, src_col, device=dev, stream=stream)
@@ -390,7 +403,7 @@ def run_gpu(args):
         peaks = json.load(open(ppath))
     peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    probe_name = "hash" if args.probe == "hash" else "search"
+    probe_name = resolved_probe(args.probe, rp)
     traffic = None
     tpath = os.path.join(ROOT, "profiles", f"dram_traffic_{args.workload}.txt")
     if os.path.exists(tpath):
@@ -405,7 +418,7 @@ def run_gpu(args):
         # counters describe the kernel only while its source is unchanged
         if hashlib.sha256(src).hexdigest()[:16] == rec.get("source_sha"):
             traffic = rec
-    if sect is not None:
+    if sect is not None and f"{name[dom]}_{probe_name}" in sect:
         K, tms = times[dom]
         spb = sect[f"{name[dom]}_{probe_name}"]["sectors_per_sample"]
         ach = spb * 32.0 * K / (tms / 1000.0) / 1e9
@@ -422,13 +435,13 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "budget_per_gpu": args.budget, "seed": args.seed, "probe": args.probe,
+        "config": {"workload": WORKLOAD, "budget_per_gpu": args.budget, "seed": args.seed, "probe": resolved_probe(args.probe, rp),
                    "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}"},
         "e2e": {"value": samples_per_step / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": roof,
         "clocks": clk,
-        "gpu_launches": launches_per_step(k, args.budget, mix) * args.steps,
+        "gpu_launches": launches_per_step(k, args.budget, mix, probe_name == "filter") * args.steps,
         "wall_s_timed": t_wall,
         "step_ms": step_ms,
     }

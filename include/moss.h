@@ -77,10 +77,18 @@ extern "C" {
 
 /* How the induced-edge tests of CIS() (Algorithms 1, 3, 4) are answered:
  * SEARCH: binary search in the shorter sorted neighbour list (O(log d) loads);
- * HASH (default): one lookup in a hashed set of all edges (one 16-byte bucket
- * load in the common case).  Both give identical results. */
+ * HASH: one lookup in a hashed set of all edges (one 16-byte bucket load in
+ * the common case);
+ * FILTER: the hashed set behind a blocked Bloom filter of about 8 bits per
+ * edge (3 bits of one 32-bit word per edge, no false negatives): a pair the
+ * filter rejects is a non-edge without touching the set, so on a graph whose
+ * set does not fit the L2 cache most probes stay in L2;
+ * AUTO (default): FILTER when the set exceeds 64 MiB, else HASH, decided by
+ * moss_build_tables.  All give identical results. */
 #define MOSS_PROBE_SEARCH  0
 #define MOSS_PROBE_HASH    1
+#define MOSS_PROBE_FILTER  2
+#define MOSS_PROBE_AUTO    3
 
 typedef struct moss_graph moss_graph;
 
@@ -133,7 +141,8 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
 /* Sampling tables (Sec. 4.1.3 WeightRandomVertex, Sec. 5.1.4): the per-list
  * alias tables of sigma^(v) (eq. 1), the vertex alias tables of pi (k_mask
  * bit 4) and rho^(1), rho^(2) (k_mask bit 5) from the exact weights computed
- * at load, and, under MOSS_PROBE_HASH, the hashed edge set.  k_mask: any
+ * at load, and the hashed edge set and its filter as the probe strategy
+ * needs them.  k_mask: any
  * non-empty combination of (1<<4), (1<<5) and MOSS_TABLES_4MIN, which adds
  * the MOSS-4Min tables (Sec. 4.2): every N_v ordered by the total order,
  * d_{v,u} per slot, Gamma-check_v, the alias tables of sigma-check^(v)
@@ -145,8 +154,8 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
 int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream);
 
 /* Select the probe strategy (MOSS_PROBE_*) for later samples.  Switching to
- * MOSS_PROBE_HASH requires moss_build_tables afterwards (MOSS_ESTATE until
- * then). */
+ * a strategy whose structures were not built (the hashed set, the filter)
+ * requires moss_build_tables afterwards (MOSS_ESTATE until then). */
 int moss_set_probe(moss_graph *g, int strategy);
 
 /* Sample-and-estimate.  k = 4: MOSS-4 with K = budget.  k = 5: T-5 with
@@ -335,6 +344,9 @@ int moss_graph_stats(const moss_graph *g, moss_stats *out);
  *   MOSS_TABLE_MIN_SLOT  nnz x {uint64 sigma-check threshold, uint32 alias
  *                        (position in N_v), u, off_u, d_u, d_{v,u}, d_{u,v}}
  *   MOSS_TABLE_MIN_LIST  nnz x {uint32 x, d_x}: each N_v highest first
+ * and, after a build under MOSS_PROBE_FILTER (or AUTO choosing it):
+ *   MOSS_TABLE_FILTER    W x uint32 filter words, W the largest power of two
+ *                        <= nnz / 8 (at least 1)
  * bytes must equal the table size.  Synchronous. */
 #define MOSS_TABLE_VERT   0
 #define MOSS_TABLE_SLOT   1
@@ -346,6 +358,7 @@ int moss_graph_stats(const moss_graph *g, moss_stats *out);
 #define MOSS_TABLE_MIN_VERT  11
 #define MOSS_TABLE_MIN_SLOT  12
 #define MOSS_TABLE_MIN_LIST  13
+#define MOSS_TABLE_FILTER    14
 int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t bytes);
 
 void moss_graph_free(moss_graph *g);

@@ -11,7 +11,8 @@ ordered-list entries of 8 B.  Each
 probe is either a lower-bound search with early exit in the shorter sorted
 list (MOSS_PROBE_SEARCH, which also reads the two vertex records) or the home
 bucket of the hashed edge set (MOSS_PROBE_HASH, 16 B buckets; the rare
-continuation into the next bucket is not counted).
+continuation into the next bucket is not counted), or the word of the edge
+filter followed by that bucket only when the filter passes (MOSS_PROBE_FILTER).
 The draws are replayed from the oracle's Philox words and tables, so the
 count is exact per sample; the mean over a few thousand samples is the
 per-sample figure used by the roofline ("achieved" = figure x 32 B x samples
@@ -46,6 +47,33 @@ def idx(x: int, m: int) -> int:
 M64 = (1 << 64) - 1
 
 
+def filter_hash(k):
+    """The library's edge-filter finaliser (second xor-shift-multiply chain);
+    k a Python int or a numpy uint64 array."""
+    if isinstance(k, np.ndarray):
+        u = np.uint64
+        k = k ^ u(0x9e3779b97f4a7c15)
+        k = k ^ (k >> u(31))
+        k = k * u(0xbf58476d1ce4e5b9)
+        k = k ^ (k >> u(27))
+        k = k * u(0x94d049bb133111eb)
+        return k ^ (k >> u(31))
+    k ^= 0x9e3779b97f4a7c15
+    k ^= k >> 31
+    k = (k * 0xbf58476d1ce4e5b9) & M64
+    k ^= k >> 27
+    k = (k * 0x94d049bb133111eb) & M64
+    return k ^ (k >> 31)
+
+
+def filter_mask(h):
+    if isinstance(h, np.ndarray):
+        one = np.uint32(1)
+        return ((one << (h & np.uint64(31)).astype(np.uint32)) | (one << ((h >> np.uint64(5)) & np.uint64(31)).astype(np.uint32))
+                | (one << ((h >> np.uint64(10)) & np.uint64(31)).astype(np.uint32)))
+    return (1 << (h & 31)) | (1 << ((h >> 5) & 31)) | (1 << ((h >> 10) & 31))
+
+
 def edge_bucket(a: int, b: int, shift: int) -> int:
     """Home bucket of edge {a, b} in the library's hashed edge set (key
     (min << 32) | max through three xor-shift-multiply steps, top bits)."""
@@ -73,6 +101,17 @@ class Replay:
         while buckets < len(col):
             buckets <<= 1
         self.shift = 64 - (buckets.bit_length() - 1)
+        if probe == "filter":   # the library's filter: largest power of two <= nnz / 8 words
+            words = 1
+            while words * 2 <= len(col) // 8:
+                words <<= 1
+            self.fshift = 64 - (words.bit_length() - 1)
+            owner = np.repeat(np.arange(self.g.n, dtype=np.uint64), self.deg.astype(np.int64))
+            c64 = col.astype(np.uint64)
+            keep = owner < c64
+            h = filter_hash((owner[keep] << np.uint64(32)) | c64[keep])
+            self.filter = np.zeros(words, dtype=np.uint32)
+            np.bitwise_or.at(self.filter, (h >> np.uint64(self.fshift)).astype(np.int64), filter_mask(h))
 
     def min_tables(self):
         if not hasattr(self, "rank"):
@@ -119,6 +158,15 @@ class Replay:
         return out
 
     def probe(self, a, b, touched):
+        if self.probe_kind == "filter":   # filter word (8 per sector); the set only when it may hold the pair
+            a, b = int(a), int(b)
+            h = filter_hash((min(a, b) << 32) | max(a, b))
+            w = h >> self.fshift
+            touched.add(("filter", w >> 3))
+            m = filter_mask(h)
+            if int(self.filter[w]) & m == m:
+                touched.add(("hash", edge_bucket(a, b, self.shift) >> 1))
+            return
         if self.probe_kind == "hash":   # home bucket of 16 B: two per sector
             touched.add(("hash", edge_bucket(int(a), int(b), self.shift) >> 1))
             return
@@ -221,10 +269,11 @@ def model(workload: str, samples: int = 4000, seed: int = 42) -> dict:
     rp, col = synth.workload(workload)
     out = {"workload": workload, "samples": samples, "seed": seed,
            "layout": ("32 B vertex alias records with the alias's vertex record, 16 B vertex/slot records, "
-                      "4 B ids and ACC, 8 B Q, 16 B edge-hash buckets (home bucket counted); MOSS-4Min: 16 B "
+                      "4 B ids and ACC, 8 B Q, 16 B edge-hash buckets (home bucket counted), 4 B edge-filter words "
+                      "(the set's bucket only when the filter passes); MOSS-4Min: 16 B "
                       "vertex, 32 B slot, 8 B list records; 32 B sectors"),
            "source": "written by oracle/sector_model.py"}
-    for probe, suffix in (("search", "_search"), ("hash", "_hash")):
+    for probe, suffix in (("search", "_search"), ("hash", "_hash"), ("filter", "_filter")):
         rep = Replay(rp, col, probe)
         for method, name in ((0, "MOSS4"), (1, "T5"), (2, "PATH5")):
             first = 1_000_000

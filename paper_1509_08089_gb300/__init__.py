@@ -25,11 +25,12 @@ LIB_PATH = os.path.join(_HERE, "libmoss.so")
 MOSS_OK, MOSS_EINVAL, MOSS_ENOMEM, MOSS_ECUDA, MOSS_EGRAPH, MOSS_EOVERFLOW, MOSS_ESTATE = 0, -1, -2, -3, -4, -5, -6
 MOSS_EBUSY = -7
 MOSS4, T5, PATH5, MOSS4MIN = 0, 1, 2, 3
-PROBE_SEARCH, PROBE_HASH = 0, 1
+PROBE_SEARCH, PROBE_HASH, PROBE_FILTER, PROBE_AUTO = 0, 1, 2, 3
 NSLOTS = 22
 TABLES_4MIN = 1 << 6
 TABLE_VERT, TABLE_SLOT, TABLE_ACC, TABLE_SEED0, TABLE_GAMMA0 = 0, 1, 2, 3, 6
 TABLE_MIN_SEED, TABLE_MIN_GAMMA, TABLE_MIN_VERT, TABLE_MIN_SLOT, TABLE_MIN_LIST = 9, 10, 11, 12, 13
+TABLE_FILTER = 14
 
 
 class moss_stats(ctypes.Structure):
@@ -467,12 +468,19 @@ class Graph:
     """Owning wrapper: load, build, sample, free."""
 
     def __init__(self, row_ptr, col, device: int = 0, stream=None, k_mask: int = (1 << 4) | (1 << 5),
-                 probe: int = PROBE_HASH):
+                 probe: int = PROBE_AUTO):
         self.handle = moss_graph_load_csr(row_ptr, col, device=device, stream=stream)
         self.device = device
         moss_set_probe(self.handle, probe)
+        self.k_mask = k_mask
         if k_mask:
             moss_build_tables(self.handle, k_mask, stream)
+
+    def set_probe(self, probe: int, stream=None):
+        """Switch the probe strategy, building what it needs."""
+        moss_set_probe(self.handle, probe)
+        if self.k_mask:
+            moss_build_tables(self.handle, self.k_mask, stream)
 
     def estimate(self, k: int, budget: int, seed: int, stream=None) -> dict:
         return result_dict(moss_sample_estimate(self.handle, k, budget, seed, stream))

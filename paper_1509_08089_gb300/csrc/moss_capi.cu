@@ -179,9 +179,11 @@ struct moss_graph {
     uint32_t *flags = nullptr;   // device status: [0] error bits, [1] matched twins
     uint32_t *defer = nullptr;   // Path-5 deferral bitmap (kDeferChunk bits)
     void *arena = nullptr;       // every device array above lives in this one allocation
-    int probe = MOSS_PROBE_HASH; // membership tests: hashed edge set or list search
+    int probe = MOSS_PROBE_AUTO; // membership tests (MOSS_PROBE_*), as requested
     unsigned long long *hash = nullptr;  // 2 keys per bucket
     uint64_t hash_buckets = 0;
+    uint32_t *filter = nullptr;  // Bloom filter in front of the hash
+    uint64_t filter_words = 0;
     moss_result res_host{};      // host staging of the result
     uint32_t flags_host[2] = {0, 0};
 };
@@ -194,8 +196,28 @@ void release(moss_graph *g) {
     // ordered on the legacy default stream, i.e. after the work of blocking streams
     if (g->arena) cudaFreeAsync(g->arena, 0);
     if (g->hash) cudaFreeAsync(g->hash, 0);
+    if (g->filter) cudaFreeAsync(g->filter, 0);
     if (g->min_arena) cudaFreeAsync(g->min_arena, 0);
     delete g;
+}
+
+// buckets of the hashed edge set: the next power of two >= nnz (>= 4 slots per edge)
+uint64_t hash_buckets_for(uint64_t nnz) {
+    uint64_t b = 2;
+    while (b < nnz) b <<= 1;
+    return b;
+}
+
+// words of the edge filter: the largest power of two <= nnz / 8 (4 to 8 bits per edge)
+uint64_t filter_words_for(uint64_t nnz) {
+    uint64_t w = 1;
+    while (w * 2 <= nnz / 8) w <<= 1;
+    return w;
+}
+
+int effective_probe(const moss_graph *g) {
+    if (g->probe != MOSS_PROBE_AUTO) return g->probe;
+    return hash_buckets_for(g->nnz) * 16 > (64ull << 20) ? MOSS_PROBE_FILTER : MOSS_PROBE_HASH;
 }
 
 DevGraph view(const moss_graph *g) {
@@ -211,12 +233,18 @@ DevGraph view(const moss_graph *g) {
     d.rlist = g->rlist;
     d.defer = g->defer;
     d.n = g->n;
-    const bool use_hash = g->probe == MOSS_PROBE_HASH && (g->built >> 4 & 1u);
+    const int eff = effective_probe(g);
+    const bool use_hash = eff != MOSS_PROBE_SEARCH && (g->built >> 4 & 1u);
+    const bool use_filter = eff == MOSS_PROBE_FILTER && (g->built >> 6 & 1u);
     d.hash = use_hash ? reinterpret_cast<const uint4 *>(g->hash) : nullptr;
+    d.filter = use_hash && use_filter ? g->filter : nullptr;
     uint32_t lg = 0;
     while ((1ULL << lg) < g->hash_buckets) ++lg;
     d.hash_mask = use_hash ? (uint32_t)(g->hash_buckets - 1) : 0;
     d.hash_shift = 64 - lg;
+    uint32_t lf = 0;
+    while ((1ULL << lf) < g->filter_words) ++lf;
+    d.filter_shift = 64 - lf;
     return d;
 }
 
@@ -281,7 +309,9 @@ int read_flags(moss_graph *g, cudaStream_t s) {
 }
 
 bool method_ready(const moss_graph *g, int method) {
-    const bool probes = g->probe != MOSS_PROBE_HASH || (g->built >> 4 & 1u);
+    const int eff = effective_probe(g);
+    const bool probes = eff == MOSS_PROBE_SEARCH ||
+                        ((g->built >> 4 & 1u) && (eff != MOSS_PROBE_FILTER || (g->built >> 6 & 1u)));
     if (method == MOSS_METHOD_MOSS4MIN) return (g->built >> 5 & 1u) && probes;
     return (g->built >> 3 & 1u) && (g->built >> method & 1u) && probes;
 }
@@ -470,11 +500,11 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
     if (e == cudaSuccess && nt > 0)
         e = launch_seed_alias(g->n, g->tot, nt, which, w, seed, vrec, scratch, g->flags, s);
     cudaFreeAsync(scratch, s);
-    bool hashed = false;
-    if (e == cudaSuccess && g->probe == MOSS_PROBE_HASH) {
+    bool hashed = false, filtered = false;
+    const int eff = effective_probe(g);
+    if (e == cudaSuccess && eff != MOSS_PROBE_SEARCH) {
         // at least 4 slots per undirected edge: buckets = next power of two >= nnz
-        uint64_t buckets = 2;
-        while (buckets < g->nnz) buckets <<= 1;
+        const uint64_t buckets = hash_buckets_for(g->nnz);
         if (buckets > (1ULL << 32)) return fail(MOSS_EOVERFLOW, "edge hash above 2^32 buckets");
         if (g->hash && g->hash_buckets != buckets) {
             cudaFreeAsync(g->hash, s);
@@ -492,6 +522,23 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
             e = launch_edge_hash(g->nnz, g->col, g->owner, g->hash, (uint32_t)(buckets - 1), 64 - lg, s);
         hashed = e == cudaSuccess;
     }
+    if (e == cudaSuccess && eff == MOSS_PROBE_FILTER) {
+        const uint64_t words = filter_words_for(g->nnz);
+        if (g->filter && g->filter_words != words) {
+            cudaFreeAsync(g->filter, s);
+            g->filter = nullptr;
+        }
+        if (!g->filter) {
+            e = pool_alloc(g->device, reinterpret_cast<void **>(&g->filter), words * 4, s);
+            if (e != cudaSuccess) return cuda_fail(e, "allocating edge filter");
+            g->filter_words = words;
+        }
+        uint32_t lf = 0;
+        while ((1ULL << lf) < words) ++lf;
+        e = cudaMemsetAsync(g->filter, 0, words * 4, s);
+        if (e == cudaSuccess) e = launch_edge_filter(g->nnz, g->col, g->owner, g->filter, 64 - lf, s);
+        filtered = e == cudaSuccess;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "table kernels");
     bool min_built = false;
     if (k_mask & MOSS_TABLES_4MIN) {
@@ -507,12 +554,13 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
     if (k_mask & (1u << 5)) g->built |= 6u;
     if (hashed) g->built |= 1u << 4;
     if (min_built) g->built |= 1u << 5;
+    if (filtered) g->built |= 1u << 6;
     return MOSS_OK;
 }
 
 int moss_set_probe(moss_graph *g, int strategy) {
     if (!g) return fail(MOSS_EINVAL, "graph is NULL");
-    if (strategy != MOSS_PROBE_SEARCH && strategy != MOSS_PROBE_HASH)
+    if (strategy < MOSS_PROBE_SEARCH || strategy > MOSS_PROBE_AUTO)
         return fail(MOSS_EINVAL, "unknown probe strategy %d", strategy);
     g->probe = strategy;
     return MOSS_OK;
@@ -705,6 +753,10 @@ int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t b
     } else if (table >= MOSS_TABLE_GAMMA0 && table < MOSS_TABLE_GAMMA0 + 3) {
         src = g->gam[table - MOSS_TABLE_GAMMA0];
         need = (uint64_t)g->n * 16;
+    } else if (table == MOSS_TABLE_FILTER) {
+        if (!(g->built >> 6 & 1u)) return fail(MOSS_ESTATE, "edge filter not built");
+        src = g->filter;
+        need = g->filter_words * 4;
     } else if (table >= MOSS_TABLE_MIN_SEED && table <= MOSS_TABLE_MIN_LIST) {
         if (!(g->built >> 5 & 1u)) return fail(MOSS_ESTATE, "MOSS-4Min tables not built");
         switch (table) {

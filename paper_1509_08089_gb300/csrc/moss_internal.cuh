@@ -65,9 +65,11 @@ struct DevGraph {
     const uint4 *mslot;
     const uint2 *rlist;
     const uint4 *hash;      // hashed edge set (2 keys per 16 B bucket), or null: probe by search
+    const uint32_t *filter; // Bloom filter in front of the hash, or null
     uint32_t *defer;        // Path-5 deferral bitmap, kDeferChunk bits
     uint32_t hash_mask;     // buckets - 1
     uint32_t hash_shift;    // 64 - log2(buckets)
+    uint32_t filter_shift;  // 64 - log2(filter words)
     uint32_t n;
 };
 
@@ -90,6 +92,24 @@ __host__ __device__ inline uint32_t edge_bucket(uint64_t k, uint32_t shift) {
     k *= 0xc4ceb9fe1a85ec53ULL;
     k ^= k >> 33;
     return (uint32_t)(k >> shift);
+}
+
+// ----------------------------------------------------------- edge filter --
+// Blocked Bloom filter over the same keys: word = top bits of a second
+// 64-bit finaliser (different constants), three bit positions from its low
+// bits; a key is possibly present when all three bits of its word are set.
+__host__ __device__ inline uint64_t filter_hash(uint64_t k) {
+    k ^= 0x9e3779b97f4a7c15ULL;
+    k ^= k >> 31;
+    k *= 0xbf58476d1ce4e5b9ULL;
+    k ^= k >> 27;
+    k *= 0x94d049bb133111ebULL;
+    k ^= k >> 31;
+    return k;
+}
+
+__host__ __device__ inline uint32_t filter_mask(uint64_t h) {
+    return (1u << (h & 31u)) | (1u << ((h >> 5) & 31u)) | (1u << ((h >> 10) & 31u));
 }
 
 // Status flags raised by kernels (bitwise OR into a device word).
@@ -194,6 +214,9 @@ cudaError_t launch_slots(uint32_t n, uint64_t nnz, const uint32_t *col, uint4 *v
 cudaError_t launch_totals(const u128 *partials, int blocks, DevTotals *tot, cudaStream_t s);
 cudaError_t launch_edge_hash(uint64_t nnz, const uint32_t *col, const uint32_t *owner, unsigned long long *table,
                              uint32_t mask, uint32_t shift, cudaStream_t s);
+// filter of 2^(64 - shift) words, zeroed beforehand
+cudaError_t launch_edge_filter(uint64_t nnz, const uint32_t *col, const uint32_t *owner, uint32_t *filter,
+                               uint32_t shift, cudaStream_t s);
 cudaError_t launch_sigma_alias(uint32_t n, const uint4 *vert, const uint32_t *acc, uint4 *slot,
                                uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s);
 // vertex alias tables of up to 3 weights in the same launches (seed[t]: 2n

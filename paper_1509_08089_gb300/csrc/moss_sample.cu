@@ -146,10 +146,19 @@ __device__ __forceinline__ uint32_t probe_hash(const DevGraph &g, const uint32_t
     uint32_t bk[P];
     uint32_t found = 0, pending = (1u << P) - 1u;
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-        key[p] = edge_key(a[p], b[p]);
-        bk[p] = edge_bucket(key[p], g.hash_shift);
+    for (int p = 0; p < P; ++p) key[p] = edge_key(a[p], b[p]);
+    if (g.filter) {   // warp-uniform: only pairs the filter cannot rule out go to the set
+        uint32_t word[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) word[p] = ld1(g.filter + (filter_hash(key[p]) >> g.filter_shift));
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const uint32_t m = filter_mask(filter_hash(key[p]));
+            if ((word[p] & m) != m) pending &= ~(1u << p);
+        }
     }
+#pragma unroll
+    for (int p = 0; p < P; ++p) bk[p] = edge_bucket(key[p], g.hash_shift);
     for (uint32_t it = 0; pending != 0 && it <= g.hash_mask; ++it) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -593,7 +602,7 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocks)
     __shared__ uint8_t lut5[kLut];
     __shared__ uint32_t hist[kWarps][kSlots];
     __shared__ DevGraph gsh[kWarps];
-    static_assert(sizeof(DevGraph) % 4 == 0 && sizeof(DevGraph) / 4 <= 32, "graph descriptor staging");
+    static_assert(sizeof(DevGraph) % 4 == 0 && sizeof(DevGraph) / 4 <= 64, "graph descriptor staging");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < 64; i += kThreads) lut4[i] = g_lut4[i];
     for (int i = threadIdx.x; i < kLut; i += kThreads) lut5[i] = g_lut5[i];
@@ -610,8 +619,8 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocks)
             if (tasks[lo + half].tile0 <= t) { lo += half + 1; len -= half + 1; } else { len = half; }
         }
         const BatchTask tk = tasks[lo - 1];
-        if (lane < (int)(sizeof(DevGraph) / 4))
-            reinterpret_cast<uint32_t *>(&gsh[warp])[lane] = reinterpret_cast<const uint32_t *>(graphs + tk.graph)[lane];
+        for (int wd = lane; wd < (int)(sizeof(DevGraph) / 4); wd += 32)
+            reinterpret_cast<uint32_t *>(&gsh[warp])[wd] = reinterpret_cast<const uint32_t *>(graphs + tk.graph)[wd];
         if (lane < kSlots) hist[warp][lane] = 0;
         __syncwarp();
         const DevGraph &g = gsh[warp];

@@ -297,6 +297,18 @@ __global__ void k_edge_hash(uint64_t nnz, const uint32_t *__restrict__ col, cons
     }
 }
 
+// --------------------------------------------------------- edge filter ---
+// One thread per slot sets the three bits of each edge {v, x}, v < x.
+__global__ void k_edge_filter(uint64_t nnz, const uint32_t *__restrict__ col, const uint32_t *__restrict__ owner,
+                              uint32_t *filter, uint32_t shift) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = owner[p], x = col[p];
+        if (x <= v) continue;
+        const uint64_t h = filter_hash(edge_key(v, x));
+        atomicOr(filter + (h >> shift), filter_mask(h));
+    }
+}
+
 // ------------------------------------------------ per-list sigma tables ---
 // weight of position p of N_v from the ACC prefix
 __device__ __forceinline__ uint32_t acc_weight(const uint32_t *acc, uint32_t o, uint32_t d, uint32_t S, uint32_t p) {
@@ -767,6 +779,13 @@ cudaError_t launch_edge_hash(uint64_t nnz, const uint32_t *col, const uint32_t *
                              uint32_t mask, uint32_t shift, cudaStream_t s) {
     if (nnz == 0) return cudaSuccess;
     k_edge_hash<<<flat_blocks(nnz), 256, 0, s>>>(nnz, col, owner, table, mask, shift);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_edge_filter(uint64_t nnz, const uint32_t *col, const uint32_t *owner, uint32_t *filter,
+                               uint32_t shift, cudaStream_t s) {
+    if (nnz == 0) return cudaSuccess;
+    k_edge_filter<<<flat_blocks(nnz), 256, 0, s>>>(nnz, col, owner, filter, shift);
     return cudaGetLastError();
 }
 

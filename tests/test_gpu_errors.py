@@ -71,6 +71,11 @@ def test_state_and_argument_errors():
         with pytest.raises(moss.MossError) as ei:
             moss.moss_set_probe(g.handle, 7)
         assert ei.value.status == moss.MOSS_EINVAL
+    with moss.Graph(rp, col, probe=moss.PROBE_HASH) as g:
+        moss.moss_set_probe(g.handle, moss.PROBE_FILTER)     # filter not built yet
+        with pytest.raises(moss.MossError) as ei:
+            moss.moss_sample_estimate(g.handle, 4, 100, 1)
+        assert ei.value.status == moss.MOSS_ESTATE
     with pytest.raises(moss.MossError) as ei:
         moss.moss_graph_load_csr(rp, col, device=99)
     assert ei.value.status == moss.MOSS_EINVAL

@@ -130,14 +130,14 @@ def test_min_records_bit_exact(name):
     first, count = (12_345, 100_003) if name != "cl_n100k" else (49_990_000, 20_011)
     seed = 0xBEEF
     ocnt, ocls, overts = og.run(oracle.MOSS4MIN, seed, count, first=first, record=True)
-    for probe in (moss.PROBE_SEARCH, moss.PROBE_HASH):
-        moss.moss_set_probe(g.handle, probe)
+    for probe in (moss.PROBE_SEARCH, moss.PROBE_HASH, moss.PROBE_FILTER):
+        g.set_probe(probe)
         cls, verts = gpu_records(g, first, count, seed)
         bad = np.nonzero(ocls != cls)[0]
         assert bad.size == 0, (probe, bad[:5], ocls[bad[:5]], cls[bad[:5]], overts[bad[:3]], verts[bad[:3]])
         assert np.array_equal(verts, overts), probe
         assert np.array_equal(gpu_counts(g, first, count, seed), ocnt), probe
-    moss.moss_set_probe(g.handle, moss.PROBE_HASH)
+    g.set_probe(moss.PROBE_AUTO)
     if name == "diamond":
         hit = [i for i in range(count) if set(overts[i, :4]) == {0, 1, 2, 3}]
         assert hit and all(overts[i, 4] == 3 for i in hit)
@@ -170,8 +170,8 @@ def close(r, o, og):
 def test_estimate_min_matches_oracle(name):
     rp, col, og, g = pair(name)
     K, Km, seed = 200_001, 150_003, 77
-    for probe in (moss.PROBE_SEARCH, moss.PROBE_HASH):
-        moss.moss_set_probe(g.handle, probe)
+    for probe in (moss.PROBE_SEARCH, moss.PROBE_HASH, moss.PROBE_FILTER):
+        g.set_probe(probe)
         r = g.estimate_min(K, Km, seed)
         o = og.estimate_min(K, Km, seed)
         assert tuple(r["K"]) == tuple(o["K"])
@@ -180,7 +180,7 @@ def test_estimate_min_matches_oracle(name):
         assert np.array_equal(r["hits"][0], ref4)
         assert np.array_equal(r["hits"][1], refm)
         close(r, o, og)
-    moss.moss_set_probe(g.handle, moss.PROBE_HASH)
+    g.set_probe(moss.PROBE_AUTO)
 
 
 def test_finalize_min_and_covariance():

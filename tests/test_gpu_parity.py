@@ -106,6 +106,42 @@ def test_tables_bit_exact(name):
     assert st.d_max == int(deg.max())
 
 
+def filter_words(filter_hash, nnz):
+    w = 1
+    while w * 2 <= nnz // 8:
+        w <<= 1
+    return w
+
+
+@pytest.mark.parametrize("name", ["gnp12", "rgg2k", "cl_n2k", "cl_n100k"])
+def test_edge_filter_bits(name):
+    """The filter holds exactly the bits of the edges (no false negatives) and
+    rejects most non-edges."""
+    from oracle.sector_model import filter_hash, filter_mask
+    rp, col, og, g = pair(name)
+    g.set_probe(moss.PROBE_FILTER)
+    nnz = len(col)
+    W = filter_words(filter_hash, nnz)
+    shift = np.uint64(64 - (W.bit_length() - 1))
+    F = moss.moss_table_export(g.handle, moss.TABLE_FILTER, np.zeros(W, dtype=np.uint32))
+    owner = np.repeat(np.arange(len(rp) - 1, dtype=np.uint64), np.diff(rp.astype(np.int64)))
+    c64 = col.astype(np.uint64)
+    keep = owner < c64
+    h = filter_hash((owner[keep] << np.uint64(32)) | c64[keep])
+    ref = np.zeros(W, dtype=np.uint32)
+    np.bitwise_or.at(ref, (h >> shift).astype(np.int64), filter_mask(h))
+    assert np.array_equal(F, ref)
+    rng = np.random.default_rng(1)
+    a = rng.integers(0, len(rp) - 1, 20000).astype(np.uint64)
+    b = rng.integers(0, len(rp) - 1, 20000).astype(np.uint64)
+    hh = filter_hash((np.minimum(a, b) << np.uint64(32)) | np.maximum(a, b))
+    m = filter_mask(hh)
+    passed = (F[(hh >> shift).astype(np.int64)] & m) == m
+    if nnz >= 100_000:
+        assert passed.mean() < 0.15
+    g.set_probe(moss.PROBE_AUTO)
+
+
 @pytest.mark.parametrize("name", ["gnp12", "cl_n200", "rgg2k", "cl_n2k", "cl_n100k"])
 @pytest.mark.parametrize("method", [0, 1, 2])
 def test_records_bit_exact(name, method):
@@ -116,21 +152,22 @@ def test_records_bit_exact(name, method):
     seed = 0xC0FFEE + method
     ocnt, ocls, overts = og.run(method, seed, count, first=first, record=True)
     ncol = 4 if method == 0 else 5
-    for probe in (moss.PROBE_SEARCH, moss.PROBE_HASH):
-        moss.moss_set_probe(g.handle, probe)
+    for probe in (moss.PROBE_SEARCH, moss.PROBE_HASH, moss.PROBE_FILTER):
+        g.set_probe(probe)
         cls, verts = gpu_records(g, method, first, count, seed)
         bad = np.nonzero(ocls != cls)[0]
         assert bad.size == 0, (probe, bad[:5], ocls[bad[:5]], cls[bad[:5]], overts[bad[:3]], verts[bad[:3]])
         assert np.array_equal(verts[:, :ncol], overts[:, :ncol])
-    moss.moss_set_probe(g.handle, moss.PROBE_HASH)
+    g.set_probe(moss.PROBE_AUTO)
 
 
 @pytest.mark.parametrize("name", ["gnp12", "cl_n200", "rgg2k", "cl_n2k"])
 def test_counts_and_estimates(name):
     rp, col, og, g = pair(name)
     budget, seed = 200_001, 99
-    for k, probe in ((4, moss.PROBE_SEARCH), (4, moss.PROBE_HASH), (5, moss.PROBE_SEARCH), (5, moss.PROBE_HASH)):
-        moss.moss_set_probe(g.handle, probe)
+    for k, probe in ((4, moss.PROBE_SEARCH), (4, moss.PROBE_HASH), (4, moss.PROBE_FILTER),
+                     (5, moss.PROBE_SEARCH), (5, moss.PROBE_HASH), (5, moss.PROBE_FILTER)):
+        g.set_probe(probe)
         r = g.estimate(k, budget, seed)
         o = og.estimate(k, budget, seed)
         if k == 4:
@@ -144,7 +181,7 @@ def test_counts_and_estimates(name):
             assert np.array_equal(r["hits"][1], ref2)
         assert tuple(r["K"]) == tuple(o["K"])
         close_estimates(r, o, og, k)
-    moss.moss_set_probe(g.handle, moss.PROBE_HASH)
+    g.set_probe(moss.PROBE_AUTO)
 
 
 def close_estimates(r, o, og, k):
