@@ -4,7 +4,8 @@ For each sampled CIS, the set of distinct 32 B sectors the sampling step must
 read under the device layout the library documents (include/moss.h and its
 kernels): vertex alias records of 32 B (one sector, carrying the alias's
 vertex record, so the drawn vertex's own 16 B record is read only when the
-column keeps the draw), per-slot sigma records of 16 B, vertex records of
+column keeps the draw), per-slot sigma records of 32 B (one sector, with the
+alias position's pick), vertex records of
 16 B, neighbour ids of 4 B, ACC entries of 4 B, Q_v of 8 B; for MOSS-4Min its
 vertex records of 16 B, per-slot records of 32 B (one sector) and
 ordered-list entries of 8 B.  Each
@@ -190,12 +191,10 @@ class Replay:
     def sigma(self, v, xc, xt, touched):
         o, d, S = int(self.rp[v]), int(self.deg[v]), int(self.S[v])
         j = idx(xc, d)
-        touched.add(("slot", (o + j) >> 1))
+        touched.add(("slot", o + j))   # 32 B record: the column's pick and its alias's
         if idx(xt, S) < int(self.thr[o + j]):
             return j
-        a = int(self.alias[o + j])
-        touched.add(("slot", (o + a) >> 1))
-        return a
+        return int(self.alias[o + j])
 
     def sample(self, method, seed, s, verts, cls):
         t = set()
@@ -221,8 +220,8 @@ class Replay:
                     col_list = list(self.col[o:o + d])
                     iu = col_list.index(int(verts[1]))
                     iw = col_list.index(int(verts[2]))
-                    t.add(("slot", (o + iu) >> 1))
-                    t.add(("slot", (o + iw) >> 1))
+                    t.add(("slot", o + iu))
+                    t.add(("slot", o + iw))
             u, w, r, tt = (int(z) for z in verts[1:5])
             t.add(("vert", u >> 1))
             t.add(("vert", w >> 1))
@@ -268,7 +267,8 @@ class Replay:
 def model(workload: str, samples: int = 4000, seed: int = 42) -> dict:
     rp, col = synth.workload(workload)
     out = {"workload": workload, "samples": samples, "seed": seed,
-           "layout": ("32 B vertex alias records with the alias's vertex record, 16 B vertex/slot records, "
+           "layout": ("32 B vertex alias records with the alias's vertex record, 32 B slot records with the "
+                      "alias's pick, 16 B vertex records, "
                       "4 B ids and ACC, 8 B Q, 16 B edge-hash buckets (home bucket counted), 4 B edge-filter words "
                       "(the set's bucket only when the filter passes); MOSS-4Min: 16 B "
                       "vertex, 32 B slot, 8 B list records; 32 B sectors"),

@@ -388,7 +388,7 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
             }
             g->vert = c.take<uint4>(n);
             g->col = c.take<uint32_t>(nnz);
-            g->slot = c.take<uint4>(nnz);
+            g->slot = c.take<uint4>(2 * nnz);
             g->acc = c.take<uint32_t>(nnz);
             g->owner = c.take<uint32_t>(nnz);
             g->sq = c.take<uint64_t>(nnz);
@@ -744,7 +744,7 @@ int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t b
     const void *src = nullptr;
     uint64_t need = 0;
     if (table == MOSS_TABLE_VERT) { src = g->vert; need = (uint64_t)g->n * 16; }
-    else if (table == MOSS_TABLE_SLOT) { src = g->slot; need = g->nnz * 16; }
+    else if (table == MOSS_TABLE_SLOT) { src = g->slot; need = g->nnz * 32; }
     else if (table == MOSS_TABLE_ACC) { src = g->acc; need = g->nnz * 4; }
     else if (table >= MOSS_TABLE_SEED0 && table < MOSS_TABLE_SEED0 + 3) {
         if (!(g->built >> (table - MOSS_TABLE_SEED0) & 1u)) return fail(MOSS_ESTATE, "vertex table not built");

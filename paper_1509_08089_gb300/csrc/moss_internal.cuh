@@ -3,10 +3,12 @@
 // Device layout of a loaded graph (all arrays in HBM, owned by moss_graph):
 //   vert[n]   uint4 {off, deg, S_v, 0}           S_v = sum_{x in N_v} (d_x - 1)
 //   col[nnz]  uint32 sorted neighbour lists N_v   (the CSR, Table 1)
-//   slot[nnz] uint4 {col, thr, alias, twin}       per-list alias table of
-//             sigma^(v) (eq. 1): keep the column when y < thr for y uniform
-//             in [0, S_v), else take position alias; twin = position of v in
-//             N_col (POS of Sec. 4.1.3, used to exclude v from N_col)
+//   slot[2 nnz] two uint4 per position, one 32-byte sector:
+//             {col, thr, alias, twin} -- per-list alias table of sigma^(v)
+//             (eq. 1): keep the column when y < thr for y uniform in
+//             [0, S_v), else take position alias; twin = position of v in
+//             N_col (POS of Sec. 4.1.3, used to exclude v from N_col) --
+//             and {col, twin} of the alias position, {0, 0}
 //   acc[nnz]  uint32 ACC_sigma^(v) exclusive prefix of (d_x - 1) within N_v
 //   sq[nnz]   uint64 exclusive prefix of (d_x - 1)^2 within N_v: with ACC it
 //             gives the prefix of tau^(v) weights (d_x - 1)(S_v - d_x + 1) as

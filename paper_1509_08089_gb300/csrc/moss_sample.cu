@@ -79,15 +79,15 @@ __device__ __forceinline__ VertexPick draw_vertex(const uint4 *seed, const uint4
     return VertexPick{r.lo.z, r.hi};
 }
 
-// WeightRandomVertex(N_v, sigma^(v)) through the list's alias table
+// WeightRandomVertex(N_v, sigma^(v)) through the list's alias table: one
+// 32-byte slot record holds the column's pick and its alias's
 __device__ __forceinline__ Pick draw_sigma(const uint4 *slot, uint32_t ov, uint32_t dv, uint32_t Sv, uint64_t xc,
                                            uint64_t xt) {
     const uint32_t j = (uint32_t)word_index(xc, dv);
-    const uint4 rec = ld4(slot + ov + j);
+    const Sector rec = ld8(slot + 2 * (uint64_t)(ov + j));
     const uint64_t y = word_index(xt, Sv);
-    if (y < rec.y) return Pick{j, rec.x, rec.w};
-    const uint4 al = ld4(slot + ov + rec.z);
-    return Pick{rec.z, al.x, al.w};
+    if (y < rec.lo.y) return Pick{j, rec.lo.x, rec.lo.w};
+    return Pick{rec.lo.z, rec.hi.x, rec.hi.y};
 }
 
 __device__ __forceinline__ uint32_t skip1(uint32_t j, uint32_t e) { return j < e ? j : j + 1; }
@@ -418,7 +418,7 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
             const Words4 d4 = philox4x64(s, 3, 2, 0, seed, 0);
             uint32_t iu, iw;
             path5_fallback(g.acc, g.sq, v, vr, d4.x[0], d4.x[1], iu, iw);
-            const uint4 su = ld4(g.slot + vr.x + iu), sw = ld4(g.slot + vr.x + iw);
+            const uint4 su = ld4(g.slot + 2 * (uint64_t)(vr.x + iu)), sw = ld4(g.slot + 2 * (uint64_t)(vr.x + iw));
             pu = Pick{iu, su.x, su.w};
             pw = Pick{iw, sw.x, sw.w};
         }

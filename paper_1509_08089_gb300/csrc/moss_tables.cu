@@ -82,7 +82,7 @@ __global__ void k_slot_weights(uint32_t n, uint64_t nnz, const uint32_t *__restr
             w = dx ? dx - 1 : 0;
         }
         acc[p] = w;    // turned into the prefix by k_slots
-        slot[p] = make_uint4(x, 0u, 0u, 0u);
+        slot[2 * p] = make_uint4(x, 0u, 0u, 0u);
     }
     if (err) atomicOr(flags, err);
 }
@@ -264,8 +264,8 @@ __global__ void k_twin(uint32_t n, uint64_t nnz, const uint4 *__restrict__ vert,
             continue;
         }
         uint32_t *s32 = reinterpret_cast<uint32_t *>(slot);
-        s32[4 * p + 3] = lo - xr.x;                           // POS of v in N_x
-        s32[4 * (uint64_t)lo + 3] = (uint32_t)(p - vr.x);     // POS of x in N_v
+        s32[8 * p + 3] = lo - xr.x;                           // POS of v in N_x
+        s32[8 * (uint64_t)lo + 3] = (uint32_t)(p - vr.x);     // POS of x in N_v
         matched += 2;
     }
     if (err) atomicOr(flags, err);
@@ -310,6 +310,17 @@ __global__ void k_edge_filter(uint64_t nnz, const uint32_t *__restrict__ col, co
 }
 
 // ------------------------------------------------ per-list sigma tables ---
+// Slot record (32 bytes) of position j of N_v: {col, thr, alias, twin} and
+// {col, twin} of the alias position, so a draw that takes the alias needs no
+// second load.  The twins were set at load.
+__device__ __forceinline__ void set_sigma(uint32_t *slot32, uint32_t o, uint32_t j, uint32_t thr, uint32_t alias) {
+    uint32_t *r = slot32 + 8 * (uint64_t)(o + j);
+    const uint32_t *a = slot32 + 8 * (uint64_t)(o + alias);
+    r[1] = thr;
+    r[2] = alias;
+    r[4] = a[0];
+    r[5] = a[3];
+}
 // weight of position p of N_v from the ACC prefix
 __device__ __forceinline__ uint32_t acc_weight(const uint32_t *acc, uint32_t o, uint32_t d, uint32_t S, uint32_t p) {
     return (p + 1 < d ? acc[o + p + 1] : S) - acc[o + p];
@@ -327,10 +338,7 @@ __global__ void __launch_bounds__(kTableThreads) k_sigma_alias(uint32_t n, const
         if (d == 0 || (d > kLongList && S != 0)) continue;   // long lists: k_sigma_alias_long
         uint32_t *slot32 = reinterpret_cast<uint32_t *>(slot);
         if (S == 0) {  // never drawn (Gamma_v = 0): keep every column
-            for (uint32_t p = lane; p < d; p += kWarp) {
-                slot32[4 * (uint64_t)(o + p) + 1] = 0;
-                slot32[4 * (uint64_t)(o + p) + 2] = p;
-            }
+            for (uint32_t p = lane; p < d; p += kWarp) set_sigma(slot32, o, p, 0, p);
             continue;
         }
         const uint64_t W = S;
@@ -385,8 +393,7 @@ __global__ void __launch_bounds__(kTableThreads) k_sigma_alias(uint32_t n, const
                     const uint64_t A = pre[o + i];
                     while (pre[o + d - 1 - k] < A) ++k;
                     const uint32_t j = idx[o + i];
-                    slot32[4 * (uint64_t)(o + j) + 1] = acc_weight(acc, o, d, S, j) * d;
-                    slot32[4 * (uint64_t)(o + j) + 2] = idx[o + d - 1 - k];
+                    set_sigma(slot32, o, j, acc_weight(acc, o, d, S, j) * d, idx[o + d - 1 - k]);
                 }
             }
         }
@@ -413,8 +420,7 @@ __global__ void __launch_bounds__(kTableThreads) k_sigma_alias(uint32_t n, const
                         thr = (uint32_t)W;
                         alias = j;
                     }
-                    slot32[4 * (uint64_t)(o + j) + 1] = thr;
-                    slot32[4 * (uint64_t)(o + j) + 2] = alias;
+                    set_sigma(slot32, o, j, thr, alias);
                 }
             }
         }
@@ -435,8 +441,7 @@ __global__ void __launch_bounds__(kLongThreads) k_sigma_alias_long(uint32_t n, c
             block_alias<uint64_t, kLongThreads>(
                 d, (uint64_t)S, [&](uint32_t j) { return (uint64_t)acc_weight(acc, o, d, S, j); }, idx + o, pre + o,
                 [&](uint32_t j, uint64_t thr, uint32_t alias) {
-                    slot32[4 * (uint64_t)(o + j) + 1] = (uint32_t)thr;
-                    slot32[4 * (uint64_t)(o + j) + 2] = alias;
+                    set_sigma(slot32, o, j, (uint32_t)thr, alias);
                 });
         });
 }

@@ -34,7 +34,7 @@ def test_large_tables_bit_exact(big):
     assert np.array_equal(vert[:, 1], deg.astype(np.uint32))
     assert np.array_equal(vert[:, 2], S.astype(np.uint32))
     thr, alias, acc = og.sigma_table()
-    slot = moss.moss_table_export(g.handle, moss.TABLE_SLOT, np.zeros((nnz, 4), dtype=np.uint32))
+    slot = moss.moss_table_export(g.handle, moss.TABLE_SLOT, np.zeros((nnz, 8), dtype=np.uint32))
     assert np.array_equal(slot[:, 1], thr.astype(np.uint32))
     assert np.array_equal(slot[:, 2], alias)
     owner = np.repeat(np.arange(n, dtype=np.int64), deg.astype(np.int64))

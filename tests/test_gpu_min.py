@@ -104,7 +104,7 @@ def test_min_tables_bit_exact(name):
     assert np.array_equal(ms[:, 5].astype(np.int64), deg[c64])
     assert np.array_equal(ms[:, 6].astype(np.uint64), rk)
     # d_{u,v}: the rank held by the twin slot (u -> v)
-    slot = moss.moss_table_export(g.handle, moss.TABLE_SLOT, np.zeros((nnz, 4), dtype=np.uint32))
+    slot = moss.moss_table_export(g.handle, moss.TABLE_SLOT, np.zeros((nnz, 8), dtype=np.uint32))
     twin_pos = rp.astype(np.int64)[c64] + slot[:, 3].astype(np.int64)
     assert np.array_equal(ms[:, 7].astype(np.uint64), rk[twin_pos])
     mv = moss.moss_table_export(g.handle, moss.TABLE_MIN_VERT, np.zeros((n, 4), dtype=np.uint32))

@@ -75,7 +75,7 @@ def test_tables_bit_exact(name):
     thr, alias, acc = og.sigma_table()
     acc_g = moss.moss_table_export(g.handle, moss.TABLE_ACC, np.zeros(nnz, dtype=np.uint32))
     assert np.array_equal(acc_g, acc.astype(np.uint32))
-    slot = moss.moss_table_export(g.handle, moss.TABLE_SLOT, np.zeros((nnz, 4), dtype=np.uint32))
+    slot = moss.moss_table_export(g.handle, moss.TABLE_SLOT, np.zeros((nnz, 8), dtype=np.uint32))
     assert np.array_equal(slot[:, 0], col)
     assert np.array_equal(slot[:, 1], thr.astype(np.uint32))
     assert np.array_equal(slot[:, 2], alias)
@@ -88,6 +88,10 @@ def test_tables_bit_exact(name):
         assert np.array_equal(slot[:, 3].astype(np.int64), pos)
     else:  # large graph: check the defining property on all slots
         assert np.array_equal(col[rp.astype(np.int64)[c64] + slot[:, 3].astype(np.int64)].astype(np.int64), owner)
+    # the second half of each record repeats the alias position's column and twin
+    apos = rp.astype(np.int64)[owner] + slot[:, 2].astype(np.int64)
+    assert np.array_equal(slot[:, 4], slot[apos, 0])
+    assert np.array_equal(slot[:, 5], slot[apos, 3])
     for l in range(3):
         sthr, T, salias = og.seed_table(l)
         seed = moss.moss_table_export(g.handle, moss.TABLE_SEED0 + l, np.zeros((n, 8), dtype=np.uint32))
