@@ -189,12 +189,54 @@ class Replay:
                 ln = half
 
     def sigma(self, v, xc, xt, touched):
+        """One sigma draw: the 32 B slot record (the column's pick and its
+        alias's)."""
         o, d, S = int(self.rp[v]), int(self.deg[v]), int(self.S[v])
         j = idx(xc, d)
-        touched.add(("slot", o + j))   # 32 B record: the column's pick and its alias's
+        touched.add(("slot", o + j))
         if idx(xt, S) < int(self.thr[o + j]):
             return j
         return int(self.alias[o + j])
+
+    def fallback(self, v, x12, x13, touched):
+        """The Path-5 fallback as the kernel runs it: tau by binary search
+        over S ACC - sq, mu by binary search over ACC with u's interval removed."""
+        o, d, S = int(self.rp[v]), int(self.deg[v]), int(self.S[v])
+        acc = [int(a) for a in self.acc[o:o + d]]
+        w = [(acc[i + 1] if i + 1 < d else S) - acc[i] for i in range(d)]
+        sq = [0] * d
+        for i in range(1, d):
+            sq[i] = sq[i - 1] + w[i - 1] ** 2
+        touched.add(("acc", (o + d - 1) >> 3))
+        touched.add(("sq", (o + d - 1) >> 2))
+        G = S * S - (sq[d - 1] + w[d - 1] ** 2)
+        y = idx(x12, G)
+        lo, ln = 0, d
+        while ln > 0:
+            half = ln >> 1
+            p = lo + half
+            touched.add(("acc", (o + p) >> 3))
+            touched.add(("sq", (o + p) >> 2))
+            if S * acc[p] - sq[p] <= y:
+                lo, ln = p + 1, ln - half - 1
+            else:
+                ln = half
+        iu = lo - 1
+        touched.add(("acc", (o + iu) >> 3))
+        if iu + 1 < d:
+            touched.add(("acc", (o + iu + 1) >> 3))
+        y2 = idx(x13, S - w[iu])
+        if y2 >= acc[iu]:
+            y2 += w[iu]
+        lo, ln = 0, d
+        while ln > 0:
+            half = ln >> 1
+            touched.add(("acc", (o + lo + half) >> 3))
+            if acc[lo + half] <= y2:
+                lo, ln = lo + half + 1, ln - half - 1
+            else:
+                ln = half
+        return iu, lo - 1
 
     def sample(self, method, seed, s, verts, cls):
         t = set()
@@ -212,14 +254,10 @@ class Replay:
             if iu == iw:
                 iu = self.sigma(v, x[8], x[9], t)
                 iw = self.sigma(v, x[10], x[11], t)
-                if iu == iw:  # fallback: ACC scan and search, Q_v, two slot records
-                    d = int(self.deg[v])
-                    for i in range(d):
-                        t.add(("acc", (o + i) >> 3))
-                    t.add(("q", v >> 2))
-                    col_list = list(self.col[o:o + d])
-                    iu = col_list.index(int(verts[1]))
-                    iw = col_list.index(int(verts[2]))
+                if iu == iw:  # fallback: two binary searches and two slot records
+                    iu, iw = self.fallback(v, x[12], x[13], t)
+                    # the binary searches land where the oracle's scan did
+                    assert int(self.col[o + iu]) == int(verts[1]) and int(self.col[o + iw]) == int(verts[2])
                     t.add(("slot", o + iu))
                     t.add(("slot", o + iw))
             u, w, r, tt = (int(z) for z in verts[1:5])
