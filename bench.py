@@ -238,15 +238,15 @@ def resolved_probe(name: str, row_ptr) -> str:
 
 
 def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False) -> int:
-    """Kernels of one step: load 6 (vertices, owners, slot weights, slot scans,
-    twins, totals); build 7
-    (two sigma alias passes, four vertex-table phases, edge hash); MOSS-4Min
+    """Kernels of one step: load 7 (vertices, owners, slot weights, short and
+    long slot scans, twins, totals); build 8 (two sigma alias passes, the
+    alias-half fill, four vertex-table phases, edge hash); MOSS-4Min
     build 11 (three sort tiers, slot records, two alias passes, total, four
     vertex-table phases); per sub-method a sampler and a reduce, Path-5 per
     chunk of DEFER_CHUNK ids a main launch, a deferred launch and a reduce;
     one finalize."""
     from paper_1509_08089_gb300.dist import sub_budgets
-    n = 6 + 7 + (1 if filtered else 0) + (11 if mix else 0) + 1
+    n = 7 + 8 + (1 if filtered else 0) + (11 if mix else 0) + 1
     for m, K in sub_budgets(k, budget, mix):
         n += 3 * -(-K // DEFER_CHUNK) if m == 2 else 2
     return n

@@ -329,9 +329,13 @@ int moss_graph_stats(const moss_graph *g, moss_stats *out);
 
 /* Copy one internal table to host memory (verification and debugging).
  *   MOSS_TABLE_VERT   n x {uint32 off, deg, S_v, 0}
- *   MOSS_TABLE_SLOT   nnz x {uint32 col, sigma threshold, sigma alias
- *                            (position in N_v), twin (position of v in N_col),
- *                            col and twin of the alias position, 0, 0}
+ *   MOSS_TABLE_SLOT   nnz x {uint32 col, nb, sigma threshold, sigma
+ *                            alias (position in N_v), off, then col, nb and
+ *                            off of the alias position}: for the neighbour
+ *                            x = col with twin = position of v in N_x,
+ *                            nb = twin | d_x << 16 and off = offset of N_x
+ *                            when d_x < 2^16, else nb = 0xFFFFFFFF and
+ *                            off = twin
  *   MOSS_TABLE_ACC    nnz x uint32 ACC_sigma^(v) exclusive prefix (Sec. 4.1.3)
  *   MOSS_TABLE_SEED0+l n x {uint64 threshold T, uint32 alias, uint32 0,
  *                      then the alias's MOSS_TABLE_VERT record} (32 bytes),

@@ -5,8 +5,10 @@ read under the device layout the library documents (include/moss.h and its
 kernels): vertex alias records of 32 B (one sector, carrying the alias's
 vertex record, so the drawn vertex's own 16 B record is read only when the
 column keeps the draw), per-slot sigma records of 32 B (one sector, with the
-alias position's pick), vertex records of
-16 B, neighbour ids of 4 B, ACC entries of 4 B, Q_v of 8 B; for MOSS-4Min its
+alias position's pick, and for both picks the picked neighbour's list and
+twin, so its vertex record is read only for a neighbour of degree 2^16 or
+more), vertex records of 16 B, neighbour ids of 4 B, ACC entries of 4 B and
+prefixes of squares of 8 B (Path-5 fallback); for MOSS-4Min its
 vertex records of 16 B, per-slot records of 32 B (one sector) and
 ordered-list entries of 8 B.  Each
 probe is either a lower-bound search with early exit in the shorter sorted
@@ -188,6 +190,12 @@ class Replay:
             else:
                 ln = half
 
+    def hub(self, x, touched):
+        """The slot record carries a picked neighbour's list and twin; only a
+        neighbour with 2^16 or more neighbours needs its vertex record."""
+        if int(self.deg[x]) >= 1 << 16:
+            touched.add(("vert", x >> 1))
+
     def sigma(self, v, xc, xt, touched):
         """One sigma draw: the 32 B slot record (the column's pick and its
         alias's)."""
@@ -261,8 +269,8 @@ class Replay:
                     t.add(("slot", o + iu))
                     t.add(("slot", o + iw))
             u, w, r, tt = (int(z) for z in verts[1:5])
-            t.add(("vert", u >> 1))
-            t.add(("vert", w >> 1))
+            self.hub(u, t)
+            self.hub(w, t)
             ju = int(np.searchsorted(self.col[self.rp[u]:self.rp[u + 1]], r))
             jt = int(np.searchsorted(self.col[self.rp[w]:self.rp[w + 1]], tt))
             t.add(("col", (int(self.rp[u]) + ju) >> 3))
@@ -278,7 +286,7 @@ class Replay:
         u, w, r = int(verts[1]), int(verts[2]), int(verts[3])
         col_v = self.col[o:o + int(self.deg[v])]
         t.add(("col", (o + int(np.searchsorted(col_v, w))) >> 3))
-        t.add(("vert", u >> 1))
+        self.hub(u, t)
         if method == 0:
             ju = int(np.searchsorted(self.col[self.rp[u]:self.rp[u + 1]], r))
             t.add(("col", (int(self.rp[u]) + ju) >> 3))
@@ -306,7 +314,7 @@ def model(workload: str, samples: int = 4000, seed: int = 42) -> dict:
     rp, col = synth.workload(workload)
     out = {"workload": workload, "samples": samples, "seed": seed,
            "layout": ("32 B vertex alias records with the alias's vertex record, 32 B slot records with the "
-                      "alias's pick, 16 B vertex records, "
+                      "alias's pick and both picks' neighbour list and twin, 16 B vertex records, "
                       "4 B ids and ACC, 8 B Q, 16 B edge-hash buckets (home bucket counted), 4 B edge-filter words "
                       "(the set's bucket only when the filter passes); MOSS-4Min: 16 B "
                       "vertex, 32 B slot, 8 B list records; 32 B sectors"),

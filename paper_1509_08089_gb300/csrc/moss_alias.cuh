@@ -55,14 +55,60 @@ __device__ __forceinline__ T block_incl_scan(T v, T &total, T *smem) {
     return off + v;
 }
 
+// Inclusive scans over the block of three values at once (one pair of
+// barriers): c, D and E become their inclusive prefixes, tc, tD and tE the
+// block sums.  Every thread of the block must call it.
+template <typename T, int NT>
+__device__ __forceinline__ void block_scan3(uint64_t &c, T &D, T &E, uint64_t &tc, T &tD, T &tE) {
+    __shared__ uint64_t s_c[NT / 32];
+    __shared__ T s_D[NT / 32], s_E[NT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 1; k < 32; k <<= 1) {
+        const uint64_t c1 = shfl_up_any<uint64_t>(c, k);
+        const T D1 = shfl_up_any<T>(D, k), E1 = shfl_up_any<T>(E, k);
+        if (lane >= k) {
+            c += c1;
+            D += D1;
+            E += E1;
+        }
+    }
+    if (lane == 31) {
+        s_c[warp] = c;
+        s_D[warp] = D;
+        s_E[warp] = E;
+    }
+    __syncthreads();
+    uint64_t oc = 0, ac = 0;
+    T oD = 0, aD = 0, oE = 0, aE = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) {
+        const uint64_t x = s_c[w];
+        const T y = s_D[w], z = s_E[w];
+        if (w < warp) {
+            oc += x;
+            oD += y;
+            oE += z;
+        }
+        ac += x;
+        aD += y;
+        aE += z;
+    }
+    __syncthreads();
+    c += oc;
+    D += oD;
+    E += oE;
+    tc = ac;
+    tD = aD;
+    tE = aE;
+}
+
 // Alias table of the list of d entries with weights weight(j) (d * w_j and W
 // must fit T) and capacity W > 0; idx (d uint32) and pre (d T) are scratch;
 // store(j, thr, alias) receives each entry's threshold (<= W) and alias
 // position.  Every thread of the block must call it.
 template <typename T, int NT, typename Weight, typename Store>
 __device__ void block_alias(uint32_t d, T W, Weight weight, uint32_t *idx, T *pre, Store store) {
-    __shared__ uint32_t s_cnt[2][NT / 32];
-    __shared__ T s_sum[2][NT / 32];
     const int tid = threadIdx.x;
     uint32_t nl = 0, nh = 0;
     T Arun = 0, Prun = 0;
@@ -72,12 +118,12 @@ __device__ void block_alias(uint32_t d, T W, Weight weight, uint32_t *idx, T *pr
         const T q = valid ? (T)weight(j) * (T)d : (T)0;
         const bool light = valid && q < W, heavy = valid && !light;
         const T D = light ? W - q : (T)0, E = heavy ? q - W : (T)0;
-        uint32_t tl, th;
-        T tD, tE;
-        const uint32_t il = block_incl_scan<uint32_t, NT>(light ? 1u : 0u, tl, s_cnt[0]);
-        const uint32_t ih = block_incl_scan<uint32_t, NT>(heavy ? 1u : 0u, th, s_cnt[1]);
-        const T iD = block_incl_scan<T, NT>(D, tD, s_sum[0]);
-        const T iE = block_incl_scan<T, NT>(E, tE, s_sum[1]);
+        // light and heavy counts packed in one 64-bit lane (low, high word)
+        uint64_t ic = light ? 1ull : (heavy ? 1ull << 32 : 0ull), tc;
+        T iD = D, iE = E, tD, tE;
+        block_scan3<T, NT>(ic, iD, iE, tc, tD, tE);
+        const uint32_t il = (uint32_t)ic, ih = (uint32_t)(ic >> 32);
+        const uint32_t tl = (uint32_t)tc, th = (uint32_t)(tc >> 32);
         if (light) {
             const uint32_t r = nl + il - 1;
             idx[r] = j;

@@ -483,7 +483,7 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
     uint32_t *idx = static_cast<uint32_t *>(scratch);
     uint64_t *pre = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(scratch) + ((g->nnz * 4 + 255) & ~255ULL));
     e = cudaMemsetAsync(g->flags, 0, 2 * sizeof(uint32_t), s);
-    if (e == cudaSuccess) e = launch_sigma_alias(g->n, g->vert, g->acc, g->slot, idx, pre, s);
+    if (e == cudaSuccess) e = launch_sigma_alias(g->n, g->nnz, g->vert, g->acc, g->owner, g->slot, idx, pre, s);
     int which[3], nt = 0;
     u128 *w[3];
     uint4 *seed[3];

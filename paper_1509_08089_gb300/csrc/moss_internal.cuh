@@ -4,11 +4,14 @@
 //   vert[n]   uint4 {off, deg, S_v, 0}           S_v = sum_{x in N_v} (d_x - 1)
 //   col[nnz]  uint32 sorted neighbour lists N_v   (the CSR, Table 1)
 //   slot[2 nnz] two uint4 per position, one 32-byte sector:
-//             {col, thr, alias, twin} -- per-list alias table of sigma^(v)
-//             (eq. 1): keep the column when y < thr for y uniform in
-//             [0, S_v), else take position alias; twin = position of v in
-//             N_col (POS of Sec. 4.1.3, used to exclude v from N_col) --
-//             and {col, twin} of the alias position, {0, 0}
+//             {col, nb, thr, alias} {off, alias col, alias nb, alias off} --
+//             per-list alias table of sigma^(v) (eq. 1): keep the column when
+//             y < thr for y uniform in [0, S_v), else take position alias --
+//             with what a draw needs of the picked neighbour x = col: its
+//             list N_x (off, d_x) and twin = position of v in N_x (POS of
+//             Sec. 4.1.3, used to exclude v from N_x).  nb packs
+//             twin | d_x << 16 when d_x < 2^16; for a larger list nb is
+//             kSlotHub, off holds twin and N_x comes from vert[x].
 //   acc[nnz]  uint32 ACC_sigma^(v) exclusive prefix of (d_x - 1) within N_v
 //   sq[nnz]   uint64 exclusive prefix of (d_x - 1)^2 within N_v: with ACC it
 //             gives the prefix of tau^(v) weights (d_x - 1)(S_v - d_x + 1) as
@@ -45,6 +48,19 @@ namespace moss {
 constexpr int kSlots = 22;            // [0] collisions, [1..21] classes
 
 constexpr int kMethods = 4;          // MOSS-4, T-5, Path-5, MOSS-4Min
+// slot record: nb of a neighbour with 2^16 or more neighbours of its own
+constexpr uint32_t kSlotHub = 0xffffffffu;
+constexpr uint32_t kSlotDegLimit = 1u << 16;
+
+// nb and off words of a slot record for neighbour degree dx and twin tw
+__host__ __device__ __forceinline__ uint32_t slot_nb(uint32_t dx, uint32_t tw) {
+    return dx < kSlotDegLimit ? (tw | dx << 16) : kSlotHub;
+}
+// twin of position p from the 32-bit view of the slot records
+__device__ __forceinline__ uint32_t slot_twin(const uint32_t *s32, uint64_t p) {
+    const uint32_t nb = s32[8 * p + 1];
+    return nb == kSlotHub ? s32[8 * p + 4] : (nb & (kSlotDegLimit - 1));
+}
 // Path-5 samples run in chunks of kDeferChunk ids; a sample whose first pair
 // of sigma draws collides is flagged in a bitmap and redone by a second launch
 constexpr uint64_t kDeferChunk = 1ull << 25;
@@ -219,8 +235,8 @@ cudaError_t launch_edge_hash(uint64_t nnz, const uint32_t *col, const uint32_t *
 // filter of 2^(64 - shift) words, zeroed beforehand
 cudaError_t launch_edge_filter(uint64_t nnz, const uint32_t *col, const uint32_t *owner, uint32_t *filter,
                                uint32_t shift, cudaStream_t s);
-cudaError_t launch_sigma_alias(uint32_t n, const uint4 *vert, const uint32_t *acc, uint4 *slot,
-                               uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s);
+cudaError_t launch_sigma_alias(uint32_t n, uint64_t nnz, const uint4 *vert, const uint32_t *acc, const uint32_t *owner,
+                               uint4 *slot, uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s);
 // vertex alias tables of up to 3 weights in the same launches (seed[t]: 2n
 // uint4, vrec[t]: the n vertex records copied beside each alias); scratch of
 // seed_scratch_bytes(n) bytes

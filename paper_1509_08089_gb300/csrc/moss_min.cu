@@ -210,7 +210,7 @@ __global__ void k_min_slots(uint64_t nnz, const uint4 *__restrict__ vert, const 
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t u = col[p];
         const uint4 ur = vert[u];
-        const uint32_t twin = slot[2 * p].w;
+        const uint32_t twin = slot_twin(reinterpret_cast<const uint32_t *>(slot), p);
         mslot[2 * p] = make_uint4(0u, 0u, 0u, u);
         mslot[2 * p + 1] = make_uint4(ur.x, ur.y, rank[p], rank[(uint64_t)ur.x + twin]);
     }

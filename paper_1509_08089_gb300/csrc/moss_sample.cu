@@ -5,9 +5,10 @@
 // every sample is an independent chain of dependent gathers:
 //   Philox words -> vertex alias record (32 B, with the alias's vertex record;
 //   vert[v] (16 B) only when the column keeps the draw) -> sigma
-//   record(s) of N_v (16 B each) -> uniform list picks (4 B) -> vert[] of the
-//   new vertices -> lock-step binary searches for the unknown pairs ->
-//   edge mask -> class through a shared-memory table.
+//   record(s) of N_v (32 B each, carrying the picked neighbour's list and
+//   twin) -> uniform list picks (4 B) -> the unknown pairs, probed together
+//   (hashed edge set, or lock-step binary searches) -> edge mask -> class
+//   through a shared-memory table.
 // Counts are aggregated per warp with __match_any_sync into shared-memory
 // histograms and leave the block as one row of per-block partials; a second
 // kernel adds the rows in a fixed order.  No global atomics.
@@ -47,6 +48,8 @@ struct Pick {
     uint32_t pos;   // position in N_v
     uint32_t id;    // the vertex
     uint32_t twin;  // position of v in N_id
+    uint32_t off;   // N_id = col[off .. off + deg)
+    uint32_t deg;
 };
 
 // one 32-byte sector in a single 256-bit load (32-byte aligned)
@@ -79,15 +82,30 @@ __device__ __forceinline__ VertexPick draw_vertex(const uint4 *seed, const uint4
     return VertexPick{r.lo.z, r.hi};
 }
 
+// The neighbour half of a slot record (col, nb, off): a neighbour with 2^16
+// or more neighbours keeps its twin in off and its list in vert[].
+__device__ __forceinline__ Pick unpack_pick(const uint4 *vert, uint32_t pos, uint32_t id, uint32_t nb, uint32_t off) {
+    if (nb != kSlotHub) return Pick{pos, id, nb & (kSlotDegLimit - 1), off, nb >> 16};
+    const uint4 r = ld4(vert + id);
+    return Pick{pos, id, off, r.x, r.y};
+}
+
 // WeightRandomVertex(N_v, sigma^(v)) through the list's alias table: one
-// 32-byte slot record holds the column's pick and its alias's
-__device__ __forceinline__ Pick draw_sigma(const uint4 *slot, uint32_t ov, uint32_t dv, uint32_t Sv, uint64_t xc,
-                                           uint64_t xt) {
+// 32-byte slot record holds the column's pick and its alias's, each with the
+// picked neighbour's list and twin
+__device__ __forceinline__ Pick draw_sigma(const uint4 *slot, const uint4 *vert, uint32_t ov, uint32_t dv, uint32_t Sv,
+                                           uint64_t xc, uint64_t xt) {
     const uint32_t j = (uint32_t)word_index(xc, dv);
-    const Sector rec = ld8(slot + 2 * (uint64_t)(ov + j));
-    const uint64_t y = word_index(xt, Sv);
-    if (y < rec.lo.y) return Pick{j, rec.lo.x, rec.lo.w};
-    return Pick{rec.lo.z, rec.hi.x, rec.hi.y};
+    const Sector rec = ld8(slot + 2 * (uint64_t)(ov + j));   // {col, nb, thr, alias} {off, alias col, nb, off}
+    const bool keep = word_index(xt, Sv) < rec.lo.z;
+    return unpack_pick(vert, keep ? j : rec.lo.w, keep ? rec.lo.x : rec.hi.y, keep ? rec.lo.y : rec.hi.z,
+                       keep ? rec.hi.x : rec.hi.w);
+}
+
+// the pick of position p of N_v from its own half of the slot record
+__device__ __forceinline__ Pick slot_pick(const uint4 *slot, const uint4 *vert, uint32_t ov, uint32_t p) {
+    const Sector rec = ld8(slot + 2 * (uint64_t)(ov + p));
+    return unpack_pick(vert, p, rec.lo.x, rec.lo.y, rec.hi.x);
 }
 
 __device__ __forceinline__ uint32_t skip1(uint32_t j, uint32_t e) { return j < e ? j : j + 1; }
@@ -192,12 +210,11 @@ __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t 
     const VertexPick pv = draw_vertex(g.seed[0], g.vert, g.n, a.x[0], a.x[1]);
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
-    const Pick pu = draw_sigma(g.slot, vr.x, vr.y, vr.z, a.x[2], a.x[3]);
+    const Pick pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, a.x[2], a.x[3]);
     const uint32_t jw = skip1((uint32_t)word_index(b.x[0], vr.y - 1), pu.pos);
     const uint32_t w = ld1(g.col + vr.x + jw);
-    const uint4 ur = ld4(g.vert + pu.id);
-    const uint32_t jr = skip1((uint32_t)word_index(b.x[1], ur.y - 1), pu.twin);
-    const uint32_t r = ld1(g.col + ur.x + jr);
+    const uint32_t jr = skip1((uint32_t)word_index(b.x[1], pu.deg - 1), pu.twin);
+    const uint32_t r = ld1(g.col + pu.off + jr);
     out.v[0] = v; out.v[1] = pu.id; out.v[2] = w; out.v[3] = r; out.v[4] = 0;
     if (r == pu.id || r == w) {
         out.cls = 0;
@@ -209,7 +226,7 @@ __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t 
     if (HASH) {
         f = probe_hash<3>(g, A, B);
     } else {
-        const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r);
+        const uint4 ur = make_uint4(pu.off, pu.deg, 0u, 0u), wr = ld4(g.vert + w), rr = ld4(g.vert + r);
         const uint4 ra[3] = {vr, ur, wr}, rb[3] = {rr, wr, rr};
         f = probe_pairs<3>(g.col, ra, rb, A, B);
     }
@@ -227,14 +244,13 @@ __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lu
     const VertexPick pv = draw_vertex(g.seed[1], g.vert, g.n, a.x[0], a.x[1]);
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
-    const Pick pu = draw_sigma(g.slot, vr.x, vr.y, vr.z, a.x[2], a.x[3]);
+    const Pick pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, a.x[2], a.x[3]);
     const uint32_t jw = skip1((uint32_t)word_index(b.x[0], vr.y - 1), pu.pos);
     const uint32_t jr = skip2((uint32_t)word_index(b.x[1], vr.y - 2), pu.pos, jw);
     const uint32_t w = ld1(g.col + vr.x + jw);
     const uint32_t r = ld1(g.col + vr.x + jr);
-    const uint4 ur = ld4(g.vert + pu.id);
-    const uint32_t jt = skip1((uint32_t)word_index(b.x[2], ur.y - 1), pu.twin);
-    const uint32_t t = ld1(g.col + ur.x + jt);
+    const uint32_t jt = skip1((uint32_t)word_index(b.x[2], pu.deg - 1), pu.twin);
+    const uint32_t t = ld1(g.col + pu.off + jt);
     out.v[0] = v; out.v[1] = pu.id; out.v[2] = w; out.v[3] = r; out.v[4] = t;
     if (t == w || t == r) {
         out.cls = 0;
@@ -246,6 +262,7 @@ __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lu
     if (HASH) {
         f = probe_hash<6>(g, A, B);
     } else {
+        const uint4 ur = make_uint4(pu.off, pu.deg, 0u, 0u);
         const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r), tr = ld4(g.vert + t);
         const uint4 ra[6] = {ur, ur, wr, vr, wr, rr}, rb[6] = {wr, rr, rr, tr, tr, tr};
         f = probe_pairs<6>(g.col, ra, rb, A, B);
@@ -311,16 +328,14 @@ __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *l
     const uint32_t v = pv.v;
     const uint4 mv = pv.rec;                           // {off, d_v, Gamma-check_v}
     const uint64_t Gv = ((uint64_t)mv.w << 32) | mv.z;
-    // WeightRandomVertex(N_v, sigma-check^(v)): 32-byte slot records
-    uint32_t j = (uint32_t)word_index(a.x[2], mv.y);
-    uint4 sa = ld4(g.mslot + 2 * (uint64_t)(mv.x + j));
+    // WeightRandomVertex(N_v, sigma-check^(v)): 32-byte slot records, each
+    // read whole in one load
+    const uint32_t j = (uint32_t)word_index(a.x[2], mv.y);
+    Sector ms = ld8(g.mslot + 2 * (uint64_t)(mv.x + j));
     const uint64_t y = word_index(a.x[3], Gv);
-    if (!(y < (((uint64_t)sa.y << 32) | sa.x))) {
-        j = sa.z;
-        sa = ld4(g.mslot + 2 * (uint64_t)(mv.x + j));
-    }
-    const uint4 sb = ld4(g.mslot + 2 * (uint64_t)(mv.x + j) + 1);   // {off_u, d_u, d_{v,u}, d_{u,v}}
-    const uint32_t u = sa.w;
+    if (!(y < (((uint64_t)ms.lo.y << 32) | ms.lo.x))) ms = ld8(g.mslot + 2 * (uint64_t)(mv.x + ms.lo.z));
+    const uint4 sb = ms.hi;   // {off_u, d_u, d_{v,u}, d_{u,v}}
+    const uint32_t u = ms.lo.w;
     const uint2 we = ld2(g.rlist + mv.x + (uint32_t)word_index(b.x[0], sb.z));   // w in N_{v,u}
     const uint2 re = ld2(g.rlist + sb.x + (uint32_t)word_index(b.x[1], sb.w));   // r in N_{u,v}
     const uint32_t w = we.x, r = re.x;
@@ -404,29 +419,27 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
     const Words4 b = philox4x64(s, 1, 2, 0, seed, 0);
-    Pick pu = draw_sigma(g.slot, vr.x, vr.y, vr.z, b.x[0], b.x[1]);
-    Pick pw = draw_sigma(g.slot, vr.x, vr.y, vr.z, b.x[2], b.x[3]);
+    Pick pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, b.x[0], b.x[1]);
+    Pick pw = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, b.x[2], b.x[3]);
     if (pu.pos == pw.pos) {
         if (DEFER) {
             out.cls = kDeferred;
             return out;
         }
         const Words4 c = philox4x64(s, 2, 2, 0, seed, 0);
-        pu = draw_sigma(g.slot, vr.x, vr.y, vr.z, c.x[0], c.x[1]);
-        pw = draw_sigma(g.slot, vr.x, vr.y, vr.z, c.x[2], c.x[3]);
+        pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, c.x[0], c.x[1]);
+        pw = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, c.x[2], c.x[3]);
         if (pu.pos == pw.pos) {
             const Words4 d4 = philox4x64(s, 3, 2, 0, seed, 0);
             uint32_t iu, iw;
             path5_fallback(g.acc, g.sq, v, vr, d4.x[0], d4.x[1], iu, iw);
-            const uint4 su = ld4(g.slot + 2 * (uint64_t)(vr.x + iu)), sw = ld4(g.slot + 2 * (uint64_t)(vr.x + iw));
-            pu = Pick{iu, su.x, su.w};
-            pw = Pick{iw, sw.x, sw.w};
+            pu = slot_pick(g.slot, g.vert, vr.x, iu);
+            pw = slot_pick(g.slot, g.vert, vr.x, iw);
         }
     }
     const uint32_t u = pu.id, w = pw.id;
-    const uint4 ur = ld4(g.vert + u), wr = ld4(g.vert + w);
-    const uint32_t r = ld1(g.col + ur.x + skip1((uint32_t)word_index(a.x[2], ur.y - 1), pu.twin));
-    const uint32_t t = ld1(g.col + wr.x + skip1((uint32_t)word_index(a.x[3], wr.y - 1), pw.twin));
+    const uint32_t r = ld1(g.col + pu.off + skip1((uint32_t)word_index(a.x[2], pu.deg - 1), pu.twin));
+    const uint32_t t = ld1(g.col + pw.off + skip1((uint32_t)word_index(a.x[3], pw.deg - 1), pw.twin));
     out.v[0] = v; out.v[1] = u; out.v[2] = w; out.v[3] = r; out.v[4] = t;
     if (t == u || r == w || t == r) {
         out.cls = 0;
@@ -438,6 +451,7 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
     if (HASH) {
         f = probe_hash<6>(g, A, B);
     } else {
+        const uint4 ur = make_uint4(pu.off, pu.deg, 0u, 0u), wr = make_uint4(pw.off, pw.deg, 0u, 0u);
         const uint4 rr = ld4(g.vert + r), tr = ld4(g.vert + t);
         const uint4 ra[6] = {vr, vr, ur, ur, wr, rr}, rb[6] = {rr, tr, wr, tr, rr, tr};
         f = probe_pairs<6>(g.col, ra, rb, A, B);

@@ -72,17 +72,19 @@ __global__ void k_slot_weights(uint32_t n, uint64_t nnz, const uint32_t *__restr
     uint32_t err = 0;
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t v = owner[p], x = col[p];
-        uint32_t w = 0;
+        uint32_t w = 0, ox = 0;
         if (x >= n) {
             err |= kErrRange;
         } else {
             if (x == v) err |= kErrSelf;
             if (p > 0 && owner[p - 1] == v && col[p - 1] >= x) err |= kErrOrder;
-            const uint32_t dx = vert[x].y;
-            w = dx ? dx - 1 : 0;
+            const uint4 xr = vert[x];
+            w = xr.y ? xr.y - 1 : 0;
+            ox = xr.x;
         }
         acc[p] = w;    // turned into the prefix by k_slots
         slot[2 * p] = make_uint4(x, 0u, 0u, 0u);
+        slot[2 * p + 1] = make_uint4(ox, 0u, 0u, 0u);   // nb and, for a hub, off: k_twin
     }
     if (err) atomicOr(flags, err);
 }
@@ -264,8 +266,12 @@ __global__ void k_twin(uint32_t n, uint64_t nnz, const uint4 *__restrict__ vert,
             continue;
         }
         uint32_t *s32 = reinterpret_cast<uint32_t *>(slot);
-        s32[8 * p + 3] = lo - xr.x;                           // POS of v in N_x
-        s32[8 * (uint64_t)lo + 3] = (uint32_t)(p - vr.x);     // POS of x in N_v
+        const uint32_t tp = lo - xr.x;                 // POS of v in N_x
+        const uint32_t tl = (uint32_t)(p - vr.x);      // POS of x in N_v
+        s32[8 * p + 1] = slot_nb(xr.y, tp);
+        if (xr.y >= kSlotDegLimit) s32[8 * p + 4] = tp;
+        s32[8 * (uint64_t)lo + 1] = slot_nb(vr.y, tl);
+        if (vr.y >= kSlotDegLimit) s32[8 * (uint64_t)lo + 4] = tl;
         matched += 2;
     }
     if (err) atomicOr(flags, err);
@@ -310,27 +316,32 @@ __global__ void k_edge_filter(uint64_t nnz, const uint32_t *__restrict__ col, co
 }
 
 // ------------------------------------------------ per-list sigma tables ---
-// Slot record (32 bytes) of position j of N_v: {col, thr, alias, twin} and
-// {col, twin} of the alias position, so a draw that takes the alias needs no
-// second load.  The twins were set at load.
+// Slot record (32 bytes) of position j of N_v: {col, nb, thr, alias} {off,
+// alias col, alias nb, alias off}, so a draw that takes the alias needs no
+// second load.  col, nb and off were set at load; the alias passes write thr
+// and alias (one 8-byte store), and k_slot_alias_fill then copies col, nb
+// and off of the alias position into words 5..7.
 __device__ __forceinline__ void set_sigma(uint32_t *slot32, uint32_t o, uint32_t j, uint32_t thr, uint32_t alias) {
-    uint32_t *r = slot32 + 8 * (uint64_t)(o + j);
-    const uint32_t *a = slot32 + 8 * (uint64_t)(o + alias);
-    r[1] = thr;
-    r[2] = alias;
-    r[4] = a[0];
-    r[5] = a[3];
+    *reinterpret_cast<uint2 *>(slot32 + 8 * (uint64_t)(o + j) + 2) = make_uint2(thr, alias);
 }
 // weight of position p of N_v from the ACC prefix
+// (read-only loads: acc is not written while the alias tables are built, so
+// they need not wait for the passes' stores to the slot records)
 __device__ __forceinline__ uint32_t acc_weight(const uint32_t *acc, uint32_t o, uint32_t d, uint32_t S, uint32_t p) {
-    return (p + 1 < d ? acc[o + p + 1] : S) - acc[o + p];
+    return (p + 1 < d ? __ldg(acc + o + p + 1) : S) - __ldg(acc + o + p);
 }
 
+// A warp per list of at most kLongList entries; the split (idx, pre) of the
+// list being built lives in the warp's share of shared memory, so the
+// searches and merges of pass 2 wait on shared rather than global loads.
 __global__ void __launch_bounds__(kTableThreads) k_sigma_alias(uint32_t n, const uint4 *__restrict__ vert,
-                                                              const uint32_t *__restrict__ acc, uint4 *slot,
-                                                              uint32_t *idx, uint64_t *pre) {
+                                                              const uint32_t *__restrict__ acc, uint4 *slot) {
+    __shared__ uint64_t s_pre[kTableThreads / kWarp][kLongList];
+    __shared__ uint32_t s_idx[kTableThreads / kWarp][kLongList];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
+    uint64_t *pre = s_pre[warp];
+    uint32_t *idx = s_idx[warp];
     const uint32_t below = (1u << lane) - 1u;
     for (uint64_t v = (uint64_t)blockIdx.x * wpb + warp; v < n; v += (uint64_t)gridDim.x * wpb) {
         const uint4 vr = vert[v];
@@ -361,12 +372,12 @@ __global__ void __launch_bounds__(kTableThreads) k_sigma_alias(uint32_t n, const
             const uint64_t Eincl = warp_incl_scan64(E, lane);
             if (valid && light) {
                 const uint32_t r = nl + __popc(lmask & below);
-                idx[o + r] = j;
-                pre[o + r] = Arun + Dincl - D;            // exclusive A_i
+                idx[r] = j;
+                pre[r] = Arun + Dincl - D;            // exclusive A_i
             } else if (valid) {
                 const uint32_t r = nh + __popc(hmask & below);
-                idx[o + d - 1 - r] = j;
-                pre[o + d - 1 - r] = Prun + Eincl;        // inclusive P_k
+                idx[d - 1 - r] = j;
+                pre[d - 1 - r] = Prun + Eincl;        // inclusive P_k
             }
             nl += __popc(lmask);
             nh += __popc(hmask);
@@ -383,17 +394,17 @@ __global__ void __launch_bounds__(kTableThreads) k_sigma_alias(uint32_t n, const
             const uint32_t cl = (nl + kWarp - 1) / kWarp;
             const uint32_t i0 = lane * cl, i1 = min(nl, i0 + cl);
             if (i0 < i1) {
-                const uint64_t A0 = pre[o + i0];
+                const uint64_t A0 = pre[i0];
                 uint32_t k = 0, len = nh;           // first heavy k with P_k >= A
                 while (len > 0) {
                     const uint32_t half = len >> 1;
-                    if (pre[o + d - 1 - (k + half)] < A0) { k += half + 1; len -= half + 1; } else { len = half; }
+                    if (pre[d - 1 - (k + half)] < A0) { k += half + 1; len -= half + 1; } else { len = half; }
                 }
                 for (uint32_t i = i0; i < i1; ++i) {
-                    const uint64_t A = pre[o + i];
-                    while (pre[o + d - 1 - k] < A) ++k;
-                    const uint32_t j = idx[o + i];
-                    set_sigma(slot32, o, j, acc_weight(acc, o, d, S, j) * d, idx[o + d - 1 - k]);
+                    const uint64_t A = pre[i];
+                    while (pre[d - 1 - k] < A) ++k;
+                    const uint32_t j = idx[i];
+                    set_sigma(slot32, o, j, acc_weight(acc, o, d, S, j) * d, idx[d - 1 - k]);
                 }
             }
         }
@@ -401,21 +412,21 @@ __global__ void __launch_bounds__(kTableThreads) k_sigma_alias(uint32_t n, const
             const uint32_t ch = (nh + kWarp - 1) / kWarp;
             const uint32_t k0 = lane * ch, k1 = min(nh, k0 + ch);
             if (k0 < k1) {
-                const uint64_t P0 = pre[o + d - 1 - k0];
+                const uint64_t P0 = pre[d - 1 - k0];
                 uint32_t i = 0, len = nl;           // first light i with A_i > P_k
                 while (len > 0) {
                     const uint32_t half = len >> 1;
-                    if (pre[o + i + half] <= P0) { i += half + 1; len -= half + 1; } else { len = half; }
+                    if (pre[i + half] <= P0) { i += half + 1; len -= half + 1; } else { len = half; }
                 }
                 for (uint32_t k = k0; k < k1; ++k) {
-                    const uint64_t Pk = pre[o + d - 1 - k];
-                    while (i < nl && pre[o + i] <= Pk) ++i;
-                    const uint32_t j = idx[o + d - 1 - k];
+                    const uint64_t Pk = pre[d - 1 - k];
+                    while (i < nl && pre[i] <= Pk) ++i;
+                    const uint32_t j = idx[d - 1 - k];
                     uint32_t thr, alias;
                     if (Pk < Ptot) {
-                        const uint64_t Ai = i < nl ? pre[o + i] : Ptot;
+                        const uint64_t Ai = i < nl ? pre[i] : Ptot;
                         thr = (uint32_t)(W + Pk - Ai);
-                        alias = idx[o + d - 1 - (k + 1)];
+                        alias = idx[d - 1 - (k + 1)];
                     } else {
                         thr = (uint32_t)W;
                         alias = j;
@@ -428,22 +439,46 @@ __global__ void __launch_bounds__(kTableThreads) k_sigma_alias(uint32_t n, const
     }
 }
 
-// lists longer than kLongList: a block per list (moss_alias.cuh)
+// lists longer than kLongList: a block per list (moss_alias.cuh); a list of
+// at most kLongSmemList entries keeps its split in dynamic shared memory, a
+// longer one in its range of the global scratch (idx, pre).  The grid has a
+// block per kSigmaChunk vertices, so the hardware scheduler spreads the long
+// lists over the SMs as blocks finish instead of a fixed share per block.
+constexpr uint32_t kLongSmemList = 4096;
+constexpr size_t kLongSmemBytes = (size_t)kLongSmemList * (sizeof(uint64_t) + sizeof(uint32_t));
+constexpr int kSigmaChunk = 32;
+
 __global__ void __launch_bounds__(kLongThreads) k_sigma_alias_long(uint32_t n, const uint4 *__restrict__ vert,
                                                                   const uint32_t *__restrict__ acc, uint4 *slot,
                                                                   uint32_t *idx, uint64_t *pre) {
+    extern __shared__ uint64_t s_split[];   // kLongSmemList pre, then kLongSmemList idx
     uint32_t *slot32 = reinterpret_cast<uint32_t *>(slot);
-    for_each_vertex<kLongThreads>(
+    for_each_vertex<kLongThreads, kSigmaChunk>(
         n, vert, [](uint4 vr) { return vr.y > kLongList && vr.z != 0; },
         [&](uint32_t v) {
             const uint4 vr = vert[v];
             const uint32_t o = vr.x, d = vr.y, S = vr.z;
+            const bool fits = d <= kLongSmemList;
             block_alias<uint64_t, kLongThreads>(
-                d, (uint64_t)S, [&](uint32_t j) { return (uint64_t)acc_weight(acc, o, d, S, j); }, idx + o, pre + o,
+                d, (uint64_t)S, [&](uint32_t j) { return (uint64_t)acc_weight(acc, o, d, S, j); },
+                fits ? reinterpret_cast<uint32_t *>(s_split + kLongSmemList) : idx + o, fits ? s_split : pre + o,
                 [&](uint32_t j, uint64_t thr, uint32_t alias) {
                     set_sigma(slot32, o, j, (uint32_t)thr, alias);
                 });
         });
+}
+
+// One thread per slot: words 5..7 of each record from words 0, 1 and 4 of
+// its alias position's record (written before this launch, read only here).
+__global__ void k_slot_alias_fill(uint64_t nnz, const uint4 *__restrict__ vert, const uint32_t *__restrict__ owner,
+                                  uint4 *slot) {
+    uint32_t *s32 = reinterpret_cast<uint32_t *>(slot);
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t a = (uint64_t)vert[owner[p]].x + s32[8 * p + 3];
+        const uint32_t col = s32[8 * a], nb = s32[8 * a + 1], off = s32[8 * a + 4];
+        s32[8 * p + 5] = col;
+        *reinterpret_cast<uint2 *>(s32 + 8 * p + 6) = make_uint2(nb, off);
+    }
 }
 
 // ---------------------------------------------------- vertex (seed) tables ---
@@ -794,12 +829,18 @@ cudaError_t launch_edge_filter(uint64_t nnz, const uint32_t *col, const uint32_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_sigma_alias(uint32_t n, const uint4 *vert, const uint32_t *acc, uint4 *slot,
-                               uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s) {
-    k_sigma_alias<<<table_blocks(n), kTableThreads, 0, s>>>(n, vert, acc, slot, scratch_idx, scratch_pre);
+cudaError_t launch_sigma_alias(uint32_t n, uint64_t nnz, const uint4 *vert, const uint32_t *acc, const uint32_t *owner,
+                               uint4 *slot, uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s) {
+    k_sigma_alias<<<table_blocks(n), kTableThreads, 0, s>>>(n, vert, acc, slot);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_sigma_alias_long<<<long_blocks(n), kLongThreads, 0, s>>>(n, vert, acc, slot, scratch_idx, scratch_pre);
+    e = cudaFuncSetAttribute(k_sigma_alias_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSmemBytes);
+    if (e != cudaSuccess) return e;
+    const unsigned chunks = (unsigned)(((uint64_t)n + kSigmaChunk - 1) / kSigmaChunk);
+    k_sigma_alias_long<<<chunks ? chunks : 1, kLongThreads, kLongSmemBytes, s>>>(n, vert, acc, slot, scratch_idx,
+                                                                                  scratch_pre);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_slot_alias_fill<<<flat_blocks(nnz), 256, 0, s>>>(nnz, vert, owner, slot);
     return cudaGetLastError();
 }
 

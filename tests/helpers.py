@@ -123,3 +123,26 @@ def class_counts(cis: dict, nclass: int) -> np.ndarray:
     for cls in cis.values():
         c[cls] += 1
     return c
+
+
+SLOT_HUB = 0xFFFFFFFF
+
+
+def slot_twin(slot: np.ndarray) -> np.ndarray:
+    """Twin (position of v in N_col) of exported 32-byte slot records: the low
+    16 bits of word 1, or word 4 for a neighbour of degree 2^16 or more."""
+    nb = slot[:, 1].astype(np.int64)
+    return np.where(nb == SLOT_HUB, slot[:, 4].astype(np.int64), nb & 0xFFFF)
+
+
+def expected_slot_neighbour(rp: np.ndarray, col: np.ndarray, twin: np.ndarray):
+    """Words 1 and 4 of the slot records that the library's layout defines
+    for neighbour lists (rp, col) and twins: (twin | d_x << 16, off_x), or
+    (SLOT_HUB, twin) when d_x >= 2^16."""
+    c64 = col.astype(np.int64)
+    rp64 = rp.astype(np.int64)
+    dx = rp64[c64 + 1] - rp64[c64]
+    hub = dx >= 1 << 16
+    nb = np.where(hub, SLOT_HUB, twin | (dx << 16))
+    off = np.where(hub, twin, rp64[c64])
+    return nb.astype(np.uint32), off.astype(np.uint32)

@@ -11,6 +11,7 @@ import pytest
 import oracle
 import synth
 import paper_1509_08089_gb300 as moss
+from helpers import expected_slot_neighbour, slot_twin
 from oracle.finalize import PHI5
 
 torch = pytest.importorskip("torch")
@@ -35,10 +36,16 @@ def test_large_tables_bit_exact(big):
     assert np.array_equal(vert[:, 2], S.astype(np.uint32))
     thr, alias, acc = og.sigma_table()
     slot = moss.moss_table_export(g.handle, moss.TABLE_SLOT, np.zeros((nnz, 8), dtype=np.uint32))
-    assert np.array_equal(slot[:, 1], thr.astype(np.uint32))
-    assert np.array_equal(slot[:, 2], alias)
+    assert np.array_equal(slot[:, 2], thr.astype(np.uint32))
+    assert np.array_equal(slot[:, 3], alias)
     owner = np.repeat(np.arange(n, dtype=np.int64), deg.astype(np.int64))
-    assert np.array_equal(col[rp.astype(np.int64)[col.astype(np.int64)] + slot[:, 3].astype(np.int64)], owner)
+    twin = slot_twin(slot)
+    assert np.array_equal(col[rp.astype(np.int64)[col.astype(np.int64)] + twin], owner)
+    nb, off = expected_slot_neighbour(rp, col, twin)
+    assert np.array_equal(slot[:, 1], nb)
+    assert np.array_equal(slot[:, 4], off)
+    apos = rp.astype(np.int64)[owner] + slot[:, 3].astype(np.int64)
+    assert np.array_equal(slot[:, 5:8], slot[apos][:, [0, 1, 4]])
     for l in range(3):
         _, T, salias = og.seed_table(l)
         seed = moss.moss_table_export(g.handle, moss.TABLE_SEED0 + l, np.zeros((n, 8), dtype=np.uint32))

@@ -16,6 +16,7 @@ import pytest
 import oracle
 import synth
 import paper_1509_08089_gb300 as moss
+from helpers import slot_twin
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -105,7 +106,7 @@ def test_min_tables_bit_exact(name):
     assert np.array_equal(ms[:, 6].astype(np.uint64), rk)
     # d_{u,v}: the rank held by the twin slot (u -> v)
     slot = moss.moss_table_export(g.handle, moss.TABLE_SLOT, np.zeros((nnz, 8), dtype=np.uint32))
-    twin_pos = rp.astype(np.int64)[c64] + slot[:, 3].astype(np.int64)
+    twin_pos = rp.astype(np.int64)[c64] + slot_twin(slot)
     assert np.array_equal(ms[:, 7].astype(np.uint64), rk[twin_pos])
     mv = moss.moss_table_export(g.handle, moss.TABLE_MIN_VERT, np.zeros((n, 4), dtype=np.uint32))
     assert np.array_equal(mv[:, 0], rp[:-1].astype(np.uint32))

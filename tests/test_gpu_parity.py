@@ -14,9 +14,22 @@ import pytest
 import oracle
 import synth
 import paper_1509_08089_gb300 as moss
+from helpers import expected_slot_neighbour, slot_twin
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+def hub_graph():
+    """A star of 70,000 leaves, so one neighbour list holds 2^16 entries or
+    more (slot records of that neighbour keep their twin in place of the list
+    offset), with 60,000 random leaf-leaf edges and a second hub of 300."""
+    rng = np.random.default_rng(11)
+    leaves = 70_000
+    edges = [(0, i) for i in range(1, leaves + 1)]
+    edges += zip(rng.integers(1, leaves + 1, 60_000), rng.integers(1, leaves + 1, 60_000))
+    edges += [(leaves + 1, int(x)) for x in rng.integers(1, leaves + 1, 300)]
+    return synth.from_edges(leaves + 2, edges)
+
 
 GRAPHS = {
     "gnp12": lambda: synth.gnp(12, 0.45, 5),
@@ -24,6 +37,7 @@ GRAPHS = {
     "rgg2k": lambda: synth.rgg(2000, 12.0, seed=3),
     "cl_n2k": lambda: synth.workload("cl_n2k"),
     "cl_n100k": lambda: synth.workload("cl_n100k"),
+    "hub70k": hub_graph,
 }
 
 _cache = {}
@@ -77,21 +91,27 @@ def test_tables_bit_exact(name):
     assert np.array_equal(acc_g, acc.astype(np.uint32))
     slot = moss.moss_table_export(g.handle, moss.TABLE_SLOT, np.zeros((nnz, 8), dtype=np.uint32))
     assert np.array_equal(slot[:, 0], col)
-    assert np.array_equal(slot[:, 1], thr.astype(np.uint32))
-    assert np.array_equal(slot[:, 2], alias)
+    assert np.array_equal(slot[:, 2], thr.astype(np.uint32))
+    assert np.array_equal(slot[:, 3], alias)
     # twin: position of v in N_col
     owner = np.repeat(np.arange(n, dtype=np.int64), deg.astype(np.int64))
     c64 = col.astype(np.int64)
     pos = np.array([np.searchsorted(col[rp[x]:rp[x + 1]], v) for v, x in zip(owner, c64)], dtype=np.int64) \
         if nnz <= 200_000 else None
+    twin = slot_twin(slot)
     if pos is not None:
-        assert np.array_equal(slot[:, 3].astype(np.int64), pos)
+        assert np.array_equal(twin, pos)
     else:  # large graph: check the defining property on all slots
-        assert np.array_equal(col[rp.astype(np.int64)[c64] + slot[:, 3].astype(np.int64)].astype(np.int64), owner)
-    # the second half of each record repeats the alias position's column and twin
-    apos = rp.astype(np.int64)[owner] + slot[:, 2].astype(np.int64)
-    assert np.array_equal(slot[:, 4], slot[apos, 0])
-    assert np.array_equal(slot[:, 5], slot[apos, 3])
+        assert np.array_equal(col[rp.astype(np.int64)[c64] + twin].astype(np.int64), owner)
+    # words 1 and 4: the neighbour's degree and list offset with the twin
+    nb, off = expected_slot_neighbour(rp, col, twin)
+    assert np.array_equal(slot[:, 1], nb)
+    assert np.array_equal(slot[:, 4], off)
+    # words 5..7 repeat the alias position's words 0, 1 and 4
+    apos = rp.astype(np.int64)[owner] + slot[:, 3].astype(np.int64)
+    assert np.array_equal(slot[:, 5], slot[apos, 0])
+    assert np.array_equal(slot[:, 6], slot[apos, 1])
+    assert np.array_equal(slot[:, 7], slot[apos, 4])
     for l in range(3):
         sthr, T, salias = og.seed_table(l)
         seed = moss.moss_table_export(g.handle, moss.TABLE_SEED0 + l, np.zeros((n, 8), dtype=np.uint32))
@@ -146,7 +166,7 @@ def test_edge_filter_bits(name):
     g.set_probe(moss.PROBE_AUTO)
 
 
-@pytest.mark.parametrize("name", ["gnp12", "cl_n200", "rgg2k", "cl_n2k", "cl_n100k"])
+@pytest.mark.parametrize("name", ["gnp12", "cl_n200", "rgg2k", "cl_n2k", "cl_n100k", "hub70k"])
 @pytest.mark.parametrize("method", [0, 1, 2])
 def test_records_bit_exact(name, method):
     rp, col, og, g = pair(name)
@@ -165,7 +185,7 @@ def test_records_bit_exact(name, method):
     g.set_probe(moss.PROBE_AUTO)
 
 
-@pytest.mark.parametrize("name", ["gnp12", "cl_n200", "rgg2k", "cl_n2k"])
+@pytest.mark.parametrize("name", ["gnp12", "cl_n200", "rgg2k", "cl_n2k", "hub70k"])
 def test_counts_and_estimates(name):
     rp, col, og, g = pair(name)
     budget, seed = 200_001, 99
