@@ -228,13 +228,14 @@ DEFER_CHUNK = 1 << 25   # Path-5 sample ids per main/deferred launch pair
 
 def resolved_probe(name: str, row_ptr) -> str:
     """The strategy the library picks for --probe auto: the filtered set when
-    the hashed set (next power of two >= nnz buckets of 16 B) exceeds 64 MiB."""
+    the hashed set (next power of two >= nnz / 2 buckets of 32 B) exceeds
+    64 MiB."""
     if name != "auto":
         return name
     nnz, b = int(row_ptr[-1]), 2
-    while b < nnz:
+    while b < (nnz + 1) // 2:
         b <<= 1
-    return "filter" if b * 16 > (64 << 20) else "hash"
+    return "filter" if b * 32 > (64 << 20) else "hash"
 
 
 def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False) -> int:

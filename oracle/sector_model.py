@@ -13,7 +13,7 @@ vertex records of 16 B, per-slot records of 32 B (one sector) and
 ordered-list entries of 8 B.  Each
 probe is either a lower-bound search with early exit in the shorter sorted
 list (MOSS_PROBE_SEARCH, which also reads the two vertex records) or the home
-bucket of the hashed edge set (MOSS_PROBE_HASH, 16 B buckets; the rare
+bucket of the hashed edge set (MOSS_PROBE_HASH, 32 B buckets of four keys; the rare
 continuation into the next bucket is not counted), or the word of the edge
 filter followed by that bucket only when the filter passes (MOSS_PROBE_FILTER).
 The draws are replayed from the oracle's Philox words and tables, so the
@@ -100,8 +100,8 @@ class Replay:
         thr, alias, acc = self.g.sigma_table()
         self.thr, self.alias, self.acc = thr.astype(np.int64), alias.astype(np.int64), acc.astype(np.int64)
         self.probe_kind = probe
-        buckets = 2
-        while buckets < len(col):
+        buckets = 2   # the library's table: next power of two >= nnz / 2 buckets
+        while buckets < (len(col) + 1) // 2:
             buckets <<= 1
         self.shift = 64 - (buckets.bit_length() - 1)
         if probe == "filter":   # the library's filter: largest power of two <= nnz / 8 words
@@ -168,10 +168,10 @@ class Replay:
             touched.add(("filter", w >> 3))
             m = filter_mask(h)
             if int(self.filter[w]) & m == m:
-                touched.add(("hash", edge_bucket(a, b, self.shift) >> 1))
+                touched.add(("hash", edge_bucket(a, b, self.shift)))
             return
-        if self.probe_kind == "hash":   # home bucket of 16 B: two per sector
-            touched.add(("hash", edge_bucket(int(a), int(b), self.shift) >> 1))
+        if self.probe_kind == "hash":   # home bucket: one 32 B sector
+            touched.add(("hash", edge_bucket(int(a), int(b), self.shift)))
             return
         da, db = self.deg[a], self.deg[b]
         if da <= db:
@@ -315,7 +315,7 @@ def model(workload: str, samples: int = 4000, seed: int = 42) -> dict:
     out = {"workload": workload, "samples": samples, "seed": seed,
            "layout": ("32 B vertex alias records with the alias's vertex record, 32 B slot records with the "
                       "alias's pick and both picks' neighbour list and twin, 16 B vertex records, "
-                      "4 B ids and ACC, 8 B Q, 16 B edge-hash buckets (home bucket counted), 4 B edge-filter words "
+                      "4 B ids and ACC, 8 B Q, 32 B edge-hash buckets (home bucket counted), 4 B edge-filter words "
                       "(the set's bucket only when the filter passes); MOSS-4Min: 16 B "
                       "vertex, 32 B slot, 8 B list records; 32 B sectors"),
            "source": "written by oracle/sector_model.py"}

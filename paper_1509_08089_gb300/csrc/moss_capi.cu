@@ -180,7 +180,7 @@ struct moss_graph {
     uint32_t *defer = nullptr;   // Path-5 deferral bitmap (kDeferChunk bits)
     void *arena = nullptr;       // every device array above lives in this one allocation
     int probe = MOSS_PROBE_AUTO; // membership tests (MOSS_PROBE_*), as requested
-    unsigned long long *hash = nullptr;  // 2 keys per bucket
+    unsigned long long *hash = nullptr;  // kBucketKeys keys per bucket
     uint64_t hash_buckets = 0;
     uint32_t *filter = nullptr;  // Bloom filter in front of the hash
     uint64_t filter_words = 0;
@@ -201,10 +201,11 @@ void release(moss_graph *g) {
     delete g;
 }
 
-// buckets of the hashed edge set: the next power of two >= nnz (>= 4 slots per edge)
+// buckets of the hashed edge set: the next power of two >= nnz / 2, so at
+// least 4 slots per undirected edge (nnz / 2 edges, kBucketKeys slots each)
 uint64_t hash_buckets_for(uint64_t nnz) {
     uint64_t b = 2;
-    while (b < nnz) b <<= 1;
+    while (b < (nnz + 1) / 2) b <<= 1;
     return b;
 }
 
@@ -217,7 +218,7 @@ uint64_t filter_words_for(uint64_t nnz) {
 
 int effective_probe(const moss_graph *g) {
     if (g->probe != MOSS_PROBE_AUTO) return g->probe;
-    return hash_buckets_for(g->nnz) * 16 > (64ull << 20) ? MOSS_PROBE_FILTER : MOSS_PROBE_HASH;
+    return hash_buckets_for(g->nnz) * 8 * kBucketKeys > (64ull << 20) ? MOSS_PROBE_FILTER : MOSS_PROBE_HASH;
 }
 
 DevGraph view(const moss_graph *g) {
@@ -503,7 +504,7 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
     bool hashed = false, filtered = false;
     const int eff = effective_probe(g);
     if (e == cudaSuccess && eff != MOSS_PROBE_SEARCH) {
-        // at least 4 slots per undirected edge: buckets = next power of two >= nnz
+        // at least 4 slots per undirected edge
         const uint64_t buckets = hash_buckets_for(g->nnz);
         if (buckets > (1ULL << 32)) return fail(MOSS_EOVERFLOW, "edge hash above 2^32 buckets");
         if (g->hash && g->hash_buckets != buckets) {
@@ -511,13 +512,13 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
             g->hash = nullptr;
         }
         if (!g->hash) {
-            e = pool_alloc(g->device, reinterpret_cast<void **>(&g->hash), buckets * 16, s);
+            e = pool_alloc(g->device, reinterpret_cast<void **>(&g->hash), buckets * 8 * kBucketKeys, s);
             if (e != cudaSuccess) return cuda_fail(e, "allocating edge hash");
             g->hash_buckets = buckets;
         }
         uint32_t lg = 0;
         while ((1ULL << lg) < buckets) ++lg;
-        e = cudaMemsetAsync(g->hash, 0xFF, buckets * 16, s);
+        e = cudaMemsetAsync(g->hash, 0xFF, buckets * 8 * kBucketKeys, s);
         if (e == cudaSuccess)
             e = launch_edge_hash(g->nnz, g->col, g->owner, g->hash, (uint32_t)(buckets - 1), 64 - lg, s);
         hashed = e == cudaSuccess;

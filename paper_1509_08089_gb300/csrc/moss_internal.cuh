@@ -82,7 +82,7 @@ struct DevGraph {
     const uint4 *mvert;     // MOSS-4Min tables (null until built)
     const uint4 *mslot;
     const uint2 *rlist;
-    const uint4 *hash;      // hashed edge set (2 keys per 16 B bucket), or null: probe by search
+    const uint4 *hash;      // hashed edge set (4 keys per 32 B bucket), or null: probe by search
     const uint32_t *filter; // Bloom filter in front of the hash, or null
     uint32_t *defer;        // Path-5 deferral bitmap, kDeferChunk bits
     uint32_t hash_mask;     // buckets - 1
@@ -93,10 +93,12 @@ struct DevGraph {
 
 // ------------------------------------------------------- hashed edge set --
 // Key of the undirected edge {a, b}: (min << 32) | max; empty slot: ~0.
-// Buckets hold two keys (16 B); a bucket's second slot is filled only after
-// its first, and keys are never removed, so a lookup walking from the home
-// bucket can stop at the first bucket whose second slot is empty.
+// Buckets hold four keys (32 B, one sector, read by one 256-bit load); a
+// bucket's slot k is filled only after its slot k-1, and keys are never
+// removed, so a lookup walking from the home bucket can stop at the first
+// bucket whose last slot is empty.
 constexpr uint64_t kEmptyKey = ~0ULL;
+constexpr int kBucketKeys = 4;
 
 __host__ __device__ inline uint64_t edge_key(uint32_t a, uint32_t b) {
     return a < b ? ((uint64_t)a << 32) | b : ((uint64_t)b << 32) | a;

@@ -156,7 +156,7 @@ __device__ __forceinline__ uint32_t probe_pairs(const uint32_t *col, const uint4
     return found;
 }
 
-// Membership tests through the hashed edge set: one 16-byte bucket load per
+// Membership tests through the hashed edge set: one 32-byte bucket load per
 // pair in the common case, all P loads issued together.
 template <int P>
 __device__ __forceinline__ uint32_t probe_hash(const DevGraph &g, const uint32_t (&a)[P], const uint32_t (&b)[P]) {
@@ -181,12 +181,14 @@ __device__ __forceinline__ uint32_t probe_hash(const DevGraph &g, const uint32_t
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (pending >> p & 1u) {
-                const uint4 e = ld4(g.hash + bk[p]);
-                const uint64_t k0 = ((uint64_t)e.y << 32) | e.x, k1 = ((uint64_t)e.w << 32) | e.z;
-                if (k0 == key[p] || k1 == key[p]) {
+                const Sector e = ld8(g.hash + 2 * (uint64_t)bk[p]);
+                const uint32_t lo = (uint32_t)key[p], hi = (uint32_t)(key[p] >> 32);
+                const bool hit = (e.lo.x == lo && e.lo.y == hi) || (e.lo.z == lo && e.lo.w == hi) ||
+                                 (e.hi.x == lo && e.hi.y == hi) || (e.hi.z == lo && e.hi.w == hi);
+                if (hit) {
                     found |= 1u << p;
                     pending &= ~(1u << p);
-                } else if (k1 == kEmptyKey) {
+                } else if (e.hi.z == 0xffffffffu && e.hi.w == 0xffffffffu) {   // last slot empty
                     pending &= ~(1u << p);
                 } else {
                     bk[p] = (bk[p] + 1) & g.hash_mask;
@@ -671,13 +673,21 @@ __global__ void k_batch_reduce(const BatchTask *tasks, uint32_t tile_samples, co
 }
 
 // accumulate: add to out (later chunks of one count) instead of overwriting
+// One block of 32 x kSlots threads: thread t adds slot t % kSlots of every
+// 32nd row from row t / kSlots (consecutive threads read consecutive words),
+// then 32 partial sums per slot are added in shared memory.
 __global__ void k_reduce(const uint64_t *partials, int blocks, uint64_t *out, int accumulate) {
-    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ uint64_t part[32][kSlots];
+    const int c = threadIdx.x % kSlots, r0 = threadIdx.x / kSlots;
     uint64_t s = 0;
-    for (int b = lane; b < blocks; b += 32) s += partials[(uint64_t)b * kSlots + c];
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
-    if (lane == 0) out[c] = accumulate ? out[c] + s : s;
+    for (int b = r0; b < blocks; b += 32) s += partials[(uint64_t)b * kSlots + c];
+    part[r0][c] = s;
+    __syncthreads();
+    if (threadIdx.x < kSlots) {
+        uint64_t t = 0;
+        for (int r = 0; r < 32; ++r) t += part[r][threadIdx.x];
+        out[threadIdx.x] = accumulate ? out[threadIdx.x] + t : t;
+    }
 }
 
 template <int M, bool R>

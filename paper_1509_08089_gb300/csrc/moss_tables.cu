@@ -216,19 +216,35 @@ __global__ void __launch_bounds__(kLongThreads) k_slots_long(uint32_t n, uint4 *
     if (threadIdx.x == 0) t.store(partials + (uint64_t)blockIdx.x * 6);
 }
 
-__global__ void k_totals(const u128 *partials, int blocks, DevTotals *tot) {
-    const int lane = threadIdx.x;  // one warp
+// One block of kTotalsThreads: each thread adds a strided share of the rows,
+// then warps and the block combine (exact integer sums and a maximum, so the
+// order does not matter).
+constexpr int kTotalsThreads = 1024;
+
+__device__ __forceinline__ void warp_totals(u128 (&s)[6]) {
+    for (int j = 0; j < 5; ++j) s[j] = warp_sum128(s[j]);
+    for (int d = 16; d > 0; d >>= 1) {
+        const u128 o = shfl_down_u128(s[5], d);
+        s[5] = o > s[5] ? o : s[5];
+    }
+}
+
+__global__ void __launch_bounds__(kTotalsThreads) k_totals(const u128 *partials, int blocks, DevTotals *tot) {
+    __shared__ u128 w_tot[kTotalsThreads / kWarp][6];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     u128 s[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = lane; b < blocks; b += kWarp)
+    for (int b = threadIdx.x; b < blocks; b += kTotalsThreads)
         for (int j = 0; j < 6; ++j) {
             u128 x = partials[(uint64_t)b * 6 + j];
             s[j] = j == 5 ? (x > s[j] ? x : s[j]) : s[j] + x;
         }
-    for (int j = 0; j < 5; ++j) s[j] = warp_sum128(s[j]);
-    for (int d = 16; d > 0; d >>= 1) {
-        u128 o = shfl_down_u128(s[5], d);
-        s[5] = o > s[5] ? o : s[5];
-    }
+    warp_totals(s);
+    if (lane == 0)
+        for (int j = 0; j < 6; ++j) w_tot[warp][j] = s[j];
+    __syncthreads();
+    if (warp != 0) return;
+    for (int j = 0; j < 6; ++j) s[j] = w_tot[lane][j];   // kTotalsThreads / kWarp == 32 rows
+    warp_totals(s);
     if (lane == 0) {
         tot->gamma[0] = s[0];
         tot->gamma[1] = s[1];
@@ -283,9 +299,9 @@ __global__ void k_twin(uint32_t n, uint64_t nnz, const uint4 *__restrict__ vert,
 
 // ----------------------------------------------------- hashed edge set ---
 // One thread per slot inserts the edge {v, x} with v < x by compare-and-swap
-// into the first free slot from the home bucket on.  The table has at least
-// four slots per edge, so a free slot always exists and the walk is bounded
-// by the bucket count.
+// into the first free slot from the home bucket on, slots of a bucket in
+// order.  The table has at least four slots per edge, so a free slot always
+// exists and the walk is bounded by the bucket count.
 __global__ void k_edge_hash(uint64_t nnz, const uint32_t *__restrict__ col, const uint32_t *__restrict__ owner,
                             unsigned long long *table, uint32_t mask, uint32_t shift) {
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
@@ -293,11 +309,13 @@ __global__ void k_edge_hash(uint64_t nnz, const uint32_t *__restrict__ col, cons
         if (x <= v) continue;
         const unsigned long long key = edge_key(v, x);
         uint32_t b = edge_bucket(key, shift);
-        for (uint64_t it = 0; it <= mask; ++it) {
-            unsigned long long old = atomicCAS(table + 2ull * b, (unsigned long long)kEmptyKey, key);
-            if (old == kEmptyKey || old == key) break;
-            old = atomicCAS(table + 2ull * b + 1, (unsigned long long)kEmptyKey, key);
-            if (old == kEmptyKey || old == key) break;
+        bool done = false;
+        for (uint64_t it = 0; it <= mask && !done; ++it) {
+            for (int k = 0; k < kBucketKeys && !done; ++k) {
+                const unsigned long long old =
+                    atomicCAS(table + (uint64_t)kBucketKeys * b + k, (unsigned long long)kEmptyKey, key);
+                done = old == kEmptyKey || old == key;
+            }
             b = (b + 1) & mask;
         }
     }
@@ -811,7 +829,7 @@ cudaError_t launch_slots(uint32_t n, uint64_t nnz, const uint32_t *col, uint4 *v
 }
 
 cudaError_t launch_totals(const u128 *partials, int blocks, DevTotals *tot, cudaStream_t s) {
-    k_totals<<<1, kWarp, 0, s>>>(partials, blocks, tot);
+    k_totals<<<1, kTotalsThreads, 0, s>>>(partials, blocks, tot);
     return cudaGetLastError();
 }
 
