@@ -407,37 +407,50 @@ __device__ __noinline__ void path5_fallback(const uint32_t *acc, const uint64_t 
     iw = lo - 1;
 }
 
-// DEFER: a sample whose first attempt collides returns kDeferred at once (the
-// retry and the fallback are left to k_sample_deferred, which calls this with
-// DEFER = false), so that their live state does not set the register budget
-// of the main launch.
+// Path-5 in stages, so that the rare paths do not set the register budget
+// of the common one: STAGE 0 takes the first attempt and returns kDeferred
+// when it collides (the main launch); STAGE 1 the second attempt of such a
+// sample, again kDeferred when it collides; STAGE 2 the fallback of a sample
+// whose two attempts collided; STAGE 3 all three in turn.  The draws depend
+// only on the sample id, so the stages give the sample the same result as
+// STAGE 3.
 constexpr int kDeferred = 254;
 
-template <bool HASH, bool DEFER>
+template <bool HASH, int STAGE>
 __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
     const Words4 a = philox4x64(s, 0, 2, 0, seed, 0);
     const VertexPick pv = draw_vertex(g.seed[2], g.vert, g.n, a.x[0], a.x[1]);
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
-    const Words4 b = philox4x64(s, 1, 2, 0, seed, 0);
-    Pick pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, b.x[0], b.x[1]);
-    Pick pw = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, b.x[2], b.x[3]);
-    if (pu.pos == pw.pos) {
-        if (DEFER) {
+    Pick pu, pw;
+    bool collide = true;
+    if (STAGE == 0 || STAGE == 3) {
+        const Words4 b = philox4x64(s, 1, 2, 0, seed, 0);
+        pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, b.x[0], b.x[1]);
+        pw = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, b.x[2], b.x[3]);
+        collide = pu.pos == pw.pos;
+        if (STAGE == 0 && collide) {
             out.cls = kDeferred;
             return out;
         }
+    }
+    if (STAGE == 1 || (STAGE == 3 && collide)) {
         const Words4 c = philox4x64(s, 2, 2, 0, seed, 0);
         pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, c.x[0], c.x[1]);
         pw = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, c.x[2], c.x[3]);
-        if (pu.pos == pw.pos) {
-            const Words4 d4 = philox4x64(s, 3, 2, 0, seed, 0);
-            uint32_t iu, iw;
-            path5_fallback(g.acc, g.sq, v, vr, d4.x[0], d4.x[1], iu, iw);
-            pu = slot_pick(g.slot, g.vert, vr.x, iu);
-            pw = slot_pick(g.slot, g.vert, vr.x, iw);
+        collide = pu.pos == pw.pos;
+        if (STAGE == 1 && collide) {
+            out.cls = kDeferred;
+            return out;
         }
+    }
+    if (STAGE == 2 || (STAGE == 3 && collide)) {
+        const Words4 d4 = philox4x64(s, 3, 2, 0, seed, 0);
+        uint32_t iu, iw;
+        path5_fallback(g.acc, g.sq, v, vr, d4.x[0], d4.x[1], iu, iw);
+        pu = slot_pick(g.slot, g.vert, vr.x, iu);
+        pw = slot_pick(g.slot, g.vert, vr.x, iw);
     }
     const uint32_t u = pu.id, w = pw.id;
     const uint32_t r = ld1(g.col + pu.off + skip1((uint32_t)word_index(a.x[2], pu.deg - 1), pu.twin));
@@ -473,11 +486,12 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
 // Resident blocks per SM each sampler is compiled for: the loop is bound by
 // memory latency, so more warps in flight help until register spills cost
 // more than they hide (measured: 6 blocks of 256 threads for every main
-// sampler; Path-5 reaches it only with its retry path deferred, whose own
-// launch runs at 4).
+// sampler; Path-5 reaches it only with its second attempt and fallback
+// deferred).  The second-attempt launch runs 5 blocks, the fallback launch 4.
 template <int METHOD>
 constexpr int min_blocks() { return 6; }
-constexpr int kDeferBlocks = 4;
+template <int STAGE>
+constexpr int defer_min_blocks() { return STAGE == 1 ? 5 : 4; }
 
 template <int METHOD, bool RECORD, bool HASH>
 __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGraph g, uint64_t first, uint64_t count, uint64_t seed,
@@ -502,7 +516,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGr
             Sample sm;
             if (METHOD == 0) sm = sample_moss4<HASH>(g, lut, seed, s);
             else if (METHOD == 1) sm = sample_t5<HASH>(g, lut, seed, s);
-            else if (METHOD == 2) sm = sample_path5<HASH, true>(g, lut, seed, s);
+            else if (METHOD == 2) sm = sample_path5<HASH, 0>(g, lut, seed, s);
             else sm = sample_min<HASH>(g, lut, seed, s);
             deferred = METHOD == 2 && sm.cls == kDeferred;
             if (!deferred) {
@@ -531,47 +545,44 @@ __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGr
     }
 }
 
-// The Path-5 samples a main launch deferred.  A warp takes 32 bitmap words
-// (1,024 ids), lists their flagged ids in shared memory (a warp scan of the
-// words' popcounts places them), then draws them 32 at a time, one per lane,
-// in full (second attempt, fallback); counts are aggregated as in k_sample and
-// written to this launch's own partial rows.
-template <bool RECORD, bool HASH>
-__global__ void __launch_bounds__(kThreads, kDeferBlocks)
+// The Path-5 samples a launch deferred, redrawn by the next stage (STAGE 1:
+// second attempt, re-deferring the samples that collide again; STAGE 2:
+// fallback).  A warp takes windows of 32 bitmap words (grid-stride); it
+// appends each window's flagged ids to a list in shared memory (a warp scan
+// of the words' popcounts places them) and draws from the list 32 at a time,
+// one per lane, keeping fewer than 32 ids over to its next window, so every
+// round but the warp's last runs with all lanes busy however sparse the
+// flags.  STAGE 1 clears the words it reads and sets the bits of re-deferred
+// samples again (plain stores: a window's words belong to one warp).  Counts
+// are aggregated as in k_sample into this launch's partial rows; STAGE 2,
+// launched with no more blocks than STAGE 1, adds into STAGE 1's rows.
+constexpr uint32_t kDeferList = 1024 + 32;   // a window's ids plus the carry-over
+
+template <bool RECORD, bool HASH, int STAGE>
+__global__ void __launch_bounds__(kThreads, defer_min_blocks<STAGE>())
     k_sample_deferred(DevGraph g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
                       uint8_t *classes, uint32_t *verts) {
+    static_assert(STAGE == 1 || STAGE == 2, "deferred stages are 1 and 2");
     __shared__ uint8_t lut[kLut];
     __shared__ uint32_t hist[kWarps][kSlots];
-    __shared__ uint32_t list[kWarps][32 * 32];
+    __shared__ uint32_t list[kWarps][kDeferList];   // ids relative to the chunk's first
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kLut; i += kThreads) lut[i] = g_lut5[i];
     for (int i = threadIdx.x; i < kWarps * kSlots; i += kThreads) (&hist[0][0])[i] = 0;
     __syncthreads();
     const uint64_t words = (count + 31) / 32;
     const uint64_t stride = (uint64_t)gridDim.x * kWarps * 32;
-    for (uint64_t w0 = ((uint64_t)blockIdx.x * kWarps + warp) * 32; w0 < words; w0 += stride) {
-        const uint64_t w = w0 + lane;
-        uint32_t bits = w < words ? g.defer[w] : 0u;
-        // exclusive prefix of the popcounts: where this word's ids go in the list
-        const uint32_t c = __popc(bits);
-        uint32_t incl = c;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += t;
-        }
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        uint32_t at = incl - c;
-        while (bits) {
-            list[warp][at++] = (uint32_t)(lane * 32 + __ffs(bits) - 1);   // id - 32 w0
-            bits &= bits - 1;
-        }
-        __syncwarp();
-        for (uint32_t j0 = 0; j0 < total; j0 += 32) {
-            int cls = kSlots;
-            if (j0 + lane < total) {
-                const uint64_t i = w0 * 32 + list[warp][j0 + lane];   // < count: only drawn ids are flagged
-                const Sample sm = sample_path5<HASH, false>(g, lut, seed, first + i);
+    uint32_t *lst = list[warp];
+    // draws lst[k0 + lane] for lane < cnt (warp-uniform arguments)
+    auto round = [&](uint32_t k0, uint32_t cnt) {
+        int cls = kSlots;
+        bool again = false;
+        uint64_t i = 0;
+        if ((uint32_t)lane < cnt) {
+            i = lst[k0 + lane];   // < count: only drawn ids are flagged
+            const Sample sm = sample_path5<HASH, STAGE>(g, lut, seed, first + i);
+            again = STAGE == 1 && sm.cls == kDeferred;
+            if (!again) {
                 cls = sm.cls;
                 if (RECORD) {
                     classes[i] = (uint8_t)sm.cls;
@@ -581,16 +592,64 @@ __global__ void __launch_bounds__(kThreads, kDeferBlocks)
                     }
                 }
             }
-            const uint32_t peers = __match_any_sync(0xffffffffu, cls);
-            if (cls < kSlots && lane == __ffs(peers) - 1) atomicAdd(&hist[warp][cls], (uint32_t)__popc(peers));
         }
-        __syncwarp();   // the list is refilled for the next 32 words
+        if (STAGE == 1 && __any_sync(0xffffffffu, again)) {
+            // OR of the re-deferred bits per word; the first lane of each word stores it
+            const uint64_t wi = again ? i >> 5 : ~0ull;
+            const uint32_t bit = again ? 1u << (i & 31) : 0u;
+            uint32_t bits = 0, first_lane = 32;
+            for (int l = 0; l < 32; ++l) {
+                const uint64_t wl = __shfl_sync(0xffffffffu, wi, l);
+                const uint32_t bl = __shfl_sync(0xffffffffu, bit, l);
+                if (wl == wi) {
+                    bits |= bl;
+                    first_lane = min(first_lane, (uint32_t)l);
+                }
+            }
+            if (again && first_lane == (uint32_t)lane) g.defer[wi] |= bits;
+            __syncwarp();
+        }
+        const uint32_t peers = __match_any_sync(0xffffffffu, cls);
+        if (cls < kSlots && lane == __ffs(peers) - 1) atomicAdd(&hist[warp][cls], (uint32_t)__popc(peers));
+    };
+    uint32_t n = 0;   // ids waiting in the list (warp-uniform, < 32 between windows)
+    for (uint64_t w0 = ((uint64_t)blockIdx.x * kWarps + warp) * 32; w0 < words; w0 += stride) {
+        const uint64_t w = w0 + lane;
+        uint32_t bits = w < words ? g.defer[w] : 0u;
+        if (STAGE == 1 && bits) g.defer[w] = 0u;   // re-deferred ids are set again by round()
+        const uint32_t c = __popc(bits);
+        uint32_t incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t at = n + incl - c;
+        while (bits) {
+            lst[at++] = (uint32_t)(w * 32 + __ffs(bits) - 1);
+            bits &= bits - 1;
+        }
+        n += total;
+        __syncwarp();
+        uint32_t done = 0;
+        for (; n - done >= 32; done += 32) round(done, 32);
+        if (done) {   // move the remainder (< 32 ids) to the front
+            const uint32_t rem = n - done;
+            const uint32_t x = (uint32_t)lane < rem ? lst[done + lane] : 0u;
+            __syncwarp();
+            if ((uint32_t)lane < rem) lst[lane] = x;
+            __syncwarp();
+            n = rem;
+        }
     }
+    if (n) round(0, n);
     __syncthreads();
     if (threadIdx.x < kSlots) {
         uint64_t sum = 0;
         for (int w = 0; w < kWarps; ++w) sum += hist[w][threadIdx.x];
-        partials[(uint64_t)blockIdx.x * kSlots + threadIdx.x] = sum;
+        uint64_t *row = partials + (uint64_t)blockIdx.x * kSlots + threadIdx.x;
+        *row = STAGE == 1 ? sum : *row + sum;
     }
 }
 
@@ -608,7 +667,7 @@ __device__ __forceinline__ int sample_any(const DevGraph &g, const uint8_t *lut4
                                           uint64_t seed, uint64_t s) {
     if (method == 0) return sample_moss4<HASH>(g, lut4, seed, s).cls;
     if (method == 1) return sample_t5<HASH>(g, lut5, seed, s).cls;
-    return sample_path5<HASH, false>(g, lut5, seed, s).cls;
+    return sample_path5<HASH, 3>(g, lut5, seed, s).cls;
 }
 
 __global__ void __launch_bounds__(kThreads, kBatchBlocks)
@@ -748,29 +807,31 @@ cudaError_t launch_sample(int method, const DevGraph &g, uint64_t first, uint64_
     }
 }
 
+template <int STAGE>
 cudaError_t launch_deferred(const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
                             int blocks, uint8_t *classes, uint32_t *verts, cudaStream_t s) {
     const bool rec = classes != nullptr;
     if (g.hash) {
-        if (rec) k_sample_deferred<true, true><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-        else k_sample_deferred<false, true><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+        if (rec) k_sample_deferred<true, true, STAGE><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+        else k_sample_deferred<false, true, STAGE><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
     } else {
-        if (rec) k_sample_deferred<true, false><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-        else k_sample_deferred<false, false><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+        if (rec) k_sample_deferred<true, false, STAGE><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+        else k_sample_deferred<false, false, STAGE><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
     }
     return cudaGetLastError();
 }
 
-int defer_blocks(int device) {
+// blocks of a deferred stage: its resident blocks per SM times the SMs
+int defer_blocks(int device, int stage) {
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    return sms * kDeferBlocks;
+    return sms * (stage == 1 ? defer_min_blocks<1>() : defer_min_blocks<2>());
 }
 
 }  // namespace
 
 int sample_rows(int method, int device) {
-    return sample_blocks(method, device) + (method == 2 ? defer_blocks(device) : 0);
+    return sample_blocks(method, device) + (method == 2 ? defer_blocks(device, 1) : 0);
 }
 
 cudaError_t launch_counts(int method, const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed,
@@ -786,16 +847,17 @@ cudaError_t launch_counts(int method, const DevGraph &g, uint64_t first, uint64_
         k_reduce<<<1, 32 * kSlots, 0, s>>>(partials, blocks, counts_dev, 0);
         return cudaGetLastError();
     }
-    const int dblocks = defer_blocks(dev);
+    // the fallback stage adds into the first rows of the second-attempt stage
+    const int d1 = defer_blocks(dev, 1), d2 = min(defer_blocks(dev, 2), d1);
     for (uint64_t c0 = 0; c0 < count; c0 += kDeferChunk) {
         const uint64_t len = count - c0 < kDeferChunk ? count - c0 : kDeferChunk;
         uint8_t *cl = classes ? classes + c0 : nullptr;
         uint32_t *vt = verts ? verts + 5 * c0 : nullptr;
+        uint64_t *drows = partials + (uint64_t)blocks * kSlots;
         if ((e = launch_sample(2, g, first + c0, len, seed, partials, blocks, cl, vt, s)) != cudaSuccess) return e;
-        if ((e = launch_deferred(g, first + c0, len, seed, partials + (uint64_t)blocks * kSlots, dblocks, cl, vt, s)) !=
-            cudaSuccess)
-            return e;
-        k_reduce<<<1, 32 * kSlots, 0, s>>>(partials, blocks + dblocks, counts_dev, c0 > 0 ? 1 : 0);
+        if ((e = launch_deferred<1>(g, first + c0, len, seed, drows, d1, cl, vt, s)) != cudaSuccess) return e;
+        if ((e = launch_deferred<2>(g, first + c0, len, seed, drows, d2, cl, vt, s)) != cudaSuccess) return e;
+        k_reduce<<<1, 32 * kSlots, 0, s>>>(partials, blocks + d1, counts_dev, c0 > 0 ? 1 : 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
