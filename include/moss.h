@@ -349,6 +349,12 @@ int moss_graph_stats(const moss_graph *g, moss_stats *out);
  *   MOSS_TABLE_MIN_SLOT  nnz x {uint64 sigma-check threshold, uint32 alias
  *                        (position in N_v), u, off_u, d_u, d_{v,u}, d_{u,v}}
  *   MOSS_TABLE_MIN_LIST  nnz x {uint32 x, d_x}: each N_v highest first
+ *   MOSS_TABLE_MIN_PICK  nnz x {uint32 threshold, u, off_u, d_{v,u} |
+ *                        d_{u,v} << 16, then the alias position's u, off_u,
+ *                        d_{v,u} | d_{u,v} << 16, and d_u | alias's d_u << 16}
+ *                        -- meaningful where Gamma-check_v < 2^32 and every
+ *                        field fits 16 bits; otherwise the last word is
+ *                        0xFFFFFFFF
  * and, after a build under MOSS_PROBE_FILTER (or AUTO choosing it):
  *   MOSS_TABLE_FILTER    W x uint32 filter words, W the largest power of two
  *                        <= nnz / 8 (at least 1)
@@ -364,6 +370,7 @@ int moss_graph_stats(const moss_graph *g, moss_stats *out);
 #define MOSS_TABLE_MIN_SLOT  12
 #define MOSS_TABLE_MIN_LIST  13
 #define MOSS_TABLE_FILTER    14
+#define MOSS_TABLE_MIN_PICK  15
 int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t bytes);
 
 void moss_graph_free(moss_graph *g);

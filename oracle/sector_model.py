@@ -9,8 +9,9 @@ alias position's pick, and for both picks the picked neighbour's list and
 twin, so its vertex record is read only for a neighbour of degree 2^16 or
 more), vertex records of 16 B, neighbour ids of 4 B, ACC entries of 4 B and
 prefixes of squares of 8 B (Path-5 fallback); for MOSS-4Min its
-vertex records of 16 B, per-slot records of 32 B (one sector) and
-ordered-list entries of 8 B.  Each
+vertex records of 16 B, per-slot pick records of 32 B (one sector with the
+draw and both possible picks; two slot records of 32 B where the list's
+total or a field is too wide) and ordered-list entries of 8 B.  Each
 probe is either a lower-bound search with early exit in the shorter sorted
 list (MOSS_PROBE_SEARCH, which also reads the two vertex records) or the home
 bucket of the hashed edge set (MOSS_PROBE_HASH, 32 B buckets of four keys; the rare
@@ -123,6 +124,25 @@ class Replay:
             self.gam_m = gam
             self.seed_m = T
 
+    def rank_twin(self, v, p):
+        """d_{u,v} for position p (v -> u): the rank held by the twin slot."""
+        u = int(self.col[p])
+        ou = int(self.rp[u])
+        return int(self.rank[ou + int(np.searchsorted(self.col[ou:self.rp[u + 1]], v))])
+
+    def pick_fits(self, v, p):
+        """The library reads a MOSS-4Min pick record for a list with
+        Gamma-check_v < 2^32 when d_u, d_{v,u} and d_{u,v} of the position
+        and of its alias position all fit 16 bits (below 0xFFFF)."""
+        if int(self.gam_m[v]) >= 1 << 32:
+            return False
+        ap = int(self.rp[v]) + int(self.calias_m[p])
+        for q in (p, ap):
+            fields = (int(self.deg[int(self.col[q])]), int(self.rank[q]), self.rank_twin(v, q))
+            if max(fields) >= 0xFFFF:
+                return False
+        return True
+
     def sample_min(self, seed, s, verts, cls):
         """Sectors of one MOSS-4Min sample (Algorithm 2)."""
         self.min_tables()
@@ -135,14 +155,19 @@ class Replay:
             t.add(("mvert", v >> 1))
         o, d = int(self.rp[v]), int(self.deg[v])
         j = idx(x[2], d)
-        t.add(("mslot", o + j))
-        if idx(x[3], self.gam_m[v]) >= int(self.cthr_m[o + j]):
-            j = int(self.calias_m[o + j])
+        if self.pick_fits(v, o + j):   # the pick record serves the whole draw
+            t.add(("mpick", o + j))
+            if idx(x[3], self.gam_m[v]) >= int(self.cthr_m[o + j]):
+                j = int(self.calias_m[o + j])
+        else:
             t.add(("mslot", o + j))
+            if idx(x[3], self.gam_m[v]) >= int(self.cthr_m[o + j]):
+                j = int(self.calias_m[o + j])
+                t.add(("mslot", o + j))
         u = int(self.col[o + j])
         dvu = int(self.rank[o + j])
         ou = int(self.rp[u])
-        duv = int(self.rank[ou + int(np.searchsorted(self.col[ou:self.rp[u + 1]], v))])
+        duv = self.rank_twin(v, o + j)
         t.add(("rlist", (o + idx(x[4], dvu)) >> 2))
         t.add(("rlist", (ou + idx(x[5], duv)) >> 2))
         w, r = int(verts[2]), int(verts[3])
@@ -317,7 +342,7 @@ def model(workload: str, samples: int = 4000, seed: int = 42) -> dict:
                       "alias's pick and both picks' neighbour list and twin, 16 B vertex records, "
                       "4 B ids and ACC, 8 B Q, 32 B edge-hash buckets (home bucket counted), 4 B edge-filter words "
                       "(the set's bucket only when the filter passes); MOSS-4Min: 16 B "
-                      "vertex, 32 B slot, 8 B list records; 32 B sectors"),
+                      "vertex, 32 B pick (32 B slot where too wide), 8 B list records; 32 B sectors"),
            "source": "written by oracle/sector_model.py"}
     for probe, suffix in (("search", "_search"), ("hash", "_hash"), ("filter", "_filter")):
         rep = Replay(rp, col, probe)

@@ -127,9 +127,33 @@ int mask_class(int k, uint32_t mask) {
     return -1;
 }
 
+// c(s) of Sec. 4.2 for a 4-vertex CIS with edge mask `mask` over the roles
+// 0..3 (pair bits (0,1),(0,2),(0,3),(1,2),(1,3),(2,3)) whose vertices are
+// ordered by `above`: bit b set when the first vertex of pair b is above the
+// second in the total order.  Counts the 3-paths p0-p1-p2-p3 with p0 above p2
+// and p3 above p1, each unordered path once (the orientation whose end roles
+// satisfy p0 < p3).
+int centred_paths_of(uint32_t mask, uint32_t above) {
+    auto bit = [](int a, int b) { return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5); };   // a < b
+    auto edge = [&](int a, int b) { return (mask >> (a < b ? bit(a, b) : bit(b, a)) & 1u) != 0; };
+    auto over = [&](int a, int b) { return a < b ? (above >> bit(a, b) & 1u) != 0 : (above >> bit(b, a) & 1u) == 0; };
+    int c = 0;
+    for (int e0 = 0; e0 < 4; ++e0)
+        for (int e3 = e0 + 1; e3 < 4; ++e3) {
+            int mid[2], k = 0;
+            for (int x = 0; x < 4; ++x)
+                if (x != e0 && x != e3) mid[k++] = x;
+            for (int o = 0; o < 2; ++o) {
+                const int p1 = mid[o], p2 = mid[1 - o];
+                if (edge(e0, p1) && edge(p1, p2) && edge(p2, e3) && over(e0, p2) && over(e3, p1)) ++c;
+            }
+        }
+    return c;
+}
+
 std::mutex g_lut_mutex;
 bool g_lut_ready[64] = {};
-uint8_t g_lut4_h[64], g_lut5_h[1024];
+uint8_t g_lut4_h[64], g_lut5_h[1024], g_lutc_h[4096];
 bool g_lut_built = false;
 
 int ensure_luts(int device) {
@@ -137,11 +161,15 @@ int ensure_luts(int device) {
     if (!g_lut_built) {
         for (uint32_t m = 0; m < 64; ++m) g_lut4_h[m] = (uint8_t)mask_class(4, m);
         for (uint32_t m = 0; m < 1024; ++m) g_lut5_h[m] = (uint8_t)mask_class(5, m);
+        for (uint32_t i = 0; i < 4096; ++i) {   // counted classes only: 4-cycle, diamond, 4-clique
+            const int cls = g_lut4_h[i >> 6];
+            g_lutc_h[i] = (uint8_t)(cls == 3 || cls == 5 || cls == 6 ? centred_paths_of(i >> 6, i & 63u) : 0);
+        }
         g_lut_built = true;
     }
     if (device < 0 || device >= 64) return fail(MOSS_EINVAL, "device ordinal %d out of range", device);
     if (!g_lut_ready[device]) {
-        upload_luts(g_lut4_h, g_lut5_h);
+        upload_luts(g_lut4_h, g_lut5_h, g_lutc_h);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "uploading class tables");
         g_lut_ready[device] = true;
@@ -166,6 +194,7 @@ struct moss_graph {
     uint4 *seed[kMethods] = {nullptr, nullptr, nullptr, nullptr};
     uint4 *mvert = nullptr;      // MOSS-4Min tables, in min_arena
     uint4 *mslot = nullptr;
+    uint4 *mpick = nullptr;
     uint2 *rlist = nullptr;
     void *min_arena = nullptr;
     DevTotals *tot = nullptr;
@@ -231,6 +260,7 @@ DevGraph view(const moss_graph *g) {
     for (int l = 0; l < kMethods; ++l) d.seed[l] = g->seed[l];
     d.mvert = g->mvert;
     d.mslot = g->mslot;
+    d.mpick = g->mpick;
     d.rlist = g->rlist;
     d.defer = g->defer;
     d.n = g->n;
@@ -450,6 +480,7 @@ static int build_min_tables(moss_graph *g, cudaStream_t s) {
             }
             g->mvert = c.take<uint4>(g->n);
             g->mslot = c.take<uint4>(2 * g->nnz);
+            g->mpick = c.take<uint4>(2 * g->nnz);
             g->rlist = c.take<uint2>(g->nnz);
             g->gam[3] = c.take<u128>(g->n);
             g->seed[3] = c.take<uint4>(2 * (uint64_t)g->n);
@@ -458,7 +489,8 @@ static int build_min_tables(moss_graph *g, cudaStream_t s) {
     void *scratch = nullptr;
     if ((e = pool_alloc(g->device, &scratch, min_scratch_bytes(g->n, g->nnz), s)) != cudaSuccess)
         return cuda_fail(e, "allocating scratch");
-    e = launch_min_tables(g->n, g->nnz, g->vert, g->col, g->owner, g->slot, g->mvert, g->mslot, g->rlist, g->gam[3],
+    e = launch_min_tables(g->n, g->nnz, g->vert, g->col, g->owner, g->slot, g->mvert, g->mslot, g->mpick, g->rlist,
+                          g->gam[3],
                           g->seed[3], g->tot, scratch, g->flags, s);
     cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) return cuda_fail(e, "MOSS-4Min table kernels");
@@ -758,13 +790,14 @@ int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t b
         if (!(g->built >> 6 & 1u)) return fail(MOSS_ESTATE, "edge filter not built");
         src = g->filter;
         need = g->filter_words * 4;
-    } else if (table >= MOSS_TABLE_MIN_SEED && table <= MOSS_TABLE_MIN_LIST) {
+    } else if ((table >= MOSS_TABLE_MIN_SEED && table <= MOSS_TABLE_MIN_LIST) || table == MOSS_TABLE_MIN_PICK) {
         if (!(g->built >> 5 & 1u)) return fail(MOSS_ESTATE, "MOSS-4Min tables not built");
         switch (table) {
             case MOSS_TABLE_MIN_SEED: src = g->seed[3]; need = (uint64_t)g->n * 32; break;
             case MOSS_TABLE_MIN_GAMMA: src = g->gam[3]; need = (uint64_t)g->n * 16; break;
             case MOSS_TABLE_MIN_VERT: src = g->mvert; need = (uint64_t)g->n * 16; break;
             case MOSS_TABLE_MIN_SLOT: src = g->mslot; need = g->nnz * 32; break;
+            case MOSS_TABLE_MIN_PICK: src = g->mpick; need = g->nnz * 32; break;
             default: src = g->rlist; need = g->nnz * 8; break;
         }
     } else {

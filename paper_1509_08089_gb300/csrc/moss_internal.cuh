@@ -30,6 +30,12 @@
 //             sigma-check^(v) (eq. 3): keep the column when y < thr for y
 //             uniform in [0, Gamma-check_v), else take position alias --
 //             and {off_u, d_u, d_{v,u}, d_{u,v}}
+//   mpick[2 nnz] two uint4 per slot, one 32-byte sector, read instead of
+//             mslot by a draw from a list with Gamma-check_v < 2^32:
+//             {thr, u, off_u, d_{v,u} | d_{u,v} << 16} {alias's u, off_u,
+//             d_{v,u} | d_{u,v} << 16, d_u | alias's d_u << 16} -- the draw
+//             and both possible picks in one load; the last word is
+//             kSlotHub when a field does not fit 16 bits (mslot then serves)
 //   rlist[nnz] uint2 {x, d_x}: N_v ordered by the total order (degree, then
 //             id; Sec. 3.2), highest first, so N_{v,u} is its first d_{v,u}
 //             entries
@@ -81,6 +87,7 @@ struct DevGraph {
     const uint4 *seed[kMethods];
     const uint4 *mvert;     // MOSS-4Min tables (null until built)
     const uint4 *mslot;
+    const uint4 *mpick;
     const uint2 *rlist;
     const uint4 *hash;      // hashed edge set (4 keys per 32 B bucket), or null: probe by search
     const uint32_t *filter; // Bloom filter in front of the hash, or null
@@ -253,12 +260,13 @@ int slot_partial_rows(uint32_t n);   // rows of 6 u128 totals launch_slots write
 // the sigma-check alias tables, tot->gamma[3] and its vertex alias table)
 uint64_t min_scratch_bytes(uint32_t n, uint64_t nnz);
 cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const uint32_t *col,
-                              const uint32_t *owner, const uint4 *slot, uint4 *mvert, uint4 *mslot, uint2 *rlist,
-                              u128 *gmin, uint4 *seed_min, DevTotals *tot, void *scratch, uint32_t *flags,
-                              cudaStream_t s);
+                              const uint32_t *owner, const uint4 *slot, uint4 *mvert, uint4 *mslot, uint4 *mpick,
+                              uint2 *rlist, u128 *gmin, uint4 *seed_min, DevTotals *tot, void *scratch,
+                              uint32_t *flags, cudaStream_t s);
 
 // moss_sample.cu
-void upload_luts(const uint8_t *lut4, const uint8_t *lut5);
+// class of each 4- and 5-vertex edge mask; c(s) of MOSS-4Min by (mask << 6 | order bits)
+void upload_luts(const uint8_t *lut4, const uint8_t *lut5, const uint8_t *lutc);
 // Counts (22 uint64 at counts_dev) of samples [first, first+count) of one
 // method, with optional per-sample records (classes, verts: count and 5*count
 // entries); partials holds sample_rows(method) rows of 22 uint64.  Path-5 runs

@@ -411,6 +411,23 @@ struct MinScratch {
     uint64_t bytes;
 };
 
+// per slot p of a list with Gamma-check_v < 2^32: the pick record (layout in
+// moss_internal.cuh) from p's mslot record and its alias position's
+__global__ void k_min_pick(uint64_t nnz, const uint32_t *__restrict__ owner, const uint4 *__restrict__ mvert,
+                           const uint4 *__restrict__ mslot, uint4 *mpick) {
+    constexpr uint32_t kNarrow = 0xffffu;   // fields below this fit a half word
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 mv = mvert[owner[p]];
+        const uint4 a0 = mslot[2 * p], a1 = mslot[2 * p + 1];
+        const uint64_t ap = (uint64_t)mv.x + a0.z;
+        const uint4 b0 = mslot[2 * ap], b1 = mslot[2 * ap + 1];
+        const bool fits = mv.w == 0 && a1.y < kNarrow && a1.z < kNarrow && a1.w < kNarrow && b1.y < kNarrow &&
+                          b1.z < kNarrow && b1.w < kNarrow;
+        mpick[2 * p] = make_uint4(a0.x, a0.w, a1.x, a1.z | a1.w << 16);
+        mpick[2 * p + 1] = make_uint4(b0.w, b1.x, b1.z | b1.w << 16, fits ? (a1.y | b1.y << 16) : kSlotHub);
+    }
+}
+
 MinScratch carve(void *base, uint32_t n, uint64_t nnz) {
     MinScratch m{};
     uint8_t *p = static_cast<uint8_t *>(base);
@@ -436,10 +453,9 @@ MinScratch carve(void *base, uint32_t n, uint64_t nnz) {
 uint64_t min_scratch_bytes(uint32_t n, uint64_t nnz) { return carve(nullptr, n, nnz).bytes; }
 
 cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const uint32_t *col,
-                              const uint32_t *owner, const uint4 *slot, uint4 *mvert, uint4 *mslot, uint2 *rlist,
-                              u128 *gmin, uint4 *seed_min, DevTotals *tot, void *scratch, uint32_t *flags,
-                              cudaStream_t s) {
-    (void)owner;
+                              const uint32_t *owner, const uint4 *slot, uint4 *mvert, uint4 *mslot, uint4 *mpick,
+                              uint2 *rlist, u128 *gmin, uint4 *seed_min, DevTotals *tot, void *scratch,
+                              uint32_t *flags, cudaStream_t s) {
     const MinScratch m = carve(scratch, n, nnz);
     cudaError_t e;
     if (nnz) {
@@ -462,6 +478,10 @@ cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const
     k_min_alias_long<<<grid_for((uint64_t)n, kListThreads, 4), kListThreads, 0, s>>>(n, vert, mvert, mslot, m.rank,
                                                                           reinterpret_cast<u128 *>(m.a));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (nnz) {
+        k_min_pick<<<grid_for(nnz, 256, 16), 256, 0, s>>>(nnz, owner, mvert, mslot, mpick);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     k_min_total<<<1, kWarp, 0, s>>>(m.partials, (int)ab, tot);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int which[1] = {3};

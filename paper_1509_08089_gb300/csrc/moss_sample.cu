@@ -39,6 +39,7 @@ constexpr int kLut = 1024;
 
 __device__ uint8_t g_lut4[64];
 __device__ uint8_t g_lut5[1024];
+__device__ uint8_t g_lutc[4096];   // c(s) of MOSS-4Min by (edge mask << 6 | order bits)
 
 __device__ __forceinline__ uint4 ld4(const uint4 *p) { return __ldg(p); }
 __device__ __forceinline__ uint2 ld2(const uint2 *p) { return __ldg(p); }
@@ -283,33 +284,13 @@ __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lu
 }
 
 // ------------------------------------------------------------- MOSS-4Min --
-// Bit of the pair (a, b) in the order (0,1),(0,2),(0,3),(1,2),(1,3),(2,3).
-__device__ __forceinline__ constexpr int pair_bit4(int a, int b) {
-    return a > b ? pair_bit4(b, a) : (a == 0 ? b - 1 : (a == 1 ? b + 1 : 5));
-}
 
-// c(s): 3-paths p0-p1-p2-p3 of the CIS with p0 above p2 and p3 above p1 in the
-// total order.  mask holds the CIS's edges over the roles 0..3, key[] the
-// order keys (d_x << 32) | x; each unordered path is visited once, as the
-// vertex order whose end roles satisfy p0 < p3.
-__device__ __forceinline__ uint32_t centred_paths(uint32_t mask, const uint64_t (&key)[4]) {
-    uint32_t c = 0;
-#pragma unroll
-    for (int e0 = 0; e0 < 4; ++e0) {
-#pragma unroll
-        for (int e3 = e0 + 1; e3 < 4; ++e3) {
-            const int m0 = (e0 != 0 && e3 != 0) ? 0 : ((e0 != 1 && e3 != 1) ? 1 : 2);
-            const int m1 = 6 - e0 - e3 - m0;
-#pragma unroll
-            for (int o = 0; o < 2; ++o) {
-                const int p1 = o ? m1 : m0, p2 = o ? m0 : m1;
-                const bool path = (mask >> pair_bit4(e0, p1) & 1u) && (mask >> pair_bit4(p1, p2) & 1u) &&
-                                  (mask >> pair_bit4(p2, e3) & 1u);
-                c += path && key[e0] > key[p2] && key[e3] > key[p1];
-            }
-        }
-    }
-    return c;
+// order bits of the four roles for the c(s) table: bit b set when the first
+// role of pair b ((0,1),(0,2),(0,3),(1,2),(1,3),(2,3)) is above the second;
+// key[] holds the order keys (d_x << 32) | x
+__device__ __forceinline__ uint32_t order_bits(const uint64_t (&key)[4]) {
+    return (uint32_t)(key[0] > key[1]) | (uint32_t)(key[0] > key[2]) << 1 | (uint32_t)(key[0] > key[3]) << 2 |
+           (uint32_t)(key[1] > key[2]) << 3 | (uint32_t)(key[1] > key[3]) << 4 | (uint32_t)(key[2] > key[3]) << 5;
 }
 
 // count slot of a MOSS-4Min hit: 4-cycles 0..3, diamonds 4..9, 4-cliques
@@ -322,7 +303,8 @@ __device__ __forceinline__ int min_slot(int cls, uint32_t c) {
 }
 
 template <bool HASH>
-__device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
+__device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *lut, const uint8_t *lutc, uint64_t seed,
+                                             uint64_t s) {
     Sample out;
     const Words4 a = philox4x64(s, 0, 3, 0, seed, 0);
     const Words4 b = philox4x64(s, 1, 3, 0, seed, 0);
@@ -330,14 +312,29 @@ __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *l
     const uint32_t v = pv.v;
     const uint4 mv = pv.rec;                           // {off, d_v, Gamma-check_v}
     const uint64_t Gv = ((uint64_t)mv.w << 32) | mv.z;
-    // WeightRandomVertex(N_v, sigma-check^(v)): 32-byte slot records, each
-    // read whole in one load
+    // WeightRandomVertex(N_v, sigma-check^(v)): from a list with
+    // Gamma-check_v < 2^32, one pick record carries the draw and both
+    // possible picks; otherwise (or when a field overflows 16 bits) the slot
+    // record, and the alias position's when the column does not keep the draw
     const uint32_t j = (uint32_t)word_index(a.x[2], mv.y);
-    Sector ms = ld8(g.mslot + 2 * (uint64_t)(mv.x + j));
     const uint64_t y = word_index(a.x[3], Gv);
-    if (!(y < (((uint64_t)ms.lo.y << 32) | ms.lo.x))) ms = ld8(g.mslot + 2 * (uint64_t)(mv.x + ms.lo.z));
-    const uint4 sb = ms.hi;   // {off_u, d_u, d_{v,u}, d_{u,v}}
-    const uint32_t u = ms.lo.w;
+    uint4 sb;   // {off_u, d_u, d_{v,u}, d_{u,v}}
+    uint32_t u;
+    Sector pk;
+    pk.hi.w = kSlotHub;
+    if (mv.w == 0) pk = ld8(g.mpick + 2 * (uint64_t)(mv.x + j));
+    if (pk.hi.w != kSlotHub) {
+        const bool keep = y < pk.lo.x;
+        const uint32_t dd = keep ? pk.lo.w : pk.hi.z;
+        u = keep ? pk.lo.y : pk.hi.x;
+        sb = make_uint4(keep ? pk.lo.z : pk.hi.y, keep ? (pk.hi.w & 0xffffu) : (pk.hi.w >> 16), dd & 0xffffu,
+                        dd >> 16);
+    } else {
+        Sector ms = ld8(g.mslot + 2 * (uint64_t)(mv.x + j));
+        if (!(y < (((uint64_t)ms.lo.y << 32) | ms.lo.x))) ms = ld8(g.mslot + 2 * (uint64_t)(mv.x + ms.lo.z));
+        sb = ms.hi;
+        u = ms.lo.w;
+    }
     const uint2 we = ld2(g.rlist + mv.x + (uint32_t)word_index(b.x[0], sb.z));   // w in N_{v,u}
     const uint2 re = ld2(g.rlist + sb.x + (uint32_t)word_index(b.x[1], sb.w));   // r in N_{u,v}
     const uint32_t w = we.x, r = re.x;
@@ -360,11 +357,10 @@ __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *l
     // known: v-u, v-w, u-r
     const uint32_t mask = 0x1u | 0x2u | ((f & 1u) << 2) | (((f >> 1) & 1u) << 3) | 0x10u | (((f >> 2) & 1u) << 5);
     out.cls = lut[mask];
-    if (out.cls == 3 || out.cls == 5 || out.cls == 6) {
-        const uint64_t key[4] = {((uint64_t)mv.y << 32) | v, ((uint64_t)sb.y << 32) | u, ((uint64_t)we.y << 32) | w,
-                                 ((uint64_t)re.y << 32) | r};
-        out.v[4] = centred_paths(mask, key);
-    }
+    // c(s) from the table (zero for the classes MOSS-4Min does not count)
+    const uint64_t key[4] = {((uint64_t)mv.y << 32) | v, ((uint64_t)sb.y << 32) | u, ((uint64_t)we.y << 32) | w,
+                             ((uint64_t)re.y << 32) | r};
+    out.v[4] = lutc[mask << 6 | order_bits(key)];
     return out;
 }
 
@@ -497,11 +493,14 @@ template <int METHOD, bool RECORD, bool HASH>
 __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGraph g, uint64_t first, uint64_t count, uint64_t seed,
                                                      uint64_t *partials, uint8_t *classes, uint32_t *verts) {
     __shared__ uint8_t lut[kLut];
+    __shared__ uint8_t lutc[METHOD == 3 ? 4096 : 1];
     __shared__ uint32_t hist[kWarps][kSlots];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint8_t *src = (METHOD == 0 || METHOD == 3) ? g_lut4 : g_lut5;
     const int lut_n = (METHOD == 0 || METHOD == 3) ? 64 : 1024;
     for (int i = threadIdx.x; i < lut_n; i += kThreads) lut[i] = src[i];
+    if (METHOD == 3)
+        for (int i = threadIdx.x; i < 4096; i += kThreads) lutc[i] = g_lutc[i];
     for (int i = threadIdx.x; i < kWarps * kSlots; i += kThreads) (&hist[0][0])[i] = 0;
     __syncthreads();
     const uint64_t stride = (uint64_t)gridDim.x * kThreads;
@@ -517,7 +516,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGr
             if (METHOD == 0) sm = sample_moss4<HASH>(g, lut, seed, s);
             else if (METHOD == 1) sm = sample_t5<HASH>(g, lut, seed, s);
             else if (METHOD == 2) sm = sample_path5<HASH, 0>(g, lut, seed, s);
-            else sm = sample_min<HASH>(g, lut, seed, s);
+            else sm = sample_min<HASH>(g, lut, lutc, seed, s);
             deferred = METHOD == 2 && sm.cls == kDeferred;
             if (!deferred) {
                 cls = METHOD == 3 ? min_slot(sm.cls, sm.v[4]) : sm.cls;
@@ -761,9 +760,10 @@ cudaError_t launch_one(const DevGraph &g, uint64_t first, uint64_t count, uint64
 
 }  // namespace
 
-void upload_luts(const uint8_t *lut4, const uint8_t *lut5) {
+void upload_luts(const uint8_t *lut4, const uint8_t *lut5, const uint8_t *lutc) {
     cudaMemcpyToSymbol(g_lut4, lut4, 64);
     cudaMemcpyToSymbol(g_lut5, lut5, 1024);
+    cudaMemcpyToSymbol(g_lutc, lutc, 4096);
 }
 
 int sample_blocks(int method, int device) {

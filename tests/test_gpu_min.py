@@ -33,6 +33,17 @@ def hub_graph():
     return synth.from_edges(n, [(0, i) for i in range(1, n)] + list(zip(a.tolist(), b.tolist())))
 
 
+def two_hubs():
+    """Two adjacent hubs, each joined to the same 100,000 leaves, plus 50,000
+    random leaf edges: the second hub's Gamma-check exceeds 2^32 and the hubs'
+    degrees exceed 2^16, so the sampler takes its two-record path there."""
+    rng = np.random.default_rng(8)
+    leaves = 100_000
+    edges = [(0, 1)] + [(h, i) for h in (0, 1) for i in range(2, leaves + 2)]
+    edges += zip(rng.integers(2, leaves + 2, 50_000).tolist(), rng.integers(2, leaves + 2, 50_000).tolist())
+    return synth.from_edges(leaves + 2, edges)
+
+
 def decorated_diamond():
     return synth.from_edges(8, [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 4), (2, 5), (3, 6), (3, 7)])
 
@@ -44,6 +55,7 @@ GRAPHS = {
     "rgg2k": lambda: synth.rgg(2000, 12.0, seed=3),
     "cl_n2k": lambda: synth.workload("cl_n2k"),
     "hub12k": hub_graph,
+    "twohub100k": two_hubs,
     "cl_n100k": lambda: synth.workload("cl_n100k"),
 }
 
@@ -121,6 +133,26 @@ def test_min_tables_bit_exact(name):
     assert np.array_equal(seed[:, 4:8], mv[alias.astype(np.int64)])
     st = g.stats()
     assert (int(st.gamma[3][0]) | (int(st.gamma[3][1]) << 64)) == og.Gamma_min
+    # pick records: the draw and both possible picks, from the oracle's tables
+    pk = moss.moss_table_export(g.handle, moss.TABLE_MIN_PICK, np.zeros((nnz, 8), dtype=np.uint32))
+    owner = np.repeat(np.arange(n, dtype=np.int64), deg)
+    apos = rp.astype(np.int64)[owner] + calias.astype(np.int64)
+    duv = rk[twin_pos].astype(np.int64)
+    du = deg[c64]
+    narrow = np.array([int(gam[v]) < (1 << 32) for v in range(n)], dtype=bool)[owner]
+    small = (du < 0xFFFF) & (rk.astype(np.int64) < 0xFFFF) & (duv < 0xFFFF)
+    fits = narrow & small & small[apos]
+    expect = np.where(fits, du | (du[apos] << 16), 0xFFFFFFFF).astype(np.uint32)
+    assert np.array_equal(pk[:, 7], expect)
+    f = fits
+    assert np.array_equal(pk[f, 0].astype(np.uint64), cthr[f])
+    assert np.array_equal(pk[f, 1], col[f])
+    assert np.array_equal(pk[f, 2].astype(np.int64), rp.astype(np.int64)[c64][f])
+    dd = (rk.astype(np.int64) | (duv << 16)).astype(np.uint32)
+    assert np.array_equal(pk[f, 3], dd[f])
+    assert np.array_equal(pk[f, 4], col[apos][f])
+    assert np.array_equal(pk[f, 5].astype(np.int64), rp.astype(np.int64)[c64][apos][f])
+    assert np.array_equal(pk[f, 6], dd[apos][f])
 
 
 @pytest.mark.parametrize("name", list(GRAPHS))
