@@ -40,172 +40,6 @@ __device__ __forceinline__ double u128_to_double(u128 x) {
     return (double)(uint64_t)(x >> 64) * 18446744073709551616.0 + (double)(uint64_t)x;
 }
 
-// omega_i = eta_i / sum_j eta_j over the classes (Sec. 6.3)
-__device__ void concentrations(moss_result &r) {
-    double t = 0.0;
-    for (int i = 1; i <= r.n_classes; ++i) t += r.est[i];
-    for (int i = 0; i < kSlots; ++i) r.conc[i] = 0.0;
-    if (t != 0.0)
-        for (int i = 1; i <= r.n_classes; ++i) r.conc[i] = r.est[i] / t;
-}
-
-// hits0/hits1: counts of the first and second sub-method (hits1 may be null);
-// cov (nullable, 22 x 22 row-major) receives the covariance matrix
-__device__ void finalize_one(const FinalizeIn &in, const uint64_t *hits0, const uint64_t *hits1,
-                             const DevTotals *tot, moss_result *out, double *cov = nullptr) {
-    moss_result r;
-    memset(&r, 0, sizeof(r));
-    r.k = in.k;
-    r.K[0] = in.K[0];
-    r.K[1] = in.K[1];
-    for (int i = 0; i < kSlots; ++i) {
-        r.hits[0][i] = hits0 ? hits0[i] : 0;
-        r.hits[1][i] = hits1 ? hits1[i] : 0;
-    }
-    if (in.k == 4) {
-        r.n_classes = 6;
-        const double G = u128_to_double(tot->gamma[0]);
-        const double K = (double)in.K[0];
-        double p[7] = {0, 0, 0, 0, 0, 0, 0};
-        if (in.K[0] > 0 && G > 0) {
-            for (int i = 1; i <= 6; ++i) {
-                if (i == 2) continue;
-                p[i] = 2.0 * kPhi4[i - 1][0] / G;
-                r.est[i] = (double)r.hits[0][i] / (K * p[i]);
-            }
-            for (int i = 1; i <= 6; ++i) {
-                if (i == 2) continue;
-                r.var[i] = r.est[i] / K * (1.0 / p[i] - r.est[i]);
-            }
-            const double s = r.est[4] + 2.0 * r.est[5] + 4.0 * r.est[6];
-            r.var[2] = (r.est[4] / p[4] + 4.0 * r.est[5] / p[5] + 16.0 * r.est[6] / p[6] - s * s) / K;
-            r.triangles = (double)r.hits[0][0] * G / (6.0 * K);
-            r.triangles_var = r.triangles / K * (G / 6.0 - r.triangles);
-        }
-        r.est[2] = u128_to_double(tot->lambda3) - r.est[4] - 2.0 * r.est[5] - 4.0 * r.est[6];
-        concentrations(r);
-        if (cov) {
-            // Cov(n_i, n_j) = -n_i n_j / K (proof of Theorem 3); n_2 is linear in n_4, n_5, n_6
-            for (int i = 0; i < kSlots * kSlots; ++i) cov[i] = 0.0;
-            if (in.K[0] > 0 && G > 0) {
-                const int sm[5] = {1, 3, 4, 5, 6};
-                for (int a = 0; a < 5; ++a)
-                    for (int b = 0; b < 5; ++b) {
-                        const int i = sm[a], j = sm[b];
-                        cov[i * kSlots + j] = i == j ? r.var[i] : -r.est[i] * r.est[j] / K;
-                    }
-                for (int j = 1; j <= 6; ++j) {
-                    if (j == 2) continue;
-                    const double c = -(cov[4 * kSlots + j] + 2.0 * cov[5 * kSlots + j] + 4.0 * cov[6 * kSlots + j]);
-                    cov[2 * kSlots + j] = c;
-                    cov[j * kSlots + 2] = c;
-                }
-                cov[2 * kSlots + 2] = r.var[2];
-            }
-        }
-        *out = r;
-        return;
-    }
-    r.n_classes = 21;
-    const double G[2] = {u128_to_double(tot->gamma[1]), u128_to_double(tot->gamma[2])};
-    const double K[2] = {(double)in.K[0], (double)in.K[1]};
-    const bool avail[2] = {in.K[0] > 0 && G[0] > 0, in.K[1] > 0 && G[1] > 0};
-    double p[2][kSlots], eh[2][kSlots], plug[kSlots], a[2][kSlots];
-    for (int l = 0; l < 2; ++l)
-        for (int i = 0; i < kSlots; ++i) { p[l][i] = 0; eh[l][i] = 0; a[l][i] = 0; }
-    for (int i = 0; i < kSlots; ++i) plug[i] = 0;
-    for (int l = 0; l < 2; ++l) {
-        if (!avail[l]) continue;
-        for (int i = 1; i <= 21; ++i) {
-            if (kPhi5[i - 1][l] > 0) {
-                p[l][i] = 2.0 * kPhi5[i - 1][l] / G[l];
-                eh[l][i] = (double)r.hits[l][i] / (K[l] * p[l][i]);
-            }
-        }
-    }
-    for (int i = 1; i <= 21; ++i) {
-        if (i == 2) continue;
-        const bool s0 = avail[0] && kPhi5[i - 1][0] > 0, s1 = avail[1] && kPhi5[i - 1][1] > 0;
-        if (!s0 && !s1) continue;
-        if (s0 != s1) {
-            const int l = s0 ? 0 : 1;
-            const double e = eh[l][i];
-            plug[i] = e;
-            r.est[i] = e;
-            r.var[i] = e / K[l] * (1.0 / p[l][i] - e);
-            a[l][i] = 1.0;
-            continue;
-        }
-        const double e = ((double)r.hits[0][i] + (double)r.hits[1][i]) / (K[0] * p[0][i] + K[1] * p[1][i]);
-        plug[i] = e;
-        const double V1 = fmax(e / K[0] * (1.0 / p[0][i] - e), 0.0);
-        const double V2 = fmax(e / K[1] * (1.0 / p[1][i] - e), 0.0);
-        if (V1 + V2 > 0.0) {
-            a[0][i] = V2 / (V1 + V2);
-            a[1][i] = V1 / (V1 + V2);
-            r.var[i] = V1 * V2 / (V1 + V2);
-        } else {
-            a[0][i] = a[1][i] = 0.5;
-            r.var[i] = 0.0;
-        }
-        r.est[i] = a[0][i] * eh[0][i] + a[1][i] * eh[1][i];
-    }
-    for (int l = 0; l < 2; ++l)
-        for (int i = 0; i < kSlots; ++i) r.lambda[l][i] = a[l][i];
-    // eta_2 from the Lambda_4 identity and its variance (Theorem 10)
-    double s = 0.0;
-    for (int i = 1; i <= 21; ++i)
-        if (i != 2 && kPhi5[i - 1][2] > 0) s += kPhi5[i - 1][2] * r.est[i];
-    r.est[2] = u128_to_double(tot->lambda4) - s;
-    double v2 = 0.0;
-    for (int i = 1; i <= 21; ++i)
-        if (i != 2 && kPhi5[i - 1][2] > 0) v2 += kPhi5[i - 1][2] * kPhi5[i - 1][2] * r.var[i];
-    // sum_{i != j} phi_i phi_j Cov(i, j) with Cov = -sum_l b_i b_j / K_l,
-    // b_i = phi_i a^(l)_i plug_i: the pair sum is (sum b)^2 - sum b^2 per l
-    for (int l = 0; l < 2; ++l) {
-        if (!avail[l]) continue;
-        double sb = 0.0, sbb = 0.0;
-        for (int i = 1; i <= 21; ++i) {
-            if (i == 2 || kPhi5[i - 1][2] == 0) continue;
-            const double b = kPhi5[i - 1][2] * (a[l][i] * plug[i]);
-            sb += b;
-            sbb += b * b;
-        }
-        v2 -= (sb * sb - sbb) / K[l];
-    }
-    r.var[2] = v2;
-    concentrations(r);
-    if (cov) {
-        // Cov(eta_i, eta_j) = -plug_i plug_j sum_l a_i a_j / K_l (Theorem 10);
-        // eta_2 = Lambda_4 - sum phi^(3)_i eta_i is linear in the others
-        for (int i = 0; i < kSlots * kSlots; ++i) cov[i] = 0.0;
-        for (int i = 1; i <= 21; ++i) {
-            if (i == 2) continue;
-            for (int j = 1; j <= 21; ++j) {
-                if (j == 2) continue;
-                double c = 0.0;
-                if (i == j) {
-                    c = r.var[i];
-                } else {
-                    for (int l = 0; l < 2; ++l)
-                        if (avail[l]) c -= (a[l][i] * plug[i]) * (a[l][j] * plug[j]) / K[l];
-                }
-                cov[i * kSlots + j] = c;
-            }
-        }
-        for (int j = 1; j <= 21; ++j) {
-            if (j == 2) continue;
-            double c2 = 0.0;
-            for (int i = 1; i <= 21; ++i)
-                if (i != 2 && kPhi5[i - 1][2] > 0) c2 -= kPhi5[i - 1][2] * cov[i * kSlots + j];
-            cov[2 * kSlots + j] = c2;
-            cov[j * kSlots + 2] = c2;
-        }
-        cov[2 * kSlots + 2] = r.var[2];
-    }
-    *out = r;
-}
-
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
@@ -213,9 +47,9 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 // MOSS-5 with one warp: lane i is class i (1..21); the sums over classes
-// (the eta_2 identity, its variance, the concentrations) are warp sums.  Same
-// arithmetic as the k = 5 branch of finalize_one, which it replaces on the
-// launch paths; only the order of those sums differs.
+// (the eta_2 identity, its variance, the concentrations) are warp sums.
+// hits0/hits1: counts of the two sub-methods (either may be null); cov
+// (nullable, 22 x 22 row-major) receives the covariance matrix.
 __device__ void finalize5_warp(const FinalizeIn &in, const uint64_t *hits0, const uint64_t *hits1,
                                const DevTotals *tot, moss_result *out, double *cov) {
     const int i = threadIdx.x & 31;
@@ -325,133 +159,160 @@ __device__ void finalize5_warp(const FinalizeIn &in, const uint64_t *hits0, cons
     }
 }
 
-// MOSS-4 (hits0, K[0]) mixed with MOSS-4Min (hits1 = (class, c) slots, K[1])
-__device__ void finalize_mix(const FinalizeIn &in, const uint64_t *hits0, const uint64_t *hits1, const DevTotals *tot,
-                             moss_result *out, double *cov) {
-    moss_result r;
-    memset(&r, 0, sizeof(r));
-    r.k = 4;
-    r.n_classes = 6;
-    for (int i = 0; i < kSlots; ++i) {
-        r.hits[0][i] = hits0 ? hits0[i] : 0;
-        r.hits[1][i] = hits1 ? hits1[i] : 0;
-    }
-    const double G = u128_to_double(tot->gamma[0]), Gm = u128_to_double(tot->gamma[3]);
+// k = 4, alone (MOSS-4) or mixed with MOSS-4Min, with one warp: lane i is
+// class i (1..6); the eta_2 identity, its variance and the covariances are
+// formed on every lane from the values of classes 4, 5, 6 gathered by
+// shuffles, in the order the formulas are written; the concentrations' sum
+// is a warp sum.
+__device__ void finalize4_warp(const FinalizeIn &in, const uint64_t *hits0, const uint64_t *hits1,
+                               const DevTotals *tot, moss_result *out, double *cov) {
+    const int i = threadIdx.x & 31;
+    const bool cls = i >= 1 && i <= 6, mix = in.mix != 0;
+    const double G = u128_to_double(tot->gamma[0]), Gm = mix ? u128_to_double(tot->gamma[3]) : 0.0;
     const double K = (double)in.K[0], Km = (double)in.K[1];
-    const bool avail0 = in.K[0] > 0 && G > 0, avail1 = in.K[1] > 0 && Gm > 0;
-    r.K[0] = avail0 ? in.K[0] : 0;
-    r.K[1] = avail1 ? in.K[1] : 0;
-    const int first[7] = {0, 0, 0, 0, 0, 4, 10}, nslot[7] = {0, 0, 0, 4, 0, 6, 12};
-    const double thm4_inv_c[7] = {0, 0, 0, 1.0, 0, 1.0, 1.0 / 3.0};
-    double p[7], e4[7], em[7], h[7], plug[7], a[2][7];
-    for (int i = 0; i < 7; ++i) { p[i] = e4[i] = em[i] = h[i] = plug[i] = a[0][i] = a[1][i] = 0.0; }
-    if (avail0) {
-        for (int i = 1; i <= 6; ++i) {
-            if (i == 2) continue;
-            p[i] = 2.0 * kPhi4[i - 1][0] / G;                  // Theorem 2
-            e4[i] = (double)r.hits[0][i] / (K * p[i]);
-        }
+    const bool av0 = in.K[0] > 0 && G > 0, av1 = mix && in.K[1] > 0 && Gm > 0;
+    const uint64_t h0 = (i < kSlots && hits0) ? hits0[i] : 0, h1 = (i < kSlots && hits1) ? hits1[i] : 0;
+    const bool s0 = av0 && cls && i != 2;
+    double p = 0.0, e4 = 0.0;
+    if (s0) {
+        p = 2.0 * kPhi4[i - 1][0] / G;                    // Theorem 2
+        e4 = (double)h0 / (K * p);
     }
-    if (avail1) {
-        for (int i = 3; i <= 6; ++i) {
-            if (nslot[i] == 0) continue;
-            double sa = 0.0, sb = 0.0;
-            for (int c = 1; c <= nslot[i]; ++c) {
-                const double m = (double)r.hits[1][first[i] + c - 1];
-                sa += m / c;
-                sb += m / (c * c);
-            }
-            em[i] = Gm / (2.0 * Km) * sa;
-            h[i] = sa > 0 ? sb / sa : thm4_inv_c[i];
+    // MOSS-4Min: classes 3, 5, 6 from their (class, c) slots (Theorems 4, 5)
+    const int first = i == 3 ? 0 : (i == 5 ? 4 : 10), nslot = i == 3 ? 4 : (i == 5 ? 6 : (i == 6 ? 12 : 0));
+    const bool s1 = av1 && nslot > 0;
+    double em = 0.0, h = 0.0;
+    if (s1) {
+        double sa = 0.0, sb = 0.0;
+        for (int c = 1; c <= nslot; ++c) {
+            const double m = (double)hits1[first + c - 1];
+            sa += m / c;
+            sb += m / (c * c);
         }
+        em = Gm / (2.0 * Km) * sa;
+        h = sa > 0 ? sb / sa : (i == 6 ? 1.0 / 3.0 : 1.0);
     }
-    for (int i = 1; i <= 6; ++i) {
-        if (i == 2) continue;
-        const bool s0 = avail0, s1 = avail1 && nslot[i] > 0;
-        if (!s0 && !s1) continue;
-        if (s0 != s1) {
-            if (s0) {
-                const double e = e4[i];
-                plug[i] = e;
-                r.var[i] = e / K * (1.0 / p[i] - e);           // Theorem 3
-                r.est[i] = e;
-                a[0][i] = 1.0;
-            } else {
-                const double e = em[i];
-                plug[i] = e;
-                r.var[i] = (e * Gm * h[i] / 2.0 - e * e) / Km;  // Theorem 5, per-CIS probabilities
-                r.est[i] = e;
-                a[1][i] = 1.0;
-            }
-            continue;
-        }
-        const double e = (K * e4[i] + Km * em[i]) / (K + Km);
-        plug[i] = e;
-        const double V1 = fmax(e / K * (1.0 / p[i] - e), 0.0);
-        const double V2 = fmax((e * Gm * h[i] / 2.0 - e * e) / Km, 0.0);
-        if (V1 + V2 > 0.0) {
-            a[0][i] = V2 / (V1 + V2);
-            a[1][i] = V1 / (V1 + V2);
-            r.var[i] = V1 * V2 / (V1 + V2);                      // Theorem 1
+    double est = 0.0, var = 0.0, plug = 0.0, a0 = 0.0, a1 = 0.0;
+    if (s0 != s1) {
+        if (s0) {
+            plug = est = e4;
+            var = e4 / K * (1.0 / p - e4);                 // Theorem 3
+            a0 = 1.0;
         } else {
-            a[0][i] = a[1][i] = 0.5;
-            r.var[i] = 0.0;
+            plug = est = em;
+            var = (em * Gm * h / 2.0 - em * em) / Km;      // Theorem 5, per-CIS probabilities
+            a1 = 1.0;
         }
-        r.est[i] = a[0][i] * e4[i] + a[1][i] * em[i];
-    }
-    for (int i = 0; i < 7; ++i) {
-        r.lambda[0][i] = a[0][i];
-        r.lambda[1][i] = a[1][i];
-    }
-    // Cov(i, j) = -plug_i plug_j sum_l a_i a_j / K_l for i != j (a sample lands in one class)
-    double cv[7][7];
-    for (int i = 0; i < 7; ++i)
-        for (int j = 0; j < 7; ++j) {
-            double c = 0.0;
-            if (i == j) {
-                c = r.var[i];
-            } else {
-                if (avail0) c -= (a[0][i] * plug[i]) * (a[0][j] * plug[j]) / K;
-                if (avail1) c -= (a[1][i] * plug[i]) * (a[1][j] * plug[j]) / Km;
-            }
-            cv[i][j] = c;
+    } else if (s0) {
+        const double e = (K * e4 + Km * em) / (K + Km);
+        plug = e;
+        const double V1 = fmax(e / K * (1.0 / p - e), 0.0);
+        const double V2 = fmax((e * Gm * h / 2.0 - e * e) / Km, 0.0);
+        if (V1 + V2 > 0.0) {
+            a0 = V2 / (V1 + V2);
+            a1 = V1 / (V1 + V2);
+            var = V1 * V2 / (V1 + V2);                     // Theorem 1
+        } else {
+            a0 = a1 = 0.5;
+            var = 0.0;
         }
+        est = a0 * e4 + a1 * em;
+    }
+    // classes 4, 5, 6 on every lane: n_2 = Lambda_3 - n_4 - 2 n_5 - 4 n_6 (eq. 2)
+    double E[7], Vv[7], P[7], B0[7], B1[7];
+    for (int c = 4; c <= 6; ++c) {
+        E[c] = __shfl_sync(0xffffffffu, est, c);
+        Vv[c] = __shfl_sync(0xffffffffu, var, c);
+        P[c] = __shfl_sync(0xffffffffu, p, c);
+        B0[c] = __shfl_sync(0xffffffffu, a0 * plug, c);
+        B1[c] = __shfl_sync(0xffffffffu, a1 * plug, c);
+    }
+    const double est2 = u128_to_double(tot->lambda3) - E[4] - 2.0 * E[5] - 4.0 * E[6];
     const double coef[7] = {0, 0, 0, 0, 1.0, 2.0, 4.0};
-    r.est[2] = u128_to_double(tot->lambda3) - r.est[4] - 2.0 * r.est[5] - 4.0 * r.est[6];   // eq. (2)
     double v2 = 0.0;
-    for (int i = 4; i <= 6; ++i)
-        for (int j = 4; j <= 6; ++j) v2 += coef[i] * coef[j] * cv[i][j];
-    for (int j = 1; j <= 6; ++j) {
-        if (j == 2) continue;
-        double c2 = 0.0;
-        for (int i = 4; i <= 6; ++i) c2 -= coef[i] * cv[i][j];
-        cv[2][j] = cv[j][2] = c2;
+    if (!mix) {
+        if (av0) {
+            const double s = E[4] + 2.0 * E[5] + 4.0 * E[6];
+            v2 = (E[4] / P[4] + 4.0 * E[5] / P[5] + 16.0 * E[6] / P[6] - s * s) / K;
+        }
+    } else if (av0 || av1) {
+        for (int r = 4; r <= 6; ++r)
+            for (int c = 4; c <= 6; ++c) {
+                double cv = Vv[r];
+                if (r != c) {
+                    cv = 0.0;
+                    if (av0) cv -= B0[r] * B0[c] / K;
+                    if (av1) cv -= B1[r] * B1[c] / Km;
+                }
+                v2 += coef[r] * coef[c] * cv;
+            }
     }
-    r.var[2] = (avail0 || avail1) ? v2 : 0.0;
-    cv[2][2] = r.var[2];
-    if (avail0) {
-        r.triangles = (double)r.hits[0][0] * G / (6.0 * K);
-        r.triangles_var = r.triangles / K * (G / 6.0 - r.triangles);
+    if (i == 2) {
+        est = est2;
+        var = v2;
     }
-    concentrations(r);
+    const double t = warp_sum_d(cls ? est : 0.0);          // concentrations (Sec. 6.3)
+    if (i < kSlots) {
+        out->hits[0][i] = h0;
+        out->hits[1][i] = h1;
+        out->est[i] = est;
+        out->var[i] = var;
+        out->lambda[0][i] = mix ? a0 : 0.0;
+        out->lambda[1][i] = mix ? a1 : 0.0;
+        out->conc[i] = (cls && t != 0.0) ? est / t : 0.0;
+    }
+    if (i == 0) {
+        out->k = 4;
+        out->n_classes = 6;
+        out->K[0] = mix ? (av0 ? in.K[0] : 0) : in.K[0];
+        out->K[1] = mix ? (av1 ? in.K[1] : 0) : in.K[1];
+        out->triangles = av0 ? (double)h0 * G / (6.0 * K) : 0.0;
+        out->triangles_var = av0 ? out->triangles / K * (G / 6.0 - out->triangles) : 0.0;
+    }
     if (cov) {
-        for (int i = 0; i < kSlots * kSlots; ++i) cov[i] = 0.0;
-        for (int i = 1; i <= 6; ++i)
-            for (int j = 1; j <= 6; ++j) cov[i * kSlots + j] = cv[i][j];
+        // lane j fills column j: Cov(n_i, n_j) = -sum_l b_i b_j / K_l off the
+        // diagonal (b = a^(l) plug; -n_i n_j / K for MOSS-4 alone), row and
+        // column 2 from the linear identity
+        for (int r = 0; r < kSlots; ++r)
+            if (i < kSlots) cov[r * kSlots + i] = 0.0;
+        __syncwarp();
+        const bool colj = cls && i != 2 && (mix || av0);
+        const double b0 = mix ? a0 * plug : est, b1 = a1 * plug;
+        double c2 = 0.0;
+        for (int r = 1; r <= 6; ++r) {
+            const double b0r = __shfl_sync(0xffffffffu, b0, r), b1r = __shfl_sync(0xffffffffu, b1, r);
+            if (r == 2 || !colj) continue;
+            double c = 0.0;
+            if (r == i) {
+                c = var;
+            } else if (mix) {
+                if (av0) c -= b0r * b0 / K;
+                if (av1) c -= b1r * b1 / Km;
+            } else {
+                c = -b0r * b0 / K;
+            }
+            cov[r * kSlots + i] = c;
+            if (r >= 4) {
+                if (mix) c2 -= coef[r] * c;
+                else c2 += coef[r] * c;
+            }
+        }
+        __syncwarp();
+        if (colj) {
+            if (!mix) c2 = -c2;
+            cov[2 * kSlots + i] = c2;
+            cov[i * kSlots + 2] = c2;
+        } else if (i == 2 && (mix || av0)) {
+            cov[2 * kSlots + 2] = v2;
+        }
     }
-    *out = r;
 }
 
-// called by a whole warp: MOSS-5 uses every lane, the k = 4 paths lane 0
+// called by a whole warp: a lane per class
 __device__ void finalize_any(const FinalizeIn &in, const uint64_t *hits0, const uint64_t *hits1,
                              const DevTotals *tot, moss_result *out, double *cov = nullptr) {
-    if (in.k == 5 && !in.mix) {
-        finalize5_warp(in, hits0, hits1, tot, out, cov);
-        return;
-    }
-    if ((threadIdx.x & 31) != 0) return;
-    if (in.mix) finalize_mix(in, hits0, hits1, tot, out, cov);
-    else finalize_one(in, hits0, hits1, tot, out, cov);
+    if (in.k == 5 && !in.mix) finalize5_warp(in, hits0, hits1, tot, out, cov);
+    else finalize4_warp(in, hits0, hits1, tot, out, cov);
 }
 
 // one warp
