@@ -8,10 +8,11 @@
 //   * lists of at most 128 entries: a warp per list, each entry's rank is the
 //     count of keys above its own;
 //   * lists of at most kTile entries: a block per list, bitonic sort in
-//     shared memory;
+//     shared memory, each key's list position moving with it;
 //   * longer lists: a block per list sorts tiles of kTile keys in shared
-//     memory, then merges runs pairwise in global memory, each key placed by
-//     one binary search in the partner run (keys are distinct).
+//     memory, then merges runs pairwise in global memory, each key (with its
+//     position) placed by one binary search in the partner run (keys are
+//     distinct).
 // Then per slot (v -> u): u, d_u, off_u, d_{v,u} and d_{u,v} (the rank of the
 // twin slot); per list: Gamma-check_v = sum_u d_{v,u} d_{u,v} and the alias
 // table of sigma-check^(v) (eq. 3) -- the parallel closed form of the sweep
@@ -33,29 +34,6 @@ constexpr uint32_t kWarpKeys = 4;     // k_rank_warp: lists up to 128 entries
 constexpr uint32_t kLongList = 256;   // longer lists: k_min_alias_long, a block per list
 
 __device__ __forceinline__ uint64_t order_key(uint32_t x, uint32_t dx) { return ((uint64_t)dx << 32) | x; }
-
-// position of x in the increasing list col[o, o + d)
-__device__ __forceinline__ uint32_t find_pos(const uint32_t *col, uint32_t o, uint32_t d, uint32_t x) {
-    uint32_t lo = 0, len = d;
-    while (len > 0) {
-        const uint32_t half = len >> 1;
-        if (col[o + lo + half] < x) {
-            lo += half + 1;
-            len -= half + 1;
-        } else {
-            len = half;
-        }
-    }
-    return lo;
-}
-
-// position q of the sorted list holds key: record the entry and u's rank
-__device__ __forceinline__ void emit(const uint32_t *col, uint32_t o, uint32_t d, uint32_t q, uint64_t key,
-                                     uint2 *rlist, uint32_t *rank) {
-    const uint32_t x = (uint32_t)key, dx = (uint32_t)(key >> 32);
-    rlist[o + q] = make_uint2(x, dx);
-    rank[o + find_pos(col, o, d, x)] = q;
-}
 
 // lists of at most kWarpKeys * 32 entries: lane l holds entries l, l + 32, ...;
 // an entry's rank is the number of keys above its own, counted against every
@@ -85,10 +63,12 @@ __global__ void __launch_bounds__(kListThreads) k_rank_warp(uint32_t n, const ui
 #pragma unroll
         for (int kk = 0; kk < kWarpKeys; ++kk) {
             if (kk >= rounds) break;                  // warp-uniform
-            for (int j = 0; j < kWarp; ++j) {
+            const int m = min((int)d - kk * kWarp, kWarp);
+            for (int j = 0; j < m; ++j) {
                 const uint64_t other = __shfl_sync(0xffffffffu, key[kk], j);
 #pragma unroll
-                for (int k = 0; k < kWarpKeys; ++k) r[k] += other > key[k];
+                for (int k = 0; k < kWarpKeys; ++k)
+                    if (k < rounds) r[k] += other > key[k];   // warp-uniform
             }
         }
 #pragma unroll
@@ -108,9 +88,10 @@ __device__ __forceinline__ uint32_t pow2_at_least(uint32_t x) {
     return p;
 }
 
-// keys of col[o + base, o + base + len) into k[0, P), zero padded (zero sorts last)
+// keys of col[o + base, o + base + len) into k[0, P), zero padded (zero sorts
+// last), with each key's position in the list in id[]
 __device__ void load_keys(const uint4 *vert, const uint32_t *col, uint32_t o, uint32_t base, uint32_t len,
-                          uint32_t P, uint64_t *k) {
+                          uint32_t P, uint64_t *k, uint16_t *id) {
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
         uint64_t key = 0;
         if (i < len) {
@@ -118,12 +99,14 @@ __device__ void load_keys(const uint4 *vert, const uint32_t *col, uint32_t o, ui
             key = order_key(x, vert[x].y);
         }
         k[i] = key;
+        id[i] = (uint16_t)i;
     }
     __syncthreads();
 }
 
-// block-wide bitonic sort of k[0, P), P a power of two, highest first
-__device__ void bitonic_desc(uint64_t *k, uint32_t P) {
+// block-wide bitonic sort of k[0, P), P a power of two, highest first; id[]
+// moves with its key
+__device__ void bitonic_desc(uint64_t *k, uint16_t *id, uint32_t P) {
     for (uint32_t size = 2; size <= P; size <<= 1)
         for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
             for (uint32_t t = threadIdx.x; t < P / 2; t += blockDim.x) {
@@ -133,26 +116,36 @@ __device__ void bitonic_desc(uint64_t *k, uint32_t P) {
                 if ((a < b) == down) {
                     k[i] = b;
                     k[j] = a;
+                    const uint16_t t0 = id[i];
+                    id[i] = id[j];
+                    id[j] = t0;
                 }
             }
             __syncthreads();
         }
 }
 
+// a block per 32 vertex records (the scheduler spreads the lists), a list's
+// keys and positions sorted together in shared memory
 __global__ void __launch_bounds__(kSortThreads) k_rank_block(uint32_t n, const uint4 *__restrict__ vert,
                                                             const uint32_t *__restrict__ col, uint2 *rlist,
                                                             uint32_t *rank) {
     __shared__ uint64_t k[kTile];
+    __shared__ uint16_t id[kTile];
     for_each_vertex<kSortThreads, kWarp>(
         n, vert, [](uint4 vr) { return vr.y > kWarpKeys * (uint32_t)kWarp && vr.y <= kTile; },
         [&](uint32_t v) {
             const uint4 vr = vert[v];
             const uint32_t o = vr.x, d = vr.y;
             const uint32_t P = pow2_at_least(d);
-            load_keys(vert, col, o, 0, d, P, k);
-            bitonic_desc(k, P);
-            for (uint32_t q = threadIdx.x; q < d; q += blockDim.x) emit(col, o, d, q, k[q], rlist, rank);
-            __syncthreads();   // k is refilled for the next list
+            load_keys(vert, col, o, 0, d, P, k, id);
+            bitonic_desc(k, id, P);
+            for (uint32_t q = threadIdx.x; q < d; q += blockDim.x) {
+                const uint64_t key = k[q];
+                rlist[o + q] = make_uint2((uint32_t)key, (uint32_t)(key >> 32));
+                rank[o + id[q]] = q;
+            }
+            __syncthreads();   // k and id are refilled for the next list
         });
 }
 
@@ -160,20 +153,26 @@ __global__ void __launch_bounds__(kSortThreads) k_rank_block(uint32_t n, const u
 // of length L merged pairwise between a[] and b[] until one run is left
 __global__ void __launch_bounds__(kSortThreads) k_rank_long(uint32_t n, const uint4 *__restrict__ vert,
                                                            const uint32_t *__restrict__ col, uint64_t *a,
-                                                           uint64_t *b, uint2 *rlist, uint32_t *rank) {
+                                                           uint64_t *b, uint32_t *ia, uint32_t *ib, uint2 *rlist,
+                                                           uint32_t *rank) {
     __shared__ uint64_t k[kTile];
+    __shared__ uint16_t id[kTile];
     for_each_vertex<kSortThreads>(n, vert, [](uint4 vr) { return vr.y > kTile; }, [&](uint32_t v) {
         const uint4 vr = vert[v];
         const uint32_t o = vr.x, d = vr.y;
         for (uint32_t base = 0; base < d; base += kTile) {
             const uint32_t len = min(kTile, d - base);
             const uint32_t P = pow2_at_least(len);
-            load_keys(vert, col, o, base, len, P, k);
-            bitonic_desc(k, P);
-            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) a[(uint64_t)o + base + i] = k[i];
+            load_keys(vert, col, o, base, len, P, k, id);
+            bitonic_desc(k, id, P);
+            for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) {
+                a[(uint64_t)o + base + i] = k[i];
+                ia[(uint64_t)o + base + i] = base + id[i];
+            }
             __syncthreads();
         }
         uint64_t *src = a, *dst = b;
+        uint32_t *isrc = ia, *idst = ib;
         for (uint64_t L = kTile; L < d; L <<= 1) {
             for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
                 const uint64_t run = i / L, start = run * L;
@@ -193,13 +192,21 @@ __global__ void __launch_bounds__(kSortThreads) k_rank_long(uint32_t n, const ui
                 }
                 const uint64_t above = ps < d ? lo - ps : 0;
                 dst[(uint64_t)o + ms + (i - start) + above] = key;
+                idst[(uint64_t)o + ms + (i - start) + above] = isrc[(uint64_t)o + i];
             }
             __syncthreads();
             uint64_t *t = src;
             src = dst;
             dst = t;
+            uint32_t *it = isrc;
+            isrc = idst;
+            idst = it;
         }
-        for (uint32_t q = threadIdx.x; q < d; q += blockDim.x) emit(col, o, d, q, src[(uint64_t)o + q], rlist, rank);
+        for (uint32_t q = threadIdx.x; q < d; q += blockDim.x) {
+            const uint64_t key = src[(uint64_t)o + q];
+            rlist[o + q] = make_uint2((uint32_t)key, (uint32_t)(key >> 32));
+            rank[o + isrc[(uint64_t)o + q]] = q;
+        }
         __syncthreads();
     });
 }
@@ -216,9 +223,16 @@ __global__ void k_min_slots(uint64_t nnz, const uint4 *__restrict__ vert, const 
     }
 }
 
+// (a read-only load: the alias passes write only the first half of each record)
 __device__ __forceinline__ uint64_t min_weight(const uint4 *mslot, uint64_t p) {
-    const uint4 r = mslot[2 * p + 1];
+    const uint4 r = __ldg(mslot + 2 * p + 1);
     return (uint64_t)r.z * r.w;   // d_{v,u} d_{u,v}
+}
+
+// threshold and alias position into the first half of a slot record
+__device__ __forceinline__ void set_min_alias(uint32_t *m32, uint64_t p, uint64_t thr, uint32_t alias) {
+    *reinterpret_cast<uint2 *>(m32 + 8 * p) = make_uint2((uint32_t)thr, (uint32_t)(thr >> 32));
+    m32[8 * p + 2] = alias;
 }
 
 // warp per list: Gamma-check_v, mvert, and the alias table of sigma-check^(v)
@@ -227,12 +241,126 @@ __device__ __forceinline__ uint64_t min_weight(const uint4 *mslot, uint64_t p) {
 // exclusive prefix of the light deficits and P_k the inclusive prefix of the
 // heavy excesses: light i keeps q_i and aliases heavy min{k : P_k >= A_i};
 // heavy k keeps W + P_k - A_{i'} (i' = min{i : A_i > P_k}) and aliases heavy
-// k+1, or keeps W when P_k is the total.
-__global__ void __launch_bounds__(kListThreads) k_min_alias(uint32_t n, const uint4 *__restrict__ vert, uint4 *mslot,
-                                                           uint4 *mvert, u128 *gmin, uint32_t *idx, u128 *pre,
-                                                           u128 *partials) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+// k+1, or keeps W when P_k is the total.  The split (idx, pre) of the list
+// being built lives in the warp's share of shared memory; the prefixes are
+// 64-bit when d W fits (every list short enough for this kernel with W below
+// 2^56), else 128-bit.
+template <typename T>
+__device__ __forceinline__ T warp_scan_any(T v, int lane);
+template <>
+__device__ __forceinline__ uint64_t warp_scan_any<uint64_t>(uint64_t v, int lane) {
+    return warp_incl_scan64(v, lane);
+}
+template <>
+__device__ __forceinline__ u128 warp_scan_any<u128>(u128 v, int lane) {
+    return warp_incl_scan128(v, lane);
+}
+__device__ __forceinline__ uint64_t shfl_idx_any(uint64_t v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ u128 shfl_idx_any(u128 v, int src) { return shfl_idx_u128(v, src); }
+
+// alias table of sigma-check^(v) for the list at o of d <= kLongList entries
+// with total W > 0, one warp; pre holds kLongList T, idx kLongList positions
+template <typename T>
+__device__ void warp_min_alias(const uint4 *mslot, uint32_t *m32, uint32_t o, uint32_t d, uint64_t W, T *pre,
+                               uint32_t *idx) {
+    const int lane = threadIdx.x & 31;
     const uint32_t below = (1u << lane) - 1u;
+    // pass 1: lights to the front, heavies to the back, with their prefixes
+    uint32_t nl = 0, nh = 0;
+    T Arun = 0, Prun = 0;
+    for (uint32_t base = 0; base < d; base += kWarp) {
+        const uint32_t j = base + lane;
+        const bool valid = j < d;
+        const T q = valid ? (T)min_weight(mslot, (uint64_t)o + j) * (T)d : (T)0;
+        const bool light = valid && q < W;
+        const uint32_t lmask = __ballot_sync(0xffffffffu, light);
+        const uint32_t hmask = __ballot_sync(0xffffffffu, valid && !light);
+        const T D = light ? (T)W - q : (T)0;
+        const T E = valid && !light ? q - (T)W : (T)0;
+        const T Dincl = warp_scan_any<T>(D, lane);
+        const T Eincl = warp_scan_any<T>(E, lane);
+        if (light) {
+            const uint32_t r = nl + __popc(lmask & below);
+            idx[r] = j;
+            pre[r] = Arun + Dincl - D;          // exclusive A_i
+        } else if (valid) {
+            const uint32_t r = nh + __popc(hmask & below);
+            idx[d - 1 - r] = j;
+            pre[d - 1 - r] = Prun + Eincl;      // inclusive P_k
+        }
+        nl += __popc(lmask);
+        nh += __popc(hmask);
+        Arun += shfl_idx_any(Dincl, 31);
+        Prun += shfl_idx_any(Eincl, 31);
+    }
+    __syncwarp();
+    const T Ptot = Prun;   // == Arun
+    const uint64_t ob = o;
+    // pass 2: each lane merges a contiguous run of lights, then of heavies
+    {
+        const uint32_t cl = (nl + kWarp - 1) / kWarp;
+        const uint32_t i0 = lane * cl, i1 = min(nl, i0 + cl);
+        if (i0 < i1) {
+            const T A0 = pre[i0];
+            uint32_t k = 0, len = nh;   // first heavy with P_k >= A
+            while (len > 0) {
+                const uint32_t half = len >> 1;
+                if (pre[d - 1 - (k + half)] < A0) {
+                    k += half + 1;
+                    len -= half + 1;
+                } else {
+                    len = half;
+                }
+            }
+            for (uint32_t i = i0; i < i1; ++i) {
+                const T A = pre[i];
+                while (pre[d - 1 - k] < A) ++k;
+                const uint32_t j = idx[i];
+                const uint64_t thr = min_weight(mslot, ob + j) * (uint64_t)d;   // q_j < W < 2^64
+                set_min_alias(m32, ob + j, thr, idx[d - 1 - k]);
+            }
+        }
+    }
+    {
+        const uint32_t ch = (nh + kWarp - 1) / kWarp;
+        const uint32_t k0 = lane * ch, k1 = min(nh, k0 + ch);
+        if (k0 < k1) {
+            const T P0 = pre[d - 1 - k0];
+            uint32_t i = 0, len = nl;   // first light with A_i > P_k
+            while (len > 0) {
+                const uint32_t half = len >> 1;
+                if (pre[i + half] <= P0) {
+                    i += half + 1;
+                    len -= half + 1;
+                } else {
+                    len = half;
+                }
+            }
+            for (uint32_t k = k0; k < k1; ++k) {
+                const T Pk = pre[d - 1 - k];
+                while (i < nl && pre[i] <= Pk) ++i;
+                const uint32_t j = idx[d - 1 - k];
+                uint64_t thr;
+                uint32_t alias;
+                if (Pk < Ptot) {
+                    const T Ai = i < nl ? pre[i] : Ptot;
+                    thr = (uint64_t)((T)W + Pk - Ai);
+                    alias = idx[d - 1 - (k + 1)];
+                } else {
+                    thr = W;
+                    alias = j;
+                }
+                set_min_alias(m32, ob + j, thr, alias);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kListThreads) k_min_alias(uint32_t n, const uint4 *__restrict__ vert, uint4 *mslot,
+                                                           uint4 *mvert, u128 *gmin, u128 *partials) {
+    __shared__ u128 s_pre[kListThreads / kWarp][kLongList];
+    __shared__ uint32_t s_idx[kListThreads / kWarp][kLongList];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     uint32_t *m32 = reinterpret_cast<uint32_t *>(mslot);
     u128 total = 0;
     for (uint64_t v = (uint64_t)blockIdx.x * wpb + warp; v < n; v += (uint64_t)gridDim.x * wpb) {
@@ -250,106 +378,13 @@ __global__ void __launch_bounds__(kListThreads) k_min_alias(uint32_t n, const ui
         }
         if (d == 0 || (d > kLongList && W != 0)) continue;
         if (W == 0) {   // never drawn: keep every column
-            for (uint32_t j = lane; j < d; j += kWarp) {
-                m32[8 * ((uint64_t)o + j) + 0] = 0;
-                m32[8 * ((uint64_t)o + j) + 1] = 0;
-                m32[8 * ((uint64_t)o + j) + 2] = j;
-            }
+            for (uint32_t j = lane; j < d; j += kWarp) set_min_alias(m32, (uint64_t)o + j, 0, j);
             continue;
         }
-        // pass 1: lights to the front, heavies to the back, with their prefixes
-        uint32_t nl = 0, nh = 0;
-        u128 Arun = 0, Prun = 0;
-        for (uint32_t base = 0; base < d; base += kWarp) {
-            const uint32_t j = base + lane;
-            const bool valid = j < d;
-            const u128 q = valid ? (u128)min_weight(mslot, (uint64_t)o + j) * d : 0;
-            const bool light = valid && q < W;
-            const uint32_t lmask = __ballot_sync(0xffffffffu, light);
-            const uint32_t hmask = __ballot_sync(0xffffffffu, valid && !light);
-            const u128 D = light ? (u128)W - q : 0;
-            const u128 E = valid && !light ? q - W : 0;
-            const u128 Dincl = warp_incl_scan128(D, lane);
-            const u128 Eincl = warp_incl_scan128(E, lane);
-            if (light) {
-                const uint32_t r = nl + __popc(lmask & below);
-                idx[(uint64_t)o + r] = j;
-                pre[(uint64_t)o + r] = Arun + Dincl - D;          // exclusive A_i
-            } else if (valid) {
-                const uint32_t r = nh + __popc(hmask & below);
-                idx[(uint64_t)o + d - 1 - r] = j;
-                pre[(uint64_t)o + d - 1 - r] = Prun + Eincl;      // inclusive P_k
-            }
-            nl += __popc(lmask);
-            nh += __popc(hmask);
-            Arun += shfl_idx_u128(Dincl, 31);
-            Prun += shfl_idx_u128(Eincl, 31);
-        }
-        __syncwarp();
-        const u128 Ptot = Prun;   // == Arun
-        const uint64_t ob = o;
-        // pass 2: each lane merges a contiguous run of lights, then of heavies
-        {
-            const uint32_t cl = (nl + kWarp - 1) / kWarp;
-            const uint32_t i0 = lane * cl, i1 = min(nl, i0 + cl);
-            if (i0 < i1) {
-                const u128 A0 = pre[ob + i0];
-                uint32_t k = 0, len = nh;   // first heavy with P_k >= A
-                while (len > 0) {
-                    const uint32_t half = len >> 1;
-                    if (pre[ob + d - 1 - (k + half)] < A0) {
-                        k += half + 1;
-                        len -= half + 1;
-                    } else {
-                        len = half;
-                    }
-                }
-                for (uint32_t i = i0; i < i1; ++i) {
-                    const u128 A = pre[ob + i];
-                    while (pre[ob + d - 1 - k] < A) ++k;
-                    const uint32_t j = idx[ob + i];
-                    const uint64_t thr = min_weight(mslot, ob + j) * (uint64_t)d;   // q_j < W < 2^64
-                    m32[8 * (ob + j) + 0] = (uint32_t)thr;
-                    m32[8 * (ob + j) + 1] = (uint32_t)(thr >> 32);
-                    m32[8 * (ob + j) + 2] = idx[ob + d - 1 - k];
-                }
-            }
-        }
-        {
-            const uint32_t ch = (nh + kWarp - 1) / kWarp;
-            const uint32_t k0 = lane * ch, k1 = min(nh, k0 + ch);
-            if (k0 < k1) {
-                const u128 P0 = pre[ob + d - 1 - k0];
-                uint32_t i = 0, len = nl;   // first light with A_i > P_k
-                while (len > 0) {
-                    const uint32_t half = len >> 1;
-                    if (pre[ob + i + half] <= P0) {
-                        i += half + 1;
-                        len -= half + 1;
-                    } else {
-                        len = half;
-                    }
-                }
-                for (uint32_t k = k0; k < k1; ++k) {
-                    const u128 Pk = pre[ob + d - 1 - k];
-                    while (i < nl && pre[ob + i] <= Pk) ++i;
-                    const uint32_t j = idx[ob + d - 1 - k];
-                    uint64_t thr;
-                    uint32_t alias;
-                    if (Pk < Ptot) {
-                        const u128 Ai = i < nl ? pre[ob + i] : Ptot;
-                        thr = (uint64_t)((u128)W + Pk - Ai);
-                        alias = idx[ob + d - 1 - (k + 1)];
-                    } else {
-                        thr = W;
-                        alias = j;
-                    }
-                    m32[8 * (ob + j) + 0] = (uint32_t)thr;
-                    m32[8 * (ob + j) + 1] = (uint32_t)(thr >> 32);
-                    m32[8 * (ob + j) + 2] = alias;
-                }
-            }
-        }
+        if (W < (1ull << 56))   // q = w d <= W kLongList < 2^64
+            warp_min_alias<uint64_t>(mslot, m32, o, d, W, reinterpret_cast<uint64_t *>(s_pre[warp]), s_idx[warp]);
+        else
+            warp_min_alias<u128>(mslot, m32, o, d, W, s_pre[warp], s_idx[warp]);
         __syncwarp();
     }
     // block share of Gamma-check (lane 0 of each warp holds its warp's)
@@ -364,24 +399,29 @@ __global__ void __launch_bounds__(kListThreads) k_min_alias(uint32_t n, const ui
 }
 
 // the alias tables of lists longer than kLongList, a block per list, after
-// k_min_alias has written Gamma-check_v into mvert
+// k_min_alias has written Gamma-check_v into mvert; a block per kWarp vertex
+// records (the scheduler spreads the long lists), the split of a list of at
+// most kMinSmemList entries in dynamic shared memory, of a longer one in its
+// range of the global scratch (idx, pre)
+constexpr uint32_t kMinSmemList = 2048;
+constexpr size_t kMinSmemBytes = (size_t)kMinSmemList * (sizeof(u128) + sizeof(uint32_t));
+
 __global__ void __launch_bounds__(kListThreads) k_min_alias_long(uint32_t n, const uint4 *__restrict__ vert,
                                                                 const uint4 *__restrict__ mvert, uint4 *mslot,
                                                                 uint32_t *idx, u128 *pre) {
+    extern __shared__ u128 s_split[];   // kMinSmemList prefixes, then kMinSmemList positions
     uint32_t *m32 = reinterpret_cast<uint32_t *>(mslot);
-    for_each_vertex<kListThreads>(
+    for_each_vertex<kListThreads, kWarp>(
         n, mvert, [](uint4 mv) { return mv.y > kLongList && (mv.z | mv.w) != 0; },
         [&](uint32_t v) {
             const uint4 mv = mvert[v];
             const uint32_t o = mv.x, d = mv.y;
             const uint64_t W = ((uint64_t)mv.w << 32) | mv.z;
+            const bool fits = d <= kMinSmemList;
             block_alias<u128, kListThreads>(
-                d, (u128)W, [&](uint32_t j) { return (u128)min_weight(mslot, (uint64_t)o + j); }, idx + o, pre + o,
-                [&](uint32_t j, u128 thr, uint32_t alias) {
-                    m32[8 * ((uint64_t)o + j) + 0] = (uint32_t)thr;
-                    m32[8 * ((uint64_t)o + j) + 1] = (uint32_t)((uint64_t)thr >> 32);
-                    m32[8 * ((uint64_t)o + j) + 2] = alias;
-                });
+                d, (u128)W, [&](uint32_t j) { return (u128)min_weight(mslot, (uint64_t)o + j); },
+                fits ? reinterpret_cast<uint32_t *>(s_split + kMinSmemList) : idx + o, fits ? s_split : pre + o,
+                [&](uint32_t j, u128 thr, uint32_t alias) { set_min_alias(m32, (uint64_t)o + j, (uint64_t)thr, alias); });
         });
 }
 
@@ -406,6 +446,7 @@ unsigned grid_for(uint64_t items, int per_block, int cap_per_sm) {
 struct MinScratch {
     uint32_t *rank;   // nnz, then reused as the alias split order
     uint64_t *a, *b;  // nnz each (long-list merges), then reused as u128 prefixes
+    uint32_t *ia, *ib;  // nnz each: list positions of the keys in a, b
     u128 *partials;
     void *seed;       // vertex alias scratch
     uint64_t bytes;
@@ -442,6 +483,8 @@ MinScratch carve(void *base, uint32_t n, uint64_t nnz) {
     m.rank = reinterpret_cast<uint32_t *>(take(nnz * 4));
     m.a = reinterpret_cast<uint64_t *>(take(nnz * 16));
     m.b = m.a ? m.a + nnz : nullptr;
+    m.ia = reinterpret_cast<uint32_t *>(take(nnz * 8));
+    m.ib = m.ia ? m.ia + nnz : nullptr;
     m.partials = reinterpret_cast<u128 *>(take((uint64_t)alias_blocks * 16));
     m.seed = take(seed_scratch_bytes(n));
     m.bytes = off;
@@ -462,21 +505,24 @@ cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const
         k_rank_warp<<<grid_for((uint64_t)n, kListThreads / kWarp, 8), kListThreads, 0, s>>>(n, vert, col, rlist,
                                                                                              m.rank);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_rank_block<<<grid_for((uint64_t)n, kWarp, 4), kSortThreads, 0, s>>>(n, vert, col, rlist, m.rank);
+        const unsigned chunks = (unsigned)(((uint64_t)n + kWarp - 1) / kWarp);
+        k_rank_block<<<chunks, kSortThreads, 0, s>>>(n, vert, col, rlist, m.rank);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_rank_long<<<grid_for((uint64_t)n, kSortThreads, 1), kSortThreads, 0, s>>>(n, vert, col, m.a, m.b, rlist,
-                                                                                    m.rank);
+        k_rank_long<<<grid_for((uint64_t)n, kSortThreads, 1), kSortThreads, 0, s>>>(n, vert, col, m.a, m.b, m.ia,
+                                                                                    m.ib, rlist, m.rank);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         k_min_slots<<<grid_for(nnz, 256, 16), 256, 0, s>>>(nnz, vert, col, slot, m.rank, mslot);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const unsigned ab = grid_for((uint64_t)n, kListThreads / kWarp, 8);
     // the rank array is dead now: it holds the split order, a[]/b[] the prefixes
-    k_min_alias<<<ab, kListThreads, 0, s>>>(n, vert, mslot, mvert, gmin, m.rank, reinterpret_cast<u128 *>(m.a),
-                                             m.partials);
+    k_min_alias<<<ab, kListThreads, 0, s>>>(n, vert, mslot, mvert, gmin, m.partials);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_min_alias_long<<<grid_for((uint64_t)n, kListThreads, 4), kListThreads, 0, s>>>(n, vert, mvert, mslot, m.rank,
-                                                                          reinterpret_cast<u128 *>(m.a));
+    e = cudaFuncSetAttribute(k_min_alias_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMinSmemBytes);
+    if (e != cudaSuccess) return e;
+    const unsigned chunks = (unsigned)(((uint64_t)n + kWarp - 1) / kWarp);
+    k_min_alias_long<<<chunks, kListThreads, kMinSmemBytes, s>>>(n, vert, mvert, mslot, m.rank,
+                                                                  reinterpret_cast<u128 *>(m.a));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (nnz) {
         k_min_pick<<<grid_for(nnz, 256, 16), 256, 0, s>>>(nnz, owner, mvert, mslot, mpick);
