@@ -29,10 +29,10 @@
  *     their device memory and release it in moss_graph_free.
  *   - A moss_graph may be used by one host thread at a time.
  *
- * Random numbers: Philox4x64-10 (Salmon et al., SC'11).  Word i of sample s of
- * method t under seed k is word (i mod 4) of Philox4x64-10(counter
- * {s, i div 4, t, 0}, key {k, 0}); t = 0 (MOSS-4), 1 (T-5), 2 (Path-5),
- * 3 (MOSS-4Min).  The
+ * Random numbers: SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) in counter
+ * form.  Word i (0 <= i < 16) of sample s of method t under seed k is output
+ * number (4 s + t) 16 + i + 1 of SplitMix64 seeded with k; t = 0 (MOSS-4),
+ * 1 (T-5), 2 (Path-5), 3 (MOSS-4Min).  The
  * counts of a sample range are therefore independent of launch shape, stream
  * and device count, and shards [a,b) + [b,c) add up to [a,c) exactly.
  */

@@ -7,7 +7,7 @@ and shares no code with it.
 Contents
 * ``moss_oracle.c`` (compiled with gcc on first use): exact integer vertex
   weights and totals (Table 1), alias tables for WeightRandomVertex
-  (Sec. 4.1.3), the Philox4x64-10 word schedule, the per-sample steps of
+  (Sec. 4.1.3), the counter-form SplitMix64 word schedule, the per-sample steps of
   Algorithm 1 (MOSS-4), Algorithm 2 (MOSS-4Min, Sec. 4.2: the total order,
   N_{u,v}, the weights Gamma-check_v and sigma-check, and c(s), the number
   of 3-paths of a CIS that the method can draw), Algorithm 3 (T-5) and
@@ -62,7 +62,8 @@ def _load():
         lib.oracle_sigma_table.argtypes = [ctypes.c_void_p, _u64p, _u32p, _u64p]
         lib.oracle_alias_build.argtypes = [ctypes.c_uint64, _u64p, _u64p, _u32p]
         lib.oracle_alias_build.restype = ctypes.c_int
-        lib.oracle_philox.argtypes = [_u64p, _u64p, _u64p]
+        lib.oracle_splitmix.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        lib.oracle_splitmix.restype = ctypes.c_uint64
         lib.oracle_classify.argtypes = [ctypes.c_int, ctypes.c_uint32]
         lib.oracle_classify.restype = ctypes.c_int
         lib.oracle_sample_words.argtypes = [ctypes.c_void_p, ctypes.c_int, _u64p, _u32p, ctypes.POINTER(ctypes.c_int)]
@@ -88,13 +89,15 @@ def _u128(lohi) -> int:
     return int(lohi[0]) | (int(lohi[1]) << 64)
 
 
-def philox4x64(ctr, key) -> list[int]:
-    """One Philox4x64-10 block."""
-    c = np.array(ctr, dtype=np.uint64)
-    k = np.array(key, dtype=np.uint64)
-    out = np.zeros(4, dtype=np.uint64)
-    _load().oracle_philox(_p(c, _u64p), _p(k, _u64p), _p(out, _u64p))
-    return [int(x) for x in out]
+def splitmix64(seed: int, k: int) -> int:
+    """Output number k >= 1 of SplitMix64 seeded with seed."""
+    return int(_load().oracle_splitmix(seed % (1 << 64), k % (1 << 64)))
+
+
+def sample_words(method: int, seed: int, s: int, n: int = 16) -> list[int]:
+    """Words x_0 .. x_{n-1} of sample s of a method: output (4 s + method) 16 +
+    i + 1 of SplitMix64 seeded with seed."""
+    return [splitmix64(seed, (4 * s + method) * 16 + i + 1) for i in range(n)]
 
 
 def classify(k: int, mask: int) -> int:

@@ -4,7 +4,7 @@
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
  * CPU-baseline leg of the benchmark may load this file's library.  It shares
  * no code with the CUDA library: everything here (weights, alias tables, the
- * Philox generator, sampling, classification, enumeration) is written out
+ * SplitMix64 generator, sampling, classification, enumeration) is written out
  * independently, sequentially and without any blocking or fusion.
  *
  * Paper: P. Wang, J. Tao, J. Zhao, X. Guan, "Moss: A Scalable Tool for
@@ -25,9 +25,11 @@
  *  - ESU enumeration (Wernicke 2006, cited in the paper's introduction) of
  *    every connected induced k-subgraph, for exact ground truth.
  *
- * RNG: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Word i of sample s
- * of method tag t under seed k is word (i mod 4) of
- * Philox4x64-10(counter = {s, i div 4, t, 0}, key = {k, 0}).
+ * RNG: SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014), used in counter form: word i (0 <= i < 16) of
+ * sample s of method tag t under seed k is output number (4 s + t) 16 + i + 1
+ * of the generator seeded with k, i.e. mix(k + ((4 s + t) 16 + i + 1) gamma).
+ * The paper draws uniform choices without fixing a generator.
  * Word schedule (x_i = word i):
  *   MOSS-4 : x0,x1 seed draw (column, threshold); x2,x3 sigma draw of u;
  *            x4 w; x5 r.
@@ -47,25 +49,17 @@ typedef unsigned __int128 u128;
 
 enum { M_MOSS4 = 0, M_T5 = 1, M_P5 = 2 };
 
-/* ------------------------------------------------------------ Philox ---- */
-/* Philox4x64-10: ten rounds of two 64x64->128 multiplies with a Weyl-sequence
- * key schedule (Salmon et al. 2011, Sec. 4 and Table 2 of that paper). */
-void oracle_philox(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
-    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
-    uint64_t k0 = key[0], k1 = key[1];
-    for (int round = 0; round < 10; round++) {
-        u128 p0 = (u128)0xD2E7470EE14C6C93ULL * c0;
-        u128 p1 = (u128)0xCA5A826395121157ULL * c2;
-        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
-        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
-        c0 = hi1 ^ c1 ^ k0;
-        c1 = lo1;
-        c2 = hi0 ^ c3 ^ k1;
-        c3 = lo0;
-        k0 += 0x9E3779B97F4A7C15ULL;
-        k1 += 0xBB67AE8584CAA73BULL;
-    }
-    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+/* -------------------------------------------------------- SplitMix64 ---- */
+/* Output number k >= 1 of SplitMix64 seeded with seed: the state advances by
+ * the Weyl increment gamma = 0x9E3779B97F4A7C15 before each output, and the
+ * output is the state through the mixing function (xor-shift 30, multiply by
+ * 0xBF58476D1CE4E5B9, xor-shift 27, multiply by 0x94D049BB133111EB,
+ * xor-shift 31), all modulo 2^64. */
+uint64_t oracle_splitmix(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + k * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
 }
 
 static uint64_t index_of(uint64_t x, uint64_t m) { return (uint64_t)(((u128)x * m) >> 64); }
@@ -500,12 +494,9 @@ int oracle_sample_words(const ctx *c, int method, const uint64_t *words, uint32_
     return 0;
 }
 
-/* words of sample s: x[i] = Philox4x64-10({s, i/4, tag, 0}, {seed, 0})[i%4] */
+/* words of sample s: x[i] = output (4 s + tag) 16 + i + 1 of SplitMix64(seed) */
 static void sample_words(int method, uint64_t seed, uint64_t s, uint64_t *x) {
-    for (uint64_t b = 0; b < 4; b++) {
-        uint64_t ctr[4] = {s, b, (uint64_t)method, 0}, key[2] = {seed, 0};
-        oracle_philox(ctr, key, x + 4 * b);
-    }
+    for (uint64_t i = 0; i < 16; i++) x[i] = oracle_splitmix(seed, (4 * s + (uint64_t)method) * 16 + i + 1);
 }
 
 /* Run samples s in [first, first+count) of one method: counts[0] collisions,

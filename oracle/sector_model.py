@@ -17,7 +17,7 @@ list (MOSS_PROBE_SEARCH, which also reads the two vertex records) or the home
 bucket of the hashed edge set (MOSS_PROBE_HASH, 32 B buckets of four keys; the rare
 continuation into the next bucket is not counted), or the word of the edge
 filter followed by that bucket only when the filter passes (MOSS_PROBE_FILTER).
-The draws are replayed from the oracle's Philox words and tables, so the
+The draws are replayed from the oracle's words and tables, so the
 count is exact per sample; the mean over a few thousand samples is the
 per-sample figure used by the roofline ("achieved" = figure x 32 B x samples
 / kernel time).
@@ -180,10 +180,7 @@ class Replay:
         return len(t)
 
     def words(self, method, seed, s, blocks):
-        out = []
-        for b in range(blocks):
-            out += oracle.philox4x64([s, b, method, 0], [seed, 0])
-        return out
+        return oracle.sample_words(method, seed, s, 4 * blocks)
 
     def probe(self, a, b, touched):
         if self.probe_kind == "filter":   # filter word (8 per sector); the set only when it may hold the pair

@@ -206,27 +206,29 @@ __device__ __forceinline__ u128 warp_sum128(u128 v) {
     return v;
 }
 
-// ---------------------------------------------------------------- Philox --
-// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
-// as 1, 2, 3", SC'11): ten rounds, each multiplying counter words 0 and 2 by
-// the two round constants (128-bit products), crossing the halves and
-// xoring in the key; the key advances by a Weyl increment between rounds.
+// ------------------------------------------------------------ SplitMix64 --
+// SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014) in counter form: word i (0 <= i < 16) of sample s
+// of method t under seed k is output number (4 s + t) 16 + i + 1 of the
+// generator seeded with k: the state k advanced by that many Weyl increments,
+// through the generator's mixing function.  Every word is independent of the
+// others, so a sample computes only the words it reads.
 struct Words4 { uint64_t x[4]; };
 
-__device__ __forceinline__ Words4 philox4x64(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
-                                             uint64_t k0, uint64_t k1) {
-    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
-    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
-        uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
-        uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
-        k0 += W0; k1 += W1;
-    }
+constexpr uint64_t kSplitMixGamma = 0x9E3779B97F4A7C15ULL;
+
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// words 4 blk .. 4 blk + 3 of sample s of method t
+__device__ __forceinline__ Words4 sample_words4(uint64_t seed, uint32_t t, uint64_t s, uint32_t blk) {
+    const uint64_t base = seed + ((4 * s + t) * 16 + 4 * blk + 1) * kSplitMixGamma;
     Words4 w;
-    w.x[0] = c0; w.x[1] = c1; w.x[2] = c2; w.x[3] = c3;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w.x[k] = splitmix_mix(base + (uint64_t)k * kSplitMixGamma);
     return w;
 }
 

@@ -3,7 +3,7 @@
 //
 // One thread draws one sample at a time (grid-stride over sample ids), so
 // every sample is an independent chain of dependent gathers:
-//   Philox words -> vertex alias record (32 B, with the alias's vertex record;
+//   random words -> vertex alias record (32 B, with the alias's vertex record;
 //   vert[v] (16 B) only when the column keeps the draw) -> sigma
 //   record(s) of N_v (32 B each, carrying the picked neighbour's list and
 //   twin) -> uniform list picks (4 B) -> the unknown pairs, probed together
@@ -13,8 +13,8 @@
 // histograms and leave the block as one row of per-block partials; a second
 // kernel adds the rows in a fixed order.  No global atomics.
 //
-// Word schedule (x_i = word i of the sample; Philox4x64-10 counter
-// {s, i div 4, method, 0}, key {seed, 0}):
+// Word schedule (x_i = word i of the sample, output (4 s + method) 16 + i + 1
+// of SplitMix64 seeded with seed; sample_words4 in moss_internal.cuh):
 //   MOSS-4 : x0,x1 vertex draw; x2,x3 sigma draw of u; x4 w; x5 r.
 //   T-5    : x0,x1 vertex draw; x2,x3 sigma of u; x4 w; x5 r; x6 t.
 //   MOSS-4Min: x0,x1 vertex draw (pi-check); x2,x3 sigma-check draw of u;
@@ -208,8 +208,8 @@ struct Sample {
 template <bool HASH>
 __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
-    const Words4 a = philox4x64(s, 0, 0, 0, seed, 0);
-    const Words4 b = philox4x64(s, 1, 0, 0, seed, 0);
+    const Words4 a = sample_words4(seed, 0, s, 0);
+    const Words4 b = sample_words4(seed, 0, s, 1);
     const VertexPick pv = draw_vertex(g.seed[0], g.vert, g.n, a.x[0], a.x[1]);
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
@@ -242,8 +242,8 @@ __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t 
 template <bool HASH>
 __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
-    const Words4 a = philox4x64(s, 0, 1, 0, seed, 0);
-    const Words4 b = philox4x64(s, 1, 1, 0, seed, 0);
+    const Words4 a = sample_words4(seed, 1, s, 0);
+    const Words4 b = sample_words4(seed, 1, s, 1);
     const VertexPick pv = draw_vertex(g.seed[1], g.vert, g.n, a.x[0], a.x[1]);
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
@@ -306,8 +306,8 @@ template <bool HASH>
 __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *lut, const uint8_t *lutc, uint64_t seed,
                                              uint64_t s) {
     Sample out;
-    const Words4 a = philox4x64(s, 0, 3, 0, seed, 0);
-    const Words4 b = philox4x64(s, 1, 3, 0, seed, 0);
+    const Words4 a = sample_words4(seed, 3, s, 0);
+    const Words4 b = sample_words4(seed, 3, s, 1);
     const VertexPick pv = draw_vertex(g.seed[3], g.mvert, g.n, a.x[0], a.x[1]);
     const uint32_t v = pv.v;
     const uint4 mv = pv.rec;                           // {off, d_v, Gamma-check_v}
@@ -415,14 +415,14 @@ constexpr int kDeferred = 254;
 template <bool HASH, int STAGE>
 __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
-    const Words4 a = philox4x64(s, 0, 2, 0, seed, 0);
+    const Words4 a = sample_words4(seed, 2, s, 0);
     const VertexPick pv = draw_vertex(g.seed[2], g.vert, g.n, a.x[0], a.x[1]);
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
     Pick pu, pw;
     bool collide = true;
     if (STAGE == 0 || STAGE == 3) {
-        const Words4 b = philox4x64(s, 1, 2, 0, seed, 0);
+        const Words4 b = sample_words4(seed, 2, s, 1);
         pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, b.x[0], b.x[1]);
         pw = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, b.x[2], b.x[3]);
         collide = pu.pos == pw.pos;
@@ -432,7 +432,7 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
         }
     }
     if (STAGE == 1 || (STAGE == 3 && collide)) {
-        const Words4 c = philox4x64(s, 2, 2, 0, seed, 0);
+        const Words4 c = sample_words4(seed, 2, s, 2);
         pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, c.x[0], c.x[1]);
         pw = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, c.x[2], c.x[3]);
         collide = pu.pos == pw.pos;
@@ -442,7 +442,7 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
         }
     }
     if (STAGE == 2 || (STAGE == 3 && collide)) {
-        const Words4 d4 = philox4x64(s, 3, 2, 0, seed, 0);
+        const Words4 d4 = sample_words4(seed, 2, s, 3);
         uint32_t iu, iw;
         path5_fallback(g.acc, g.sq, v, vr, d4.x[0], d4.x[1], iu, iw);
         pu = slot_pick(g.slot, g.vert, vr.x, iu);

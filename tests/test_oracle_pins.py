@@ -1,6 +1,7 @@
 """Pins of the oracle's building blocks against things other than itself (CPU).
 
-* Philox4x64-10 against numpy's independent implementation.
+* SplitMix64 against its published reference outputs (tests/golden), and the
+  word schedule against the generator's sequence.
 * Alias tables: exact integer mass identity (each item gets w_j / W).
 * Vertex weights Gamma, Gamma^(1), Gamma^(2), Lambda_3, Lambda_4 against
   brute-force counts of the draw sequences / subgraphs they stand for
@@ -12,6 +13,7 @@
 from __future__ import annotations
 
 import itertools
+import os
 
 import numpy as np
 import pytest
@@ -23,20 +25,42 @@ from helpers import adjacency_sets, brute_force_cis, class_counts, mask_classes,
 TWO64 = 1 << 64
 
 
-# ------------------------------------------------------------------ Philox --
-@pytest.mark.parametrize("seed", [0, 1, 42, 2**63 + 5])
-def test_philox_matches_numpy(seed):
-    rng = np.random.default_rng(seed % 1000)
-    for _ in range(20):
-        ctr = [int(x) for x in rng.integers(0, 2**63, size=4, dtype=np.int64)]
-        key = [seed % TWO64, int(rng.integers(0, 2**63))]
-        bg = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=np.array(ctr, dtype=np.uint64))
-        # numpy advances the counter by one before producing a block
-        ref = [int(x) for x in bg.random_raw(4)]
-        nxt = [(ctr[0] + 1) % TWO64] + ctr[1:]
-        if nxt[0] == 0:
-            nxt[1] = (nxt[1] + 1) % TWO64
-        assert oracle.philox4x64(nxt, key) == ref
+# -------------------------------------------------------------- SplitMix64 --
+def _splitmix_golden():
+    out = {}
+    for line in open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "splitmix64.txt")):
+        if line.strip() and not line.startswith("#"):
+            kind, *vals = line.split()
+            out[kind] = [int(v) for v in vals]
+    return out
+
+
+def test_splitmix_reference_outputs():
+    seed, *ref = _splitmix_golden()["outputs"]
+    assert [oracle.splitmix64(seed, k) for k in range(1, len(ref) + 1)] == ref
+
+
+def test_splitmix_reference_buckets():
+    seed, count, *ref = _splitmix_golden()["buckets"]
+    counts = [0] * 5
+    for k in range(1, count + 1):
+        counts[oracle.splitmix64(seed, k) * 5 >> 64] += 1
+    assert counts == ref
+
+
+def test_word_schedule_follows_the_sequence():
+    """Sample 0 of method 0 reads the generator's first outputs; sample s of
+    method t starts 16 (4 s + t) outputs in, without overlap."""
+    seed, *ref = _splitmix_golden()["outputs"]
+    assert oracle.sample_words(0, seed, 0, len(ref)) == ref
+    w = oracle.sample_words(2, seed, 3, 16)
+    assert w[0] == oracle.splitmix64(seed, (4 * 3 + 2) * 16 + 1)
+    seen = set()
+    for s in range(4):
+        for t in range(4):
+            ws = oracle.sample_words(t, seed, s, 16)
+            assert not seen & set(ws)
+            seen |= set(ws)
 
 
 # ------------------------------------------------------------------- alias --
