@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 
@@ -150,6 +151,8 @@ int centred_paths_of(uint32_t mask, uint32_t above) {
         }
     return c;
 }
+
+std::atomic<int> g_sms[64];   // SM counts, 0 until queried
 
 std::mutex g_lut_mutex;
 bool g_lut_ready[64] = {};
@@ -444,7 +447,7 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
     {
         u128 *tp = reinterpret_cast<u128 *>(g->partials + (uint64_t)prow * kSlots);
         STEP(launch_slots(n, nnz, g->col, g->vert, g->slot, g->acc, g->owner, g->sq, g->gam[0], g->gam[1], g->gam[2],
-                          tp, blocks, g->flags, s),
+                          tp, blocks, g->flags, s, aux_streams()),
              "slot kernels");
         STEP(launch_totals(tp, slot_partial_rows(n), g->tot, s), "totals kernel");
     }
@@ -503,20 +506,70 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
         return fail(MOSS_EINVAL, "k_mask must combine (1<<4), (1<<5) and MOSS_TABLES_4MIN");
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // one scratch buffer, used first by the per-list tables then by the vertex tables
-    const uint64_t sigma_bytes = ((g->nnz * 4 + 255) & ~255ULL) + g->nnz * 8;
+    // three independent chains: the per-list tables (and MOSS-4Min's) on s,
+    // the edge hash (and filter) and the vertex tables on the caller thread's
+    // auxiliary streams when it has them; each chain has its own scratch
+    const uint64_t sigma_bytes = ((g->nnz * 4 + 255) & ~255ULL) + ((g->nnz * 8 + 255) & ~255ULL);
     const uint64_t seed_bytes = seed_scratch_bytes(g->n);
-    const uint64_t scratch_bytes = sigma_bytes > seed_bytes ? sigma_bytes : seed_bytes;
     void *scratch = nullptr;
     int rc = MOSS_OK;
     cudaError_t e;
     g->built = 0;
-    if ((e = pool_alloc(g->device, &scratch, scratch_bytes, s)) != cudaSuccess)
+    const int eff = effective_probe(g);
+    const bool want_hash = eff != MOSS_PROBE_SEARCH, want_filter = eff == MOSS_PROBE_FILTER;
+    const uint64_t buckets = hash_buckets_for(g->nnz), words = filter_words_for(g->nnz);
+    if (want_hash && buckets > (1ULL << 32)) return fail(MOSS_EOVERFLOW, "edge hash above 2^32 buckets");
+    // allocations first, on s, so that every chain may use them after the fork
+    if (want_hash && g->hash && g->hash_buckets != buckets) {
+        cudaFreeAsync(g->hash, s);
+        g->hash = nullptr;
+    }
+    if (want_hash && !g->hash) {
+        if ((e = pool_alloc(g->device, reinterpret_cast<void **>(&g->hash), buckets * 8 * kBucketKeys, s)) !=
+            cudaSuccess)
+            return cuda_fail(e, "allocating edge hash");
+        g->hash_buckets = buckets;
+    }
+    if (want_filter && g->filter && g->filter_words != words) {
+        cudaFreeAsync(g->filter, s);
+        g->filter = nullptr;
+    }
+    if (want_filter && !g->filter) {
+        if ((e = pool_alloc(g->device, reinterpret_cast<void **>(&g->filter), words * 4, s)) != cudaSuccess)
+            return cuda_fail(e, "allocating edge filter");
+        g->filter_words = words;
+    }
+    if ((e = pool_alloc(g->device, &scratch, sigma_bytes + seed_bytes, s)) != cudaSuccess)
         return cuda_fail(e, "allocating scratch");
     uint32_t *idx = static_cast<uint32_t *>(scratch);
     uint64_t *pre = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(scratch) + ((g->nnz * 4 + 255) & ~255ULL));
+    void *seed_scratch = static_cast<uint8_t *>(scratch) + sigma_bytes;
     e = cudaMemsetAsync(g->flags, 0, 2 * sizeof(uint32_t), s);
-    if (e == cudaSuccess) e = launch_sigma_alias(g->n, g->nnz, g->vert, g->acc, g->owner, g->slot, idx, pre, s);
+    const AuxStreams *aux = e == cudaSuccess ? aux_streams() : nullptr;
+    if (aux && aux->fork(s) != cudaSuccess) {
+        cudaGetLastError();
+        aux = nullptr;
+    }
+    cudaStream_t sh = aux ? aux->a[0] : s, sv = aux ? aux->a[1] : s;
+    // edge hash and filter
+    bool hashed = false, filtered = false;
+    cudaError_t eh = cudaSuccess;
+    if (e == cudaSuccess && want_hash) {
+        uint32_t lg = 0;
+        while ((1ULL << lg) < buckets) ++lg;
+        eh = cudaMemsetAsync(g->hash, 0xFF, buckets * 8 * kBucketKeys, sh);
+        if (eh == cudaSuccess)
+            eh = launch_edge_hash(g->nnz, g->col, g->owner, g->hash, (uint32_t)(buckets - 1), 64 - lg, sh);
+        hashed = eh == cudaSuccess;
+    }
+    if (e == cudaSuccess && eh == cudaSuccess && want_filter) {
+        uint32_t lf = 0;
+        while ((1ULL << lf) < words) ++lf;
+        eh = cudaMemsetAsync(g->filter, 0, words * 4, sh);
+        if (eh == cudaSuccess) eh = launch_edge_filter(g->nnz, g->col, g->owner, g->filter, 64 - lf, sh);
+        filtered = eh == cudaSuccess;
+    }
+    // vertex alias tables
     int which[3], nt = 0;
     u128 *w[3];
     uint4 *seed[3];
@@ -530,54 +583,23 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
             ++nt;
         }
     }
-    if (e == cudaSuccess && nt > 0)
-        e = launch_seed_alias(g->n, g->tot, nt, which, w, seed, vrec, scratch, g->flags, s);
-    cudaFreeAsync(scratch, s);
-    bool hashed = false, filtered = false;
-    const int eff = effective_probe(g);
-    if (e == cudaSuccess && eff != MOSS_PROBE_SEARCH) {
-        // at least 4 slots per undirected edge
-        const uint64_t buckets = hash_buckets_for(g->nnz);
-        if (buckets > (1ULL << 32)) return fail(MOSS_EOVERFLOW, "edge hash above 2^32 buckets");
-        if (g->hash && g->hash_buckets != buckets) {
-            cudaFreeAsync(g->hash, s);
-            g->hash = nullptr;
-        }
-        if (!g->hash) {
-            e = pool_alloc(g->device, reinterpret_cast<void **>(&g->hash), buckets * 8 * kBucketKeys, s);
-            if (e != cudaSuccess) return cuda_fail(e, "allocating edge hash");
-            g->hash_buckets = buckets;
-        }
-        uint32_t lg = 0;
-        while ((1ULL << lg) < buckets) ++lg;
-        e = cudaMemsetAsync(g->hash, 0xFF, buckets * 8 * kBucketKeys, s);
-        if (e == cudaSuccess)
-            e = launch_edge_hash(g->nnz, g->col, g->owner, g->hash, (uint32_t)(buckets - 1), 64 - lg, s);
-        hashed = e == cudaSuccess;
-    }
-    if (e == cudaSuccess && eff == MOSS_PROBE_FILTER) {
-        const uint64_t words = filter_words_for(g->nnz);
-        if (g->filter && g->filter_words != words) {
-            cudaFreeAsync(g->filter, s);
-            g->filter = nullptr;
-        }
-        if (!g->filter) {
-            e = pool_alloc(g->device, reinterpret_cast<void **>(&g->filter), words * 4, s);
-            if (e != cudaSuccess) return cuda_fail(e, "allocating edge filter");
-            g->filter_words = words;
-        }
-        uint32_t lf = 0;
-        while ((1ULL << lf) < words) ++lf;
-        e = cudaMemsetAsync(g->filter, 0, words * 4, s);
-        if (e == cudaSuccess) e = launch_edge_filter(g->nnz, g->col, g->owner, g->filter, 64 - lf, s);
-        filtered = e == cudaSuccess;
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "table kernels");
+    cudaError_t ev = cudaSuccess;
+    if (e == cudaSuccess && nt > 0) ev = launch_seed_alias(g->n, g->tot, nt, which, w, seed, vrec, seed_scratch, g->flags, sv);
+    // per-list tables, then MOSS-4Min's
+    if (e == cudaSuccess) e = launch_sigma_alias(g->n, g->nnz, g->vert, g->acc, g->owner, g->slot, idx, pre, s);
     bool min_built = false;
-    if (k_mask & MOSS_TABLES_4MIN) {
-        if ((rc = build_min_tables(g, s))) return rc;
-        min_built = true;
+    if (e == cudaSuccess && (k_mask & MOSS_TABLES_4MIN)) {
+        rc = build_min_tables(g, s);
+        min_built = rc == MOSS_OK;
     }
+    if (aux) {
+        const cudaError_t ej = aux->join(s);
+        if (e == cudaSuccess) e = ej;
+    }
+    cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = eh != cudaSuccess ? eh : ev;
+    if (e != cudaSuccess) return cuda_fail(e, "table kernels");
+    if (rc) return rc;
     MOSS_CUDA(cudaMemcpyAsync(&g->tot_h, g->tot, sizeof(DevTotals), cudaMemcpyDeviceToHost, s), "reading totals");
     rc = read_flags(g, s);
     if (rc) return rc;
@@ -816,6 +838,74 @@ void moss_graph_free(moss_graph *g) { release(g); }
 
 // ------------------------------------------- access for other translation units
 namespace moss {
+
+int device_sms(int device) {
+    if (device < 0 || device >= 64) return 1;
+    int v = g_sms[device].load(std::memory_order_relaxed);
+    if (v == 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v < 1) v = 1;
+        g_sms[device].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
+int current_sms() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return device_sms(dev);
+}
+
+cudaError_t AuxStreams::fork(cudaStream_t s) const {
+    cudaError_t e = cudaEventRecord(forked, s);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(a[i], forked, 0);
+    return e;
+}
+
+cudaError_t AuxStreams::join(cudaStream_t s) const {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2; ++i) {
+        cudaError_t ei = cudaEventRecord(done[i], a[i]);
+        if (ei == cudaSuccess) ei = cudaStreamWaitEvent(s, done[i], 0);
+        if (e == cudaSuccess) e = ei;
+    }
+    return e;
+}
+
+namespace {
+// per host thread and device; released when the thread exits
+struct AuxSet {
+    AuxStreams dev[64];
+    bool tried[64] = {};
+    ~AuxSet() {
+        for (auto &x : dev) {
+            for (int i = 0; i < 2; ++i) {
+                if (x.a[i]) cudaStreamDestroy(x.a[i]);
+                if (x.done[i]) cudaEventDestroy(x.done[i]);
+            }
+            if (x.forked) cudaEventDestroy(x.forked);
+        }
+    }
+};
+thread_local AuxSet t_aux;
+}  // namespace
+
+const AuxStreams *aux_streams() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return nullptr;
+    AuxStreams &x = t_aux.dev[d];
+    if (!t_aux.tried[d]) {
+        t_aux.tried[d] = true;
+        bool ok = cudaEventCreateWithFlags(&x.forked, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < 2 && ok; ++i)
+            ok = cudaStreamCreateWithFlags(&x.a[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&x.done[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            x = AuxStreams{};   // stay on the caller's stream (handles created so far are dropped)
+        }
+    }
+    return x.a[0] ? &x : nullptr;
+}
 
 int graph_info(const moss_graph *g, GraphInfo *out) {
     out->view = view(g);

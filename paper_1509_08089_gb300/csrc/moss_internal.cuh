@@ -233,13 +233,30 @@ __device__ __forceinline__ Words4 sample_words4(uint64_t seed, uint32_t t, uint6
 }
 
 // ----------------------------------------------------- host-side launches --
+// Two auxiliary streams of the calling host thread on one device, with the
+// events of one fork (both wait for what was queued on s) and one join (s
+// waits for both), for independent chains of the table build.
+struct AuxStreams {
+    cudaStream_t a[2] = {nullptr, nullptr};
+    cudaEvent_t forked = nullptr, done[2] = {nullptr, nullptr};
+    cudaError_t fork(cudaStream_t s) const;
+    cudaError_t join(cudaStream_t s) const;
+};
+// the calling thread's auxiliary streams on the current device (created on
+// first use; null when they cannot be created: callers then stay on s)
+const AuxStreams *aux_streams();
+
+// SM count of a device (of the current device), queried once per device
+int device_sms(int device);
+int current_sms();
+
 // moss_tables.cu
 cudaError_t launch_vertices(const void *row_ptr, int is64, uint32_t n, uint64_t nnz, uint4 *vert,
                             uint32_t *flags, cudaStream_t s);
 // flags[0]: kErr* bits; flags[1]: slots whose twin was matched (must reach nnz)
 cudaError_t launch_slots(uint32_t n, uint64_t nnz, const uint32_t *col, uint4 *vert, uint4 *slot, uint32_t *acc,
                          uint32_t *owner, uint64_t *sq, u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials,
-                         int blocks, uint32_t *flags, cudaStream_t s);
+                         int blocks, uint32_t *flags, cudaStream_t s, const AuxStreams *aux);
 cudaError_t launch_totals(const u128 *partials, int blocks, DevTotals *tot, cudaStream_t s);
 cudaError_t launch_edge_hash(uint64_t nnz, const uint32_t *col, const uint32_t *owner, unsigned long long *table,
                              uint32_t mask, uint32_t shift, cudaStream_t s);

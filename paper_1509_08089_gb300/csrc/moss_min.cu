@@ -434,9 +434,7 @@ __global__ void k_min_total(const u128 *partials, int blocks, DevTotals *tot) {
 }
 
 unsigned grid_for(uint64_t items, int per_block, int cap_per_sm) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = current_sms();
     uint64_t b = (items + per_block - 1) / per_block;
     const uint64_t cap = (uint64_t)sms * cap_per_sm;
     if (b > cap) b = cap;

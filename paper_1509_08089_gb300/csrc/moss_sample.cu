@@ -27,6 +27,8 @@
 //            u removed from ACC (Sec. 5.1.4).
 // RandomVertex(N_v - X) (Sec. 4.1.3) takes the j-th admissible position,
 // skipping the excluded positions of X in list order.
+#include <atomic>
+
 #include "moss_internal.cuh"
 
 namespace moss {
@@ -766,9 +768,17 @@ void upload_luts(const uint8_t *lut4, const uint8_t *lut5, const uint8_t *lutc) 
     cudaMemcpyToSymbol(g_lutc, lutc, 4096);
 }
 
+// resident blocks per SM of each sampler on each device, 0 until queried
+std::atomic<int> g_sample_per_sm[64][kMethods];
+
 int sample_blocks(int method, int device) {
-    int sms = 148, per = 1;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int sms = device_sms(device);
+    const bool cached = device >= 0 && device < 64 && method >= 0 && method < kMethods;
+    if (cached) {
+        const int c = g_sample_per_sm[device][method].load(std::memory_order_relaxed);
+        if (c > 0) return sms * c;
+    }
+    int per = 1;
     cudaError_t e = cudaSuccess;
     int per_h = 1;
     if (method == 0) {
@@ -786,6 +796,7 @@ int sample_blocks(int method, int device) {
     }
     if (e != cudaSuccess || per < 1) per = 1;
     if (per_h > per) per = per_h;   // grid sized for the faster (hash) variant
+    if (cached && e == cudaSuccess) g_sample_per_sm[device][method].store(per, std::memory_order_relaxed);
     return sms * per;
 }
 
@@ -823,9 +834,7 @@ cudaError_t launch_deferred(const DevGraph &g, uint64_t first, uint64_t count, u
 
 // blocks of a deferred stage: its resident blocks per SM times the SMs
 int defer_blocks(int device, int stage) {
-    int sms = 148;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    return sms * (stage == 1 ? defer_min_blocks<1>() : defer_min_blocks<2>());
+    return device_sms(device) * (stage == 1 ? defer_min_blocks<1>() : defer_min_blocks<2>());
 }
 
 }  // namespace
@@ -864,8 +873,8 @@ cudaError_t launch_counts(int method, const DevGraph &g, uint64_t first, uint64_
 }
 
 int batch_blocks(int device) {
-    int sms = 148, per = 1;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int sms = device_sms(device);
+    int per = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample_batch, kThreads, 0) != cudaSuccess || per < 1)
         per = 1;
     return sms * per;

@@ -269,7 +269,9 @@ __global__ void k_twin(uint32_t n, uint64_t nnz, const uint4 *__restrict__ vert,
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t v = owner[p], x = col[p];
         if (x >= n || x == v) continue;  // flagged by the slot pass
-        const uint4 vr = vert[v], xr = vert[x];
+        // {off, deg} only: k_slots may be writing S_v into the same records
+        const uint2 vr = reinterpret_cast<const uint2 *>(vert)[2 * (uint64_t)v];
+        const uint2 xr = reinterpret_cast<const uint2 *>(vert)[2 * (uint64_t)x];
         const bool mine = vr.y > xr.y || (vr.y == xr.y && v < x);
         if (!mine) continue;
         uint32_t lo = xr.x, len = xr.y;
@@ -761,9 +763,7 @@ __global__ void k_seed_fill(uint32_t n, const DevTotals *tot, SeedTasks tasks) {
 
 // ------------------------------------------------------------- launches ---
 int table_blocks(uint32_t n) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = current_sms();
     const uint64_t warps_needed = (uint64_t)n;
     uint64_t blocks = (warps_needed + (kTableThreads / kWarp) - 1) / (kTableThreads / kWarp);
     const uint64_t cap = (uint64_t)sms * 8;
@@ -791,17 +791,13 @@ static unsigned long_blocks(uint32_t n);
 int slot_partial_rows(uint32_t n) { return table_blocks(n) + (int)long_blocks(n); }
 
 static unsigned long_blocks(uint32_t n) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = current_sms();
     const uint64_t cap = (uint64_t)sms * 4, chunks = ((uint64_t)n + kLongThreads - 1) / kLongThreads;
     return (unsigned)(chunks < cap ? (chunks ? chunks : 1) : cap);
 }
 
 static unsigned flat_blocks(uint64_t items) {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = current_sms();
     uint64_t b = (items + 255) / 256;
     const uint64_t cap = (uint64_t)sms * 16;
     if (b > cap) b = cap;
@@ -810,7 +806,7 @@ static unsigned flat_blocks(uint64_t items) {
 
 cudaError_t launch_slots(uint32_t n, uint64_t nnz, const uint32_t *col, uint4 *vert, uint4 *slot, uint32_t *acc,
                          uint32_t *owner, uint64_t *sq, u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials,
-                         int blocks, uint32_t *flags, cudaStream_t s) {
+                         int blocks, uint32_t *flags, cudaStream_t s, const AuxStreams *aux) {
     k_owner<<<blocks, kTableThreads, 0, s>>>(n, vert, owner);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -818,14 +814,24 @@ cudaError_t launch_slots(uint32_t n, uint64_t nnz, const uint32_t *col, uint4 *v
         k_slot_weights<<<flat_blocks(nnz), 256, 0, s>>>(n, nnz, col, vert, owner, slot, acc, flags);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    // the twin pass touches none of what the list scans write: it runs beside them
+    cudaStream_t ts = s;
+    if (nnz && aux && (e = aux->fork(s)) == cudaSuccess) ts = aux->a[0];
+    if (e != cudaSuccess) return e;
+    if (nnz) k_twin<<<flat_blocks(nnz), 256, 0, ts>>>(n, nnz, vert, col, owner, slot, flags);
+    cudaError_t et = cudaGetLastError();
     k_slots<<<blocks, kTableThreads, 0, s>>>(n, vert, acc, sq, gam0, gam1, gam2, partials);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_slots_long<<<long_blocks(n), kLongThreads, 0, s>>>(n, vert, acc, sq, gam0, gam1, gam2,
-                                                         partials + (uint64_t)blocks * 6);
     e = cudaGetLastError();
-    if (e != cudaSuccess || nnz == 0) return e;
-    k_twin<<<flat_blocks(nnz), 256, 0, s>>>(n, nnz, vert, col, owner, slot, flags);
-    return cudaGetLastError();
+    if (e == cudaSuccess) {
+        k_slots_long<<<long_blocks(n), kLongThreads, 0, s>>>(n, vert, acc, sq, gam0, gam1, gam2,
+                                                             partials + (uint64_t)blocks * 6);
+        e = cudaGetLastError();
+    }
+    if (ts != s) {
+        const cudaError_t ej = aux->join(s);
+        if (e == cudaSuccess) e = ej;
+    }
+    return e != cudaSuccess ? e : et;
 }
 
 cudaError_t launch_totals(const u128 *partials, int blocks, DevTotals *tot, cudaStream_t s) {
