@@ -506,9 +506,12 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
         return fail(MOSS_EINVAL, "k_mask must combine (1<<4), (1<<5) and MOSS_TABLES_4MIN");
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // three independent chains: the per-list tables (and MOSS-4Min's) on s,
-    // the edge hash (and filter) and the vertex tables on the caller thread's
-    // auxiliary streams when it has them; each chain has its own scratch
+    // independent chains on s and the caller thread's auxiliary streams (when
+    // it has them), each with its own scratch: the per-list tables on s, the
+    // vertex tables on the second auxiliary stream, the edge hash (and
+    // filter) on the first -- or, when the MOSS-4Min tables are built (the
+    // longest chain), those on the first and the edge hash after the
+    // per-list tables on s
     const uint64_t sigma_bytes = ((g->nnz * 4 + 255) & ~255ULL) + ((g->nnz * 8 + 255) & ~255ULL);
     const uint64_t seed_bytes = seed_scratch_bytes(g->n);
     void *scratch = nullptr;
@@ -550,7 +553,33 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
         cudaGetLastError();
         aux = nullptr;
     }
-    cudaStream_t sh = aux ? aux->a[0] : s, sv = aux ? aux->a[1] : s;
+    const bool want_min = (k_mask & MOSS_TABLES_4MIN) != 0;
+    cudaStream_t sv = aux ? aux->a[1] : s, sm = aux ? aux->a[0] : s, sh = aux && !want_min ? aux->a[0] : s;
+    // MOSS-4Min tables
+    bool min_built = false;
+    if (e == cudaSuccess && want_min) {
+        rc = build_min_tables(g, sm);
+        min_built = rc == MOSS_OK;
+    }
+    // vertex alias tables
+    int which[3], nt = 0;
+    u128 *w[3];
+    uint4 *seed[3];
+    const uint4 *vrec[3] = {g->vert, g->vert, g->vert};
+    for (int l = 0; l < 3; ++l) {
+        const bool want = (l == 0 && (k_mask & (1u << 4))) || (l > 0 && (k_mask & (1u << 5)));
+        if (want) {
+            which[nt] = l;
+            w[nt] = g->gam[l];
+            seed[nt] = g->seed[l];
+            ++nt;
+        }
+    }
+    cudaError_t ev = cudaSuccess;
+    if (e == cudaSuccess && nt > 0)
+        ev = launch_seed_alias(g->n, g->tot, nt, which, w, seed, vrec, seed_scratch, g->flags, sv);
+    // per-list tables
+    if (e == cudaSuccess) e = launch_sigma_alias(g->n, g->nnz, g->vert, g->acc, g->owner, g->slot, idx, pre, s);
     // edge hash and filter
     bool hashed = false, filtered = false;
     cudaError_t eh = cudaSuccess;
@@ -568,29 +597,6 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
         eh = cudaMemsetAsync(g->filter, 0, words * 4, sh);
         if (eh == cudaSuccess) eh = launch_edge_filter(g->nnz, g->col, g->owner, g->filter, 64 - lf, sh);
         filtered = eh == cudaSuccess;
-    }
-    // vertex alias tables
-    int which[3], nt = 0;
-    u128 *w[3];
-    uint4 *seed[3];
-    const uint4 *vrec[3] = {g->vert, g->vert, g->vert};
-    for (int l = 0; l < 3; ++l) {
-        const bool want = (l == 0 && (k_mask & (1u << 4))) || (l > 0 && (k_mask & (1u << 5)));
-        if (want) {
-            which[nt] = l;
-            w[nt] = g->gam[l];
-            seed[nt] = g->seed[l];
-            ++nt;
-        }
-    }
-    cudaError_t ev = cudaSuccess;
-    if (e == cudaSuccess && nt > 0) ev = launch_seed_alias(g->n, g->tot, nt, which, w, seed, vrec, seed_scratch, g->flags, sv);
-    // per-list tables, then MOSS-4Min's
-    if (e == cudaSuccess) e = launch_sigma_alias(g->n, g->nnz, g->vert, g->acc, g->owner, g->slot, idx, pre, s);
-    bool min_built = false;
-    if (e == cudaSuccess && (k_mask & MOSS_TABLES_4MIN)) {
-        rc = build_min_tables(g, s);
-        min_built = rc == MOSS_OK;
     }
     if (aux) {
         const cudaError_t ej = aux->join(s);
