@@ -245,6 +245,12 @@ typedef struct moss_batch moss_batch;
 int moss_batch_create(int device, moss_batch **out);
 /* Append a request; *index (nullable) receives its position in the results. */
 int moss_batch_add(moss_batch *b, moss_graph *g, int k, uint64_t budget, uint64_t seed, int *index);
+/* Append a MOSS-4 + MOSS-4Min request (the mix of Sec. 4.2, Theorem 1):
+ * budget MOSS-4 samples and budget_min MOSS-4Min samples, finalized as
+ * moss_sample_estimate_min is, whose result it equals.  The graph needs the
+ * k = 4 tables and MOSS_TABLES_4MIN (MOSS_ESTATE otherwise). */
+int moss_batch_add_min(moss_batch *b, moss_graph *g, uint64_t budget, uint64_t budget_min, uint64_t seed,
+                       int *index);
 int moss_batch_size(const moss_batch *b);
 int moss_batch_clear(moss_batch *b);
 /* Samples per tile (32 .. 2^30; default 8192). */
@@ -303,6 +309,12 @@ int moss_server_add_graph(moss_server *s, moss_graph *g, int *graph_id);
 /* budget > 0: fixed budget; budget == 0: derive it from target_rse. */
 int moss_server_submit(moss_server *s, int graph_id, int k, uint64_t budget, double target_rse, uint64_t seed,
                        uint64_t *request_id);
+/* Submit a MOSS-4 + MOSS-4Min request with explicit budgets (budget MOSS-4,
+ * budget_min MOSS-4Min samples); its result equals moss_sample_estimate_min
+ * on the same graph and seed.  The graph needs the k = 4 tables and
+ * MOSS_TABLES_4MIN (MOSS_ESTATE otherwise). */
+int moss_server_submit_min(moss_server *s, int graph_id, uint64_t budget, uint64_t budget_min, uint64_t seed,
+                           uint64_t *request_id);
 /* Block until the request finishes (MOSS_EBUSY after timeout_s); out and
  * stats are nullable.  A request can be waited for once. */
 int moss_server_wait(moss_server *s, uint64_t request_id, double timeout_s, moss_result *out,

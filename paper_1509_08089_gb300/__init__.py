@@ -106,6 +106,7 @@ def load():
         "moss_version": ([], ctypes.c_char_p),
         "moss_batch_create": ([ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
         "moss_batch_add": ([_vp, _vp, ctypes.c_int, _u64, _u64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "moss_batch_add_min": ([_vp, _vp, _u64, _u64, _u64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "moss_batch_size": ([_vp], ctypes.c_int),
         "moss_batch_clear": ([_vp], ctypes.c_int),
         "moss_batch_set_tile": ([_vp, ctypes.c_uint32], ctypes.c_int),
@@ -118,6 +119,8 @@ def load():
         "moss_server_add_graph": ([_vp, _vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "moss_server_submit": ([_vp, ctypes.c_int, ctypes.c_int, _u64, ctypes.c_double, _u64,
                                 ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "moss_server_submit_min": ([_vp, ctypes.c_int, _u64, _u64, _u64, ctypes.POINTER(ctypes.c_uint64)],
+                                   ctypes.c_int),
         "moss_server_wait": ([_vp, _u64, ctypes.c_double, ctypes.POINTER(moss_result),
                               ctypes.POINTER(moss_request_stats)], ctypes.c_int),
         "moss_server_stats": ([_vp, ctypes.POINTER(moss_server_info)], ctypes.c_int),
@@ -289,6 +292,12 @@ def moss_batch_add(b: int, g: int, k: int, budget: int, seed: int) -> int:
     return idx.value
 
 
+def moss_batch_add_min(b: int, g: int, budget: int, budget_min: int, seed: int) -> int:
+    idx = ctypes.c_int(-1)
+    _check(load().moss_batch_add_min(b, g, budget, budget_min, seed, ctypes.byref(idx)))
+    return idx.value
+
+
 def moss_batch_size(b: int) -> int:
     return load().moss_batch_size(b)
 
@@ -347,6 +356,12 @@ def moss_server_submit(s: int, graph_id: int, k: int, budget: int = 0, target_rs
     return rid.value
 
 
+def moss_server_submit_min(s: int, graph_id: int, budget: int, budget_min: int, seed: int = 1) -> int:
+    rid = ctypes.c_uint64(0)
+    _check(load().moss_server_submit_min(s, graph_id, budget, budget_min, seed, ctypes.byref(rid)))
+    return rid.value
+
+
 def moss_server_wait(s: int, request_id: int, timeout_s: float = 600.0):
     r = moss_result()
     st = moss_request_stats()
@@ -385,6 +400,9 @@ class Server:
 
     def submit(self, graph_id: int, k: int, budget: int = 0, target_rse: float = 0.0, seed: int = 1) -> int:
         return moss_server_submit(self.handle, graph_id, k, budget, target_rse, seed)
+
+    def submit_min(self, graph_id: int, budget: int, budget_min: int, seed: int = 1) -> int:
+        return moss_server_submit_min(self.handle, graph_id, budget, budget_min, seed)
 
     def wait(self, request_id: int, timeout_s: float = 600.0):
         r, st = moss_server_wait(self.handle, request_id, timeout_s)
@@ -431,6 +449,9 @@ class Batch:
 
     def add(self, graph: "Graph", k: int, budget: int, seed: int) -> int:
         return moss_batch_add(self.handle, graph.handle, k, budget, seed)
+
+    def add_min(self, graph: "Graph", budget: int, budget_min: int, seed: int) -> int:
+        return moss_batch_add_min(self.handle, graph.handle, budget, budget_min, seed)
 
     def run(self, stream=None) -> list[dict]:
         return [result_dict(r) for r in moss_batch_run(self.handle, stream)]

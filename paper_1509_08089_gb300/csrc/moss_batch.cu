@@ -2,8 +2,9 @@
 // persistent launch.
 //
 // A batch is a list of requests (graph, k, budget, seed).  Each request
-// becomes one task per sub-method (MOSS-4; or T-5 and Path-5 with
-// K1 = floor(B/2), K2 = B - K1 as in moss_sample_estimate), each task a run
+// becomes one task per sub-method (MOSS-4; T-5 and Path-5 with K1 =
+// floor(B/2), K2 = B - K1 as in moss_sample_estimate; or MOSS-4 and
+// MOSS-4Min with K and K-check as in moss_sample_estimate_min), each task a run
 // of tiles of `tile` sample ids.  One persistent kernel drains the tile list
 // through a device counter; per-tile counts are summed per task in tile order
 // and finalized per request on the device.  Since every sample is keyed by
@@ -30,6 +31,8 @@ struct Req {
     moss_graph *g;
     int k;
     uint64_t budget, seed;
+    bool mix;              // MOSS-4 with MOSS-4Min (k = 4)
+    uint64_t budget_min;   // K-check of the mix
 };
 
 template <typename T>
@@ -102,6 +105,7 @@ int plan(moss_batch *b) {
         const bool sigma = (gi.built >> 3) & 1u;
         BatchRequest &br = reqs[r];
         br.in.k = q.k;
+        br.in.mix = q.mix ? 1 : 0;
         br.in.K[0] = br.in.K[1] = 0;
         br.tot = gi.tot;
         br.task[0] = br.task[1] = -1;
@@ -110,6 +114,10 @@ int plan(moss_batch *b) {
         if (q.k == 4) {
             methods[nm] = 0;
             Ks[nm++] = gi.total_nonzero[0] ? q.budget : 0;
+            if (q.mix) {
+                methods[nm] = 3;
+                Ks[nm++] = gi.total_nonzero[3] ? q.budget_min : 0;
+            }
         } else {
             methods[nm] = 1;
             Ks[nm++] = gi.total_nonzero[1] ? q.budget / 2 : 0;
@@ -118,7 +126,8 @@ int plan(moss_batch *b) {
         }
         for (int j = 0; j < nm; ++j) {
             const int m = methods[j];
-            if (!sigma || !((gi.built >> m) & 1u)) return set_error(MOSS_ESTATE, "tables of a batched graph not built");
+            const unsigned bit = m == 3 ? 5u : (unsigned)m;   // MOSS-4Min tables: bit 5
+            if (!sigma || !((gi.built >> bit) & 1u)) return set_error(MOSS_ESTATE, "tables of a batched graph not built");
             br.in.K[j] = Ks[j];
             if (Ks[j] == 0) continue;
             BatchTask t;
@@ -247,7 +256,20 @@ int moss_batch_add(moss_batch *b, moss_graph *g, int k, uint64_t budget, uint64_
     if (gi.device != b->device) return set_error(MOSS_EINVAL, "graph lives on another device than the batch");
     const unsigned need = (1u << 3) | (k == 4 ? 1u : 6u);
     if ((gi.built & need) != need) return set_error(MOSS_ESTATE, "tables for this k are not built");
-    b->reqs.push_back(Req{g, k, budget, seed});
+    b->reqs.push_back(Req{g, k, budget, seed, false, 0});
+    if (index) *index = (int)b->reqs.size() - 1;
+    b->dirty = true;
+    return MOSS_OK;
+}
+
+int moss_batch_add_min(moss_batch *b, moss_graph *g, uint64_t budget, uint64_t budget_min, uint64_t seed, int *index) {
+    if (!b || !g) return set_error(MOSS_EINVAL, "NULL argument");
+    GraphInfo gi;
+    graph_info(g, &gi);
+    if (gi.device != b->device) return set_error(MOSS_EINVAL, "graph lives on another device than the batch");
+    const unsigned need = (1u << 3) | 1u | (1u << 5);
+    if ((gi.built & need) != need) return set_error(MOSS_ESTATE, "MOSS-4 and MOSS-4Min tables are not built");
+    b->reqs.push_back(Req{g, 4, budget, seed, true, budget_min});
     if (index) *index = (int)b->reqs.size() - 1;
     b->dirty = true;
     return MOSS_OK;

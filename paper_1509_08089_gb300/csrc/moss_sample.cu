@@ -663,11 +663,17 @@ __global__ void __launch_bounds__(kThreads, defer_min_blocks<STAGE>())
 // warp ran which tile, and equal the counts of a solo launch of the task.
 constexpr int kBatchBlocks = 4;   // resident blocks per SM (Path-5 bound)
 
+// the count slot of sample s of a method: its class, or for MOSS-4Min its
+// (class, c) slot
 template <bool HASH>
-__device__ __forceinline__ int sample_any(const DevGraph &g, const uint8_t *lut4, const uint8_t *lut5, uint32_t method,
-                                          uint64_t seed, uint64_t s) {
+__device__ __forceinline__ int sample_any(const DevGraph &g, const uint8_t *lut4, const uint8_t *lut5,
+                                          const uint8_t *lutc, uint32_t method, uint64_t seed, uint64_t s) {
     if (method == 0) return sample_moss4<HASH>(g, lut4, seed, s).cls;
     if (method == 1) return sample_t5<HASH>(g, lut5, seed, s).cls;
+    if (method == 3) {
+        const Sample sm = sample_min<HASH>(g, lut4, lutc, seed, s);
+        return min_slot(sm.cls, sm.v[4]);
+    }
     return sample_path5<HASH, 3>(g, lut5, seed, s).cls;
 }
 
@@ -676,12 +682,14 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocks)
                    unsigned long long *next_tile, uint32_t *tile_counts) {
     __shared__ uint8_t lut4[64];
     __shared__ uint8_t lut5[kLut];
+    __shared__ uint8_t lutc[4096];
     __shared__ uint32_t hist[kWarps][kSlots];
     __shared__ DevGraph gsh[kWarps];
     static_assert(sizeof(DevGraph) % 4 == 0 && sizeof(DevGraph) / 4 <= 64, "graph descriptor staging");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < 64; i += kThreads) lut4[i] = g_lut4[i];
     for (int i = threadIdx.x; i < kLut; i += kThreads) lut5[i] = g_lut5[i];
+    for (int i = threadIdx.x; i < 4096; i += kThreads) lutc[i] = g_lutc[i];
     __syncthreads();
     for (;;) {
         unsigned long long t = 0;
@@ -708,8 +716,8 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocks)
             const uint32_t i = base + lane;
             int cls = kSlots;
             if (i < cnt)
-                cls = hashed ? sample_any<true>(g, lut4, lut5, tk.method, tk.seed, f + i)
-                             : sample_any<false>(g, lut4, lut5, tk.method, tk.seed, f + i);
+                cls = hashed ? sample_any<true>(g, lut4, lut5, lutc, tk.method, tk.seed, f + i)
+                             : sample_any<false>(g, lut4, lut5, lutc, tk.method, tk.seed, f + i);
             const uint32_t peers = __match_any_sync(0xffffffffu, cls);
             if (cls < kSlots && lane == __ffs(peers) - 1) atomicAdd(&hist[warp][cls], (uint32_t)__popc(peers));
         }

@@ -46,6 +46,7 @@ double now_s() {
 struct SReq {
     uint64_t id = 0;
     int graph = 0, k = 4;
+    bool mix = false;            // MOSS-4 with MOSS-4Min (k = 4, explicit budgets)
     double target = 0;
     uint64_t seed = 0;
     bool pilot = false;          // budget still to be derived from the first chunk
@@ -82,8 +83,17 @@ cudaError_t grow_host(T **p, size_t *cap, size_t need) {
     return e;
 }
 
-// sub-methods of a request: (method, budget share)
-int sub_methods(int k, uint64_t budget, const bool nonzero[3], int m[2], uint64_t K[2]) {
+// sub-methods of a request: (method, budget share); the mix draws budget
+// MOSS-4 and budget_min MOSS-4Min samples
+int sub_methods(int k, bool mix, uint64_t budget, uint64_t budget_min, const bool nonzero[kMethods], int m[2],
+                uint64_t K[2]) {
+    if (mix) {
+        m[0] = 0;
+        m[1] = 3;
+        K[0] = nonzero[0] ? budget : 0;
+        K[1] = nonzero[3] ? budget_min : 0;
+        return 2;
+    }
     if (k == 4) {
         m[0] = 0;
         K[0] = nonzero[0] ? budget : 0;
@@ -215,6 +225,7 @@ int finalize(moss_server *s, const std::vector<SReq *> &fin) {
     for (size_t i = 0; i < n; ++i) {
         const SReq &q = *fin[i];
         br[i].in.k = q.k;
+        br[i].in.mix = q.mix ? 1 : 0;
         br[i].in.K[0] = q.K[0];
         br[i].in.K[1] = q.K[1];
         br[i].tot = s->ginfo[q.graph].tot;
@@ -279,7 +290,7 @@ void scheduler(moss_server *s) {
                 SReq &q = s->reqs[id];
                 int m[2];
                 uint64_t Kdummy[2];
-                const int nsub = sub_methods(q.k, 0, s->ginfo[q.graph].total_nonzero, m, Kdummy);
+                const int nsub = sub_methods(q.k, q.mix, 0, 0, s->ginfo[q.graph].total_nonzero, m, Kdummy);
                 for (int j = 0; j < nsub; ++j) {
                     if (q.next[j] >= q.K[j]) continue;
                     const uint64_t c = std::min(share, q.K[j] - q.next[j]);
@@ -330,7 +341,7 @@ void scheduler(moss_server *s) {
                     q.budget = b;
                     int m[2];
                     uint64_t K[2];
-                    sub_methods(q.k, b, s->ginfo[q.graph].total_nonzero, m, K);
+                    sub_methods(q.k, false, b, 0, s->ginfo[q.graph].total_nonzero, m, K);
                     q.K[0] = K[0];
                     q.K[1] = K[1];
                     if (q.done[0] < q.K[0] || q.done[1] < q.K[1]) {
@@ -443,11 +454,45 @@ int moss_server_submit(moss_server *s, int graph_id, int k, uint64_t budget, dou
     int m[2];
     if (budget) {
         q.budget = budget;
-        sub_methods(k, budget, s->ginfo[graph_id].total_nonzero, m, q.K);
+        sub_methods(k, false, budget, 0, s->ginfo[graph_id].total_nonzero, m, q.K);
     } else {
         q.pilot = true;
-        sub_methods(k, s->cfg.pilot_samples, s->ginfo[graph_id].total_nonzero, m, q.K);
+        sub_methods(k, false, s->cfg.pilot_samples, 0, s->ginfo[graph_id].total_nonzero, m, q.K);
     }
+    const uint64_t id = q.id;
+    s->reqs.emplace(id, q);
+    s->pending.push_back(id);
+    if (request_id) *request_id = id;
+    lk.unlock();
+    s->cv_work.notify_one();
+    return MOSS_OK;
+}
+
+int moss_server_submit_min(moss_server *s, int graph_id, uint64_t budget, uint64_t budget_min, uint64_t seed,
+                           uint64_t *request_id) {
+    if (!s) return set_error(MOSS_EINVAL, "NULL server");
+    if (budget == 0 && budget_min == 0) return set_error(MOSS_EINVAL, "give the MOSS-4 or MOSS-4Min budget");
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->status != MOSS_OK) return set_error(s->status, "the server stopped after an error");
+    if (graph_id < 0 || graph_id >= (int)s->graphs.size()) return set_error(MOSS_EINVAL, "unknown graph id");
+    const unsigned need = (1u << 3) | 1u | (1u << 5);
+    if ((s->ginfo[graph_id].built & need) != need)
+        return set_error(MOSS_ESTATE, "MOSS-4 and MOSS-4Min tables of this graph are not built");
+    if (!s->started) {
+        s->started = true;
+        s->worker = std::thread(scheduler, s);
+    }
+    SReq q;
+    q.id = s->next_id++;
+    q.graph = graph_id;
+    q.k = 4;
+    q.mix = true;
+    q.seed = seed;
+    q.t_arrive = now_s();
+    if (s->first_submit == 0) s->first_submit = q.t_arrive;
+    int m[2];
+    q.budget = budget + budget_min;
+    sub_methods(4, true, budget, budget_min, s->ginfo[graph_id].total_nonzero, m, q.K);
     const uint64_t id = q.id;
     s->reqs.emplace(id, q);
     s->pending.push_back(id);

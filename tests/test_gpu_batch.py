@@ -107,12 +107,46 @@ def test_batch_against_oracle(fleet):
     assert res[3]["est"][1] == pytest.approx(9.0)   # cycle C_9: eta_1 = 9 exactly
 
 
+def test_batch_min_requests_equal_solo_runs():
+    """MOSS-4 + MOSS-4Min requests, mixed with plain k = 4 and 5 requests in
+    one batch, equal moss_sample_estimate_min (and the oracle's counts)."""
+    mask = (1 << 4) | (1 << 5) | moss.TABLES_4MIN
+    csrs = uneven_graphs(6, 5) + [synth.complete(7)]
+    graphs = [moss.Graph(rp, col, k_mask=mask) for rp, col in csrs]
+    try:
+        picks = [(i, 20_000 + 1_000 * i, 15_000 + 700 * i, 31 + i) for i in range(len(graphs))]
+        with moss.Batch() as batch:
+            for gi, K, Km, seed in picks:
+                batch.add_min(graphs[gi], K, Km, seed)
+                batch.add(graphs[gi], 5, K, seed)
+            res = batch.run()
+            for tile in (100, 4096):
+                batch.set_tile(tile)
+                for a, b in zip(res, batch.run()):
+                    same(a, b)
+        for j, (gi, K, Km, seed) in enumerate(picks):
+            r = res[2 * j]
+            same(r, graphs[gi].estimate_min(K, Km, seed))
+            assert np.array_equal(r["lam"], graphs[gi].estimate_min(K, Km, seed)["lam"])
+            same(res[2 * j + 1], graphs[gi].estimate(5, K, seed))
+        og = oracle.OracleGraph(*csrs[0])
+        og.build_min()
+        gi, K, Km, seed = picks[0]
+        assert np.array_equal(res[0]["hits"][1], og.run(oracle.MOSS4MIN, seed, Km))
+    finally:
+        for g in graphs:
+            g.close()
+
+
 def test_batch_rejects_unbuilt_graph_and_handles_empty():
     rp, col = synth.cycle(10)
     with moss.Graph(rp, col, k_mask=1 << 4) as g, moss.Batch() as batch:
         assert batch.run() == []
         with pytest.raises(moss.MossError) as ei:
             batch.add(g, 5, 100, 1)
+        assert ei.value.status == moss.MOSS_ESTATE
+        with pytest.raises(moss.MossError) as ei:
+            batch.add_min(g, 100, 100, 1)
         assert ei.value.status == moss.MOSS_ESTATE
         batch.add(g, 4, 100, 1)
         assert batch.run()[0]["est"][1] == pytest.approx(10.0)

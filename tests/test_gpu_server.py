@@ -71,6 +71,35 @@ def test_server_results_equal_solo_runs(pool, cfg):
         assert st["latency_s"] >= st["queue_s"] >= 0.0
 
 
+def test_server_min_requests_equal_solo_runs():
+    """MOSS-4 + MOSS-4Min requests served among plain ones equal
+    moss_sample_estimate_min with the same budgets and seed."""
+    mask = (1 << 4) | (1 << 5) | moss.TABLES_4MIN
+    csrs = [synth.chung_lu(2500, 2.3, 8.0, 60.0, seed=7), synth.rgg(3000, 12.0, seed=8)]
+    graphs = [moss.Graph(rp, col, k_mask=mask) for rp, col in csrs]
+    try:
+        with moss.Server(max_active=8, tick_samples=300_000, tile_samples=1024) as server:
+            gids = [server.add_graph(g) for g in graphs]
+            subs = []
+            for j in range(6):
+                gi = j % 2
+                K, Km, seed = 40_000 + 9_000 * j, 30_000 + 7_000 * j, 100 + j
+                subs.append(("min", gi, (K, Km, seed), server.submit_min(gids[gi], K, Km, seed=seed)))
+                subs.append(("k5", gi, (K, seed), server.submit(gids[gi], 5, budget=K, seed=seed)))
+            for kind, gi, args, rid in subs:
+                r, st = server.wait(rid)
+                solo = graphs[gi].estimate_min(*args) if kind == "min" else graphs[gi].estimate(5, *args)
+                assert tuple(r["K"]) == tuple(solo["K"])
+                assert np.array_equal(r["hits"], solo["hits"])
+                assert np.array_equal(r["est"], solo["est"])
+                assert np.array_equal(r["var"], solo["var"])
+            with pytest.raises(moss.MossError):
+                server.submit_min(gids[0], 0, 0)
+    finally:
+        for g in graphs:
+            g.close()
+
+
 def test_target_budget_meets_target(pool):
     with moss.Server(min_budget=1_000, max_budget=50_000_000, pilot_samples=50_000) as server:
         gid = server.add_graph(pool[2])
@@ -91,6 +120,9 @@ def test_server_rejects_bad_requests(pool):
             server.submit(gid + 5, 4, budget=100)
         with pytest.raises(moss.MossError):
             server.submit(gid, 4)          # neither budget nor target
+        with pytest.raises(moss.MossError) as ei:
+            server.submit_min(gid, 100, 100)   # MOSS-4Min tables not built
+        assert ei.value.status == moss.MOSS_ESTATE
         rid = server.submit(gid, 4, budget=10_000, seed=1)
         server.wait(rid)
         with pytest.raises(moss.MossError):
