@@ -119,6 +119,8 @@ def oracle_rate(build, sample_wall, samples, budget):
 
 
 def calibrate_per_worker(workload, k, seed, seconds, mix=False):
+    """Samples per worker process for about `seconds` of sampling, and the
+    oracle's sampling rate on one core (samples/s) measured on the way."""
     import oracle
     import synth
     rp, col = synth.workload(workload)
@@ -131,7 +133,7 @@ def calibrate_per_worker(workload, k, seed, seconds, mix=False):
     for m in methods:
         g.run(m, seed, n // len(methods))
     per = (time.perf_counter() - t0) / n
-    return max(len(methods), int(seconds / per))
+    return max(len(methods), int(seconds / per)), 1.0 / per
 
 
 def make_pool(cores):
@@ -149,7 +151,7 @@ def run_reference(args):
         args.k = 4
     METRIC, WORKLOAD = describe(args.workload, args.k, mix)
     cores = os.cpu_count() or 1
-    per_worker = calibrate_per_worker(args.workload, args.k, args.seed, 3.0, mix)
+    per_worker, single = calibrate_per_worker(args.workload, args.k, args.seed, 3.0, mix)
     with make_pool(cores) as pool:
         for _ in range(args.warmup):
             oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker, mix)
@@ -167,7 +169,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * args.budget / v,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "budget": args.budget, "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle", "sample": sample,
+                         "single_core_sampling_rate": single},
         "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -456,7 +459,7 @@ def run_gpu(args):
         "step_ms": step_ms,
     }
     if pool is not None:
-        per_worker = calibrate_per_worker(args.workload, k, args.seed, 12.0, mix)
+        per_worker, single = calibrate_per_worker(args.workload, k, args.seed, 12.0, mix)
         b, sw, n, wall = oracle_pass(pool, cores, args.workload, k, args.seed, per_worker, mix)
         v, rate = oracle_rate(b, sw, n, args.budget)
         pool.shutdown()
@@ -464,7 +467,7 @@ def run_gpu(args):
             "value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
             "sample": (f"{n} samples ({'T-5/Path-5 evenly' if k == 5 else ('MOSS-4/MOSS-4Min evenly' if mix else 'MOSS-4')}) over {cores} processes in "
                        f"{sw:.1f} s + table build {b:.2f} s, extrapolated to the {args.budget}-sample budget"),
-            "sampling_rate": rate}
+            "sampling_rate": rate, "single_core_sampling_rate": single}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
