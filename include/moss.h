@@ -387,6 +387,16 @@ int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t b
 
 void moss_graph_free(moss_graph *g);
 
+/* The library's classification tables (host only, no GPU needed; any
+ * pointer may be NULL): class4[64] and class5[1024] map an edge mask over
+ * the sampled roles (pair bits (0,1),(0,2),...) to its class M_i (Sec. 4.1.2,
+ * Table 2; 0 when disconnected); centred[4096] holds c(s) of MOSS-4Min
+ * (Sec. 4.2: the 3-paths p0-p1-p2-p3 with p0 above p2 and p3 above p1, each
+ * once) at index mask << 6 | order, order bit b set when the first role of
+ * pair b is above the second, and 0 for classes other than 4-cycle, diamond
+ * and 4-clique. */
+int moss_class_tables(uint8_t *class4, uint8_t *class5, uint8_t *centred);
+
 const char *moss_strerror(int status);
 const char *moss_last_error_detail(void);
 const char *moss_version(void);

@@ -104,6 +104,7 @@ def load():
         "moss_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "moss_last_error_detail": ([], ctypes.c_char_p),
         "moss_version": ([], ctypes.c_char_p),
+        "moss_class_tables": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
         "moss_batch_create": ([ctypes.c_int, ctypes.POINTER(_vp)], ctypes.c_int),
         "moss_batch_add": ([_vp, _vp, ctypes.c_int, _u64, _u64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "moss_batch_add_min": ([_vp, _vp, _u64, _u64, _u64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -174,6 +175,15 @@ def _stream(stream, device: int | None = None) -> int | None:
 # ------------------------------------------------------------ C ABI calls --
 def moss_version() -> str:
     return load().moss_version().decode()
+
+
+def moss_class_tables():
+    """(class4[64], class5[1024], centred[4096]) as uint8 arrays (host only)."""
+    c4 = np.zeros(64, dtype=np.uint8)
+    c5 = np.zeros(1024, dtype=np.uint8)
+    cc = np.zeros(4096, dtype=np.uint8)
+    _check(load().moss_class_tables(c4.ctypes.data, c5.ctypes.data, cc.ctypes.data))
+    return c4, c5, cc
 
 
 def moss_strerror(status: int) -> str:

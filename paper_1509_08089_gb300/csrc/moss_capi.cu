@@ -159,8 +159,8 @@ bool g_lut_ready[64] = {};
 uint8_t g_lut4_h[64], g_lut5_h[1024], g_lutc_h[4096];
 bool g_lut_built = false;
 
-int ensure_luts(int device) {
-    std::lock_guard<std::mutex> lk(g_lut_mutex);
+// the host copies of the tables (callers hold g_lut_mutex)
+void build_host_luts() {
     if (!g_lut_built) {
         for (uint32_t m = 0; m < 64; ++m) g_lut4_h[m] = (uint8_t)mask_class(4, m);
         for (uint32_t m = 0; m < 1024; ++m) g_lut5_h[m] = (uint8_t)mask_class(5, m);
@@ -170,6 +170,11 @@ int ensure_luts(int device) {
         }
         g_lut_built = true;
     }
+}
+
+int ensure_luts(int device) {
+    std::lock_guard<std::mutex> lk(g_lut_mutex);
+    build_host_luts();
     if (device < 0 || device >= 64) return fail(MOSS_EINVAL, "device ordinal %d out of range", device);
     if (!g_lut_ready[device]) {
         upload_luts(g_lut4_h, g_lut5_h, g_lutc_h);
@@ -353,6 +358,15 @@ bool method_ready(const moss_graph *g, int method) {
 }  // namespace
 
 extern "C" {
+
+int moss_class_tables(uint8_t *class4, uint8_t *class5, uint8_t *centred) {
+    std::lock_guard<std::mutex> lk(g_lut_mutex);
+    build_host_luts();
+    if (class4) memcpy(class4, g_lut4_h, sizeof(g_lut4_h));
+    if (class5) memcpy(class5, g_lut5_h, sizeof(g_lut5_h));
+    if (centred) memcpy(centred, g_lutc_h, sizeof(g_lutc_h));
+    return MOSS_OK;
+}
 
 const char *moss_version(void) { return "moss-gb300 0.1 (sm_103a)"; }
 
