@@ -444,11 +444,12 @@ class Server:
 # ------------------------------------------------------------ convenience --
 def result_dict(r: moss_result) -> dict:
     """moss_result as plain Python/numpy values."""
+    view = np.ctypeslib.as_array
     return {"k": r.k, "K": (int(r.K[0]), int(r.K[1])),
-            "hits": np.array([[int(x) for x in r.hits[l]] for l in range(2)], dtype=np.uint64),
-            "est": np.array(list(r.est)), "var": np.array(list(r.var)),
-            "lam": np.array([list(r.lambda_[l]) for l in range(2)]),
-            "triangles": r.triangles, "triangles_var": r.triangles_var, "conc": np.array(list(r.conc))}
+            "hits": view(r.hits).astype(np.uint64, copy=True),
+            "est": view(r.est).copy(), "var": view(r.var).copy(),
+            "lam": view(r.lambda_).copy(),
+            "triangles": r.triangles, "triangles_var": r.triangles_var, "conc": view(r.conc).copy()}
 
 
 class Batch:

@@ -521,11 +521,11 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
     DeviceGuard dg(g->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // independent chains on s and the caller thread's auxiliary streams (when
-    // it has them), each with its own scratch: the per-list tables on s, the
-    // vertex tables on the second auxiliary stream, the edge hash (and
-    // filter) on the first -- or, when the MOSS-4Min tables are built (the
-    // longest chain), those on the first and the edge hash after the
-    // per-list tables on s
+    // it has them), each with its own scratch: the per-list tables of short
+    // lists on s and of long lists on the first auxiliary stream, the vertex
+    // tables on the second, the edge hash (and filter) on the third -- or,
+    // when the MOSS-4Min tables are built (the longest chain), those on the
+    // third and the edge hash after the per-list tables on s
     const uint64_t sigma_bytes = ((g->nnz * 4 + 255) & ~255ULL) + ((g->nnz * 8 + 255) & ~255ULL);
     const uint64_t seed_bytes = seed_scratch_bytes(g->n);
     void *scratch = nullptr;
@@ -568,7 +568,7 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
         aux = nullptr;
     }
     const bool want_min = (k_mask & MOSS_TABLES_4MIN) != 0;
-    cudaStream_t sv = aux ? aux->a[1] : s, sm = aux ? aux->a[0] : s, sh = aux && !want_min ? aux->a[0] : s;
+    cudaStream_t sv = aux ? aux->a[1] : s, sm = aux ? aux->a[2] : s, sh = aux && !want_min ? aux->a[2] : s;
     // MOSS-4Min tables
     bool min_built = false;
     if (e == cudaSuccess && want_min) {
@@ -593,7 +593,8 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
     if (e == cudaSuccess && nt > 0)
         ev = launch_seed_alias(g->n, g->tot, nt, which, w, seed, vrec, seed_scratch, g->flags, sv);
     // per-list tables
-    if (e == cudaSuccess) e = launch_sigma_alias(g->n, g->nnz, g->vert, g->acc, g->owner, g->slot, idx, pre, s);
+    if (e == cudaSuccess)
+        e = launch_sigma_alias(g->n, g->nnz, g->vert, g->acc, g->owner, g->slot, idx, pre, s, aux, 0);
     // edge hash and filter
     bool hashed = false, filtered = false;
     cudaError_t eh = cudaSuccess;
@@ -877,18 +878,23 @@ int current_sms() {
 
 cudaError_t AuxStreams::fork(cudaStream_t s) const {
     cudaError_t e = cudaEventRecord(forked, s);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(a[i], forked, 0);
+    for (int i = 0; i < kAuxStreams && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(a[i], forked, 0);
     return e;
 }
 
 cudaError_t AuxStreams::join(cudaStream_t s) const {
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kAuxStreams; ++i) {
         cudaError_t ei = cudaEventRecord(done[i], a[i]);
         if (ei == cudaSuccess) ei = cudaStreamWaitEvent(s, done[i], 0);
         if (e == cudaSuccess) e = ei;
     }
     return e;
+}
+
+cudaError_t AuxStreams::wait_for(cudaStream_t s, int i) const {
+    cudaError_t e = cudaEventRecord(mid, a[i]);
+    return e == cudaSuccess ? cudaStreamWaitEvent(s, mid, 0) : e;
 }
 
 namespace {
@@ -898,11 +904,12 @@ struct AuxSet {
     bool tried[64] = {};
     ~AuxSet() {
         for (auto &x : dev) {
-            for (int i = 0; i < 2; ++i) {
+            for (int i = 0; i < kAuxStreams; ++i) {
                 if (x.a[i]) cudaStreamDestroy(x.a[i]);
                 if (x.done[i]) cudaEventDestroy(x.done[i]);
             }
             if (x.forked) cudaEventDestroy(x.forked);
+            if (x.mid) cudaEventDestroy(x.mid);
         }
     }
 };
@@ -915,8 +922,9 @@ const AuxStreams *aux_streams() {
     AuxStreams &x = t_aux.dev[d];
     if (!t_aux.tried[d]) {
         t_aux.tried[d] = true;
-        bool ok = cudaEventCreateWithFlags(&x.forked, cudaEventDisableTiming) == cudaSuccess;
-        for (int i = 0; i < 2 && ok; ++i)
+        bool ok = cudaEventCreateWithFlags(&x.forked, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&x.mid, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < kAuxStreams && ok; ++i)
             ok = cudaStreamCreateWithFlags(&x.a[i], cudaStreamNonBlocking) == cudaSuccess &&
                  cudaEventCreateWithFlags(&x.done[i], cudaEventDisableTiming) == cudaSuccess;
         if (!ok) {

@@ -233,14 +233,17 @@ __device__ __forceinline__ Words4 sample_words4(uint64_t seed, uint32_t t, uint6
 }
 
 // ----------------------------------------------------- host-side launches --
-// Two auxiliary streams of the calling host thread on one device, with the
-// events of one fork (both wait for what was queued on s) and one join (s
-// waits for both), for independent chains of the table build.
+// Auxiliary streams of the calling host thread on one device, with the
+// events of one fork (each waits for what was queued on s), one join (s
+// waits for all of them) and one hand-over (s waits for one of them
+// mid-chain), for independent chains of the table build.
+constexpr int kAuxStreams = 3;
 struct AuxStreams {
-    cudaStream_t a[2] = {nullptr, nullptr};
-    cudaEvent_t forked = nullptr, done[2] = {nullptr, nullptr};
+    cudaStream_t a[kAuxStreams] = {};
+    cudaEvent_t forked = nullptr, done[kAuxStreams] = {}, mid = nullptr;
     cudaError_t fork(cudaStream_t s) const;
     cudaError_t join(cudaStream_t s) const;
+    cudaError_t wait_for(cudaStream_t s, int i) const;   // s waits for what is queued on a[i] so far
 };
 // the calling thread's auxiliary streams on the current device (created on
 // first use; null when they cannot be created: callers then stay on s)
@@ -263,8 +266,10 @@ cudaError_t launch_edge_hash(uint64_t nnz, const uint32_t *col, const uint32_t *
 // filter of 2^(64 - shift) words, zeroed beforehand
 cudaError_t launch_edge_filter(uint64_t nnz, const uint32_t *col, const uint32_t *owner, uint32_t *filter,
                                uint32_t shift, cudaStream_t s);
+// aux (nullable, already forked from s): the long lists go to aux->a[long_stream]
 cudaError_t launch_sigma_alias(uint32_t n, uint64_t nnz, const uint4 *vert, const uint32_t *acc, const uint32_t *owner,
-                               uint4 *slot, uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s);
+                               uint4 *slot, uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s,
+                               const AuxStreams *aux, int long_stream);
 // vertex alias tables of up to 3 weights in the same launches (seed[t]: 2n
 // uint4, vrec[t]: the n vertex records copied beside each alias); scratch of
 // seed_scratch_bytes(n) bytes

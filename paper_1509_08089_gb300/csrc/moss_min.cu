@@ -19,6 +19,8 @@
 // used for sigma^(v) in moss_tables.cu, here in 128-bit arithmetic since
 // q_j = w_j d_v can exceed 2^64; the exact total Gamma-check; and the vertex
 // alias table of pi-check through the seed-table kernels.
+#include <atomic>
+
 #include "moss_alias.cuh"
 #include "moss_internal.cuh"
 
@@ -516,8 +518,14 @@ cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const
     // the rank array is dead now: it holds the split order, a[]/b[] the prefixes
     k_min_alias<<<ab, kListThreads, 0, s>>>(n, vert, mslot, mvert, gmin, m.partials);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_min_alias_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMinSmemBytes);
-    if (e != cudaSuccess) return e;
+    static std::atomic<bool> attr_set[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev].load(std::memory_order_relaxed)) {
+        e = cudaFuncSetAttribute(k_min_alias_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMinSmemBytes);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev].store(true, std::memory_order_relaxed);
+    }
     const unsigned chunks = (unsigned)(((uint64_t)n + kWarp - 1) / kWarp);
     k_min_alias_long<<<chunks, kListThreads, kMinSmemBytes, s>>>(n, vert, mvert, mslot, m.rank,
                                                                   reinterpret_cast<u128 *>(m.a));

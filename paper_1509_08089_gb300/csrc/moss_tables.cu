@@ -23,6 +23,8 @@
 // Both prefix sums and every search are parallel, so the per-list tables
 // (a warp per list) and the vertex tables (a block scan over V, then one
 // thread per item) are built without a sequential pass.
+#include <atomic>
+
 #include "moss_alias.cuh"
 #include "moss_internal.cuh"
 
@@ -814,24 +816,24 @@ cudaError_t launch_slots(uint32_t n, uint64_t nnz, const uint32_t *col, uint4 *v
         k_slot_weights<<<flat_blocks(nnz), 256, 0, s>>>(n, nnz, col, vert, owner, slot, acc, flags);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    // the twin pass touches none of what the list scans write: it runs beside them
-    cudaStream_t ts = s;
-    if (nnz && aux && (e = aux->fork(s)) == cudaSuccess) ts = aux->a[0];
-    if (e != cudaSuccess) return e;
+    // the twin pass touches none of what the list scans write, and the short
+    // and long list scans touch different lists and rows: all three run side
+    // by side on the auxiliary streams when there are some
+    const bool forked = aux && aux->fork(s) == cudaSuccess;
+    if (aux && !forked) cudaGetLastError();
+    cudaStream_t ts = forked ? aux->a[0] : s, ls = forked ? aux->a[1] : s;
     if (nnz) k_twin<<<flat_blocks(nnz), 256, 0, ts>>>(n, nnz, vert, col, owner, slot, flags);
     cudaError_t et = cudaGetLastError();
+    k_slots_long<<<long_blocks(n), kLongThreads, 0, ls>>>(n, vert, acc, sq, gam0, gam1, gam2,
+                                                          partials + (uint64_t)blocks * 6);
+    cudaError_t el = cudaGetLastError();
     k_slots<<<blocks, kTableThreads, 0, s>>>(n, vert, acc, sq, gam0, gam1, gam2, partials);
     e = cudaGetLastError();
-    if (e == cudaSuccess) {
-        k_slots_long<<<long_blocks(n), kLongThreads, 0, s>>>(n, vert, acc, sq, gam0, gam1, gam2,
-                                                             partials + (uint64_t)blocks * 6);
-        e = cudaGetLastError();
-    }
-    if (ts != s) {
+    if (forked) {
         const cudaError_t ej = aux->join(s);
         if (e == cudaSuccess) e = ej;
     }
-    return e != cudaSuccess ? e : et;
+    return e != cudaSuccess ? e : (et != cudaSuccess ? et : el);
 }
 
 cudaError_t launch_totals(const u128 *partials, int blocks, DevTotals *tot, cudaStream_t s) {
@@ -854,16 +856,32 @@ cudaError_t launch_edge_filter(uint64_t nnz, const uint32_t *col, const uint32_t
 }
 
 cudaError_t launch_sigma_alias(uint32_t n, uint64_t nnz, const uint4 *vert, const uint32_t *acc, const uint32_t *owner,
-                               uint4 *slot, uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s) {
-    k_sigma_alias<<<table_blocks(n), kTableThreads, 0, s>>>(n, vert, acc, slot);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_sigma_alias_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSmemBytes);
-    if (e != cudaSuccess) return e;
+                               uint4 *slot, uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s,
+                               const AuxStreams *aux, int long_stream) {
+    // the short and the long lists are built side by side (long lists on
+    // aux->a[long_stream], forked from s by the caller); the fill waits for both
+    static std::atomic<bool> attr_set[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = cudaSuccess;
+    if (dev < 0 || dev >= 64 || !attr_set[dev].load(std::memory_order_relaxed)) {
+        e = cudaFuncSetAttribute(k_sigma_alias_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSmemBytes);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev].store(true, std::memory_order_relaxed);
+    }
     const unsigned chunks = (unsigned)(((uint64_t)n + kSigmaChunk - 1) / kSigmaChunk);
-    k_sigma_alias_long<<<chunks ? chunks : 1, kLongThreads, kLongSmemBytes, s>>>(n, vert, acc, slot, scratch_idx,
-                                                                                  scratch_pre);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    cudaStream_t ls = aux ? aux->a[long_stream] : s;
+    k_sigma_alias_long<<<chunks ? chunks : 1, kLongThreads, kLongSmemBytes, ls>>>(n, vert, acc, slot, scratch_idx,
+                                                                                   scratch_pre);
+    cudaError_t el = cudaGetLastError();
+    k_sigma_alias<<<table_blocks(n), kTableThreads, 0, s>>>(n, vert, acc, slot);
+    e = cudaGetLastError();
+    if (aux) {
+        const cudaError_t ew = aux->wait_for(s, long_stream);
+        if (el == cudaSuccess) el = ew;
+    }
+    if (e != cudaSuccess) return e;
+    if (el != cudaSuccess) return el;
     k_slot_alias_fill<<<flat_blocks(nnz), 256, 0, s>>>(nnz, vert, owner, slot);
     return cudaGetLastError();
 }
