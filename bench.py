@@ -254,12 +254,12 @@ def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False) ->
     """Kernels of one step: load 7 (vertices, owners, slot weights, short and
     long slot scans, twins, totals); build 8 (two sigma alias passes, the
     alias-half fill, four vertex-table phases, edge hash); MOSS-4Min
-    build 11 (three sort tiers, slot records, two alias passes, total, four
-    vertex-table phases); per sub-method a sampler and a reduce, Path-5 per
+    build 12 (three sort tiers, slot records, two alias passes, pick records,
+    total, four vertex-table phases); per sub-method a sampler and a reduce, Path-5 per
     chunk of DEFER_CHUNK ids a main launch, the second-attempt and fallback
     launches and a reduce; one finalize."""
     from paper_1509_08089_gb300.dist import sub_budgets
-    n = 7 + 8 + (1 if filtered else 0) + (11 if mix else 0) + 1
+    n = 7 + 8 + (1 if filtered else 0) + (12 if mix else 0) + 1
     for m, K in sub_budgets(k, budget, mix):
         n += 4 * -(-K // DEFER_CHUNK) if m == 2 else 2
     return n
