@@ -484,7 +484,7 @@ fail_out:
 }
 
 // The MOSS-4Min tables in their own allocation (made once per graph).
-static int build_min_tables(moss_graph *g, cudaStream_t s) {
+static int build_min_tables(moss_graph *g, cudaStream_t s, const AuxStreams *aux) {
     cudaError_t e;
     if (!g->min_arena) {
         Carver c;
@@ -508,7 +508,7 @@ static int build_min_tables(moss_graph *g, cudaStream_t s) {
         return cuda_fail(e, "allocating scratch");
     e = launch_min_tables(g->n, g->nnz, g->vert, g->col, g->owner, g->slot, g->mvert, g->mslot, g->mpick, g->rlist,
                           g->gam[3],
-                          g->seed[3], g->tot, scratch, g->flags, s);
+                          g->seed[3], g->tot, scratch, g->flags, s, aux);
     cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) return cuda_fail(e, "MOSS-4Min table kernels");
     return MOSS_OK;
@@ -572,7 +572,7 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
     // MOSS-4Min tables
     bool min_built = false;
     if (e == cudaSuccess && want_min) {
-        rc = build_min_tables(g, sm);
+        rc = build_min_tables(g, sm, aux);
         min_built = rc == MOSS_OK;
     }
     // vertex alias tables
@@ -878,13 +878,13 @@ int current_sms() {
 
 cudaError_t AuxStreams::fork(cudaStream_t s) const {
     cudaError_t e = cudaEventRecord(forked, s);
-    for (int i = 0; i < kAuxStreams && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(a[i], forked, 0);
+    for (int i = 0; i < kAuxOuter && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(a[i], forked, 0);
     return e;
 }
 
 cudaError_t AuxStreams::join(cudaStream_t s) const {
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < kAuxStreams; ++i) {
+    for (int i = 0; i < kAuxOuter; ++i) {
         cudaError_t ei = cudaEventRecord(done[i], a[i]);
         if (ei == cudaSuccess) ei = cudaStreamWaitEvent(s, done[i], 0);
         if (e == cudaSuccess) e = ei;
@@ -910,6 +910,10 @@ struct AuxSet {
             }
             if (x.forked) cudaEventDestroy(x.forked);
             if (x.mid) cudaEventDestroy(x.mid);
+            if (x.sub_fork) cudaEventDestroy(x.sub_fork);
+            if (x.sub_mid) cudaEventDestroy(x.sub_mid);
+            for (auto ev : x.sub_done)
+                if (ev) cudaEventDestroy(ev);
         }
     }
 };
@@ -923,7 +927,11 @@ const AuxStreams *aux_streams() {
     if (!t_aux.tried[d]) {
         t_aux.tried[d] = true;
         bool ok = cudaEventCreateWithFlags(&x.forked, cudaEventDisableTiming) == cudaSuccess &&
-                  cudaEventCreateWithFlags(&x.mid, cudaEventDisableTiming) == cudaSuccess;
+                  cudaEventCreateWithFlags(&x.mid, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&x.sub_fork, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&x.sub_mid, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&x.sub_done[0], cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&x.sub_done[1], cudaEventDisableTiming) == cudaSuccess;
         for (int i = 0; i < kAuxStreams && ok; ++i)
             ok = cudaStreamCreateWithFlags(&x.a[i], cudaStreamNonBlocking) == cudaSuccess &&
                  cudaEventCreateWithFlags(&x.done[i], cudaEventDisableTiming) == cudaSuccess;

@@ -234,13 +234,16 @@ __device__ __forceinline__ Words4 sample_words4(uint64_t seed, uint32_t t, uint6
 
 // ----------------------------------------------------- host-side launches --
 // Auxiliary streams of the calling host thread on one device, with the
-// events of one fork (each waits for what was queued on s), one join (s
-// waits for all of them) and one hand-over (s waits for one of them
-// mid-chain), for independent chains of the table build.
-constexpr int kAuxStreams = 3;
+// events of one fork (a[0..2] each wait for what was queued on s), one join
+// (s waits for all of them) and one hand-over (s waits for one of them
+// mid-chain), for independent chains of the table build; a[3], a[4] and the
+// sub_* events serve the chains' own inner forks (the MOSS-4Min tables).
+constexpr int kAuxStreams = 5;
+constexpr int kAuxOuter = 3;
 struct AuxStreams {
     cudaStream_t a[kAuxStreams] = {};
     cudaEvent_t forked = nullptr, done[kAuxStreams] = {}, mid = nullptr;
+    cudaEvent_t sub_fork = nullptr, sub_done[2] = {}, sub_mid = nullptr;
     cudaError_t fork(cudaStream_t s) const;
     cudaError_t join(cudaStream_t s) const;
     cudaError_t wait_for(cudaStream_t s, int i) const;   // s waits for what is queued on a[i] so far
@@ -286,7 +289,7 @@ uint64_t min_scratch_bytes(uint32_t n, uint64_t nnz);
 cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const uint32_t *col,
                               const uint32_t *owner, const uint4 *slot, uint4 *mvert, uint4 *mslot, uint4 *mpick,
                               uint2 *rlist, u128 *gmin, uint4 *seed_min, DevTotals *tot, void *scratch,
-                              uint32_t *flags, cudaStream_t s);
+                              uint32_t *flags, cudaStream_t s, const AuxStreams *aux);
 
 // moss_sample.cu
 // class of each 4- and 5-vertex edge mask; c(s) of MOSS-4Min by (mask << 6 | order bits)

@@ -400,25 +400,35 @@ __global__ void __launch_bounds__(kListThreads) k_min_alias(uint32_t n, const ui
     }
 }
 
-// the alias tables of lists longer than kLongList, a block per list, after
-// k_min_alias has written Gamma-check_v into mvert; a block per kWarp vertex
-// records (the scheduler spreads the long lists), the split of a list of at
-// most kMinSmemList entries in dynamic shared memory, of a longer one in its
-// range of the global scratch (idx, pre)
+// the alias tables of lists longer than kLongList, a block per list; each
+// block forms Gamma-check_v itself (the same integer sum k_min_alias writes
+// into mvert), so the two kernels may run side by side.  A block per kWarp
+// vertex records (the scheduler spreads the long lists); the split of a list
+// of at most kMinSmemList entries in dynamic shared memory, of a longer one in
+// its range of the global scratch (idx, pre)
 constexpr uint32_t kMinSmemList = 2048;
 constexpr size_t kMinSmemBytes = (size_t)kMinSmemList * (sizeof(u128) + sizeof(uint32_t));
 
 __global__ void __launch_bounds__(kListThreads) k_min_alias_long(uint32_t n, const uint4 *__restrict__ vert,
-                                                                const uint4 *__restrict__ mvert, uint4 *mslot,
-                                                                uint32_t *idx, u128 *pre) {
+                                                                uint4 *mslot, uint32_t *idx, u128 *pre) {
     extern __shared__ u128 s_split[];   // kMinSmemList prefixes, then kMinSmemList positions
+    __shared__ uint64_t s_w[kListThreads / kWarp];
     uint32_t *m32 = reinterpret_cast<uint32_t *>(mslot);
     for_each_vertex<kListThreads, kWarp>(
-        n, mvert, [](uint4 mv) { return mv.y > kLongList && (mv.z | mv.w) != 0; },
+        n, vert, [](uint4 vr) { return vr.y > kLongList; },
         [&](uint32_t v) {
-            const uint4 mv = mvert[v];
-            const uint32_t o = mv.x, d = mv.y;
-            const uint64_t W = ((uint64_t)mv.w << 32) | mv.z;
+            const uint4 vr = vert[v];
+            const uint32_t o = vr.x, d = vr.y;
+            uint64_t W = 0;
+            for (uint32_t j = threadIdx.x; j < d; j += kListThreads) W += min_weight(mslot, (uint64_t)o + j);
+#pragma unroll
+            for (int sft = 16; sft > 0; sft >>= 1) W += __shfl_down_sync(0xffffffffu, W, sft);
+            if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = W;
+            __syncthreads();
+            W = 0;
+            for (int w = 0; w < kListThreads / kWarp; ++w) W += s_w[w];
+            __syncthreads();   // s_w is refilled for the next list
+            if (W == 0) return;   // block-uniform: k_min_alias keeps every column
             const bool fits = d <= kMinSmemList;
             block_alias<u128, kListThreads>(
                 d, (u128)W, [&](uint32_t j) { return (u128)min_weight(mslot, (uint64_t)o + j); },
@@ -498,26 +508,46 @@ uint64_t min_scratch_bytes(uint32_t n, uint64_t nnz) { return carve(nullptr, n, 
 cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const uint32_t *col,
                               const uint32_t *owner, const uint4 *slot, uint4 *mvert, uint4 *mslot, uint4 *mpick,
                               uint2 *rlist, u128 *gmin, uint4 *seed_min, DevTotals *tot, void *scratch,
-                              uint32_t *flags, cudaStream_t s) {
+                              uint32_t *flags, cudaStream_t s, const AuxStreams *aux) {
+    // With helper streams h0, h1 (aux->a[3], a[4]): the three sort tiers side
+    // by side (disjoint lists), then the slot records on s; the short-list
+    // alias tables, the total and the vertex table on s, beside the long-list
+    // alias tables and (once the short ones are done) the pick records on h0.
     const MinScratch m = carve(scratch, n, nnz);
-    cudaError_t e;
+    cudaStream_t h0 = aux ? aux->a[3] : s, h1 = aux ? aux->a[4] : s;
+    cudaError_t e = cudaSuccess, eh = cudaSuccess;
+    auto fork = [&](int k) {   // h0 (and h1) wait for what is queued on s
+        if (!aux) return;
+        if (e == cudaSuccess) e = cudaEventRecord(aux->sub_fork, s);
+        for (int i = 0; i < k && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(aux->a[3 + i], aux->sub_fork, 0);
+    };
+    auto join = [&](int k) {   // s waits for h0 (and h1); done even after an error
+        if (!aux) return;
+        for (int i = 0; i < k; ++i) {
+            cudaError_t ei = cudaEventRecord(aux->sub_done[i], aux->a[3 + i]);
+            if (ei == cudaSuccess) ei = cudaStreamWaitEvent(s, aux->sub_done[i], 0);
+            if (e == cudaSuccess) e = ei;
+        }
+    };
     if (nnz) {
-        k_rank_warp<<<grid_for((uint64_t)n, kListThreads / kWarp, 8), kListThreads, 0, s>>>(n, vert, col, rlist,
-                                                                                             m.rank);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const unsigned chunks = (unsigned)(((uint64_t)n + kWarp - 1) / kWarp);
-        k_rank_block<<<chunks, kSortThreads, 0, s>>>(n, vert, col, rlist, m.rank);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_rank_long<<<grid_for((uint64_t)n, kSortThreads, 1), kSortThreads, 0, s>>>(n, vert, col, m.a, m.b, m.ia,
-                                                                                    m.ib, rlist, m.rank);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        fork(2);
+        if (e == cudaSuccess) {
+            const unsigned chunks = (unsigned)(((uint64_t)n + kWarp - 1) / kWarp);
+            k_rank_block<<<chunks, kSortThreads, 0, h0>>>(n, vert, col, rlist, m.rank);
+            eh = cudaGetLastError();
+            k_rank_long<<<grid_for((uint64_t)n, kSortThreads, 1), kSortThreads, 0, h1>>>(n, vert, col, m.a, m.b, m.ia,
+                                                                                        m.ib, rlist, m.rank);
+            if (eh == cudaSuccess) eh = cudaGetLastError();
+            k_rank_warp<<<grid_for((uint64_t)n, kListThreads / kWarp, 8), kListThreads, 0, s>>>(n, vert, col, rlist,
+                                                                                                 m.rank);
+            e = cudaGetLastError();
+        }
+        join(2);
+        if (e == cudaSuccess) e = eh;
+        if (e != cudaSuccess) return e;
         k_min_slots<<<grid_for(nnz, 256, 16), 256, 0, s>>>(nnz, vert, col, slot, m.rank, mslot);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const unsigned ab = grid_for((uint64_t)n, kListThreads / kWarp, 8);
-    // the rank array is dead now: it holds the split order, a[]/b[] the prefixes
-    k_min_alias<<<ab, kListThreads, 0, s>>>(n, vert, mslot, mvert, gmin, m.partials);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     static std::atomic<bool> attr_set[64];
     int dev = 0;
     cudaGetDevice(&dev);
@@ -526,21 +556,36 @@ cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev].store(true, std::memory_order_relaxed);
     }
+    const unsigned ab = grid_for((uint64_t)n, kListThreads / kWarp, 8);
+    fork(1);
+    if (e != cudaSuccess) return e;
+    // the rank array is dead now: the long-list kernel reuses it (split order) with a[] (prefixes)
     const unsigned chunks = (unsigned)(((uint64_t)n + kWarp - 1) / kWarp);
-    k_min_alias_long<<<chunks, kListThreads, kMinSmemBytes, s>>>(n, vert, mvert, mslot, m.rank,
-                                                                  reinterpret_cast<u128 *>(m.a));
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (nnz) {
-        k_min_pick<<<grid_for(nnz, 256, 16), 256, 0, s>>>(nnz, owner, mvert, mslot, mpick);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_min_alias_long<<<chunks, kListThreads, kMinSmemBytes, h0>>>(n, vert, mslot, m.rank, reinterpret_cast<u128 *>(m.a));
+    eh = cudaGetLastError();
+    k_min_alias<<<ab, kListThreads, 0, s>>>(n, vert, mslot, mvert, gmin, m.partials);
+    e = cudaGetLastError();
+    if (aux && e == cudaSuccess) {   // the pick records need both alias passes and mvert
+        e = cudaEventRecord(aux->sub_mid, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h0, aux->sub_mid, 0);
     }
-    k_min_total<<<1, kWarp, 0, s>>>(m.partials, (int)ab, tot);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int which[1] = {3};
-    u128 *w[1] = {gmin};
-    uint4 *sd[1] = {seed_min};
-    const uint4 *vr[1] = {mvert};
-    return launch_seed_alias(n, tot, 1, which, w, sd, vr, m.seed, flags, s);
+    if (e == cudaSuccess && eh == cudaSuccess && nnz) {
+        k_min_pick<<<grid_for(nnz, 256, 16), 256, 0, h0>>>(nnz, owner, mvert, mslot, mpick);
+        eh = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_min_total<<<1, kWarp, 0, s>>>(m.partials, (int)ab, tot);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        const int which[1] = {3};
+        u128 *w[1] = {gmin};
+        uint4 *sd[1] = {seed_min};
+        const uint4 *vr[1] = {mvert};
+        e = launch_seed_alias(n, tot, 1, which, w, sd, vr, m.seed, flags, s);
+    }
+    join(1);
+    return e != cudaSuccess ? e : eh;
 }
 
 }  // namespace moss
