@@ -127,8 +127,13 @@ __device__ void bitonic_desc(uint64_t *k, uint16_t *id, uint32_t P) {
         }
 }
 
-// a block per 32 vertex records (the scheduler spreads the lists), a list's
-// keys and positions sorted together in shared memory
+// a block per 32 vertex records (the scheduler spreads the lists).  A list
+// of at most kCountList entries ranks each key by counting the keys above it
+// (every thread reads the same key at a time: shared-memory broadcasts, no
+// barrier per step); a longer one sorts keys and positions together
+// (bitonic, a barrier per stage).
+constexpr uint32_t kCountList = 1024;
+
 __global__ void __launch_bounds__(kSortThreads) k_rank_block(uint32_t n, const uint4 *__restrict__ vert,
                                                             const uint32_t *__restrict__ col, uint2 *rlist,
                                                             uint32_t *rank) {
@@ -139,6 +144,22 @@ __global__ void __launch_bounds__(kSortThreads) k_rank_block(uint32_t n, const u
         [&](uint32_t v) {
             const uint4 vr = vert[v];
             const uint32_t o = vr.x, d = vr.y;
+            if (d <= kCountList) {
+                for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
+                    const uint32_t x = col[o + i];
+                    k[i] = order_key(x, vert[x].y);
+                }
+                __syncthreads();
+                for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
+                    const uint64_t key = k[i];
+                    uint32_t r = 0;
+                    for (uint32_t j = 0; j < d; ++j) r += k[j] > key;
+                    rlist[o + r] = make_uint2((uint32_t)key, (uint32_t)(key >> 32));
+                    rank[o + i] = r;
+                }
+                __syncthreads();   // k is refilled for the next list
+                return;
+            }
             const uint32_t P = pow2_at_least(d);
             load_keys(vert, col, o, 0, d, P, k, id);
             bitonic_desc(k, id, P);
