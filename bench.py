@@ -443,6 +443,20 @@ def run_gpu(args):
                 "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak, "traffic": tb,
                 "algorithmic_bytes_per_sample": spb * 32.0, "samples_per_launch": K,
                 "launch_ms": tms, "kernel_times_ms": {name[m]: times[m][1] for m in times}}
+        # the ceiling of the access pattern itself: independent random 32 B
+        # sector reads, from an L2-resident buffer and from one 32x the L2
+        l2_rate = moss.moss_gather_rate(64 << 20, dev, stream) * 32.0 / 1e9
+        hbm_rate = moss.moss_gather_rate(4 << 30, dev, stream) * 32.0 / 1e9
+        roof["gather_ceiling"] = {"unit": "GB/s", "l2_resident_64MiB": l2_rate, "hbm_4GiB": hbm_rate,
+                                  "frac_of_l2_gather": ach / l2_rate}
+        if tb is not None:
+            # a load that misses L2 fills a whole 128 B line from DRAM (ncu on
+            # the gather kernel: 125 B of DRAM reads per load from 4 GiB), so
+            # DRAM bytes / 128 are the sampler's random HBM accesses, to be set
+            # against the gather kernel's accesses per second
+            fetch = tb / 128.0 / (tms / 1000.0)
+            roof["gather_ceiling"]["dram_line_fetches_per_s"] = fetch
+            roof["gather_ceiling"]["frac_of_hbm_gather"] = fetch / (hbm_rate * 1e9 / 32.0)
 
     out = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,

@@ -397,6 +397,21 @@ void moss_graph_free(moss_graph *g);
  * and 4-clique. */
 int moss_class_tables(uint8_t *class4, uint8_t *class5, uint8_t *centred);
 
+/* Measurement helper, not a step of the method.  Every sampler step reads
+ * one 32-byte sector at an address no other lane shares (Sec. 4.1.3: alias
+ * draws, uniform list picks and adjacency probes at random positions), so
+ * the samplers are bounded by the rate of independent random sector reads,
+ * not by streaming bandwidth.  This call allocates a zeroed device buffer of
+ * `bytes` (a positive multiple of 32) on `device`, reads 2^28 sectors of it
+ * at uniform random positions from a full persistent grid (four independent
+ * 256-bit loads in flight per thread) after one warm-up launch of the same
+ * length, and writes the sectors per second of the timed launch (CUDA
+ * events on `stream`, NULL = default stream) to *sectors_per_s.  A buffer
+ * smaller than L2 measures the L2 random-read ceiling, one far larger the
+ * HBM one.  Synchronous; frees its buffer before returning.  Errors:
+ * MOSS_EINVAL (NULL output, bad size or device), MOSS_ENOMEM, MOSS_ECUDA. */
+int moss_gather_rate(uint64_t bytes, int device, void *stream, double *sectors_per_s);
+
 const char *moss_strerror(int status);
 const char *moss_last_error_detail(void);
 const char *moss_version(void);

@@ -127,6 +127,7 @@ def load():
         "moss_server_stats": ([_vp, ctypes.POINTER(moss_server_info)], ctypes.c_int),
         "moss_server_free": ([_vp], None),
         "moss_budget_for_target": ([ctypes.c_int, _vp, _vp, ctypes.c_double, _u64, _u64], ctypes.c_uint64),
+        "moss_gather_rate": ([_u64, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -184,6 +185,14 @@ def moss_class_tables():
     cc = np.zeros(4096, dtype=np.uint8)
     _check(load().moss_class_tables(c4.ctypes.data, c5.ctypes.data, cc.ctypes.data))
     return c4, c5, cc
+
+
+def moss_gather_rate(nbytes: int, device: int = 0, stream=None) -> float:
+    """Random 32-byte sector reads per second sustained over a buffer of
+    nbytes (see include/moss.h: the samplers' gather ceiling)."""
+    out = ctypes.c_double(0.0)
+    _check(load().moss_gather_rate(int(nbytes), int(device), _stream(stream, device), ctypes.byref(out)))
+    return out.value
 
 
 def moss_strerror(status: int) -> str:

@@ -83,3 +83,15 @@ def test_state_and_argument_errors():
     rp, col = synth.cycle(8)
     with moss.Graph(rp, col) as g:
         assert g.estimate(4, 1000, 2)["est"][1] == pytest.approx(8.0)
+
+
+def test_gather_rate():
+    # the measurement helper: L2-resident random sector reads are served
+    # faster than ones spread over a buffer far larger than L2
+    l2 = moss.moss_gather_rate(64 << 20)
+    hbm = moss.moss_gather_rate(2 << 30)
+    assert l2 > 0 and hbm > 0
+    assert l2 > 2 * hbm
+    with pytest.raises(moss.MossError) as ei:
+        moss.moss_gather_rate(48)
+    assert ei.value.status == moss.MOSS_EINVAL

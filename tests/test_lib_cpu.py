@@ -63,6 +63,11 @@ def test_argument_checks_before_device():
     K = np.zeros(2, dtype=np.uint64)
     H = np.zeros(44, dtype=np.uint64)
     assert lib.moss_finalize_min(None, K.ctypes.data, H.ctypes.data, None, None, ctypes.byref(r)) == moss.MOSS_EINVAL
+    rate = ctypes.c_double(1.0)
+    assert lib.moss_gather_rate(64 << 20, 0, None, None) == moss.MOSS_EINVAL
+    assert lib.moss_gather_rate(0, 0, None, ctypes.byref(rate)) == moss.MOSS_EINVAL and rate.value == 0.0
+    assert lib.moss_gather_rate(33, 0, None, ctypes.byref(rate)) == moss.MOSS_EINVAL
+    assert lib.moss_gather_rate(64 << 20, -1, None, ctypes.byref(rate)) == moss.MOSS_EINVAL
     lib.moss_graph_free(None)
 
 
