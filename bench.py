@@ -235,7 +235,7 @@ class Clocks:
 
 
 # ------------------------------------------------------------------- GPU --
-DEFER_CHUNK = 1 << 25   # Path-5 sample ids per main/deferred launch pair
+DEFER_CHUNK = 1 << 26   # Path-5 sample ids per main/deferred launch pair
 
 
 def resolved_probe(name: str, row_ptr) -> str:

@@ -69,7 +69,7 @@ __device__ __forceinline__ uint32_t slot_twin(const uint32_t *s32, uint64_t p) {
 }
 // Path-5 samples run in chunks of kDeferChunk ids; a sample whose first pair
 // of sigma draws collides is flagged in a bitmap and redone by a second launch
-constexpr uint64_t kDeferChunk = 1ull << 25;
+constexpr uint64_t kDeferChunk = 1ull << 26;
 
 struct alignas(16) DevTotals {
     u128 gamma[kMethods];             // Gamma, Gamma^(1), Gamma^(2), Gamma-check

@@ -68,6 +68,22 @@ __device__ __forceinline__ Sector ld8(const uint4 *p) {
     return r;
 }
 
+// The same load marked evict-first in L2, for the per-slot records (sigma
+// slot records, MOSS-4Min pick records): they are the largest and least
+// densely used tables of a sampler, so with the working set at the size of
+// the L2 they are the ones to give up first, which keeps the denser edge
+// hash, neighbour lists and vertex alias records resident.
+__device__ __forceinline__ Sector ld8_first(const uint4 *p) {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    Sector r;
+    asm("ld.global.nc.L2::cache_hint.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+        : "=r"(r.lo.x), "=r"(r.lo.y), "=r"(r.lo.z), "=r"(r.lo.w), "=r"(r.hi.x), "=r"(r.hi.y), "=r"(r.hi.z),
+          "=r"(r.hi.w)
+        : "l"(p), "l"(pol));
+    return r;
+}
+
 struct VertexPick {
     uint32_t v;
     uint4 rec;      // v's vertex record (vert, or mvert for MOSS-4Min)
@@ -99,7 +115,7 @@ __device__ __forceinline__ Pick unpack_pick(const uint4 *vert, uint32_t pos, uin
 __device__ __forceinline__ Pick draw_sigma(const uint4 *slot, const uint4 *vert, uint32_t ov, uint32_t dv, uint32_t Sv,
                                            uint64_t xc, uint64_t xt) {
     const uint32_t j = (uint32_t)word_index(xc, dv);
-    const Sector rec = ld8(slot + 2 * (uint64_t)(ov + j));   // {col, nb, thr, alias} {off, alias col, nb, off}
+    const Sector rec = ld8_first(slot + 2 * (uint64_t)(ov + j));   // {col, nb, thr, alias} {off, alias col, nb, off}
     const bool keep = word_index(xt, Sv) < rec.lo.z;
     return unpack_pick(vert, keep ? j : rec.lo.w, keep ? rec.lo.x : rec.hi.y, keep ? rec.lo.y : rec.hi.z,
                        keep ? rec.hi.x : rec.hi.w);
@@ -324,7 +340,7 @@ __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *l
     uint32_t u;
     Sector pk;
     pk.hi.w = kSlotHub;
-    if (mv.w == 0) pk = ld8(g.mpick + 2 * (uint64_t)(mv.x + j));
+    if (mv.w == 0) pk = ld8_first(g.mpick + 2 * (uint64_t)(mv.x + j));
     if (pk.hi.w != kSlotHub) {
         const bool keep = y < pk.lo.x;
         const uint32_t dd = keep ? pk.lo.w : pk.hi.z;
@@ -532,8 +548,10 @@ __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGr
             }
         }
         if (METHOD == 2) {   // one bitmap word per 32 sample ids, written by the warp that drew them
+            // (streaming store: the word is read once, by the next launch, and
+            // should not push the tables out of L2 meanwhile)
             const uint32_t bits = __ballot_sync(0xffffffffu, deferred);
-            if (lane == 0) g.defer[base >> 5] = bits;
+            if (lane == 0) __stcs(g.defer + (base >> 5), bits);
         }
         const uint32_t peers = __match_any_sync(0xffffffffu, cls);
         if (cls < kSlots && lane == __ffs(peers) - 1) atomicAdd(&hist[warp][cls], (uint32_t)__popc(peers));
@@ -616,7 +634,7 @@ __global__ void __launch_bounds__(kThreads, defer_min_blocks<STAGE>())
     uint32_t n = 0;   // ids waiting in the list (warp-uniform, < 32 between windows)
     for (uint64_t w0 = ((uint64_t)blockIdx.x * kWarps + warp) * 32; w0 < words; w0 += stride) {
         const uint64_t w = w0 + lane;
-        uint32_t bits = w < words ? g.defer[w] : 0u;
+        uint32_t bits = w < words ? __ldcs(g.defer + w) : 0u;
         if (STAGE == 1 && bits) g.defer[w] = 0u;   // re-deferred ids are set again by round()
         const uint32_t c = __popc(bits);
         uint32_t incl = c;

@@ -31,6 +31,13 @@ def hub_graph():
     return synth.from_edges(leaves + 2, edges)
 
 
+def circulant(n, offsets):
+    """Vertex i adjacent to i +- o (mod n) for each offset o: a regular graph
+    (degree 8 for (1, 2, 3, 4), 9 with n / 2 added) dense in triangles, so
+    every class of both k and the collision paths occur often."""
+    return synth.from_edges(n, [(i, (i + o) % n) for i in range(n) for o in offsets])
+
+
 GRAPHS = {
     "gnp12": lambda: synth.gnp(12, 0.45, 5),
     "cl_n200": lambda: synth.chung_lu(200, 2.3, 6.0, 30.0, seed=7),
@@ -38,6 +45,8 @@ GRAPHS = {
     "cl_n2k": lambda: synth.workload("cl_n2k"),
     "cl_n100k": lambda: synth.workload("cl_n100k"),
     "hub70k": hub_graph,
+    "circ8": lambda: circulant(300, (1, 2, 3, 4)),
+    "circ9": lambda: circulant(300, (1, 2, 3, 4, 150)),
 }
 
 _cache = {}
@@ -166,7 +175,7 @@ def test_edge_filter_bits(name):
     g.set_probe(moss.PROBE_AUTO)
 
 
-@pytest.mark.parametrize("name", ["gnp12", "cl_n200", "rgg2k", "cl_n2k", "cl_n100k", "hub70k"])
+@pytest.mark.parametrize("name", ["gnp12", "cl_n200", "rgg2k", "cl_n2k", "cl_n100k", "hub70k", "circ8", "circ9"])
 @pytest.mark.parametrize("method", [0, 1, 2])
 def test_records_bit_exact(name, method):
     rp, col, og, g = pair(name)
@@ -185,7 +194,7 @@ def test_records_bit_exact(name, method):
     g.set_probe(moss.PROBE_AUTO)
 
 
-@pytest.mark.parametrize("name", ["gnp12", "cl_n200", "rgg2k", "cl_n2k", "hub70k"])
+@pytest.mark.parametrize("name", ["gnp12", "cl_n200", "rgg2k", "cl_n2k", "hub70k", "circ8"])
 def test_counts_and_estimates(name):
     rp, col, og, g = pair(name)
     budget, seed = 200_001, 99
