@@ -650,7 +650,7 @@ static int sample_into(moss_graph *g, int method, uint64_t first, uint64_t count
         return fail(MOSS_EINVAL, "method %d has total weight 0 on this graph: no sample exists", method);
     if (first + count < first) return fail(MOSS_EOVERFLOW, "sample range wraps");
     const DevGraph dv = view(g);
-    const int blocks = sample_blocks(method, g->device);
+    const int blocks = sample_launch_blocks(method, g->device, dv);
     // per-warp 32-bit counters: keep each launch below 2^31 samples per warp
     const uint64_t max_chunk = (uint64_t)blocks * 8 * (1ULL << 31);
     if (count == 0) {

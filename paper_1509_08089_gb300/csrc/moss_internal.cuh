@@ -302,7 +302,8 @@ void upload_luts(const uint8_t *lut4, const uint8_t *lut5, const uint8_t *lutc);
 cudaError_t launch_counts(int method, const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed,
                           uint64_t *partials, uint8_t *classes, uint32_t *verts, uint64_t *counts_dev,
                           cudaStream_t s);
-int sample_blocks(int method, int device);   // blocks of one sampler launch
+int sample_blocks(int method, int device);   // the most blocks any variant of a sampler launches
+int sample_launch_blocks(int method, int device, const DevGraph &g);   // blocks of the variant g uses
 int sample_rows(int method, int device);     // partial-count rows launch_counts needs
 
 // moss_finalize.cu

@@ -78,7 +78,7 @@ extern "C" int moss_sample_counts_noalloc(moss_graph *g, int method, uint64_t fi
     int rc = MOSS_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     uint64_t *partials = nullptr;
-    const int blocks = sample_blocks(method, gi.device);
+    const int blocks = sample_launch_blocks(method, gi.device, gi.view);
     const uint64_t max_chunk = (uint64_t)blocks * 8 * (1ULL << 31);
     if (sample_rows(method, gi.device) > kNoAllocMaxBlocks) {
         rc = set_error(MOSS_EOVERFLOW, "this GPU needs more than 2048 blocks of partial counts, the fixed maximum");

@@ -27,6 +27,7 @@
 //            u removed from ACC (Sec. 5.1.4).
 // RandomVertex(N_v - X) (Sec. 4.1.3) takes the j-th admissible position,
 // skipping the excluded positions of X in list order.
+#include <algorithm>
 #include <atomic>
 
 #include "moss_internal.cuh"
@@ -91,11 +92,14 @@ struct VertexPick {
 
 // WeightRandomVertex(V, .) through a vertex alias table whose 32-byte column
 // records carry the alias's vertex record: one load, plus the column's own
-// record only when the column keeps the draw
+// record only when the column keeps the draw.  HINT (graphs behind the edge
+// filter): the record is read evict-first, since that table is as large as
+// the L2 and drawn uniformly, so a line is rarely read twice.
+template <bool HINT>
 __device__ __forceinline__ VertexPick draw_vertex(const uint4 *seed, const uint4 *vrec, uint32_t n, uint64_t xc,
                                                   uint64_t xt) {
     const uint32_t c = (uint32_t)word_index(xc, n);
-    const Sector r = ld8(seed + 2 * (uint64_t)c);
+    const Sector r = HINT ? ld8_first(seed + 2 * (uint64_t)c) : ld8(seed + 2 * (uint64_t)c);
     const uint64_t T = ((uint64_t)r.lo.y << 32) | r.lo.x;
     if (xt < T) return VertexPick{c, ld4(vrec + c)};
     return VertexPick{r.lo.z, r.hi};
@@ -176,8 +180,11 @@ __device__ __forceinline__ uint32_t probe_pairs(const uint32_t *col, const uint4
 }
 
 // Membership tests through the hashed edge set: one 32-byte bucket load per
-// pair in the common case, all P loads issued together.
-template <int P>
+// pair in the common case, all P loads issued together.  HINT (behind the
+// filter): the set is far larger than the L2 and a bucket is rarely read
+// twice, so buckets are read evict-first, which keeps the filter, lists and
+// hub slot records resident.
+template <int P, bool HINT>
 __device__ __forceinline__ uint32_t probe_hash(const DevGraph &g, const uint32_t (&a)[P], const uint32_t (&b)[P]) {
     uint64_t key[P];
     uint32_t bk[P];
@@ -200,7 +207,7 @@ __device__ __forceinline__ uint32_t probe_hash(const DevGraph &g, const uint32_t
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (pending >> p & 1u) {
-                const Sector e = ld8(g.hash + 2 * (uint64_t)bk[p]);
+                const Sector e = HINT ? ld8_first(g.hash + 2 * (uint64_t)bk[p]) : ld8(g.hash + 2 * (uint64_t)bk[p]);
                 const uint32_t lo = (uint32_t)key[p], hi = (uint32_t)(key[p] >> 32);
                 const bool hit = (e.lo.x == lo && e.lo.y == hi) || (e.lo.z == lo && e.lo.w == hi) ||
                                  (e.hi.x == lo && e.hi.y == hi) || (e.hi.z == lo && e.hi.w == hi);
@@ -223,12 +230,12 @@ struct Sample {
     int cls;
 };
 
-template <bool HASH>
+template <bool HASH, bool HINT = false>
 __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
     const Words4 a = sample_words4(seed, 0, s, 0);
     const Words4 b = sample_words4(seed, 0, s, 1);
-    const VertexPick pv = draw_vertex(g.seed[0], g.vert, g.n, a.x[0], a.x[1]);
+    const VertexPick pv = draw_vertex<HINT>(g.seed[0], g.vert, g.n, a.x[0], a.x[1]);
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
     const Pick pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, a.x[2], a.x[3]);
@@ -245,7 +252,7 @@ __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t 
     const uint32_t A[3] = {v, pu.id, w}, B[3] = {r, w, r};
     uint32_t f;
     if (HASH) {
-        f = probe_hash<3>(g, A, B);
+        f = probe_hash<3, HINT>(g, A, B);
     } else {
         const uint4 ur = make_uint4(pu.off, pu.deg, 0u, 0u), wr = ld4(g.vert + w), rr = ld4(g.vert + r);
         const uint4 ra[3] = {vr, ur, wr}, rb[3] = {rr, wr, rr};
@@ -257,12 +264,12 @@ __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t 
     return out;
 }
 
-template <bool HASH>
+template <bool HASH, bool HINT = false>
 __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
     const Words4 a = sample_words4(seed, 1, s, 0);
     const Words4 b = sample_words4(seed, 1, s, 1);
-    const VertexPick pv = draw_vertex(g.seed[1], g.vert, g.n, a.x[0], a.x[1]);
+    const VertexPick pv = draw_vertex<HINT>(g.seed[1], g.vert, g.n, a.x[0], a.x[1]);
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
     const Pick pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, a.x[2], a.x[3]);
@@ -281,7 +288,7 @@ __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lu
     const uint32_t A[6] = {pu.id, pu.id, w, v, w, r}, B[6] = {w, r, r, t, t, t};
     uint32_t f;
     if (HASH) {
-        f = probe_hash<6>(g, A, B);
+        f = probe_hash<6, HINT>(g, A, B);
     } else {
         const uint4 ur = make_uint4(pu.off, pu.deg, 0u, 0u);
         const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r), tr = ld4(g.vert + t);
@@ -320,13 +327,13 @@ __device__ __forceinline__ int min_slot(int cls, uint32_t c) {
     return kSlots;
 }
 
-template <bool HASH>
+template <bool HASH, bool HINT = false>
 __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *lut, const uint8_t *lutc, uint64_t seed,
                                              uint64_t s) {
     Sample out;
     const Words4 a = sample_words4(seed, 3, s, 0);
     const Words4 b = sample_words4(seed, 3, s, 1);
-    const VertexPick pv = draw_vertex(g.seed[3], g.mvert, g.n, a.x[0], a.x[1]);
+    const VertexPick pv = draw_vertex<HINT>(g.seed[3], g.mvert, g.n, a.x[0], a.x[1]);
     const uint32_t v = pv.v;
     const uint4 mv = pv.rec;                           // {off, d_v, Gamma-check_v}
     const uint64_t Gv = ((uint64_t)mv.w << 32) | mv.z;
@@ -365,7 +372,7 @@ __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *l
     const uint32_t A[3] = {v, u, w}, B[3] = {r, w, r};
     uint32_t f;
     if (HASH) {
-        f = probe_hash<3>(g, A, B);
+        f = probe_hash<3, HINT>(g, A, B);
     } else {
         const uint4 vr = make_uint4(mv.x, mv.y, 0u, 0u), ur = make_uint4(sb.x, sb.y, 0u, 0u);
         const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r);
@@ -430,11 +437,11 @@ __device__ __noinline__ void path5_fallback(const uint32_t *acc, const uint64_t 
 // STAGE 3.
 constexpr int kDeferred = 254;
 
-template <bool HASH, int STAGE>
+template <bool HASH, int STAGE, bool HINT = false>
 __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
     const Words4 a = sample_words4(seed, 2, s, 0);
-    const VertexPick pv = draw_vertex(g.seed[2], g.vert, g.n, a.x[0], a.x[1]);
+    const VertexPick pv = draw_vertex<HINT>(g.seed[2], g.vert, g.n, a.x[0], a.x[1]);
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
     Pick pu, pw;
@@ -478,7 +485,7 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
     const uint32_t A[6] = {v, v, u, u, w, r}, B[6] = {r, t, w, t, r, t};
     uint32_t f;
     if (HASH) {
-        f = probe_hash<6>(g, A, B);
+        f = probe_hash<6, HINT>(g, A, B);
     } else {
         const uint4 ur = make_uint4(pu.off, pu.deg, 0u, 0u), wr = make_uint4(pw.off, pw.deg, 0u, 0u);
         const uint4 rr = ld4(g.vert + r), tr = ld4(g.vert + t);
@@ -507,7 +514,7 @@ constexpr int min_blocks() { return 6; }
 template <int STAGE>
 constexpr int defer_min_blocks() { return STAGE == 1 ? 5 : 4; }
 
-template <int METHOD, bool RECORD, bool HASH>
+template <int METHOD, bool RECORD, bool HASH, bool HINT = false>
 __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGraph g, uint64_t first, uint64_t count, uint64_t seed,
                                                      uint64_t *partials, uint8_t *classes, uint32_t *verts) {
     __shared__ uint8_t lut[kLut];
@@ -531,10 +538,10 @@ __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGr
         if (i < count) {
             const uint64_t s = first + i;
             Sample sm;
-            if (METHOD == 0) sm = sample_moss4<HASH>(g, lut, seed, s);
-            else if (METHOD == 1) sm = sample_t5<HASH>(g, lut, seed, s);
-            else if (METHOD == 2) sm = sample_path5<HASH, 0>(g, lut, seed, s);
-            else sm = sample_min<HASH>(g, lut, lutc, seed, s);
+            if (METHOD == 0) sm = sample_moss4<HASH, HINT>(g, lut, seed, s);
+            else if (METHOD == 1) sm = sample_t5<HASH, HINT>(g, lut, seed, s);
+            else if (METHOD == 2) sm = sample_path5<HASH, 0, HINT>(g, lut, seed, s);
+            else sm = sample_min<HASH, HINT>(g, lut, lutc, seed, s);
             deferred = METHOD == 2 && sm.cls == kDeferred;
             if (!deferred) {
                 cls = METHOD == 3 ? min_slot(sm.cls, sm.v[4]) : sm.cls;
@@ -577,7 +584,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGr
 // launched with no more blocks than STAGE 1, adds into STAGE 1's rows.
 constexpr uint32_t kDeferList = 1024 + 32;   // a window's ids plus the carry-over
 
-template <bool RECORD, bool HASH, int STAGE>
+template <bool RECORD, bool HASH, int STAGE, bool HINT = false>
 __global__ void __launch_bounds__(kThreads, defer_min_blocks<STAGE>())
     k_sample_deferred(DevGraph g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
                       uint8_t *classes, uint32_t *verts) {
@@ -599,7 +606,7 @@ __global__ void __launch_bounds__(kThreads, defer_min_blocks<STAGE>())
         uint64_t i = 0;
         if ((uint32_t)lane < cnt) {
             i = lst[k0 + lane];   // < count: only drawn ids are flagged
-            const Sample sm = sample_path5<HASH, STAGE>(g, lut, seed, first + i);
+            const Sample sm = sample_path5<HASH, STAGE, HINT>(g, lut, seed, first + i);
             again = STAGE == 1 && sm.cls == kDeferred;
             if (!again) {
                 cls = sm.cls;
@@ -779,7 +786,9 @@ __global__ void k_reduce(const uint64_t *partials, int blocks, uint64_t *out, in
 template <int M, bool R>
 cudaError_t launch_one(const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
                        int blocks, uint8_t *classes, uint32_t *verts, cudaStream_t s) {
-    if (g.hash)
+    if (g.hash && g.filter)
+        k_sample<M, R, true, true><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    else if (g.hash)
         k_sample<M, R, true><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
     else
         k_sample<M, R, false><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
@@ -794,36 +803,48 @@ void upload_luts(const uint8_t *lut4, const uint8_t *lut5, const uint8_t *lutc) 
     cudaMemcpyToSymbol(g_lutc, lutc, 4096);
 }
 
-// resident blocks per SM of each sampler on each device, 0 until queried
-std::atomic<int> g_sample_per_sm[64][kMethods];
+// resident blocks per SM of each sampler variant (0 search, 1 hash, 2
+// filter) on each device, 0 until queried
+std::atomic<int> g_sample_per_sm[64][kMethods][3];
 
-int sample_blocks(int method, int device) {
-    const int sms = device_sms(device);
+template <int M>
+cudaError_t occupancy3(int (&per)[3]) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], k_sample<M, false, false>, kThreads, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], k_sample<M, false, true>, kThreads, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[2], k_sample<M, false, true, true>, kThreads, 0);
+    return e;
+}
+
+// resident blocks per SM of a variant (at least 1)
+int sample_per_sm(int method, int device, int variant) {
     const bool cached = device >= 0 && device < 64 && method >= 0 && method < kMethods;
     if (cached) {
-        const int c = g_sample_per_sm[device][method].load(std::memory_order_relaxed);
-        if (c > 0) return sms * c;
+        const int c = g_sample_per_sm[device][method][variant].load(std::memory_order_relaxed);
+        if (c > 0) return c;
     }
+    int per[3] = {1, 1, 1};
+    cudaError_t e;
+    if (method == 0) e = occupancy3<0>(per);
+    else if (method == 1) e = occupancy3<1>(per);
+    else if (method == 2) e = occupancy3<2>(per);
+    else e = occupancy3<3>(per);
+    for (int v = 0; v < 3; ++v) {
+        if (e != cudaSuccess || per[v] < 1) per[v] = 1;
+        if (cached && e == cudaSuccess) g_sample_per_sm[device][method][v].store(per[v], std::memory_order_relaxed);
+    }
+    return per[variant];
+}
+
+int sample_blocks(int method, int device) {
     int per = 1;
-    cudaError_t e = cudaSuccess;
-    int per_h = 1;
-    if (method == 0) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<0, false, false>, kThreads, 0);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_sample<0, false, true>, kThreads, 0);
-    } else if (method == 1) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<1, false, false>, kThreads, 0);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_sample<1, false, true>, kThreads, 0);
-    } else if (method == 2) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<2, false, false>, kThreads, 0);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_sample<2, false, true>, kThreads, 0);
-    } else {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample<3, false, false>, kThreads, 0);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_h, k_sample<3, false, true>, kThreads, 0);
-    }
-    if (e != cudaSuccess || per < 1) per = 1;
-    if (per_h > per) per = per_h;   // grid sized for the faster (hash) variant
-    if (cached && e == cudaSuccess) g_sample_per_sm[device][method].store(per, std::memory_order_relaxed);
-    return sms * per;
+    for (int v = 0; v < 3; ++v) per = std::max(per, sample_per_sm(method, device, v));
+    return device_sms(device) * per;   // the most any variant launches
+}
+
+int sample_launch_blocks(int method, int device, const DevGraph &g) {
+    return device_sms(device) * sample_per_sm(method, device, g.hash ? (g.filter ? 2 : 1) : 0);
 }
 
 namespace {
@@ -848,7 +869,10 @@ template <int STAGE>
 cudaError_t launch_deferred(const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
                             int blocks, uint8_t *classes, uint32_t *verts, cudaStream_t s) {
     const bool rec = classes != nullptr;
-    if (g.hash) {
+    if (g.hash && g.filter) {
+        if (rec) k_sample_deferred<true, true, STAGE, true><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+        else k_sample_deferred<false, true, STAGE, true><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    } else if (g.hash) {
         if (rec) k_sample_deferred<true, true, STAGE><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
         else k_sample_deferred<false, true, STAGE><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
     } else {
@@ -874,7 +898,7 @@ cudaError_t launch_counts(int method, const DevGraph &g, uint64_t first, uint64_
                           cudaStream_t s) {
     int dev = 0;
     cudaGetDevice(&dev);
-    const int blocks = sample_blocks(method, dev);
+    const int blocks = sample_launch_blocks(method, dev, g);
     cudaError_t e;
     if (method != 2) {
         if ((e = launch_sample(method, g, first, count, seed, partials, blocks, classes, verts, s)) != cudaSuccess)
