@@ -1,0 +1,58 @@
+"""bench.py's output contract and launch arithmetic, on the CPU: the
+reference arm (the CPU oracle) prints one JSON line with the keys the
+measurement contract names, and the launch count it claims for the GPU arm
+follows the kernels a step runs."""
+from __future__ import annotations
+
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+from conftest import ROOT
+
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_reference_arm_json_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "1", "--workload", "cl_n2k", "--budget", "200000"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["value"] > 0 and d["unit"] == "samples/s" and d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert "workload" in d["config"]
+
+
+@pytest.mark.parametrize("k,budget,mix,filtered,expected", [
+    # load 7 + build 8 + finalize 1; T-5: sampler + reduce; Path-5: main, two redraw stages, reduce per chunk
+    (5, 100_000_000, False, False, 16 + 2 + 4),
+    (5, 1_000_000_000, False, True, 17 + 2 + 4 * 8),   # 5e8 Path-5 ids: 8 chunks of 2^26
+    (4, 100_000_000, False, False, 16 + 2),
+    (4, 100_000_000, True, False, 16 + 12 + 2 + 2),    # MOSS-4 + MOSS-4Min with its 12 table kernels
+])
+def test_launches_per_step(k, budget, mix, filtered, expected):
+    assert bench.DEFER_CHUNK == 1 << 26
+    assert bench.launches_per_step(k, budget, mix, filtered) == expected
+
+
+def test_resolved_probe_follows_the_hash_size():
+    import numpy as np
+    small = np.array([0, 1_000_000], dtype=np.int64)     # 2^19 buckets of 32 B: 16 MiB
+    large = np.array([0, 68_000_000], dtype=np.int64)    # 2^26 buckets: 2 GiB
+    assert bench.resolved_probe("auto", small) == "hash"
+    assert bench.resolved_probe("auto", large) == "filter"
+    assert bench.resolved_probe("search", large) == "search"
