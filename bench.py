@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -184,8 +185,11 @@ class Clocks:
     def __init__(self, device: int):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/moss_clocks_{os.getpid()}.csv"
+        # the raw samples go to MOSS_CLOCKS_DIR when set (kept for inspection),
+        # else to a per-process temporary file; the JSON line carries the summary
+        d = os.environ.get("MOSS_CLOCKS_DIR")
+        self.path = (os.path.join(d, f"clocks_rank{device}.csv") if d and os.path.isdir(d)
+                     else os.path.join(tempfile.gettempdir(), f"moss_clocks_{os.getpid()}_{device}.csv"))
 
     def start(self):
         try:
