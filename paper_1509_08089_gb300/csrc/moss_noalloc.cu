@@ -35,6 +35,7 @@ constexpr size_t kNoAllocScratchBytes = (size_t)kNoAllocMaxBlocks * kSlots * siz
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) uint64_t g_noalloc_partials[kNoAllocMaxBlocks * kSlots];
+static_assert(sizeof(g_noalloc_partials) == kNoAllocScratchBytes, "the held scratch is the stated size");
 
 std::mutex g_mutex;
 uint64_t *g_scratch[kMaxDevices] = {};
