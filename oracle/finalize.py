@@ -198,8 +198,8 @@ def finalize_moss4min(m, mm, K: int, Kmin: int, Gamma: int, Gamma_min: int, Lamb
         tri = m[0] * G / (6.0 * K)
         tri_var = tri / K * (G / 6.0 - tri)
     return {"k": 4, "K": (K if avail[0] else 0, Kmin if avail[1] else 0), "est": est, "var": var, "lam": lam,
-            "eta1": e4, "eta2": em, "h": h, "p": p, "cov": cov, "triangles": tri, "triangles_var": tri_var,
-            "conc": concentrations(est, 6)}
+            "eta1": e4, "eta2": em, "h": h, "p": p, "plug": plug, "cov": cov, "triangles": tri,
+            "triangles_var": tri_var, "conc": concentrations(est, 6)}
 
 
 def concentrations(est, n_classes: int) -> np.ndarray:
@@ -295,4 +295,4 @@ def finalize_moss5(m1, m2, K1: int, K2: int, Gamma1: int, Gamma2: int, Lambda4: 
                 c2 -= PHI5[i - 1, 2] * cov[i, j]
             cov[2, j] = cov[j, 2] = c2
     return {"k": 5, "K": (K1, K2), "est": est, "var": var, "lam": lam, "eta1": eh[0], "eta2": eh[1],
-            "p": p, "cov": cov, "conc": concentrations(est, 21)}
+            "p": p, "plug": plug, "cov": cov, "conc": concentrations(est, 21)}

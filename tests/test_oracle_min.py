@@ -346,3 +346,80 @@ def test_mix_with_moss4(g_small):
     # eq. (2) with the mixed classes
     for row in mix:
         assert row[2] == pytest.approx(g.Lambda3 - row[4] - 2 * row[5] - 4 * row[6])
+
+
+# --------------------------------------------------------------------------
+# The plug-in e_i = (K n-hat_i + K-check n-check_i) / (K + K-check) that sets
+# the Theorem 1 weights of the 4-cycle, diamond and 4-clique.  At the exact
+# expectations of both count vectors -- E m_i = K 2 phi_i n_i / Gamma
+# (Theorem 2) and E m_{i,c} = K-check 2 c N_{i,c} / Gamma-check, N_{i,c} the
+# class-i CISes with c(s) = c counted by brute force -- both estimates, the
+# plug-in and the mean of 1/c equal their exact values, so the weights and
+# variances equal those computed from the exact counts.  A planted slip in the
+# plug-in's denominator must fail.
+# --------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def g_small_c():
+    rp, col = synth.chung_lu(120, 2.2, 7.0, 30.0, seed=5)
+    b = Brute(rp, col)
+    cis = brute_force_cis(rp, col, 4)
+    onto = defaultdict(int)
+    for v, u, w, r in b.tuples():
+        if r != w:
+            onto[frozenset((v, u, w, r))] += 1
+    n = np.zeros(22)
+    for s, c in cis.items():
+        n[c] += 1
+    Nc = defaultdict(int)
+    for s, t in onto.items():
+        assert t % 2 == 0
+        Nc[(cis[s], t // 2)] += 1
+    g = oracle.OracleGraph(rp, col)
+    g.build_min()
+    return g, n, Nc
+
+
+def _check_min_plugin_at_expectation(fin, g, n, Nc, K, Km):
+    from oracle.finalize import PHI4
+    m = np.zeros(22)
+    for i in (1, 3, 4, 5, 6):
+        m[i] = K * 2.0 * PHI4[i - 1, 0] / float(g.Gamma[0]) * n[i]
+    mm = np.zeros(22)
+    for (cls, c), cnt in Nc.items():
+        sl = oracle.min_slot(cls, c)
+        if sl >= 0:
+            mm[sl] += Km * 2.0 * c * cnt / float(g.Gamma_min)
+    plug = fin(m, mm, K, Km, g.Gamma[0], g.Gamma_min, g.Lambda3)
+    fixed = fin(m, mm, K, Km, g.Gamma[0], g.Gamma_min, g.Lambda3, eta=n)
+    checked = 0
+    for i in (3, 5, 6):
+        if n[i] == 0:
+            continue
+        hbar = sum(cnt / c for (cls, c), cnt in Nc.items() if cls == i) / n[i]
+        assert plug["h"][i] == pytest.approx(hbar, rel=1e-12), i
+        assert plug["eta1"][i] == pytest.approx(n[i], rel=1e-12), i
+        assert plug["eta2"][i] == pytest.approx(n[i], rel=1e-12), i
+        assert plug["plug"][i] == pytest.approx(n[i], rel=1e-12), i
+        assert plug["lam"][0, i] == pytest.approx(fixed["lam"][0, i], rel=1e-12), i
+        assert plug["lam"][1, i] == pytest.approx(fixed["lam"][1, i], rel=1e-12), i
+        assert plug["var"][i] == pytest.approx(fixed["var"][i], rel=1e-12), i
+        checked += 1
+    assert checked >= 2
+
+
+@pytest.mark.parametrize("K,Km", [(4000, 4000), (1000, 9000), (9000, 700)])
+def test_min_plugin_exact_at_expected_counts(g_small_c, K, Km):
+    g, n, Nc = g_small_c
+    _check_min_plugin_at_expectation(oracle.finalize_moss4min, g, n, Nc, K, Km)
+
+
+def test_min_plugin_pin_catches_a_planted_slip(g_small_c):
+    import inspect
+    g, n, Nc = g_small_c
+    src = inspect.getsource(oracle.finalize)
+    good = "e = (K * e4[i] + Kmin * em[i]) / (K + Kmin)"
+    assert src.count(good) == 1
+    ns: dict = {}
+    exec(compile(src.replace(good, "e = (K * e4[i] + Kmin * em[i]) / (2 * K)"), "planted", "exec"), ns)
+    with pytest.raises(AssertionError):
+        _check_min_plugin_at_expectation(ns["finalize_moss4min"], g, n, Nc, 1000, 9000)

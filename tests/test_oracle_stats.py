@@ -176,3 +176,90 @@ def test_covariance_matches_sampling(g200):
         emp = np.cov(est[:, i], est[:, j])[0, 1]
         se = math.sqrt((ref[i, i] * ref[j, j] + ref[i, j] ** 2) / R)
         assert abs(emp - ref[i, j]) < Z * se, (i, j, emp, ref[i, j])
+
+
+# --------------------------------------------------------------------------
+# The pooled plug-in eta~ = (m1 + m2) / (K1 p1 + K2 p2) that sets lambda for
+# the classes of Omega_1 and Omega_2 (mix estimator, Sec. 5.1.3; Theorem 10).
+# Two properties fix it independently of its formula:
+#  (a) it is linear in the counts and equals eta at their expectations
+#      E m^(l)_i = K_l p^(l)_i eta_i (Theorems 6, 8), so it is exactly unbiased
+#      and, fed those expectations, lambda equals the fixed-lambda value of
+#      Theorem 10 computed from the exact counts;
+#  (b) it is the maximum of the likelihood of the common eta_i given both
+#      sub-methods' hit counts, each a rare-event (Poisson) count of mean
+#      K_l p^(l)_i eta_i.
+# A planted slip in its denominator must fail (a).
+# --------------------------------------------------------------------------
+def _mixed_classes():
+    return [i for i in range(1, 22) if PHI5[i - 1, 0] > 0 and PHI5[i - 1, 1] > 0]
+
+
+def _expected_counts(g, eta, K1, K2):
+    m = np.zeros((2, 22))
+    for l, K in ((0, K1), (1, K2)):
+        for i in range(1, 22):
+            if PHI5[i - 1, l] > 0:
+                m[l, i] = K * 2.0 * PHI5[i - 1, l] / float(g.Gamma[1 + l]) * eta[i]
+    return m
+
+
+def _check_plugin_at_expectation(fin, g, eta, K1, K2):
+    m = _expected_counts(g, eta, K1, K2)
+    plug = fin(m[0], m[1], K1, K2, g.Gamma[1], g.Gamma[2], g.Lambda4)
+    fixed = fin(m[0], m[1], K1, K2, g.Gamma[1], g.Gamma[2], g.Lambda4, eta=eta)
+    for i in _mixed_classes():
+        if eta[i] == 0:
+            continue
+        # the single-source estimates agree (both eta_i) and the pooled value equals them
+        assert plug["eta1"][i] == pytest.approx(eta[i], rel=1e-12)
+        assert plug["eta2"][i] == pytest.approx(eta[i], rel=1e-12)
+        assert plug["plug"][i] == pytest.approx(eta[i], rel=1e-12), i
+        assert plug["lam"][0, i] == pytest.approx(fixed["lam"][0, i], rel=1e-12), i
+        assert plug["lam"][1, i] == pytest.approx(fixed["lam"][1, i], rel=1e-12), i
+        assert plug["var"][i] == pytest.approx(fixed["var"][i], rel=1e-12), i
+
+
+@pytest.mark.parametrize("K1,K2", [(4000, 4000), (1000, 9000), (12345, 321)])
+def test_pooled_plugin_exact_at_expected_counts(g200, K1, K2):
+    eta = np.array(GOLD["cl_n200"]["esu5"], dtype=np.float64)
+    assert sum(eta[i] > 0 for i in _mixed_classes()) >= 5
+    _check_plugin_at_expectation(oracle.finalize_moss5, g200, eta, K1, K2)
+
+
+def test_pooled_plugin_is_the_joint_likelihood_maximum(g200):
+    from scipy.optimize import minimize_scalar
+    K1, K2 = 30_000, 20_000
+    m1 = g200.run(oracle.T5, 17, K1).astype(np.float64)
+    m2 = g200.run(oracle.PATH5, 17, K2).astype(np.float64)
+    r = oracle.finalize_moss5(m1, m2, K1, K2, g200.Gamma[1], g200.Gamma[2], g200.Lambda4)
+    checked = 0
+    for i in _mixed_classes():
+        if m1[i] + m2[i] == 0:
+            assert r["plug"][i] == 0.0
+            continue
+        rate = np.array([K1 * r["p"][0, i], K2 * r["p"][1, i]])
+        cnt = np.array([m1[i], m2[i]])
+
+        def nll(x):
+            return float(np.sum(rate * x - cnt * np.log(rate * x)))
+        hi = 10.0 * (cnt.sum() + 1) / rate.min()
+        opt = minimize_scalar(nll, bounds=(1e-12 * hi, hi), method="bounded",
+                              options={"xatol": 1e-10 * hi, "maxiter": 500})
+        assert opt.x == pytest.approx(r["plug"][i], rel=1e-6), i
+        checked += 1
+    assert checked >= 5
+
+
+def test_pooled_plugin_pin_catches_a_planted_slip(g200):
+    """The pin above fails on a copy of the oracle's finalize whose pooled
+    denominator is (K1 + K2) p^(1) instead of K1 p^(1) + K2 p^(2)."""
+    import inspect
+    src = inspect.getsource(oracle.finalize)
+    good = "e = (m1[i] + m2[i]) / (K1 * p[0, i] + K2 * p[1, i])"
+    assert src.count(good) == 1
+    ns: dict = {}
+    exec(compile(src.replace(good, "e = (m1[i] + m2[i]) / ((K1 + K2) * p[0, i])"), "planted", "exec"), ns)
+    eta = np.array(GOLD["cl_n200"]["esu5"], dtype=np.float64)
+    with pytest.raises(AssertionError):
+        _check_plugin_at_expectation(ns["finalize_moss5"], g200, eta, 4000, 4000)
