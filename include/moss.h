@@ -183,7 +183,9 @@ int moss_sample_counts(moss_graph *g, int method, uint64_t first, uint64_t count
  * partial counts live in one fixed device array of 360,448 bytes (2048 rows of
  * 22 uint64) that every GPU loading the library holds until exit.  The first
  * call on a device looks up that array's address (cudaGetSymbolAddress), so
- * make it before any stream capture.  Calls share the array: calls whose work
+ * make it before any stream capture; the address is kept for the life of the
+ * process, so after a cudaDeviceReset of that device the entry point must not
+ * be called again.  Calls share the array: calls whose work
  * overlaps on the GPU race and must be ordered by the caller.  MOSS_EOVERFLOW
  * if the device needs more than 2048 blocks.  Asynchronous on stream. */
 int moss_sample_counts_noalloc(moss_graph *g, int method, uint64_t first, uint64_t count, uint64_t seed,

@@ -102,7 +102,6 @@ int plan(moss_batch *b) {
             graphs.push_back(gi.view);
             gkeys.push_back(q.g);
         }
-        const bool sigma = (gi.built >> 3) & 1u;
         BatchRequest &br = reqs[r];
         br.in.k = q.k;
         br.in.mix = q.mix ? 1 : 0;
@@ -126,8 +125,7 @@ int plan(moss_batch *b) {
         }
         for (int j = 0; j < nm; ++j) {
             const int m = methods[j];
-            const unsigned bit = m == 3 ? 5u : (unsigned)m;   // MOSS-4Min tables: bit 5
-            if (!sigma || !((gi.built >> bit) & 1u)) return set_error(MOSS_ESTATE, "tables of a batched graph not built");
+            if (!gi.ready[m]) return set_error(MOSS_ESTATE, "tables of a batched graph not built");
             br.in.K[j] = Ks[j];
             if (Ks[j] == 0) continue;
             BatchTask t;
@@ -254,8 +252,8 @@ int moss_batch_add(moss_batch *b, moss_graph *g, int k, uint64_t budget, uint64_
     GraphInfo gi;
     graph_info(g, &gi);
     if (gi.device != b->device) return set_error(MOSS_EINVAL, "graph lives on another device than the batch");
-    const unsigned need = (1u << 3) | (k == 4 ? 1u : 6u);
-    if ((gi.built & need) != need) return set_error(MOSS_ESTATE, "tables for this k are not built");
+    if (k == 4 ? !gi.ready[0] : !(gi.ready[1] && gi.ready[2]))
+        return set_error(MOSS_ESTATE, "tables for this k are not built");
     b->reqs.push_back(Req{g, k, budget, seed, false, 0});
     if (index) *index = (int)b->reqs.size() - 1;
     b->dirty = true;
@@ -267,8 +265,7 @@ int moss_batch_add_min(moss_batch *b, moss_graph *g, uint64_t budget, uint64_t b
     GraphInfo gi;
     graph_info(g, &gi);
     if (gi.device != b->device) return set_error(MOSS_EINVAL, "graph lives on another device than the batch");
-    const unsigned need = (1u << 3) | 1u | (1u << 5);
-    if ((gi.built & need) != need) return set_error(MOSS_ESTATE, "MOSS-4 and MOSS-4Min tables are not built");
+    if (!gi.ready[0] || !gi.ready[3]) return set_error(MOSS_ESTATE, "MOSS-4 and MOSS-4Min tables are not built");
     b->reqs.push_back(Req{g, 4, budget, seed, true, budget_min});
     if (index) *index = (int)b->reqs.size() - 1;
     b->dirty = true;

@@ -948,7 +948,10 @@ int graph_info(const moss_graph *g, GraphInfo *out) {
     out->tot = g->tot;
     out->device = g->device;
     out->built = g->built;
-    for (int l = 0; l < kMethods; ++l) out->total_nonzero[l] = g->tot_h.gamma[l] != 0;
+    for (int l = 0; l < kMethods; ++l) {
+        out->total_nonzero[l] = g->tot_h.gamma[l] != 0;
+        out->ready[l] = method_ready(g, l);
+    }
     return MOSS_OK;
 }
 

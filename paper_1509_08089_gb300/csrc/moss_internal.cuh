@@ -350,8 +350,11 @@ struct GraphInfo {
     DevGraph view;
     const DevTotals *tot;
     int device;
-    unsigned built;          // bit l: vertex table l; bit 3: sigma tables; bit 4: edge hash; bit 5: MOSS-4Min
+    unsigned built;          // bit l: vertex table l; bit 3: sigma tables; bit 4: edge hash; bit 5: MOSS-4Min;
+                             // bit 6: edge filter
     bool total_nonzero[kMethods];   // Gamma, Gamma^(1), Gamma^(2), Gamma-check > 0
+    bool ready[kMethods];    // the method can sample: its tables and the probe tables of the graph's
+                             // probe strategy are built (what moss_sample_counts requires)
 };
 }  // namespace moss
 

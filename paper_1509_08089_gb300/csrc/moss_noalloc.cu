@@ -16,7 +16,9 @@
 // cannot use the symbol as a device address, so the first call on each device
 // looks up the array's device address with cudaGetSymbolAddress (with that
 // device current) and caches it; that first call should therefore come
-// before any stream capture.  All calls share the one array: each call's
+// before any stream capture.  The cached address lives as long as the
+// process: a cudaDeviceReset of the device makes it stale, so the entry point
+// is not to be called again after one.  All calls share the one array: each call's
 // sampling kernel overwrites every row it later reads, so nothing needs
 // clearing, but calls whose kernels overlap on the GPU (different streams,
 // no ordering between them) race on the array and must be serialised by the
@@ -66,9 +68,7 @@ extern "C" int moss_sample_counts_noalloc(moss_graph *g, int method, uint64_t fi
     if (method < 0 || method >= kMethods) return set_error(MOSS_EINVAL, "method must be 0, 1, 2 or 3");
     GraphInfo gi;
     graph_info(g, &gi);
-    const bool ready = method == MOSS_METHOD_MOSS4MIN ? ((gi.built >> 5) & 1u) != 0
-                                                     : ((gi.built >> 3) & 1u) && ((gi.built >> method) & 1u);
-    if (!ready) return set_error(MOSS_ESTATE, "tables for this method are not built");
+    if (!gi.ready[method]) return set_error(MOSS_ESTATE, "tables for this method are not built");
     if (count > 0 && !gi.total_nonzero[method])
         return set_error(MOSS_EINVAL, "method has total weight 0 on this graph: no sample exists");
     if (first + count < first) return set_error(MOSS_EOVERFLOW, "sample range wraps");

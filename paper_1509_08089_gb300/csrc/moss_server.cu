@@ -423,7 +423,8 @@ int moss_server_add_graph(moss_server *s, moss_graph *g, int *graph_id) {
     GraphInfo gi;
     graph_info(g, &gi);
     if (gi.device != s->device) return set_error(MOSS_EINVAL, "graph lives on another device");
-    if ((gi.built & 0xFu) != 0xFu) return set_error(MOSS_ESTATE, "server graphs need the tables of k = 4 and 5");
+    if (!gi.ready[0] || !gi.ready[1] || !gi.ready[2])
+        return set_error(MOSS_ESTATE, "server graphs need the tables of k = 4 and 5");
     s->graphs.push_back(g);
     s->ginfo.push_back(gi);
     if (graph_id) *graph_id = (int)s->graphs.size() - 1;
@@ -475,8 +476,7 @@ int moss_server_submit_min(moss_server *s, int graph_id, uint64_t budget, uint64
     std::unique_lock<std::mutex> lk(s->mu);
     if (s->status != MOSS_OK) return set_error(s->status, "the server stopped after an error");
     if (graph_id < 0 || graph_id >= (int)s->graphs.size()) return set_error(MOSS_EINVAL, "unknown graph id");
-    const unsigned need = (1u << 3) | 1u | (1u << 5);
-    if ((s->ginfo[graph_id].built & need) != need)
+    if (!s->ginfo[graph_id].ready[0] || !s->ginfo[graph_id].ready[3])
         return set_error(MOSS_ESTATE, "MOSS-4 and MOSS-4Min tables of this graph are not built");
     if (!s->started) {
         s->started = true;

@@ -22,7 +22,7 @@ count is exact per sample; the mean over a few thousand samples is the
 per-sample figure used by the roofline ("achieved" = figure x 32 B x samples
 / kernel time).
 
-    python oracle/sector_model.py [workload] [samples]
+    python tests/golden/sector_model.py [workload] [samples]
 writes tests/golden/sectors_<workload>.json.  Calls only the oracle and the
 shared input generator.
 """
@@ -32,7 +32,7 @@ import json
 import os
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
@@ -340,7 +340,7 @@ def model(workload: str, samples: int = 4000, seed: int = 42) -> dict:
                       "4 B ids and ACC, 8 B Q, 32 B edge-hash buckets (home bucket counted), 4 B edge-filter words "
                       "(the set's bucket only when the filter passes); MOSS-4Min: 16 B "
                       "vertex, 32 B pick (32 B slot where too wide), 8 B list records; 32 B sectors"),
-           "source": "written by oracle/sector_model.py"}
+           "source": "written by tests/golden/sector_model.py"}
     for probe, suffix in (("search", "_search"), ("hash", "_hash"), ("filter", "_filter")):
         rep = Replay(rp, col, probe)
         for method, name in ((0, "MOSS4"), (1, "T5"), (2, "PATH5")):

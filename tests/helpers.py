@@ -146,3 +146,45 @@ def expected_slot_neighbour(rp: np.ndarray, col: np.ndarray, twin: np.ndarray):
     nb = np.where(hub, SLOT_HUB, twin | (dx << 16))
     off = np.where(hub, twin, rp64[c64])
     return nb.astype(np.uint32), off.astype(np.uint32)
+
+
+def oracle_counts(og, method: int, seed: int, first: int, count: int, threads: int | None = None) -> np.ndarray:
+    """The oracle's counts of samples [first, first + count) of one method,
+    split into id chunks run on all host cores.  The oracle's sampler only
+    reads its tables and ctypes releases the GIL around it, so threads share
+    one oracle graph; integer counts add up the same in any order."""
+    import concurrent.futures as cf
+    threads = threads or os.cpu_count() or 1
+    chunk = max(1 << 16, -(-count // (8 * threads)))
+    parts = [(a, min(chunk, first + count - a)) for a in range(first, first + count, chunk)]
+    total = np.zeros(22, dtype=np.uint64)
+    if not parts:
+        return total
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        for c in ex.map(lambda p: og.run(method, seed, p[1], first=p[0]), parts):
+            total += c
+    return total
+
+
+def close_estimates(r, o, og, k):
+    """A library result r against the oracle's finalize o: estimates,
+    variances and concentrations within 1e-9 relative (the class closed by
+    an identity, n_2 or eta_2, relative to Lambda_3 or Lambda_4), the
+    triangle estimate (k = 4) and the mix weights (k = 5)."""
+    n = 7 if k == 4 else 22
+    lam = float(og.Lambda3 if k == 4 else og.Lambda4)
+    for i in range(1, n):
+        if i == 2:
+            assert abs(r["est"][i] - o["est"][i]) <= 1e-9 * max(lam, 1.0), (k, i)
+            assert abs(r["var"][i] - o["var"][i]) <= 1e-9 * max(abs(o["var"][i]), 1.0) + 1e-9 * lam ** 2 / 1e6
+            continue
+        assert abs(r["est"][i] - o["est"][i]) <= 1e-9 * max(abs(o["est"][i]), 1e-300), (k, i, r["est"][i], o["est"][i])
+        assert abs(r["var"][i] - o["var"][i]) <= 1e-9 * max(abs(o["var"][i]), 1e-300), (k, i)
+    for i in range(1, n):
+        assert abs(r["conc"][i] - o["conc"][i]) <= 1e-9 * max(abs(o["conc"][i]), 1e-300) + 1e-12, (k, i)
+    if k == 4:
+        assert abs(r["triangles"] - o["triangles"]) <= 1e-9 * max(abs(o["triangles"]), 1e-300)
+    else:
+        for i in range(1, n):
+            for l in range(2):
+                assert abs(r["lam"][l][i] - o["lam"][l][i]) <= 1e-9

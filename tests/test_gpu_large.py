@@ -1,8 +1,10 @@
 """The maximum-size workload: Chung-Lu n=4M, exponent 2.1, mean degree 17,
 max degree 20,000 (~35M edges, ~1.4 GB of device tables), 1e9 samples per
 motif size.  Tables are compared with the oracle's bit for bit, samples one
-by one at the end of the 1e9 range, and the full-budget counts by their
-invariants and by the finalize of the same counts."""
+by one at the end of the 1e9 range, the full-budget counts by their
+invariants and by the finalize of the same counts, and the counts of a
+1.4e8-id slice of every method with the oracle's over the same ids (Path-5's
+slice starts past the first 2^26-id deferral chunk and spans three of them)."""
 from __future__ import annotations
 
 import numpy as np
@@ -11,7 +13,7 @@ import pytest
 import oracle
 import synth
 import paper_1509_08089_gb300 as moss
-from helpers import expected_slot_neighbour, slot_twin
+from helpers import expected_slot_neighbour, oracle_counts, slot_twin
 from oracle.finalize import PHI5
 
 torch = pytest.importorskip("torch")
@@ -92,3 +94,19 @@ def test_large_full_budget(big, k):
         assert np.array_equal(cls.cpu().numpy(), ocls)
         ncol = 4 if method == 0 else 5
         assert np.array_equal(verts.cpu().numpy().view(np.uint32).reshape(4000, 5)[:, :ncol], overts[:, :ncol])
+
+
+SLICE = 140_000_000
+
+
+@pytest.mark.parametrize("method,first", [(0, 123_457), (1, 7), (2, (1 << 26) + 4_099)])
+def test_large_slice_counts_match_oracle(big, method, first):
+    """The counts of ids [first, first + 1.4e8) of one method, drawn by the
+    library's sampling call, equal the oracle's over the same ids."""
+    rp, col, og, g = big
+    counts = torch.zeros(22, dtype=torch.int64, device="cuda")
+    moss.moss_sample_counts(g.handle, method, first, SLICE, 42, counts)
+    torch.cuda.synchronize()
+    got = counts.cpu().numpy().view(np.uint64)
+    assert int(got.sum()) == SLICE
+    assert np.array_equal(got, oracle_counts(og, method, 42, first, SLICE))

@@ -14,7 +14,7 @@ import pytest
 import oracle
 import synth
 import paper_1509_08089_gb300 as moss
-from helpers import expected_slot_neighbour, slot_twin
+from helpers import close_estimates, expected_slot_neighbour, oracle_counts, slot_twin
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -150,7 +150,7 @@ def filter_words(filter_hash, nnz):
 def test_edge_filter_bits(name):
     """The filter holds exactly the bits of the edges (no false negatives) and
     rejects most non-edges."""
-    from oracle.sector_model import filter_hash, filter_mask
+    from golden.sector_model import filter_hash, filter_mask
     rp, col, og, g = pair(name)
     g.set_probe(moss.PROBE_FILTER)
     nnz = len(col)
@@ -215,26 +215,6 @@ def test_counts_and_estimates(name):
         assert tuple(r["K"]) == tuple(o["K"])
         close_estimates(r, o, og, k)
     g.set_probe(moss.PROBE_AUTO)
-
-
-def close_estimates(r, o, og, k):
-    n = 7 if k == 4 else 22
-    lam = float(og.Lambda3 if k == 4 else og.Lambda4)
-    for i in range(1, n):
-        if i == 2:
-            assert abs(r["est"][i] - o["est"][i]) <= 1e-9 * max(lam, 1.0), (k, i)
-            assert abs(r["var"][i] - o["var"][i]) <= 1e-9 * max(abs(o["var"][i]), 1.0) + 1e-9 * lam ** 2 / 1e6
-            continue
-        assert abs(r["est"][i] - o["est"][i]) <= 1e-9 * max(abs(o["est"][i]), 1e-300), (k, i, r["est"][i], o["est"][i])
-        assert abs(r["var"][i] - o["var"][i]) <= 1e-9 * max(abs(o["var"][i]), 1e-300), (k, i)
-    for i in range(1, n):
-        assert abs(r["conc"][i] - o["conc"][i]) <= 1e-9 * max(abs(o["conc"][i]), 1e-300) + 1e-12, (k, i)
-    if k == 4:
-        assert abs(r["triangles"] - o["triangles"]) <= 1e-9 * max(abs(o["triangles"]), 1e-300)
-    else:
-        for i in range(1, n):
-            for l in range(2):
-                assert abs(r["lam"][l][i] - o["lam"][l][i]) <= 1e-9
 
 
 @pytest.mark.parametrize("k", [4, 5])
@@ -331,8 +311,13 @@ def test_full_size_bench_config():
             assert r["hits"][0][i] == 0
         if PHI5[i - 1, 1] == 0:
             assert r["hits"][1][i] == 0
-    # the device finalize of these counts equals the oracle's finalize of them
-    o = oracle.finalize_moss5(r["hits"][0], r["hits"][1], K1, K2, og.Gamma[1], og.Gamma[2], og.Lambda4)
+    # all 2 x 22 counts of the full launch against the oracle's, run over the
+    # same 1e8 sample ids on every host core
+    om = [oracle_counts(og, method, 42, 0, K) for method, K in ((1, K1), (2, K2))]
+    assert np.array_equal(r["hits"][0], om[0])
+    assert np.array_equal(r["hits"][1], om[1])
+    # so the device finalize of these counts is compared with the oracle's whole path
+    o = oracle.finalize_moss5(om[0], om[1], K1, K2, og.Gamma[1], og.Gamma[2], og.Lambda4)
     close_estimates(r, o, og, 5)
     # the last samples of both sub-methods, one by one against the oracle
     for method, K in ((1, K1), (2, K2)):

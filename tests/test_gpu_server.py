@@ -11,22 +11,29 @@ import threading
 import numpy as np
 import pytest
 
+import oracle
 import synth
 import paper_1509_08089_gb300 as moss
+from helpers import close_estimates
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
-def pool():
+def pool_csrs():
     csrs = [synth.chung_lu(n, g, d, 60.0, seed=s)
             for n, g, d, s in ((800, 2.3, 6.0, 1), (3000, 2.6, 8.0, 2), (6000, 2.2, 10.0, 3))]
     csrs.append(synth.rgg(4000, 14.0, seed=4))
     graphs = [moss.Graph(rp, col) for rp, col in csrs]
-    yield graphs
+    yield csrs, graphs
     for g in graphs:
         g.close()
+
+
+@pytest.fixture(scope="module")
+def pool(pool_csrs):
+    return pool_csrs[1]
 
 
 def submit_all(server, gids, plan, out, lock):
@@ -127,3 +134,60 @@ def test_server_rejects_bad_requests(pool):
         server.wait(rid)
         with pytest.raises(moss.MossError):
             server.wait(rid)               # a request is waited for once
+
+
+def test_served_results_match_oracle(pool_csrs):
+    """Served results -- k = 4 and k = 5 with fixed budgets, k = 4 and k = 5
+    with target errors (budget from the pilot), and a MOSS-4 + MOSS-4Min
+    request -- each against the oracle's whole path with the request's final
+    budget and seed: counts bit for bit, estimates within 1e-9."""
+    csrs, graphs = pool_csrs
+    mask = (1 << 4) | (1 << 5) | moss.TABLES_4MIN
+    rp_m, col_m = synth.chung_lu(2500, 2.3, 8.0, 60.0, seed=7)
+    gmin = moss.Graph(rp_m, col_m, k_mask=mask)
+    try:
+        with moss.Server(max_active=16, tick_samples=400_000, tile_samples=2048, min_budget=10_000,
+                         max_budget=3_000_000, pilot_samples=20_000) as server:
+            gids = [server.add_graph(g) for g in graphs]
+            gid_m = server.add_graph(gmin)
+            plan = [(2, 4, 700_001, 0.0, 11), (1, 5, 900_000, 0.0, 12), (0, 4, 0, 0.03, 13),
+                    (3, 5, 0, 0.04, 14), (2, 5, 0, 0.05, 15)]
+            subs = [(gi, k, seed, server.submit(gids[gi], k, budget=b, target_rse=eps, seed=seed))
+                    for gi, k, b, eps, seed in plan]
+            rid_m = server.submit_min(gid_m, 300_000, 200_000, seed=16)
+            served = [(gi, k, seed, *server.wait(rid, 300.0)) for gi, k, seed, rid in subs]
+            r_m, _ = server.wait(rid_m, 300.0)
+        assert sum(1 for _, _, _, _, st in served if st["budget"] not in (700_001, 900_000)) == 3
+        for gi, k, seed, r, st in served:
+            og = oracle.OracleGraph(*csrs[gi])
+            o = og.estimate(k, st["budget"], seed)
+            assert tuple(r["K"]) == tuple(o["K"])
+            methods = (oracle.MOSS4,) if k == 4 else (oracle.T5, oracle.PATH5)
+            for slot, method in enumerate(methods):
+                K = o["K"][slot]
+                ref = og.run(method, seed, K) if K else np.zeros(22, np.uint64)
+                assert np.array_equal(r["hits"][slot], ref), (gi, k, slot)
+            close_estimates(r, o, og, k)
+        og = oracle.OracleGraph(rp_m, col_m)
+        o = og.estimate_min(300_000, 200_000, 16)
+        assert np.array_equal(r_m["hits"][0], og.run(oracle.MOSS4, 16, 300_000))
+        assert np.array_equal(r_m["hits"][1], og.run(oracle.MOSS4MIN, 16, 200_000))
+        for i in range(1, 7):
+            tol = 1e-9 * (max(float(og.Lambda3), 1.0) if i == 2 else max(abs(o["est"][i]), 1e-300))
+            assert abs(r_m["est"][i] - o["est"][i]) <= tol, i
+    finally:
+        gmin.close()
+
+
+def test_admission_waits_for_free_memory(pool):
+    """With reserve_bytes above the device's free memory no request is
+    admitted: it stays pending, and a short wait ends with MOSS_EBUSY."""
+    free, _total = torch.cuda.mem_get_info()
+    with moss.Server(reserve_bytes=free + (64 << 30)) as server:
+        gid = server.add_graph(pool[0])
+        rid = server.submit(gid, 4, budget=10_000, seed=1)
+        with pytest.raises(moss.MossError) as ei:
+            server.wait(rid, 0.3)
+        assert ei.value.status == moss.MOSS_EBUSY
+        st = server.stats()
+        assert st["pending"] == 1 and st["active"] == 0 and st["completed"] == 0 and st["ticks"] == 0

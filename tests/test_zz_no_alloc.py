@@ -52,3 +52,21 @@ def test_noalloc_rejects_unbuilt_tables():
         with pytest.raises(moss.MossError) as ei:
             moss.moss_sample_counts_noalloc(g.handle, 0, 0, 10, 1, out)
         assert ei.value.status == moss.MOSS_ESTATE
+
+
+def test_noalloc_rejects_missing_probe_tables():
+    """Like moss_sample_counts, the no-allocation call refuses a graph whose
+    probe strategy names tables that were never built."""
+    rp, col = synth.workload("cl_n2k")
+    out = torch.zeros(22, dtype=torch.int64, device="cuda")
+    with moss.Graph(rp, col, probe=moss.PROBE_SEARCH) as g:
+        moss.moss_set_probe(g.handle, moss.PROBE_HASH)        # hashed edge set not built
+        for fn in (moss.moss_sample_counts, moss.moss_sample_counts_noalloc):
+            with pytest.raises(moss.MossError) as ei:
+                fn(g.handle, 1, 0, 1000, 1, out)
+            assert ei.value.status == moss.MOSS_ESTATE
+    with moss.Graph(rp, col, probe=moss.PROBE_HASH) as g:
+        moss.moss_set_probe(g.handle, moss.PROBE_FILTER)      # edge filter not built
+        with pytest.raises(moss.MossError) as ei:
+            moss.moss_sample_counts_noalloc(g.handle, 0, 0, 1000, 1, out)
+        assert ei.value.status == moss.MOSS_ESTATE
