@@ -10,8 +10,14 @@ edges), k = 5 (T-5 + Path-5), budget 1e8 samples per rank (weak scaling).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
-bounded sample of the same workload instead (rank 0 only).
+Prints one JSON line (rank 0).  On one GPU the line also carries, each with
+its own clock record, the other terms of the headline measurement:
+``config3`` (the same step on the 34M-edge Chung-Lu graph, 1e9 samples,
+against the HBM roofline), ``batched`` (512 uneven graphs in one persistent
+launch against one launch per request) and ``served`` (a Poisson request
+stream with target errors against one request per launch).  --impl reference
+times the CPU oracle on a bounded sample of the same workload instead (rank 0
+only).
 """
 from __future__ import annotations
 
@@ -67,6 +73,10 @@ def parse():
     p.add_argument("--graphs", type=int, default=512, help="batch mode: number of graphs")
     p.add_argument("--rate", type=float, default=2000.0, help="serve mode: mean arrivals per second")
     p.add_argument("--duration", type=float, default=2.0, help="serve mode: seconds of arrivals")
+    p.add_argument("--no-extras", action="store_true",
+                   help="single mode: leave out the 34M-edge, batched and served terms of the line")
+    p.add_argument("--serve-duration", type=float, default=1.0,
+                   help="seconds of Poisson arrivals of the served term of the default line")
     p.add_argument("--probe", default="auto", choices=["auto", "hash", "filter", "search"],
                    help="induced-edge tests: auto (filtered set when the set exceeds 64 MiB, else the set), "
                         "hashed edge set, set behind a Bloom filter, or sorted-list search")
@@ -119,6 +129,15 @@ def oracle_rate(build, sample_wall, samples, budget):
     return budget / (build + budget / rate), rate
 
 
+def bench_config(args, rp, world: int, workload: str | None = None) -> dict:
+    """The `config` object of a line; both arms print the same one."""
+    wl = workload or describe(args.workload, args.k, args.mode == "min")[1]
+    return {"workload": wl, "budget_per_gpu": args.budget, "seed": args.seed,
+            "probe": resolved_probe(args.probe, rp),
+            "l2": "GPU arm: flushed (512 MB write) before every timed step; CPU oracle: not applicable",
+            "parallelism": f"replicas x{world}"}
+
+
 def calibrate_per_worker(workload, k, seed, seconds, mix=False):
     """Samples per worker process for about `seconds` of sampling, and the
     oracle's sampling rate on one core (samples/s) measured on the way."""
@@ -144,35 +163,45 @@ def make_pool(cores):
 
 
 def run_reference(args):
+    """The oracle timed on all host cores.  A step is a bounded sample of the
+    workload: every core's process builds the oracle's tables of the graph
+    and draws its share of per_worker samples (sub-methods split evenly), about
+    four seconds in all; value = samples drawn / the step's wall time, both as
+    measured (no extrapolation)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import synth
     mix = args.mode == "min"
     if mix:
         args.k = 4
-    METRIC, WORKLOAD = describe(args.workload, args.k, mix)
+    METRIC, _ = describe(args.workload, args.k, mix)
+    rp, _col = synth.workload(args.workload)
     cores = os.cpu_count() or 1
-    per_worker, single = calibrate_per_worker(args.workload, args.k, args.seed, 3.0, mix)
+    per_worker, single = calibrate_per_worker(args.workload, args.k, args.seed, 4.0, mix)
     with make_pool(cores) as pool:
         for _ in range(args.warmup):
             oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker, mix)
-        vals, walls = [], []
+        walls, counts = [], []
         for _ in range(args.steps):
             b, sw, n, wall = oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker, mix)
-            vals.append(oracle_rate(b, sw, n, args.budget)[0])
             walls.append(wall)
-    v = statistics.median(vals)
+            counts.append(n)
+    samples = counts[0]
+    wall = statistics.median(walls)
+    v = samples / wall
     split = "T-5/Path-5" if args.k == 5 else ("MOSS-4/MOSS-4Min" if mix else "MOSS-4")
-    sample = (f"{per_worker * cores} samples per step over {cores} processes ({split} split evenly) plus one "
-              f"table build; rate extrapolated to the {args.budget}-sample budget")
+    sample = (f"{samples} of the workload's {args.budget} samples per step ({split} split evenly) over {cores} "
+              f"processes, each building the oracle's tables of the graph; value = samples / measured step time")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * args.budget / v,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall, "samples_per_step": samples,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "budget": args.budget, "l2": "n/a (CPU)"},
+        "config": bench_config(args, rp, args.gpus),
         "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle", "sample": sample,
                          "single_core_sampling_rate": single},
         "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "step_ms": [1000 * w for w in walls],
     }), flush=True)
 
 
@@ -269,6 +298,137 @@ def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False) ->
     return n
 
 
+def peaks_file() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(path)) if os.path.exists(path) else {}
+
+
+def sampler_tables_bytes(rp, probe: str, methods) -> int:
+    """Bytes of the device tables a sampling call reads, by the library's
+    layout: 32 B slot records and 4 B ids per list entry, 16 B vertex records
+    and a 32 B vertex alias record per vertex and method, and the hashed edge
+    set (32 B buckets, the next power of two >= nnz / 2) or the edge filter in
+    front of it (4 B words, the largest power of two <= nnz / 8)."""
+    n, nnz = len(rp) - 1, int(rp[-1])
+    total = nnz * (32 + 4) + n * (16 + 32 * len(methods))
+    if probe in ("hash", "filter"):
+        b = 2
+        while b < (nnz + 1) // 2:
+            b <<= 1
+        total += 32 * b
+    if probe == "filter":
+        w = 1
+        while 2 * w <= max(nnz // 8, 1):
+            w <<= 1
+        total += 4 * w
+    return total
+
+
+def small_case_traffic(workload: str, key: str, samples: int):
+    """DRAM bytes (read + write) of one sampling call of `samples` ids,
+    scaled from the small-case ncu captures in
+    profiles/dram_traffic_small_<workload>.txt: with captures at two or more
+    sizes the bytes are fitted as a + b * samples (a: the cold start of the
+    tables), with one capture scaled in proportion.  None when the file is
+    missing or the sampler source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_small_{workload}.txt")
+    if not os.path.exists(path):
+        return None, None
+    rec, pts = {}, []
+    for line in open(path):
+        if not line.strip() or line.startswith("#"):
+            continue
+        a, b = line.split()[:2]
+        if "@" in a:
+            k, n = a.split("@")
+            if k == key:
+                pts.append((float(n), float(b)))
+        else:
+            rec[a] = b
+    src = b"".join(open(os.path.join(ROOT, "paper_1509_08089_gb300", "csrc", f), "rb").read()
+                   for f in ("moss_sample.cu", "moss_internal.cuh"))
+    if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha") or not pts:
+        return None, None
+    if len(pts) == 1:
+        return pts[0][1] * samples / pts[0][0], f"one capture of {int(pts[0][0])} samples, scaled in proportion"
+    x = np.array([q[0] for q in pts])
+    y = np.array([q[1] for q in pts])
+    b1, a0 = np.polyfit(x, y, 1)
+    sizes = "/".join(str(int(q)) for q in x)
+    return float(a0 + b1 * samples), f"fit a + b*samples over captures of {sizes} samples"
+
+
+def time_calls(moss, torch, h, k, budget, mix, seed, stream, l2_flush, reps=3):
+    """CUDA-event time of each sub-method's sampling call alone (the calls
+    the step makes), after one untimed call, L2 flushed before each."""
+    from paper_1509_08089_gb300.dist import sub_budgets
+    counts = torch.zeros(22, dtype=torch.int64, device=l2_flush.device)
+    times = {}
+    for m, K in sub_budgets(k, budget, mix):
+        moss.moss_sample_counts(h, m, 0, K, seed, counts, stream)
+        out = []
+        for _ in range(reps):
+            l2_flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            moss.moss_sample_counts(h, m, 0, K, seed, counts, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        times[m] = (K, statistics.median(out))
+    return times
+
+
+NAMES = {0: "MOSS4", 1: "T5", 2: "PATH5", 3: "MOSS4MIN"}
+
+
+def roofline(workload, rp, probe_name, times, methods, l2_bytes, gather, peaks):
+    """The roofline object of the slowest sampling call.  Its achieved rate
+    is algorithmic sectors per sample (tests/golden/sectors_<workload>.json)
+    x 32 B x samples per call / the call's CUDA-event time.  When the tables
+    the call reads fit the L2 the bound is the L2's random-sector rate,
+    measured in the same run by moss_gather_rate on a 64 MiB buffer;
+    otherwise the HBM copy peak of MEASURED_PEAKS.json, with the HBM
+    random-access rate (a 4 GiB buffer) beside it.  The other ceiling is kept
+    as a labelled second fraction."""
+    spath = os.path.join(ROOT, "tests", "golden", f"sectors_{workload}.json")
+    if not os.path.exists(spath):
+        return None
+    sect = json.load(open(spath))
+    dom = max(times, key=lambda m: times[m][1])
+    key = f"{NAMES[dom]}_{probe_name}"
+    if key not in sect:
+        return None
+    K, tms = times[dom]
+    spb = sect[key]["sectors_per_sample"]
+    ach = spb * 32.0 * K / (tms / 1000.0) / 1e9
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured (MEASURED_PEAKS.json copy)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+    ws = sampler_tables_bytes(rp, probe_name, methods)
+    l2_rate, hbm_rate = gather
+    tb, how = small_case_traffic(workload, key, K)
+    out = {"kernel": f"k_sample<{dom}> ({NAMES[dom]}, {probe_name} probes)", "achieved": ach, "unit": "GB/s",
+           "traffic": tb, "traffic_scaling": how, "algorithmic_bytes_per_sample": spb * 32.0,
+           "samples_per_launch": K, "launch_ms": tms, "kernel_times_ms": {NAMES[m]: times[m][1] for m in times},
+           "tables_bytes": ws, "l2_bytes": l2_bytes,
+           "gather_ceiling": {"unit": "GB/s", "l2_resident_64MiB": l2_rate, "hbm_4GiB": hbm_rate}}
+    if ws <= l2_bytes:
+        out.update({"bound": "l2", "peak": l2_rate,
+                    "peak_source": "measured in this run: random 32 B reads of a 64 MiB buffer (moss_gather_rate)",
+                    "frac": ach / l2_rate, "hbm_copy_peak": hbm_peak, "frac_of_hbm_copy_peak": ach / hbm_peak})
+    else:
+        out.update({"bound": "hbm", "peak": hbm_peak, "peak_source": hbm_src, "frac": ach / hbm_peak})
+        if tb is not None:
+            # a load that misses L2 fills a whole 128 B line (ncu on the gather
+            # kernel: 125 B of DRAM per load from 4 GiB), so DRAM bytes / 128
+            # are the call's random HBM accesses
+            fetch = tb / 128.0 / (tms / 1000.0)
+            out["dram_line_fetches_per_s"] = fetch
+            out["frac_of_hbm_gather"] = fetch / (hbm_rate * 1e9 / 32.0)
+    return out
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as tdist
@@ -286,11 +446,17 @@ def run_gpu(args):
     METRIC, WORKLOAD = describe(args.workload, args.k, mix)
     if world != args.gpus:
         raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
-    # the CPU-baseline pool is spawned before the first GPU call
+    extras = world == 1 and args.mode == "single" and not args.no_extras
+    # the host process pool (CPU baseline, input generation) is spawned before the first GPU call
     pool = None
     cores = os.cpu_count() or 1
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and (extras or not args.no_cpu_baseline):
         pool = make_pool(cores)
+    futures = {}
+    if extras:
+        futures["config3"] = pool.submit(_workload, "cl_n4m")
+        futures["batched"] = [pool.submit(_make_graph, spec) for spec in batch_specs(args.graphs)[0]]
+        futures["served"] = [pool.submit(_make_served, spec) for spec in serve_specs(64)]
     torch.cuda.set_device(local)
     dev = local
     if world > 1:
@@ -305,6 +471,7 @@ def run_gpu(args):
     rp_h = torch.from_numpy(rp.view(np.int64)).pin_memory()
     col_h = torch.from_numpy(col.view(np.int32)).pin_memory()
     l2_flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{dev}")   # > 126 MB L2
+    l2_bytes = torch.cuda.get_device_properties(dev).L2_cache_size
 
     def allreduce(counts: np.ndarray) -> np.ndarray:
         t = torch.from_numpy(counts).to(f"cuda:{dev}")
@@ -314,16 +481,16 @@ def run_gpu(args):
     probe = {"auto": moss.PROBE_AUTO, "hash": moss.PROBE_HASH, "filter": moss.PROBE_FILTER,
              "search": moss.PROBE_SEARCH}[args.probe]
 
-    def step(src_rp, src_col, seed):
+    def step(src_rp, src_col, seed, kk=k, budget=args.budget):
         h = moss.moss_graph_load_csr(src_rp, src_col, device=dev, stream=stream)
         try:
             moss.moss_set_probe(h, probe)
-            moss.moss_build_tables(h, kmask, stream)
+            moss.moss_build_tables(h, (1 << kk) | (moss.TABLES_4MIN if mix else 0), stream)
             if world == 1 and mix:
-                K4, Km = (K for _, K in sub_budgets(k, args.budget, True))
+                K4, Km = (K for _, K in sub_budgets(kk, budget, True))
                 r = moss.result_dict(moss.moss_sample_estimate_min(h, K4, Km, seed, stream))
             elif world == 1:
-                r = moss.result_dict(moss.moss_sample_estimate(h, k, args.budget, seed, stream))
+                r = moss.result_dict(moss.moss_sample_estimate(h, kk, budget, seed, stream))
             else:
                 class _G:  # the weak-scaling helper wants .handle/.device/.stats()
                     handle, device = h, dev
@@ -331,7 +498,7 @@ def run_gpu(args):
                     @staticmethod
                     def stats():
                         return moss.moss_graph_stats(h)
-                r = estimate_weak(_G, k, args.budget, seed, rank, world, allreduce, stream, mix)
+                r = estimate_weak(_G, kk, budget, seed, rank, world, allreduce, stream, mix)
         finally:
             moss.moss_graph_free(h)
         return r
@@ -340,26 +507,33 @@ def run_gpu(args):
         if world > 1:
             tdist.barrier()
 
+    def timed_steps(src_rp, src_col, nsteps, seed0, **kw):
+        """nsteps steps, L2 flushed before each, CUDA events on the stream."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(nsteps):
+            l2_flush.zero_()                 # evict the previous step's tables from L2
+            ev[i][0].record(stream)
+            step(src_rp, src_col, seed0 + i, **kw)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return [a.elapsed_time(b) for a, b in ev], time.perf_counter() - t0
+
     for i in range(args.warmup):
         step(rp_d, col_d, args.seed + i)
     torch.cuda.synchronize()
+    if futures:
+        # inputs of the other terms are generated on the host cores; let that
+        # finish before anything is timed
+        import concurrent.futures as cf
+        cf.wait([futures["config3"], *futures["batched"], *futures["served"]])
     clocks = Clocks(dev)
     clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
-    torch.cuda.synchronize()
-    t_wall0 = time.perf_counter()
-    results = []
-    for i in range(args.steps):
-        l2_flush.zero_()                 # evict the previous step's tables from L2
-        ev[i][0].record(stream)
-        results.append(step(rp_d, col_d, args.seed + 100 + i))
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    t_wall = time.perf_counter() - t_wall0
+    step_ms, t_wall = timed_steps(rp_d, col_d, args.steps, args.seed + 100)
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
         t = torch.tensor([ms], device=f"cuda:{dev}", dtype=torch.float64)
@@ -386,88 +560,26 @@ def run_gpu(args):
     h2d = rp.nbytes + col.nbytes
     d2h = __import__("ctypes").sizeof(moss.moss_result)
 
-    # ---- the dominant kernel alone (same launch as inside the step)
-    roof = None
+    # ---- the dominant sampling call alone (the same call as inside the step)
+    peaks = peaks_file()
+    probe_name = resolved_probe(args.probe, rp)
     h = moss.moss_graph_load_csr(rp_d, col_d, device=dev, stream=stream)
     try:
         moss.moss_set_probe(h, probe)
         moss.moss_build_tables(h, kmask, stream)
-        counts = torch.zeros(22, dtype=torch.int64, device=f"cuda:{dev}")
-        times = {}
-        for m, K in sub_budgets(k, args.budget, mix):
-            moss.moss_sample_counts(h, m, 0, K, args.seed, counts, stream)      # warm
-            reps = []
-            for rep in range(3):
-                l2_flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                moss.moss_sample_counts(h, m, 0, K, args.seed, counts, stream)
-                b.record(stream)
-                torch.cuda.synchronize()
-                reps.append(a.elapsed_time(b))
-            times[m] = (K, statistics.median(reps))
+        times = time_calls(moss, torch, h, k, args.budget, mix, args.seed, stream, l2_flush)
     finally:
         moss.moss_graph_free(h)
-    sect = None
-    spath = os.path.join(ROOT, "tests", "golden", f"sectors_{args.workload}.json")
-    if os.path.exists(spath):
-        sect = json.load(open(spath))
-    name = {0: "MOSS4", 1: "T5", 2: "PATH5", 3: "MOSS4MIN"}
-    dom = max(times, key=lambda m: times[m][1])
-    peaks = {}
-    ppath = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(ppath):
-        peaks = json.load(open(ppath))
-    peak = peaks.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    probe_name = resolved_probe(args.probe, rp)
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", f"dram_traffic_{args.workload}.txt")
-    if os.path.exists(tpath):
-        import hashlib
-        rec = {}
-        for line in open(tpath):
-            if line.strip() and not line.startswith("#"):
-                key, val = line.split()[:2]
-                rec[key] = val
-        src = b"".join(open(os.path.join(ROOT, "paper_1509_08089_gb300", "csrc", f), "rb").read()
-                       for f in ("moss_sample.cu", "moss_internal.cuh"))
-        # counters describe the kernel only while its source is unchanged
-        if hashlib.sha256(src).hexdigest()[:16] == rec.get("source_sha"):
-            traffic = rec
-    if sect is not None and f"{name[dom]}_{probe_name}" in sect:
-        K, tms = times[dom]
-        spb = sect[f"{name[dom]}_{probe_name}"]["sectors_per_sample"]
-        ach = spb * 32.0 * K / (tms / 1000.0) / 1e9
-        tb = None
-        if traffic is not None and f"{name[dom]}_{probe_name}" in traffic:
-            tb = float(traffic[f"{name[dom]}_{probe_name}"]) * K / float(traffic["samples_per_launch"])
-        roof = {"bound": "hbm", "kernel": f"k_sample<{dom}> ({name[dom]}, {probe_name} probes)", "achieved": ach,
-                "peak": peak,
-                "peak_source": peak_src, "unit": "GB/s", "frac": ach / peak, "traffic": tb,
-                "algorithmic_bytes_per_sample": spb * 32.0, "samples_per_launch": K,
-                "launch_ms": tms, "kernel_times_ms": {name[m]: times[m][1] for m in times}}
-        # the ceiling of the access pattern itself: independent random 32 B
-        # sector reads, from an L2-resident buffer and from one 32x the L2
-        l2_rate = moss.moss_gather_rate(64 << 20, dev, stream) * 32.0 / 1e9
-        hbm_rate = moss.moss_gather_rate(4 << 30, dev, stream) * 32.0 / 1e9
-        roof["gather_ceiling"] = {"unit": "GB/s", "l2_resident_64MiB": l2_rate, "hbm_4GiB": hbm_rate,
-                                  "frac_of_l2_gather": ach / l2_rate}
-        if tb is not None:
-            # a load that misses L2 fills a whole 128 B line from DRAM (ncu on
-            # the gather kernel: 125 B of DRAM reads per load from 4 GiB), so
-            # DRAM bytes / 128 are the sampler's random HBM accesses, to be set
-            # against the gather kernel's accesses per second
-            fetch = tb / 128.0 / (tms / 1000.0)
-            roof["gather_ceiling"]["dram_line_fetches_per_s"] = fetch
-            roof["gather_ceiling"]["frac_of_hbm_gather"] = fetch / (hbm_rate * 1e9 / 32.0)
+    gather = (moss.moss_gather_rate(64 << 20, dev, stream) * 32.0 / 1e9,
+              moss.moss_gather_rate(4 << 30, dev, stream) * 32.0 / 1e9)
+    roof = roofline(args.workload, rp, probe_name, times, [m for m, _ in sub_budgets(k, args.budget, mix)],
+                    l2_bytes, gather, peaks)
 
     out = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "budget_per_gpu": args.budget, "seed": args.seed, "probe": resolved_probe(args.probe, rp),
-                   "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}"},
+        "config": bench_config(args, rp, world, WORKLOAD),
         "e2e": {"value": samples_per_step / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": roof,
@@ -476,16 +588,54 @@ def run_gpu(args):
         "wall_s_timed": t_wall,
         "step_ms": step_ms,
     }
-    if pool is not None:
+    del rp_d, col_d, rp_h, col_h
+
+    if extras:
+        # ---- the 34M-edge graph (HBM-resident tables): k = 5, 1e9 samples per step
+        rp3, col3 = futures["config3"].result()
+        rp3_d = torch.from_numpy(rp3.view(np.int64)).to(f"cuda:{dev}")
+        col3_d = torch.from_numpy(col3.view(np.int32)).to(f"cuda:{dev}")
+        B3 = 1_000_000_000
+        for i in range(args.warmup):
+            step(rp3_d, col3_d, args.seed + i, budget=B3)
+        torch.cuda.synchronize()
+        c3 = Clocks(dev)
+        c3.start()
+        ms3, _ = timed_steps(rp3_d, col3_d, args.steps, args.seed + 100, budget=B3)
+        clk3 = c3.stop()
+        p3 = resolved_probe(args.probe, rp3)
+        h = moss.moss_graph_load_csr(rp3_d, col3_d, device=dev, stream=stream)
+        try:
+            moss.moss_set_probe(h, probe)
+            moss.moss_build_tables(h, 1 << 5, stream)
+            t3 = time_calls(moss, torch, h, 5, B3, False, args.seed, stream, l2_flush, reps=2)
+        finally:
+            moss.moss_graph_free(h)
+        del rp3_d, col3_d
+        m3 = sum(ms3) / len(ms3)
+        out["config3"] = {
+            "metric": "5-node samples/s at 34M edges", "value": B3 / (m3 / 1000.0), "unit": "samples/s",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": m3, "step_ms": ms3,
+            "config": {"workload": describe("cl_n4m", 5)[1], "budget": B3, "seed": args.seed, "probe": p3,
+                       "l2": "flushed (512 MB write) before every timed step; tables larger than the L2"},
+            "roofline": roofline("cl_n4m", rp3, p3, t3, [1, 2], l2_bytes, gather, peaks),
+            "clocks": clk3, "gpu_launches": launches_per_step(5, B3, False, p3 == "filter") * args.steps}
+        out["batched"] = measure_batched(moss, torch, [f.result() for f in futures["batched"]],
+                                         batch_specs(args.graphs)[1], args.steps, args.warmup, stream)
+        out["served"] = measure_served(moss, [f.result() for f in futures["served"]], args.rate,
+                                       args.serve_duration)
+
+    if pool is not None and not args.no_cpu_baseline:
         per_worker, single = calibrate_per_worker(args.workload, k, args.seed, 12.0, mix)
         b, sw, n, wall = oracle_pass(pool, cores, args.workload, k, args.seed, per_worker, mix)
         v, rate = oracle_rate(b, sw, n, args.budget)
-        pool.shutdown()
         out["cpu_baseline"] = {
             "value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
             "sample": (f"{n} samples ({'T-5/Path-5 evenly' if k == 5 else ('MOSS-4/MOSS-4Min evenly' if mix else 'MOSS-4')}) over {cores} processes in "
                        f"{sw:.1f} s + table build {b:.2f} s, extrapolated to the {args.budget}-sample budget"),
             "sampling_rate": rate, "single_core_sampling_rate": single}
+    if pool is not None:
+        pool.shutdown()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -493,6 +643,12 @@ def run_gpu(args):
 
 
 # ----------------------------------------------------------------- batch --
+def _workload(name):
+    sys.path.insert(0, ROOT)
+    import synth
+    return synth.workload(name)
+
+
 def _make_graph(spec):
     sys.path.insert(0, ROOT)
     import synth
@@ -502,11 +658,12 @@ def _make_graph(spec):
     return synth.rgg(n, a, seed=seed)
 
 
-def batch_workload(count: int, seed: int = 7, pool=None):
+def batch_specs(count: int, seed: int = 7):
     """The batched workload: `count` graphs, n log-uniform in [500, 50,000];
     even ones Chung-Lu (exponent 2.0-3.0, mean degree 4-12), odd ones 2-D
     random geometric (mean degree 6-30); k in {4, 5} and a budget
-    log-uniform in [1e4, 1e7] per graph."""
+    log-uniform in [1e4, 1e7] per graph.  Returns (graph specs, (k, budget,
+    seed) per graph)."""
     rng = np.random.default_rng(seed)
     specs, meta = [], []
     for i in range(count):
@@ -519,63 +676,78 @@ def batch_workload(count: int, seed: int = 7, pool=None):
         k = int(rng.choice([4, 5]))
         budget = int(np.exp(rng.uniform(np.log(1e4), np.log(1e7))))
         meta.append((k, budget, int(rng.integers(1, 2**62))))
-    csrs = list(pool.map(_make_graph, specs)) if pool is not None else [_make_graph(sp) for sp in specs]
-    return [(rp, col, k, b, sd) for (rp, col), (k, b, sd) in zip(csrs, meta)]
+    return specs, meta
+
+
+BATCH_WORKLOAD = ("{n} graphs, n 500-50,000 log-uniform, half Chung-Lu exponent 2.0-3.0, half 2-D RGG mean "
+                  "degree 6-30, k in {{4,5}}, budgets 1e4-1e7 log-uniform")
+
+
+def measure_batched(moss, torch, csrs, meta, steps, warmup, stream):
+    """Every graph's request in one persistent launch (autotuned), timed by
+    the host around the synchronous call, against one moss_sample_estimate
+    launch per request back to back; counts must agree."""
+    t0 = time.perf_counter()
+    graphs = [moss.Graph(rp, col, stream=stream) for rp, col in csrs]
+    load_s = time.perf_counter() - t0
+    total = sum(b for _, b, _ in meta)
+    edges = sum(len(col) // 2 for _, col in csrs)
+    try:
+        with moss.Batch() as batch:
+            for g, (k, b, sd) in zip(graphs, meta):
+                batch.add(g, k, b, sd)
+            tuned = batch.tune(stream)
+            for _ in range(warmup):
+                batch.run(stream)
+            clocks = Clocks(torch.cuda.current_device())
+            clocks.start()
+            times = []
+            for _ in range(steps):
+                torch.cuda.synchronize()
+                a = time.perf_counter()
+                res = batch.run(stream)
+                times.append(time.perf_counter() - a)
+            clk = clocks.stop()
+            tuning = batch.tuning()
+        plain = []
+        for _ in range(max(1, steps // 4)):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            solo = [g.estimate(k, b, sd, stream) for g, (k, b, sd) in zip(graphs, meta)]
+            plain.append(time.perf_counter() - a)
+        same = all(np.array_equal(r["hits"], q["hits"]) for r, q in zip(res, solo))
+    finally:
+        for g in graphs:
+            g.close()
+    tb, tp = statistics.median(times), statistics.median(plain)
+    return {"metric": "batched samples/s over many graphs", "value": total / tb, "unit": "samples/s",
+            "steps": steps, "warmup": warmup, "ms_per_step": 1000 * tb,
+            "timing": "host wall clock around the synchronous batch run (one CUDA graph launch)",
+            "config": {"workload": BATCH_WORKLOAD.format(n=len(csrs)), "samples_per_step": total,
+                       "edges_total": edges, "tile_samples": tuned, "tuning": tuning,
+                       "load_and_build_s": round(load_s, 2)},
+            "plain": {"value": total / tp, "ms_per_step": 1000 * tp,
+                      "what": "one moss_sample_estimate launch per request, back to back"},
+            "speedup_vs_plain": tp / tb, "identical_counts": bool(same), "clocks": clk}
 
 
 def run_batch(args):
     import torch
     import paper_1509_08089_gb300 as moss
 
+    specs, meta = batch_specs(args.graphs)
     t0 = time.perf_counter()
     with make_pool(os.cpu_count() or 1) as pool:   # spawned before the first GPU call
-        work = batch_workload(args.graphs, pool=pool)
+        csrs = list(pool.map(_make_graph, specs))
     gen_s = time.perf_counter() - t0
     torch.cuda.set_device(0)
     moss.load()
     stream = torch.cuda.current_stream()
-    graphs = [moss.Graph(rp, col, stream=stream) for rp, col, _, _, _ in work]
-    total = sum(b for _, _, _, b, _ in work)
-    edges = sum(len(col) // 2 for _, col, _, _, _ in work)
-    with moss.Batch() as batch:
-        for g, (_, _, k, b, sd) in zip(graphs, work):
-            batch.add(g, k, b, sd)
-        tile = batch.tune(stream)
-        for _ in range(args.warmup):
-            batch.run(stream)
-        clocks = Clocks(0)
-        clocks.start()
-        times = []
-        for _ in range(args.steps):
-            torch.cuda.synchronize()
-            a = time.perf_counter()
-            res = batch.run(stream)
-            times.append(time.perf_counter() - a)
-        clk = clocks.stop()
-    # the plain alternative: one sample-and-estimate launch per request
-    plain = []
-    for _ in range(max(1, args.steps // 2)):
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        solo = [g.estimate(k, b, sd, stream) for g, (_, _, k, b, sd) in zip(graphs, work)]
-        plain.append(time.perf_counter() - a)
-    same = all(np.array_equal(r["hits"], q["hits"]) for r, q in zip(res, solo))
-    for g in graphs:
-        g.close()
-    tb = statistics.median(times)
-    tp = statistics.median(plain)
-    print(json.dumps({
-        "metric": "batched samples/s over many graphs", "value": total / tb, "unit": "samples/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tb, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": (f"{args.graphs} graphs, n 500-50,000 log-uniform, half Chung-Lu exponent 2.0-3.0, "
-                                "half 2-D RGG mean degree 6-30, k in {4,5}, budgets 1e4-1e7 log-uniform"),
-                   "samples_per_step": total, "edges_total": edges, "tile_samples": tile,
-                   "generation_s": round(gen_s, 1)},
-        "plain": {"value": total / tp, "ms_per_step": 1000 * tp,
-                  "what": "one moss_sample_estimate launch per request, back to back"},
-        "speedup_vs_plain": tp / tb, "identical_counts": bool(same), "clocks": clk,
-    }), flush=True)
+    r = measure_batched(moss, torch, csrs, meta, args.steps, args.warmup, stream)
+    r.update({"n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+              "data": "synthetic"})
+    r["config"]["generation_s"] = round(gen_s, 1)
+    print(json.dumps(r), flush=True)
 
 
 # ----------------------------------------------------------------- serve --
@@ -586,7 +758,7 @@ def _make_served(spec):
     return synth.chung_lu(n, gamma, dbar, min(0.1 * n, 30 * dbar), seed=seed)
 
 
-def serve_pool(count: int, pool, seed: int = 11):
+def serve_specs(count: int, seed: int = 11):
     """`count` Chung-Lu graphs with edge counts log-uniform in [1e4, 1e7]
     (mean degree 8-20, exponent 2.1-2.8)."""
     rng = np.random.default_rng(seed)
@@ -595,7 +767,7 @@ def serve_pool(count: int, pool, seed: int = 11):
         edges = float(np.exp(rng.uniform(np.log(1e4), np.log(1e7))))
         dbar = float(rng.uniform(8.0, 20.0))
         specs.append((max(200, int(2 * edges / dbar)), float(rng.uniform(2.1, 2.8)), dbar, 30_000 + i))
-    return list(pool.map(_make_served, specs))
+    return specs
 
 
 def poisson_schedule(rate: float, duration: float, ngraphs: int, eps_lo: float, eps_hi: float, seed: int):
@@ -637,42 +809,60 @@ def serve_once(moss, graphs, schedule, config):
             "launches": int(info["ticks"])}
 
 
+SERVE_COMMON = dict(min_budget=10_000, max_budget=10_000_000, pilot_samples=20_000)
+SERVED_CFG = dict(max_active=512, tick_samples=100_000_000, tile_samples=4096, **SERVE_COMMON)
+# one request per launch: one slot, a tick as large as the largest budget
+PLAIN_CFG = dict(max_active=1, tick_samples=10_000_000, tile_samples=4096, **SERVE_COMMON)
+
+
+def measure_served(moss, csrs, rate: float, duration: float, eps=(0.01, 0.05)):
+    """A Poisson stream of target-error requests over resident graphs, served
+    with continuous batching and, on the same stream, one request per
+    launch; each with its own clock record."""
+    import torch
+    graphs = [moss.Graph(rp, col) for rp, col in csrs]
+    edges = sum(len(col) // 2 for _, col in csrs)
+    try:
+        sched = poisson_schedule(rate, duration, len(graphs), eps[0], eps[1], seed=5)
+        serve_once(moss, graphs, sched[: max(1, len(sched) // 20)], SERVED_CFG)   # warm-up
+        c = Clocks(torch.cuda.current_device())
+        c.start()
+        served = serve_once(moss, graphs, sched, SERVED_CFG)
+        served["clocks"] = c.stop()
+        c = Clocks(torch.cuda.current_device())
+        c.start()
+        plain = serve_once(moss, graphs, sched, PLAIN_CFG)
+        plain["clocks"] = c.stop()
+    finally:
+        for g in graphs:
+            g.close()
+    return {"metric": "served p99 ms vs plain", "value": served["p99_ms"], "unit": "ms", "higher_is_better": False,
+            "config": {"workload": (f"Poisson {rate:.0f} req/s for {duration} s over {len(graphs)} resident "
+                                    f"Chung-Lu graphs ({edges} edges total, 1e4-1e7 each); k in {{4,5}}; target "
+                                    f"relative SE {eps[0]:.0%}-{eps[1]:.0%}, budget from the variance formula "
+                                    "after a 2e4-sample pilot, clamped to [1e4, 1e7]; admission by free HBM"),
+                       "served": SERVED_CFG, "plain": PLAIN_CFG},
+            "served": served, "plain": plain,
+            "p99_speedup_vs_plain": plain["p99_ms"] / served["p99_ms"] if served["p99_ms"] else None}
+
+
 def run_serve(args):
     import torch
     import paper_1509_08089_gb300 as moss
 
     t0 = time.perf_counter()
     with make_pool(os.cpu_count() or 1) as pool:
-        csrs = serve_pool(64, pool)
+        csrs = list(pool.map(_make_served, serve_specs(64)))
     gen_s = time.perf_counter() - t0
     torch.cuda.set_device(0)
     moss.load()
-    graphs = [moss.Graph(rp, col) for rp, col in csrs]
-    edges = sum(len(col) // 2 for _, col in csrs)
-    common = dict(min_budget=10_000, max_budget=10_000_000, pilot_samples=20_000)
-    served_cfg = dict(max_active=512, tick_samples=100_000_000, tile_samples=4096, **common)
-    # one request per launch: one slot, a tick as large as the largest budget
-    plain_cfg = dict(max_active=1, tick_samples=10_000_000, tile_samples=4096, **common)
-    out = {}
-    for name, (lo, hi) in (("mixed", (0.01, 0.05)), ("rse_1pct", (0.01, 0.01))):
-        sched = poisson_schedule(args.rate, args.duration, len(graphs), lo, hi, seed=5)
-        serve_once(moss, graphs, sched[: max(1, len(sched) // 20)], served_cfg)   # warm-up
-        served = serve_once(moss, graphs, sched, served_cfg)
-        plain = serve_once(moss, graphs, sched, plain_cfg)
-        out[name] = {"served": served, "plain": plain}
-    for g in graphs:
-        g.close()
-    s1 = out["mixed"]["served"]
-    print(json.dumps({
-        "metric": "served p99 ms vs plain", "value": s1["p99_ms"], "unit": "ms", "n_gpus": 1,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": (f"Poisson {args.rate:.0f} req/s for {args.duration} s over 64 resident Chung-Lu graphs "
-                                f"({edges} edges total, 1e4-1e7 each); k in {{4,5}}; target relative SE 1-5% "
-                                "(and all 1%), budget from the variance formula after a 2e4-sample pilot, "
-                                "clamped to [1e4, 1e7]"), "generation_s": round(gen_s, 1),
-                   "served": served_cfg, "plain": plain_cfg},
-        "runs": out,
-    }), flush=True)
+    runs = {name: measure_served(moss, csrs, args.rate, args.duration, eps)
+            for name, eps in (("mixed", (0.01, 0.05)), ("rse_1pct", (0.01, 0.01)))}
+    r = dict(runs["mixed"])
+    r.update({"n_gpus": 1, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+              "runs": runs})
+    r["config"]["generation_s"] = round(gen_s, 1)
+    print(json.dumps(r), flush=True)
 
 
 def main():

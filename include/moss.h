@@ -262,8 +262,36 @@ uint32_t moss_batch_tile(const moss_batch *b);
  * entries) receives request i.  Ordered after prior work on `stream`;
  * synchronous. */
 int moss_batch_run(moss_batch *b, void *stream, moss_result *results);
-/* Time the batch under a few tile sizes and keep the fastest (*chosen). */
+/* Launch shape of the persistent sampler: threads per block (128, 256 or
+ * 512; the resident threads per SM stay 1,024) and resident blocks per SM
+ * (0: as many as fit, the default). */
+int moss_batch_set_launch(moss_batch *b, int threads_per_block, int blocks_per_sm);
+/* Probe strategy (MOSS_PROBE_*) the batch uses for graph g, overriding the
+ * graph's own (MOSS_PROBE_AUTO removes the override); MOSS_ESTATE when the
+ * graph lacks the tables the strategy needs.  Counts do not depend on it. */
+int moss_batch_set_graph_probe(moss_batch *b, const moss_graph *g, int strategy);
+typedef struct {
+    uint32_t tile_samples;     /* samples per tile: one warp's unit of work      */
+    int threads_per_block;     /* 128, 256 or 512                                 */
+    int blocks_per_sm;         /* resident blocks of the persistent launch per SM */
+    int tuned;                 /* 1 once moss_batch_tune has run                   */
+    int graphs;                /* distinct graphs of the batch (when tuned)        */
+    int graphs_search;         /* graphs given list-search probes                  */
+    int graphs_hash;           /* graphs given the hashed edge set                 */
+    int graphs_filter;         /* graphs given the filtered edge set               */
+    double run_s;              /* host time of one run under the chosen settings   */
+} moss_batch_tuning;
+/* Choose the batch's launch settings by measurement, then keep them:
+ * (1) each graph's probe strategy, from the SM cycles per sample of its
+ * tiles in one run with every graph on list search, one on the hashed set
+ * and one on the filtered set (each where its tables exist); (2) the tile
+ * size among 1,024 .. 65,536 samples; (3) the block shape among 128, 256 and
+ * 512 threads at 1/2, 3/4 and all of the resident blocks that fit; (4) the
+ * tile size again under that shape.  *chosen (nullable) receives the tile.
+ * Every setting leaves each request's result unchanged. */
 int moss_batch_tune(moss_batch *b, void *stream, uint32_t *chosen);
+/* The settings in force (and what the last tuning chose). */
+int moss_batch_get_tuning(const moss_batch *b, moss_batch_tuning *out);
 void moss_batch_free(moss_batch *b);
 
 /* ----------------------------------------------------------------- serving

@@ -49,6 +49,13 @@ class moss_result(ctypes.Structure):
                 ("conc", ctypes.c_double * NSLOTS)]
 
 
+class moss_batch_tuning(ctypes.Structure):
+    _fields_ = [("tile_samples", ctypes.c_uint32), ("threads_per_block", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int), ("tuned", ctypes.c_int), ("graphs", ctypes.c_int),
+                ("graphs_search", ctypes.c_int), ("graphs_hash", ctypes.c_int), ("graphs_filter", ctypes.c_int),
+                ("run_s", ctypes.c_double)]
+
+
 class moss_server_config(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int), ("tick_samples", ctypes.c_uint64), ("tile_samples", ctypes.c_uint32),
                 ("pilot_samples", ctypes.c_uint64), ("min_budget", ctypes.c_uint64), ("max_budget", ctypes.c_uint64),
@@ -114,6 +121,9 @@ def load():
         "moss_batch_tile": ([_vp], ctypes.c_uint32),
         "moss_batch_run": ([_vp, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
         "moss_batch_tune": ([_vp, _vp, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+        "moss_batch_set_launch": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "moss_batch_set_graph_probe": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
+        "moss_batch_get_tuning": ([_vp, ctypes.POINTER(moss_batch_tuning)], ctypes.c_int),
         "moss_batch_free": ([_vp], None),
         "moss_server_default_config": ([ctypes.POINTER(moss_server_config)], None),
         "moss_server_create": ([ctypes.c_int, ctypes.POINTER(moss_server_config), ctypes.POINTER(_vp)], ctypes.c_int),
@@ -346,6 +356,20 @@ def moss_batch_tune(b: int, stream=None) -> int:
     return c.value
 
 
+def moss_batch_set_launch(b: int, threads_per_block: int, blocks_per_sm: int = 0):
+    _check(load().moss_batch_set_launch(b, threads_per_block, blocks_per_sm))
+
+
+def moss_batch_set_graph_probe(b: int, g: int, strategy: int):
+    _check(load().moss_batch_set_graph_probe(b, g, strategy))
+
+
+def moss_batch_get_tuning(b: int) -> moss_batch_tuning:
+    t = moss_batch_tuning()
+    _check(load().moss_batch_get_tuning(b, ctypes.byref(t)))
+    return t
+
+
 def moss_batch_free(b: int):
     if b:
         load().moss_batch_free(b)
@@ -478,6 +502,16 @@ class Batch:
 
     def tune(self, stream=None) -> int:
         return moss_batch_tune(self.handle, stream)
+
+    def tuning(self) -> dict:
+        t = moss_batch_get_tuning(self.handle)
+        return {f: getattr(t, f) for f, _ in moss_batch_tuning._fields_}
+
+    def set_launch(self, threads_per_block: int, blocks_per_sm: int = 0):
+        moss_batch_set_launch(self.handle, threads_per_block, blocks_per_sm)
+
+    def set_probe(self, graph: "Graph", strategy: int):
+        moss_batch_set_graph_probe(self.handle, graph.handle, strategy)
 
     def set_tile(self, tile_samples: int):
         moss_batch_set_tile(self.handle, tile_samples)

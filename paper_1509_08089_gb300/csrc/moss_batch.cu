@@ -12,8 +12,14 @@
 //
 // The launch sequence (counter reset, sampler, per-task sums, finalize,
 // result copy) is captured once into a CUDA graph on the batch's own stream
-// and replayed by later runs until the request list or the tile size
-// changes.  moss_batch_tune times a few tile sizes and keeps the fastest.
+// and replayed by later runs until the request list or a launch choice
+// changes.  moss_batch_tune picks those choices by measurement: the probe
+// strategy of each graph (list search, hashed set or filtered set, from the
+// SM cycles its tiles take under each), the tile size (samples per warp task)
+// and the block shape (threads per block, resident blocks per SM).  None of
+// them changes a count: samples are keyed by id and every probe strategy
+// answers the same membership questions.
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <mutex>
@@ -54,7 +60,15 @@ struct moss_batch {
     cudaEvent_t ready = nullptr;
     std::vector<Req> reqs;
     uint32_t tile = 8192;
-    bool dirty = true;                 // request list or tile changed since the last capture
+    int threads = 256;                 // threads per block of the persistent launch
+    int per_sm = 0;                    // resident blocks per SM (0: as many as fit)
+    std::vector<std::pair<const moss_graph *, int>> probes;   // per-graph probe strategy overrides
+    bool record = false;               // record per-tile SM cycles (tuning runs)
+    bool dirty = true;                 // request list or a launch choice changed since the last capture
+    moss_batch_tuning tuning{};
+    // host copy of the current plan: tasks and the graph of each
+    std::vector<BatchTask> plan_tasks;
+    std::vector<const moss_graph *> plan_graphs;
     // device buffers
     DevGraph *d_graphs = nullptr;
     size_t cap_graphs = 0;
@@ -69,6 +83,8 @@ struct moss_batch {
     moss_result *d_results = nullptr;
     size_t cap_res = 0;
     unsigned long long *d_next = nullptr;
+    unsigned long long *d_cycles = nullptr;
+    size_t cap_cycles = 0;
     moss_result *h_results = nullptr;  // pinned
     size_t cap_hres = 0;
     // shape of the current plan
@@ -99,7 +115,13 @@ int plan(moss_batch *b) {
             if (gkeys[i] == q.g) gidx = (int)i;
         if (gidx < 0) {
             gidx = (int)graphs.size();
-            graphs.push_back(gi.view);
+            DevGraph v = gi.view;
+            for (auto &pr : b->probes)
+                if (pr.first == q.g) {
+                    int rc = graph_view_for(q.g, pr.second, &v);
+                    if (rc) return rc;
+                }
+            graphs.push_back(v);
             gkeys.push_back(q.g);
         }
         BatchRequest &br = reqs[r];
@@ -142,7 +164,10 @@ int plan(moss_batch *b) {
     }
     b->ntasks = (int)tasks.size();
     b->ntiles = tile0;
+    b->plan_tasks = tasks;
+    b->plan_graphs = gkeys;
     cudaError_t e = cudaSuccess;
+    if (b->record) e = grow(&b->d_cycles, &b->cap_cycles, (size_t)b->ntiles + 1, s);
     if (e == cudaSuccess) e = grow(&b->d_graphs, &b->cap_graphs, graphs.size() + 1, s);
     if (e == cudaSuccess) e = grow(&b->d_tasks, &b->cap_tasks, tasks.size() + 1, s);
     if (e == cudaSuccess) e = grow(&b->d_reqs, &b->cap_reqs, reqs.size() + 1, s);
@@ -168,7 +193,7 @@ int plan(moss_batch *b) {
     // the host vectors die at return: wait for the copies
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return set_error(MOSS_ECUDA, "uploading the batch plan");
-    b->blocks = batch_blocks(b->device);
+    b->blocks = batch_blocks(b->device, b->threads, b->per_sm);
     return MOSS_OK;
 }
 
@@ -179,7 +204,7 @@ cudaError_t enqueue(moss_batch *b) {
     cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess)
         e = launch_sample_batch(b->d_graphs, b->d_tasks, b->ntasks, b->ntiles, b->tile, b->d_next, b->d_tiles,
-                                b->blocks, s);
+                                b->threads, b->blocks, b->record ? b->d_cycles : nullptr, s);
     if (e == cudaSuccess) e = launch_batch_reduce(b->d_tasks, b->ntasks, b->tile, b->d_tiles, b->d_task_counts, s);
     if (e == cudaSuccess) e = launch_finalize_batch(b->d_reqs, nreq, b->d_task_counts, b->d_results, s);
     if (e == cudaSuccess && nreq)
@@ -311,32 +336,166 @@ int moss_batch_run(moss_batch *b, void *stream, moss_result *results) {
     return MOSS_OK;
 }
 
+int moss_batch_set_launch(moss_batch *b, int threads_per_block, int blocks_per_sm) {
+    if (!b) return set_error(MOSS_EINVAL, "NULL batch");
+    if (threads_per_block != 128 && threads_per_block != 256 && threads_per_block != 512)
+        return set_error(MOSS_EINVAL, "threads per block must be 128, 256 or 512");
+    if (blocks_per_sm < 0) return set_error(MOSS_EINVAL, "blocks per SM must be >= 0 (0: as many as fit)");
+    if (threads_per_block != b->threads || blocks_per_sm != b->per_sm) b->dirty = true;
+    b->threads = threads_per_block;
+    b->per_sm = blocks_per_sm;
+    return MOSS_OK;
+}
+
+int moss_batch_set_graph_probe(moss_batch *b, const moss_graph *g, int strategy) {
+    if (!b || !g) return set_error(MOSS_EINVAL, "NULL argument");
+    DevGraph v;
+    int rc = graph_view_for(g, strategy, &v);   // the tables the strategy needs must exist
+    if (rc) return rc;
+    for (size_t i = 0; i < b->probes.size(); ++i)
+        if (b->probes[i].first == g) {
+            b->probes.erase(b->probes.begin() + (long)i);
+            break;
+        }
+    if (strategy != MOSS_PROBE_AUTO) b->probes.push_back({g, strategy});
+    b->dirty = true;
+    return MOSS_OK;
+}
+
+int moss_batch_get_tuning(const moss_batch *b, moss_batch_tuning *out) {
+    if (!b || !out) return set_error(MOSS_EINVAL, "NULL argument");
+    *out = b->tuning;
+    out->tile_samples = b->tile;
+    out->threads_per_block = b->threads;
+    out->blocks_per_sm = b->per_sm > 0 ? b->per_sm : batch_max_per_sm(b->threads);
+    return MOSS_OK;
+}
+
+namespace {
+
+// host time of one run (the best of `reps` after a run that plans, captures
+// and warms up)
+int timed_runs(moss_batch *b, void *stream, std::vector<moss_result> &tmp, int reps, double *best) {
+    int rc = moss_batch_run(b, stream, tmp.data());
+    if (rc) return rc;
+    *best = 1e300;
+    for (int r = 0; r < reps; ++r) {
+        auto t0 = std::chrono::steady_clock::now();
+        if ((rc = moss_batch_run(b, stream, tmp.data()))) return rc;
+        const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        *best = dt < *best ? dt : *best;
+    }
+    return MOSS_OK;
+}
+
+}  // namespace
+
 int moss_batch_tune(moss_batch *b, void *stream, uint32_t *chosen) {
     if (!b) return set_error(MOSS_EINVAL, "NULL batch");
     if (b->reqs.empty()) return set_error(MOSS_EINVAL, "empty batch");
+    Guard dg(b->device);
     std::vector<moss_result> tmp(b->reqs.size());
-    const uint32_t cands[] = {1024, 4096, 16384, 65536};
-    uint32_t best = b->tile;
-    double best_t = 1e300;
-    for (uint32_t c : cands) {
-        int rc = moss_batch_set_tile(b, c);
-        if (rc) return rc;
-        if ((rc = moss_batch_run(b, stream, tmp.data()))) return rc;  // plan + capture + warm
-        double t = 1e300;
-        for (int rep = 0; rep < 2; ++rep) {
-            auto t0 = std::chrono::steady_clock::now();
-            if ((rc = moss_batch_run(b, stream, tmp.data()))) return rc;
-            const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-            t = dt < t ? dt : t;
+    int rc;
+    // 1. probe strategy per graph: one run with every graph on each strategy
+    //    it has tables for; a graph's cost under a strategy is the SM cycles
+    //    of its tiles per sample
+    std::vector<const moss_graph *> gs;
+    for (const Req &q : b->reqs)
+        if (std::find(gs.begin(), gs.end(), q.g) == gs.end()) gs.push_back(q.g);
+    const int strategies[3] = {MOSS_PROBE_SEARCH, MOSS_PROBE_HASH, MOSS_PROBE_FILTER};
+    std::vector<double> cost(gs.size() * 3, -1.0);
+    const auto saved = b->probes;
+    for (int si = 0; si < 3; ++si) {
+        b->probes.clear();
+        std::vector<bool> avail(gs.size(), false);
+        for (size_t gi = 0; gi < gs.size(); ++gi) {
+            DevGraph v;
+            if (graph_view_for(gs[gi], strategies[si], &v) == MOSS_OK) {
+                b->probes.push_back({gs[gi], strategies[si]});
+                avail[gi] = true;
+            }
         }
-        if (t < best_t) {
-            best_t = t;
-            best = c;
+        b->record = true;
+        b->dirty = true;
+        double t;
+        if ((rc = timed_runs(b, stream, tmp, 1, &t))) break;
+        std::vector<unsigned long long> cyc(b->ntiles);
+        if (b->ntiles && cudaMemcpy(cyc.data(), b->d_cycles, b->ntiles * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost) != cudaSuccess) {
+            rc = set_error(MOSS_ECUDA, "reading tile cycles");
+            break;
+        }
+        std::vector<double> c(gs.size(), 0.0), n(gs.size(), 0.0);
+        for (const BatchTask &t : b->plan_tasks) {
+            const moss_graph *g = b->plan_graphs[t.graph];
+            const size_t gi = (size_t)(std::find(gs.begin(), gs.end(), g) - gs.begin());
+            const uint64_t nt = (t.count + b->tile - 1) / b->tile;
+            for (uint64_t j = 0; j < nt; ++j) c[gi] += (double)cyc[t.tile0 + j];
+            n[gi] += (double)t.count;
+        }
+        for (size_t gi = 0; gi < gs.size(); ++gi)
+            if (avail[gi] && n[gi] > 0) cost[gi * 3 + si] = c[gi] / n[gi];
+    }
+    b->record = false;
+    b->dirty = true;
+    if (rc) {
+        b->probes = saved;
+        return rc;
+    }
+    b->probes.clear();
+    int per_strategy[3] = {0, 0, 0};
+    for (size_t gi = 0; gi < gs.size(); ++gi) {
+        int best = -1;
+        for (int si = 0; si < 3; ++si)
+            if (cost[gi * 3 + si] >= 0 && (best < 0 || cost[gi * 3 + si] < cost[gi * 3 + best])) best = si;
+        if (best < 0) {   // no tile of this graph ran (zero budgets): keep its own strategy
+            continue;
+        }
+        b->probes.push_back({gs[gi], strategies[best]});
+        ++per_strategy[best];
+    }
+    // 2. tile size, 3. block shape, 4. tile size again under that shape
+    const uint32_t tiles[] = {1024, 4096, 16384, 65536};
+    double best_t = 1e300;
+    auto try_tiles = [&]() -> int {
+        uint32_t best = b->tile;
+        for (uint32_t c : tiles) {
+            int r = moss_batch_set_tile(b, c);
+            double t;
+            if (r || (r = timed_runs(b, stream, tmp, 2, &t))) return r;
+            if (t < best_t) {
+                best_t = t;
+                best = c;
+            }
+        }
+        return moss_batch_set_tile(b, best);
+    };
+    if ((rc = try_tiles())) return rc;
+    int best_threads = b->threads, best_per = b->per_sm;
+    for (int th : {128, 256, 512}) {
+        const int mx = batch_max_per_sm(th);
+        int pers[3] = {mx, (3 * mx + 3) / 4, (mx + 1) / 2};
+        for (int pi = 0; pi < 3; ++pi) {
+            if (pi > 0 && pers[pi] == pers[pi - 1]) continue;
+            if ((rc = moss_batch_set_launch(b, th, pers[pi]))) return rc;
+            double t;
+            if ((rc = timed_runs(b, stream, tmp, 2, &t))) return rc;
+            if (t < best_t) {
+                best_t = t;
+                best_threads = th;
+                best_per = pers[pi];
+            }
         }
     }
-    int rc = moss_batch_set_tile(b, best);
-    if (rc) return rc;
-    if (chosen) *chosen = best;
+    if ((rc = moss_batch_set_launch(b, best_threads, best_per))) return rc;
+    if ((rc = try_tiles())) return rc;
+    b->tuning.graphs = (int)gs.size();
+    b->tuning.graphs_search = per_strategy[0];
+    b->tuning.graphs_hash = per_strategy[1];
+    b->tuning.graphs_filter = per_strategy[2];
+    b->tuning.run_s = best_t;
+    b->tuning.tuned = 1;
+    if (chosen) *chosen = b->tile;
     return MOSS_OK;
 }
 
@@ -348,6 +507,7 @@ void moss_batch_free(moss_batch *b) {
     void *dev[] = {b->d_graphs, b->d_tasks, b->d_reqs, b->d_tiles, b->d_task_counts, b->d_results};
     for (void *p : dev)
         if (p) cudaFreeAsync(p, b->stream);
+    if (b->d_cycles) cudaFreeAsync(b->d_cycles, b->stream);
     if (b->d_next) cudaFree(b->d_next);
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->h_results) cudaFreeHost(b->h_results);

@@ -258,7 +258,7 @@ int effective_probe(const moss_graph *g) {
     return hash_buckets_for(g->nnz) * 8 * kBucketKeys > (64ull << 20) ? MOSS_PROBE_FILTER : MOSS_PROBE_HASH;
 }
 
-DevGraph view(const moss_graph *g) {
+DevGraph view_with(const moss_graph *g, int eff) {
     DevGraph d;
     d.vert = g->vert;
     d.col = g->col;
@@ -272,7 +272,6 @@ DevGraph view(const moss_graph *g) {
     d.rlist = g->rlist;
     d.defer = g->defer;
     d.n = g->n;
-    const int eff = effective_probe(g);
     const bool use_hash = eff != MOSS_PROBE_SEARCH && (g->built >> 4 & 1u);
     const bool use_filter = eff == MOSS_PROBE_FILTER && (g->built >> 6 & 1u);
     d.hash = use_hash ? reinterpret_cast<const uint4 *>(g->hash) : nullptr;
@@ -286,6 +285,8 @@ DevGraph view(const moss_graph *g) {
     d.filter_shift = 64 - lf;
     return d;
 }
+
+DevGraph view(const moss_graph *g) { return view_with(g, effective_probe(g)); }
 
 void describe_flags(uint32_t f, char *buf, size_t len) {
     buf[0] = 0;
@@ -941,6 +942,16 @@ const AuxStreams *aux_streams() {
         }
     }
     return x.a[0] ? &x : nullptr;
+}
+
+int graph_view_for(const moss_graph *g, int strategy, DevGraph *out) {
+    const bool hash = (g->built >> 4 & 1u) != 0, filter = (g->built >> 6 & 1u) != 0;
+    if (strategy == MOSS_PROBE_AUTO) strategy = effective_probe(g);
+    if (strategy == MOSS_PROBE_HASH && !hash) return set_error(MOSS_ESTATE, "hashed edge set not built");
+    if (strategy == MOSS_PROBE_FILTER && !(hash && filter)) return set_error(MOSS_ESTATE, "edge filter not built");
+    if (strategy < MOSS_PROBE_SEARCH || strategy > MOSS_PROBE_FILTER) return set_error(MOSS_EINVAL, "unknown probe strategy");
+    *out = view_with(g, strategy);
+    return MOSS_OK;
 }
 
 int graph_info(const moss_graph *g, GraphInfo *out) {

@@ -334,14 +334,16 @@ struct BatchRequest {
     const DevTotals *tot;
     int task[2];      // task index per sub-method, -1 when it draws nothing
 };
-// persistent sampler over a batch: tile_counts[t][22] per tile
+// persistent sampler over a batch: tile_counts[t][22] per tile; threads per
+// block 128, 256 or 512; tile_cycles (nullable) receives each tile's SM cycles
 cudaError_t launch_sample_batch(const DevGraph *graphs, const BatchTask *tasks, int ntasks, uint64_t ntiles,
                                 uint32_t tile_samples, unsigned long long *next_tile, uint32_t *tile_counts,
-                                int blocks, cudaStream_t s);
+                                int threads, int blocks, unsigned long long *tile_cycles, cudaStream_t s);
 // task_counts[task][22] = sum of the task's tile rows, in tile order
 cudaError_t launch_batch_reduce(const BatchTask *tasks, int ntasks, uint32_t tile_samples,
                                 const uint32_t *tile_counts, uint64_t *task_counts, cudaStream_t s);
-int batch_blocks(int device);
+int batch_max_per_sm(int threads);                    // resident blocks per SM at most
+int batch_blocks(int device, int threads, int per_sm);  // grid; per_sm <= 0: the most that fit
 cudaError_t launch_finalize_batch(const BatchRequest *reqs, int nreq, const uint64_t *task_counts, void *results,
                                   cudaStream_t s);
 
@@ -361,5 +363,8 @@ struct GraphInfo {
 struct moss_graph;
 namespace moss {
 int graph_info(const moss_graph *g, GraphInfo *out);
+// the device view of g with the given probe strategy (MOSS_PROBE_*; AUTO: the
+// graph's own); MOSS_ESTATE when the tables it needs are not built
+int graph_view_for(const moss_graph *g, int strategy, DevGraph *out);
 int set_error(int code, const char *detail);   // records the thread's error detail
 }  // namespace moss

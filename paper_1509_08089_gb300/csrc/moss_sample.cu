@@ -702,21 +702,30 @@ __device__ __forceinline__ int sample_any(const DevGraph &g, const uint8_t *lut4
     return sample_path5<HASH, 3>(g, lut5, seed, s).cls;
 }
 
-__global__ void __launch_bounds__(kThreads, kBatchBlocks)
+// Persistent sampler over a batch: warps take tiles of `tile_samples` ids of
+// one task from a device counter.  THREADS per block is a tuning choice (the
+// resident threads per SM stay the same: THREADS x blocks = 1,024).  With
+// tile_cycles non-null the first lane of a warp records each tile's
+// duration in SM clock cycles (the autotuner's per-graph cost of a probe
+// strategy).
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, kBatchBlocks * kThreads / THREADS)
     k_sample_batch(const DevGraph *graphs, const BatchTask *tasks, int ntasks, uint64_t ntiles, uint32_t tile_samples,
-                   unsigned long long *next_tile, uint32_t *tile_counts) {
+                   unsigned long long *next_tile, uint32_t *tile_counts, unsigned long long *tile_cycles) {
+    constexpr int kW = THREADS / 32;
     __shared__ uint8_t lut4[64];
     __shared__ uint8_t lut5[kLut];
     __shared__ uint8_t lutc[4096];
-    __shared__ uint32_t hist[kWarps][kSlots];
-    __shared__ DevGraph gsh[kWarps];
+    __shared__ uint32_t hist[kW][kSlots];
+    __shared__ DevGraph gsh[kW];
     static_assert(sizeof(DevGraph) % 4 == 0 && sizeof(DevGraph) / 4 <= 64, "graph descriptor staging");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < 64; i += kThreads) lut4[i] = g_lut4[i];
-    for (int i = threadIdx.x; i < kLut; i += kThreads) lut5[i] = g_lut5[i];
-    for (int i = threadIdx.x; i < 4096; i += kThreads) lutc[i] = g_lutc[i];
+    for (int i = threadIdx.x; i < 64; i += THREADS) lut4[i] = g_lut4[i];
+    for (int i = threadIdx.x; i < kLut; i += THREADS) lut5[i] = g_lut5[i];
+    for (int i = threadIdx.x; i < 4096; i += THREADS) lutc[i] = g_lutc[i];
     __syncthreads();
     for (;;) {
+        const long long c0 = clock64();
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(next_tile, 1ull);
         t = __shfl_sync(0xffffffffu, t, 0);
@@ -748,6 +757,7 @@ __global__ void __launch_bounds__(kThreads, kBatchBlocks)
         }
         __syncwarp();
         if (lane < kSlots) tile_counts[t * kSlots + lane] = hist[warp][lane];
+        if (tile_cycles && lane == 0) tile_cycles[t] = (unsigned long long)(clock64() - c0);
         __syncwarp();
     }
 }
@@ -922,19 +932,34 @@ cudaError_t launch_counts(int method, const DevGraph &g, uint64_t first, uint64_
     return cudaSuccess;
 }
 
-int batch_blocks(int device) {
-    const int sms = device_sms(device);
-    int per = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample_batch, kThreads, 0) != cudaSuccess || per < 1)
-        per = 1;
-    return sms * per;
+int batch_max_per_sm(int threads) {
+    int per = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (threads == 128) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample_batch<128>, 128, 0);
+    if (threads == 256) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample_batch<256>, 256, 0);
+    if (threads == 512) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample_batch<512>, 512, 0);
+    return e == cudaSuccess && per > 0 ? per : 1;
+}
+
+int batch_blocks(int device, int threads, int per_sm) {
+    const int max = batch_max_per_sm(threads);
+    const int per = per_sm <= 0 || per_sm > max ? max : per_sm;
+    return device_sms(device) * per;
 }
 
 cudaError_t launch_sample_batch(const DevGraph *graphs, const BatchTask *tasks, int ntasks, uint64_t ntiles,
                                 uint32_t tile_samples, unsigned long long *next_tile, uint32_t *tile_counts,
-                                int blocks, cudaStream_t s) {
+                                int threads, int blocks, unsigned long long *tile_cycles, cudaStream_t s) {
     if (ntasks <= 0 || ntiles == 0) return cudaSuccess;
-    k_sample_batch<<<blocks, kThreads, 0, s>>>(graphs, tasks, ntasks, ntiles, tile_samples, next_tile, tile_counts);
+    if (threads == 128)
+        k_sample_batch<128><<<blocks, 128, 0, s>>>(graphs, tasks, ntasks, ntiles, tile_samples, next_tile, tile_counts,
+                                                   tile_cycles);
+    else if (threads == 512)
+        k_sample_batch<512><<<blocks, 512, 0, s>>>(graphs, tasks, ntasks, ntiles, tile_samples, next_tile, tile_counts,
+                                                   tile_cycles);
+    else
+        k_sample_batch<256><<<blocks, 256, 0, s>>>(graphs, tasks, ntasks, ntiles, tile_samples, next_tile, tile_counts,
+                                                   tile_cycles);
     return cudaGetLastError();
 }
 

@@ -204,7 +204,7 @@ int run_tick(moss_server *s, const std::vector<BatchTask> &tasks, uint64_t ntile
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_next, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess)
         e = launch_sample_batch(s->d_graphs, s->d_tasks, (int)tasks.size(), ntiles, s->cfg.tile_samples, s->d_next,
-                                s->d_tiles, s->blocks, st);
+                                s->d_tiles, 256, s->blocks, nullptr, st);
     if (e == cudaSuccess)
         e = launch_batch_reduce(s->d_tasks, (int)tasks.size(), s->cfg.tile_samples, s->d_tiles, s->d_task_counts, st);
     if (e == cudaSuccess)
@@ -406,7 +406,7 @@ int moss_server_create(int device, const moss_server_config *cfg, moss_server **
     cudaSetDevice(device);
     const bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
                     cudaMalloc(reinterpret_cast<void **>(&s->d_next), sizeof(unsigned long long)) == cudaSuccess;
-    s->blocks = batch_blocks(device);
+    s->blocks = batch_blocks(device, 256, 0);
     if (prev >= 0) cudaSetDevice(prev);
     if (!ok) {
         moss_server_free(s);

@@ -150,3 +150,55 @@ def test_batch_rejects_unbuilt_graph_and_handles_empty():
         assert ei.value.status == moss.MOSS_ESTATE
         batch.add(g, 4, 100, 1)
         assert batch.run()[0]["est"][1] == pytest.approx(10.0)
+
+
+def test_every_tuner_setting_leaves_results_unchanged(fleet):
+    """Each launch setting the autotuner chooses among -- threads per block,
+    resident blocks per SM, each graph's probe strategy -- and the tuned
+    choice itself give every request exactly its solo result."""
+    csrs, graphs = fleet
+    filt = [moss.Graph(rp, col, probe=moss.PROBE_FILTER) for rp, col in csrs[:4]]     # all three strategies
+    srch = [moss.Graph(rp, col, probe=moss.PROBE_SEARCH) for rp, col in csrs[4:6]]    # list search only
+    pool = graphs + filt + srch
+    try:
+        reqs = requests(len(pool), 17)
+        solo = [pool[gi].estimate(k, budget, seed) for gi, k, budget, seed in reqs]
+        with moss.Batch() as batch:
+            for gi, k, budget, seed in reqs:
+                batch.add(pool[gi], k, budget, seed)
+            batch.set_tile(2048)
+            for threads in (128, 256, 512):
+                for per_sm in (1, 0):
+                    batch.set_launch(threads, per_sm)
+                    for a, b in zip(solo, batch.run()):
+                        same(b, a)
+            batch.set_launch(256, 0)
+            for strategy in (moss.PROBE_SEARCH, moss.PROBE_HASH, moss.PROBE_FILTER):
+                for g in pool:
+                    try:
+                        batch.set_probe(g, strategy)
+                    except moss.MossError as e:       # the graph lacks that strategy's tables
+                        assert e.status == moss.MOSS_ESTATE
+                        assert strategy != moss.PROBE_SEARCH
+                for a, b in zip(solo, batch.run()):
+                    same(b, a)
+            with pytest.raises(moss.MossError) as ei:
+                batch.set_probe(srch[0], moss.PROBE_HASH)
+            assert ei.value.status == moss.MOSS_ESTATE
+            with pytest.raises(moss.MossError):
+                batch.set_launch(100, 0)
+            for g in pool:
+                batch.set_probe(g, moss.PROBE_AUTO)
+            chosen = batch.tune()
+            t = batch.tuning()
+            assert t["tuned"] == 1 and t["tile_samples"] == chosen
+            assert t["threads_per_block"] in (128, 256, 512) and t["blocks_per_sm"] >= 1
+            assert t["graphs"] == len(pool)
+            # every graph that drew samples got a strategy it has tables for
+            assert len(pool) - 1 <= t["graphs_search"] + t["graphs_hash"] + t["graphs_filter"] <= len(pool)
+            assert t["graphs_filter"] <= len(filt) and t["graphs_search"] >= len(srch)
+            for a, b in zip(solo, batch.run()):
+                same(b, a)
+    finally:
+        for g in filt + srch:
+            g.close()
