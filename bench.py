@@ -77,6 +77,8 @@ def parse():
                    help="single mode: leave out the 34M-edge, batched and served terms of the line")
     p.add_argument("--serve-duration", type=float, default=1.0,
                    help="seconds of Poisson arrivals of the served term of the default line")
+    p.add_argument("--rng", default="splitmix64", choices=["splitmix64", "philox4x32"],
+                   help="word generator of the samples (both sides of the comparison use it)")
     p.add_argument("--probe", default="auto", choices=["auto", "hash", "filter", "search"],
                    help="induced-edge tests: auto (filtered set when the set exceeds 64 MiB, else the set), "
                         "hashed edge set, set behind a Bloom filter, or sorted-list search")
@@ -87,7 +89,7 @@ def parse():
 def _oracle_worker(args):
     """One process of the CPU baseline: build the oracle's tables for the
     workload, then draw its share of samples of each sub-method."""
-    workload, k, seed, shares = args
+    workload, k, seed, shares, rng = args
     sys.path.insert(0, ROOT)
     import oracle
     import synth
@@ -98,7 +100,7 @@ def _oracle_worker(args):
         g.build_min()
     t1 = time.perf_counter()
     for method, first, count in shares:
-        g.run(method, seed, count, first=first)
+        g.run(method, seed, count, first=first, rng=rng)
     t2 = time.perf_counter()
     return t1 - t0, t2 - t1, sum(c for _, _, c in shares)
 
@@ -107,12 +109,12 @@ def sub_methods(k, mix=False):
     return ([0, 3] if mix else [0]) if k == 4 else [1, 2]
 
 
-def oracle_pass(pool, cores, workload, k, seed, per_worker, mix=False):
+def oracle_pass(pool, cores, workload, k, seed, per_worker, mix=False, rng=0):
     methods = sub_methods(k, mix)
     jobs = []
     for w in range(cores):
         shares = [(m, w * per_worker // len(methods), per_worker // len(methods)) for m in methods]
-        jobs.append((workload, k, seed, shares))
+        jobs.append((workload, k, seed, shares, rng))
     t0 = time.perf_counter()
     res = list(pool.map(_oracle_worker, jobs))
     wall = time.perf_counter() - t0
@@ -133,12 +135,15 @@ def bench_config(args, rp, world: int, workload: str | None = None) -> dict:
     """The `config` object of a line; both arms print the same one."""
     wl = workload or describe(args.workload, args.k, args.mode == "min")[1]
     return {"workload": wl, "budget_per_gpu": args.budget, "seed": args.seed,
-            "probe": resolved_probe(args.probe, rp),
+            "probe": resolved_probe(args.probe, rp), "rng": args.rng,
             "l2": "GPU arm: flushed (512 MB write) before every timed step; CPU oracle: not applicable",
             "parallelism": f"replicas x{world}"}
 
 
-def calibrate_per_worker(workload, k, seed, seconds, mix=False):
+RNG_IDS = {"splitmix64": 0, "philox4x32": 1}   # the same numbering on both sides
+
+
+def calibrate_per_worker(workload, k, seed, seconds, mix=False, rng=0):
     """Samples per worker process for about `seconds` of sampling, and the
     oracle's sampling rate on one core (samples/s) measured on the way."""
     import oracle
@@ -151,7 +156,7 @@ def calibrate_per_worker(workload, k, seed, seconds, mix=False):
     n = 20_000
     t0 = time.perf_counter()
     for m in methods:
-        g.run(m, seed, n // len(methods))
+        g.run(m, seed, n // len(methods), rng=rng)
     per = (time.perf_counter() - t0) / n
     return max(len(methods), int(seconds / per)), 1.0 / per
 
@@ -178,13 +183,14 @@ def run_reference(args):
     METRIC, _ = describe(args.workload, args.k, mix)
     rp, _col = synth.workload(args.workload)
     cores = os.cpu_count() or 1
-    per_worker, single = calibrate_per_worker(args.workload, args.k, args.seed, 4.0, mix)
+    rng = RNG_IDS[args.rng]
+    per_worker, single = calibrate_per_worker(args.workload, args.k, args.seed, 4.0, mix, rng)
     with make_pool(cores) as pool:
         for _ in range(args.warmup):
-            oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker, mix)
+            oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker, mix, rng)
         walls, counts = [], []
         for _ in range(args.steps):
-            b, sw, n, wall = oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker, mix)
+            b, sw, n, wall = oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker, mix, rng)
             walls.append(wall)
             counts.append(n)
     samples = counts[0]
@@ -224,7 +230,7 @@ class Clocks:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -481,10 +487,13 @@ def run_gpu(args):
     probe = {"auto": moss.PROBE_AUTO, "hash": moss.PROBE_HASH, "filter": moss.PROBE_FILTER,
              "search": moss.PROBE_SEARCH}[args.probe]
 
+    rng = RNG_IDS[args.rng]
+
     def step(src_rp, src_col, seed, kk=k, budget=args.budget):
         h = moss.moss_graph_load_csr(src_rp, src_col, device=dev, stream=stream)
         try:
             moss.moss_set_probe(h, probe)
+            moss.moss_set_rng(h, rng)
             moss.moss_build_tables(h, (1 << kk) | (moss.TABLES_4MIN if mix else 0), stream)
             if world == 1 and mix:
                 K4, Km = (K for _, K in sub_budgets(kk, budget, True))
@@ -566,6 +575,7 @@ def run_gpu(args):
     h = moss.moss_graph_load_csr(rp_d, col_d, device=dev, stream=stream)
     try:
         moss.moss_set_probe(h, probe)
+        moss.moss_set_rng(h, rng)
         moss.moss_build_tables(h, kmask, stream)
         times = time_calls(moss, torch, h, k, args.budget, mix, args.seed, stream, l2_flush)
     finally:
@@ -607,6 +617,7 @@ def run_gpu(args):
         h = moss.moss_graph_load_csr(rp3_d, col3_d, device=dev, stream=stream)
         try:
             moss.moss_set_probe(h, probe)
+            moss.moss_set_rng(h, rng)
             moss.moss_build_tables(h, 1 << 5, stream)
             t3 = time_calls(moss, torch, h, 5, B3, False, args.seed, stream, l2_flush, reps=2)
         finally:
@@ -617,17 +628,18 @@ def run_gpu(args):
             "metric": "5-node samples/s at 34M edges", "value": B3 / (m3 / 1000.0), "unit": "samples/s",
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": m3, "step_ms": ms3,
             "config": {"workload": describe("cl_n4m", 5)[1], "budget": B3, "seed": args.seed, "probe": p3,
+                       "rng": args.rng,
                        "l2": "flushed (512 MB write) before every timed step; tables larger than the L2"},
             "roofline": roofline("cl_n4m", rp3, p3, t3, [1, 2], l2_bytes, gather, peaks),
             "clocks": clk3, "gpu_launches": launches_per_step(5, B3, False, p3 == "filter") * args.steps}
         out["batched"] = measure_batched(moss, torch, [f.result() for f in futures["batched"]],
-                                         batch_specs(args.graphs)[1], args.steps, args.warmup, stream)
+                                         batch_specs(args.graphs)[1], args.steps, args.warmup, stream, rng)
         out["served"] = measure_served(moss, [f.result() for f in futures["served"]], args.rate,
-                                       args.serve_duration)
+                                       args.serve_duration, rng=rng)
 
     if pool is not None and not args.no_cpu_baseline:
-        per_worker, single = calibrate_per_worker(args.workload, k, args.seed, 12.0, mix)
-        b, sw, n, wall = oracle_pass(pool, cores, args.workload, k, args.seed, per_worker, mix)
+        per_worker, single = calibrate_per_worker(args.workload, k, args.seed, 12.0, mix, rng)
+        b, sw, n, wall = oracle_pass(pool, cores, args.workload, k, args.seed, per_worker, mix, rng)
         v, rate = oracle_rate(b, sw, n, args.budget)
         out["cpu_baseline"] = {
             "value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
@@ -683,12 +695,12 @@ BATCH_WORKLOAD = ("{n} graphs, n 500-50,000 log-uniform, half Chung-Lu exponent 
                   "degree 6-30, k in {{4,5}}, budgets 1e4-1e7 log-uniform")
 
 
-def measure_batched(moss, torch, csrs, meta, steps, warmup, stream):
+def measure_batched(moss, torch, csrs, meta, steps, warmup, stream, rng=0):
     """Every graph's request in one persistent launch (autotuned), timed by
     the host around the synchronous call, against one moss_sample_estimate
     launch per request back to back; counts must agree."""
     t0 = time.perf_counter()
-    graphs = [moss.Graph(rp, col, stream=stream) for rp, col in csrs]
+    graphs = [moss.Graph(rp, col, stream=stream, rng=rng) for rp, col in csrs]
     load_s = time.perf_counter() - t0
     total = sum(b for _, b, _ in meta)
     edges = sum(len(col) // 2 for _, col in csrs)
@@ -743,7 +755,7 @@ def run_batch(args):
     torch.cuda.set_device(0)
     moss.load()
     stream = torch.cuda.current_stream()
-    r = measure_batched(moss, torch, csrs, meta, args.steps, args.warmup, stream)
+    r = measure_batched(moss, torch, csrs, meta, args.steps, args.warmup, stream, RNG_IDS[args.rng])
     r.update({"n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
               "data": "synthetic"})
     r["config"]["generation_s"] = round(gen_s, 1)
@@ -815,12 +827,12 @@ SERVED_CFG = dict(max_active=512, tick_samples=100_000_000, tile_samples=4096, *
 PLAIN_CFG = dict(max_active=1, tick_samples=10_000_000, tile_samples=4096, **SERVE_COMMON)
 
 
-def measure_served(moss, csrs, rate: float, duration: float, eps=(0.01, 0.05)):
+def measure_served(moss, csrs, rate: float, duration: float, eps=(0.01, 0.05), rng=0):
     """A Poisson stream of target-error requests over resident graphs, served
     with continuous batching and, on the same stream, one request per
     launch; each with its own clock record."""
     import torch
-    graphs = [moss.Graph(rp, col) for rp, col in csrs]
+    graphs = [moss.Graph(rp, col, rng=rng) for rp, col in csrs]
     edges = sum(len(col) // 2 for _, col in csrs)
     try:
         sched = poisson_schedule(rate, duration, len(graphs), eps[0], eps[1], seed=5)
@@ -856,7 +868,7 @@ def run_serve(args):
     gen_s = time.perf_counter() - t0
     torch.cuda.set_device(0)
     moss.load()
-    runs = {name: measure_served(moss, csrs, args.rate, args.duration, eps)
+    runs = {name: measure_served(moss, csrs, args.rate, args.duration, eps, RNG_IDS[args.rng])
             for name, eps in (("mixed", (0.01, 0.05)), ("rse_1pct", (0.01, 0.01)))}
     r = dict(runs["mixed"])
     r.update({"n_gpus": 1, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",

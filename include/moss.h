@@ -158,6 +158,23 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream);
  * requires moss_build_tables afterwards (MOSS_ESTATE until then). */
 int moss_set_probe(moss_graph *g, int strategy);
 
+/* Word generator of the graph's samples (every sampling call, batch and
+ * server request on it); the paper draws uniformly without naming one.
+ *   MOSS_RNG_SPLITMIX64 (default): word i (0 <= i < 16) of sample s of
+ *     method t under seed k is output (4 s + t) 16 + i + 1 of SplitMix64
+ *     (Steele, Lea, Flood, OOPSLA 2014) seeded with k.
+ *   MOSS_RNG_PHILOX4X32: words 2b, 2b+1 are the outputs of Philox4x32-10
+ *     (Salmon et al., SC 2011) for the counter (s mod 2^32, s div 2^32, t, b)
+ *     under the key (k mod 2^32, k div 2^32), low output first.
+ * Either is counter-based: a sample's draws depend on (seed, method, id)
+ * alone, so counts do not depend on launch shape, stream or device count.
+ * Changing it needs no table rebuild.  MOSS_EINVAL for another value;
+ * moss_get_rng returns the current one (MOSS_EINVAL for NULL). */
+#define MOSS_RNG_SPLITMIX64 0
+#define MOSS_RNG_PHILOX4X32 1
+int moss_set_rng(moss_graph *g, int rng);
+int moss_get_rng(const moss_graph *g);
+
 /* Sample-and-estimate.  k = 4: MOSS-4 with K = budget.  k = 5: T-5 with
  * K1 = floor(budget/2) and Path-5 with K2 = budget - K1 (K1 = K2, Sec. 5.1.5).
  * A sub-method whose total weight is 0 draws nothing (its classes cannot

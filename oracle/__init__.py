@@ -7,7 +7,8 @@ and shares no code with it.
 Contents
 * ``moss_oracle.c`` (compiled with gcc on first use): exact integer vertex
   weights and totals (Table 1), alias tables for WeightRandomVertex
-  (Sec. 4.1.3), the counter-form SplitMix64 word schedule, the per-sample steps of
+  (Sec. 4.1.3), the counter-form SplitMix64 and Philox4x32-10 word
+  schedules, the per-sample steps of
   Algorithm 1 (MOSS-4), Algorithm 2 (MOSS-4Min, Sec. 4.2: the total order,
   N_{u,v}, the weights Gamma-check_v and sigma-check, and c(s), the number
   of 3-paths of a CIS that the method can draw), Algorithm 3 (T-5) and
@@ -33,6 +34,7 @@ _LIB = os.path.join(_HERE, "libmoss_oracle.so")
 _lib = None
 
 MOSS4, T5, PATH5, MOSS4MIN = 0, 1, 2, 3
+SPLITMIX64, PHILOX4X32 = 0, 1     # word generators
 
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
@@ -71,6 +73,11 @@ def _load():
         lib.oracle_run.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                    _u64p, _u8p, _u32p]
         lib.oracle_run.restype = ctypes.c_int
+        lib.oracle_run_rng.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                       ctypes.c_uint64, _u64p, _u8p, _u32p]
+        lib.oracle_run_rng.restype = ctypes.c_int
+        lib.oracle_philox4x32.argtypes = [_u32p, _u32p, _u32p]
+        lib.oracle_words.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, _u64p]
         lib.oracle_esu.argtypes = [ctypes.c_void_p, ctypes.c_int, _u64p]
         lib.oracle_esu.restype = ctypes.c_int
         lib.oracle_build_min.argtypes = [ctypes.c_void_p]
@@ -94,10 +101,26 @@ def splitmix64(seed: int, k: int) -> int:
     return int(_load().oracle_splitmix(seed % (1 << 64), k % (1 << 64)))
 
 
-def sample_words(method: int, seed: int, s: int, n: int = 16) -> list[int]:
-    """Words x_0 .. x_{n-1} of sample s of a method: output (4 s + method) 16 +
-    i + 1 of SplitMix64 seeded with seed."""
-    return [splitmix64(seed, (4 * s + method) * 16 + i + 1) for i in range(n)]
+def sample_words(method: int, seed: int, s: int, n: int = 16, rng: int = SPLITMIX64) -> list[int]:
+    """Words x_0 .. x_{n-1} of sample s of a method: SplitMix64 output
+    (4 s + method) 16 + i + 1 under seed; or, with rng=PHILOX4X32, words 2b,
+    2b+1 from Philox4x32-10 block (s lo, s hi, method, b) under the key
+    (seed lo, seed hi)."""
+    if rng == SPLITMIX64:
+        return [splitmix64(seed, (4 * s + method) * 16 + i + 1) for i in range(n)]
+    x = np.zeros(16, dtype=np.uint64)
+    _load().oracle_words(rng, method, seed % (1 << 64), s % (1 << 64), _p(x, _u64p))
+    return [int(v) for v in x[:n]]
+
+
+def philox4x32(counter, key) -> list[int]:
+    """The four 32-bit outputs of Philox4x32-10 for a 4-word counter and a
+    2-word key."""
+    c = np.array([int(v) for v in counter], dtype=np.uint32)
+    k = np.array([int(v) for v in key], dtype=np.uint32)
+    o = np.zeros(4, dtype=np.uint32)
+    _load().oracle_philox4x32(_p(c, _u32p), _p(k, _u32p), _p(o, _u32p))
+    return [int(v) for v in o]
 
 
 def classify(k: int, mask: int) -> int:
@@ -213,19 +236,19 @@ class OracleGraph:
             raise ValueError("method has zero total weight on this graph")
         return [int(v) for v in verts], cls.value
 
-    def run(self, method: int, seed: int, count: int, first: int = 0, record: bool = False):
+    def run(self, method: int, seed: int, count: int, first: int = 0, record: bool = False, rng: int = SPLITMIX64):
         """Counts (uint64[22]; [0] = collisions) of samples first..first+count-1.
         With record=True also per-sample classes (uint8) and vertices (uint32[.,5]).
         MOSS-4Min (method 3) counts by (class, c) slot (:func:`min_slot`) and
-        records c(s) as the fifth vertex entry."""
+        records c(s) as the fifth vertex entry.  rng picks the word generator."""
         if method == MOSS4MIN:
             self.build_min()
         counts = np.zeros(22, dtype=np.uint64)
         classes = np.zeros(max(count, 1), dtype=np.uint8) if record else None
         verts = np.zeros((max(count, 1), 5), dtype=np.uint32) if record else None
-        rc = _load().oracle_run(self._ctx, method, seed, first, count, _p(counts, _u64p),
-                                _p(classes, _u8p) if record else None,
-                                _p(verts, _u32p) if record else None)
+        rc = _load().oracle_run_rng(self._ctx, method, rng, seed, first, count, _p(counts, _u64p),
+                                    _p(classes, _u8p) if record else None,
+                                    _p(verts, _u32p) if record else None)
         if rc == -1:
             raise ValueError("method has zero total weight on this graph")
         if rc:
@@ -242,28 +265,28 @@ class OracleGraph:
         return counts
 
     # -- the whole path -----------------------------------------------------
-    def estimate(self, k: int, budget: int, seed: int, **kw):
+    def estimate(self, k: int, budget: int, seed: int, rng: int = SPLITMIX64, **kw):
         """Sample-and-estimate as the library defines it: k=4 runs MOSS-4 with
         K=budget; k=5 runs T-5 with K1=floor(budget/2) and Path-5 with
         K2=budget-K1 (K1=K2, Sec. 5.1.5)."""
         if k == 4:
             K = budget if self.Gamma[0] > 0 else 0
-            m = self.run(MOSS4, seed, K) if K else np.zeros(22, dtype=np.uint64)
+            m = self.run(MOSS4, seed, K, rng=rng) if K else np.zeros(22, dtype=np.uint64)
             return finalize_moss4(m, K, self.Gamma[0], self.Lambda3, **kw)
         K1 = budget // 2
         K2 = budget - K1
         K1 = K1 if self.Gamma[1] > 0 else 0
         K2 = K2 if self.Gamma[2] > 0 else 0
-        m1 = self.run(T5, seed, K1) if K1 else np.zeros(22, dtype=np.uint64)
-        m2 = self.run(PATH5, seed, K2) if K2 else np.zeros(22, dtype=np.uint64)
+        m1 = self.run(T5, seed, K1, rng=rng) if K1 else np.zeros(22, dtype=np.uint64)
+        m2 = self.run(PATH5, seed, K2, rng=rng) if K2 else np.zeros(22, dtype=np.uint64)
         return finalize_moss5(m1, m2, K1, K2, self.Gamma[1], self.Gamma[2], self.Lambda4, **kw)
 
-    def estimate_min(self, budget: int, budget_min: int, seed: int, **kw):
+    def estimate_min(self, budget: int, budget_min: int, seed: int, rng: int = SPLITMIX64, **kw):
         """MOSS-4 with K = budget and MOSS-4Min with K-check = budget_min on
         the same seed, mixed by Theorem 1 (Sec. 4.2)."""
         Gm = self.build_min()
         K = budget if self.Gamma[0] > 0 else 0
         Km = budget_min if Gm > 0 else 0
-        m = self.run(MOSS4, seed, K) if K else np.zeros(22, dtype=np.uint64)
-        mm = self.run(MOSS4MIN, seed, Km) if Km else np.zeros(22, dtype=np.uint64)
+        m = self.run(MOSS4, seed, K, rng=rng) if K else np.zeros(22, dtype=np.uint64)
+        mm = self.run(MOSS4MIN, seed, Km, rng=rng) if Km else np.zeros(22, dtype=np.uint64)
         return finalize_moss4min(m, mm, K, Km, self.Gamma[0], Gm, self.Lambda3, **kw)

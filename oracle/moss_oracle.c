@@ -29,7 +29,12 @@
  * generators", OOPSLA 2014), used in counter form: word i (0 <= i < 16) of
  * sample s of method tag t under seed k is output number (4 s + t) 16 + i + 1
  * of the generator seeded with k, i.e. mix(k + ((4 s + t) 16 + i + 1) gamma).
- * The paper draws uniform choices without fixing a generator.
+ * The paper draws uniform choices without fixing a generator.  The second
+ * generator is Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3", SC 2011): words 2b and 2b+1 of sample s of
+ * method tag t under seed k are the four 32-bit outputs of block
+ * (s mod 2^32, s div 2^32, t, b) under the key (k mod 2^32, k div 2^32),
+ * low half first: x_2b = out0 + 2^32 out1, x_2b+1 = out2 + 2^32 out3.
  * Word schedule (x_i = word i):
  *   MOSS-4 : x0,x1 seed draw (column, threshold); x2,x3 sigma draw of u;
  *            x4 w; x5 r.
@@ -60,6 +65,30 @@ uint64_t oracle_splitmix(uint64_t seed, uint64_t k) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
     return z ^ (z >> 31);
+}
+
+/* Philox4x32-10: ten rounds on the counter (c0, c1, c2, c3) under the key
+ * (k0, k1).  A round takes the two 64-bit products p = 0xD2511F53 c0 and
+ * q = 0xCD9E8D57 c2 and makes the counter (hi(q) ^ c1 ^ k0, lo(q),
+ * hi(p) ^ c3 ^ k1, lo(p)); between rounds the key grows by the Weyl
+ * increments (0x9E3779B9, 0xBB67AE85) modulo 2^32. */
+void oracle_philox4x32(const uint32_t in[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = in[0], c1 = in[1], c2 = in[2], c3 = in[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p = (uint64_t)0xD2511F53u * c0;
+        uint64_t q = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(q >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)q;
+        uint32_t n2 = (uint32_t)(p >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
 static uint64_t index_of(uint64_t x, uint64_t m) { return (uint64_t)(((u128)x * m) >> 64); }
@@ -494,22 +523,39 @@ int oracle_sample_words(const ctx *c, int method, const uint64_t *words, uint32_
     return 0;
 }
 
-/* words of sample s: x[i] = output (4 s + tag) 16 + i + 1 of SplitMix64(seed) */
-static void sample_words(int method, uint64_t seed, uint64_t s, uint64_t *x) {
+/* words of sample s under a generator: SplitMix64 (rng 0), x[i] = output
+ * (4 s + tag) 16 + i + 1 of SplitMix64(seed); Philox4x32-10 (rng 1), x[2b],
+ * x[2b+1] from block (s lo, s hi, tag, b) under the key (seed lo, seed hi) */
+static void sample_words(int rng, int method, uint64_t seed, uint64_t s, uint64_t *x) {
+    if (rng == 1) {
+        const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        for (uint32_t b = 0; b < 8; b++) {
+            const uint32_t ctr[4] = {(uint32_t)s, (uint32_t)(s >> 32), (uint32_t)method, b};
+            uint32_t o[4];
+            oracle_philox4x32(ctr, key, o);
+            x[2 * b] = (uint64_t)o[0] | ((uint64_t)o[1] << 32);
+            x[2 * b + 1] = (uint64_t)o[2] | ((uint64_t)o[3] << 32);
+        }
+        return;
+    }
     for (uint64_t i = 0; i < 16; i++) x[i] = oracle_splitmix(seed, (4 * s + (uint64_t)method) * 16 + i + 1);
 }
 
-/* Run samples s in [first, first+count) of one method: counts[0] collisions,
+/* the words x[0..15] of sample s of a method under a generator (for tests) */
+void oracle_words(int rng, int method, uint64_t seed, uint64_t s, uint64_t *x) { sample_words(rng, method, seed, s, x); }
+
+/* Run samples s in [first, first+count) of one method, words from generator
+ * rng (0 SplitMix64, 1 Philox4x32-10): counts[0] collisions,
  * counts[i] class i; for MOSS-4Min (method 3) counts[min_slot(class, c)]
  * instead.  classes/verts (nullable) receive per-sample records. */
-int oracle_run(const ctx *c, int method, uint64_t seed, uint64_t first, uint64_t count,
-               uint64_t *counts, uint8_t *classes, uint32_t *verts) {
+int oracle_run_rng(const ctx *c, int method, int rng, uint64_t seed, uint64_t first, uint64_t count,
+                   uint64_t *counts, uint8_t *classes, uint32_t *verts) {
     for (int i = 0; i < 22; i++) counts[i] = 0;
     if (!method_ok(c, method)) return -1;
     uint64_t x[16];
     uint32_t vv[5];
     for (uint64_t k = 0; k < count; k++) {
-        sample_words(method, seed, first + k, x);
+        sample_words(rng, method, seed, first + k, x);
         int cls;
         if (method == 3) {
             /* Algorithm 2: counts by (class, c(s)) slot */
@@ -526,6 +572,12 @@ int oracle_run(const ctx *c, int method, uint64_t seed, uint64_t first, uint64_t
         if (verts) memcpy(verts + 5 * k, vv, sizeof(vv));
     }
     return 0;
+}
+
+/* oracle_run_rng with SplitMix64 words */
+int oracle_run(const ctx *c, int method, uint64_t seed, uint64_t first, uint64_t count,
+               uint64_t *counts, uint8_t *classes, uint32_t *verts) {
+    return oracle_run_rng(c, method, 0, seed, first, count, counts, classes, verts);
 }
 
 /* --------------------------------------------------------- MOSS-4Min ---- */

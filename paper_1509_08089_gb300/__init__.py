@@ -26,6 +26,7 @@ MOSS_OK, MOSS_EINVAL, MOSS_ENOMEM, MOSS_ECUDA, MOSS_EGRAPH, MOSS_EOVERFLOW, MOSS
 MOSS_EBUSY = -7
 MOSS4, T5, PATH5, MOSS4MIN = 0, 1, 2, 3
 PROBE_SEARCH, PROBE_HASH, PROBE_FILTER, PROBE_AUTO = 0, 1, 2, 3
+RNG_SPLITMIX64, RNG_PHILOX4X32 = 0, 1
 NSLOTS = 22
 TABLES_4MIN = 1 << 6
 TABLE_VERT, TABLE_SLOT, TABLE_ACC, TABLE_SEED0, TABLE_GAMMA0 = 0, 1, 2, 3, 6
@@ -97,6 +98,8 @@ def load():
                                  ctypes.POINTER(_vp)], ctypes.c_int),
         "moss_build_tables": ([_vp, ctypes.c_uint, _vp], ctypes.c_int),
         "moss_set_probe": ([_vp, ctypes.c_int], ctypes.c_int),
+        "moss_set_rng": ([_vp, ctypes.c_int], ctypes.c_int),
+        "moss_get_rng": ([_vp], ctypes.c_int),
         "moss_sample_estimate": ([_vp, ctypes.c_int, _u64, _u64, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
         "moss_sample_counts": ([_vp, ctypes.c_int, _u64, _u64, _u64, _vp, _vp], ctypes.c_int),
         "moss_sample_records": ([_vp, ctypes.c_int, _u64, _u64, _u64, _vp, _vp, _vp], ctypes.c_int),
@@ -233,6 +236,14 @@ def moss_build_tables(g: int, k_mask: int = (1 << 4) | (1 << 5), stream=None):
 
 def moss_set_probe(g: int, strategy: int):
     _check(load().moss_set_probe(g, strategy))
+
+
+def moss_set_rng(g: int, rng: int):
+    _check(load().moss_set_rng(g, rng))
+
+
+def moss_get_rng(g: int) -> int:
+    return load().moss_get_rng(g)
 
 
 def moss_sample_estimate(g: int, k: int, budget: int, seed: int, stream=None) -> moss_result:
@@ -544,10 +555,11 @@ class Graph:
     """Owning wrapper: load, build, sample, free."""
 
     def __init__(self, row_ptr, col, device: int = 0, stream=None, k_mask: int = (1 << 4) | (1 << 5),
-                 probe: int = PROBE_AUTO):
+                 probe: int = PROBE_AUTO, rng: int = RNG_SPLITMIX64):
         self.handle = moss_graph_load_csr(row_ptr, col, device=device, stream=stream)
         self.device = device
         moss_set_probe(self.handle, probe)
+        moss_set_rng(self.handle, rng)
         self.k_mask = k_mask
         if k_mask:
             moss_build_tables(self.handle, k_mask, stream)
@@ -557,6 +569,10 @@ class Graph:
         moss_set_probe(self.handle, probe)
         if self.k_mask:
             moss_build_tables(self.handle, self.k_mask, stream)
+
+    def set_rng(self, rng: int):
+        """Word generator of later samples (RNG_SPLITMIX64 or RNG_PHILOX4X32)."""
+        moss_set_rng(self.handle, rng)
 
     def estimate(self, k: int, budget: int, seed: int, stream=None) -> dict:
         return result_dict(moss_sample_estimate(self.handle, k, budget, seed, stream))

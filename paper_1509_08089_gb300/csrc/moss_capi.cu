@@ -217,6 +217,7 @@ struct moss_graph {
     uint32_t *defer = nullptr;   // Path-5 deferral bitmap (kDeferChunk bits)
     void *arena = nullptr;       // every device array above lives in this one allocation
     int probe = MOSS_PROBE_AUTO; // membership tests (MOSS_PROBE_*), as requested
+    int rng = MOSS_RNG_SPLITMIX64;   // word generator of the samples (MOSS_RNG_*)
     unsigned long long *hash = nullptr;  // kBucketKeys keys per bucket
     uint64_t hash_buckets = 0;
     uint32_t *filter = nullptr;  // Bloom filter in front of the hash
@@ -272,6 +273,7 @@ DevGraph view_with(const moss_graph *g, int eff) {
     d.rlist = g->rlist;
     d.defer = g->defer;
     d.n = g->n;
+    d.rng = g->rng == MOSS_RNG_PHILOX4X32 ? kRngPhilox : kRngSplitMix;
     const bool use_hash = eff != MOSS_PROBE_SEARCH && (g->built >> 4 & 1u);
     const bool use_filter = eff == MOSS_PROBE_FILTER && (g->built >> 6 & 1u);
     d.hash = use_hash ? reinterpret_cast<const uint4 *>(g->hash) : nullptr;
@@ -642,6 +644,15 @@ int moss_set_probe(moss_graph *g, int strategy) {
     g->probe = strategy;
     return MOSS_OK;
 }
+
+int moss_set_rng(moss_graph *g, int rng) {
+    if (!g) return fail(MOSS_EINVAL, "graph is NULL");
+    if (rng != MOSS_RNG_SPLITMIX64 && rng != MOSS_RNG_PHILOX4X32) return fail(MOSS_EINVAL, "unknown generator %d", rng);
+    g->rng = rng;
+    return MOSS_OK;
+}
+
+int moss_get_rng(const moss_graph *g) { return g ? g->rng : MOSS_EINVAL; }
 
 static int sample_into(moss_graph *g, int method, uint64_t first, uint64_t count, uint64_t seed, cudaStream_t s,
                        uint64_t *counts_dev, uint8_t *classes, uint32_t *verts) {

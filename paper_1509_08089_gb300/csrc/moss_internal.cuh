@@ -96,6 +96,7 @@ struct DevGraph {
     uint32_t hash_shift;    // 64 - log2(buckets)
     uint32_t filter_shift;  // 64 - log2(filter words)
     uint32_t n;
+    uint32_t rng;           // word generator: kRngSplitMix or kRngPhilox
 };
 
 // ------------------------------------------------------- hashed edge set --
@@ -213,7 +214,7 @@ __device__ __forceinline__ u128 warp_sum128(u128 v) {
 // generator seeded with k: the state k advanced by that many Weyl increments,
 // through the generator's mixing function.  Every word is independent of the
 // others, so a sample computes only the words it reads.
-struct Words4 { uint64_t x[4]; };
+struct Words2 { uint64_t x[2]; };
 
 constexpr uint64_t kSplitMixGamma = 0x9E3779B97F4A7C15ULL;
 
@@ -223,12 +224,49 @@ __device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
     return z ^ (z >> 31);
 }
 
-// words 4 blk .. 4 blk + 3 of sample s of method t
-__device__ __forceinline__ Words4 sample_words4(uint64_t seed, uint32_t t, uint64_t s, uint32_t blk) {
-    const uint64_t base = seed + ((4 * s + t) * 16 + 4 * blk + 1) * kSplitMixGamma;
-    Words4 w;
+// --------------------------------------------------------- Philox4x32-10 --
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC 2011): ten rounds on a 128-bit counter (c0..c3) under
+// a 64-bit key (k0, k1).  A round forms the 64-bit products p = M0 c0 and
+// q = M1 c2 and makes the counter (hi q ^ c1 ^ k0, lo q, hi p ^ c3 ^ k1,
+// lo p); the key grows by the Weyl increments between rounds.  Words 2b and
+// 2b+1 of sample s of method t under seed k are the outputs of block
+// (s lo, s hi, t, b) under the key (k lo, k hi), low output first.
+constexpr int kRngSplitMix = 0, kRngPhilox = 1;
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) w.x[k] = splitmix_mix(base + (uint64_t)k * kSplitMixGamma);
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += kPhiloxW0;
+            k1 += kPhiloxW1;
+        }
+        const uint32_t p_hi = __umulhi(kPhiloxM0, c.x), p_lo = kPhiloxM0 * c.x;
+        const uint32_t q_hi = __umulhi(kPhiloxM1, c.z), q_lo = kPhiloxM1 * c.z;
+        c = make_uint4(q_hi ^ c.y ^ k0, q_lo, p_hi ^ c.w ^ k1, p_lo);
+    }
+    return c;
+}
+
+// words 2 p and 2 p + 1 of sample s of method t under generator RNG: one
+// Philox block, or two SplitMix64 outputs.  Samplers fetch each pair where
+// they first read it, which keeps the words' live ranges short (a word the
+// caller never reads is not computed: everything is inlined).
+template <int RNG>
+__device__ __forceinline__ Words2 sample_words2(uint64_t seed, uint32_t t, uint64_t s, uint32_t p) {
+    Words2 w;
+    if (RNG == kRngPhilox) {
+        const uint4 o = philox4x32_10(make_uint4((uint32_t)s, (uint32_t)(s >> 32), t, p), (uint32_t)seed,
+                                      (uint32_t)(seed >> 32));
+        w.x[0] = (uint64_t)o.x | ((uint64_t)o.y << 32);
+        w.x[1] = (uint64_t)o.z | ((uint64_t)o.w << 32);
+    } else {
+        const uint64_t base = seed + ((4 * s + t) * 16 + 2 * p + 1) * kSplitMixGamma;
+        w.x[0] = splitmix_mix(base);
+        w.x[1] = splitmix_mix(base + kSplitMixGamma);
+    }
     return w;
 }
 

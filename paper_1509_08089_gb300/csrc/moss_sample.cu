@@ -14,7 +14,8 @@
 // kernel adds the rows in a fixed order.  No global atomics.
 //
 // Word schedule (x_i = word i of the sample, output (4 s + method) 16 + i + 1
-// of SplitMix64 seeded with seed; sample_words4 in moss_internal.cuh):
+// of SplitMix64 seeded with seed, or Philox4x32-10 block i / 2; sample_words2
+// in moss_internal.cuh):
 //   MOSS-4 : x0,x1 vertex draw; x2,x3 sigma draw of u; x4 w; x5 r.
 //   T-5    : x0,x1 vertex draw; x2,x3 sigma of u; x4 w; x5 r; x6 t.
 //   MOSS-4Min: x0,x1 vertex draw (pi-check); x2,x3 sigma-check draw of u;
@@ -230,18 +231,19 @@ struct Sample {
     int cls;
 };
 
-template <bool HASH, bool HINT = false>
+template <int RNG, bool HASH, bool HINT = false>
 __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
-    const Words4 a = sample_words4(seed, 0, s, 0);
-    const Words4 b = sample_words4(seed, 0, s, 1);
-    const VertexPick pv = draw_vertex<HINT>(g.seed[0], g.vert, g.n, a.x[0], a.x[1]);
+    const Words2 x01 = sample_words2<RNG>(seed, 0, s, 0);
+    const VertexPick pv = draw_vertex<HINT>(g.seed[0], g.vert, g.n, x01.x[0], x01.x[1]);
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
-    const Pick pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, a.x[2], a.x[3]);
-    const uint32_t jw = skip1((uint32_t)word_index(b.x[0], vr.y - 1), pu.pos);
+    const Words2 x23 = sample_words2<RNG>(seed, 0, s, 1);
+    const Pick pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, x23.x[0], x23.x[1]);
+    const Words2 x45 = sample_words2<RNG>(seed, 0, s, 2);
+    const uint32_t jw = skip1((uint32_t)word_index(x45.x[0], vr.y - 1), pu.pos);
     const uint32_t w = ld1(g.col + vr.x + jw);
-    const uint32_t jr = skip1((uint32_t)word_index(b.x[1], pu.deg - 1), pu.twin);
+    const uint32_t jr = skip1((uint32_t)word_index(x45.x[1], pu.deg - 1), pu.twin);
     const uint32_t r = ld1(g.col + pu.off + jr);
     out.v[0] = v; out.v[1] = pu.id; out.v[2] = w; out.v[3] = r; out.v[4] = 0;
     if (r == pu.id || r == w) {
@@ -264,20 +266,22 @@ __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t 
     return out;
 }
 
-template <bool HASH, bool HINT = false>
+template <int RNG, bool HASH, bool HINT = false>
 __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
-    const Words4 a = sample_words4(seed, 1, s, 0);
-    const Words4 b = sample_words4(seed, 1, s, 1);
-    const VertexPick pv = draw_vertex<HINT>(g.seed[1], g.vert, g.n, a.x[0], a.x[1]);
+    const Words2 x01 = sample_words2<RNG>(seed, 1, s, 0);
+    const VertexPick pv = draw_vertex<HINT>(g.seed[1], g.vert, g.n, x01.x[0], x01.x[1]);
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
-    const Pick pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, a.x[2], a.x[3]);
-    const uint32_t jw = skip1((uint32_t)word_index(b.x[0], vr.y - 1), pu.pos);
-    const uint32_t jr = skip2((uint32_t)word_index(b.x[1], vr.y - 2), pu.pos, jw);
+    const Words2 x23 = sample_words2<RNG>(seed, 1, s, 1);
+    const Pick pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, x23.x[0], x23.x[1]);
+    const Words2 x45 = sample_words2<RNG>(seed, 1, s, 2);
+    const uint32_t jw = skip1((uint32_t)word_index(x45.x[0], vr.y - 1), pu.pos);
+    const uint32_t jr = skip2((uint32_t)word_index(x45.x[1], vr.y - 2), pu.pos, jw);
     const uint32_t w = ld1(g.col + vr.x + jw);
     const uint32_t r = ld1(g.col + vr.x + jr);
-    const uint32_t jt = skip1((uint32_t)word_index(b.x[2], pu.deg - 1), pu.twin);
+    const Words2 x67 = sample_words2<RNG>(seed, 1, s, 3);
+    const uint32_t jt = skip1((uint32_t)word_index(x67.x[0], pu.deg - 1), pu.twin);
     const uint32_t t = ld1(g.col + pu.off + jt);
     out.v[0] = v; out.v[1] = pu.id; out.v[2] = w; out.v[3] = r; out.v[4] = t;
     if (t == w || t == r) {
@@ -327,13 +331,12 @@ __device__ __forceinline__ int min_slot(int cls, uint32_t c) {
     return kSlots;
 }
 
-template <bool HASH, bool HINT = false>
+template <int RNG, bool HASH, bool HINT = false>
 __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *lut, const uint8_t *lutc, uint64_t seed,
                                              uint64_t s) {
     Sample out;
-    const Words4 a = sample_words4(seed, 3, s, 0);
-    const Words4 b = sample_words4(seed, 3, s, 1);
-    const VertexPick pv = draw_vertex<HINT>(g.seed[3], g.mvert, g.n, a.x[0], a.x[1]);
+    const Words2 x01 = sample_words2<RNG>(seed, 3, s, 0);
+    const VertexPick pv = draw_vertex<HINT>(g.seed[3], g.mvert, g.n, x01.x[0], x01.x[1]);
     const uint32_t v = pv.v;
     const uint4 mv = pv.rec;                           // {off, d_v, Gamma-check_v}
     const uint64_t Gv = ((uint64_t)mv.w << 32) | mv.z;
@@ -341,8 +344,9 @@ __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *l
     // Gamma-check_v < 2^32, one pick record carries the draw and both
     // possible picks; otherwise (or when a field overflows 16 bits) the slot
     // record, and the alias position's when the column does not keep the draw
-    const uint32_t j = (uint32_t)word_index(a.x[2], mv.y);
-    const uint64_t y = word_index(a.x[3], Gv);
+    const Words2 x23 = sample_words2<RNG>(seed, 3, s, 1);
+    const uint32_t j = (uint32_t)word_index(x23.x[0], mv.y);
+    const uint64_t y = word_index(x23.x[1], Gv);
     uint4 sb;   // {off_u, d_u, d_{v,u}, d_{u,v}}
     uint32_t u;
     Sector pk;
@@ -360,8 +364,9 @@ __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *l
         sb = ms.hi;
         u = ms.lo.w;
     }
-    const uint2 we = ld2(g.rlist + mv.x + (uint32_t)word_index(b.x[0], sb.z));   // w in N_{v,u}
-    const uint2 re = ld2(g.rlist + sb.x + (uint32_t)word_index(b.x[1], sb.w));   // r in N_{u,v}
+    const Words2 x45 = sample_words2<RNG>(seed, 3, s, 2);
+    const uint2 we = ld2(g.rlist + mv.x + (uint32_t)word_index(x45.x[0], sb.z));   // w in N_{v,u}
+    const uint2 re = ld2(g.rlist + sb.x + (uint32_t)word_index(x45.x[1], sb.w));   // r in N_{u,v}
     const uint32_t w = we.x, r = re.x;
     out.v[0] = v; out.v[1] = u; out.v[2] = w; out.v[3] = r; out.v[4] = 0;
     if (r == u || r == w) {
@@ -437,19 +442,20 @@ __device__ __noinline__ void path5_fallback(const uint32_t *acc, const uint64_t 
 // STAGE 3.
 constexpr int kDeferred = 254;
 
-template <bool HASH, int STAGE, bool HINT = false>
+template <int RNG, bool HASH, int STAGE, bool HINT = false>
 __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
-    const Words4 a = sample_words4(seed, 2, s, 0);
-    const VertexPick pv = draw_vertex<HINT>(g.seed[2], g.vert, g.n, a.x[0], a.x[1]);
+    const Words2 x01 = sample_words2<RNG>(seed, 2, s, 0);
+    const VertexPick pv = draw_vertex<HINT>(g.seed[2], g.vert, g.n, x01.x[0], x01.x[1]);
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
     Pick pu, pw;
     bool collide = true;
     if (STAGE == 0 || STAGE == 3) {
-        const Words4 b = sample_words4(seed, 2, s, 1);
-        pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, b.x[0], b.x[1]);
-        pw = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, b.x[2], b.x[3]);
+        const Words2 x45 = sample_words2<RNG>(seed, 2, s, 2);
+        const Words2 x67 = sample_words2<RNG>(seed, 2, s, 3);
+        pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, x45.x[0], x45.x[1]);
+        pw = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, x67.x[0], x67.x[1]);
         collide = pu.pos == pw.pos;
         if (STAGE == 0 && collide) {
             out.cls = kDeferred;
@@ -457,9 +463,10 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
         }
     }
     if (STAGE == 1 || (STAGE == 3 && collide)) {
-        const Words4 c = sample_words4(seed, 2, s, 2);
-        pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, c.x[0], c.x[1]);
-        pw = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, c.x[2], c.x[3]);
+        const Words2 x89 = sample_words2<RNG>(seed, 2, s, 4);
+        const Words2 x1011 = sample_words2<RNG>(seed, 2, s, 5);
+        pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, x89.x[0], x89.x[1]);
+        pw = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, x1011.x[0], x1011.x[1]);
         collide = pu.pos == pw.pos;
         if (STAGE == 1 && collide) {
             out.cls = kDeferred;
@@ -467,15 +474,16 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
         }
     }
     if (STAGE == 2 || (STAGE == 3 && collide)) {
-        const Words4 d4 = sample_words4(seed, 2, s, 3);
+        const Words2 x1213 = sample_words2<RNG>(seed, 2, s, 6);
         uint32_t iu, iw;
-        path5_fallback(g.acc, g.sq, v, vr, d4.x[0], d4.x[1], iu, iw);
+        path5_fallback(g.acc, g.sq, v, vr, x1213.x[0], x1213.x[1], iu, iw);
         pu = slot_pick(g.slot, g.vert, vr.x, iu);
         pw = slot_pick(g.slot, g.vert, vr.x, iw);
     }
     const uint32_t u = pu.id, w = pw.id;
-    const uint32_t r = ld1(g.col + pu.off + skip1((uint32_t)word_index(a.x[2], pu.deg - 1), pu.twin));
-    const uint32_t t = ld1(g.col + pw.off + skip1((uint32_t)word_index(a.x[3], pw.deg - 1), pw.twin));
+    const Words2 x23 = sample_words2<RNG>(seed, 2, s, 1);
+    const uint32_t r = ld1(g.col + pu.off + skip1((uint32_t)word_index(x23.x[0], pu.deg - 1), pu.twin));
+    const uint32_t t = ld1(g.col + pw.off + skip1((uint32_t)word_index(x23.x[1], pw.deg - 1), pw.twin));
     out.v[0] = v; out.v[1] = u; out.v[2] = w; out.v[3] = r; out.v[4] = t;
     if (t == u || r == w || t == r) {
         out.cls = 0;
@@ -509,13 +517,19 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
 // more than they hide (measured: 6 blocks of 256 threads for every main
 // sampler; Path-5 reaches it only with its second attempt and fallback
 // deferred).  The second-attempt launch runs 5 blocks, the fallback launch 4.
-template <int METHOD>
-constexpr int min_blocks() { return 6; }
+// Under Philox words the Path-5 and MOSS-4Min samplers and the redraw stages
+// hold the generator's state beside their records and would spill at those
+// register budgets, so they are compiled for one block fewer (4 for the
+// redraws); the grid of a main launch follows each instance's occupancy.
+template <int METHOD, int RNG>
+constexpr int min_blocks() { return RNG == kRngPhilox && (METHOD == 2 || METHOD == 3) ? 5 : 6; }
 template <int STAGE>
 constexpr int defer_min_blocks() { return STAGE == 1 ? 5 : 4; }
+template <int STAGE, int RNG>
+constexpr int defer_bound_blocks() { return RNG == kRngPhilox ? 4 : defer_min_blocks<STAGE>(); }
 
-template <int METHOD, bool RECORD, bool HASH, bool HINT = false>
-__global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGraph g, uint64_t first, uint64_t count, uint64_t seed,
+template <int METHOD, bool RECORD, bool HASH, bool HINT, int RNG>
+__global__ void __launch_bounds__(kThreads, min_blocks<METHOD, RNG>()) k_sample(DevGraph g, uint64_t first, uint64_t count, uint64_t seed,
                                                      uint64_t *partials, uint8_t *classes, uint32_t *verts) {
     __shared__ uint8_t lut[kLut];
     __shared__ uint8_t lutc[METHOD == 3 ? 4096 : 1];
@@ -538,10 +552,10 @@ __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGr
         if (i < count) {
             const uint64_t s = first + i;
             Sample sm;
-            if (METHOD == 0) sm = sample_moss4<HASH, HINT>(g, lut, seed, s);
-            else if (METHOD == 1) sm = sample_t5<HASH, HINT>(g, lut, seed, s);
-            else if (METHOD == 2) sm = sample_path5<HASH, 0, HINT>(g, lut, seed, s);
-            else sm = sample_min<HASH, HINT>(g, lut, lutc, seed, s);
+            if (METHOD == 0) sm = sample_moss4<RNG, HASH, HINT>(g, lut, seed, s);
+            else if (METHOD == 1) sm = sample_t5<RNG, HASH, HINT>(g, lut, seed, s);
+            else if (METHOD == 2) sm = sample_path5<RNG, HASH, 0, HINT>(g, lut, seed, s);
+            else sm = sample_min<RNG, HASH, HINT>(g, lut, lutc, seed, s);
             deferred = METHOD == 2 && sm.cls == kDeferred;
             if (!deferred) {
                 cls = METHOD == 3 ? min_slot(sm.cls, sm.v[4]) : sm.cls;
@@ -584,8 +598,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks<METHOD>()) k_sample(DevGr
 // launched with no more blocks than STAGE 1, adds into STAGE 1's rows.
 constexpr uint32_t kDeferList = 1024 + 32;   // a window's ids plus the carry-over
 
-template <bool RECORD, bool HASH, int STAGE, bool HINT = false>
-__global__ void __launch_bounds__(kThreads, defer_min_blocks<STAGE>())
+template <bool RECORD, bool HASH, int STAGE, bool HINT, int RNG>
+__global__ void __launch_bounds__(kThreads, defer_bound_blocks<STAGE, RNG>())
     k_sample_deferred(DevGraph g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
                       uint8_t *classes, uint32_t *verts) {
     static_assert(STAGE == 1 || STAGE == 2, "deferred stages are 1 and 2");
@@ -606,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, defer_min_blocks<STAGE>())
         uint64_t i = 0;
         if ((uint32_t)lane < cnt) {
             i = lst[k0 + lane];   // < count: only drawn ids are flagged
-            const Sample sm = sample_path5<HASH, STAGE, HINT>(g, lut, seed, first + i);
+            const Sample sm = sample_path5<RNG, HASH, STAGE, HINT>(g, lut, seed, first + i);
             again = STAGE == 1 && sm.cls == kDeferred;
             if (!again) {
                 cls = sm.cls;
@@ -690,16 +704,16 @@ constexpr int kBatchBlocks = 4;   // resident blocks per SM (Path-5 bound)
 
 // the count slot of sample s of a method: its class, or for MOSS-4Min its
 // (class, c) slot
-template <bool HASH>
+template <bool HASH, int RNG>
 __device__ __forceinline__ int sample_any(const DevGraph &g, const uint8_t *lut4, const uint8_t *lut5,
                                           const uint8_t *lutc, uint32_t method, uint64_t seed, uint64_t s) {
-    if (method == 0) return sample_moss4<HASH>(g, lut4, seed, s).cls;
-    if (method == 1) return sample_t5<HASH>(g, lut5, seed, s).cls;
+    if (method == 0) return sample_moss4<RNG, HASH>(g, lut4, seed, s).cls;
+    if (method == 1) return sample_t5<RNG, HASH>(g, lut5, seed, s).cls;
     if (method == 3) {
-        const Sample sm = sample_min<HASH>(g, lut4, lutc, seed, s);
+        const Sample sm = sample_min<RNG, HASH>(g, lut4, lutc, seed, s);
         return min_slot(sm.cls, sm.v[4]);
     }
-    return sample_path5<HASH, 3>(g, lut5, seed, s).cls;
+    return sample_path5<RNG, HASH, 3>(g, lut5, seed, s).cls;
 }
 
 // Persistent sampler over a batch: warps take tiles of `tile_samples` ids of
@@ -746,12 +760,18 @@ __global__ void __launch_bounds__(THREADS, kBatchBlocks * kThreads / THREADS)
         const uint64_t left = tk.first + tk.count - f;
         const uint32_t cnt = (uint32_t)(left < tile_samples ? left : tile_samples);
         const bool hashed = g.hash != nullptr;
+        const bool philox = g.rng == kRngPhilox;   // warp-uniform: a tile belongs to one graph
         for (uint32_t base = 0; base < cnt; base += 32) {
             const uint32_t i = base + lane;
             int cls = kSlots;
-            if (i < cnt)
-                cls = hashed ? sample_any<true>(g, lut4, lut5, lutc, tk.method, tk.seed, f + i)
-                             : sample_any<false>(g, lut4, lut5, lutc, tk.method, tk.seed, f + i);
+            if (i < cnt) {
+                if (philox)
+                    cls = hashed ? sample_any<true, kRngPhilox>(g, lut4, lut5, lutc, tk.method, tk.seed, f + i)
+                                 : sample_any<false, kRngPhilox>(g, lut4, lut5, lutc, tk.method, tk.seed, f + i);
+                else
+                    cls = hashed ? sample_any<true, kRngSplitMix>(g, lut4, lut5, lutc, tk.method, tk.seed, f + i)
+                                 : sample_any<false, kRngSplitMix>(g, lut4, lut5, lutc, tk.method, tk.seed, f + i);
+            }
             const uint32_t peers = __match_any_sync(0xffffffffu, cls);
             if (cls < kSlots && lane == __ffs(peers) - 1) atomicAdd(&hist[warp][cls], (uint32_t)__popc(peers));
         }
@@ -793,16 +813,24 @@ __global__ void k_reduce(const uint64_t *partials, int blocks, uint64_t *out, in
     }
 }
 
+template <int M, bool R, int RNG>
+cudaError_t launch_one_rng(const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
+                           int blocks, uint8_t *classes, uint32_t *verts, cudaStream_t s) {
+    if (g.hash && g.filter)
+        k_sample<M, R, true, true, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    else if (g.hash)
+        k_sample<M, R, true, false, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    else
+        k_sample<M, R, false, false, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    return cudaGetLastError();
+}
+
 template <int M, bool R>
 cudaError_t launch_one(const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
                        int blocks, uint8_t *classes, uint32_t *verts, cudaStream_t s) {
-    if (g.hash && g.filter)
-        k_sample<M, R, true, true><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-    else if (g.hash)
-        k_sample<M, R, true><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-    else
-        k_sample<M, R, false><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-    return cudaGetLastError();
+    if (g.rng == kRngPhilox)
+        return launch_one_rng<M, R, kRngPhilox>(g, first, count, seed, partials, blocks, classes, verts, s);
+    return launch_one_rng<M, R, kRngSplitMix>(g, first, count, seed, partials, blocks, classes, verts, s);
 }
 
 }  // namespace
@@ -813,17 +841,26 @@ void upload_luts(const uint8_t *lut4, const uint8_t *lut5, const uint8_t *lutc) 
     cudaMemcpyToSymbol(g_lutc, lutc, 4096);
 }
 
-// resident blocks per SM of each sampler variant (0 search, 1 hash, 2
-// filter) on each device, 0 until queried
-std::atomic<int> g_sample_per_sm[64][kMethods][3];
+// resident blocks per SM of each sampler variant (probe 0 search, 1 hash, 2
+// filter; + 3 under Philox words) on each device, 0 until queried
+constexpr int kVariants = 6;
+std::atomic<int> g_sample_per_sm[64][kMethods][kVariants];
+
+template <int M, int RNG>
+cudaError_t occupancy3(int *per) {
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], k_sample<M, false, false, false, RNG>, kThreads, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], k_sample<M, false, true, false, RNG>, kThreads, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[2], k_sample<M, false, true, true, RNG>, kThreads, 0);
+    return e;
+}
 
 template <int M>
-cudaError_t occupancy3(int (&per)[3]) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], k_sample<M, false, false>, kThreads, 0);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], k_sample<M, false, true>, kThreads, 0);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[2], k_sample<M, false, true, true>, kThreads, 0);
+cudaError_t occupancy6(int (&per)[kVariants]) {
+    cudaError_t e = occupancy3<M, kRngSplitMix>(per);
+    if (e == cudaSuccess) e = occupancy3<M, kRngPhilox>(per + 3);
     return e;
 }
 
@@ -834,13 +871,13 @@ int sample_per_sm(int method, int device, int variant) {
         const int c = g_sample_per_sm[device][method][variant].load(std::memory_order_relaxed);
         if (c > 0) return c;
     }
-    int per[3] = {1, 1, 1};
+    int per[kVariants] = {1, 1, 1, 1, 1, 1};
     cudaError_t e;
-    if (method == 0) e = occupancy3<0>(per);
-    else if (method == 1) e = occupancy3<1>(per);
-    else if (method == 2) e = occupancy3<2>(per);
-    else e = occupancy3<3>(per);
-    for (int v = 0; v < 3; ++v) {
+    if (method == 0) e = occupancy6<0>(per);
+    else if (method == 1) e = occupancy6<1>(per);
+    else if (method == 2) e = occupancy6<2>(per);
+    else e = occupancy6<3>(per);
+    for (int v = 0; v < kVariants; ++v) {
         if (e != cudaSuccess || per[v] < 1) per[v] = 1;
         if (cached && e == cudaSuccess) g_sample_per_sm[device][method][v].store(per[v], std::memory_order_relaxed);
     }
@@ -849,12 +886,13 @@ int sample_per_sm(int method, int device, int variant) {
 
 int sample_blocks(int method, int device) {
     int per = 1;
-    for (int v = 0; v < 3; ++v) per = std::max(per, sample_per_sm(method, device, v));
+    for (int v = 0; v < kVariants; ++v) per = std::max(per, sample_per_sm(method, device, v));
     return device_sms(device) * per;   // the most any variant launches
 }
 
 int sample_launch_blocks(int method, int device, const DevGraph &g) {
-    return device_sms(device) * sample_per_sm(method, device, g.hash ? (g.filter ? 2 : 1) : 0);
+    return device_sms(device) *
+           sample_per_sm(method, device, (g.hash ? (g.filter ? 2 : 1) : 0) + (g.rng == kRngPhilox ? 3 : 0));
 }
 
 namespace {
@@ -875,21 +913,29 @@ cudaError_t launch_sample(int method, const DevGraph &g, uint64_t first, uint64_
     }
 }
 
+template <int STAGE, int RNG>
+cudaError_t launch_deferred_rng(const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
+                                int blocks, uint8_t *classes, uint32_t *verts, cudaStream_t s) {
+    const bool rec = classes != nullptr;
+    if (g.hash && g.filter) {
+        if (rec) k_sample_deferred<true, true, STAGE, true, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+        else k_sample_deferred<false, true, STAGE, true, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    } else if (g.hash) {
+        if (rec) k_sample_deferred<true, true, STAGE, false, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+        else k_sample_deferred<false, true, STAGE, false, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    } else {
+        if (rec) k_sample_deferred<true, false, STAGE, false, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+        else k_sample_deferred<false, false, STAGE, false, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    }
+    return cudaGetLastError();
+}
+
 template <int STAGE>
 cudaError_t launch_deferred(const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
                             int blocks, uint8_t *classes, uint32_t *verts, cudaStream_t s) {
-    const bool rec = classes != nullptr;
-    if (g.hash && g.filter) {
-        if (rec) k_sample_deferred<true, true, STAGE, true><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-        else k_sample_deferred<false, true, STAGE, true><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-    } else if (g.hash) {
-        if (rec) k_sample_deferred<true, true, STAGE><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-        else k_sample_deferred<false, true, STAGE><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-    } else {
-        if (rec) k_sample_deferred<true, false, STAGE><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-        else k_sample_deferred<false, false, STAGE><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-    }
-    return cudaGetLastError();
+    if (g.rng == kRngPhilox)
+        return launch_deferred_rng<STAGE, kRngPhilox>(g, first, count, seed, partials, blocks, classes, verts, s);
+    return launch_deferred_rng<STAGE, kRngSplitMix>(g, first, count, seed, partials, blocks, classes, verts, s);
 }
 
 // blocks of a deferred stage: its resident blocks per SM times the SMs

@@ -148,7 +148,8 @@ def expected_slot_neighbour(rp: np.ndarray, col: np.ndarray, twin: np.ndarray):
     return nb.astype(np.uint32), off.astype(np.uint32)
 
 
-def oracle_counts(og, method: int, seed: int, first: int, count: int, threads: int | None = None) -> np.ndarray:
+def oracle_counts(og, method: int, seed: int, first: int, count: int, threads: int | None = None,
+                  rng: int = 0) -> np.ndarray:
     """The oracle's counts of samples [first, first + count) of one method,
     split into id chunks run on all host cores.  The oracle's sampler only
     reads its tables and ctypes releases the GIL around it, so threads share
@@ -161,7 +162,7 @@ def oracle_counts(og, method: int, seed: int, first: int, count: int, threads: i
     if not parts:
         return total
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        for c in ex.map(lambda p: og.run(method, seed, p[1], first=p[0]), parts):
+        for c in ex.map(lambda p: og.run(method, seed, p[1], first=p[0], rng=rng), parts):
             total += c
     return total
 

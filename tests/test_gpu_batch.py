@@ -107,6 +107,34 @@ def test_batch_against_oracle(fleet):
     assert res[3]["est"][1] == pytest.approx(9.0)   # cycle C_9: eta_1 = 9 exactly
 
 
+def test_batch_mixes_generators():
+    """Graphs drawing Philox words and graphs drawing SplitMix64 words in one
+    launch: each request equals its solo run and the oracle's counts under
+    its graph's generator."""
+    csrs = uneven_graphs(4, 8)
+    rngs = [moss.RNG_PHILOX4X32, moss.RNG_SPLITMIX64, moss.RNG_PHILOX4X32, moss.RNG_SPLITMIX64]
+    graphs = [moss.Graph(rp, col, rng=r) for (rp, col), r in zip(csrs, rngs)]
+    try:
+        picks = [(i, k, 30_011 + 1000 * i, 70 + i) for i in range(4) for k in (4, 5)]
+        with moss.Batch() as batch:
+            for gi, k, budget, seed in picks:
+                batch.add(graphs[gi], k, budget, seed)
+            res = batch.run()
+        for (gi, k, budget, seed), r in zip(picks, res):
+            same(r, graphs[gi].estimate(k, budget, seed))
+            og = oracle.OracleGraph(*csrs[gi])
+            orng = oracle.PHILOX4X32 if rngs[gi] == moss.RNG_PHILOX4X32 else oracle.SPLITMIX64
+            if k == 4:
+                assert np.array_equal(r["hits"][0], og.run(oracle.MOSS4, seed, budget, rng=orng))
+            else:
+                K1, K2 = budget // 2, budget - budget // 2
+                assert np.array_equal(r["hits"][0], og.run(oracle.T5, seed, K1, rng=orng))
+                assert np.array_equal(r["hits"][1], og.run(oracle.PATH5, seed, K2, rng=orng))
+    finally:
+        for g in graphs:
+            g.close()
+
+
 def test_batch_min_requests_equal_solo_runs():
     """MOSS-4 + MOSS-4Min requests, mixed with plain k = 4 and 5 requests in
     one batch, equal moss_sample_estimate_min (and the oracle's counts)."""

@@ -155,22 +155,31 @@ def test_min_tables_bit_exact(name):
     assert np.array_equal(pk[f, 6], dd[apos][f])
 
 
+RNGS = [("splitmix64", moss.RNG_SPLITMIX64, oracle.SPLITMIX64), ("philox4x32", moss.RNG_PHILOX4X32, oracle.PHILOX4X32)]
+
+
+@pytest.mark.parametrize("rng", RNGS, ids=lambda r: r[0])
 @pytest.mark.parametrize("name", list(GRAPHS))
-def test_min_records_bit_exact(name):
+def test_min_records_bit_exact(name, rng):
+    _, lib_rng, orc_rng = rng
     rp, col, og, g = pair(name)
     if og.Gamma_min == 0:
         pytest.skip("no admissible tuple")
     first, count = (12_345, 100_003) if name != "cl_n100k" else (49_990_000, 20_011)
     seed = 0xBEEF
-    ocnt, ocls, overts = og.run(oracle.MOSS4MIN, seed, count, first=first, record=True)
-    for probe in (moss.PROBE_SEARCH, moss.PROBE_HASH, moss.PROBE_FILTER):
-        g.set_probe(probe)
-        cls, verts = gpu_records(g, first, count, seed)
-        bad = np.nonzero(ocls != cls)[0]
-        assert bad.size == 0, (probe, bad[:5], ocls[bad[:5]], cls[bad[:5]], overts[bad[:3]], verts[bad[:3]])
-        assert np.array_equal(verts, overts), probe
-        assert np.array_equal(gpu_counts(g, first, count, seed), ocnt), probe
-    g.set_probe(moss.PROBE_AUTO)
+    ocnt, ocls, overts = og.run(oracle.MOSS4MIN, seed, count, first=first, record=True, rng=orc_rng)
+    g.set_rng(lib_rng)
+    try:
+        for probe in (moss.PROBE_SEARCH, moss.PROBE_HASH, moss.PROBE_FILTER):
+            g.set_probe(probe)
+            cls, verts = gpu_records(g, first, count, seed)
+            bad = np.nonzero(ocls != cls)[0]
+            assert bad.size == 0, (probe, bad[:5], ocls[bad[:5]], cls[bad[:5]], overts[bad[:3]], verts[bad[:3]])
+            assert np.array_equal(verts, overts), probe
+            assert np.array_equal(gpu_counts(g, first, count, seed), ocnt), probe
+    finally:
+        g.set_rng(moss.RNG_SPLITMIX64)
+        g.set_probe(moss.PROBE_AUTO)
     if name == "diamond":
         hit = [i for i in range(count) if set(overts[i, :4]) == {0, 1, 2, 3}]
         assert hit and all(overts[i, 4] == 3 for i in hit)
@@ -199,21 +208,27 @@ def close(r, o, og):
     assert abs(r["triangles"] - o["triangles"]) <= 1e-9 * max(abs(o["triangles"]), 1e-300)
 
 
+@pytest.mark.parametrize("rng", RNGS, ids=lambda r: r[0])
 @pytest.mark.parametrize("name", ["gnp12", "diamond", "cl_n200", "rgg2k", "cl_n2k", "hub12k"])
-def test_estimate_min_matches_oracle(name):
+def test_estimate_min_matches_oracle(name, rng):
+    _, lib_rng, orc_rng = rng
     rp, col, og, g = pair(name)
     K, Km, seed = 200_001, 150_003, 77
-    for probe in (moss.PROBE_SEARCH, moss.PROBE_HASH, moss.PROBE_FILTER):
-        g.set_probe(probe)
-        r = g.estimate_min(K, Km, seed)
-        o = og.estimate_min(K, Km, seed)
-        assert tuple(r["K"]) == tuple(o["K"])
-        ref4 = og.run(oracle.MOSS4, seed, K) if og.Gamma[0] else np.zeros(22, np.uint64)
-        refm = og.run(oracle.MOSS4MIN, seed, Km) if og.Gamma_min else np.zeros(22, np.uint64)
-        assert np.array_equal(r["hits"][0], ref4)
-        assert np.array_equal(r["hits"][1], refm)
-        close(r, o, og)
-    g.set_probe(moss.PROBE_AUTO)
+    g.set_rng(lib_rng)
+    try:
+        for probe in (moss.PROBE_SEARCH, moss.PROBE_HASH, moss.PROBE_FILTER):
+            g.set_probe(probe)
+            r = g.estimate_min(K, Km, seed)
+            o = og.estimate_min(K, Km, seed, rng=orc_rng)
+            assert tuple(r["K"]) == tuple(o["K"])
+            ref4 = og.run(oracle.MOSS4, seed, K, rng=orc_rng) if og.Gamma[0] else np.zeros(22, np.uint64)
+            refm = og.run(oracle.MOSS4MIN, seed, Km, rng=orc_rng) if og.Gamma_min else np.zeros(22, np.uint64)
+            assert np.array_equal(r["hits"][0], ref4)
+            assert np.array_equal(r["hits"][1], refm)
+            close(r, o, og)
+    finally:
+        g.set_rng(moss.RNG_SPLITMIX64)
+        g.set_probe(moss.PROBE_AUTO)
 
 
 def test_finalize_min_and_covariance():

@@ -175,46 +175,76 @@ def test_edge_filter_bits(name):
     g.set_probe(moss.PROBE_AUTO)
 
 
+RNGS = [("splitmix64", moss.RNG_SPLITMIX64, oracle.SPLITMIX64), ("philox4x32", moss.RNG_PHILOX4X32, oracle.PHILOX4X32)]
+
+
+@pytest.mark.parametrize("rng", RNGS, ids=lambda r: r[0])
 @pytest.mark.parametrize("name", ["gnp12", "cl_n200", "rgg2k", "cl_n2k", "cl_n100k", "hub70k", "circ8", "circ9"])
 @pytest.mark.parametrize("method", [0, 1, 2])
-def test_records_bit_exact(name, method):
+def test_records_bit_exact(name, method, rng):
+    _, lib_rng, orc_rng = rng
     rp, col, og, g = pair(name)
     if og.Gamma[method] == 0:
         pytest.skip("method has no sample on this graph")
     first, count = (12_345, 100_003) if name != "cl_n100k" else (49_990_000, 20_011)
     seed = 0xC0FFEE + method
-    ocnt, ocls, overts = og.run(method, seed, count, first=first, record=True)
+    ocnt, ocls, overts = og.run(method, seed, count, first=first, record=True, rng=orc_rng)
     ncol = 4 if method == 0 else 5
-    for probe in (moss.PROBE_SEARCH, moss.PROBE_HASH, moss.PROBE_FILTER):
-        g.set_probe(probe)
-        cls, verts = gpu_records(g, method, first, count, seed)
-        bad = np.nonzero(ocls != cls)[0]
-        assert bad.size == 0, (probe, bad[:5], ocls[bad[:5]], cls[bad[:5]], overts[bad[:3]], verts[bad[:3]])
-        assert np.array_equal(verts[:, :ncol], overts[:, :ncol])
-    g.set_probe(moss.PROBE_AUTO)
+    g.set_rng(lib_rng)
+    try:
+        for probe in (moss.PROBE_SEARCH, moss.PROBE_HASH, moss.PROBE_FILTER):
+            g.set_probe(probe)
+            cls, verts = gpu_records(g, method, first, count, seed)
+            bad = np.nonzero(ocls != cls)[0]
+            assert bad.size == 0, (probe, bad[:5], ocls[bad[:5]], cls[bad[:5]], overts[bad[:3]], verts[bad[:3]])
+            assert np.array_equal(verts[:, :ncol], overts[:, :ncol])
+            assert np.array_equal(gpu_counts(g, method, first, count, seed), ocnt), probe
+    finally:
+        g.set_rng(moss.RNG_SPLITMIX64)
+        g.set_probe(moss.PROBE_AUTO)
 
 
+@pytest.mark.parametrize("rng", RNGS, ids=lambda r: r[0])
 @pytest.mark.parametrize("name", ["gnp12", "cl_n200", "rgg2k", "cl_n2k", "hub70k", "circ8"])
-def test_counts_and_estimates(name):
+def test_counts_and_estimates(name, rng):
+    _, lib_rng, orc_rng = rng
     rp, col, og, g = pair(name)
     budget, seed = 200_001, 99
-    for k, probe in ((4, moss.PROBE_SEARCH), (4, moss.PROBE_HASH), (4, moss.PROBE_FILTER),
-                     (5, moss.PROBE_SEARCH), (5, moss.PROBE_HASH), (5, moss.PROBE_FILTER)):
-        g.set_probe(probe)
-        r = g.estimate(k, budget, seed)
-        o = og.estimate(k, budget, seed)
-        if k == 4:
-            ref = og.run(oracle.MOSS4, seed, budget) if og.Gamma[0] else np.zeros(22, np.uint64)
-            assert np.array_equal(r["hits"][0], ref)
-        else:
-            K1, K2 = budget // 2, budget - budget // 2
-            ref1 = og.run(oracle.T5, seed, K1) if og.Gamma[1] else np.zeros(22, np.uint64)
-            ref2 = og.run(oracle.PATH5, seed, K2) if og.Gamma[2] else np.zeros(22, np.uint64)
-            assert np.array_equal(r["hits"][0], ref1)
-            assert np.array_equal(r["hits"][1], ref2)
-        assert tuple(r["K"]) == tuple(o["K"])
-        close_estimates(r, o, og, k)
-    g.set_probe(moss.PROBE_AUTO)
+    g.set_rng(lib_rng)
+    try:
+        for k, probe in ((4, moss.PROBE_SEARCH), (4, moss.PROBE_HASH), (4, moss.PROBE_FILTER),
+                         (5, moss.PROBE_SEARCH), (5, moss.PROBE_HASH), (5, moss.PROBE_FILTER)):
+            g.set_probe(probe)
+            r = g.estimate(k, budget, seed)
+            o = og.estimate(k, budget, seed, rng=orc_rng)
+            if k == 4:
+                ref = og.run(oracle.MOSS4, seed, budget, rng=orc_rng) if og.Gamma[0] else np.zeros(22, np.uint64)
+                assert np.array_equal(r["hits"][0], ref)
+            else:
+                K1, K2 = budget // 2, budget - budget // 2
+                ref1 = og.run(oracle.T5, seed, K1, rng=orc_rng) if og.Gamma[1] else np.zeros(22, np.uint64)
+                ref2 = og.run(oracle.PATH5, seed, K2, rng=orc_rng) if og.Gamma[2] else np.zeros(22, np.uint64)
+                assert np.array_equal(r["hits"][0], ref1)
+                assert np.array_equal(r["hits"][1], ref2)
+            assert tuple(r["K"]) == tuple(o["K"])
+            close_estimates(r, o, og, k)
+    finally:
+        g.set_rng(moss.RNG_SPLITMIX64)
+        g.set_probe(moss.PROBE_AUTO)
+
+
+def test_generator_setting():
+    rp, col, og, g = pair("cl_n200")
+    assert moss.moss_get_rng(g.handle) == moss.RNG_SPLITMIX64
+    with pytest.raises(moss.MossError) as ei:
+        moss.moss_set_rng(g.handle, 2)
+    assert ei.value.status == moss.MOSS_EINVAL
+    g.set_rng(moss.RNG_PHILOX4X32)
+    assert moss.moss_get_rng(g.handle) == moss.RNG_PHILOX4X32
+    a = g.estimate(5, 50_000, 3)
+    g.set_rng(moss.RNG_SPLITMIX64)
+    b = g.estimate(5, 50_000, 3)
+    assert not np.array_equal(a["hits"], b["hits"])     # other words, other samples
 
 
 @pytest.mark.parametrize("k", [4, 5])
@@ -325,6 +355,14 @@ def test_full_size_bench_config():
         _, ocls, overts = og.run(method, 42, 5000, first=K - 5000, record=True)
         assert np.array_equal(cls, ocls)
         assert np.array_equal(verts, overts)
+    # under Philox words: the full launch's counts against the oracle's too
+    g.set_rng(moss.RNG_PHILOX4X32)
+    try:
+        rp_ = g.estimate(5, B, seed=42)
+    finally:
+        g.set_rng(moss.RNG_SPLITMIX64)
+    for slot, (method, K) in enumerate(((1, K1), (2, K2))):
+        assert np.array_equal(rp_["hits"][slot], oracle_counts(og, method, 42, 0, K, rng=oracle.PHILOX4X32))
     # an independent seed agrees within the stated variances
     r2 = g.estimate(5, B, seed=43)
     for i in range(1, 22):

@@ -139,12 +139,13 @@ def test_server_rejects_bad_requests(pool):
 def test_served_results_match_oracle(pool_csrs):
     """Served results -- k = 4 and k = 5 with fixed budgets, k = 4 and k = 5
     with target errors (budget from the pilot), and a MOSS-4 + MOSS-4Min
-    request -- each against the oracle's whole path with the request's final
-    budget and seed: counts bit for bit, estimates within 1e-9."""
+    request on a graph drawing Philox words -- each against the oracle's
+    whole path with the request's final budget and seed: counts bit for bit,
+    estimates within 1e-9."""
     csrs, graphs = pool_csrs
     mask = (1 << 4) | (1 << 5) | moss.TABLES_4MIN
     rp_m, col_m = synth.chung_lu(2500, 2.3, 8.0, 60.0, seed=7)
-    gmin = moss.Graph(rp_m, col_m, k_mask=mask)
+    gmin = moss.Graph(rp_m, col_m, k_mask=mask, rng=moss.RNG_PHILOX4X32)    # served under Philox words
     try:
         with moss.Server(max_active=16, tick_samples=400_000, tile_samples=2048, min_budget=10_000,
                          max_budget=3_000_000, pilot_samples=20_000) as server:
@@ -169,9 +170,9 @@ def test_served_results_match_oracle(pool_csrs):
                 assert np.array_equal(r["hits"][slot], ref), (gi, k, slot)
             close_estimates(r, o, og, k)
         og = oracle.OracleGraph(rp_m, col_m)
-        o = og.estimate_min(300_000, 200_000, 16)
-        assert np.array_equal(r_m["hits"][0], og.run(oracle.MOSS4, 16, 300_000))
-        assert np.array_equal(r_m["hits"][1], og.run(oracle.MOSS4MIN, 16, 200_000))
+        o = og.estimate_min(300_000, 200_000, 16, rng=oracle.PHILOX4X32)
+        assert np.array_equal(r_m["hits"][0], og.run(oracle.MOSS4, 16, 300_000, rng=oracle.PHILOX4X32))
+        assert np.array_equal(r_m["hits"][1], og.run(oracle.MOSS4MIN, 16, 200_000, rng=oracle.PHILOX4X32))
         for i in range(1, 7):
             tol = 1e-9 * (max(float(og.Lambda3), 1.0) if i == 2 else max(abs(o["est"][i]), 1e-300))
             assert abs(r_m["est"][i] - o["est"][i]) <= tol, i

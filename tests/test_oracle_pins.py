@@ -2,6 +2,9 @@
 
 * SplitMix64 against its published reference outputs (tests/golden), and the
   word schedule against the generator's sequence.
+* Philox4x32-10 against an independent implementation (Triton's, run by its
+  CPU interpreter in a child process) on fixed and random counters and keys,
+  and its word schedule against the block layout it defines.
 * Alias tables: exact integer mass identity (each item gets w_j / W).
 * Vertex weights Gamma, Gamma^(1), Gamma^(2), Lambda_3, Lambda_4 against
   brute-force counts of the draw sequences / subgraphs they stand for
@@ -23,6 +26,101 @@ import synth
 from helpers import adjacency_sets, brute_force_cis, class_counts, mask_classes, phi4, table2
 
 TWO64 = 1 << 64
+
+
+# ------------------------------------------------------------ Philox4x32 --
+_TRITON_PHILOX = r"""
+import json, sys
+import numpy as np
+import torch, triton, triton.language as tl
+
+@triton.jit
+def k(seed_ptr, c_ptr, out_ptr, N: tl.constexpr):
+    i = tl.arange(0, N)
+    seed = tl.load(seed_ptr + i)
+    a, b, c, d = tl.philox(seed, tl.load(c_ptr + 4 * i), tl.load(c_ptr + 4 * i + 1), tl.load(c_ptr + 4 * i + 2),
+                           tl.load(c_ptr + 4 * i + 3), n_rounds=10)
+    tl.store(out_ptr + 4 * i, a)
+    tl.store(out_ptr + 4 * i + 1, b)
+    tl.store(out_ptr + 4 * i + 2, c)
+    tl.store(out_ptr + 4 * i + 3, d)
+
+cases = json.load(sys.stdin)
+n = len(cases)
+seed = torch.tensor(np.array([kk[0] | (kk[1] << 32) for _, kk in cases], dtype=np.uint64))
+ctr = torch.tensor(np.array([x for c, _ in cases for x in c], dtype=np.uint32))
+out = torch.zeros(4 * n, dtype=torch.uint32)
+k[(1,)](seed, ctr, out, N=n)
+print(json.dumps([int(x) for x in out.numpy().view(np.uint32)]))
+"""
+
+
+def test_philox_matches_an_independent_implementation():
+    """The oracle's Philox4x32-10 against triton.language.philox (10 rounds,
+    key = the seed's low and high halves), evaluated on the CPU by Triton's
+    interpreter in a child process."""
+    import json
+    import subprocess
+    import sys
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(2024)
+    cases = [([0, 0, 0, 0], [0, 0]), ([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2), ([1, 0, 0, 0], [0, 0]),
+             ([0, 0, 0, 1], [0, 1])]
+    cases += [([int(x) for x in rng.integers(0, 2**32, 4)], [int(x) for x in rng.integers(0, 2**32, 2)])
+              for _ in range(60)]          # 64 lanes: a power of two for tl.arange
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    r = subprocess.run([sys.executable, "-c", _TRITON_PHILOX], input=json.dumps(cases), capture_output=True,
+                       text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    ref = json.loads(r.stdout.strip().splitlines()[-1])
+    got = [x for c, kk in cases for x in oracle.philox4x32(c, kk)]
+    assert got == ref
+
+
+def test_philox_word_schedule_is_the_block_layout():
+    """Words 2b and 2b+1 of sample s of method t are block (s lo, s hi, t, b)
+    under the key (seed lo, seed hi), low output first."""
+    seed, s, t = 0x0123456789ABCDEF, (7 << 32) + 99, 2
+    w = oracle.sample_words(t, seed, s, 16, rng=oracle.PHILOX4X32)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for b in range(8):
+        o = oracle.philox4x32([s & 0xFFFFFFFF, s >> 32, t, b], key)
+        assert w[2 * b] == o[0] | (o[1] << 32)
+        assert w[2 * b + 1] == o[2] | (o[3] << 32)
+    # different methods and samples never share a block
+    assert oracle.sample_words(1, seed, s, 2, rng=oracle.PHILOX4X32) != w[:2]
+    assert oracle.sample_words(t, seed, s + 1, 2, rng=oracle.PHILOX4X32) != w[:2]
+
+
+def test_philox_words_are_uniform():
+    """Chi-square of the top four bits of 2^15 words (16 cells)."""
+    counts = np.zeros(16)
+    for s in range(2048):
+        for x in oracle.sample_words(0, 77, s, 16, rng=oracle.PHILOX4X32):
+            counts[x >> 60] += 1
+    e = counts.sum() / 16
+    chi2 = float(((counts - e) ** 2 / e).sum())
+    assert chi2 < 45.0          # chi^2_15 exceeds 45 with probability < 1e-4
+
+
+def test_philox_drives_the_samplers_unbiasedly():
+    """Estimates under Philox words: the mean over 120 seeds is within 4.5
+    sigma / sqrt(R) of the exact ESU counts (Theorems 3 and 10)."""
+    import json
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "esu_counts.json")))
+    rp, col = synth.chung_lu(200, 2.3, 6.0, 30.0, seed=7)
+    g = oracle.OracleGraph(rp, col)
+    R = 120
+    for k, key, budget in ((4, "esu4", 20_000), (5, "esu5", 20_000)):
+        eta = np.array(gold["cl_n200"][key], dtype=np.float64)
+        ref = g.estimate(k, budget, seed=0, eta=eta)
+        est = np.array([g.estimate(k, budget, seed=900 + s, rng=oracle.PHILOX4X32)["est"] for s in range(R)])
+        for i in range(1, 7 if k == 4 else 22):
+            if i == 2 or eta[i] == 0:
+                continue
+            assert abs(est[:, i].mean() - eta[i]) < 4.5 * np.sqrt(ref["var"][i] / R) + 0.02 * eta[i] * (k == 5), (k, i)
+    # the generator matters: the same seed gives other samples than SplitMix64
+    assert not np.array_equal(g.run(oracle.T5, 3, 1000), g.run(oracle.T5, 3, 1000, rng=oracle.PHILOX4X32))
 
 
 # -------------------------------------------------------------- SplitMix64 --
