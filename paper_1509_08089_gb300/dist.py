@@ -42,23 +42,46 @@ def weak_ranges(k: int, budget: int, rank: int, mix: bool = False) -> list[tuple
     return [(m, rank * K, K) for m, K in sub_budgets(k, budget, mix)]
 
 
-def estimate_weak(g, k: int, budget: int, seed: int, rank: int, world: int,
-                  allreduce: Callable[[np.ndarray], np.ndarray], stream=None, mix: bool = False) -> dict:
-    """One weak-scaled estimate: this rank's counts, summed over ranks by
-    ``allreduce`` (int64[2, 22] -> int64[2, 22]), then the device finalize.
-    Methods whose total weight is zero draw nothing (as in the single call)."""
-    import torch
+class DeviceShards:
+    """The device side of :func:`estimate_weak`: this rank's counts in one
+    device buffer (one row per sub-method), read back once."""
 
-    stats = g.stats()
-    counts = torch.zeros((2, NSLOTS), dtype=torch.int64, device=f"cuda:{g.device}")
+    def __init__(self, g, stream=None):
+        import torch
+        self.g, self.stream = g, stream
+        self.stats = g.stats()
+        self.buf = torch.zeros((2, NSLOTS), dtype=torch.int64, device=f"cuda:{g.device}")
+
+    def has_weight(self, method: int) -> bool:
+        return not (self.stats.gamma[method][0] == 0 and self.stats.gamma[method][1] == 0)
+
+    def count(self, slot: int, method: int, first: int, count: int, seed: int):
+        moss_sample_counts(self.g.handle, method, first, count, seed, self.buf[slot], self.stream)
+
+    def counts(self) -> np.ndarray:
+        return self.buf.cpu().numpy()
+
+    def finalize(self, k: int, mix: bool, K: np.ndarray, hits: np.ndarray) -> dict:
+        if mix:
+            return result_dict(moss_finalize_min(self.g.handle, K, hits, self.stream))
+        return result_dict(moss_finalize(self.g.handle, k, K, hits, self.stream))
+
+
+def estimate_weak(g, k: int, budget: int, seed: int, rank: int, world: int,
+                  allreduce: Callable[[np.ndarray], np.ndarray], stream=None, mix: bool = False,
+                  shards=None) -> dict:
+    """One weak-scaled estimate: this rank's counts, summed over ranks by
+    ``allreduce`` (int64[2, 22] -> int64[2, 22]), then the finalize of the
+    summed counts with K_l = per-rank count x world.  Methods whose total
+    weight is zero draw nothing (as in the single call).  ``shards`` (default
+    :class:`DeviceShards` of g) does the counting and the finalize; any
+    object with the same four methods can stand in for it."""
+    sh = shards if shards is not None else DeviceShards(g, stream)
     K = [0, 0]
     for slot, (m, first, count) in enumerate(weak_ranges(k, budget, rank, mix)):
-        if stats.gamma[m][0] == 0 and stats.gamma[m][1] == 0:
+        if not sh.has_weight(m):
             continue
-        moss_sample_counts(g.handle, m, first, count, seed, counts[slot], stream)
+        sh.count(slot, m, first, count, seed)
         K[slot] = count * world
-    total = allreduce(counts.cpu().numpy())
-    Ka, Ha = np.array(K, dtype=np.uint64), total.astype(np.uint64)
-    if mix:
-        return result_dict(moss_finalize_min(g.handle, Ka, Ha, stream))
-    return result_dict(moss_finalize(g.handle, k, Ka, Ha, stream))
+    total = allreduce(sh.counts())
+    return sh.finalize(k, mix, np.array(K, dtype=np.uint64), total.astype(np.uint64))
