@@ -362,6 +362,13 @@ int moss_server_submit(moss_server *s, int graph_id, int k, uint64_t budget, dou
  * MOSS_TABLES_4MIN (MOSS_ESTATE otherwise). */
 int moss_server_submit_min(moss_server *s, int graph_id, uint64_t budget, uint64_t budget_min, uint64_t seed,
                            uint64_t *request_id);
+/* A MOSS-4 + MOSS-4Min request with a target relative standard error in
+ * (0, 1): a pilot of pilot_samples (split evenly) sets the total budget B by
+ * moss_budget_for_target_min, and the request then draws K = floor(B/2)
+ * MOSS-4 and K-check = B - K MOSS-4Min samples; its result equals
+ * moss_sample_estimate_min(graph, K, K-check, seed). */
+int moss_server_submit_min_target(moss_server *s, int graph_id, double target_rse, uint64_t seed,
+                                  uint64_t *request_id);
 /* Block until the request finishes (MOSS_EBUSY after timeout_s); out and
  * stats are nullable.  A request can be waited for once. */
 int moss_server_wait(moss_server *s, uint64_t request_id, double timeout_s, moss_result *out,
@@ -372,6 +379,17 @@ void moss_server_free(moss_server *s);
 /* The budget rule above, from pilot counts K[2], hits[2][22] (host only). */
 uint64_t moss_budget_for_target(int k, const uint64_t *K, const uint64_t *hits, double target,
                                 uint64_t min_budget, uint64_t max_budget);
+/* The budget rule of MOSS-4 + MOSS-4Min requests (host only), from pilot
+ * counts K = {K, K-check} and hits[0] (MOSS-4 classes), hits[1] (MOSS-4Min
+ * (class, c) slots).  For each class with at least 10 pilot hits in a
+ * source, that source's relative variance per sample: 1/f - 1 for MOSS-4
+ * (Theorem 3, f the hit fraction) and K-check b / a^2 - 1 for MOSS-4Min
+ * (Theorem 5 with per-CIS probabilities; a = sum_c m_c / c, b = sum_c m_c /
+ * c^2); a class seen by both takes their Theorem 1 combination r1 r2 /
+ * (r1 + r2).  Since the request draws K = K-check = B / 2, B = 2 r / eps^2,
+ * the largest over classes, clamped to [min_budget, max_budget]. */
+uint64_t moss_budget_for_target_min(const uint64_t *K, const uint64_t *hits, double target, uint64_t min_budget,
+                                    uint64_t max_budget);
 
 /* The covariance matrix of the estimates of moss_finalize's inputs: cov_host
  * (22 x 22 doubles, row-major, host) receives Cov(est_i, est_j) for classes

@@ -140,6 +140,9 @@ def load():
         "moss_server_stats": ([_vp, ctypes.POINTER(moss_server_info)], ctypes.c_int),
         "moss_server_free": ([_vp], None),
         "moss_budget_for_target": ([ctypes.c_int, _vp, _vp, ctypes.c_double, _u64, _u64], ctypes.c_uint64),
+        "moss_budget_for_target_min": ([_vp, _vp, ctypes.c_double, _u64, _u64], ctypes.c_uint64),
+        "moss_server_submit_min_target": ([_vp, ctypes.c_int, ctypes.c_double, _u64,
+                                           ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
         "moss_gather_rate": ([_u64, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -440,6 +443,18 @@ def moss_budget_for_target(k: int, K, hits, target: float, min_budget: int, max_
     return int(load().moss_budget_for_target(k, _ptr(Ka), _ptr(Ha), target, min_budget, max_budget))
 
 
+def moss_budget_for_target_min(K, hits, target: float, min_budget: int, max_budget: int) -> int:
+    Ka = np.ascontiguousarray(K, dtype=np.uint64)
+    Ha = np.ascontiguousarray(hits, dtype=np.uint64)
+    return int(load().moss_budget_for_target_min(_ptr(Ka), _ptr(Ha), target, min_budget, max_budget))
+
+
+def moss_server_submit_min_target(s: int, graph_id: int, target_rse: float, seed: int = 1) -> int:
+    rid = ctypes.c_uint64(0)
+    _check(load().moss_server_submit_min_target(s, graph_id, target_rse, seed, ctypes.byref(rid)))
+    return rid.value
+
+
 class Server:
     """Owning wrapper of a request server (see moss_server_* in include/moss.h)."""
 
@@ -455,7 +470,12 @@ class Server:
     def submit(self, graph_id: int, k: int, budget: int = 0, target_rse: float = 0.0, seed: int = 1) -> int:
         return moss_server_submit(self.handle, graph_id, k, budget, target_rse, seed)
 
-    def submit_min(self, graph_id: int, budget: int, budget_min: int, seed: int = 1) -> int:
+    def submit_min(self, graph_id: int, budget: int = 0, budget_min: int = 0, seed: int = 1,
+                   target_rse: float = 0.0) -> int:
+        """A MOSS-4 + MOSS-4Min request: explicit budgets, or a target
+        relative standard error whose pilot sets them."""
+        if target_rse > 0.0:
+            return moss_server_submit_min_target(self.handle, graph_id, target_rse, seed)
         return moss_server_submit_min(self.handle, graph_id, budget, budget_min, seed)
 
     def wait(self, request_id: int, timeout_s: float = 600.0):

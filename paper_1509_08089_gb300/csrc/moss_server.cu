@@ -131,6 +131,43 @@ extern "C" uint64_t moss_budget_for_target(int k, const uint64_t *K, const uint6
     return (uint64_t)b;
 }
 
+extern "C" uint64_t moss_budget_for_target_min(const uint64_t *K, const uint64_t *hits, double target,
+                                               uint64_t min_budget, uint64_t max_budget) {
+    // per-sample relative variance of each source's estimate of class i from
+    // the pilot, then the Theorem 1 mix of the two; the mix draws K = K-check
+    // = B / 2, so the relative variance r / (B / 2) reaches eps^2 at B = 2 r / eps^2
+    static const int first_slot[7] = {-1, -1, -1, 0, -1, 4, 10};   // MOSS-4Min (class, c) slots
+    static const int nslots[7] = {0, 0, 0, 4, 0, 6, 12};
+    double need = 0.0;
+    for (int i = 1; i <= 6; ++i) {
+        if (i == 2) continue;   // the 3-star is never sampled: eq. (2) closes it
+        double r1 = -1.0, r2 = -1.0;
+        if (K[0] > 0 && hits[i] >= 10) r1 = (double)K[0] / (double)hits[i] - 1.0;   // Theorem 3: 1/f - 1
+        if (K[1] > 0 && nslots[i] > 0) {
+            double a = 0.0, b = 0.0, m = 0.0;
+            for (int c = 1; c <= nslots[i]; ++c) {
+                const double x = (double)hits[kSlots + first_slot[i] + c - 1];
+                a += x / c;
+                b += x / ((double)c * c);
+                m += x;
+            }
+            // Theorem 5 with per-CIS probabilities: Gamma-check h / (2 n) - 1 = K-check b / a^2 - 1
+            if (m >= 10) r2 = (double)K[1] * b / (a * a) - 1.0;
+        }
+        double r;
+        if (r1 > 0 && r2 > 0) r = r1 * r2 / (r1 + r2);   // Theorem 1
+        else if (r1 > 0) r = r1;
+        else if (r2 > 0) r = r2;
+        else continue;
+        const double B = 2.0 * r / (target * target);
+        need = B > need ? B : need;
+    }
+    double b = std::ceil(need);
+    if (b < (double)min_budget) b = (double)min_budget;
+    if (b > (double)max_budget) b = (double)max_budget;
+    return (uint64_t)b;
+}
+
 struct moss_server {
     int device = 0;
     moss_server_config cfg{};
@@ -334,14 +371,16 @@ void scheduler(moss_server *s) {
                 }
                 if (q.pilot) {   // the pilot chunk sets the budget
                     q.pilot = false;
-                    uint64_t b = moss_budget_for_target(q.k, q.K, &q.hits[0][0], q.target, s->cfg.min_budget,
-                                                        s->cfg.max_budget);
+                    uint64_t b = q.mix ? moss_budget_for_target_min(q.K, &q.hits[0][0], q.target, s->cfg.min_budget,
+                                                                    s->cfg.max_budget)
+                                       : moss_budget_for_target(q.k, q.K, &q.hits[0][0], q.target,
+                                                                s->cfg.min_budget, s->cfg.max_budget);
                     const uint64_t pilot_total = q.K[0] + q.K[1];
                     if (b < pilot_total) b = pilot_total;
                     q.budget = b;
                     int m[2];
                     uint64_t K[2];
-                    sub_methods(q.k, false, b, 0, s->ginfo[q.graph].total_nonzero, m, K);
+                    sub_methods(q.k, q.mix, q.mix ? b / 2 : b, b - b / 2, s->ginfo[q.graph].total_nonzero, m, K);
                     q.K[0] = K[0];
                     q.K[1] = K[1];
                     if (q.done[0] < q.K[0] || q.done[1] < q.K[1]) {
@@ -469,10 +508,10 @@ int moss_server_submit(moss_server *s, int graph_id, int k, uint64_t budget, dou
     return MOSS_OK;
 }
 
-int moss_server_submit_min(moss_server *s, int graph_id, uint64_t budget, uint64_t budget_min, uint64_t seed,
-                           uint64_t *request_id) {
-    if (!s) return set_error(MOSS_EINVAL, "NULL server");
-    if (budget == 0 && budget_min == 0) return set_error(MOSS_EINVAL, "give the MOSS-4 or MOSS-4Min budget");
+// a MOSS-4 + MOSS-4Min request: explicit budgets, or (target > 0) a pilot
+// of pilot_samples split evenly whose counts set the budget
+static int submit_min(moss_server *s, int graph_id, uint64_t budget, uint64_t budget_min, double target, uint64_t seed,
+               uint64_t *request_id) {
     std::unique_lock<std::mutex> lk(s->mu);
     if (s->status != MOSS_OK) return set_error(s->status, "the server stopped after an error");
     if (graph_id < 0 || graph_id >= (int)s->graphs.size()) return set_error(MOSS_EINVAL, "unknown graph id");
@@ -488,9 +527,15 @@ int moss_server_submit_min(moss_server *s, int graph_id, uint64_t budget, uint64
     q.k = 4;
     q.mix = true;
     q.seed = seed;
+    q.target = target;
     q.t_arrive = now_s();
     if (s->first_submit == 0) s->first_submit = q.t_arrive;
     int m[2];
+    if (target > 0.0) {   // pilot: the configured pilot samples, split evenly
+        q.pilot = true;
+        budget = s->cfg.pilot_samples / 2;
+        budget_min = s->cfg.pilot_samples - budget;
+    }
     q.budget = budget + budget_min;
     sub_methods(4, true, budget, budget_min, s->ginfo[graph_id].total_nonzero, m, q.K);
     const uint64_t id = q.id;
@@ -500,6 +545,20 @@ int moss_server_submit_min(moss_server *s, int graph_id, uint64_t budget, uint64
     lk.unlock();
     s->cv_work.notify_one();
     return MOSS_OK;
+}
+
+int moss_server_submit_min(moss_server *s, int graph_id, uint64_t budget, uint64_t budget_min, uint64_t seed,
+                           uint64_t *request_id) {
+    if (!s) return set_error(MOSS_EINVAL, "NULL server");
+    if (budget == 0 && budget_min == 0) return set_error(MOSS_EINVAL, "give the MOSS-4 or MOSS-4Min budget");
+    return submit_min(s, graph_id, budget, budget_min, 0.0, seed, request_id);
+}
+
+int moss_server_submit_min_target(moss_server *s, int graph_id, double target_rse, uint64_t seed,
+                                  uint64_t *request_id) {
+    if (!s) return set_error(MOSS_EINVAL, "NULL server");
+    if (!(target_rse > 0.0 && target_rse < 1.0)) return set_error(MOSS_EINVAL, "target relative error must be in (0, 1)");
+    return submit_min(s, graph_id, 0, 0, target_rse, seed, request_id);
 }
 
 int moss_server_wait(moss_server *s, uint64_t request_id, double timeout_s, moss_result *out,

@@ -156,8 +156,10 @@ def test_served_results_match_oracle(pool_csrs):
             subs = [(gi, k, seed, server.submit(gids[gi], k, budget=b, target_rse=eps, seed=seed))
                     for gi, k, b, eps, seed in plan]
             rid_m = server.submit_min(gid_m, 300_000, 200_000, seed=16)
+            rid_t = server.submit_min(gid_m, target_rse=0.03, seed=18)     # budget from its pilot
             served = [(gi, k, seed, *server.wait(rid, 300.0)) for gi, k, seed, rid in subs]
             r_m, _ = server.wait(rid_m, 300.0)
+            r_t, st_t = server.wait(rid_t, 300.0)
         assert sum(1 for _, _, _, _, st in served if st["budget"] not in (700_001, 900_000)) == 3
         for gi, k, seed, r, st in served:
             og = oracle.OracleGraph(*csrs[gi])
@@ -176,6 +178,17 @@ def test_served_results_match_oracle(pool_csrs):
         for i in range(1, 7):
             tol = 1e-9 * (max(float(og.Lambda3), 1.0) if i == 2 else max(abs(o["est"][i]), 1e-300))
             assert abs(r_m["est"][i] - o["est"][i]) <= tol, i
+        # the target-error MOSS-4 + MOSS-4Min request: K = floor(B/2), K-check = B - K
+        K, Km = r_t["K"]
+        assert K == st_t["budget"] // 2 and Km == st_t["budget"] - K and st_t["budget"] >= 20_000
+        o = og.estimate_min(K, Km, 18, rng=oracle.PHILOX4X32)
+        assert np.array_equal(r_t["hits"][0], og.run(oracle.MOSS4, 18, K, rng=oracle.PHILOX4X32))
+        assert np.array_equal(r_t["hits"][1], og.run(oracle.MOSS4MIN, 18, Km, rng=oracle.PHILOX4X32))
+        for i in range(1, 7):
+            tol = 1e-9 * (max(float(og.Lambda3), 1.0) if i == 2 else max(abs(o["est"][i]), 1e-300))
+            assert abs(r_t["est"][i] - o["est"][i]) <= tol, i
+            if i != 2 and r_t["hits"][0][i] >= 200:       # well-sampled classes meet the target
+                assert np.sqrt(r_t["var"][i]) / r_t["est"][i] <= 0.035, i
     finally:
         gmin.close()
 
