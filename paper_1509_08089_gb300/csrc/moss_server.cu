@@ -7,7 +7,17 @@
 // sample ids of every active request, sized so the tick holds about
 // `tick_samples` samples shared fairly between the requests.  Requests that
 // arrive while a tick runs join the next one, so small requests finish in a
-// tick or two while large ones keep streaming.  Counts are accumulated per
+// tick or two while large ones keep streaming.  Under overload (samples
+// for at least two more full ticks can be scheduled already) ticks are
+// double-buffered: while tick N runs, the scheduler plans tick N+1 from what is
+// already known (every request's next sample ids; a request still waiting
+// for its pilot's counts sits one tick out) and queues it behind tick N, so
+// the GPU does not idle while the host takes tick N's counts back.  Below
+// that a queued tick would mostly hold back requests that arrive or finish
+// their pilot meanwhile (adding a tick to their latency), so the next tick
+// is planned after tick N returns.
+// Requests that finish are finalized on a second stream, so their results
+// do not wait behind a queued tick.  Counts are accumulated per
 // request in exact integers; a finished request is finalized on the device
 // (the same arithmetic as moss_sample_estimate).  Since every sample is keyed
 // by its id, a served result equals moss_sample_estimate with the same final
@@ -71,6 +81,22 @@ cudaError_t grow(T **p, size_t *cap, size_t need, cudaStream_t s) {
     if (e == cudaSuccess) *cap = c;
     return e;
 }
+
+// the buffers of one tick in flight
+struct TickBuffers {
+    BatchTask *d_tasks = nullptr;
+    size_t cap_tasks = 0;
+    uint32_t *d_tiles = nullptr;
+    size_t cap_tiles = 0;
+    uint64_t *d_task_counts = nullptr;
+    size_t cap_tc = 0;
+    uint64_t *h_task_counts = nullptr;   // pinned
+    size_t cap_htc = 0;
+    unsigned long long *d_next = nullptr;
+    cudaEvent_t start = nullptr, end = nullptr;   // timed: the tick's span on the stream
+    std::vector<BatchTask> tasks;
+    std::vector<std::pair<uint64_t, int>> owner;   // (request id, sub-method slot) of each task
+};
 
 template <typename T>
 cudaError_t grow_host(T **p, size_t *cap, size_t need) {
@@ -181,20 +207,13 @@ struct moss_server {
     uint64_t next_id = 1;
     bool stop = false, started = false;
     std::thread worker;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;      // ticks
+    cudaStream_t fin_stream = nullptr;  // finalize of finished requests
     int status = MOSS_OK;          // sticky error of the scheduler
     // device / pinned buffers
     DevGraph *d_graphs = nullptr;
     size_t cap_graphs = 0;
-    BatchTask *d_tasks = nullptr;
-    size_t cap_tasks = 0;
-    uint32_t *d_tiles = nullptr;
-    size_t cap_tiles = 0;
-    uint64_t *d_task_counts = nullptr;
-    size_t cap_tc = 0;
-    uint64_t *h_task_counts = nullptr;
-    size_t cap_htc = 0;
-    unsigned long long *d_next = nullptr;
+    TickBuffers tick[2];           // two ticks in flight at most
     BatchRequest *d_breq = nullptr;
     size_t cap_breq = 0;
     uint64_t *d_totals = nullptr;
@@ -218,8 +237,10 @@ int fail_server(moss_server *s, int code, const char *what) {
     return set_error(code, what);
 }
 
-// one tick: sample the given tasks, return per-task counts in h_task_counts
-int run_tick(moss_server *s, const std::vector<BatchTask> &tasks, uint64_t ntiles) {
+// queue one tick on the stream: sample the tasks of buffer set tb, sum them
+// per task and copy the counts to tb's pinned host array; `end` records
+// when they have arrived
+int enqueue_tick(moss_server *s, TickBuffers &tb, uint64_t ntiles) {
     cudaStream_t st = s->stream;
     cudaError_t e = cudaSuccess;
     if (!s->graphs_uploaded) {
@@ -232,22 +253,26 @@ int run_tick(moss_server *s, const std::vector<BatchTask> &tasks, uint64_t ntile
         if (e != cudaSuccess) return fail_server(s, MOSS_ECUDA, "uploading server graphs");
         s->graphs_uploaded = true;
     }
-    if (e == cudaSuccess) e = grow(&s->d_tasks, &s->cap_tasks, tasks.size() + 1, st);
-    if (e == cudaSuccess) e = grow(&s->d_tiles, &s->cap_tiles, (size_t)(ntiles + 1) * kSlots, st);
-    if (e == cudaSuccess) e = grow(&s->d_task_counts, &s->cap_tc, (tasks.size() + 1) * kSlots, st);
-    if (e == cudaSuccess) e = grow_host(&s->h_task_counts, &s->cap_htc, (tasks.size() + 1) * kSlots);
+    const size_t nt = tb.tasks.size();
+    if (e == cudaSuccess) e = grow(&tb.d_tasks, &tb.cap_tasks, nt + 1, st);
+    if (e == cudaSuccess) e = grow(&tb.d_tiles, &tb.cap_tiles, (size_t)(ntiles + 1) * kSlots, st);
+    if (e == cudaSuccess) e = grow(&tb.d_task_counts, &tb.cap_tc, (nt + 1) * kSlots, st);
+    if (e == cudaSuccess) e = grow_host(&tb.h_task_counts, &tb.cap_htc, (nt + 1) * kSlots);
     if (e != cudaSuccess) return fail_server(s, MOSS_ENOMEM, "server tick buffers");
-    e = cudaMemcpyAsync(s->d_tasks, tasks.data(), tasks.size() * sizeof(BatchTask), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_next, 0, sizeof(unsigned long long), st);
+    // tb.tasks and tb.owner stay as they are until the tick is taken back
+    e = cudaEventRecord(tb.start, st);
     if (e == cudaSuccess)
-        e = launch_sample_batch(s->d_graphs, s->d_tasks, (int)tasks.size(), ntiles, s->cfg.tile_samples, s->d_next,
-                                s->d_tiles, 256, s->blocks, nullptr, st);
+        e = cudaMemcpyAsync(tb.d_tasks, tb.tasks.data(), nt * sizeof(BatchTask), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tb.d_next, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess)
-        e = launch_batch_reduce(s->d_tasks, (int)tasks.size(), s->cfg.tile_samples, s->d_tiles, s->d_task_counts, st);
+        e = launch_sample_batch(s->d_graphs, tb.d_tasks, (int)nt, ntiles, s->cfg.tile_samples, tb.d_next, tb.d_tiles,
+                                256, s->blocks, nullptr, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->h_task_counts, s->d_task_counts, tasks.size() * kSlots * sizeof(uint64_t),
+        e = launch_batch_reduce(tb.d_tasks, (int)nt, s->cfg.tile_samples, tb.d_tiles, tb.d_task_counts, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tb.h_task_counts, tb.d_task_counts, nt * kSlots * sizeof(uint64_t),
                             cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaEventRecord(tb.end, st);
     if (e != cudaSuccess) return fail_server(s, MOSS_ECUDA, "server tick");
     return MOSS_OK;
 }
@@ -255,7 +280,7 @@ int run_tick(moss_server *s, const std::vector<BatchTask> &tasks, uint64_t ntile
 // finalize finished requests on the device (one thread each)
 int finalize(moss_server *s, const std::vector<SReq *> &fin) {
     if (fin.empty()) return MOSS_OK;
-    cudaStream_t st = s->stream;
+    cudaStream_t st = s->fin_stream;
     const size_t n = fin.size();
     std::vector<BatchRequest> br(n);
     std::vector<uint64_t> tot(2 * n * kSlots);
@@ -299,112 +324,163 @@ void admit(moss_server *s, double t) {
     }
 }
 
-void scheduler(moss_server *s) {
-    cudaSetDevice(s->device);
-    std::vector<BatchTask> tasks;
-    std::vector<std::pair<uint64_t, int>> owner;   // (request id, sub-method slot) of each task
-    for (;;) {
-        tasks.clear();
-        owner.clear();
-        uint64_t ntiles = 0;
-        {
-            std::unique_lock<std::mutex> lk(s->mu);
-            if (s->stop) break;   // shutting down: unfinished requests are abandoned
-            if (s->cfg.reserve_bytes) {
-                size_t fr = 0, totb = 0;
-                if (cudaMemGetInfo(&fr, &totb) == cudaSuccess) s->free_bytes = fr;
-            }
-            admit(s, now_s());
-            if (s->active.empty()) {
-                s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+// plan the next tick into tb from the active requests (under the lock):
+// the next fair-share chunk of every sub-method with ids left to schedule;
+// returns the tick's tile count (0: nothing to run)
+uint64_t plan_tick(moss_server *s, TickBuffers &tb) {
+    tb.tasks.clear();
+    tb.owner.clear();
+    uint64_t ntiles = 0;
+    const uint64_t tile = s->cfg.tile_samples;
+    size_t open = 0;   // requests with ids left to schedule
+    for (uint64_t id : s->active) {
+        const SReq &q = s->reqs[id];
+        if (q.next[0] < q.K[0] || q.next[1] < q.K[1]) ++open;
+    }
+    if (open == 0) return 0;
+    uint64_t share = s->cfg.tick_samples / open;
+    share = share < tile ? tile : share - share % tile;
+    for (uint64_t id : s->active) {
+        SReq &q = s->reqs[id];
+        int m[2];
+        uint64_t Kdummy[2];
+        const int nsub = sub_methods(q.k, q.mix, 0, 0, s->ginfo[q.graph].total_nonzero, m, Kdummy);
+        bool any = false;
+        for (int j = 0; j < nsub; ++j) {
+            if (q.next[j] >= q.K[j]) continue;
+            const uint64_t c = std::min(share, q.K[j] - q.next[j]);
+            BatchTask t;
+            t.seed = q.seed;
+            t.first = q.next[j];
+            t.count = c;
+            t.tile0 = ntiles;
+            t.graph = (uint32_t)q.graph;
+            t.method = (uint32_t)m[j];
+            tb.tasks.push_back(t);
+            tb.owner.push_back({id, j});
+            ntiles += (c + tile - 1) / tile;
+            q.next[j] += c;
+            any = true;
+        }
+        if (any) ++q.ticks;
+    }
+    return ntiles;
+}
+
+// take a finished tick back: add its counts to its requests, set the budget
+// of requests whose pilot it completed, and return the requests it finished
+void take_tick(moss_server *s, TickBuffers &tb, std::vector<SReq *> &fin) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, tb.start, tb.end);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->busy_s += ms * 1e-3;
+    ++s->ticks;
+    for (size_t i = 0; i < tb.tasks.size(); ++i) {
+        SReq &q = s->reqs[tb.owner[i].first];
+        const int j = tb.owner[i].second;
+        for (int c = 0; c < kSlots; ++c) q.hits[j][c] += tb.h_task_counts[i * kSlots + c];
+        q.done[j] += tb.tasks[i].count;
+        s->samples += tb.tasks[i].count;
+    }
+    std::vector<uint64_t> still;
+    for (uint64_t id : s->active) {
+        SReq &q = s->reqs[id];
+        const bool all = q.done[0] >= q.K[0] && q.done[1] >= q.K[1];
+        if (!all) {
+            still.push_back(id);
+            continue;
+        }
+        if (q.pilot) {   // the pilot chunk sets the budget
+            q.pilot = false;
+            uint64_t b = q.mix ? moss_budget_for_target_min(q.K, &q.hits[0][0], q.target, s->cfg.min_budget,
+                                                            s->cfg.max_budget)
+                               : moss_budget_for_target(q.k, q.K, &q.hits[0][0], q.target, s->cfg.min_budget,
+                                                        s->cfg.max_budget);
+            const uint64_t pilot_total = q.K[0] + q.K[1];
+            if (b < pilot_total) b = pilot_total;
+            q.budget = b;
+            int m[2];
+            uint64_t K[2];
+            sub_methods(q.k, q.mix, q.mix ? b / 2 : b, b - b / 2, s->ginfo[q.graph].total_nonzero, m, K);
+            q.K[0] = K[0];
+            q.K[1] = K[1];
+            if (q.done[0] < q.K[0] || q.done[1] < q.K[1]) {
+                still.push_back(id);
                 continue;
             }
-            // fair share of the tick, in whole tiles
-            const uint64_t tile = s->cfg.tile_samples;
-            uint64_t share = s->cfg.tick_samples / s->active.size();
-            share = share < tile ? tile : share - share % tile;
-            for (uint64_t id : s->active) {
-                SReq &q = s->reqs[id];
-                int m[2];
-                uint64_t Kdummy[2];
-                const int nsub = sub_methods(q.k, q.mix, 0, 0, s->ginfo[q.graph].total_nonzero, m, Kdummy);
-                for (int j = 0; j < nsub; ++j) {
-                    if (q.next[j] >= q.K[j]) continue;
-                    const uint64_t c = std::min(share, q.K[j] - q.next[j]);
-                    BatchTask t;
-                    t.seed = q.seed;
-                    t.first = q.next[j];
-                    t.count = c;
-                    t.tile0 = ntiles;
-                    t.graph = (uint32_t)q.graph;
-                    t.method = (uint32_t)m[j];
-                    tasks.push_back(t);
-                    owner.push_back({id, j});
-                    ntiles += (c + tile - 1) / tile;
-                    q.next[j] += c;
-                }
-                ++q.ticks;
-            }
         }
-        const double t0 = now_s();
-        if (!tasks.empty() && run_tick(s, tasks, ntiles) != MOSS_OK) break;
-        const double t1 = now_s();
-        std::vector<SReq *> fin;
-        {
+        fin.push_back(&q);
+    }
+    s->active.swap(still);
+}
+
+void scheduler(moss_server *s) {
+    cudaSetDevice(s->device);
+    int queued[2] = {-1, -1};   // buffer sets of the ticks in flight, oldest first
+    int nq = 0;
+    for (;;) {
+        // with a tick in flight, queue the next one now only under backlog
+        bool ahead = nq == 0;
+        if (nq == 1) {
             std::lock_guard<std::mutex> lk(s->mu);
-            s->busy_s += t1 - t0;
-            ++s->ticks;
-            for (size_t i = 0; i < tasks.size(); ++i) {
-                SReq &q = s->reqs[owner[i].first];
-                const int j = owner[i].second;
-                for (int c = 0; c < kSlots; ++c) q.hits[j][c] += s->h_task_counts[i * kSlots + c];
-                q.done[j] += tasks[i].count;
-                s->samples += tasks[i].count;
-            }
-            std::vector<uint64_t> still;
+            uint64_t left = 0;
             for (uint64_t id : s->active) {
-                SReq &q = s->reqs[id];
-                const bool all = q.done[0] >= q.K[0] && q.done[1] >= q.K[1];
-                if (!all) {
-                    still.push_back(id);
+                const SReq &q = s->reqs[id];
+                left += (q.K[0] - q.next[0]) + (q.K[1] - q.next[1]);
+            }
+            ahead = left >= 2 * s->cfg.tick_samples;
+        }
+        // plan and queue a tick while a buffer set is free
+        bool launched = false;
+        if (ahead) {
+            const int b = nq == 0 ? 0 : 1 - queued[0];
+            uint64_t ntiles = 0;
+            {
+                std::unique_lock<std::mutex> lk(s->mu);
+                if (s->stop) break;   // shutting down: unfinished requests are abandoned
+                if (s->cfg.reserve_bytes) {
+                    size_t fr = 0, totb = 0;
+                    if (cudaMemGetInfo(&fr, &totb) == cudaSuccess) s->free_bytes = fr;
+                }
+                admit(s, now_s());
+                ntiles = plan_tick(s, s->tick[b]);
+                if (ntiles == 0 && nq == 0) {   // nothing to run and nothing in flight
+                    s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
                     continue;
                 }
-                if (q.pilot) {   // the pilot chunk sets the budget
-                    q.pilot = false;
-                    uint64_t b = q.mix ? moss_budget_for_target_min(q.K, &q.hits[0][0], q.target, s->cfg.min_budget,
-                                                                    s->cfg.max_budget)
-                                       : moss_budget_for_target(q.k, q.K, &q.hits[0][0], q.target,
-                                                                s->cfg.min_budget, s->cfg.max_budget);
-                    const uint64_t pilot_total = q.K[0] + q.K[1];
-                    if (b < pilot_total) b = pilot_total;
-                    q.budget = b;
-                    int m[2];
-                    uint64_t K[2];
-                    sub_methods(q.k, q.mix, q.mix ? b / 2 : b, b - b / 2, s->ginfo[q.graph].total_nonzero, m, K);
-                    q.K[0] = K[0];
-                    q.K[1] = K[1];
-                    if (q.done[0] < q.K[0] || q.done[1] < q.K[1]) {
-                        still.push_back(id);
-                        continue;
-                    }
+            }
+            if (ntiles > 0) {
+                if (enqueue_tick(s, s->tick[b], ntiles) != MOSS_OK) break;
+                queued[nq++] = b;
+                launched = true;
+            }
+        }
+        // with two ticks queued, or nothing new to queue, take the oldest back
+        if (nq == 2 || (!launched && nq > 0)) {
+            TickBuffers &tb = s->tick[queued[0]];
+            if (cudaEventSynchronize(tb.end) != cudaSuccess) {
+                fail_server(s, MOSS_ECUDA, "server tick");
+                break;
+            }
+            queued[0] = queued[1];
+            --nq;
+            std::vector<SReq *> fin;
+            take_tick(s, tb, fin);
+            if (finalize(s, fin) != MOSS_OK) break;
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                const double t = now_s();
+                for (SReq *q : fin) {
+                    q->state = 2;
+                    q->t_done = t;
+                    ++s->completed;
+                    s->last_done = t;
                 }
-                fin.push_back(&q);
             }
-            s->active.swap(still);
+            if (!fin.empty()) s->cv_done.notify_all();
         }
-        if (finalize(s, fin) != MOSS_OK) break;
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            const double t = now_s();
-            for (SReq *q : fin) {
-                q->state = 2;
-                q->t_done = t;
-                ++s->completed;
-                s->last_done = t;
-            }
-        }
-        if (!fin.empty()) s->cv_done.notify_all();
     }
+    if (s->stream) cudaStreamSynchronize(s->stream);   // no tick left running on the buffers
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
     s->cv_done.notify_all();
@@ -443,8 +519,11 @@ int moss_server_create(int device, const moss_server_config *cfg, moss_server **
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(device);
-    const bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
-                    cudaMalloc(reinterpret_cast<void **>(&s->d_next), sizeof(unsigned long long)) == cudaSuccess;
+    bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&s->fin_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (TickBuffers &tb : s->tick)
+        ok = ok && cudaMalloc(reinterpret_cast<void **>(&tb.d_next), sizeof(unsigned long long)) == cudaSuccess &&
+             cudaEventCreate(&tb.start) == cudaSuccess && cudaEventCreate(&tb.end) == cudaSuccess;
     s->blocks = batch_blocks(device, 256, 0);
     if (prev >= 0) cudaSetDevice(prev);
     if (!ok) {
@@ -611,15 +690,29 @@ void moss_server_free(moss_server *s) {
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(s->device);
+    if (s->fin_stream) {   // the finalize buffers live on the finalize stream
+        void *fdev[] = {s->d_breq, s->d_totals, s->d_results};
+        for (void *p : fdev)
+            if (p) cudaFreeAsync(p, s->fin_stream);
+        cudaStreamSynchronize(s->fin_stream);
+    }
     if (s->stream) {
-        void *dev[] = {s->d_graphs, s->d_tasks, s->d_tiles, s->d_task_counts, s->d_breq, s->d_totals, s->d_results};
-        for (void *p : dev)
-            if (p) cudaFreeAsync(p, s->stream);
+        if (s->d_graphs) cudaFreeAsync(s->d_graphs, s->stream);
+        for (TickBuffers &tb : s->tick) {
+            void *tdev[] = {tb.d_tasks, tb.d_tiles, tb.d_task_counts};
+            for (void *p : tdev)
+                if (p) cudaFreeAsync(p, s->stream);
+        }
         cudaStreamSynchronize(s->stream);
         cudaStreamDestroy(s->stream);
     }
-    if (s->d_next) cudaFree(s->d_next);
-    if (s->h_task_counts) cudaFreeHost(s->h_task_counts);
+    if (s->fin_stream) cudaStreamDestroy(s->fin_stream);
+    for (TickBuffers &tb : s->tick) {
+        if (tb.d_next) cudaFree(tb.d_next);
+        if (tb.h_task_counts) cudaFreeHost(tb.h_task_counts);
+        if (tb.start) cudaEventDestroy(tb.start);
+        if (tb.end) cudaEventDestroy(tb.end);
+    }
     if (s->h_results) cudaFreeHost(s->h_results);
     if (prev >= 0) cudaSetDevice(prev);
     delete s;
