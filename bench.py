@@ -289,16 +289,19 @@ def resolved_probe(name: str, row_ptr) -> str:
     return "filter" if b * 32 > (64 << 20) else "hash"
 
 
-def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False) -> int:
+def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False, two_level: bool = False) -> int:
     """Kernels of one step: load 7 (vertices, owners, slot weights, short and
     long slot scans, twins, totals); build 8 (two sigma alias passes, the
-    alias-half fill, four vertex-table phases, edge hash); MOSS-4Min
-    build 12 (three sort tiers, slot records, two alias passes, pick records,
-    total, four vertex-table phases); per sub-method a sampler and a reduce, Path-5 per
-    chunk of DEFER_CHUNK ids a main launch, the second-attempt and fallback
-    launches and a reduce; one finalize."""
+    alias-half fill, four alias phases of the vertex tables, edge hash), 3
+    more (the level split) for two-level vertex tables; MOSS-4Min build 12
+    (three sort tiers, slot records, two alias passes, pick records, total,
+    four alias phases of its vertex table), again 3 more with two levels; per
+    sub-method a sampler and a reduce, Path-5 per chunk of DEFER_CHUNK ids a
+    main launch, the second-attempt and fallback launches and a reduce; one
+    finalize."""
     from paper_1509_08089_gb300.dist import sub_budgets
-    n = 7 + 8 + (1 if filtered else 0) + (12 if mix else 0) + 1
+    split = 3 if two_level else 0
+    n = 7 + 8 + split + (1 if filtered else 0) + ((12 + split) if mix else 0) + 1
     for m, K in sub_budgets(k, budget, mix):
         n += 4 * -(-K // DEFER_CHUNK) if m == 2 else 2
     return n
@@ -594,7 +597,8 @@ def run_gpu(args):
                 "d2h_bytes_per_step": d2h},
         "roofline": roof,
         "clocks": clk,
-        "gpu_launches": launches_per_step(k, args.budget, mix, probe_name == "filter") * args.steps,
+        "gpu_launches": launches_per_step(k, args.budget, mix, probe_name == "filter", len(rp) - 1 >= 1 << 20)
+        * args.steps,
         "wall_s_timed": t_wall,
         "step_ms": step_ms,
     }
@@ -631,7 +635,7 @@ def run_gpu(args):
                        "rng": args.rng,
                        "l2": "flushed (512 MB write) before every timed step; tables larger than the L2"},
             "roofline": roofline("cl_n4m", rp3, p3, t3, [1, 2], l2_bytes, gather, peaks),
-            "clocks": clk3, "gpu_launches": launches_per_step(5, B3, False, p3 == "filter") * args.steps}
+            "clocks": clk3, "gpu_launches": launches_per_step(5, B3, False, p3 == "filter", True) * args.steps}
         out["batched"] = measure_batched(moss, torch, [f.result() for f in futures["batched"]],
                                          batch_specs(args.graphs)[1], args.steps, args.warmup, stream, rng)
         out["served"] = measure_served(moss, [f.result() for f in futures["served"]], args.rate,

@@ -57,10 +57,12 @@ def _load():
         lib = ctypes.CDLL(build())
         lib.oracle_new.argtypes = [ctypes.c_uint32, _u64p, _u32p]
         lib.oracle_new.restype = ctypes.c_void_p
+        lib.oracle_new_split.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int]
+        lib.oracle_new_split.restype = ctypes.c_void_p
         lib.oracle_free.argtypes = [ctypes.c_void_p]
         lib.oracle_totals.argtypes = [ctypes.c_void_p, _u64p]
         lib.oracle_vertex.argtypes = [ctypes.c_void_p, _u64p, _u64p, _u64p, _u64p]
-        lib.oracle_seed_table.argtypes = [ctypes.c_void_p, ctypes.c_int, _u64p, _u64p, _u32p]
+        lib.oracle_vertex_table.argtypes = [ctypes.c_void_p, ctypes.c_int, _u32p, _u64p, _u32p, _u64p, _u64p, _u32p]
         lib.oracle_sigma_table.argtypes = [ctypes.c_void_p, _u64p, _u32p, _u64p]
         lib.oracle_alias_build.argtypes = [ctypes.c_uint64, _u64p, _u64p, _u32p]
         lib.oracle_alias_build.restype = ctypes.c_int
@@ -83,7 +85,7 @@ def _load():
         lib.oracle_build_min.argtypes = [ctypes.c_void_p]
         lib.oracle_build_min.restype = ctypes.c_int
         lib.oracle_min_total.argtypes = [ctypes.c_void_p, _u64p]
-        lib.oracle_min_tables.argtypes = [ctypes.c_void_p, _u32p, _u64p, _u64p, _u32p, _u64p, _u64p, _u32p]
+        lib.oracle_min_tables.argtypes = [ctypes.c_void_p, _u32p, _u64p, _u64p, _u32p, _u64p]
         _lib = lib
     return _lib
 
@@ -145,16 +147,28 @@ def alias_build(weights) -> tuple[list[int], list[int]]:
     return [_u128(thr[2 * j:2 * j + 2]) for j in range(m)], [int(a) for a in alias[:m]]
 
 
-class OracleGraph:
-    """The oracle's view of one graph: weights, tables and the samplers."""
+VSPLIT = 20           # heavy vertices of a two-level vertex table: w_v 2^VSPLIT >= W
+ONE_LEVEL = 64        # the split value of a single-level vertex table
 
-    def __init__(self, row_ptr: np.ndarray, col: np.ndarray):
+
+def default_split(n: int) -> int:
+    """Two levels (split 20) from 2^20 vertices on, one level below."""
+    return VSPLIT if n >= 1 << 20 else ONE_LEVEL
+
+
+class OracleGraph:
+    """The oracle's view of one graph: weights, tables and the samplers.
+    vsplit sets the heavy level of the vertex tables (w_v 2^vsplit >= W;
+    ONE_LEVEL: a single table; None: default_split(n))."""
+
+    def __init__(self, row_ptr: np.ndarray, col: np.ndarray, vsplit: int | None = None):
         self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.uint64)
         self.col = np.ascontiguousarray(col, dtype=np.uint32)
         self.n = len(self.row_ptr) - 1
         self.nnz = int(self.row_ptr[-1])
+        self.vsplit = vsplit = default_split(self.n) if vsplit is None else vsplit
         col_buf = self.col if self.nnz else np.zeros(1, dtype=np.uint32)
-        self._ctx = _load().oracle_new(self.n, _p(self.row_ptr, _u64p), _p(col_buf, _u32p))
+        self._ctx = _load().oracle_new_split(self.n, _p(self.row_ptr, _u64p), _p(col_buf, _u32p), vsplit)
         if not self._ctx:
             raise MemoryError("oracle_new")
         t = np.zeros(10, dtype=np.uint64)
@@ -180,13 +194,24 @@ class OracleGraph:
         gam = [[_u128(g[(l * 2 * n) + 2 * v:(l * 2 * n) + 2 * v + 2]) for v in range(self.n)] for l in range(3)]
         return deg[:self.n], S[:self.n], Q[:self.n], gam
 
-    def seed_table(self, which: int):
+    def vertex_table(self, which: int) -> dict:
+        """Two-level vertex table of weight which (0 Gamma, 1 Gamma^(1),
+        2 Gamma^(2), 3 Gamma-check), in column order: nh heavy columns, then
+        the light ones; per column its vertex (self), threshold (thr, exact),
+        quantized threshold T and alias; TL = the light level's word bound."""
+        if which == 3:
+            self.build_min()
         n = max(self.n, 1)
+        nh = np.zeros(1, dtype=np.uint32)
+        TL = np.zeros(1, dtype=np.uint64)
+        self_ = np.zeros(n, dtype=np.uint32)
         thr = np.zeros(2 * n, dtype=np.uint64)
         T = np.zeros(n, dtype=np.uint64)
         alias = np.zeros(n, dtype=np.uint32)
-        _load().oracle_seed_table(self._ctx, which, _p(thr, _u64p), _p(T, _u64p), _p(alias, _u32p))
-        return [_u128(thr[2 * v:2 * v + 2]) for v in range(self.n)], T[:self.n], alias[:self.n]
+        _load().oracle_vertex_table(self._ctx, which, _p(nh, _u32p), _p(TL, _u64p), _p(self_, _u32p),
+                                    _p(thr, _u64p), _p(T, _u64p), _p(alias, _u32p))
+        return {"nh": int(nh[0]), "TL": int(TL[0]), "self": self_[:self.n], "T": T[:self.n],
+                "alias": alias[:self.n], "thr": [_u128(thr[2 * v:2 * v + 2]) for v in range(self.n)]}
 
     def sigma_table(self):
         m = max(self.nnz, 1)
@@ -207,7 +232,7 @@ class OracleGraph:
 
     def min_tables(self):
         """(ordered lists, d_{v,u} per slot, sigma-check thresholds and
-        aliases per slot, Gamma-check_v, vertex thresholds T, vertex aliases)."""
+        aliases per slot, Gamma-check_v); the vertex table is vertex_table(3)."""
         self.build_min()
         m, n = max(self.nnz, 1), max(self.n, 1)
         rl = np.zeros(m, dtype=np.uint32)
@@ -215,12 +240,10 @@ class OracleGraph:
         ct = np.zeros(m, dtype=np.uint64)
         ca = np.zeros(m, dtype=np.uint32)
         g = np.zeros(2 * n, dtype=np.uint64)
-        T = np.zeros(n, dtype=np.uint64)
-        al = np.zeros(n, dtype=np.uint32)
         _load().oracle_min_tables(self._ctx, _p(rl, _u32p), _p(rk, _u64p), _p(ct, _u64p), _p(ca, _u32p),
-                                  _p(g, _u64p), _p(T, _u64p), _p(al, _u32p))
+                                  _p(g, _u64p))
         gam = [_u128(g[2 * v:2 * v + 2]) for v in range(self.n)]
-        return (rl[:self.nnz], rk[:self.nnz], ct[:self.nnz], ca[:self.nnz], gam, T[:self.n], al[:self.n])
+        return (rl[:self.nnz], rk[:self.nnz], ct[:self.nnz], ca[:self.nnz], gam)
 
     # -- sampling -----------------------------------------------------------
     def sample_words(self, method: int, words) -> tuple[list[int], int]:

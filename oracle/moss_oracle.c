@@ -15,7 +15,10 @@
  *    the totals of Table 1;
  *  - WeightRandomVertex (Sec. 4.1.3) realised with alias tables built by a
  *    sequential sweep (Walker/Vose alias method, sweeping variant) in exact
- *    integer arithmetic;
+ *    integer arithmetic; over V, on graphs of 2^20 vertices or more, in two
+ *    levels: the heavy vertices (w_v 2^t >= W, t = 20 unless chosen) and the
+ *    light ones each get an alias table, and a separate word picks the level
+ *    with probability floor(W_light 2^64 / W) / 2^64 for the light one;
  *  - RandomVertex(N_v - X) (Sec. 4.1.3): a uniform index over the d_v - |X|
  *    admissible positions, skipping the excluded positions in list order;
  *  - MOSS-4 (Algorithm 1), T-5 (Algorithm 3), Path-5 (Algorithm 4);
@@ -36,10 +39,10 @@
  * (s mod 2^32, s div 2^32, t, b) under the key (k mod 2^32, k div 2^32),
  * low half first: x_2b = out0 + 2^32 out1, x_2b+1 = out2 + 2^32 out3.
  * Word schedule (x_i = word i):
- *   MOSS-4 : x0,x1 seed draw (column, threshold); x2,x3 sigma draw of u;
- *            x4 w; x5 r.
- *   T-5    : x0,x1 seed; x2,x3 sigma of u; x4 w; x5 r; x6 t.
- *   Path-5 : x0,x1 seed; x2 r; x3 t; attempt a in {0,1}: x(4+4a),x(5+4a)
+ *   MOSS-4 : x0,x1 seed draw (column, threshold), x6 its level; x2,x3 sigma
+ *            draw of u; x4 w; x5 r.
+ *   T-5    : x0,x1 seed, x7 its level; x2,x3 sigma of u; x4 w; x5 r; x6 t.
+ *   Path-5 : x0,x1 seed, x14 its level; x2 r; x3 t; attempt a in {0,1}: x(4+4a),x(5+4a)
  *            sigma draw of u, x(6+4a),x(7+4a) sigma draw of w, accepted when
  *            the two positions differ; if both attempts collide, x12 draws u
  *            from tau^(v) and x13 draws w from mu^(v,u) by the prefix-sum
@@ -51,6 +54,19 @@
 #include <string.h>
 
 typedef unsigned __int128 u128;
+
+/* WeightRandomVertex(V, .) in two levels: columns [0, nh) form the alias
+ * table of the heavy vertices (ascending ids), columns [nh, n) that of the
+ * light ones; each column keeps its own vertex with probability T / 2^64 and
+ * else gives its alias. */
+typedef struct {
+    uint32_t nh;        /* heavy vertices */
+    uint64_t TL;        /* the light level is drawn iff the level word < TL */
+    uint32_t *self;     /* vertex of each column */
+    u128 *thr;          /* threshold in units where a column holds its level's total */
+    uint64_t *T;        /* floor(thr 2^64 / level total), saturated */
+    uint32_t *alias;    /* alias vertex of each column */
+} vtab;
 
 enum { M_MOSS4 = 0, M_T5 = 1, M_P5 = 2 };
 
@@ -104,10 +120,9 @@ typedef struct {
     u128 *gam[3];       /* Gamma_v, Gamma^(1)_v, Gamma^(2)_v */
     u128 tot[3];        /* Gamma, Gamma^(1), Gamma^(2) */
     u128 lam3, lam4;
-    /* seed alias tables over V, one per weight */
-    u128 *sthr[3];      /* threshold in units where a column holds tot */
-    uint64_t *sT[3];    /* floor(thr 2^64 / tot), saturated */
-    uint32_t *salias[3];
+    /* two-level vertex tables over V, one per weight */
+    int vsplit;         /* heavy vertices: w_v 2^vsplit >= W */
+    vtab vt[3];
     /* sigma alias tables over each N_v (weights d_x - 1), local positions */
     uint64_t *gthr;
     uint32_t *galias;
@@ -118,9 +133,7 @@ typedef struct {
     uint64_t *rank;     /* slot (v->u): d_{v,u} = |{x in N_v : x > u}| */
     u128 *gmin;         /* Gamma-check_v = sum_{x in N_v} d_{v,x} d_{x,v} */
     u128 tmin;          /* Gamma-check */
-    u128 *mthr;         /* vertex alias table of Gamma-check */
-    uint64_t *mT;
-    uint32_t *malias;
+    vtab mvt;           /* vertex table of Gamma-check */
     uint64_t *cthr;     /* per-list alias tables of sigma-check (eq. 3) */
     uint32_t *calias;
 } ctx;
@@ -182,6 +195,73 @@ static uint64_t quantize(u128 thr, u128 W) {
     return q;
 }
 
+static void vtab_free(vtab *t) {
+    free(t->self); free(t->thr); free(t->T); free(t->alias);
+    t->self = NULL; t->thr = NULL; t->T = NULL; t->alias = NULL;
+}
+
+/* The two-level table of weights w[0..n) with total W: heavy iff
+ * w_v >= ceil(W / 2^split) (so at most 2^split of them); each level's table
+ * is the sweep over its vertices in ascending id order; the light level is
+ * drawn iff the level word < floor(W_L 2^64 / W).  split = 64: no heavy
+ * level, one table over all vertices.  W = 0: never drawn. */
+static int vtab_build(vtab *t, uint32_t n, const u128 *w, u128 W, int split) {
+    uint64_t n1 = n ? n : 1;
+    t->self = (uint32_t *)malloc(sizeof(uint32_t) * n1);
+    t->thr = (u128 *)malloc(sizeof(u128) * n1);
+    t->T = (uint64_t *)malloc(sizeof(uint64_t) * n1);
+    t->alias = (uint32_t *)malloc(sizeof(uint32_t) * n1);
+    u128 *sw = (u128 *)malloc(sizeof(u128) * n1);
+    u128 *st = (u128 *)malloc(sizeof(u128) * n1);
+    uint32_t *sa = (uint32_t *)malloc(sizeof(uint32_t) * n1);
+    if (!t->self || !t->thr || !t->T || !t->alias || !sw || !st || !sa) {
+        free(sw); free(st); free(sa);
+        vtab_free(t);
+        return -1;
+    }
+    t->nh = 0;
+    t->TL = 0;
+    if (W == 0) {
+        for (uint32_t v = 0; v < n; v++) { t->self[v] = v; t->thr[v] = 0; t->T[v] = 0; t->alias[v] = v; }
+        free(sw); free(st); free(sa);
+        return 0;
+    }
+    const int one_level = split >= 64;
+    u128 cut = one_level ? 0 : W >> split;
+    if (!one_level && (cut << split) != W) cut += 1;   /* ceil(W / 2^split) */
+    uint32_t k = 0;
+    u128 WH = 0;
+    for (uint32_t v = 0; v < n; v++)
+        if (!one_level && w[v] >= cut) { t->self[k++] = v; WH += w[v]; }
+    t->nh = k;
+    for (uint32_t v = 0; v < n; v++)
+        if (one_level || w[v] < cut) t->self[k++] = v;
+    const u128 WL = W - WH;
+    for (int level = 0; level < 2; level++) {
+        const uint32_t c0 = level == 0 ? 0 : t->nh, m = level == 0 ? t->nh : n - t->nh;
+        const u128 Wl = level == 0 ? WH : WL;
+        for (uint32_t i = 0; i < m; i++) sw[i] = w[t->self[c0 + i]];
+        if (alias_sweep(m, sw, st, sa)) { free(sw); free(st); free(sa); vtab_free(t); return -1; }
+        for (uint32_t i = 0; i < m; i++) {
+            t->thr[c0 + i] = st[i];
+            t->T[c0 + i] = quantize(st[i], Wl);
+            t->alias[c0 + i] = t->self[c0 + sa[i]];
+        }
+    }
+    t->TL = t->nh == 0 ? 0 : quantize(WL, W);
+    free(sw); free(st); free(sa);
+    return 0;
+}
+
+/* WeightRandomVertex with a two-level table: level word xl, column word xc,
+ * threshold word xt */
+static uint32_t vtab_draw(const vtab *t, uint32_t n, uint64_t xl, uint64_t xc, uint64_t xt) {
+    const int light = t->nh == 0 || xl < t->TL;
+    const uint64_t m = light ? n - t->nh : t->nh;
+    const uint64_t col = (light ? t->nh : 0) + index_of(xc, m);
+    return xt < t->T[col] ? t->self[col] : t->alias[col];
+}
+
 /* standalone entry for tests: weights as lo/hi u64 pairs */
 int oracle_alias_build(uint64_t m, const uint64_t *w_lohi, uint64_t *thr_lohi, uint32_t *alias) {
     u128 *w = (u128 *)malloc(sizeof(u128) * (m ? m : 1));
@@ -199,9 +279,9 @@ int oracle_alias_build(uint64_t m, const uint64_t *w_lohi, uint64_t *thr_lohi, u
 void oracle_free(ctx *c) {
     if (!c) return;
     free(c->off); free(c->col); free(c->deg); free(c->S); free(c->Q);
-    for (int l = 0; l < 3; l++) { free(c->gam[l]); free(c->sthr[l]); free(c->sT[l]); free(c->salias[l]); }
+    for (int l = 0; l < 3; l++) { free(c->gam[l]); vtab_free(&c->vt[l]); }
     free(c->gthr); free(c->galias); free(c->acc);
-    free(c->rlist); free(c->rank); free(c->gmin); free(c->mthr); free(c->mT); free(c->malias);
+    free(c->rlist); free(c->rank); free(c->gmin); vtab_free(&c->mvt);
     free(c->cthr); free(c->calias);
     free(c);
 }
@@ -213,10 +293,14 @@ static u128 choose(uint64_t d, int k) {
     return r;
 }
 
-ctx *oracle_new(uint32_t n, const uint64_t *row_ptr, const uint32_t *col) {
+/* vsplit: heavy vertices of the vertex tables have w_v 2^vsplit >= W (0..63;
+ * 64: one level) */
+ctx *oracle_new_split(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, int vsplit) {
+    if (vsplit < 0 || vsplit > 64) return NULL;
     ctx *c = (ctx *)calloc(1, sizeof(ctx));
     if (!c) return NULL;
     c->n = n;
+    c->vsplit = vsplit;
     c->nnz = row_ptr[n];
     uint64_t nnz1 = c->nnz ? c->nnz : 1;
     c->off = (uint64_t *)malloc(sizeof(uint64_t) * (n + 1));
@@ -242,10 +326,7 @@ ctx *oracle_new(uint32_t n, const uint64_t *row_ptr, const uint32_t *col) {
     }
     for (int l = 0; l < 3; l++) {
         c->gam[l] = (u128 *)malloc(sizeof(u128) * (n ? n : 1));
-        c->sthr[l] = (u128 *)malloc(sizeof(u128) * (n ? n : 1));
-        c->sT[l] = (uint64_t *)malloc(sizeof(uint64_t) * (n ? n : 1));
-        c->salias[l] = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
-        if (!c->gam[l] || !c->sthr[l] || !c->sT[l] || !c->salias[l]) { oracle_free(c); return NULL; }
+        if (!c->gam[l]) { oracle_free(c); return NULL; }
     }
     for (uint32_t v = 0; v < n; v++) {
         uint64_t d = c->deg[v];
@@ -261,10 +342,8 @@ ctx *oracle_new(uint32_t n, const uint64_t *row_ptr, const uint32_t *col) {
         c->lam4 += choose(d, 4);   /* Lambda_4 = sum C(d_v, 4)  (Sec. 5.1.3) */
     }
     /* WeightRandomVertex(V, pi), (V, rho^(1)), (V, rho^(2)) tables */
-    for (int l = 0; l < 3; l++) {
-        if (alias_sweep(n, c->gam[l], c->sthr[l], c->salias[l])) { oracle_free(c); return NULL; }
-        for (uint32_t v = 0; v < n; v++) c->sT[l][v] = quantize(c->sthr[l][v], c->tot[l]);
-    }
+    for (int l = 0; l < 3; l++)
+        if (vtab_build(&c->vt[l], n, c->gam[l], c->tot[l], c->vsplit)) { oracle_free(c); return NULL; }
     /* WeightRandomVertex(N_v, sigma^(v)) tables and ACC_sigma^(v) */
     u128 *w = (u128 *)malloc(sizeof(u128) * nnz1), *t = (u128 *)malloc(sizeof(u128) * nnz1);
     if (!w || !t) { free(w); free(t); oracle_free(c); return NULL; }
@@ -282,6 +361,11 @@ ctx *oracle_new(uint32_t n, const uint64_t *row_ptr, const uint32_t *col) {
     free(w);
     free(t);
     return c;
+}
+
+/* the default split: two levels (split 20) from 2^20 vertices, else one */
+ctx *oracle_new(uint32_t n, const uint64_t *row_ptr, const uint32_t *col) {
+    return oracle_new_split(n, row_ptr, col, n >= (1u << 20) ? 20 : 64);
 }
 
 /* --------------------------------------------------------- accessors ---- */
@@ -305,11 +389,17 @@ void oracle_vertex(const ctx *c, uint64_t *deg, uint64_t *S, uint64_t *Q, uint64
     }
 }
 
-void oracle_seed_table(const ctx *c, int l, uint64_t *thr_lohi, uint64_t *T, uint32_t *alias) {
+/* the two-level vertex table of weight l (0..2; 3: Gamma-check), column order */
+void oracle_vertex_table(const ctx *c, int l, uint32_t *nh, uint64_t *TL, uint32_t *self, uint64_t *thr_lohi,
+                         uint64_t *T, uint32_t *alias) {
+    const vtab *t = l == 3 ? &c->mvt : &c->vt[l];
+    *nh = t->nh;
+    *TL = t->TL;
     for (uint32_t v = 0; v < c->n; v++) {
-        put128(thr_lohi + 2 * (uint64_t)v, c->sthr[l][v]);
-        T[v] = c->sT[l][v];
-        alias[v] = c->salias[l][v];
+        self[v] = t->self[v];
+        put128(thr_lohi + 2 * (uint64_t)v, t->thr[v]);
+        T[v] = t->T[v];
+        alias[v] = t->alias[v];
     }
 }
 
@@ -398,10 +488,9 @@ static int classify_vertices(const ctx *c, int k, const uint32_t *x) {
 }
 
 /* ----------------------------------------------------------- sampling ---- */
-/* WeightRandomVertex(V, .) with the seed table of weight l */
-static uint32_t draw_seed(const ctx *c, int l, uint64_t xc, uint64_t xt) {
-    uint64_t col = index_of(xc, c->n);
-    return xt < c->sT[l][col] ? (uint32_t)col : c->salias[l][col];
+/* WeightRandomVertex(V, .) with the vertex table of weight l */
+static uint32_t draw_seed(const ctx *c, int l, uint64_t xl, uint64_t xc, uint64_t xt) {
+    return vtab_draw(&c->vt[l], c->n, xl, xc, xt);
 }
 
 /* WeightRandomVertex(N_v, sigma^(v)): returns the position in N_v */
@@ -462,7 +551,7 @@ static void draw_pair(const ctx *c, uint32_t v, const uint64_t *x, uint64_t *pu,
 static int sample_one(const ctx *c, int method, const uint64_t *x, uint32_t *out) {
     if (method == M_MOSS4) {
         /* Algorithm 1 */
-        uint32_t v = draw_seed(c, 0, x[0], x[1]);
+        uint32_t v = draw_seed(c, 0, x[6], x[0], x[1]);
         uint64_t ov = c->off[v], dv = c->deg[v];
         uint64_t iu = draw_sigma(c, v, x[2], x[3]);
         uint32_t u = c->col[ov + iu];
@@ -475,7 +564,7 @@ static int sample_one(const ctx *c, int method, const uint64_t *x, uint32_t *out
     }
     if (method == M_T5) {
         /* Algorithm 3 */
-        uint32_t v = draw_seed(c, 1, x[0], x[1]);
+        uint32_t v = draw_seed(c, 1, x[7], x[0], x[1]);
         uint64_t ov = c->off[v], dv = c->deg[v];
         uint64_t iu = draw_sigma(c, v, x[2], x[3]);
         uint32_t u = c->col[ov + iu];
@@ -489,7 +578,7 @@ static int sample_one(const ctx *c, int method, const uint64_t *x, uint32_t *out
         return classify_vertices(c, 5, out);
     }
     /* Algorithm 4 */
-    uint32_t v = draw_seed(c, 2, x[0], x[1]);
+    uint32_t v = draw_seed(c, 2, x[14], x[0], x[1]);
     uint64_t ov = c->off[v];
     uint64_t iu, iw;
     draw_pair(c, v, x, &iu, &iw);
@@ -601,13 +690,10 @@ int oracle_build_min(ctx *c) {
     c->rlist = (uint32_t *)malloc(sizeof(uint32_t) * nnz1);
     c->rank = (uint64_t *)malloc(sizeof(uint64_t) * nnz1);
     c->gmin = (u128 *)calloc(n1, sizeof(u128));
-    c->mthr = (u128 *)malloc(sizeof(u128) * n1);
-    c->mT = (uint64_t *)malloc(sizeof(uint64_t) * n1);
-    c->malias = (uint32_t *)malloc(sizeof(uint32_t) * n1);
     c->cthr = (uint64_t *)malloc(sizeof(uint64_t) * nnz1);
     c->calias = (uint32_t *)malloc(sizeof(uint32_t) * nnz1);
     uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * nnz1);
-    if (!c->rlist || !c->rank || !c->gmin || !c->mthr || !c->mT || !c->malias || !c->cthr || !c->calias || !keys) {
+    if (!c->rlist || !c->rank || !c->gmin || !c->cthr || !c->calias || !keys) {
         free(keys);
         return -1;
     }
@@ -644,8 +730,7 @@ int oracle_build_min(ctx *c) {
         if (alias_sweep(d, w, t, c->calias + o)) { free(keys); free(w); free(t); return -1; }
         for (uint64_t i = 0; i < d; i++) c->cthr[o + i] = (uint64_t)t[i];
     }
-    if (alias_sweep(c->n, c->gmin, c->mthr, c->malias)) { free(keys); free(w); free(t); return -1; }
-    for (uint32_t v = 0; v < c->n; v++) c->mT[v] = quantize(c->mthr[v], c->tmin);
+    if (vtab_build(&c->mvt, c->n, c->gmin, c->tmin, c->vsplit)) { free(keys); free(w); free(t); return -1; }
     free(keys);
     free(w);
     free(t);
@@ -686,12 +771,12 @@ static int min_slot(int cls, int cp) {
     return -1;
 }
 
-/* Algorithm 2 from explicit words: x0,x1 vertex draw, x2,x3 sigma-check draw
- * of u, x4 w (uniform in N_{v,u}), x5 r (uniform in N_{u,v}).  Returns the
- * class (0 = collision) and *cp = c(s) for classes 3, 5, 6 (else 0). */
+/* Algorithm 2 from explicit words: x0,x1 vertex draw (x6 its level), x2,x3
+ * sigma-check draw of u, x4 w (uniform in N_{v,u}), x5 r (uniform in
+ * N_{u,v}).  Returns the class (0 = collision) and *cp = c(s) for classes 3,
+ * 5, 6 (else 0). */
 static int sample_min(const ctx *c, const uint64_t *x, uint32_t *out, int *cp) {
-    uint64_t col = index_of(x[0], c->n);
-    uint32_t v = x[1] < c->mT[col] ? (uint32_t)col : c->malias[col];
+    uint32_t v = vtab_draw(&c->mvt, c->n, x[6], x[0], x[1]);
     uint64_t ov = c->off[v];
     uint64_t j = index_of(x[2], c->deg[v]);
     uint64_t y = index_of(x[3], (uint64_t)c->gmin[v]);
@@ -725,7 +810,7 @@ int oracle_min_words(const ctx *c, const uint64_t *words, uint32_t *verts, int *
 void oracle_min_total(const ctx *c, uint64_t *out) { put128(out, c->tmin); }
 
 void oracle_min_tables(const ctx *c, uint32_t *rlist, uint64_t *rank, uint64_t *cthr, uint32_t *calias,
-                       uint64_t *gmin_lohi, uint64_t *mT, uint32_t *malias) {
+                       uint64_t *gmin_lohi) {
     for (uint64_t p = 0; p < c->nnz; p++) {
         rlist[p] = c->rlist[p];
         rank[p] = c->rank[p];
@@ -734,8 +819,6 @@ void oracle_min_tables(const ctx *c, uint32_t *rlist, uint64_t *rank, uint64_t *
     }
     for (uint32_t v = 0; v < c->n; v++) {
         put128(gmin_lohi + 2 * (uint64_t)v, c->gmin[v]);
-        mT[v] = c->mT[v];
-        malias[v] = c->malias[v];
     }
 }
 

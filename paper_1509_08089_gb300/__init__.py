@@ -27,6 +27,7 @@ MOSS_EBUSY = -7
 MOSS4, T5, PATH5, MOSS4MIN = 0, 1, 2, 3
 PROBE_SEARCH, PROBE_HASH, PROBE_FILTER, PROBE_AUTO = 0, 1, 2, 3
 RNG_SPLITMIX64, RNG_PHILOX4X32 = 0, 1
+VERTEX_SPLIT_DEFAULT, VERTEX_ONE_LEVEL = 20, 64
 NSLOTS = 22
 TABLES_4MIN = 1 << 6
 TABLE_VERT, TABLE_SLOT, TABLE_ACC, TABLE_SEED0, TABLE_GAMMA0 = 0, 1, 2, 3, 6
@@ -99,6 +100,9 @@ def load():
         "moss_build_tables": ([_vp, ctypes.c_uint, _vp], ctypes.c_int),
         "moss_set_probe": ([_vp, ctypes.c_int], ctypes.c_int),
         "moss_set_rng": ([_vp, ctypes.c_int], ctypes.c_int),
+        "moss_set_vertex_split": ([_vp, ctypes.c_int], ctypes.c_int),
+        "moss_vertex_levels": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64)],
+                               ctypes.c_int),
         "moss_get_rng": ([_vp], ctypes.c_int),
         "moss_sample_estimate": ([_vp, ctypes.c_int, _u64, _u64, _vp, ctypes.POINTER(moss_result)], ctypes.c_int),
         "moss_sample_counts": ([_vp, ctypes.c_int, _u64, _u64, _u64, _vp, _vp], ctypes.c_int),
@@ -247,6 +251,17 @@ def moss_set_rng(g: int, rng: int):
 
 def moss_get_rng(g: int) -> int:
     return load().moss_get_rng(g)
+
+
+def moss_set_vertex_split(g: int, split: int):
+    _check(load().moss_set_vertex_split(g, split))
+
+
+def moss_vertex_levels(g: int, which: int) -> tuple[int, int]:
+    """(heavy columns, light-level bound) of vertex table which."""
+    nh, tl = ctypes.c_uint32(0), ctypes.c_uint64(0)
+    _check(load().moss_vertex_levels(g, which, ctypes.byref(nh), ctypes.byref(tl)))
+    return nh.value, tl.value
 
 
 def moss_sample_estimate(g: int, k: int, budget: int, seed: int, stream=None) -> moss_result:
@@ -575,11 +590,15 @@ class Graph:
     """Owning wrapper: load, build, sample, free."""
 
     def __init__(self, row_ptr, col, device: int = 0, stream=None, k_mask: int = (1 << 4) | (1 << 5),
-                 probe: int = PROBE_AUTO, rng: int = RNG_SPLITMIX64):
+                 probe: int = PROBE_AUTO, rng: int = RNG_SPLITMIX64, vsplit: int | None = None):
+        """vsplit: heavy level of the vertex tables (0..63, VERTEX_ONE_LEVEL;
+        None: the library's default for the graph's size)."""
         self.handle = moss_graph_load_csr(row_ptr, col, device=device, stream=stream)
         self.device = device
         moss_set_probe(self.handle, probe)
         moss_set_rng(self.handle, rng)
+        if vsplit is not None:
+            moss_set_vertex_split(self.handle, vsplit)
         self.k_mask = k_mask
         if k_mask:
             moss_build_tables(self.handle, k_mask, stream)

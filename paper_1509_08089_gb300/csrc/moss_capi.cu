@@ -218,6 +218,7 @@ struct moss_graph {
     void *arena = nullptr;       // every device array above lives in this one allocation
     int probe = MOSS_PROBE_AUTO; // membership tests (MOSS_PROBE_*), as requested
     int rng = MOSS_RNG_SPLITMIX64;   // word generator of the samples (MOSS_RNG_*)
+    int vsplit = MOSS_VERTEX_ONE_LEVEL;   // heavy level of the vertex tables: w_v 2^vsplit >= W (set at load)
     unsigned long long *hash = nullptr;  // kBucketKeys keys per bucket
     uint64_t hash_buckets = 0;
     uint32_t *filter = nullptr;  // Bloom filter in front of the hash
@@ -274,6 +275,10 @@ DevGraph view_with(const moss_graph *g, int eff) {
     d.defer = g->defer;
     d.n = g->n;
     d.rng = g->rng == MOSS_RNG_PHILOX4X32 ? kRngPhilox : kRngSplitMix;
+    for (int l = 0; l < kMethods; ++l) {
+        d.nheavy[l] = g->tot_h.level[l].nh;
+        d.tlight[l] = g->tot_h.level[l].tl;
+    }
     const bool use_hash = eff != MOSS_PROBE_SEARCH && (g->built >> 4 & 1u);
     const bool use_filter = eff == MOSS_PROBE_FILTER && (g->built >> 6 & 1u);
     d.hash = use_hash ? reinterpret_cast<const uint4 *>(g->hash) : nullptr;
@@ -410,6 +415,7 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
     if (!g) return fail(MOSS_ENOMEM, "host allocation");
     g->device = device;
     g->n = n;
+    g->vsplit = n >= (1u << 20) ? MOSS_VERTEX_SPLIT_DEFAULT : MOSS_VERTEX_ONE_LEVEL;
     g->nnz = nnz;
     void *rp_dev = nullptr;
     const size_t rp_bytes = (size_t)(n + 1ULL) * (row_ptr_is_64 ? 8 : 4);
@@ -510,8 +516,7 @@ static int build_min_tables(moss_graph *g, cudaStream_t s, const AuxStreams *aux
     if ((e = pool_alloc(g->device, &scratch, min_scratch_bytes(g->n, g->nnz), s)) != cudaSuccess)
         return cuda_fail(e, "allocating scratch");
     e = launch_min_tables(g->n, g->nnz, g->vert, g->col, g->owner, g->slot, g->mvert, g->mslot, g->mpick, g->rlist,
-                          g->gam[3],
-                          g->seed[3], g->tot, scratch, g->flags, s, aux);
+                          g->gam[3], g->seed[3], g->tot, scratch, g->flags, g->vsplit, s, aux);
     cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) return cuda_fail(e, "MOSS-4Min table kernels");
     return MOSS_OK;
@@ -594,7 +599,7 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
     }
     cudaError_t ev = cudaSuccess;
     if (e == cudaSuccess && nt > 0)
-        ev = launch_seed_alias(g->n, g->tot, nt, which, w, seed, vrec, seed_scratch, g->flags, sv);
+        ev = launch_seed_alias(g->n, g->tot, nt, which, w, seed, vrec, seed_scratch, g->flags, g->vsplit, sv);
     // per-list tables
     if (e == cudaSuccess)
         e = launch_sigma_alias(g->n, g->nnz, g->vert, g->acc, g->owner, g->slot, idx, pre, s, aux, 0);
@@ -653,6 +658,23 @@ int moss_set_rng(moss_graph *g, int rng) {
 }
 
 int moss_get_rng(const moss_graph *g) { return g ? g->rng : MOSS_EINVAL; }
+
+int moss_set_vertex_split(moss_graph *g, int split) {
+    if (!g) return fail(MOSS_EINVAL, "graph is NULL");
+    if (split < 0 || split > MOSS_VERTEX_ONE_LEVEL)
+        return fail(MOSS_EINVAL, "vertex split %d outside 0..%d", split, MOSS_VERTEX_ONE_LEVEL);
+    if (split != g->vsplit) g->built &= ~0xFu & ~(1u << 5);   // vertex tables follow at the next build
+    g->vsplit = split;
+    return MOSS_OK;
+}
+
+int moss_vertex_levels(const moss_graph *g, int which, uint32_t *nheavy, uint64_t *tlight) {
+    if (!g || !nheavy || !tlight) return fail(MOSS_EINVAL, "NULL argument");
+    if (which < 0 || which >= kMethods) return fail(MOSS_EINVAL, "which must be 0..3");
+    *nheavy = g->tot_h.level[which].nh;
+    *tlight = g->tot_h.level[which].tl;
+    return MOSS_OK;
+}
 
 static int sample_into(moss_graph *g, int method, uint64_t first, uint64_t count, uint64_t seed, cudaStream_t s,
                        uint64_t *counts_dev, uint8_t *classes, uint32_t *verts) {

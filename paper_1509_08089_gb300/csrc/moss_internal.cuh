@@ -71,11 +71,22 @@ __device__ __forceinline__ uint32_t slot_twin(const uint32_t *s32, uint64_t p) {
 // of sigma draws collides is flagged in a bitmap and redone by a second launch
 constexpr uint64_t kDeferChunk = 1ull << 26;
 
+// The split of a vertex table into its two levels: the heavy vertices
+// (w_v >= ceil(W / 2^split)) take columns [0, nh) in ascending id order, the
+// light ones columns [nh, n); a draw takes the light level when its level
+// word is below tl = floor(W_L 2^64 / W) (always when nh = 0).
+struct alignas(16) SeedLevel {
+    u128 WH, WL;                      // the levels' total weights
+    uint64_t tl;
+    uint32_t nh, pad;
+};
+
 struct alignas(16) DevTotals {
     u128 gamma[kMethods];             // Gamma, Gamma^(1), Gamma^(2), Gamma-check
     u128 lambda3, lambda4;            // Lambda_3, Lambda_4
     uint32_t d_max;
     uint32_t pad[3];
+    SeedLevel level[kMethods];        // the vertex tables' levels
 };
 
 struct DevGraph {
@@ -97,6 +108,8 @@ struct DevGraph {
     uint32_t filter_shift;  // 64 - log2(filter words)
     uint32_t n;
     uint32_t rng;           // word generator: kRngSplitMix or kRngPhilox
+    uint32_t nheavy[kMethods];   // heavy columns of each vertex table (SeedLevel)
+    uint64_t tlight[kMethods];   // light-level bound of each vertex table
 };
 
 // ------------------------------------------------------- hashed edge set --
@@ -270,6 +283,13 @@ __device__ __forceinline__ Words2 sample_words2(uint64_t seed, uint32_t t, uint6
     return w;
 }
 
+// word i of sample s of method t under generator RNG alone
+template <int RNG>
+__device__ __forceinline__ uint64_t sample_word(uint64_t seed, uint32_t t, uint64_t s, uint32_t i) {
+    const Words2 w = sample_words2<RNG>(seed, t, s, i >> 1);
+    return w.x[i & 1];
+}
+
 // ----------------------------------------------------- host-side launches --
 // Auxiliary streams of the calling host thread on one device, with the
 // events of one fork (a[0..2] each wait for what was queued on s), one join
@@ -311,11 +331,12 @@ cudaError_t launch_edge_filter(uint64_t nnz, const uint32_t *col, const uint32_t
 cudaError_t launch_sigma_alias(uint32_t n, uint64_t nnz, const uint4 *vert, const uint32_t *acc, const uint32_t *owner,
                                uint4 *slot, uint32_t *scratch_idx, uint64_t *scratch_pre, cudaStream_t s,
                                const AuxStreams *aux, int long_stream);
-// vertex alias tables of up to 3 weights in the same launches (seed[t]: 2n
-// uint4, vrec[t]: the n vertex records copied beside each alias); scratch of
-// seed_scratch_bytes(n) bytes
-cudaError_t launch_seed_alias(uint32_t n, const DevTotals *tot, int ntables, const int *which, u128 *const *w,
-                              uint4 *const *seed, const uint4 *const *vrec, void *scratch, uint32_t *flags,
+// two-level vertex alias tables of up to 3 weights in the same launches
+// (seed[t]: 2n uint4, vrec[t]: the n vertex records copied beside each
+// alias; the levels go to tot->level[which[t]]; heavy: w_v 2^split >= W;
+// split 64: one table over all vertices); scratch of seed_scratch_bytes(n) bytes
+cudaError_t launch_seed_alias(uint32_t n, DevTotals *tot, int ntables, const int *which, u128 *const *w,
+                              uint4 *const *seed, const uint4 *const *vrec, void *scratch, uint32_t *flags, int split,
                               cudaStream_t s);
 uint64_t seed_scratch_bytes(uint32_t n);
 int table_blocks(uint32_t n);
@@ -327,7 +348,7 @@ uint64_t min_scratch_bytes(uint32_t n, uint64_t nnz);
 cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const uint32_t *col,
                               const uint32_t *owner, const uint4 *slot, uint4 *mvert, uint4 *mslot, uint4 *mpick,
                               uint2 *rlist, u128 *gmin, uint4 *seed_min, DevTotals *tot, void *scratch,
-                              uint32_t *flags, cudaStream_t s, const AuxStreams *aux);
+                              uint32_t *flags, int split, cudaStream_t s, const AuxStreams *aux);
 
 // moss_sample.cu
 // class of each 4- and 5-vertex edge mask; c(s) of MOSS-4Min by (mask << 6 | order bits)

@@ -529,7 +529,7 @@ uint64_t min_scratch_bytes(uint32_t n, uint64_t nnz) { return carve(nullptr, n, 
 cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const uint32_t *col,
                               const uint32_t *owner, const uint4 *slot, uint4 *mvert, uint4 *mslot, uint4 *mpick,
                               uint2 *rlist, u128 *gmin, uint4 *seed_min, DevTotals *tot, void *scratch,
-                              uint32_t *flags, cudaStream_t s, const AuxStreams *aux) {
+                              uint32_t *flags, int split, cudaStream_t s, const AuxStreams *aux) {
     // With helper streams h0, h1 (aux->a[3], a[4]): the three sort tiers side
     // by side (disjoint lists), then the slot records on s; the short-list
     // alias tables, the total and the vertex table on s, beside the long-list
@@ -603,7 +603,7 @@ cudaError_t launch_min_tables(uint32_t n, uint64_t nnz, const uint4 *vert, const
         u128 *w[1] = {gmin};
         uint4 *sd[1] = {seed_min};
         const uint4 *vr[1] = {mvert};
-        e = launch_seed_alias(n, tot, 1, which, w, sd, vr, m.seed, flags, s);
+        e = launch_seed_alias(n, tot, 1, which, w, sd, vr, m.seed, flags, split, s);
     }
     join(1);
     return e != cudaSuccess ? e : eh;

@@ -16,11 +16,13 @@
 // Word schedule (x_i = word i of the sample, output (4 s + method) 16 + i + 1
 // of SplitMix64 seeded with seed, or Philox4x32-10 block i / 2; sample_words2
 // in moss_internal.cuh):
-//   MOSS-4 : x0,x1 vertex draw; x2,x3 sigma draw of u; x4 w; x5 r.
-//   T-5    : x0,x1 vertex draw; x2,x3 sigma of u; x4 w; x5 r; x6 t.
-//   MOSS-4Min: x0,x1 vertex draw (pi-check); x2,x3 sigma-check draw of u;
-//            x4 w (uniform in N_{v,u}); x5 r (uniform in N_{u,v}).
-//   Path-5 : x0,x1 vertex draw; x2 r; x3 t; attempts a = 0,1 use
+//   MOSS-4 : x0,x1 vertex draw (column, threshold), x6 its level; x2,x3 sigma
+//            draw of u; x4 w; x5 r.
+//   T-5    : x0,x1 vertex draw, x7 its level; x2,x3 sigma of u; x4 w; x5 r;
+//            x6 t.
+//   MOSS-4Min: x0,x1 vertex draw (pi-check), x6 its level; x2,x3 sigma-check
+//            draw of u; x4 w (uniform in N_{v,u}); x5 r (uniform in N_{u,v}).
+//   Path-5 : x0,x1 vertex draw, x14 its level; x2 r; x3 t; attempts a = 0,1 use
 //            x(4+4a)..x(7+4a) for two independent sigma draws (u, w), kept
 //            when the positions differ (sigma_u sigma_w / (1 - sum sigma^2)
 //            is exactly tau_u mu_w of Sec. 5.1.2); if both collide, x12 draws
@@ -93,16 +95,26 @@ struct VertexPick {
 
 // WeightRandomVertex(V, .) through a vertex alias table whose 32-byte column
 // records carry the alias's vertex record: one load, plus the column's own
-// record only when the column keeps the draw.  HINT (graphs behind the edge
-// filter): the record is read evict-first, since that table is as large as
-// the L2 and drawn uniformly, so a line is rarely read twice.
-template <bool HINT>
-__device__ __forceinline__ VertexPick draw_vertex(const uint4 *seed, const uint4 *vrec, uint32_t n, uint64_t xc,
-                                                  uint64_t xt) {
-    const uint32_t c = (uint32_t)word_index(xc, n);
-    const Sector r = HINT ? ld8_first(seed + 2 * (uint64_t)c) : ld8(seed + 2 * (uint64_t)c);
+// record only when the column keeps the draw.  The table has two levels: the
+// level word picks the light one (columns nh..n-1) when it is below the
+// level's bound, else the heavy one (columns 0..nh-1: the few vertices that
+// carry almost all the weight, a table small enough to stay cached).  HINT
+// (graphs behind the edge filter): a light record is read evict-first, since
+// that table is as large as the L2 and drawn uniformly, so a line is rarely
+// read twice.
+// The level word (word lw of the sample) is generated only for a table with
+// a heavy level (uniform across the launch).
+template <bool HINT, int RNG>
+__device__ __forceinline__ VertexPick draw_vertex(const DevGraph &g, int l, const uint4 *vrec, uint64_t seed,
+                                                  uint64_t s, uint32_t lw, uint64_t xc, uint64_t xt) {
+    const uint32_t nh = g.nheavy[l];
+    bool light = true;
+    if (nh != 0) light = sample_word<RNG>(seed, (uint32_t)l, s, lw) < g.tlight[l];
+    const uint32_t c = (light ? nh : 0u) + (uint32_t)word_index(xc, light ? g.n - nh : nh);
+    const uint4 *rec = g.seed[l] + 2 * (uint64_t)c;
+    const Sector r = HINT && light ? ld8_first(rec) : ld8(rec);   // {T lo, T hi, alias, self} {alias's record}
     const uint64_t T = ((uint64_t)r.lo.y << 32) | r.lo.x;
-    if (xt < T) return VertexPick{c, ld4(vrec + c)};
+    if (xt < T) return VertexPick{r.lo.w, ld4(vrec + r.lo.w)};
     return VertexPick{r.lo.z, r.hi};
 }
 
@@ -235,7 +247,7 @@ template <int RNG, bool HASH, bool HINT = false>
 __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
     const Words2 x01 = sample_words2<RNG>(seed, 0, s, 0);
-    const VertexPick pv = draw_vertex<HINT>(g.seed[0], g.vert, g.n, x01.x[0], x01.x[1]);
+    const VertexPick pv = draw_vertex<HINT, RNG>(g, 0, g.vert, seed, s, 6, x01.x[0], x01.x[1]);   // x6: level
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
     const Words2 x23 = sample_words2<RNG>(seed, 0, s, 1);
@@ -270,7 +282,7 @@ template <int RNG, bool HASH, bool HINT = false>
 __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
     const Words2 x01 = sample_words2<RNG>(seed, 1, s, 0);
-    const VertexPick pv = draw_vertex<HINT>(g.seed[1], g.vert, g.n, x01.x[0], x01.x[1]);
+    const VertexPick pv = draw_vertex<HINT, RNG>(g, 1, g.vert, seed, s, 7, x01.x[0], x01.x[1]);   // x7: level
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
     const Words2 x23 = sample_words2<RNG>(seed, 1, s, 1);
@@ -280,8 +292,7 @@ __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lu
     const uint32_t jr = skip2((uint32_t)word_index(x45.x[1], vr.y - 2), pu.pos, jw);
     const uint32_t w = ld1(g.col + vr.x + jw);
     const uint32_t r = ld1(g.col + vr.x + jr);
-    const Words2 x67 = sample_words2<RNG>(seed, 1, s, 3);
-    const uint32_t jt = skip1((uint32_t)word_index(x67.x[0], pu.deg - 1), pu.twin);
+    const uint32_t jt = skip1((uint32_t)word_index(sample_word<RNG>(seed, 1, s, 6), pu.deg - 1), pu.twin);
     const uint32_t t = ld1(g.col + pu.off + jt);
     out.v[0] = v; out.v[1] = pu.id; out.v[2] = w; out.v[3] = r; out.v[4] = t;
     if (t == w || t == r) {
@@ -336,7 +347,7 @@ __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *l
                                              uint64_t s) {
     Sample out;
     const Words2 x01 = sample_words2<RNG>(seed, 3, s, 0);
-    const VertexPick pv = draw_vertex<HINT>(g.seed[3], g.mvert, g.n, x01.x[0], x01.x[1]);
+    const VertexPick pv = draw_vertex<HINT, RNG>(g, 3, g.mvert, seed, s, 6, x01.x[0], x01.x[1]);   // x6: level
     const uint32_t v = pv.v;
     const uint4 mv = pv.rec;                           // {off, d_v, Gamma-check_v}
     const uint64_t Gv = ((uint64_t)mv.w << 32) | mv.z;
@@ -446,7 +457,7 @@ template <int RNG, bool HASH, int STAGE, bool HINT = false>
 __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
     const Words2 x01 = sample_words2<RNG>(seed, 2, s, 0);
-    const VertexPick pv = draw_vertex<HINT>(g.seed[2], g.vert, g.n, x01.x[0], x01.x[1]);
+    const VertexPick pv = draw_vertex<HINT, RNG>(g, 2, g.vert, seed, s, 14, x01.x[0], x01.x[1]);   // x14: level
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
     Pick pu, pw;

@@ -519,27 +519,46 @@ struct alignas(16) SeedAgg {
     uint32_t nl, nh, pad0, pad1;
 };
 
-// One vertex table being built: weights, output, and its scratch.
+// One level of one vertex table being built: weights, output, and its
+// scratch.  Items are the level's columns: item j is column base + j, the
+// vertex perm[base + j], with weight w[vertex]; base, the item count and the
+// level's total are read from the table's SeedLevel (filled by the split
+// kernels before).
 struct SeedTask {
     const u128 *w;
-    uint4 *seed;       // 2 per column: {T, alias, 0} and the alias's vertex record
-    const uint4 *vrec; // vertex records copied into seed
-    uint32_t *idx;     // n: lights from the front, heavies from the back
-    u128 *pre;         // n: A_i (lights) / P_k (heavies)
+    uint4 *seed;           // 2 per column: {T lo, T hi, alias, self} and the alias's vertex record
+    const uint4 *vrec;     // vertex records copied into seed
+    const uint32_t *perm;  // column -> vertex (heavy ids ascending, then light ids ascending); null: identity
+    int level;             // 0: the heavy columns [0, nh); 1: the light ones [nh, n); 2: one level, all n
+    uint32_t *idx;         // items: lights from the front, heavies from the back (of the level's count)
+    u128 *pre;             // A_i (lights) / P_k (heavies)
     SeedSplit *split;
-    SeedAgg *agg;      // one per chunk
-    int which;         // 0 Gamma, 1 Gamma^(1), 2 Gamma^(2)
+    SeedAgg *agg;          // one per chunk
+    int which;             // 0 Gamma, 1 Gamma^(1), 2 Gamma^(2), 3 Gamma-check
 };
 struct SeedTasks {
-    SeedTask t[3];
+    SeedTask t[2 * 3];
 };
 
-__device__ __forceinline__ void seed_item(const SeedTask &T, uint64_t j, uint32_t n, u128 W, bool &light,
-                                          bool &heavy, u128 &D, u128 &E) {
+__device__ __forceinline__ uint32_t task_base(const SeedTask &T, const DevTotals *tot) {
+    return T.level == 1 ? tot->level[T.which].nh : 0u;
+}
+__device__ __forceinline__ uint32_t task_items(const SeedTask &T, const DevTotals *tot, uint32_t n) {
+    return T.level == 2 ? n : T.level == 1 ? n - tot->level[T.which].nh : tot->level[T.which].nh;
+}
+__device__ __forceinline__ u128 task_total(const SeedTask &T, const DevTotals *tot) {
+    return T.level == 2 ? tot->gamma[T.which] : T.level == 1 ? tot->level[T.which].WL : tot->level[T.which].WH;
+}
+__device__ __forceinline__ uint32_t task_vertex(const SeedTask &T, uint32_t column) {
+    return T.perm ? T.perm[column] : column;
+}
+
+__device__ __forceinline__ void seed_item(const SeedTask &T, uint64_t j, uint32_t m, uint32_t base, u128 W,
+                                          bool &light, bool &heavy, u128 &D, u128 &E) {
     light = heavy = false;
     D = E = 0;
-    if (j < n) {
-        const u128 q = T.w[j] * (u128)n;
+    if (j < m) {
+        const u128 q = T.w[task_vertex(T, base + (uint32_t)j)] * (u128)m;
         light = q < W;
         heavy = !light;
         if (light) D = W - q; else E = q - W;
@@ -585,13 +604,154 @@ __device__ __forceinline__ void block_scan4(bool light, bool heavy, u128 D, u128
     __syncthreads();
 }
 
+// floor(thr 2^64 / W) for thr <= W, saturated (binary long division)
+__device__ __forceinline__ uint64_t quantize64(u128 thr, u128 W) {
+    if (W == 0) return 0;
+    if (thr >= W) return ~0ULL;
+    uint64_t qq = 0;
+    u128 r = thr;
+    for (int i = 0; i < 64; ++i) {
+        const bool carry = (uint64_t)(r >> 127) != 0;
+        r <<= 1;
+        qq <<= 1;
+        if (carry || r >= W) { r -= W; qq |= 1; }
+    }
+    return qq;
+}
+
+// ---- the split into levels (per table): heavy iff w_v >= ceil(W / 2^split)
+struct LevelTask {
+    const u128 *w;
+    uint32_t *perm;
+    SeedAgg *agg;          // per chunk: nh (heavies) and E (their weight), then their exclusive offsets
+    int which;
+};
+struct LevelTasks {
+    LevelTask t[3];
+};
+
+__device__ __forceinline__ u128 heavy_cut(u128 W, int split) {
+    u128 c = W >> split;
+    if ((c << split) != W) c += 1;
+    return c;
+}
+
+// per-chunk count and weight of the heavy vertices (and the overflow check
+// of the whole table: w_v n must fit 128 bits)
+__global__ void __launch_bounds__(kSeedThreads) k_level_count(uint32_t n, const DevTotals *tot, LevelTasks tasks,
+                                                             int split, uint32_t *flags) {
+    const LevelTask &T = tasks.t[blockIdx.y];
+    const u128 W = tot->gamma[T.which];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && n > 1 && W > (~(u128)0) / n) atomicOr(flags, kErrOverflow);
+    if (W == 0) return;
+    const u128 cut = heavy_cut(W, split);
+    const uint64_t base = (uint64_t)blockIdx.x * kSeedChunk;
+    SeedAgg acc;
+    acc.nl = acc.nh = 0;
+    acc.D = acc.E = 0;
+    for (int r = 0; r < kSeedRounds; ++r) {
+        const uint64_t j = base + (uint64_t)r * kSeedThreads + threadIdx.x;
+        const bool heavy = j < n && T.w[j] >= cut;
+        uint32_t xl, xh;
+        u128 xD, xE;
+        SeedAgg t;
+        block_scan4(false, heavy, 0, heavy ? T.w[j] : 0, xl, xh, xD, xE, t);
+        acc.nh += t.nh;
+        acc.E += t.E;
+    }
+    if (threadIdx.x == 0) T.agg[blockIdx.x] = acc;
+}
+
+// exclusive offsets of the chunks (one block per table) and the level record
+__global__ void __launch_bounds__(kSeedThreads) k_level_offsets(uint32_t chunks, DevTotals *tot, LevelTasks tasks) {
+    const LevelTask &T = tasks.t[blockIdx.x];
+    const u128 W = tot->gamma[T.which];
+    SeedLevel &L = tot->level[T.which];
+    if (W == 0) {
+        if (threadIdx.x == 0) { L.nh = 0; L.tl = 0; L.WH = 0; L.WL = 0; }
+        return;
+    }
+    __shared__ uint32_t run_h;
+    __shared__ u128 run_E;
+    __shared__ uint32_t sh[kSeedThreads];
+    __shared__ u128 sE[kSeedThreads];
+    if (threadIdx.x == 0) { run_h = 0; run_E = 0; }
+    __syncthreads();
+    for (uint32_t b0 = 0; b0 < chunks; b0 += kSeedThreads) {
+        const uint32_t b = b0 + threadIdx.x;
+        uint32_t h = 0;
+        u128 E = 0;
+        if (b < chunks) { h = T.agg[b].nh; E = T.agg[b].E; }
+        sh[threadIdx.x] = h;
+        sE[threadIdx.x] = E;
+        __syncthreads();
+        for (int d = 1; d < kSeedThreads; d <<= 1) {   // inclusive scan (Hillis-Steele)
+            uint32_t h2 = 0;
+            u128 E2 = 0;
+            if ((int)threadIdx.x >= d) { h2 = sh[threadIdx.x - d]; E2 = sE[threadIdx.x - d]; }
+            __syncthreads();
+            sh[threadIdx.x] += h2;
+            sE[threadIdx.x] += E2;
+            __syncthreads();
+        }
+        if (b < chunks) {
+            T.agg[b].nh = run_h + sh[threadIdx.x] - h;
+            T.agg[b].E = run_E + sE[threadIdx.x] - E;
+        }
+        __syncthreads();
+        if (threadIdx.x == kSeedThreads - 1) { run_h += sh[threadIdx.x]; run_E += sE[threadIdx.x]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        L.nh = run_h;
+        L.WH = run_E;
+        L.WL = W - run_E;
+        L.tl = run_h ? quantize64(W - run_E, W) : 0;
+    }
+}
+
+// column order: every heavy vertex at its rank among the heavies, every light
+// one at nh + its rank among the lights (a table of total 0: the identity)
+__global__ void __launch_bounds__(kSeedThreads) k_level_place(uint32_t n, const DevTotals *tot, LevelTasks tasks,
+                                                             int split) {
+    const LevelTask &T = tasks.t[blockIdx.y];
+    const u128 W = tot->gamma[T.which];
+    const uint64_t base = (uint64_t)blockIdx.x * kSeedChunk;
+    if (W == 0) {
+        for (int r = 0; r < kSeedRounds; ++r) {
+            const uint64_t j = base + (uint64_t)r * kSeedThreads + threadIdx.x;
+            if (j < n) T.perm[j] = (uint32_t)j;
+        }
+        return;
+    }
+    const u128 cut = heavy_cut(W, split);
+    const uint32_t nh = tot->level[T.which].nh;
+    uint32_t before = T.agg[blockIdx.x].nh;   // heavies in earlier chunks
+    for (int r = 0; r < kSeedRounds; ++r) {
+        const uint64_t j = base + (uint64_t)r * kSeedThreads + threadIdx.x;
+        const bool heavy = j < n && T.w[j] >= cut;
+        uint32_t xl, xh;
+        u128 xD, xE;
+        SeedAgg t;
+        block_scan4(false, heavy, 0, 0, xl, xh, xD, xE, t);
+        if (j < n) {
+            const uint32_t hb = before + xh;   // heavies before j
+            T.perm[heavy ? hb : nh + ((uint32_t)j - hb)] = (uint32_t)j;
+        }
+        before += t.nh;
+    }
+}
+
+// ---- the alias table of each level, in four phases (closed form of the sweep)
 // phase 1: per-chunk aggregates
 __global__ void __launch_bounds__(kSeedThreads) k_seed_count(uint32_t n, const DevTotals *tot, SeedTasks tasks,
                                                             uint32_t *flags) {
     const SeedTask &T = tasks.t[blockIdx.y];
-    const u128 W = tot->gamma[T.which];
-    if (blockIdx.x == 0 && threadIdx.x == 0 && n > 1 && W > (~(u128)0) / n) atomicOr(flags, kErrOverflow);
+    const u128 W = task_total(T, tot);
+    // one level: the overflow check of the table (w_v n must fit 128 bits) is here
+    if (flags && blockIdx.x == 0 && threadIdx.x == 0 && n > 1 && W > (~(u128)0) / n) atomicOr(flags, kErrOverflow);
     if (W == 0) return;
+    const uint32_t m = task_items(T, tot, n), b0 = task_base(T, tot);
     const uint64_t base = (uint64_t)blockIdx.x * kSeedChunk;
     SeedAgg acc;
     acc.nl = acc.nh = 0;
@@ -599,7 +759,7 @@ __global__ void __launch_bounds__(kSeedThreads) k_seed_count(uint32_t n, const D
     for (int r = 0; r < kSeedRounds; ++r) {
         bool light, heavy;
         u128 D, E;
-        seed_item(T, base + (uint64_t)r * kSeedThreads + threadIdx.x, n, W, light, heavy, D, E);
+        seed_item(T, base + (uint64_t)r * kSeedThreads + threadIdx.x, m, b0, W, light, heavy, D, E);
         uint32_t xl, xh;
         u128 xD, xE;
         SeedAgg t;
@@ -612,11 +772,18 @@ __global__ void __launch_bounds__(kSeedThreads) k_seed_count(uint32_t n, const D
     if (threadIdx.x == 0) T.agg[blockIdx.x] = acc;
 }
 
-// phase 2: exclusive scan of the chunk aggregates (one block per table)
+// phase 2: exclusive scan of the chunk aggregates (one block per level)
 __global__ void __launch_bounds__(kSeedThreads) k_seed_offsets(uint32_t chunks, const DevTotals *tot,
                                                               SeedTasks tasks) {
     const SeedTask &T = tasks.t[blockIdx.x];
-    if (tot->gamma[T.which] == 0) {
+    if (T.level == 2 && threadIdx.x == 0) {   // one level: the record says so (no heavy vertex)
+        SeedLevel &L = const_cast<DevTotals *>(tot)->level[T.which];
+        L.nh = 0;
+        L.tl = 0;
+        L.WH = 0;
+        L.WL = tot->gamma[T.which];
+    }
+    if (task_total(T, tot) == 0) {
         if (threadIdx.x == 0) { T.split->nl = 0; T.split->nh = 0; T.split->total = 0; }
         return;
     }
@@ -668,15 +835,16 @@ __global__ void __launch_bounds__(kSeedThreads) k_seed_offsets(uint32_t chunks, 
 // phase 3: place every item at its split position with its prefix
 __global__ void __launch_bounds__(kSeedThreads) k_seed_place(uint32_t n, const DevTotals *tot, SeedTasks tasks) {
     const SeedTask &T = tasks.t[blockIdx.y];
-    const u128 W = tot->gamma[T.which];
+    const u128 W = task_total(T, tot);
     if (W == 0) return;
+    const uint32_t m = task_items(T, tot, n), b0 = task_base(T, tot);
     const uint64_t base = (uint64_t)blockIdx.x * kSeedChunk;
     SeedAgg off = T.agg[blockIdx.x];
     for (int r = 0; r < kSeedRounds; ++r) {
         const uint64_t j = base + (uint64_t)r * kSeedThreads + threadIdx.x;
         bool light, heavy;
         u128 D, E;
-        seed_item(T, j, n, W, light, heavy, D, E);
+        seed_item(T, j, m, b0, W, light, heavy, D, E);
         uint32_t xl, xh;
         u128 xD, xE;
         SeedAgg t;
@@ -687,8 +855,8 @@ __global__ void __launch_bounds__(kSeedThreads) k_seed_place(uint32_t n, const D
             T.pre[rnk] = off.D + xD;                       // exclusive A_i
         } else if (heavy) {
             const uint32_t rnk = off.nh + xh;
-            T.idx[n - 1 - rnk] = (uint32_t)j;
-            T.pre[n - 1 - rnk] = off.E + xE + E;           // inclusive P_k
+            T.idx[m - 1 - rnk] = (uint32_t)j;
+            T.pre[m - 1 - rnk] = off.E + xE + E;           // inclusive P_k
         }
         off.nl += t.nl;
         off.nh += t.nh;
@@ -697,33 +865,22 @@ __global__ void __launch_bounds__(kSeedThreads) k_seed_place(uint32_t n, const D
     }
 }
 
-// floor(thr 2^64 / W) for thr <= W, saturated (binary long division)
-__device__ __forceinline__ uint64_t quantize64(u128 thr, u128 W) {
-    if (W == 0) return 0;
-    if (thr >= W) return ~0ULL;
-    uint64_t qq = 0;
-    u128 r = thr;
-    for (int i = 0; i < 64; ++i) {
-        const bool carry = (uint64_t)(r >> 127) != 0;
-        r <<= 1;
-        qq <<= 1;
-        if (carry || r >= W) { r -= W; qq |= 1; }
-    }
-    return qq;
-}
-
-// phase 4: thresholds and aliases, one thread per position of the split order
+// phase 4: thresholds and aliases, one thread per position of the split
+// order; records {T lo, T hi, alias, self} + the alias's vertex record at the
+// item's column
 __global__ void k_seed_fill(uint32_t n, const DevTotals *tot, SeedTasks tasks) {
     const SeedTask &T = tasks.t[blockIdx.y];
-    const u128 W = tot->gamma[T.which];
+    const u128 W = task_total(T, tot);
+    const uint32_t m = task_items(T, tot, n), b0 = task_base(T, tot);
     const uint32_t *idx = T.idx;
     const u128 *pre = T.pre;
     const uint32_t nl = T.split->nl, nh = T.split->nh;
     const u128 Ptot = T.split->total;
-    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n; p += (uint64_t)gridDim.x * blockDim.x) {
-        if (W == 0) {
-            T.seed[2 * p] = make_uint4(0u, 0u, (uint32_t)p, 0u);
-            T.seed[2 * p + 1] = T.vrec[p];
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < m; p += (uint64_t)gridDim.x * blockDim.x) {
+        if (W == 0) {   // a level without weight is never drawn
+            const uint32_t v = task_vertex(T, b0 + (uint32_t)p);
+            T.seed[2 * (uint64_t)(b0 + p)] = make_uint4(0u, 0u, v, v);
+            T.seed[2 * (uint64_t)(b0 + p) + 1] = T.vrec[v];
             continue;
         }
         const uint32_t j = idx[p];
@@ -734,12 +891,12 @@ __global__ void k_seed_fill(uint32_t n, const DevTotals *tot, SeedTasks tasks) {
             uint32_t lo = 0, len = nh;
             while (len > 0) {
                 uint32_t half = len >> 1;
-                if (pre[n - 1 - (lo + half)] < A) { lo += half + 1; len -= half + 1; } else { len = half; }
+                if (pre[m - 1 - (lo + half)] < A) { lo += half + 1; len -= half + 1; } else { len = half; }
             }
-            thr = T.w[j] * (u128)n;
-            alias = idx[n - 1 - lo];
+            thr = T.w[task_vertex(T, b0 + j)] * (u128)m;
+            alias = idx[m - 1 - lo];
         } else {
-            const uint32_t k = (uint32_t)(n - 1 - p);
+            const uint32_t k = (uint32_t)(m - 1 - p);
             const u128 Pk = pre[p];
             if (Pk < Ptot) {
                 uint32_t lo = 0, len = nl;
@@ -749,15 +906,16 @@ __global__ void k_seed_fill(uint32_t n, const DevTotals *tot, SeedTasks tasks) {
                 }
                 const u128 Ai = lo < nl ? pre[lo] : Ptot;
                 thr = W + Pk - Ai;
-                alias = idx[n - 1 - (k + 1)];
+                alias = idx[m - 1 - (k + 1)];
             } else {
                 thr = W;
                 alias = j;
             }
         }
         const uint64_t Tq = quantize64(thr, W);
-        T.seed[2 * (uint64_t)j] = make_uint4((uint32_t)Tq, (uint32_t)(Tq >> 32), alias, 0u);
-        T.seed[2 * (uint64_t)j + 1] = T.vrec[alias];
+        const uint32_t av = task_vertex(T, b0 + alias), sv = task_vertex(T, b0 + j);
+        T.seed[2 * (uint64_t)(b0 + j)] = make_uint4((uint32_t)Tq, (uint32_t)(Tq >> 32), av, sv);
+        T.seed[2 * (uint64_t)(b0 + j) + 1] = T.vrec[av];
     }
 }
 
@@ -888,16 +1046,21 @@ cudaError_t launch_sigma_alias(uint32_t n, uint64_t nnz, const uint4 *vert, cons
 
 uint64_t seed_scratch_bytes(uint32_t n) {
     const uint64_t chunks = ((uint64_t)n + kSeedChunk - 1) / kSeedChunk;
-    const uint64_t per = (uint64_t)n * 4 + 256 + (uint64_t)n * 16 + 256 + sizeof(SeedSplit) + 256 +
-                         chunks * sizeof(SeedAgg) + 256;
-    return 3 * per;
+    // per table: the column order and the split's chunk aggregates; per level:
+    // the split order, its prefixes, its totals and chunk aggregates
+    const uint64_t table = (uint64_t)n * 4 + 256 + chunks * sizeof(SeedAgg) + 256;
+    const uint64_t level = (uint64_t)n * 4 + 256 + (uint64_t)n * 16 + 256 + sizeof(SeedSplit) + 256 +
+                           chunks * sizeof(SeedAgg) + 256;
+    return 3 * (table + 2 * level);
 }
 
-cudaError_t launch_seed_alias(uint32_t n, const DevTotals *tot, int ntables, const int *which, u128 *const *w,
-                              uint4 *const *seed, const uint4 *const *vrec, void *scratch, uint32_t *flags,
+cudaError_t launch_seed_alias(uint32_t n, DevTotals *tot, int ntables, const int *which, u128 *const *w,
+                              uint4 *const *seed, const uint4 *const *vrec, void *scratch, uint32_t *flags, int split,
                               cudaStream_t s) {
-    if (ntables < 1 || ntables > 3) return cudaErrorInvalidValue;
+    if (ntables < 1 || ntables > 3 || split < 0 || split > 64) return cudaErrorInvalidValue;
+    const bool one_level = split == 64;   // one table over all vertices, in id order
     const uint32_t chunks = (uint32_t)(((uint64_t)n + kSeedChunk - 1) / kSeedChunk);
+    LevelTasks lt = {};
     SeedTasks tasks = {};
     uint8_t *p = static_cast<uint8_t *>(scratch);
     auto take = [&](uint64_t bytes) {
@@ -905,29 +1068,48 @@ cudaError_t launch_seed_alias(uint32_t n, const DevTotals *tot, int ntables, con
         p += (bytes + 255) & ~(uint64_t)255;
         return r;
     };
+    const int per = one_level ? 1 : 2;   // tasks per table
     for (int t = 0; t < ntables; ++t) {
-        SeedTask &T = tasks.t[t];
-        T.w = w[t];
-        T.seed = seed[t];
-        T.vrec = vrec[t];
-        T.which = which[t];
-        T.idx = reinterpret_cast<uint32_t *>(take((uint64_t)n * 4));
-        T.pre = reinterpret_cast<u128 *>(take((uint64_t)n * 16));
-        T.split = reinterpret_cast<SeedSplit *>(take(sizeof(SeedSplit)));
-        T.agg = reinterpret_cast<SeedAgg *>(take((uint64_t)chunks * sizeof(SeedAgg)));
+        LevelTask &L = lt.t[t];
+        L.w = w[t];
+        L.which = which[t];
+        L.perm = one_level ? nullptr : reinterpret_cast<uint32_t *>(take((uint64_t)n * 4));
+        L.agg = one_level ? nullptr : reinterpret_cast<SeedAgg *>(take((uint64_t)chunks * sizeof(SeedAgg)));
+        for (int level = 0; level < per; ++level) {
+            SeedTask &T = tasks.t[per * t + level];
+            T.w = w[t];
+            T.seed = seed[t];
+            T.vrec = vrec[t];
+            T.perm = L.perm;
+            T.level = one_level ? 2 : level;
+            T.which = which[t];
+            T.idx = reinterpret_cast<uint32_t *>(take((uint64_t)n * 4));
+            T.pre = reinterpret_cast<u128 *>(take((uint64_t)n * 16));
+            T.split = reinterpret_cast<SeedSplit *>(take(sizeof(SeedSplit)));
+            T.agg = reinterpret_cast<SeedAgg *>(take((uint64_t)chunks * sizeof(SeedAgg)));
+        }
     }
-    k_seed_count<<<dim3(chunks, ntables), kSeedThreads, 0, s>>>(n, tot, tasks, flags);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_seed_offsets<<<ntables, kSeedThreads, 0, s>>>(chunks, tot, tasks);
+    const int nt = per * ntables;
+    cudaError_t e = cudaSuccess;
+    if (!one_level) {
+        k_level_count<<<dim3(chunks, ntables), kSeedThreads, 0, s>>>(n, tot, lt, split, flags);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_level_offsets<<<ntables, kSeedThreads, 0, s>>>(chunks, tot, lt);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_level_place<<<dim3(chunks, ntables), kSeedThreads, 0, s>>>(n, tot, lt, split);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_seed_count<<<dim3(chunks, nt), kSeedThreads, 0, s>>>(n, tot, tasks, one_level ? flags : nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_seed_place<<<dim3(chunks, ntables), kSeedThreads, 0, s>>>(n, tot, tasks);
+    k_seed_offsets<<<nt, kSeedThreads, 0, s>>>(chunks, tot, tasks);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_seed_place<<<dim3(chunks, nt), kSeedThreads, 0, s>>>(n, tot, tasks);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int threads = 256;
     uint64_t blocks = ((uint64_t)n + threads - 1) / threads;
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    k_seed_fill<<<dim3((unsigned)blocks, ntables), threads, 0, s>>>(n, tot, tasks);
+    k_seed_fill<<<dim3((unsigned)blocks, nt), threads, 0, s>>>(n, tot, tasks);
     return cudaGetLastError();
 }
 

@@ -90,6 +90,17 @@ def edge_bucket(a: int, b: int, shift: int) -> int:
     return k >> shift
 
 
+LEVEL_WORD = {0: 6, 1: 7, 2: 14, 3: 6}   # word of the vertex draw's level, per method
+
+
+def vertex_column(vt, n, xl, xc):
+    """Column of a two-level vertex table that a draw reads: the light
+    level's when the level word is below its bound (or no vertex is heavy)."""
+    nh = vt["nh"]
+    light = nh == 0 or xl < vt["TL"]
+    return (nh + idx(xc, n - nh)) if light else idx(xc, nh)
+
+
 class Replay:
     def __init__(self, rp, col, probe="search"):
         self.g = oracle.OracleGraph(rp, col)
@@ -97,7 +108,7 @@ class Replay:
         self.col = col
         self.deg = np.diff(self.rp)
         self.S = self.g.vertex()[1].astype(np.int64)
-        self.seed = [self.g.seed_table(l)[1:] for l in range(3)]
+        self.seed = [self.g.vertex_table(l) for l in range(3)]
         thr, alias, acc = self.g.sigma_table()
         self.thr, self.alias, self.acc = thr.astype(np.int64), alias.astype(np.int64), acc.astype(np.int64)
         self.probe_kind = probe
@@ -119,10 +130,10 @@ class Replay:
 
     def min_tables(self):
         if not hasattr(self, "rank"):
-            rl, rk, cthr, calias, gam, T, al = self.g.min_tables()
+            rl, rk, cthr, calias, gam = self.g.min_tables()
             self.rank, self.cthr_m, self.calias_m = rk.astype(np.int64), cthr, calias.astype(np.int64)
             self.gam_m = gam
-            self.seed_m = T
+            self.seed_m = self.g.vertex_table(3)
 
     def rank_twin(self, v, p):
         """d_{u,v} for position p (v -> u): the rank held by the twin slot."""
@@ -148,10 +159,10 @@ class Replay:
         self.min_tables()
         t = set()
         x = self.words(3, seed, s, 2)
-        c = idx(x[0], self.g.n)
+        c = vertex_column(self.seed_m, self.g.n, x[6], x[0])
         t.add(("seedm", c))
         v = int(verts[0])
-        if x[1] < int(self.seed_m[c]):   # the column keeps the draw: its own record
+        if x[1] < int(self.seed_m["T"][c]):   # the column keeps the draw: its own record
             t.add(("mvert", v >> 1))
         o, d = int(self.rp[v]), int(self.deg[v])
         j = idx(x[2], d)
@@ -270,12 +281,12 @@ class Replay:
 
     def sample(self, method, seed, s, verts, cls):
         t = set()
-        T, al = self.seed[method]
+        vt = self.seed[method]
         x = self.words(method, seed, s, 4)
-        c = idx(x[0], self.g.n)
+        c = vertex_column(vt, self.g.n, x[LEVEL_WORD[method]], x[0])
         t.add(("seed", c))
         v = int(verts[0])
-        if x[1] < int(T[c]):   # the column keeps the draw: its own vertex record
+        if x[1] < int(vt["T"][c]):   # the column keeps the draw: its own vertex record
             t.add(("vert", v >> 1))
         o = int(self.rp[v])
         if method == 2:

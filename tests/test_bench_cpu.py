@@ -37,16 +37,18 @@ def test_reference_arm_json_line():
     assert "workload" in d["config"]
 
 
-@pytest.mark.parametrize("k,budget,mix,filtered,expected", [
+@pytest.mark.parametrize("k,budget,mix,filtered,two,expected", [
     # load 7 + build 8 + finalize 1; T-5: sampler + reduce; Path-5: main, two redraw stages, reduce per chunk
-    (5, 100_000_000, False, False, 16 + 2 + 4),
-    (5, 1_000_000_000, False, True, 17 + 2 + 4 * 8),   # 5e8 Path-5 ids: 8 chunks of 2^26
-    (4, 100_000_000, False, False, 16 + 2),
-    (4, 100_000_000, True, False, 16 + 12 + 2 + 2),    # MOSS-4 + MOSS-4Min with its 12 table kernels
+    (5, 100_000_000, False, False, False, 16 + 2 + 4),
+    # two-level vertex tables add 3 split kernels; 5e8 Path-5 ids: 8 chunks of 2^26
+    (5, 1_000_000_000, False, True, True, 17 + 3 + 2 + 4 * 8),
+    (4, 100_000_000, False, False, False, 16 + 2),
+    (4, 100_000_000, True, False, False, 16 + 12 + 2 + 2),    # MOSS-4 + MOSS-4Min with its 12 table kernels
+    (4, 100_000_000, True, False, True, 16 + 3 + 15 + 2 + 2),
 ])
-def test_launches_per_step(k, budget, mix, filtered, expected):
+def test_launches_per_step(k, budget, mix, filtered, two, expected):
     assert bench.DEFER_CHUNK == 1 << 26
-    assert bench.launches_per_step(k, budget, mix, filtered) == expected
+    assert bench.launches_per_step(k, budget, mix, filtered, two) == expected
 
 
 def test_resolved_probe_follows_the_hash_size():

@@ -49,12 +49,15 @@ def test_large_tables_bit_exact(big):
     apos = rp.astype(np.int64)[owner] + slot[:, 3].astype(np.int64)
     assert np.array_equal(slot[:, 5:8], slot[apos][:, [0, 1, 4]])
     for l in range(3):
-        _, T, salias = og.seed_table(l)
+        vt = og.vertex_table(l)
+        assert moss.moss_vertex_levels(g.handle, l) == (vt["nh"], vt["TL"]), l
+        assert 0 < vt["nh"] < 100_000 and vt["TL"] > 0, l     # both levels hold weight
         seed = moss.moss_table_export(g.handle, moss.TABLE_SEED0 + l, np.zeros((n, 8), dtype=np.uint32))
         Tg = seed[:, 0].astype(np.uint64) | (seed[:, 1].astype(np.uint64) << np.uint64(32))
-        assert np.array_equal(Tg, T), l
-        assert np.array_equal(seed[:, 2], salias), l
-        assert np.array_equal(seed[:, 4:8], vert[salias.astype(np.int64)]), l
+        assert np.array_equal(Tg, vt["T"]), l
+        assert np.array_equal(seed[:, 2], vt["alias"]), l
+        assert np.array_equal(seed[:, 3], vt["self"]), l
+        assert np.array_equal(seed[:, 4:8], vert[vt["alias"].astype(np.int64)]), l
     st = g.stats()
     for l in range(3):
         assert (int(st.gamma[l][0]) | (int(st.gamma[l][1]) << 64)) == og.Gamma[l]

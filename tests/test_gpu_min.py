@@ -103,7 +103,8 @@ def u64(lo, hi):
 def test_min_tables_bit_exact(name):
     rp, col, og, g = pair(name)
     n, nnz = og.n, og.nnz
-    rl, rk, cthr, calias, gam, T, alias = og.min_tables()
+    rl, rk, cthr, calias, gam = og.min_tables()
+    vt = og.vertex_table(3)
     lst = moss.moss_table_export(g.handle, moss.TABLE_MIN_LIST, np.zeros((nnz, 2), dtype=np.uint32))
     assert np.array_equal(lst[:, 0], rl)
     deg = np.diff(rp.astype(np.int64))
@@ -127,10 +128,12 @@ def test_min_tables_bit_exact(name):
     assert [int(x) for x in gv] == gam
     gw = moss.moss_table_export(g.handle, moss.TABLE_MIN_GAMMA, np.zeros((n, 2), dtype=np.uint64))
     assert [int(a) | (int(b) << 64) for a, b in gw] == gam
+    assert moss.moss_vertex_levels(g.handle, 3) == (vt["nh"], vt["TL"])
     seed = moss.moss_table_export(g.handle, moss.TABLE_MIN_SEED, np.zeros((n, 8), dtype=np.uint32))
-    assert np.array_equal(u64(seed[:, 0], seed[:, 1]), T)
-    assert np.array_equal(seed[:, 2], alias)
-    assert np.array_equal(seed[:, 4:8], mv[alias.astype(np.int64)])
+    assert np.array_equal(u64(seed[:, 0], seed[:, 1]), vt["T"])
+    assert np.array_equal(seed[:, 2], vt["alias"])
+    assert np.array_equal(seed[:, 3], vt["self"])
+    assert np.array_equal(seed[:, 4:8], mv[vt["alias"].astype(np.int64)])
     st = g.stats()
     assert (int(st.gamma[3][0]) | (int(st.gamma[3][1]) << 64)) == og.Gamma_min
     # pick records: the draw and both possible picks, from the oracle's tables

@@ -86,6 +86,22 @@ def u128(a):
     return [int(a[i, 0]) | (int(a[i, 1]) << 64) for i in range(a.shape[0])]
 
 
+def check_vertex_table(g, og, l, vrec, table=None):
+    """Two-level vertex table l against the oracle's, column by column:
+    {T lo, T hi, alias, self} and the alias's vertex record; the level split."""
+    n = og.n
+    vt = og.vertex_table(l)
+    assert moss.moss_vertex_levels(g.handle, l) == (vt["nh"], vt["TL"]), l
+    seed = moss.moss_table_export(g.handle, table if table is not None else moss.TABLE_SEED0 + l,
+                                  np.zeros((n, 8), dtype=np.uint32))
+    Tg = seed[:, 0].astype(np.uint64) | (seed[:, 1].astype(np.uint64) << np.uint64(32))
+    assert np.array_equal(Tg, vt["T"]), l
+    assert np.array_equal(seed[:, 2], vt["alias"]), l
+    assert np.array_equal(seed[:, 3], vt["self"]), l
+    # the alias's vertex record rides in the second half of the column record
+    assert np.array_equal(seed[:, 4:8], vrec[vt["alias"].astype(np.int64)]), l
+
+
 @pytest.mark.parametrize("name", list(GRAPHS))
 def test_tables_bit_exact(name):
     rp, col, og, g = pair(name)
@@ -122,13 +138,7 @@ def test_tables_bit_exact(name):
     assert np.array_equal(slot[:, 6], slot[apos, 1])
     assert np.array_equal(slot[:, 7], slot[apos, 4])
     for l in range(3):
-        sthr, T, salias = og.seed_table(l)
-        seed = moss.moss_table_export(g.handle, moss.TABLE_SEED0 + l, np.zeros((n, 8), dtype=np.uint32))
-        Tg = seed[:, 0].astype(np.uint64) | (seed[:, 1].astype(np.uint64) << np.uint64(32))
-        assert np.array_equal(Tg, T), l
-        assert np.array_equal(seed[:, 2], salias), l
-        # the alias's vertex record rides in the second half of the column record
-        assert np.array_equal(seed[:, 4:8], vert[salias.astype(np.int64)]), l
+        check_vertex_table(g, og, l, vert)
         gw = moss.moss_table_export(g.handle, moss.TABLE_GAMMA0 + l, np.zeros((n, 2), dtype=np.uint64))
         assert u128(gw) == gam[l]
     st = g.stats()
@@ -231,6 +241,38 @@ def test_counts_and_estimates(name, rng):
     finally:
         g.set_rng(moss.RNG_SPLITMIX64)
         g.set_probe(moss.PROBE_AUTO)
+
+
+@pytest.mark.parametrize("name", ["cl_n200", "rgg2k", "cl_n2k", "hub70k"])
+def test_small_split_draws_both_levels(name):
+    """With a small split (the smallest from 3 up that leaves weight in both
+    levels of a table) both levels of the vertex draws run: tables, records
+    and counts against the oracle built with the same split."""
+    rp, col = GRAPHS[name]()
+    for split in range(3, 21):
+        og = oracle.OracleGraph(rp, col, vsplit=split)
+        if any(og.vertex_table(l)["nh"] > 0 and og.vertex_table(l)["TL"] > 0 for l in range(3)):
+            break
+    with moss.Graph(rp, col, vsplit=split) as g:
+        vert = moss.moss_table_export(g.handle, moss.TABLE_VERT, np.zeros((og.n, 4), dtype=np.uint32))
+        levels = []
+        for l in range(3):
+            check_vertex_table(g, og, l, vert)
+            levels.append(og.vertex_table(l))
+        assert any(v["nh"] > 0 and v["TL"] > 0 for v in levels)
+        for method in (0, 1, 2):
+            if og.Gamma[method] == 0:
+                continue
+            ocnt, ocls, overts = og.run(method, 77, 60_011, first=5, record=True)
+            cls, verts = gpu_records(g, method, 5, 60_011, 77)
+            assert np.array_equal(cls, ocls), method
+            ncol = 4 if method == 0 else 5
+            assert np.array_equal(verts[:, :ncol], overts[:, :ncol]), method
+            assert np.array_equal(gpu_counts(g, method, 5, 60_011, 77), ocnt), method
+        moss.moss_set_vertex_split(g.handle, split + 1)      # tables follow at the next build
+        with pytest.raises(moss.MossError) as ei:
+            g.estimate(4, 1000, 1)
+        assert ei.value.status == moss.MOSS_ESTATE
 
 
 def test_generator_setting():

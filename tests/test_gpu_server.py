@@ -108,14 +108,30 @@ def test_server_min_requests_equal_solo_runs():
 
 
 def test_target_budget_meets_target(pool):
-    with moss.Server(min_budget=1_000, max_budget=50_000_000, pilot_samples=50_000) as server:
+    """The budget is the rule applied to the pilot (the request's first
+    50,000 ids), and every class with at least 10 pilot hits ends with a
+    relative SE of at most eps sqrt((1/f - 1) / (1/f_pilot - 1)) -- eps itself
+    when the final hit fraction f equals the pilot's (Theorem 3: the
+    relative SE of a class is sqrt((1/f - 1) / K))."""
+    eps, P = 0.02, 50_000
+    with moss.Server(min_budget=1_000, max_budget=50_000_000, pilot_samples=P) as server:
         gid = server.add_graph(pool[2])
-        rid = server.submit(gid, 4, target_rse=0.02, seed=3)
+        rid = server.submit(gid, 4, target_rse=eps, seed=3)
         r, st = server.wait(rid)
-    # every class seen at least 10 times in the pilot now has relative SE <= ~2%
-    for i in (1, 3, 4, 5):
-        if r["hits"][0][i] >= 200 and r["est"][i] > 0:
-            assert np.sqrt(r["var"][i]) / r["est"][i] <= 0.025, i
+    pilot = pool[2].estimate(4, P, 3)
+    assert st["budget"] == moss.moss_budget_for_target(4, [P, 0], pilot["hits"], eps, 1_000, 50_000_000)
+    K = r["K"][0]
+    checked = 0
+    for i in (1, 3, 4, 5, 6):
+        mp = int(pilot["hits"][0][i])
+        if mp < 10:
+            continue
+        fp, f = mp / P, int(r["hits"][0][i]) / K
+        rse = np.sqrt(r["var"][i]) / r["est"][i]
+        assert rse == pytest.approx(np.sqrt((1 / f - 1) / K), rel=1e-9), i
+        assert rse <= eps * np.sqrt((1 / f - 1) / (1 / fp - 1)) * (1 + 1e-9), i
+        checked += 1
+    assert checked >= 3
 
 
 def test_server_rejects_bad_requests(pool):

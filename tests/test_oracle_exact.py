@@ -15,7 +15,10 @@ distribution, which is compared with the sampling-weight theorems:
 The CIS sets and their classes come from brute force over all k-subsets with
 networkx isomorphism (tests/helpers.py), the phi values from the paper's
 printed tables (tests/golden).  The only deviation allowed is the 2^-64
-quantisation of each draw.
+quantisation of each draw.  The vertex draw has three words (level, column,
+threshold); each test runs with one level (the default below 2^20
+vertices), at split 20 (every tiny graph's vertices are then heavy) and at
+split 2, where at most four vertices are heavy and both levels are drawn.
 """
 from __future__ import annotations
 
@@ -56,30 +59,54 @@ def triangles(adj) -> int:
     return sum(1 for a in range(n) for b in adj[a] if b > a for c in adj[b] if c > b and c in adj[a])
 
 
+LEVEL_WORD = {0: 6, 1: 7, 2: 14, 3: 6}   # index of the vertex draw's level word per method
+SPLITS = [oracle.ONE_LEVEL, oracle.VSPLIT, 2]
+
+
+def put_level(words, method, xl):
+    """words with the level word of the vertex draw set to xl."""
+    w = list(words) + [0] * (16 - len(words))
+    w[LEVEL_WORD[method]] = xl
+    return w
+
+
 class Tables:
-    def __init__(self, rp, col, which):
-        self.g = oracle.OracleGraph(rp, col)
+    def __init__(self, rp, col, which, vsplit=None):
+        self.g = oracle.OracleGraph(rp, col, vsplit=vsplit)
         self.rp = [int(x) for x in rp]
         self.col = [int(x) for x in col]
         self.n = len(rp) - 1
         self.deg = [self.rp[v + 1] - self.rp[v] for v in range(self.n)]
         self.S = [sum(self.deg[x] - 1 for x in self.col[self.rp[v]:self.rp[v + 1]]) for v in range(self.n)]
-        _, T, alias = self.g.seed_table(which)
-        self.T = [int(x) for x in T]
-        self.alias = [int(x) for x in alias]
+        vt = self.g.vertex_table(which)
+        self.nh, self.TL = vt["nh"], vt["TL"]
+        self.self_ = [int(x) for x in vt["self"]]
+        self.T = [int(x) for x in vt["T"]]
+        self.alias = [int(x) for x in vt["alias"]]
         thr, galias, acc = self.g.sigma_table()
         self.thr = [int(x) for x in thr]
         self.galias = [int(x) for x in galias]
         self.acc = [int(x) for x in acc]
 
     def seed_branches(self):
-        """(count over 2^128, x0, x1, v) for every seed-draw branch."""
-        for c in range(self.n):
-            cc = ic(c, self.n)
-            if self.T[c] > 0:
-                yield cc * self.T[c], iw(c, self.n), 0, c
-            if TWO64 - self.T[c] > 0:
-                yield cc * (TWO64 - self.T[c]), iw(c, self.n), TWO64 - 1, self.alias[c]
+        """(count over 2^192, x_level, x0, x1, v) for every seed-draw branch:
+        the light level for level words below TL (always, without heavy
+        vertices), the heavy one above; then column and threshold."""
+        levels = []
+        if self.nh == 0:
+            levels.append((TWO64, 0, 0, self.n))
+        else:
+            if self.TL > 0:
+                levels.append((self.TL, 0, self.nh, self.n - self.nh))
+            levels.append((TWO64 - self.TL, TWO64 - 1, 0, self.nh))
+        for cl, xl, base, m in levels:
+            for c in range(m):
+                cc = ic(c, m)
+                t = self.T[base + c]
+                if t > 0:
+                    yield cl * cc * t, xl, iw(c, m), 0, self.self_[base + c]
+                if TWO64 - t > 0:
+                    yield cl * cc * (TWO64 - t), xl, iw(c, m), TWO64 - 1, self.alias[base + c]
 
     def sigma_branches(self, v):
         """(count over 2^128, xc, xt, position) for every sigma-draw branch."""
@@ -118,15 +145,16 @@ def tiny_graphs():
     return out
 
 
+@pytest.mark.parametrize("vsplit", SPLITS)
 @pytest.mark.parametrize("gi", range(4))
-def test_moss4_distribution_is_theorem2(gi):
+def test_moss4_distribution_is_theorem2(gi, vsplit):
     rp, col = tiny_graphs()[gi]
-    t = Tables(rp, col, 0)
+    t = Tables(rp, col, 0, vsplit)
     g = t.g
     if g.Gamma[0] == 0:
         pytest.skip("no 3-path")
     probs = defaultdict(int)
-    for c0, x0, x1, v in t.seed_branches():
+    for c0, xl, x0, x1, v in t.seed_branches():
         dv = t.deg[v]
         assert dv >= 2 and t.S[v] > 0, "zero-weight vertex drawn"
         for c1, x2, x3, iu in t.sigma_branches(v):
@@ -134,7 +162,8 @@ def test_moss4_distribution_is_theorem2(gi):
             du = t.deg[u]
             for jw in range(dv - 1):
                 for jr in range(du - 1):
-                    verts, cls = g.sample_words(oracle.MOSS4, [x0, x1, x2, x3, iw(jw, dv - 1), iw(jr, du - 1)])
+                    verts, cls = g.sample_words(oracle.MOSS4, put_level([x0, x1, x2, x3, iw(jw, dv - 1),
+                                                                         iw(jr, du - 1)], 0, xl))
                     assert verts[0] == v and verts[1] == u
                     key = frozenset(verts[:4]) if cls else "miss"
                     probs[key] += c0 * c1 * ic(jw, dv - 1) * ic(jr, du - 1)
@@ -142,19 +171,20 @@ def test_moss4_distribution_is_theorem2(gi):
     p4 = phi4()
     adj = adjacency_sets(rp, col)
     # r = w closes a triangle: 6 ordered draws of probability 1/Gamma each
-    check_against_theorem(probs, 64 * 6, cis, lambda c: p4[c][0], g.Gamma[0],
+    check_against_theorem(probs, 64 * 7, cis, lambda c: p4[c][0], g.Gamma[0],
                           extra=Fraction(6 * triangles(adj), g.Gamma[0]))
 
 
+@pytest.mark.parametrize("vsplit", SPLITS)
 @pytest.mark.parametrize("gi", range(4))
-def test_t5_distribution_is_theorem6(gi):
+def test_t5_distribution_is_theorem6(gi, vsplit):
     rp, col = tiny_graphs()[gi]
-    t = Tables(rp, col, 1)
+    t = Tables(rp, col, 1, vsplit)
     g = t.g
     if g.Gamma[1] == 0:
         pytest.skip("no fork")
     probs = defaultdict(int)
-    for c0, x0, x1, v in t.seed_branches():
+    for c0, xl, x0, x1, v in t.seed_branches():
         dv = t.deg[v]
         assert dv >= 3
         for c1, x2, x3, iu in t.sigma_branches(v):
@@ -164,12 +194,12 @@ def test_t5_distribution_is_theorem6(gi):
                 for jr in range(dv - 2):
                     for jt in range(du - 1):
                         words = [x0, x1, x2, x3, iw(jw, dv - 1), iw(jr, dv - 2), iw(jt, du - 1)]
-                        verts, cls = g.sample_words(oracle.T5, words)
+                        verts, cls = g.sample_words(oracle.T5, put_level(words, 1, xl))
                         key = frozenset(verts) if cls else "miss"
                         probs[key] += c0 * c1 * ic(jw, dv - 1) * ic(jr, dv - 2) * ic(jt, du - 1)
     cis = brute_force_cis(rp, col, 5)
     t2 = table2()
-    check_against_theorem(probs, 64 * 7, cis, lambda c: t2[c][0], g.Gamma[1])
+    check_against_theorem(probs, 64 * 8, cis, lambda c: t2[c][0], g.Gamma[1])
 
 
 def pair_branches(t: Tables, v: int):
@@ -213,20 +243,21 @@ def pair_branches(t: Tables, v: int):
     return out
 
 
+@pytest.mark.parametrize("vsplit", SPLITS)
 @pytest.mark.parametrize("gi", range(4))
-def test_path5_distribution_is_theorem8(gi):
+def test_path5_distribution_is_theorem8(gi, vsplit):
     rp, col = tiny_graphs()[gi]
-    t = Tables(rp, col, 2)
+    t = Tables(rp, col, 2, vsplit)
     g = t.g
     if g.Gamma[2] == 0:
         pytest.skip("no 5-path")
     probs = defaultdict(int)
-    for c0, x0, x1, v in t.seed_branches():
+    for c0, xl, x0, x1, v in t.seed_branches():
         o = t.rp[v]
         pairs = defaultdict(int)
         rep = {}
         for cnt, words, iu_, iw_ in pair_branches(t, v):
-            verts, _cls = g.sample_words(oracle.PATH5, [x0, x1, 0, 0] + words)
+            verts, _cls = g.sample_words(oracle.PATH5, put_level([x0, x1, 0, 0] + words, 2, xl))
             assert verts[0] == v
             assert (verts[1], verts[2]) == (t.col[o + iu_], t.col[o + iw_])
             pairs[(iu_, iw_)] += cnt
@@ -242,12 +273,13 @@ def test_path5_distribution_is_theorem8(gi):
             du, dw = t.deg[u], t.deg[w]
             for jr in range(du - 1):
                 for jt in range(dw - 1):
-                    verts, cls = g.sample_words(oracle.PATH5, [x0, x1, iw(jr, du - 1), iw(jt, dw - 1)] + rep[(iu_, iw_)])
+                    verts, cls = g.sample_words(oracle.PATH5, put_level([x0, x1, iw(jr, du - 1), iw(jt, dw - 1)]
+                                                                         + rep[(iu_, iw_)], 2, xl))
                     key = frozenset(verts) if cls else "miss"
                     probs[key] += c0 * cnt * ic(jr, du - 1) * ic(jt, dw - 1)
     cis = brute_force_cis(rp, col, 5)
     t2 = table2()
-    check_against_theorem(probs, 64 * 14, cis, lambda c: t2[c][1], g.Gamma[2])
+    check_against_theorem(probs, 64 * 15, cis, lambda c: t2[c][1], g.Gamma[2])
 
 
 def test_path5_fallback_branch_is_reached():

@@ -99,7 +99,7 @@ def test_tables_match_definitions(gi):
     rp, col = tiny_graphs()[gi]
     b = Brute(rp, col)
     g = oracle.OracleGraph(rp, col)
-    rl, rk, cthr, calias, gam, T, alias = g.min_tables()
+    rl, rk, cthr, calias, gam = g.min_tables()
     rp = [int(x) for x in rp]
     col = [int(x) for x in col]
     for v in range(b.n):
@@ -116,54 +116,66 @@ def test_tables_match_definitions(gi):
     assert g.Gamma_min == sum(1 for _ in b.tuples())
 
 
+def vertex_branches(vt, n):
+    """(count over 2^192, x_level, x0, x1, v) of every branch of a two-level
+    vertex draw (level word, column word, threshold word)."""
+    nh, TL = vt["nh"], vt["TL"]
+    levels = [(TWO64, 0, 0, n)] if nh == 0 else (
+        ([(TL, 0, nh, n - nh)] if TL > 0 else []) + [(TWO64 - TL, TWO64 - 1, 0, nh)])
+    for cl, xl, base, m in levels:
+        for c in range(m):
+            cc = ic(c, m)
+            t = int(vt["T"][base + c])
+            if t > 0:
+                yield cl * cc * t, xl, iw(c, m), 0, int(vt["self"][base + c])
+            if TWO64 - t > 0:
+                yield cl * cc * (TWO64 - t), xl, iw(c, m), TWO64 - 1, int(vt["alias"][base + c])
+
+
+@pytest.mark.parametrize("vsplit", [oracle.ONE_LEVEL, oracle.VSPLIT, 2])
 @pytest.mark.parametrize("gi", range(5))
-def test_distribution_is_uniform_over_tuples(gi):
+def test_distribution_is_uniform_over_tuples(gi, vsplit):
     """Exact distribution of the oracle's draws: P(s) = tuples(s) / Gamma-check,
     P(r = w) = collision tuples / Gamma-check, and c(s) = tuples(s) / 2."""
     rp, col = tiny_graphs()[gi]
     b = Brute(rp, col)
-    g = oracle.OracleGraph(rp, col)
+    g = oracle.OracleGraph(rp, col, vsplit=vsplit)
     Gm = g.build_min()
     if Gm == 0:
         pytest.skip("no admissible tuple")
-    rl, rk, cthr, calias, gam, T, alias = g.min_tables()
+    rl, rk, cthr, calias, gam = g.min_tables()
+    vt = g.vertex_table(3)
     rpi = [int(x) for x in rp]
     n = b.n
     probs = defaultdict(int)
     cvals = {}
-    for c0 in range(n):
-        cc = ic(c0, n)
-        branches = []
-        if int(T[c0]) > 0:
-            branches.append((cc * int(T[c0]), iw(c0, n), 0, c0))
-        if TWO64 - int(T[c0]) > 0:
-            branches.append((cc * (TWO64 - int(T[c0])), iw(c0, n), TWO64 - 1, int(alias[c0])))
-        for p0, x0, x1, v in branches:
-            o, d = rpi[v], b.deg[v]
-            assert gam[v] > 0, "zero-weight vertex drawn"
-            for j in range(d):
-                cj = ic(j, d)
-                keep = iw(int(cthr[o + j]), gam[v])
-                sub = []
-                if keep > 0:
-                    sub.append((cj * keep, iw(j, d), 0, j))
-                if TWO64 - keep > 0:
-                    sub.append((cj * (TWO64 - keep), iw(j, d), TWO64 - 1, int(calias[o + j])))
-                for p1, x2, x3, iu in sub:
-                    dvu = int(rk[o + iu])
-                    assert dvu > 0, "zero-weight neighbour drawn"
-                    u = int(g.col[o + iu])
-                    duv = len(b.N(u, v))
-                    for jw in range(dvu):
-                        for jr in range(duv):
-                            verts, cls = g.sample_words(oracle.MOSS4MIN, [x0, x1, x2, x3, iw(jw, dvu), iw(jr, duv)])
-                            assert verts[0] == v and verts[1] == u
-                            assert verts[2] in b.N(v, u) and verts[3] in b.N(u, v)
-                            key = frozenset(verts[:4]) if cls else "miss"
-                            probs[key] += p0 * p1 * ic(jw, dvu) * ic(jr, duv)
-                            if cls:
-                                cvals.setdefault(key, set()).add((cls, verts[4]))
-    assert sum(probs.values()) == 1 << 384
+    for p0, xl, x0, x1, v in vertex_branches(vt, n):
+        o, d = rpi[v], b.deg[v]
+        assert gam[v] > 0, "zero-weight vertex drawn"
+        for j in range(d):
+            cj = ic(j, d)
+            keep = iw(int(cthr[o + j]), gam[v])
+            sub = []
+            if keep > 0:
+                sub.append((cj * keep, iw(j, d), 0, j))
+            if TWO64 - keep > 0:
+                sub.append((cj * (TWO64 - keep), iw(j, d), TWO64 - 1, int(calias[o + j])))
+            for p1, x2, x3, iu in sub:
+                dvu = int(rk[o + iu])
+                assert dvu > 0, "zero-weight neighbour drawn"
+                u = int(g.col[o + iu])
+                duv = len(b.N(u, v))
+                for jw in range(dvu):
+                    for jr in range(duv):
+                        verts, cls = g.sample_words(oracle.MOSS4MIN, [x0, x1, x2, x3, iw(jw, dvu), iw(jr, duv),
+                                                                      xl])
+                        assert verts[0] == v and verts[1] == u
+                        assert verts[2] in b.N(v, u) and verts[3] in b.N(u, v)
+                        key = frozenset(verts[:4]) if cls else "miss"
+                        probs[key] += p0 * p1 * ic(jw, dvu) * ic(jr, duv)
+                        if cls:
+                            cvals.setdefault(key, set()).add((cls, verts[4]))
+    assert sum(probs.values()) == 1 << 448
     onto = defaultdict(int)
     miss = 0
     for v, u, w, r in b.tuples():
@@ -173,10 +185,10 @@ def test_distribution_is_uniform_over_tuples(gi):
             onto[frozenset((v, u, w, r))] += 1
     for s, t in onto.items():
         ideal = Fraction(t, Gm)
-        got = Fraction(probs[s], 1 << 384)
+        got = Fraction(probs[s], 1 << 448)
         assert abs(got - ideal) <= ideal * Fraction(1, 10 ** 12), (s, float(got), float(ideal))
     assert set(k for k in probs if k != "miss") == set(onto)
-    assert abs(Fraction(probs.get("miss", 0), 1 << 384) - Fraction(miss, Gm)) <= Fraction(1, 10 ** 12)
+    assert abs(Fraction(probs.get("miss", 0), 1 << 448) - Fraction(miss, Gm)) <= Fraction(1, 10 ** 12)
     cis = brute_force_cis(rp, col, 4)
     for s, seen in cvals.items():
         assert len(seen) == 1, (s, seen)
@@ -198,7 +210,7 @@ def test_distribution_is_uniform_over_tuples(gi):
         cls, c = next(iter(cvals[s]))
         sl = oracle.min_slot(cls, c)
         if sl >= 0:
-            expected[sl] += pr / float(1 << 384)
+            expected[sl] += pr / float(1 << 448)
     res = oracle.finalize_moss4min(np.zeros(22), expected, 0, 1, 0, Gm, 0)
     eta = np.zeros(22)
     for i in (3, 5, 6):

@@ -205,24 +205,57 @@ def test_alias_all_zero_weights():
     assert thr == [0, 0, 0] and alias == [0, 1, 2]
 
 
-def test_seed_threshold_quantisation():
+def level_weights(vt, gam):
+    """(heavy vertices, light vertices, W_H, W_L) of a two-level table."""
+    nh = vt["nh"]
+    heavy = [int(v) for v in vt["self"][:nh]]
+    light = [int(v) for v in vt["self"][nh:]]
+    return heavy, light, sum(gam[v] for v in heavy), sum(gam[v] for v in light)
+
+
+@pytest.mark.parametrize("vsplit", [oracle.ONE_LEVEL, oracle.VSPLIT, 8, 3])
+def test_vertex_tables_follow_their_definition(vsplit):
+    """The two-level vertex tables: heavy vertices are exactly those with
+    w_v 2^split >= W (ascending ids, then the light ones ascending); each
+    level's table gives every vertex exactly its weight's share of the level
+    (the alias mass identity); thresholds are floor(thr 2^64 / W_level); the
+    light level's bound is floor(W_L 2^64 / W).  So a draw returns v with
+    probability w_v / W up to the 2^-64 quantisation of each word."""
     rp, col = synth.workload("cl_n2k")
-    g = oracle.OracleGraph(rp, col)
+    g = oracle.OracleGraph(rp, col, vsplit=vsplit)
+    deg, S, Q, gam = g.vertex()
     for which in range(3):
-        thr, T, alias = g.seed_table(which)
+        vt = g.vertex_table(which)
         W = g.Gamma[which]
-        for v in range(0, g.n, 7):
-            exp = min(thr[v] * TWO64 // W, TWO64 - 1)
-            assert int(T[v]) == exp
+        heavy, light, WH, WL = level_weights(vt, gam[which])
+        one = vsplit == oracle.ONE_LEVEL
+        assert heavy == [v for v in range(g.n) if not one and gam[which][v] * (1 << vsplit) >= W]
+        assert light == [v for v in range(g.n) if one or gam[which][v] * (1 << vsplit) < W]
+        assert len(heavy) <= 1 << vsplit and WH + WL == W
+        assert vt["TL"] == (min(WL * TWO64 // W, TWO64 - 1) if heavy else 0)
+        nh = vt["nh"]
+        for base, members, Wl in ((0, heavy, WH), (nh, light, WL)):
+            m = len(members)
+            if m == 0:
+                continue
+            pos = {v: i for i, v in enumerate(members)}
+            thr = vt["thr"][base:base + m]
+            alias = [pos[int(a)] for a in vt["alias"][base:base + m]]
+            alias_mass_ok([gam[which][v] for v in members], thr, alias)
+            for i in range(0, m, 7):
+                assert int(vt["T"][base + i]) == (min(thr[i] * TWO64 // Wl, TWO64 - 1) if Wl else 0)
+    if vsplit == oracle.ONE_LEVEL:   # one table over all vertices in id order
+        assert all(list(g.vertex_table(l)["self"]) == list(range(g.n)) for l in range(3))
+    if vsplit == 8:   # both levels hold mass
+        assert all(0 < g.vertex_table(l)["nh"] <= 256 and g.vertex_table(l)["TL"] > 0 for l in range(3))
+    if vsplit == 3:   # no vertex holds an eighth of Gamma or Gamma^(2): one light level only
+        assert g.vertex_table(0)["nh"] == 0 and g.vertex_table(1)["nh"] > 0
 
 
 def test_tables_of_workload_have_exact_mass():
     rp, col = synth.workload("cl_n2k")
     g = oracle.OracleGraph(rp, col)
     deg, S, Q, gam = g.vertex()
-    for which in range(3):
-        thr, _T, alias = g.seed_table(which)
-        alias_mass_ok(gam[which], thr, [int(a) for a in alias])
     gthr, galias, acc = g.sigma_table()
     for v in range(0, g.n, 13):
         o, d = int(rp[v]), int(rp[v + 1] - rp[v])
