@@ -62,6 +62,7 @@ struct moss_batch {
     uint32_t tile = 8192;
     int threads = 256;                 // threads per block of the persistent launch
     int per_sm = 0;                    // resident blocks per SM (0: as many as fit)
+    int rngs = kBatchSplitMix;         // generators of the planned graphs (kBatch*)
     std::vector<std::pair<const moss_graph *, int>> probes;   // per-graph probe strategy overrides
     bool record = false;               // record per-tile SM cycles (tuning runs)
     bool dirty = true;                 // request list or a launch choice changed since the last capture
@@ -193,7 +194,8 @@ int plan(moss_batch *b) {
     // the host vectors die at return: wait for the copies
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return set_error(MOSS_ECUDA, "uploading the batch plan");
-    b->blocks = batch_blocks(b->device, b->threads, b->per_sm);
+    b->rngs = batch_rngs(graphs.data(), graphs.size());
+    b->blocks = batch_blocks(b->device, b->threads, b->per_sm, b->rngs);
     return MOSS_OK;
 }
 
@@ -204,7 +206,7 @@ cudaError_t enqueue(moss_batch *b) {
     cudaError_t e = cudaMemsetAsync(b->d_next, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess)
         e = launch_sample_batch(b->d_graphs, b->d_tasks, b->ntasks, b->ntiles, b->tile, b->d_next, b->d_tiles,
-                                b->threads, b->blocks, b->record ? b->d_cycles : nullptr, s);
+                                b->threads, b->blocks, b->record ? b->d_cycles : nullptr, b->rngs, s);
     if (e == cudaSuccess) e = launch_batch_reduce(b->d_tasks, b->ntasks, b->tile, b->d_tiles, b->d_task_counts, s);
     if (e == cudaSuccess) e = launch_finalize_batch(b->d_reqs, nreq, b->d_task_counts, b->d_results, s);
     if (e == cudaSuccess && nreq)
@@ -367,7 +369,7 @@ int moss_batch_get_tuning(const moss_batch *b, moss_batch_tuning *out) {
     *out = b->tuning;
     out->tile_samples = b->tile;
     out->threads_per_block = b->threads;
-    out->blocks_per_sm = b->per_sm > 0 ? b->per_sm : batch_max_per_sm(b->threads);
+    out->blocks_per_sm = b->per_sm > 0 ? b->per_sm : batch_max_per_sm(b->threads, b->rngs);
     return MOSS_OK;
 }
 
@@ -473,7 +475,7 @@ int moss_batch_tune(moss_batch *b, void *stream, uint32_t *chosen) {
     if ((rc = try_tiles())) return rc;
     int best_threads = b->threads, best_per = b->per_sm;
     for (int th : {128, 256, 512}) {
-        const int mx = batch_max_per_sm(th);
+        const int mx = batch_max_per_sm(th, b->rngs);
         int pers[3] = {mx, (3 * mx + 3) / 4, (mx + 1) / 2};
         for (int pi = 0; pi < 3; ++pi) {
             if (pi > 0 && pers[pi] == pers[pi - 1]) continue;

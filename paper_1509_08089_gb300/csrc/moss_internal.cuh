@@ -394,15 +394,23 @@ struct BatchRequest {
     int task[2];      // task index per sub-method, -1 when it draws nothing
 };
 // persistent sampler over a batch: tile_counts[t][22] per tile; threads per
-// block 128, 256 or 512; tile_cycles (nullable) receives each tile's SM cycles
+// block 128, 256 or 512; tile_cycles (nullable) receives each tile's SM
+// cycles; rngs: the generators of the batch's graphs (kBatch*)
+constexpr int kBatchSplitMix = 0, kBatchPhilox = 1, kBatchBoth = 2;
 cudaError_t launch_sample_batch(const DevGraph *graphs, const BatchTask *tasks, int ntasks, uint64_t ntiles,
                                 uint32_t tile_samples, unsigned long long *next_tile, uint32_t *tile_counts,
-                                int threads, int blocks, unsigned long long *tile_cycles, cudaStream_t s);
+                                int threads, int blocks, unsigned long long *tile_cycles, int rngs, cudaStream_t s);
+// the batch generator mode of a set of graph views
+inline int batch_rngs(const DevGraph *views, size_t n) {
+    bool sm = false, ph = false;
+    for (size_t i = 0; i < n; ++i) (views[i].rng == kRngPhilox ? ph : sm) = true;
+    return sm && ph ? kBatchBoth : ph ? kBatchPhilox : kBatchSplitMix;
+}
 // task_counts[task][22] = sum of the task's tile rows, in tile order
 cudaError_t launch_batch_reduce(const BatchTask *tasks, int ntasks, uint32_t tile_samples,
                                 const uint32_t *tile_counts, uint64_t *task_counts, cudaStream_t s);
-int batch_max_per_sm(int threads);                    // resident blocks per SM at most
-int batch_blocks(int device, int threads, int per_sm);  // grid; per_sm <= 0: the most that fit
+int batch_max_per_sm(int threads, int rngs);                    // resident blocks per SM at most
+int batch_blocks(int device, int threads, int per_sm, int rngs);  // grid; per_sm <= 0: the most that fit
 cudaError_t launch_finalize_batch(const BatchRequest *reqs, int nreq, const uint64_t *task_counts, void *results,
                                   cudaStream_t s);
 

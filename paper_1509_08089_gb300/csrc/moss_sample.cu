@@ -729,11 +729,13 @@ __device__ __forceinline__ int sample_any(const DevGraph &g, const uint8_t *lut4
 
 // Persistent sampler over a batch: warps take tiles of `tile_samples` ids of
 // one task from a device counter.  THREADS per block is a tuning choice (the
-// resident threads per SM stay the same: THREADS x blocks = 1,024).  With
-// tile_cycles non-null the first lane of a warp records each tile's
-// duration in SM clock cycles (the autotuner's per-graph cost of a probe
-// strategy).
-template <int THREADS>
+// resident threads per SM stay the same: THREADS x blocks = 1,024).  RNGS:
+// the generators the batch's graphs use (kBatchSplitMix, kBatchPhilox, or
+// kBatchBoth: chosen per tile), so a single-generator batch carries one
+// sampler body.  With tile_cycles non-null the first lane of a warp records
+// each tile's duration in SM clock cycles (the autotuner's per-graph cost of
+// a probe strategy).
+template <int THREADS, int RNGS>
 __global__ void __launch_bounds__(THREADS, kBatchBlocks * kThreads / THREADS)
     k_sample_batch(const DevGraph *graphs, const BatchTask *tasks, int ntasks, uint64_t ntiles, uint32_t tile_samples,
                    unsigned long long *next_tile, uint32_t *tile_counts, unsigned long long *tile_cycles) {
@@ -771,7 +773,8 @@ __global__ void __launch_bounds__(THREADS, kBatchBlocks * kThreads / THREADS)
         const uint64_t left = tk.first + tk.count - f;
         const uint32_t cnt = (uint32_t)(left < tile_samples ? left : tile_samples);
         const bool hashed = g.hash != nullptr;
-        const bool philox = g.rng == kRngPhilox;   // warp-uniform: a tile belongs to one graph
+        // warp-uniform: a tile belongs to one graph
+        const bool philox = RNGS == kBatchPhilox || (RNGS == kBatchBoth && g.rng == kRngPhilox);
         for (uint32_t base = 0; base < cnt; base += 32) {
             const uint32_t i = base + lane;
             int cls = kSlots;
@@ -989,34 +992,64 @@ cudaError_t launch_counts(int method, const DevGraph &g, uint64_t first, uint64_
     return cudaSuccess;
 }
 
-int batch_max_per_sm(int threads) {
+template <int T>
+int max_per_sm_rngs(int rngs) {
     int per = 0;
-    cudaError_t e = cudaErrorInvalidValue;
-    if (threads == 128) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample_batch<128>, 128, 0);
-    if (threads == 256) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample_batch<256>, 256, 0);
-    if (threads == 512) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample_batch<512>, 512, 0);
+    cudaError_t e;
+    if (rngs == kBatchSplitMix) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample_batch<T, kBatchSplitMix>, T, 0);
+    else if (rngs == kBatchPhilox) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample_batch<T, kBatchPhilox>, T, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sample_batch<T, kBatchBoth>, T, 0);
     return e == cudaSuccess && per > 0 ? per : 1;
 }
 
-int batch_blocks(int device, int threads, int per_sm) {
-    const int max = batch_max_per_sm(threads);
+int batch_max_per_sm(int threads, int rngs) {
+    if (threads == 128) return max_per_sm_rngs<128>(rngs);
+    if (threads == 512) return max_per_sm_rngs<512>(rngs);
+    return max_per_sm_rngs<256>(rngs);
+}
+
+int batch_blocks(int device, int threads, int per_sm, int rngs) {
+    const int max = batch_max_per_sm(threads, rngs);
     const int per = per_sm <= 0 || per_sm > max ? max : per_sm;
     return device_sms(device) * per;
 }
 
+template <int T, int R>
+void launch_batch_kernel(const DevGraph *graphs, const BatchTask *tasks, int ntasks, uint64_t ntiles,
+                         uint32_t tile_samples, unsigned long long *next_tile, uint32_t *tile_counts, int blocks,
+                         unsigned long long *tile_cycles, cudaStream_t s) {
+    k_sample_batch<T, R><<<blocks, T, 0, s>>>(graphs, tasks, ntasks, ntiles, tile_samples, next_tile, tile_counts,
+                                              tile_cycles);
+}
+
+template <int T>
+void launch_batch_rngs(int rngs, const DevGraph *graphs, const BatchTask *tasks, int ntasks, uint64_t ntiles,
+                       uint32_t tile_samples, unsigned long long *next_tile, uint32_t *tile_counts, int blocks,
+                       unsigned long long *tile_cycles, cudaStream_t s) {
+    if (rngs == kBatchSplitMix)
+        launch_batch_kernel<T, kBatchSplitMix>(graphs, tasks, ntasks, ntiles, tile_samples, next_tile, tile_counts,
+                                               blocks, tile_cycles, s);
+    else if (rngs == kBatchPhilox)
+        launch_batch_kernel<T, kBatchPhilox>(graphs, tasks, ntasks, ntiles, tile_samples, next_tile, tile_counts,
+                                             blocks, tile_cycles, s);
+    else
+        launch_batch_kernel<T, kBatchBoth>(graphs, tasks, ntasks, ntiles, tile_samples, next_tile, tile_counts,
+                                           blocks, tile_cycles, s);
+}
+
 cudaError_t launch_sample_batch(const DevGraph *graphs, const BatchTask *tasks, int ntasks, uint64_t ntiles,
                                 uint32_t tile_samples, unsigned long long *next_tile, uint32_t *tile_counts,
-                                int threads, int blocks, unsigned long long *tile_cycles, cudaStream_t s) {
+                                int threads, int blocks, unsigned long long *tile_cycles, int rngs, cudaStream_t s) {
     if (ntasks <= 0 || ntiles == 0) return cudaSuccess;
     if (threads == 128)
-        k_sample_batch<128><<<blocks, 128, 0, s>>>(graphs, tasks, ntasks, ntiles, tile_samples, next_tile, tile_counts,
-                                                   tile_cycles);
+        launch_batch_rngs<128>(rngs, graphs, tasks, ntasks, ntiles, tile_samples, next_tile, tile_counts, blocks,
+                               tile_cycles, s);
     else if (threads == 512)
-        k_sample_batch<512><<<blocks, 512, 0, s>>>(graphs, tasks, ntasks, ntiles, tile_samples, next_tile, tile_counts,
-                                                   tile_cycles);
+        launch_batch_rngs<512>(rngs, graphs, tasks, ntasks, ntiles, tile_samples, next_tile, tile_counts, blocks,
+                               tile_cycles, s);
     else
-        k_sample_batch<256><<<blocks, 256, 0, s>>>(graphs, tasks, ntasks, ntiles, tile_samples, next_tile, tile_counts,
-                                                   tile_cycles);
+        launch_batch_rngs<256>(rngs, graphs, tasks, ntasks, ntiles, tile_samples, next_tile, tile_counts, blocks,
+                               tile_cycles, s);
     return cudaGetLastError();
 }
 

@@ -223,6 +223,7 @@ struct moss_server {
     moss_result *h_results = nullptr;
     size_t cap_hres = 0;
     int blocks = 0;
+    int rngs = kBatchSplitMix;     // generators of the server's graphs (kBatch*)
     bool graphs_uploaded = false;
     // statistics
     uint64_t ticks = 0, samples = 0, completed = 0;
@@ -252,6 +253,8 @@ int enqueue_tick(moss_server *s, TickBuffers &tb, uint64_t ntiles) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return fail_server(s, MOSS_ECUDA, "uploading server graphs");
         s->graphs_uploaded = true;
+        s->rngs = batch_rngs(gv.data(), gv.size());
+        s->blocks = batch_blocks(s->device, 256, 0, s->rngs);
     }
     const size_t nt = tb.tasks.size();
     if (e == cudaSuccess) e = grow(&tb.d_tasks, &tb.cap_tasks, nt + 1, st);
@@ -266,7 +269,7 @@ int enqueue_tick(moss_server *s, TickBuffers &tb, uint64_t ntiles) {
     if (e == cudaSuccess) e = cudaMemsetAsync(tb.d_next, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess)
         e = launch_sample_batch(s->d_graphs, tb.d_tasks, (int)nt, ntiles, s->cfg.tile_samples, tb.d_next, tb.d_tiles,
-                                256, s->blocks, nullptr, st);
+                                256, s->blocks, nullptr, s->rngs, st);
     if (e == cudaSuccess)
         e = launch_batch_reduce(tb.d_tasks, (int)nt, s->cfg.tile_samples, tb.d_tiles, tb.d_task_counts, st);
     if (e == cudaSuccess)
@@ -524,7 +527,7 @@ int moss_server_create(int device, const moss_server_config *cfg, moss_server **
     for (TickBuffers &tb : s->tick)
         ok = ok && cudaMalloc(reinterpret_cast<void **>(&tb.d_next), sizeof(unsigned long long)) == cudaSuccess &&
              cudaEventCreate(&tb.start) == cudaSuccess && cudaEventCreate(&tb.end) == cudaSuccess;
-    s->blocks = batch_blocks(device, 256, 0);
+    s->blocks = batch_blocks(device, 256, 0, kBatchSplitMix);
     if (prev >= 0) cudaSetDevice(prev);
     if (!ok) {
         moss_server_free(s);
