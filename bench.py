@@ -67,9 +67,12 @@ def parse():
     p.add_argument("--seed", type=int, default=42)
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--mode", default="single", choices=["single", "batch", "serve", "min"],
+    p.add_argument("--mode", default="single", choices=["single", "batch", "serve", "min", "call"],
                    help="single: the one-graph step; batch: many graphs in one persistent launch; serve: "
-                        "the request server; min: the one-graph step of MOSS-4 + MOSS-4Min (k=4)")
+                        "the request server; min: the one-graph step of MOSS-4 + MOSS-4Min (k=4); call: "
+                        "sampling calls of given methods and sizes alone (for profiler captures)")
+    p.add_argument("--methods", default="1,2", help="call mode: methods (0 MOSS-4, 1 T-5, 2 Path-5, 3 MOSS-4Min)")
+    p.add_argument("--counts", default="5000000,10000000", help="call mode: samples per call")
     p.add_argument("--graphs", type=int, default=512, help="batch mode: number of graphs")
     p.add_argument("--rate", type=float, default=2000.0, help="serve mode: mean arrivals per second")
     p.add_argument("--duration", type=float, default=2.0, help="serve mode: seconds of arrivals")
@@ -881,10 +884,52 @@ def run_serve(args):
     print(json.dumps(r), flush=True)
 
 
+def run_call(args):
+    """Sampling calls (moss_sample_counts) of each method and size on the
+    workload's graph, W untimed and K timed each, the L2 flushed before every
+    call; one JSON line with the median CUDA-event time of each.  The launch
+    order is fixed (methods in turn, sizes in turn, warm-up calls first), so a
+    profiler's launch list maps onto the calls."""
+    import torch
+    import synth
+    import paper_1509_08089_gb300 as moss
+    rp, col = synth.workload(args.workload)
+    torch.cuda.set_device(0)
+    moss.load()
+    stream = torch.cuda.current_stream()
+    methods = [int(x) for x in args.methods.split(",")]
+    counts = [int(x) for x in args.counts.split(",")]
+    probe = {"auto": moss.PROBE_AUTO, "hash": moss.PROBE_HASH, "filter": moss.PROBE_FILTER,
+             "search": moss.PROBE_SEARCH}[args.probe]
+    kmask = (1 << 4) | (1 << 5) | (moss.TABLES_4MIN if 3 in methods else 0)
+    l2_flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    with moss.Graph(rp, col, stream=stream, k_mask=kmask, probe=probe, rng=RNG_IDS[args.rng]) as g:
+        buf = torch.zeros(22, dtype=torch.int64, device="cuda")
+        for m in methods:
+            for c in counts:
+                ms = []
+                for i in range(args.warmup + args.steps):
+                    l2_flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    moss.moss_sample_counts(g.handle, m, 0, c, args.seed, buf, stream)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    if i >= args.warmup:
+                        ms.append(a.elapsed_time(b))
+                out[f"{NAMES[m]}@{c}"] = {"ms": statistics.median(ms), "samples_per_s": c / statistics.median(ms) * 1e3}
+    print(json.dumps({"metric": "samples/s of one sampling call", "workload": describe(args.workload, 5)[1],
+                      "probe": resolved_probe(args.probe, rp), "rng": args.rng, "steps": args.steps,
+                      "warmup": args.warmup, "calls": out}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "call":
+        run_call(args)
     elif args.mode == "batch":
         run_batch(args)
     elif args.mode == "serve":
