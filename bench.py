@@ -296,7 +296,9 @@ def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False, tw
     """Kernels of one step: load 7 (vertices, owners, slot weights, short and
     long slot scans, twins, totals); build 8 (two sigma alias passes, the
     alias-half fill, four alias phases of the vertex tables, edge hash), 3
-    more (the level split) for two-level vertex tables; MOSS-4Min build 12
+    more (the level split) for two-level vertex tables, 5 more behind the
+    edge filter (the filter, and the hubs' degree histogram, degree cut,
+    map and adjacency bits); MOSS-4Min build 12
     (three sort tiers, slot records, two alias passes, pick records, total,
     four alias phases of its vertex table), again 3 more with two levels; per
     sub-method a sampler and a reduce, Path-5 per chunk of DEFER_CHUNK ids a
@@ -304,7 +306,7 @@ def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False, tw
     finalize."""
     from paper_1509_08089_gb300.dist import sub_budgets
     split = 3 if two_level else 0
-    n = 7 + 8 + split + (1 if filtered else 0) + ((12 + split) if mix else 0) + 1
+    n = 7 + 8 + split + (5 if filtered else 0) + ((12 + split) if mix else 0) + 1
     for m, K in sub_budgets(k, budget, mix):
         n += 4 * -(-K // DEFER_CHUNK) if m == 2 else 2
     return n
@@ -320,7 +322,9 @@ def sampler_tables_bytes(rp, probe: str, methods) -> int:
     layout: 32 B slot records and 4 B ids per list entry, 16 B vertex records
     and a 32 B vertex alias record per vertex and method, and the hashed edge
     set (32 B buckets, the next power of two >= nnz / 2) or the edge filter in
-    front of it (4 B words, the largest power of two <= nnz / 8)."""
+    front of it (4 B words, the largest power of two <= nnz / 8) with the
+    hubs' map (8 B slots, the power of two >= 2 H) and adjacency bits (H^2,
+    H = min(8192, max(16, n / 16)))."""
     n, nnz = len(rp) - 1, int(rp[-1])
     total = nnz * (32 + 4) + n * (16 + 32 * len(methods))
     if probe in ("hash", "filter"):
@@ -333,6 +337,11 @@ def sampler_tables_bytes(rp, probe: str, methods) -> int:
         while 2 * w <= max(nnz // 8, 1):
             w <<= 1
         total += 4 * w
+        h = min(8192, max(16, n // 16))
+        slots = 1
+        while slots < 2 * h:
+            slots <<= 1
+        total += 8 * slots + (h * h + 31) // 32 * 4
     return total
 
 

@@ -433,13 +433,19 @@ int moss_graph_stats(const moss_graph *g, moss_stats *out);
  *                            when d_x < 2^16, else nb = 0xFFFFFFFF and
  *                            off = twin
  *   MOSS_TABLE_ACC    nnz x uint32 ACC_sigma^(v) exclusive prefix (Sec. 4.1.3)
- *   MOSS_TABLE_SEED0+l n x {uint64 threshold T, uint32 alias, uint32 0,
- *                      then the alias's MOSS_TABLE_VERT record} (32 bytes),
- *                      l = 0 pi, 1 rho^(1), 2 rho^(2)
+ *   MOSS_TABLE_SEED0+l n x {uint64 threshold T, uint32 alias vertex,
+ *                      uint32 own vertex, then the alias's MOSS_TABLE_VERT
+ *                      record} (32 bytes), l = 0 pi, 1 rho^(1), 2 rho^(2);
+ *                      one column per vertex in id order, or with two
+ *                      levels (moss_vertex_levels) the nh heavy vertices'
+ *                      columns first, then the light ones', each level an
+ *                      alias table of its own over its columns in
+ *                      ascending id order
  *   MOSS_TABLE_GAMMA0+l n x {uint64 lo, hi} vertex weight of table l
  * and, after a build with MOSS_TABLES_4MIN (Sec. 4.2):
- *   MOSS_TABLE_MIN_SEED  n x {uint64 threshold T, uint32 alias, uint32 0, then
- *                        the alias's MOSS_TABLE_MIN_VERT record} of pi-check
+ *   MOSS_TABLE_MIN_SEED  n x {uint64 threshold T, uint32 alias vertex, uint32
+ *                        own vertex, then the alias's MOSS_TABLE_MIN_VERT
+ *                        record} of pi-check, columns as MOSS_TABLE_SEED0
  *   MOSS_TABLE_MIN_GAMMA n x {uint64 lo, hi} Gamma-check_v
  *   MOSS_TABLE_MIN_VERT  n x {uint32 off, deg, Gamma-check_v lo, hi}
  *   MOSS_TABLE_MIN_SLOT  nnz x {uint64 sigma-check threshold, uint32 alias
@@ -454,6 +460,13 @@ int moss_graph_stats(const moss_graph *g, moss_stats *out);
  * and, after a build under MOSS_PROBE_FILTER (or AUTO choosing it):
  *   MOSS_TABLE_FILTER    W x uint32 filter words, W the largest power of two
  *                        <= nnz / 8 (at least 1)
+ *   MOSS_TABLE_HUB_LIST  H x uint32: the hubs -- every vertex of degree >= D,
+ *                        D the smallest degree >= 1 with at most H such
+ *                        vertices, H = min(8192, max(16, n / 16)) -- in
+ *                        arbitrary order, 0xFFFFFFFF past the last
+ *   MOSS_TABLE_HUB_BITS  ceil(H^2 / 32) x uint32: bit i H + j (word / 32, bit
+ *                        % 32) set iff hubs i and j are adjacent; edge probes
+ *                        between two hubs are answered from these bits
  * bytes must equal the table size.  Synchronous. */
 #define MOSS_TABLE_VERT   0
 #define MOSS_TABLE_SLOT   1
@@ -467,6 +480,8 @@ int moss_graph_stats(const moss_graph *g, moss_stats *out);
 #define MOSS_TABLE_MIN_LIST  13
 #define MOSS_TABLE_FILTER    14
 #define MOSS_TABLE_MIN_PICK  15
+#define MOSS_TABLE_HUB_LIST  16
+#define MOSS_TABLE_HUB_BITS  17
 int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t bytes);
 
 void moss_graph_free(moss_graph *g);

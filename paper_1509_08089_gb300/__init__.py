@@ -34,6 +34,8 @@ TABLE_VERT, TABLE_SLOT, TABLE_ACC, TABLE_SEED0, TABLE_GAMMA0 = 0, 1, 2, 3, 6
 TABLE_MIN_SEED, TABLE_MIN_GAMMA, TABLE_MIN_VERT, TABLE_MIN_SLOT, TABLE_MIN_LIST = 9, 10, 11, 12, 13
 TABLE_FILTER = 14
 TABLE_MIN_PICK = 15
+TABLE_HUB_LIST = 16
+TABLE_HUB_BITS = 17
 
 
 class moss_stats(ctypes.Structure):

@@ -223,6 +223,10 @@ struct moss_graph {
     uint64_t hash_buckets = 0;
     uint32_t *filter = nullptr;  // Bloom filter in front of the hash
     uint64_t filter_words = 0;
+    void *hub_mem = nullptr;     // hub adjacency behind the filter: map, bitmap, hub list
+    uint2 *hub_map = nullptr;
+    uint32_t *hub_bits = nullptr;
+    uint32_t *hub_list = nullptr;
     moss_result res_host{};      // host staging of the result
     uint32_t flags_host[2] = {0, 0};
 };
@@ -236,6 +240,7 @@ void release(moss_graph *g) {
     if (g->arena) cudaFreeAsync(g->arena, 0);
     if (g->hash) cudaFreeAsync(g->hash, 0);
     if (g->filter) cudaFreeAsync(g->filter, 0);
+    if (g->hub_mem) cudaFreeAsync(g->hub_mem, 0);
     if (g->min_arena) cudaFreeAsync(g->min_arena, 0);
     delete g;
 }
@@ -283,6 +288,11 @@ DevGraph view_with(const moss_graph *g, int eff) {
     const bool use_filter = eff == MOSS_PROBE_FILTER && (g->built >> 6 & 1u);
     d.hash = use_hash ? reinterpret_cast<const uint4 *>(g->hash) : nullptr;
     d.filter = use_hash && use_filter ? g->filter : nullptr;
+    const bool hubs = use_hash && use_filter && g->hub_bits;
+    d.hub_map = hubs ? g->hub_map : nullptr;
+    d.hub_bits = hubs ? g->hub_bits : nullptr;
+    d.hubs = hub_capacity(g->n);
+    d.hub_shift = 32 - hub_map_bits(d.hubs);
     uint32_t lg = 0;
     while ((1ULL << lg) < g->hash_buckets) ++lg;
     d.hash_mask = use_hash ? (uint32_t)(g->hash_buckets - 1) : 0;
@@ -564,6 +574,10 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
             return cuda_fail(e, "allocating edge filter");
         g->filter_words = words;
     }
+    if (want_filter && !g->hub_mem) {
+        if ((e = pool_alloc(g->device, &g->hub_mem, hub_bytes(g->n), s)) != cudaSuccess)
+            return cuda_fail(e, "allocating hub adjacency");
+    }
     if ((e = pool_alloc(g->device, &scratch, sigma_bytes + seed_bytes, s)) != cudaSuccess)
         return cuda_fail(e, "allocating scratch");
     uint32_t *idx = static_cast<uint32_t *>(scratch);
@@ -619,6 +633,8 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
         while ((1ULL << lf) < words) ++lf;
         eh = cudaMemsetAsync(g->filter, 0, words * 4, sh);
         if (eh == cudaSuccess) eh = launch_edge_filter(g->nnz, g->col, g->owner, g->filter, 64 - lf, sh);
+        if (eh == cudaSuccess) eh = launch_hub_tables(g->n, g->vert, g->col, g->hub_mem, &g->hub_map, &g->hub_bits,
+                                                       &g->hub_list, sh);
         filtered = eh == cudaSuccess;
     }
     if (aux) {
@@ -867,6 +883,11 @@ int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t b
         if (!(g->built >> 6 & 1u)) return fail(MOSS_ESTATE, "edge filter not built");
         src = g->filter;
         need = g->filter_words * 4;
+    } else if (table == MOSS_TABLE_HUB_LIST || table == MOSS_TABLE_HUB_BITS) {
+        if (!(g->built >> 6 & 1u) || !g->hub_bits) return fail(MOSS_ESTATE, "hub adjacency not built");
+        const uint64_t h = hub_capacity(g->n);
+        src = table == MOSS_TABLE_HUB_LIST ? static_cast<const void *>(g->hub_list) : g->hub_bits;
+        need = table == MOSS_TABLE_HUB_LIST ? h * 4 : (h * h + 31) / 32 * 4;
     } else if ((table >= MOSS_TABLE_MIN_SEED && table <= MOSS_TABLE_MIN_LIST) || table == MOSS_TABLE_MIN_PICK) {
         if (!(g->built >> 5 & 1u)) return fail(MOSS_ESTATE, "MOSS-4Min tables not built");
         switch (table) {

@@ -192,22 +192,55 @@ __device__ __forceinline__ uint32_t probe_pairs(const uint32_t *col, const uint4
     return found;
 }
 
+// hub index of vertex x behind the filter (kNoHub for a non-hub): the
+// map's home slot, then linear probing (load factor at most 1/2)
+__device__ __forceinline__ uint32_t hub_of(const DevGraph &g, uint32_t x) {
+    const uint32_t mask = (1u << (32 - g.hub_shift)) - 1u;
+    uint32_t h = hub_home(x, g.hub_shift);
+    for (uint32_t it = 0; it <= mask; ++it) {
+        const uint2 e = ld2(g.hub_map + h);
+        if (e.x == x) return e.y;
+        if (e.x == kNoHub) return kNoHub;
+        h = (h + 1) & mask;
+    }
+    return kNoHub;
+}
+
 // Membership tests through the hashed edge set: one 32-byte bucket load per
 // pair in the common case, all P loads issued together.  HINT (behind the
-// filter): the set is far larger than the L2 and a bucket is rarely read
-// twice, so buckets are read evict-first, which keeps the filter, lists and
-// hub slot records resident.
+// filter): a pair of hubs (hub indices ha, hb) is answered by one bit of the
+// hubs' adjacency bitmap; the filter rules out most other pairs; the set is
+// far larger than the L2 and a bucket is rarely read twice, so buckets are
+// read evict-first, which keeps the filter, lists and hub slot records
+// resident.
 template <int P, bool HINT>
-__device__ __forceinline__ uint32_t probe_hash(const DevGraph &g, const uint32_t (&a)[P], const uint32_t (&b)[P]) {
+__device__ __forceinline__ uint32_t probe_hash(const DevGraph &g, const uint32_t (&a)[P], const uint32_t (&b)[P],
+                                               const uint32_t (&ha)[P], const uint32_t (&hb)[P]) {
     uint64_t key[P];
     uint32_t bk[P];
     uint32_t found = 0, pending = (1u << P) - 1u;
+    if (HINT && g.hub_bits) {   // warp-uniform
+        uint32_t word[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const bool both = ha[p] != kNoHub && hb[p] != kNoHub;
+            word[p] = both ? ld1(g.hub_bits + (((uint64_t)ha[p] * g.hubs + hb[p]) >> 5)) : 0u;
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (ha[p] != kNoHub && hb[p] != kNoHub) {
+                found |= ((word[p] >> ((ha[p] * g.hubs + hb[p]) & 31u)) & 1u) << p;
+                pending &= ~(1u << p);
+            }
+        }
+    }
 #pragma unroll
     for (int p = 0; p < P; ++p) key[p] = edge_key(a[p], b[p]);
     if (g.filter) {   // warp-uniform: only pairs the filter cannot rule out go to the set
         uint32_t word[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) word[p] = ld1(g.filter + (filter_hash(key[p]) >> g.filter_shift));
+        for (int p = 0; p < P; ++p)
+            word[p] = pending >> p & 1u ? ld1(g.filter + (filter_hash(key[p]) >> g.filter_shift)) : 0u;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             const uint32_t m = filter_mask(filter_hash(key[p]));
@@ -266,7 +299,11 @@ __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t 
     const uint32_t A[3] = {v, pu.id, w}, B[3] = {r, w, r};
     uint32_t f;
     if (HASH) {
-        f = probe_hash<3, HINT>(g, A, B);
+        const bool hubs = HINT && g.hub_bits;
+        const uint32_t hv = hubs ? hub_of(g, v) : kNoHub, hu = hubs ? hub_of(g, pu.id) : kNoHub;
+        const uint32_t hw = hubs ? hub_of(g, w) : kNoHub, hr = hubs ? hub_of(g, r) : kNoHub;
+        const uint32_t HA[3] = {hv, hu, hw}, HB[3] = {hr, hw, hr};
+        f = probe_hash<3, HINT>(g, A, B, HA, HB);
     } else {
         const uint4 ur = make_uint4(pu.off, pu.deg, 0u, 0u), wr = ld4(g.vert + w), rr = ld4(g.vert + r);
         const uint4 ra[3] = {vr, ur, wr}, rb[3] = {rr, wr, rr};
@@ -303,7 +340,12 @@ __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lu
     const uint32_t A[6] = {pu.id, pu.id, w, v, w, r}, B[6] = {w, r, r, t, t, t};
     uint32_t f;
     if (HASH) {
-        f = probe_hash<6, HINT>(g, A, B);
+        const bool hubs = HINT && g.hub_bits;
+        const uint32_t hv = hubs ? hub_of(g, v) : kNoHub, hu = hubs ? hub_of(g, pu.id) : kNoHub;
+        const uint32_t hw = hubs ? hub_of(g, w) : kNoHub, hr = hubs ? hub_of(g, r) : kNoHub;
+        const uint32_t ht = hubs ? hub_of(g, t) : kNoHub;
+        const uint32_t HA[6] = {hu, hu, hw, hv, hw, hr}, HB[6] = {hw, hr, hr, ht, ht, ht};
+        f = probe_hash<6, HINT>(g, A, B, HA, HB);
     } else {
         const uint4 ur = make_uint4(pu.off, pu.deg, 0u, 0u);
         const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r), tr = ld4(g.vert + t);
@@ -388,7 +430,11 @@ __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *l
     const uint32_t A[3] = {v, u, w}, B[3] = {r, w, r};
     uint32_t f;
     if (HASH) {
-        f = probe_hash<3, HINT>(g, A, B);
+        const bool hubs = HINT && g.hub_bits;
+        const uint32_t hv = hubs ? hub_of(g, v) : kNoHub, hu = hubs ? hub_of(g, u) : kNoHub;
+        const uint32_t hw = hubs ? hub_of(g, w) : kNoHub, hr = hubs ? hub_of(g, r) : kNoHub;
+        const uint32_t HA[3] = {hv, hu, hw}, HB[3] = {hr, hw, hr};
+        f = probe_hash<3, HINT>(g, A, B, HA, HB);
     } else {
         const uint4 vr = make_uint4(mv.x, mv.y, 0u, 0u), ur = make_uint4(sb.x, sb.y, 0u, 0u);
         const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r);
@@ -504,7 +550,12 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
     const uint32_t A[6] = {v, v, u, u, w, r}, B[6] = {r, t, w, t, r, t};
     uint32_t f;
     if (HASH) {
-        f = probe_hash<6, HINT>(g, A, B);
+        const bool hubs = HINT && g.hub_bits;
+        const uint32_t hv = hubs ? hub_of(g, v) : kNoHub, hu = hubs ? hub_of(g, u) : kNoHub;
+        const uint32_t hw = hubs ? hub_of(g, w) : kNoHub, hr = hubs ? hub_of(g, r) : kNoHub;
+        const uint32_t ht = hubs ? hub_of(g, t) : kNoHub;
+        const uint32_t HA[6] = {hv, hv, hu, hu, hw, hr}, HB[6] = {hr, ht, hw, ht, hr, ht};
+        f = probe_hash<6, HINT>(g, A, B, HA, HB);
     } else {
         const uint4 ur = make_uint4(pu.off, pu.deg, 0u, 0u), wr = make_uint4(pw.off, pw.deg, 0u, 0u);
         const uint4 rr = ld4(g.vert + r), tr = ld4(g.vert + t);
@@ -528,12 +579,12 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
 // more than they hide (measured: 6 blocks of 256 threads for every main
 // sampler; Path-5 reaches it only with its second attempt and fallback
 // deferred).  The second-attempt launch runs 5 blocks, the fallback launch 4.
-// Under Philox words the Path-5 and MOSS-4Min samplers and the redraw stages
-// hold the generator's state beside their records and would spill at those
-// register budgets, so they are compiled for one block fewer (4 for the
-// redraws); the grid of a main launch follows each instance's occupancy.
+// Under Philox words the samplers and the redraw stages hold the generator's
+// state beside their records and would spill at those register budgets, so
+// they are compiled for one block fewer (4 for the redraws); the grid of a
+// main launch follows each instance's occupancy.
 template <int METHOD, int RNG>
-constexpr int min_blocks() { return RNG == kRngPhilox && (METHOD == 2 || METHOD == 3) ? 5 : 6; }
+constexpr int min_blocks() { return RNG == kRngPhilox ? 5 : 6; }
 template <int STAGE>
 constexpr int defer_min_blocks() { return STAGE == 1 ? 5 : 4; }
 template <int STAGE, int RNG>

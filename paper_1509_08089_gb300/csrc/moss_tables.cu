@@ -23,6 +23,7 @@
 // Both prefix sums and every search are parallel, so the per-list tables
 // (a warp per list) and the vertex tables (a block scan over V, then one
 // thread per item) are built without a sequential pass.
+#include <algorithm>
 #include <atomic>
 
 #include "moss_alias.cuh"
@@ -919,6 +920,95 @@ __global__ void k_seed_fill(uint32_t n, const DevTotals *tot, SeedTasks tasks) {
     }
 }
 
+// ---- hub adjacency (behind the edge filter)
+constexpr uint32_t kHubBins = 65536;   // degree histogram, degrees >= 65535 in the last bin
+
+__global__ void k_hub_hist(uint32_t n, const uint4 *__restrict__ vert, uint32_t *hist) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t d = vert[v].y;
+        if (d) atomicAdd(hist + (d < kHubBins - 1 ? d : kHubBins - 1), 1u);
+    }
+}
+
+// the smallest degree D >= 1 with at most `hubs` vertices of degree >= D
+// (kHubBins when even the last bin holds more): one block of 1,024 threads,
+// 64 bins each, a suffix scan of the threads' totals
+__global__ void __launch_bounds__(1024) k_hub_cut(const uint32_t *hist, uint32_t hubs, uint32_t *cut) {
+    __shared__ uint32_t suf[1025];
+    __shared__ uint32_t best;
+    const uint32_t t = threadIdx.x, b0 = t * 64;
+    uint32_t s = 0;
+    for (uint32_t b = b0; b < b0 + 64; ++b) s += hist[b];
+    suf[t] = s;
+    if (t == 0) { suf[1024] = 0; best = kHubBins; }
+    __syncthreads();
+    for (uint32_t d = 1; d < 1024; d <<= 1) {   // inclusive suffix scan (Hillis-Steele)
+        const uint32_t x = t + d < 1024 ? suf[t + d] : 0;
+        __syncthreads();
+        suf[t] += x;
+        __syncthreads();
+    }
+    uint32_t above = suf[t] - s;   // vertices with degree in higher threads' bins
+    uint32_t mine = kHubBins;
+    for (int b = (int)b0 + 63; b >= (int)b0; --b) {
+        above += hist[b];
+        if (above > hubs) break;
+        if (b >= 1) mine = (uint32_t)b;
+    }
+    atomicMin(&best, mine);
+    __syncthreads();
+    if (t == 0) *cut = best;
+}
+
+__device__ __forceinline__ uint32_t hub_lookup(const uint2 *map, uint32_t shift, uint32_t v) {
+    const uint32_t mask = (1u << (32 - shift)) - 1u;
+    uint32_t h = hub_home(v, shift);
+    for (uint32_t it = 0; it <= mask; ++it) {
+        const uint2 e = map[h];
+        if (e.x == v) return e.y;
+        if (e.x == kNoHub) return kNoHub;
+        h = (h + 1) & mask;
+    }
+    return kNoHub;
+}
+
+// hubs: the vertices of degree >= cut, indexed in arrival order, in the map
+__global__ void k_hub_place(uint32_t n, const uint4 *__restrict__ vert, const uint32_t *cut, uint2 *map,
+                            uint32_t shift, uint32_t *list, uint32_t *count) {
+    const uint32_t D = *cut;
+    const uint32_t mask = (1u << (32 - shift)) - 1u;
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+        if (D >= kHubBins || vert[v].y < D) continue;
+        const uint32_t i = atomicAdd(count, 1u);
+        list[i] = (uint32_t)v;
+        uint32_t h = hub_home((uint32_t)v, shift);
+        for (uint32_t it = 0; it <= mask; ++it) {
+            if (atomicCAS(&map[h].x, kNoHub, (uint32_t)v) == kNoHub) {
+                map[h].y = i;
+                break;
+            }
+            h = (h + 1) & mask;
+        }
+    }
+}
+
+// a warp per hub i: bit i H + j for every hub j in N_(hub i)
+__global__ void k_hub_bits(const uint32_t *list, const uint32_t *count, uint32_t hubs, const uint4 *__restrict__ vert,
+                           const uint32_t *__restrict__ col, const uint2 *map, uint32_t shift, uint32_t *bits) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nh = *count;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nh; i += (gridDim.x * blockDim.x) >> 5) {
+        const uint4 r = vert[list[i]];
+        for (uint32_t k = lane; k < r.y; k += 32) {
+            const uint32_t j = hub_lookup(map, shift, col[r.x + k]);
+            if (j != kNoHub) {
+                const uint64_t bit = (uint64_t)i * hubs + j;
+                atomicOr(bits + (bit >> 5), 1u << (bit & 31));
+            }
+        }
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- launches ---
@@ -1011,6 +1101,51 @@ cudaError_t launch_edge_filter(uint64_t nnz, const uint32_t *col, const uint32_t
     if (nnz == 0) return cudaSuccess;
     k_edge_filter<<<flat_blocks(nnz), 256, 0, s>>>(nnz, col, owner, filter, shift);
     return cudaGetLastError();
+}
+
+uint64_t hub_bytes(uint32_t n) {
+    const uint64_t h = hub_capacity(n), slots = 1ull << hub_map_bits((uint32_t)h);
+    return slots * 8 + h * 4 + (h * h + 31) / 32 * 4 + 256 + (uint64_t)kHubBins * 4 + 16 * 256;
+}
+
+cudaError_t launch_hub_tables(uint32_t n, const uint4 *vert, const uint32_t *col, void *mem, uint2 **map_out,
+                              uint32_t **bits_out, uint32_t **list_out, cudaStream_t s) {
+    const uint32_t H = hub_capacity(n), mb = hub_map_bits(H), shift = 32 - mb;
+    const uint64_t slots = 1ull << mb, words = ((uint64_t)H * H + 31) / 32;
+    uint8_t *p = static_cast<uint8_t *>(mem);
+    auto take = [&](uint64_t bytes) {
+        uint8_t *r = p;
+        p += (bytes + 255) & ~(uint64_t)255;
+        return r;
+    };
+    uint2 *map = reinterpret_cast<uint2 *>(take(slots * 8));
+    uint32_t *bits = reinterpret_cast<uint32_t *>(take(words * 4));
+    uint32_t *list = reinterpret_cast<uint32_t *>(take((uint64_t)H * 4));
+    uint32_t *hist = reinterpret_cast<uint32_t *>(take((uint64_t)kHubBins * 4));
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(take(8));   // [0] hubs placed, [1] the degree cut
+    cudaError_t e = cudaMemsetAsync(map, 0xFF, slots * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(list, 0xFF, (uint64_t)H * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bits, 0, words * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, (uint64_t)kHubBins * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 8, s);
+    if (e != cudaSuccess) return e;
+    const unsigned vb = (unsigned)std::min<uint64_t>(((uint64_t)n + 255) / 256, 4096);
+    if (n) {
+        k_hub_hist<<<vb, 256, 0, s>>>(n, vert, hist);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_hub_cut<<<1, 1024, 0, s>>>(hist, H, cnt + 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (n) {
+        k_hub_place<<<vb, 256, 0, s>>>(n, vert, cnt + 1, map, shift, list, cnt);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_hub_bits<<<(H + 7) / 8, 256, 0, s>>>(list, cnt, H, vert, col, map, shift, bits);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    *map_out = map;
+    *bits_out = bits;
+    *list_out = list;
+    return cudaSuccess;
 }
 
 cudaError_t launch_sigma_alias(uint32_t n, uint64_t nnz, const uint4 *vert, const uint32_t *acc, const uint32_t *owner,

@@ -185,6 +185,39 @@ def test_edge_filter_bits(name):
     g.set_probe(moss.PROBE_AUTO)
 
 
+def hub_capacity(n):
+    return min(8192, max(16, n // 16))
+
+
+@pytest.mark.parametrize("name", ["gnp12", "cl_n200", "cl_n2k", "cl_n100k", "hub70k", "circ8"])
+def test_hub_adjacency_bits(name):
+    """The hubs are every vertex of degree >= D, D the smallest degree >= 1
+    with at most H of them, and their bitmap holds exactly their edges."""
+    rp, col, og, g = pair(name)
+    g.set_probe(moss.PROBE_FILTER)
+    try:
+        n = len(rp) - 1
+        H = hub_capacity(n)
+        deg = np.diff(rp.astype(np.int64))
+        lst = moss.moss_table_export(g.handle, moss.TABLE_HUB_LIST, np.zeros(H, dtype=np.uint32))
+        bits = moss.moss_table_export(g.handle, moss.TABLE_HUB_BITS, np.zeros((H * H + 31) // 32, dtype=np.uint32))
+    finally:
+        g.set_probe(moss.PROBE_AUTO)
+    D = next(d for d in range(1, int(deg.max()) + 2) if (deg >= d).sum() <= H)
+    hubs = lst[lst != 0xFFFFFFFF].astype(np.int64)
+    assert np.array_equal(np.sort(hubs), np.nonzero(deg >= D)[0])
+    assert np.all(lst[len(hubs):] == 0xFFFFFFFF)
+    assert (len(hubs) == 0) == (name == "circ8")     # a regular graph of more than H vertices has none
+    index = np.full(n, -1, dtype=np.int64)
+    index[hubs] = np.arange(len(hubs))
+    want = np.zeros(H * H, dtype=bool)
+    for i, v in enumerate(hubs):
+        j = index[col[rp[v]:rp[v + 1]].astype(np.int64)]
+        want[i * H + j[j >= 0]] = True
+    got = np.unpackbits(bits.view(np.uint8), bitorder="little")[:H * H].astype(bool)
+    assert np.array_equal(got, want)
+
+
 RNGS = [("splitmix64", moss.RNG_SPLITMIX64, oracle.SPLITMIX64), ("philox4x32", moss.RNG_PHILOX4X32, oracle.PHILOX4X32)]
 
 
