@@ -296,9 +296,10 @@ def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False, tw
     """Kernels of one step: load 7 (vertices, owners, slot weights, short and
     long slot scans, twins, totals); build 8 (two sigma alias passes, the
     alias-half fill, four alias phases of the vertex tables, edge hash), 3
-    more (the level split) for two-level vertex tables, 5 more behind the
+    more (the level split) for two-level vertex tables, 7 more behind the
     edge filter (the filter, and the hubs' degree histogram, degree cut,
-    map and adjacency bits); MOSS-4Min build 12
+    rank-table bits, their scan, the prefixes and list, and the adjacency
+    bits); MOSS-4Min build 12
     (three sort tiers, slot records, two alias passes, pick records, total,
     four alias phases of its vertex table), again 3 more with two levels; per
     sub-method a sampler and a reduce, Path-5 per chunk of DEFER_CHUNK ids a
@@ -306,7 +307,7 @@ def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False, tw
     finalize."""
     from paper_1509_08089_gb300.dist import sub_budgets
     split = 3 if two_level else 0
-    n = 7 + 8 + split + (5 if filtered else 0) + ((12 + split) if mix else 0) + 1
+    n = 7 + 8 + split + (7 if filtered else 0) + ((12 + split) if mix else 0) + 1
     for m, K in sub_budgets(k, budget, mix):
         n += 4 * -(-K // DEFER_CHUNK) if m == 2 else 2
     return n
@@ -323,7 +324,7 @@ def sampler_tables_bytes(rp, probe: str, methods) -> int:
     and a 32 B vertex alias record per vertex and method, and the hashed edge
     set (32 B buckets, the next power of two >= nnz / 2) or the edge filter in
     front of it (4 B words, the largest power of two <= nnz / 8) with the
-    hubs' map (8 B slots, the power of two >= 2 H) and adjacency bits (H^2,
+    hubs' rank table (8 B per 32 vertices) and adjacency bits (H^2,
     H = min(8192, max(16, n / 16)))."""
     n, nnz = len(rp) - 1, int(rp[-1])
     total = nnz * (32 + 4) + n * (16 + 32 * len(methods))
@@ -338,10 +339,7 @@ def sampler_tables_bytes(rp, probe: str, methods) -> int:
             w <<= 1
         total += 4 * w
         h = min(8192, max(16, n // 16))
-        slots = 1
-        while slots < 2 * h:
-            slots <<= 1
-        total += 8 * slots + (h * h + 31) // 32 * 4
+        total += 8 * ((n + 31) // 32) + (h * h + 31) // 32 * 4
     return total
 
 

@@ -463,7 +463,8 @@ int moss_graph_stats(const moss_graph *g, moss_stats *out);
  *   MOSS_TABLE_HUB_LIST  H x uint32: the hubs -- every vertex of degree >= D,
  *                        D the smallest degree >= 1 with at most H such
  *                        vertices, H = min(8192, max(16, n / 16)) -- in
- *                        arbitrary order, 0xFFFFFFFF past the last
+ *                        ascending id order (hub i is the i-th),
+ *                        0xFFFFFFFF past the last
  *   MOSS_TABLE_HUB_BITS  ceil(H^2 / 32) x uint32: bit i H + j (word / 32, bit
  *                        % 32) set iff hubs i and j are adjacent; edge probes
  *                        between two hubs are answered from these bits

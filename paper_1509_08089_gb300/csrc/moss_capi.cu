@@ -223,8 +223,8 @@ struct moss_graph {
     uint64_t hash_buckets = 0;
     uint32_t *filter = nullptr;  // Bloom filter in front of the hash
     uint64_t filter_words = 0;
-    void *hub_mem = nullptr;     // hub adjacency behind the filter: map, bitmap, hub list
-    uint2 *hub_map = nullptr;
+    void *hub_mem = nullptr;     // hub adjacency behind the filter: rank table, bitmap, hub list
+    uint2 *hub_rank = nullptr;
     uint32_t *hub_bits = nullptr;
     uint32_t *hub_list = nullptr;
     moss_result res_host{};      // host staging of the result
@@ -289,10 +289,9 @@ DevGraph view_with(const moss_graph *g, int eff) {
     d.hash = use_hash ? reinterpret_cast<const uint4 *>(g->hash) : nullptr;
     d.filter = use_hash && use_filter ? g->filter : nullptr;
     const bool hubs = use_hash && use_filter && g->hub_bits;
-    d.hub_map = hubs ? g->hub_map : nullptr;
+    d.hub_rank = hubs ? g->hub_rank : nullptr;
     d.hub_bits = hubs ? g->hub_bits : nullptr;
     d.hubs = hub_capacity(g->n);
-    d.hub_shift = 32 - hub_map_bits(d.hubs);
     uint32_t lg = 0;
     while ((1ULL << lg) < g->hash_buckets) ++lg;
     d.hash_mask = use_hash ? (uint32_t)(g->hash_buckets - 1) : 0;
@@ -633,7 +632,7 @@ int moss_build_tables(moss_graph *g, unsigned k_mask, void *stream) {
         while ((1ULL << lf) < words) ++lf;
         eh = cudaMemsetAsync(g->filter, 0, words * 4, sh);
         if (eh == cudaSuccess) eh = launch_edge_filter(g->nnz, g->col, g->owner, g->filter, 64 - lf, sh);
-        if (eh == cudaSuccess) eh = launch_hub_tables(g->n, g->vert, g->col, g->hub_mem, &g->hub_map, &g->hub_bits,
+        if (eh == cudaSuccess) eh = launch_hub_tables(g->n, g->vert, g->col, g->hub_mem, &g->hub_rank, &g->hub_bits,
                                                        &g->hub_list, sh);
         filtered = eh == cudaSuccess;
     }

@@ -110,19 +110,19 @@ struct DevGraph {
     uint32_t rng;           // word generator: kRngSplitMix or kRngPhilox
     uint32_t nheavy[kMethods];   // heavy columns of each vertex table (SeedLevel)
     uint64_t tlight[kMethods];   // light-level bound of each vertex table
-    const uint2 *hub_map;        // behind the filter: {vertex, hub index} map of the hubs, or null
-    const uint32_t *hub_bits;    // their H x H adjacency bits
-    uint32_t hub_shift;          // 32 - log2(map slots)
+    const uint2 *hub_rank;       // behind the filter: per 32 vertices {hubs before them, hub bits}, or null
+    const uint32_t *hub_bits;    // the hubs' H x H adjacency bits
     uint32_t hubs;               // H
 };
 
 // ------------------------------------------------------- hub adjacency --
 // Behind the edge filter (graphs whose edge set leaves the L2), pairs of hubs
-// -- the vertices of highest degree, at most H = min(8192, max(16, n / 16))
-// -- are answered from an H x H bitmap of their adjacency (bit i H + j: hubs
-// i and j adjacent), exactly and from the L2; a vertex's hub index comes from
-// an open-addressing map of 2H slots (a power of two) of {vertex, index},
-// empty slots {kNoHub, kNoHub}.
+// -- every vertex of degree >= D, D the smallest degree with at most
+// H = min(8192, max(16, n / 16)) of them -- are answered from an H x H bitmap
+// of their adjacency (bit i H + j: hubs i and j adjacent), exactly and from
+// the L2.  Hub i is the i-th hub in ascending id order; its index comes from
+// one 8-byte load of the rank table: entry x / 32 = {hubs below 32 (x / 32),
+// bit t set iff vertex 32 (x / 32) + t is a hub}.
 constexpr uint32_t kNoHub = 0xFFFFFFFFu;
 constexpr uint32_t kMaxHubs = 8192;
 
@@ -130,12 +130,10 @@ inline uint32_t hub_capacity(uint32_t n) {
     const uint32_t h = n / 16 < 16 ? 16 : n / 16;
     return h < kMaxHubs ? h : kMaxHubs;
 }
-inline uint32_t hub_map_bits(uint32_t hubs) {   // log2 of the map's slots: the power of two >= 2 H
-    uint32_t b = 1;
-    while ((1u << b) < 2 * hubs) ++b;
-    return b;
+__device__ __forceinline__ uint32_t hub_index(uint2 e, uint32_t x) {
+    const uint32_t bit = 1u << (x & 31u);
+    return (e.y & bit) ? e.x + (uint32_t)__popc(e.y & (bit - 1u)) : kNoHub;
 }
-__host__ __device__ inline uint32_t hub_home(uint32_t v, uint32_t shift) { return (v * 0x9E3779B1u) >> shift; }
 
 // ------------------------------------------------------- hashed edge set --
 // Key of the undirected edge {a, b}: (min << 32) | max; empty slot: ~0.
@@ -353,11 +351,11 @@ cudaError_t launch_edge_hash(uint64_t nnz, const uint32_t *col, const uint32_t *
 cudaError_t launch_edge_filter(uint64_t nnz, const uint32_t *col, const uint32_t *owner, uint32_t *filter,
                                uint32_t shift, cudaStream_t s);
 // hub adjacency of the edge filter in `mem` (hub_bytes(n) bytes, kept with the
-// filter): the map, the bitmap and the hub list (vertex of each index,
+// filter): the rank table, the bitmap and the hub list (ascending ids,
 // kNoHub past the last) come back through the out pointers; `mem` also
 // holds the scratch of the build
 uint64_t hub_bytes(uint32_t n);
-cudaError_t launch_hub_tables(uint32_t n, const uint4 *vert, const uint32_t *col, void *mem, uint2 **map_out,
+cudaError_t launch_hub_tables(uint32_t n, const uint4 *vert, const uint32_t *col, void *mem, uint2 **rank_out,
                               uint32_t **bits_out, uint32_t **list_out, cudaStream_t s);
 // aux (nullable, already forked from s): the long lists go to aux->a[long_stream]
 cudaError_t launch_sigma_alias(uint32_t n, uint64_t nnz, const uint4 *vert, const uint32_t *acc, const uint32_t *owner,

@@ -42,6 +42,11 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kLut = 1024;
+// hub-pair bits behind the filter, per method (MOSS-4, T-5, Path-5, MOSS-4Min):
+// measured on the 34M-edge graph against the same build without them, 5e8
+// samples per call, T-5 -7.5%, Path-5 -16%, MOSS-4Min -27%, MOSS-4 +0.8% (its
+// three probes hold few hub pairs)
+constexpr bool kHubProbes[kMethods] = {false, true, true, true};
 
 __device__ uint8_t g_lut4[64];
 __device__ uint8_t g_lut5[1024];
@@ -192,69 +197,59 @@ __device__ __forceinline__ uint32_t probe_pairs(const uint32_t *col, const uint4
     return found;
 }
 
-// hub index of vertex x behind the filter (kNoHub for a non-hub): the
-// map's home slot, then linear probing (load factor at most 1/2)
-__device__ __forceinline__ uint32_t hub_of(const DevGraph &g, uint32_t x) {
-    const uint32_t mask = (1u << (32 - g.hub_shift)) - 1u;
-    uint32_t h = hub_home(x, g.hub_shift);
-    for (uint32_t it = 0; it <= mask; ++it) {
-        const uint2 e = ld2(g.hub_map + h);
-        if (e.x == x) return e.y;
-        if (e.x == kNoHub) return kNoHub;
-        h = (h + 1) & mask;
-    }
-    return kNoHub;
-}
-
 // Membership tests through the hashed edge set: one 32-byte bucket load per
 // pair in the common case, all P loads issued together.  HINT (behind the
-// filter): a pair of hubs (hub indices ha, hb) is answered by one bit of the
-// hubs' adjacency bitmap; the filter rules out most other pairs; the set is
-// far larger than the L2 and a bucket is rarely read twice, so buckets are
-// read evict-first, which keeps the filter, lists and hub slot records
-// resident.
-template <int P, bool HINT>
-__device__ __forceinline__ uint32_t probe_hash(const DevGraph &g, const uint32_t (&a)[P], const uint32_t (&b)[P],
-                                               const uint32_t (&ha)[P], const uint32_t (&hb)[P]) {
-    uint64_t key[P];
+// filter): the filter rules out most pairs; the set is far larger than the
+// L2 and a bucket is rarely read twice, so buckets are read evict-first,
+// which keeps the filter, lists and hub slot records resident.  With HUB,
+// the ends' rank-table entries come first (one 8-byte load per vertex, all
+// together), and a pair of two hubs is answered by one bit of the hubs'
+// adjacency bitmap, loaded beside the other pairs' filter words.
+template <int P, bool HINT, bool HUB>
+__device__ __forceinline__ uint32_t probe_hash(const DevGraph &g, const uint32_t (&a)[P], const uint32_t (&b)[P]) {
     uint32_t bk[P];
     uint32_t found = 0, pending = (1u << P) - 1u;
-    if (HINT && g.hub_bits) {   // warp-uniform
+    if (g.filter) {   // warp-uniform: only pairs the filter cannot rule out go to the set
+        uint32_t hubpair = 0, bit[P];
+        if (HINT && HUB && g.hub_rank) {   // warp-uniform
+            uint2 ea[P], eb[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                ea[p] = ld2(g.hub_rank + (a[p] >> 5));
+                eb[p] = ld2(g.hub_rank + (b[p] >> 5));
+            }
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const uint32_t ia = hub_index(ea[p], a[p]), ib = hub_index(eb[p], b[p]);
+                bit[p] = ia * g.hubs + ib;
+                if (ia != kNoHub && ib != kNoHub) hubpair |= 1u << p;
+            }
+        }
         uint32_t word[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const bool both = ha[p] != kNoHub && hb[p] != kNoHub;
-            word[p] = both ? ld1(g.hub_bits + (((uint64_t)ha[p] * g.hubs + hb[p]) >> 5)) : 0u;
-        }
+        for (int p = 0; p < P; ++p)
+            word[p] = ld1(hubpair >> p & 1u ? g.hub_bits + (bit[p] >> 5)
+                                             : g.filter + (filter_hash(edge_key(a[p], b[p])) >> g.filter_shift));
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            if (ha[p] != kNoHub && hb[p] != kNoHub) {
-                found |= ((word[p] >> ((ha[p] * g.hubs + hb[p]) & 31u)) & 1u) << p;
+            if (hubpair >> p & 1u) {
+                found |= (word[p] >> (bit[p] & 31u) & 1u) << p;
                 pending &= ~(1u << p);
+            } else {
+                const uint32_t m = filter_mask(filter_hash(edge_key(a[p], b[p])));
+                if ((word[p] & m) != m) pending &= ~(1u << p);
             }
         }
     }
 #pragma unroll
-    for (int p = 0; p < P; ++p) key[p] = edge_key(a[p], b[p]);
-    if (g.filter) {   // warp-uniform: only pairs the filter cannot rule out go to the set
-        uint32_t word[P];
-#pragma unroll
-        for (int p = 0; p < P; ++p)
-            word[p] = pending >> p & 1u ? ld1(g.filter + (filter_hash(key[p]) >> g.filter_shift)) : 0u;
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            const uint32_t m = filter_mask(filter_hash(key[p]));
-            if ((word[p] & m) != m) pending &= ~(1u << p);
-        }
-    }
-#pragma unroll
-    for (int p = 0; p < P; ++p) bk[p] = edge_bucket(key[p], g.hash_shift);
+    for (int p = 0; p < P; ++p) bk[p] = edge_bucket(edge_key(a[p], b[p]), g.hash_shift);
     for (uint32_t it = 0; pending != 0 && it <= g.hash_mask; ++it) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (pending >> p & 1u) {
                 const Sector e = HINT ? ld8_first(g.hash + 2 * (uint64_t)bk[p]) : ld8(g.hash + 2 * (uint64_t)bk[p]);
-                const uint32_t lo = (uint32_t)key[p], hi = (uint32_t)(key[p] >> 32);
+                const uint64_t key = edge_key(a[p], b[p]);
+                const uint32_t lo = (uint32_t)key, hi = (uint32_t)(key >> 32);
                 const bool hit = (e.lo.x == lo && e.lo.y == hi) || (e.lo.z == lo && e.lo.w == hi) ||
                                  (e.hi.x == lo && e.hi.y == hi) || (e.hi.z == lo && e.hi.w == hi);
                 if (hit) {
@@ -299,11 +294,7 @@ __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t 
     const uint32_t A[3] = {v, pu.id, w}, B[3] = {r, w, r};
     uint32_t f;
     if (HASH) {
-        const bool hubs = HINT && g.hub_bits;
-        const uint32_t hv = hubs ? hub_of(g, v) : kNoHub, hu = hubs ? hub_of(g, pu.id) : kNoHub;
-        const uint32_t hw = hubs ? hub_of(g, w) : kNoHub, hr = hubs ? hub_of(g, r) : kNoHub;
-        const uint32_t HA[3] = {hv, hu, hw}, HB[3] = {hr, hw, hr};
-        f = probe_hash<3, HINT>(g, A, B, HA, HB);
+        f = probe_hash<3, HINT, kHubProbes[0]>(g, A, B);
     } else {
         const uint4 ur = make_uint4(pu.off, pu.deg, 0u, 0u), wr = ld4(g.vert + w), rr = ld4(g.vert + r);
         const uint4 ra[3] = {vr, ur, wr}, rb[3] = {rr, wr, rr};
@@ -340,12 +331,7 @@ __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lu
     const uint32_t A[6] = {pu.id, pu.id, w, v, w, r}, B[6] = {w, r, r, t, t, t};
     uint32_t f;
     if (HASH) {
-        const bool hubs = HINT && g.hub_bits;
-        const uint32_t hv = hubs ? hub_of(g, v) : kNoHub, hu = hubs ? hub_of(g, pu.id) : kNoHub;
-        const uint32_t hw = hubs ? hub_of(g, w) : kNoHub, hr = hubs ? hub_of(g, r) : kNoHub;
-        const uint32_t ht = hubs ? hub_of(g, t) : kNoHub;
-        const uint32_t HA[6] = {hu, hu, hw, hv, hw, hr}, HB[6] = {hw, hr, hr, ht, ht, ht};
-        f = probe_hash<6, HINT>(g, A, B, HA, HB);
+        f = probe_hash<6, HINT, kHubProbes[1]>(g, A, B);
     } else {
         const uint4 ur = make_uint4(pu.off, pu.deg, 0u, 0u);
         const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r), tr = ld4(g.vert + t);
@@ -430,11 +416,7 @@ __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *l
     const uint32_t A[3] = {v, u, w}, B[3] = {r, w, r};
     uint32_t f;
     if (HASH) {
-        const bool hubs = HINT && g.hub_bits;
-        const uint32_t hv = hubs ? hub_of(g, v) : kNoHub, hu = hubs ? hub_of(g, u) : kNoHub;
-        const uint32_t hw = hubs ? hub_of(g, w) : kNoHub, hr = hubs ? hub_of(g, r) : kNoHub;
-        const uint32_t HA[3] = {hv, hu, hw}, HB[3] = {hr, hw, hr};
-        f = probe_hash<3, HINT>(g, A, B, HA, HB);
+        f = probe_hash<3, HINT, kHubProbes[3]>(g, A, B);
     } else {
         const uint4 vr = make_uint4(mv.x, mv.y, 0u, 0u), ur = make_uint4(sb.x, sb.y, 0u, 0u);
         const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r);
@@ -550,12 +532,7 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
     const uint32_t A[6] = {v, v, u, u, w, r}, B[6] = {r, t, w, t, r, t};
     uint32_t f;
     if (HASH) {
-        const bool hubs = HINT && g.hub_bits;
-        const uint32_t hv = hubs ? hub_of(g, v) : kNoHub, hu = hubs ? hub_of(g, u) : kNoHub;
-        const uint32_t hw = hubs ? hub_of(g, w) : kNoHub, hr = hubs ? hub_of(g, r) : kNoHub;
-        const uint32_t ht = hubs ? hub_of(g, t) : kNoHub;
-        const uint32_t HA[6] = {hv, hv, hu, hu, hw, hr}, HB[6] = {hr, ht, hw, ht, hr, ht};
-        f = probe_hash<6, HINT>(g, A, B, HA, HB);
+        f = probe_hash<6, HINT, kHubProbes[2]>(g, A, B);
     } else {
         const uint4 ur = make_uint4(pu.off, pu.deg, 0u, 0u), wr = make_uint4(pw.off, pw.deg, 0u, 0u);
         const uint4 rr = ld4(g.vert + r), tr = ld4(g.vert + t);

@@ -921,26 +921,45 @@ __global__ void k_seed_fill(uint32_t n, const DevTotals *tot, SeedTasks tasks) {
 }
 
 // ---- hub adjacency (behind the edge filter)
-constexpr uint32_t kHubBins = 65536;   // degree histogram, degrees >= 65535 in the last bin
+constexpr uint32_t kHubBins = 65536;    // degree histogram, degrees >= 65535 in the last bin
+constexpr uint32_t kHubSmallBins = 2048;  // counted in shared memory first
+constexpr uint32_t kHubWarpWords = 16;    // rank-table entries (32 vertices each) per warp
+constexpr uint32_t kHubBlockWarps = 8;
 
-__global__ void k_hub_hist(uint32_t n, const uint4 *__restrict__ vert, uint32_t *hist) {
+__global__ void __launch_bounds__(256) k_hub_hist(uint32_t n, const uint4 *__restrict__ vert, uint32_t *hist) {
+    __shared__ uint32_t sh[kHubSmallBins];
+    for (uint32_t b = threadIdx.x; b < kHubSmallBins; b += blockDim.x) sh[b] = 0;
+    __syncthreads();
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t d = vert[v].y;
-        if (d) atomicAdd(hist + (d < kHubBins - 1 ? d : kHubBins - 1), 1u);
+        if (d < kHubSmallBins) {
+            if (d) atomicAdd(sh + d, 1u);
+        } else {
+            atomicAdd(hist + (d < kHubBins - 1 ? d : kHubBins - 1), 1u);
+        }
     }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < kHubSmallBins; b += blockDim.x)
+        if (sh[b]) atomicAdd(hist + b, sh[b]);
 }
 
 // the smallest degree D >= 1 with at most `hubs` vertices of degree >= D
 // (kHubBins when even the last bin holds more): one block of 1,024 threads,
-// 64 bins each, a suffix scan of the threads' totals
+// 64 bins each (read as 16 independent 16-byte loads), a suffix scan of the
+// threads' totals; only the thread whose bins hold the crossing walks them
 __global__ void __launch_bounds__(1024) k_hub_cut(const uint32_t *hist, uint32_t hubs, uint32_t *cut) {
-    __shared__ uint32_t suf[1025];
+    __shared__ uint32_t suf[1024];
     __shared__ uint32_t best;
     const uint32_t t = threadIdx.x, b0 = t * 64;
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(hist + b0);
     uint32_t s = 0;
-    for (uint32_t b = b0; b < b0 + 64; ++b) s += hist[b];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const uint4 x = h4[q];
+        s += x.x + x.y + x.z + x.w;
+    }
     suf[t] = s;
-    if (t == 0) { suf[1024] = 0; best = kHubBins; }
+    if (t == 0) best = kHubBins;
     __syncthreads();
     for (uint32_t d = 1; d < 1024; d <<= 1) {   // inclusive suffix scan (Hillis-Steele)
         const uint32_t x = t + d < 1024 ? suf[t + d] : 0;
@@ -948,59 +967,96 @@ __global__ void __launch_bounds__(1024) k_hub_cut(const uint32_t *hist, uint32_t
         suf[t] += x;
         __syncthreads();
     }
-    uint32_t above = suf[t] - s;   // vertices with degree in higher threads' bins
+    const uint32_t above = suf[t] - s;   // vertices with degree in higher threads' bins
     uint32_t mine = kHubBins;
-    for (int b = (int)b0 + 63; b >= (int)b0; --b) {
-        above += hist[b];
-        if (above > hubs) break;
-        if (b >= 1) mine = (uint32_t)b;
+    if (suf[t] <= hubs) {                 // every bin of this thread qualifies
+        mine = b0 >= 1 ? b0 : 1u;
+    } else if (above <= hubs) {           // the crossing lies in this thread's bins
+        uint32_t run = above;
+        for (int b = (int)b0 + 63; b >= (int)b0; --b) {
+            run += hist[b];
+            if (run > hubs) break;
+            if (b >= 1) mine = (uint32_t)b;
+        }
     }
     atomicMin(&best, mine);
     __syncthreads();
     if (t == 0) *cut = best;
 }
 
-__device__ __forceinline__ uint32_t hub_lookup(const uint2 *map, uint32_t shift, uint32_t v) {
-    const uint32_t mask = (1u << (32 - shift)) - 1u;
-    uint32_t h = hub_home(v, shift);
-    for (uint32_t it = 0; it <= mask; ++it) {
-        const uint2 e = map[h];
-        if (e.x == v) return e.y;
-        if (e.x == kNoHub) return kNoHub;
-        h = (h + 1) & mask;
+// rank-table bits: warp w of the grid takes entries [w kHubWarpWords, +kHubWarpWords),
+// a ballot of deg >= D per 32 vertices; its hub count goes to warps[w]
+__global__ void __launch_bounds__(256) k_hub_words(uint32_t n, const uint4 *__restrict__ vert, const uint32_t *cut,
+                                                   uint2 *rank, uint32_t words, uint32_t *warps) {
+    const uint32_t D = *cut, lane = threadIdx.x & 31;
+    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t e0 = w * kHubWarpWords;
+    uint32_t count = 0;
+    for (uint32_t e = e0; e < e0 + kHubWarpWords && e < words; ++e) {
+        const uint64_t v = (uint64_t)e * 32 + lane;
+        const bool hub = D < kHubBins && v < n && vert[v].y >= D;
+        const uint32_t bits = __ballot_sync(0xffffffffu, hub);
+        if (lane == 0) rank[e].y = bits;
+        count += __popc(bits);
     }
-    return kNoHub;
+    if (lane == 0 && e0 < words) warps[w] = count;
 }
 
-// hubs: the vertices of degree >= cut, indexed in arrival order, in the map
-__global__ void k_hub_place(uint32_t n, const uint4 *__restrict__ vert, const uint32_t *cut, uint2 *map,
-                            uint32_t shift, uint32_t *list, uint32_t *count) {
-    const uint32_t D = *cut;
-    const uint32_t mask = (1u << (32 - shift)) - 1u;
-    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
-        if (D >= kHubBins || vert[v].y < D) continue;
-        const uint32_t i = atomicAdd(count, 1u);
-        list[i] = (uint32_t)v;
-        uint32_t h = hub_home((uint32_t)v, shift);
-        for (uint32_t it = 0; it <= mask; ++it) {
-            if (atomicCAS(&map[h].x, kNoHub, (uint32_t)v) == kNoHub) {
-                map[h].y = i;
-                break;
-            }
-            h = (h + 1) & mask;
+// exclusive scan of the warps' hub counts (one block of 1,024, tile by tile);
+// total -> *count
+__global__ void __launch_bounds__(1024) k_hub_offsets(uint32_t nwarps, uint32_t *warps, uint32_t *count) {
+    __shared__ uint32_t sh[1024];
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < nwarps; base += 1024) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t x = i < nwarps ? warps[i] : 0u;
+        sh[threadIdx.x] = x;
+        __syncthreads();
+        for (uint32_t d = 1; d < 1024; d <<= 1) {   // inclusive prefix (Hillis-Steele)
+            const uint32_t y = threadIdx.x >= d ? sh[threadIdx.x - d] : 0u;
+            __syncthreads();
+            sh[threadIdx.x] += y;
+            __syncthreads();
         }
+        if (i < nwarps) warps[i] = carry + sh[threadIdx.x] - x;
+        const uint32_t total = sh[1023];
+        __syncthreads();
+        carry += total;
+    }
+    if (threadIdx.x == 0) *count = carry;
+}
+
+// rank-table prefixes and the hub list (ascending ids), warp by warp from
+// the scanned counts; list entries past `hubs` (the table's capacity) are
+// never written, as the cut keeps the hubs at or below it
+__global__ void __launch_bounds__(256) k_hub_place(uint2 *rank, uint32_t words, const uint32_t *warps,
+                                                   uint32_t *list, uint32_t hubs) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t e0 = w * kHubWarpWords;
+    if (e0 >= words) return;
+    uint32_t run = warps[w];
+    for (uint32_t e = e0; e < e0 + kHubWarpWords && e < words; ++e) {
+        const uint32_t bits = rank[e].y;
+        if (lane == 0) rank[e].x = run;
+        if (bits >> lane & 1u) {
+            const uint32_t i = run + __popc(bits & ((1u << lane) - 1u));
+            if (i < hubs) list[i] = e * 32 + lane;
+        }
+        run += __popc(bits);
     }
 }
 
-// a warp per hub i: bit i H + j for every hub j in N_(hub i)
-__global__ void k_hub_bits(const uint32_t *list, const uint32_t *count, uint32_t hubs, const uint4 *__restrict__ vert,
-                           const uint32_t *__restrict__ col, const uint2 *map, uint32_t shift, uint32_t *bits) {
-    const uint32_t lane = threadIdx.x & 31;
+// a block per hub i: bit i H + j for every hub j in N_(hub i)
+__global__ void __launch_bounds__(256) k_hub_bits(const uint32_t *list, const uint32_t *count, uint32_t hubs,
+                                                  const uint4 *__restrict__ vert, const uint32_t *__restrict__ col,
+                                                  const uint2 *rank, uint32_t *bits) {
     const uint32_t nh = *count;
-    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nh; i += (gridDim.x * blockDim.x) >> 5) {
+    for (uint32_t i = blockIdx.x; i < nh && i < hubs; i += gridDim.x) {
         const uint4 r = vert[list[i]];
-        for (uint32_t k = lane; k < r.y; k += 32) {
-            const uint32_t j = hub_lookup(map, shift, col[r.x + k]);
+        for (uint32_t k = threadIdx.x; k < r.y; k += blockDim.x) {
+            const uint32_t x = col[r.x + k];
+            const uint32_t j = hub_index(rank[x >> 5], x);
             if (j != kNoHub) {
                 const uint64_t bit = (uint64_t)i * hubs + j;
                 atomicOr(bits + (bit >> 5), 1u << (bit & 31));
@@ -1103,46 +1159,55 @@ cudaError_t launch_edge_filter(uint64_t nnz, const uint32_t *col, const uint32_t
     return cudaGetLastError();
 }
 
+static uint64_t hub_words(uint32_t n) { return ((uint64_t)n + 31) / 32; }
+static uint64_t hub_warps(uint32_t n) { return (hub_words(n) + kHubWarpWords - 1) / kHubWarpWords; }
+
 uint64_t hub_bytes(uint32_t n) {
-    const uint64_t h = hub_capacity(n), slots = 1ull << hub_map_bits((uint32_t)h);
-    return slots * 8 + h * 4 + (h * h + 31) / 32 * 4 + 256 + (uint64_t)kHubBins * 4 + 16 * 256;
+    const uint64_t h = hub_capacity(n);
+    auto up = [](uint64_t b) { return (b + 255) & ~(uint64_t)255; };
+    return up((hub_words(n) + 1) * 8) + up((h * h + 31) / 32 * 4) + up(h * 4) + up((uint64_t)kHubBins * 4) +
+           up(hub_warps(n) * 4 + 4) + up(8);
 }
 
-cudaError_t launch_hub_tables(uint32_t n, const uint4 *vert, const uint32_t *col, void *mem, uint2 **map_out,
+cudaError_t launch_hub_tables(uint32_t n, const uint4 *vert, const uint32_t *col, void *mem, uint2 **rank_out,
                               uint32_t **bits_out, uint32_t **list_out, cudaStream_t s) {
-    const uint32_t H = hub_capacity(n), mb = hub_map_bits(H), shift = 32 - mb;
-    const uint64_t slots = 1ull << mb, words = ((uint64_t)H * H + 31) / 32;
+    const uint32_t H = hub_capacity(n);
+    const uint64_t words = hub_words(n), nwarps = hub_warps(n), bwords = ((uint64_t)H * H + 31) / 32;
     uint8_t *p = static_cast<uint8_t *>(mem);
     auto take = [&](uint64_t bytes) {
         uint8_t *r = p;
         p += (bytes + 255) & ~(uint64_t)255;
         return r;
     };
-    uint2 *map = reinterpret_cast<uint2 *>(take(slots * 8));
-    uint32_t *bits = reinterpret_cast<uint32_t *>(take(words * 4));
+    uint2 *rank = reinterpret_cast<uint2 *>(take((words + 1) * 8));
+    uint32_t *bits = reinterpret_cast<uint32_t *>(take(bwords * 4));
     uint32_t *list = reinterpret_cast<uint32_t *>(take((uint64_t)H * 4));
     uint32_t *hist = reinterpret_cast<uint32_t *>(take((uint64_t)kHubBins * 4));
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(take(8));   // [0] hubs placed, [1] the degree cut
-    cudaError_t e = cudaMemsetAsync(map, 0xFF, slots * 8, s);
+    uint32_t *warps = reinterpret_cast<uint32_t *>(take(nwarps * 4 + 4));
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(take(8));   // [0] hubs, [1] the degree cut
+    cudaError_t e = cudaMemsetAsync(rank, 0, (words + 1) * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(list, 0xFF, (uint64_t)H * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(bits, 0, words * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bits, 0, bwords * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, (uint64_t)kHubBins * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 8, s);
     if (e != cudaSuccess) return e;
-    const unsigned vb = (unsigned)std::min<uint64_t>(((uint64_t)n + 255) / 256, 4096);
     if (n) {
+        const unsigned vb = (unsigned)std::min<uint64_t>(((uint64_t)n + 255) / 256, 1024);
         k_hub_hist<<<vb, 256, 0, s>>>(n, vert, hist);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    k_hub_cut<<<1, 1024, 0, s>>>(hist, H, cnt + 1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (n) {
-        k_hub_place<<<vb, 256, 0, s>>>(n, vert, cnt + 1, map, shift, list, cnt);
+        k_hub_cut<<<1, 1024, 0, s>>>(hist, H, cnt + 1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        k_hub_bits<<<(H + 7) / 8, 256, 0, s>>>(list, cnt, H, vert, col, map, shift, bits);
+        const unsigned wb = (unsigned)((nwarps + kHubBlockWarps - 1) / kHubBlockWarps);
+        k_hub_words<<<wb, 32 * kHubBlockWarps, 0, s>>>(n, vert, cnt + 1, rank, (uint32_t)words, warps);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_hub_offsets<<<1, 1024, 0, s>>>((uint32_t)nwarps, warps, cnt);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_hub_place<<<wb, 32 * kHubBlockWarps, 0, s>>>(rank, (uint32_t)words, warps, list, H);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_hub_bits<<<H, 256, 0, s>>>(list, cnt, H, vert, col, rank, bits);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    *map_out = map;
+    *rank_out = rank;
     *bits_out = bits;
     *list_out = list;
     return cudaSuccess;

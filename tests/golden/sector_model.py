@@ -17,6 +17,12 @@ list (MOSS_PROBE_SEARCH, which also reads the two vertex records) or the home
 bucket of the hashed edge set (MOSS_PROBE_HASH, 32 B buckets of four keys; the rare
 continuation into the next bucket is not counted), or the word of the edge
 filter followed by that bucket only when the filter passes (MOSS_PROBE_FILTER).
+The "_filter" figures count the method's work under that layout and are the
+ones the roofline uses; the "_filter_hubs" figures count what the library's
+samplers read behind the filter with hub-pair bits: each of the sample's
+vertices looked up in the hubs' rank table (one 8 B entry per 32 vertices),
+and a pair of two hubs answered by a word of the hubs' adjacency bits instead
+of the filter and the set.
 The draws are replayed from the oracle's words and tables, so the
 count is exact per sample; the mean over a few thousand samples is the
 per-sample figure used by the roofline ("achieved" = figure x 32 B x samples
@@ -102,7 +108,7 @@ def vertex_column(vt, n, xl, xc):
 
 
 class Replay:
-    def __init__(self, rp, col, probe="search"):
+    def __init__(self, rp, col, probe="search", hubs=False):
         self.g = oracle.OracleGraph(rp, col)
         self.rp = rp.astype(np.int64)
         self.col = col
@@ -112,6 +118,7 @@ class Replay:
         thr, alias, acc = self.g.sigma_table()
         self.thr, self.alias, self.acc = thr.astype(np.int64), alias.astype(np.int64), acc.astype(np.int64)
         self.probe_kind = probe
+        self.hubs = hubs and probe == "filter"
         buckets = 2   # the library's table: next power of two >= nnz / 2 buckets
         while buckets < (len(col) + 1) // 2:
             buckets <<= 1
@@ -127,6 +134,42 @@ class Replay:
             h = filter_hash((owner[keep] << np.uint64(32)) | c64[keep])
             self.filter = np.zeros(words, dtype=np.uint32)
             np.bitwise_or.at(self.filter, (h >> np.uint64(self.fshift)).astype(np.int64), filter_mask(h))
+            if self.hubs:
+                self.hub_tables()
+
+    def hub_tables(self):
+        """The library's hubs: every vertex of degree >= D, D the smallest
+        degree >= 1 with at most H = min(8192, max(16, n / 16)) such
+        vertices; hub i is the i-th in ascending id order."""
+        n = self.g.n
+        H = min(8192, max(16, n // 16))
+        cnt = np.bincount(self.deg, minlength=int(self.deg.max()) + 2)
+        above = np.cumsum(cnt[::-1])[::-1]          # above[d] = vertices of degree >= d
+        D = next(d for d in range(1, len(above)) if above[d] <= H) if n else 1
+        hubs = np.nonzero(self.deg >= D)[0] if D < len(above) else np.zeros(0, np.int64)
+        self.hubs_H = H
+        self.hub_index = {int(v): i for i, v in enumerate(hubs)}
+
+    def hub_of(self, x, touched):
+        """Hub index of x (or None): its rank-table entry, four 8 B entries
+        (128 vertices) per sector."""
+        touched.add(("hubrank", int(x) >> 7))
+        return self.hub_index.get(int(x))
+
+    def probe_all(self, pairs, verts, touched, hubs):
+        """The probes of one sample; with hubs (Path-5 and MOSS-4Min under
+        the filter) a pair of two hubs reads one word of the hubs' bits."""
+        if not (hubs and self.hubs):
+            for a, b in pairs:
+                self.probe(a, b, touched)
+            return
+        hi = {int(z): self.hub_of(z, touched) for z in verts}
+        for a, b in pairs:
+            i, j = hi[int(a)], hi[int(b)]
+            if i is not None and j is not None:
+                touched.add(("hubbits", (i * self.hubs_H + j) >> 8))
+            else:
+                self.probe(a, b, touched)
 
     def min_tables(self):
         if not hasattr(self, "rank"):
@@ -157,7 +200,7 @@ class Replay:
     def sample_min(self, seed, s, verts, cls):
         """Sectors of one MOSS-4Min sample (Algorithm 2)."""
         self.min_tables()
-        t = set()
+        t = self.touched = set()   # kept for breakdowns by table
         x = self.words(3, seed, s, 2)
         c = vertex_column(self.seed_m, self.g.n, x[6], x[0])
         t.add(("seedm", c))
@@ -186,8 +229,7 @@ class Replay:
             if self.probe_kind == "search":
                 t.add(("vert", w >> 1))
                 t.add(("vert", r >> 1))
-            for a, b in ((v, r), (u, w), (w, r)):
-                self.probe(a, b, t)
+            self.probe_all(((v, r), (u, w), (w, r)), (v, u, w, r), t, True)
         return len(t)
 
     def words(self, method, seed, s, blocks):
@@ -280,7 +322,7 @@ class Replay:
         return iu, lo - 1
 
     def sample(self, method, seed, s, verts, cls):
-        t = set()
+        t = self.touched = set()   # kept for breakdowns by table
         vt = self.seed[method]
         x = self.words(method, seed, s, 4)
         c = vertex_column(vt, self.g.n, x[LEVEL_WORD[method]], x[0])
@@ -312,8 +354,7 @@ class Replay:
                 if self.probe_kind == "search":
                     t.add(("vert", r >> 1))
                     t.add(("vert", tt >> 1))
-                for a, b in ((v, r), (v, tt), (u, w), (u, tt), (w, r), (r, tt)):
-                    self.probe(a, b, t)
+                self.probe_all(((v, r), (v, tt), (u, w), (u, tt), (w, r), (r, tt)), (v, u, w, r, tt), t, True)
             return len(t)
         iu = self.sigma(v, x[2], x[3], t)
         u, w, r = int(verts[1]), int(verts[2]), int(verts[3])
@@ -327,8 +368,7 @@ class Replay:
                 if self.probe_kind == "search":
                     t.add(("vert", w >> 1))
                     t.add(("vert", r >> 1))
-                for a, b in ((v, r), (u, w), (w, r)):
-                    self.probe(a, b, t)
+                self.probe_all(((v, r), (u, w), (w, r)), (v, u, w, r), t, True)
             return len(t)
         tt = int(verts[4])
         t.add(("col", (o + int(np.searchsorted(col_v, r))) >> 3))
@@ -338,8 +378,7 @@ class Replay:
             if self.probe_kind == "search":
                 for z in (w, r, tt):
                     t.add(("vert", z >> 1))
-            for a, b in ((u, w), (u, r), (w, r), (v, tt), (w, tt), (r, tt)):
-                self.probe(a, b, t)
+            self.probe_all(((u, w), (u, r), (w, r), (v, tt), (w, tt), (r, tt)), (v, u, w, r, tt), t, True)
         return len(t)
 
 
@@ -350,10 +389,11 @@ def model(workload: str, samples: int = 4000, seed: int = 42) -> dict:
                       "alias's pick and both picks' neighbour list and twin, 16 B vertex records, "
                       "4 B ids and ACC, 8 B Q, 32 B edge-hash buckets (home bucket counted), 4 B edge-filter words "
                       "(the set's bucket only when the filter passes); MOSS-4Min: 16 B "
-                      "vertex, 32 B pick (32 B slot where too wide), 8 B list records; 32 B sectors"),
+                      "vertex, 32 B pick (32 B slot where too wide), 8 B list records; _filter_hubs adds 8 B "
+                      "hub-map slots and 4 B hub-bit words; 32 B sectors"),
            "source": "written by tests/golden/sector_model.py"}
-    for probe, suffix in (("search", "_search"), ("hash", "_hash"), ("filter", "_filter")):
-        rep = Replay(rp, col, probe)
+    for probe, suffix in (("search", "_search"), ("hash", "_hash"), ("filter", "_filter"), ("hubs", "_filter_hubs")):
+        rep = Replay(rp, col, "filter" if probe == "hubs" else probe, hubs=probe == "hubs")
         for method, name in ((0, "MOSS4"), (1, "T5"), (2, "PATH5")):
             first = 1_000_000
             _, cls, verts = rep.g.run(method, seed, samples, first=first, record=True)

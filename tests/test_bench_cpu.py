@@ -40,9 +40,9 @@ def test_reference_arm_json_line():
 @pytest.mark.parametrize("k,budget,mix,filtered,two,expected", [
     # load 7 + build 8 + finalize 1; T-5: sampler + reduce; Path-5: main, two redraw stages, reduce per chunk
     (5, 100_000_000, False, False, False, 16 + 2 + 4),
-    # the edge filter and its 4 hub kernels, two-level vertex tables 3 split
+    # the edge filter and its 6 hub kernels, two-level vertex tables 3 split
     # kernels; 5e8 Path-5 ids: 8 chunks of 2^26
-    (5, 1_000_000_000, False, True, True, 16 + 5 + 3 + 2 + 4 * 8),
+    (5, 1_000_000_000, False, True, True, 16 + 7 + 3 + 2 + 4 * 8),
     (4, 100_000_000, False, False, False, 16 + 2),
     (4, 100_000_000, True, False, False, 16 + 12 + 2 + 2),    # MOSS-4 + MOSS-4Min with its 12 table kernels
     (4, 100_000_000, True, False, True, 16 + 3 + 15 + 2 + 2),
