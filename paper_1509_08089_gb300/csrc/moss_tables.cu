@@ -75,7 +75,7 @@ __global__ void k_slot_weights(uint32_t n, uint64_t nnz, const uint32_t *__restr
     uint32_t err = 0;
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t v = owner[p], x = col[p];
-        uint32_t w = 0, ox = 0;
+        uint32_t w = 0, ox = 0, dx = 0;
         if (x >= n) {
             err |= kErrRange;
         } else {
@@ -84,9 +84,12 @@ __global__ void k_slot_weights(uint32_t n, uint64_t nnz, const uint32_t *__restr
             const uint4 xr = vert[x];
             w = xr.y ? xr.y - 1 : 0;
             ox = xr.x;
+            dx = xr.y;
         }
         acc[p] = w;    // turned into the prefix by k_slots
-        slot[2 * p] = make_uint4(x, 0u, 0u, 0u);
+        // words 2 and 3 (the sigma threshold and alias, written by the table
+        // build) hold x's {off, deg} until then, for k_twin
+        slot[2 * p] = make_uint4(x, 0u, ox, dx);
         slot[2 * p + 1] = make_uint4(ox, 0u, 0u, 0u);   // nb and, for a hub, off: k_twin
     }
     if (err) atomicOr(flags, err);
@@ -272,9 +275,11 @@ __global__ void k_twin(uint32_t n, uint64_t nnz, const uint4 *__restrict__ vert,
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < nnz; p += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t v = owner[p], x = col[p];
         if (x >= n || x == v) continue;  // flagged by the slot pass
-        // {off, deg} only: k_slots may be writing S_v into the same records
+        // {off, deg} only: k_slots may be writing S_v into the same records;
+        // x's comes from words 2 and 3 of the slot record (k_slot_weights), a
+        // streamed read instead of a random one
         const uint2 vr = reinterpret_cast<const uint2 *>(vert)[2 * (uint64_t)v];
-        const uint2 xr = reinterpret_cast<const uint2 *>(vert)[2 * (uint64_t)x];
+        const uint2 xr = reinterpret_cast<const uint2 *>(slot)[4 * p + 1];
         const bool mine = vr.y > xr.y || (vr.y == xr.y && v < x);
         if (!mine) continue;
         uint32_t lo = xr.x, len = xr.y;
