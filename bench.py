@@ -82,6 +82,8 @@ def parse():
                    help="seconds of Poisson arrivals of the served term of the default line")
     p.add_argument("--rng", default="splitmix64", choices=["splitmix64", "philox4x32"],
                    help="word generator of the samples (both sides of the comparison use it)")
+    p.add_argument("--vertex-split", type=int, default=-1,
+                   help="vertex-table level split of the workload's graph (0..64; default: the library's)")
     p.add_argument("--probe", default="auto", choices=["auto", "hash", "filter", "search"],
                    help="induced-edge tests: auto (filtered set when the set exceeds 64 MiB, else the set), "
                         "hashed edge set, set behind a Bloom filter, or sorted-list search")
@@ -507,6 +509,8 @@ def run_gpu(args):
         try:
             moss.moss_set_probe(h, probe)
             moss.moss_set_rng(h, rng)
+            if args.vertex_split >= 0:
+                moss.moss_set_vertex_split(h, args.vertex_split)
             moss.moss_build_tables(h, (1 << kk) | (moss.TABLES_4MIN if mix else 0), stream)
             if world == 1 and mix:
                 K4, Km = (K for _, K in sub_budgets(kk, budget, True))
@@ -589,6 +593,8 @@ def run_gpu(args):
     try:
         moss.moss_set_probe(h, probe)
         moss.moss_set_rng(h, rng)
+        if args.vertex_split >= 0:
+            moss.moss_set_vertex_split(h, args.vertex_split)
         moss.moss_build_tables(h, kmask, stream)
         times = time_calls(moss, torch, h, k, args.budget, mix, args.seed, stream, l2_flush)
     finally:
@@ -911,7 +917,8 @@ def run_call(args):
     kmask = (1 << 4) | (1 << 5) | (moss.TABLES_4MIN if 3 in methods else 0)
     l2_flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     out = {}
-    with moss.Graph(rp, col, stream=stream, k_mask=kmask, probe=probe, rng=RNG_IDS[args.rng]) as g:
+    vsplit = args.vertex_split if args.vertex_split >= 0 else None
+    with moss.Graph(rp, col, stream=stream, k_mask=kmask, probe=probe, rng=RNG_IDS[args.rng], vsplit=vsplit) as g:
         buf = torch.zeros(22, dtype=torch.int64, device="cuda")
         for m in methods:
             for c in counts:

@@ -176,20 +176,25 @@ int moss_set_rng(moss_graph *g, int rng);
 int moss_get_rng(const moss_graph *g);
 
 /* WeightRandomVertex(V, .) (Sec. 4.1.3) draws from an alias table per
- * weight, which on graphs of 2^20 vertices or more has two levels: the heavy
+ * weight, which on graphs of 2^14 vertices or more has two levels: the heavy
  * vertices, w_v 2^split >= W (at most 2^split of them, in ascending id
  * order), and the light ones; a separate word picks the light table with
  * probability floor(W_light 2^64 / W) / 2^64 (exact up to 2^-64, as every
- * threshold).  On power-law graphs a few thousand vertices carry 97-99% of
- * the weight, so most draws read a table small enough to stay cached.  The
+ * threshold).  On power-law graphs a few hundred to a few thousand vertices
+ * carry most of the weight, so most draws read a table small enough to stay
+ * cached (in L1 on graphs whose edge set is probed without the filter).  The
  * level word is x6 for MOSS-4 and MOSS-4Min, x7 for T-5 and x14 for Path-5;
  * with one level it is not read.  moss_set_vertex_split (0..63, or
- * MOSS_VERTEX_ONE_LEVEL; the default is MOSS_VERTEX_SPLIT_DEFAULT from 2^20
- * vertices, else one level) takes effect at the next moss_build_tables
+ * MOSS_VERTEX_ONE_LEVEL, for every table; the default is
+ * MOSS_VERTEX_SPLIT_DEFAULT from 2^20 vertices, MOSS_VERTEX_SPLIT_MID from
+ * 2^14, else one level -- for the MOSS-4Min table (Gamma-check) one level
+ * below 2^20 vertices, where a heavy level measured slower) takes effect at
+ * the next moss_build_tables
  * (sampling returns MOSS_ESTATE until then); moss_vertex_levels reports, for
  * weight which (0 Gamma, 1 Gamma^(1), 2 Gamma^(2), 3 Gamma-check), the
  * heavy count (0 with one level) and the light level's bound. */
 #define MOSS_VERTEX_SPLIT_DEFAULT 20
+#define MOSS_VERTEX_SPLIT_MID 12
 #define MOSS_VERTEX_ONE_LEVEL 64
 int moss_set_vertex_split(moss_graph *g, int split);
 int moss_vertex_levels(const moss_graph *g, int which, uint32_t *nheavy, uint64_t *tlight);

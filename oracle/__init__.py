@@ -59,6 +59,7 @@ def _load():
         lib.oracle_new.restype = ctypes.c_void_p
         lib.oracle_new_split.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int]
         lib.oracle_new_split.restype = ctypes.c_void_p
+        lib.oracle_set_min_split.argtypes = [ctypes.c_void_p, ctypes.c_int]
         lib.oracle_free.argtypes = [ctypes.c_void_p]
         lib.oracle_totals.argtypes = [ctypes.c_void_p, _u64p]
         lib.oracle_vertex.argtypes = [ctypes.c_void_p, _u64p, _u64p, _u64p, _u64p]
@@ -148,29 +149,45 @@ def alias_build(weights) -> tuple[list[int], list[int]]:
 
 
 VSPLIT = 20           # heavy vertices of a two-level vertex table: w_v 2^VSPLIT >= W
+VSPLIT_MID = 12       # the same from 2^14 vertices on
 ONE_LEVEL = 64        # the split value of a single-level vertex table
 
 
 def default_split(n: int) -> int:
-    """Two levels (split 20) from 2^20 vertices on, one level below."""
+    """Two levels with split 20 from 2^20 vertices on, with split 12 from
+    2^14 on, one level below."""
+    return VSPLIT if n >= 1 << 20 else (VSPLIT_MID if n >= 1 << 14 else ONE_LEVEL)
+
+
+def default_split_min(n: int) -> int:
+    """The MOSS-4Min table: two levels with split 20 from 2^20 vertices on,
+    one level below."""
     return VSPLIT if n >= 1 << 20 else ONE_LEVEL
 
 
 class OracleGraph:
     """The oracle's view of one graph: weights, tables and the samplers.
     vsplit sets the heavy level of the vertex tables (w_v 2^vsplit >= W;
-    ONE_LEVEL: a single table; None: default_split(n))."""
+    ONE_LEVEL: a single table; None: default_split(n), and
+    default_split_min(n) for the MOSS-4Min table); vsplit_min overrides the
+    MOSS-4Min table's (default: vsplit when that is given)."""
 
-    def __init__(self, row_ptr: np.ndarray, col: np.ndarray, vsplit: int | None = None):
+    def __init__(self, row_ptr: np.ndarray, col: np.ndarray, vsplit: int | None = None,
+                 vsplit_min: int | None = None):
         self.row_ptr = np.ascontiguousarray(row_ptr, dtype=np.uint64)
         self.col = np.ascontiguousarray(col, dtype=np.uint32)
         self.n = len(self.row_ptr) - 1
         self.nnz = int(self.row_ptr[-1])
+        if vsplit_min is None:
+            vsplit_min = default_split_min(self.n) if vsplit is None else vsplit
         self.vsplit = vsplit = default_split(self.n) if vsplit is None else vsplit
+        self.vsplit_min = vsplit_min
         col_buf = self.col if self.nnz else np.zeros(1, dtype=np.uint32)
         self._ctx = _load().oracle_new_split(self.n, _p(self.row_ptr, _u64p), _p(col_buf, _u32p), vsplit)
         if not self._ctx:
             raise MemoryError("oracle_new")
+        if _load().oracle_set_min_split(self._ctx, vsplit_min):
+            raise ValueError("vsplit_min out of range")
         t = np.zeros(10, dtype=np.uint64)
         _load().oracle_totals(self._ctx, _p(t, _u64p))
         self.Gamma = [_u128(t[0:2]), _u128(t[2:4]), _u128(t[4:6])]

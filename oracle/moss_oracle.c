@@ -15,10 +15,11 @@
  *    the totals of Table 1;
  *  - WeightRandomVertex (Sec. 4.1.3) realised with alias tables built by a
  *    sequential sweep (Walker/Vose alias method, sweeping variant) in exact
- *    integer arithmetic; over V, on graphs of 2^20 vertices or more, in two
- *    levels: the heavy vertices (w_v 2^t >= W, t = 20 unless chosen) and the
- *    light ones each get an alias table, and a separate word picks the level
- *    with probability floor(W_light 2^64 / W) / 2^64 for the light one;
+ *    integer arithmetic; over V, on graphs of 2^14 vertices or more, in two
+ *    levels: the heavy vertices (w_v 2^t >= W, t = 12, from 2^20 vertices
+ *    20, unless chosen) and the light ones each get an alias table, and a
+ *    separate word picks the level with probability floor(W_light 2^64 / W)
+ *    / 2^64 for the light one;
  *  - RandomVertex(N_v - X) (Sec. 4.1.3): a uniform index over the d_v - |X|
  *    admissible positions, skipping the excluded positions in list order;
  *  - MOSS-4 (Algorithm 1), T-5 (Algorithm 3), Path-5 (Algorithm 4);
@@ -122,6 +123,7 @@ typedef struct {
     u128 lam3, lam4;
     /* two-level vertex tables over V, one per weight */
     int vsplit;         /* heavy vertices: w_v 2^vsplit >= W */
+    int vsplit_min;     /* the same for the MOSS-4Min table (Gamma-check) */
     vtab vt[3];
     /* sigma alias tables over each N_v (weights d_x - 1), local positions */
     uint64_t *gthr;
@@ -301,6 +303,7 @@ ctx *oracle_new_split(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, 
     if (!c) return NULL;
     c->n = n;
     c->vsplit = vsplit;
+    c->vsplit_min = vsplit;
     c->nnz = row_ptr[n];
     uint64_t nnz1 = c->nnz ? c->nnz : 1;
     c->off = (uint64_t *)malloc(sizeof(uint64_t) * (n + 1));
@@ -363,9 +366,20 @@ ctx *oracle_new_split(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, 
     return c;
 }
 
-/* the default split: two levels (split 20) from 2^20 vertices, else one */
+/* the default splits: two levels with split 20 from 2^20 vertices, with
+ * split 12 from 2^14, else one level; the MOSS-4Min table two levels with
+ * split 20 from 2^20 vertices, else one */
 ctx *oracle_new(uint32_t n, const uint64_t *row_ptr, const uint32_t *col) {
-    return oracle_new_split(n, row_ptr, col, n >= (1u << 20) ? 20 : 64);
+    ctx *c = oracle_new_split(n, row_ptr, col, n >= (1u << 20) ? 20 : (n >= (1u << 14) ? 12 : 64));
+    if (c) c->vsplit_min = n >= (1u << 20) ? 20 : 64;
+    return c;
+}
+
+/* the split of the MOSS-4Min vertex table, before oracle_build_min (0..64) */
+int oracle_set_min_split(ctx *c, int vsplit) {
+    if (vsplit < 0 || vsplit > 64) return -1;
+    c->vsplit_min = vsplit;
+    return 0;
 }
 
 /* --------------------------------------------------------- accessors ---- */
@@ -730,7 +744,7 @@ int oracle_build_min(ctx *c) {
         if (alias_sweep(d, w, t, c->calias + o)) { free(keys); free(w); free(t); return -1; }
         for (uint64_t i = 0; i < d; i++) c->cthr[o + i] = (uint64_t)t[i];
     }
-    if (vtab_build(&c->mvt, c->n, c->gmin, c->tmin, c->vsplit)) { free(keys); free(w); free(t); return -1; }
+    if (vtab_build(&c->mvt, c->n, c->gmin, c->tmin, c->vsplit_min)) { free(keys); free(w); free(t); return -1; }
     free(keys);
     free(w);
     free(t);

@@ -27,7 +27,7 @@ MOSS_EBUSY = -7
 MOSS4, T5, PATH5, MOSS4MIN = 0, 1, 2, 3
 PROBE_SEARCH, PROBE_HASH, PROBE_FILTER, PROBE_AUTO = 0, 1, 2, 3
 RNG_SPLITMIX64, RNG_PHILOX4X32 = 0, 1
-VERTEX_SPLIT_DEFAULT, VERTEX_ONE_LEVEL = 20, 64
+VERTEX_SPLIT_DEFAULT, VERTEX_SPLIT_MID, VERTEX_ONE_LEVEL = 20, 12, 64
 NSLOTS = 22
 TABLES_4MIN = 1 << 6
 TABLE_VERT, TABLE_SLOT, TABLE_ACC, TABLE_SEED0, TABLE_GAMMA0 = 0, 1, 2, 3, 6

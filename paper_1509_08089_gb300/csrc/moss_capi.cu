@@ -219,6 +219,7 @@ struct moss_graph {
     int probe = MOSS_PROBE_AUTO; // membership tests (MOSS_PROBE_*), as requested
     int rng = MOSS_RNG_SPLITMIX64;   // word generator of the samples (MOSS_RNG_*)
     int vsplit = MOSS_VERTEX_ONE_LEVEL;   // heavy level of the vertex tables: w_v 2^vsplit >= W (set at load)
+    int vsplit_min = MOSS_VERTEX_ONE_LEVEL;   // the same for the MOSS-4Min table
     unsigned long long *hash = nullptr;  // kBucketKeys keys per bucket
     uint64_t hash_buckets = 0;
     uint32_t *filter = nullptr;  // Bloom filter in front of the hash
@@ -424,7 +425,9 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
     if (!g) return fail(MOSS_ENOMEM, "host allocation");
     g->device = device;
     g->n = n;
-    g->vsplit = n >= (1u << 20) ? MOSS_VERTEX_SPLIT_DEFAULT : MOSS_VERTEX_ONE_LEVEL;
+    g->vsplit = n >= (1u << 20) ? MOSS_VERTEX_SPLIT_DEFAULT
+                                : (n >= (1u << 14) ? MOSS_VERTEX_SPLIT_MID : MOSS_VERTEX_ONE_LEVEL);
+    g->vsplit_min = n >= (1u << 20) ? MOSS_VERTEX_SPLIT_DEFAULT : MOSS_VERTEX_ONE_LEVEL;
     g->nnz = nnz;
     void *rp_dev = nullptr;
     const size_t rp_bytes = (size_t)(n + 1ULL) * (row_ptr_is_64 ? 8 : 4);
@@ -525,7 +528,7 @@ static int build_min_tables(moss_graph *g, cudaStream_t s, const AuxStreams *aux
     if ((e = pool_alloc(g->device, &scratch, min_scratch_bytes(g->n, g->nnz), s)) != cudaSuccess)
         return cuda_fail(e, "allocating scratch");
     e = launch_min_tables(g->n, g->nnz, g->vert, g->col, g->owner, g->slot, g->mvert, g->mslot, g->mpick, g->rlist,
-                          g->gam[3], g->seed[3], g->tot, scratch, g->flags, g->vsplit, s, aux);
+                          g->gam[3], g->seed[3], g->tot, scratch, g->flags, g->vsplit_min, s, aux);
     cudaFreeAsync(scratch, s);
     if (e != cudaSuccess) return cuda_fail(e, "MOSS-4Min table kernels");
     return MOSS_OK;
@@ -678,8 +681,9 @@ int moss_set_vertex_split(moss_graph *g, int split) {
     if (!g) return fail(MOSS_EINVAL, "graph is NULL");
     if (split < 0 || split > MOSS_VERTEX_ONE_LEVEL)
         return fail(MOSS_EINVAL, "vertex split %d outside 0..%d", split, MOSS_VERTEX_ONE_LEVEL);
-    if (split != g->vsplit) g->built &= ~0xFu & ~(1u << 5);   // vertex tables follow at the next build
+    if (split != g->vsplit || split != g->vsplit_min) g->built &= ~0xFu & ~(1u << 5);   // rebuilt at the next build
     g->vsplit = split;
+    g->vsplit_min = split;
     return MOSS_OK;
 }
 

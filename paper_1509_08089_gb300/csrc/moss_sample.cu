@@ -56,6 +56,31 @@ __device__ __forceinline__ uint4 ld4(const uint4 *p) { return __ldg(p); }
 __device__ __forceinline__ uint2 ld2(const uint2 *p) { return __ldg(p); }
 __device__ __forceinline__ uint32_t ld1(const uint32_t *p) { return __ldg(p); }
 
+// Probe modes of the sampler instances: kPmPlain (list search, or the hashed
+// edge set with one-level vertex tables), kPmFilter (the edge filter in front
+// of the set: L2 hints and hub-pair bits) and kPmStream (the set with
+// two-level vertex tables, which fit the L1: the scattered loads of lists,
+// slot records and buckets skip L1 allocation, so the heavy level's records,
+// read evict-last, stay there and those draws cost no L2 request).
+constexpr int kPmPlain = 0, kPmFilter = 1, kPmStream = 2;
+constexpr uint32_t kStreamHeavy = 4096;   // heavy columns (32 B each) that kPmStream keeps in L1
+
+// a vertex record without L1 allocation
+__device__ __forceinline__ uint4 ld4_na(const uint4 *p) {
+    uint4 r;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
+}
+
+// a list entry (neighbour id) in mode PM
+template <int PM>
+__device__ __forceinline__ uint32_t ldc(const uint32_t *p) {
+    if (PM != kPmStream) return __ldg(p);
+    uint32_t r;
+    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(r) : "l"(p));
+    return r;
+}
+
 struct Pick {
     uint32_t pos;   // position in N_v
     uint32_t id;    // the vertex
@@ -77,6 +102,26 @@ __device__ __forceinline__ Sector ld8(const uint4 *p) {
     return r;
 }
 
+// The same load without L1 allocation (scattered records in kPmStream)
+__device__ __forceinline__ Sector ld8_na(const uint4 *p) {
+    Sector r;
+    asm("ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r.lo.x), "=r"(r.lo.y), "=r"(r.lo.z), "=r"(r.lo.w), "=r"(r.hi.x), "=r"(r.hi.y), "=r"(r.hi.z),
+          "=r"(r.hi.w)
+        : "l"(p));
+    return r;
+}
+
+// ... and kept in L1 as long as possible (heavy-level vertex records in kPmStream)
+__device__ __forceinline__ Sector ld8_keep(const uint4 *p) {
+    Sector r;
+    asm("ld.global.nc.L1::evict_last.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r.lo.x), "=r"(r.lo.y), "=r"(r.lo.z), "=r"(r.lo.w), "=r"(r.hi.x), "=r"(r.hi.y), "=r"(r.hi.z),
+          "=r"(r.hi.w)
+        : "l"(p));
+    return r;
+}
+
 // The same load marked evict-first in L2, for the per-slot records (sigma
 // slot records, MOSS-4Min pick records): they are the largest and least
 // densely used tables of a sampler, so with the working set at the size of
@@ -92,6 +137,27 @@ __device__ __forceinline__ Sector ld8_first(const uint4 *p) {
         : "l"(p), "l"(pol));
     return r;
 }
+__device__ __forceinline__ Sector ld8_first_na(const uint4 *p) {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    Sector r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+        : "=r"(r.lo.x), "=r"(r.lo.y), "=r"(r.lo.z), "=r"(r.lo.w), "=r"(r.hi.x), "=r"(r.hi.y), "=r"(r.hi.z),
+          "=r"(r.hi.w)
+        : "l"(p), "l"(pol));
+    return r;
+}
+
+// a scattered 32-byte record (bucket, MOSS-4Min slot record) in mode PM
+template <int PM>
+__device__ __forceinline__ Sector ld8s(const uint4 *p) {
+    return PM == kPmFilter ? ld8_first(p) : (PM == kPmStream ? ld8_na(p) : ld8(p));
+}
+// a per-slot record (sigma slot, MOSS-4Min pick) in mode PM: evict-first in L2
+template <int PM>
+__device__ __forceinline__ Sector ld8p(const uint4 *p) {
+    return PM == kPmStream ? ld8_first_na(p) : ld8_first(p);
+}
 
 struct VertexPick {
     uint32_t v;
@@ -103,13 +169,13 @@ struct VertexPick {
 // record only when the column keeps the draw.  The table has two levels: the
 // level word picks the light one (columns nh..n-1) when it is below the
 // level's bound, else the heavy one (columns 0..nh-1: the few vertices that
-// carry almost all the weight, a table small enough to stay cached).  HINT
-// (graphs behind the edge filter): a light record is read evict-first, since
-// that table is as large as the L2 and drawn uniformly, so a line is rarely
-// read twice.
+// carry almost all the weight, a table small enough to stay cached).  Behind
+// the edge filter a light record is read evict-first, since that table is as
+// large as the L2 and drawn uniformly, so a line is rarely read twice; in
+// kPmStream a heavy record is kept in L1.
 // The level word (word lw of the sample) is generated only for a table with
 // a heavy level (uniform across the launch).
-template <bool HINT, int RNG>
+template <int PM, int RNG>
 __device__ __forceinline__ VertexPick draw_vertex(const DevGraph &g, int l, const uint4 *vrec, uint64_t seed,
                                                   uint64_t s, uint32_t lw, uint64_t xc, uint64_t xt) {
     const uint32_t nh = g.nheavy[l];
@@ -117,9 +183,11 @@ __device__ __forceinline__ VertexPick draw_vertex(const DevGraph &g, int l, cons
     if (nh != 0) light = sample_word<RNG>(seed, (uint32_t)l, s, lw) < g.tlight[l];
     const uint32_t c = (light ? nh : 0u) + (uint32_t)word_index(xc, light ? g.n - nh : nh);
     const uint4 *rec = g.seed[l] + 2 * (uint64_t)c;
-    const Sector r = HINT && light ? ld8_first(rec) : ld8(rec);   // {T lo, T hi, alias, self} {alias's record}
+    const Sector r = PM == kPmFilter ? (light ? ld8_first(rec) : ld8(rec))
+                                     : (PM == kPmStream ? (light ? ld8_na(rec) : ld8_keep(rec)) : ld8(rec));
+    // {T lo, T hi, alias, self} {alias's record}
     const uint64_t T = ((uint64_t)r.lo.y << 32) | r.lo.x;
-    if (xt < T) return VertexPick{r.lo.w, ld4(vrec + r.lo.w)};
+    if (xt < T) return VertexPick{r.lo.w, PM == kPmStream && light ? ld4_na(vrec + r.lo.w) : ld4(vrec + r.lo.w)};
     return VertexPick{r.lo.z, r.hi};
 }
 
@@ -134,10 +202,11 @@ __device__ __forceinline__ Pick unpack_pick(const uint4 *vert, uint32_t pos, uin
 // WeightRandomVertex(N_v, sigma^(v)) through the list's alias table: one
 // 32-byte slot record holds the column's pick and its alias's, each with the
 // picked neighbour's list and twin
+template <int PM>
 __device__ __forceinline__ Pick draw_sigma(const uint4 *slot, const uint4 *vert, uint32_t ov, uint32_t dv, uint32_t Sv,
                                            uint64_t xc, uint64_t xt) {
     const uint32_t j = (uint32_t)word_index(xc, dv);
-    const Sector rec = ld8_first(slot + 2 * (uint64_t)(ov + j));   // {col, nb, thr, alias} {off, alias col, nb, off}
+    const Sector rec = ld8p<PM>(slot + 2 * (uint64_t)(ov + j));   // {col, nb, thr, alias} {off, alias col, nb, off}
     const bool keep = word_index(xt, Sv) < rec.lo.z;
     return unpack_pick(vert, keep ? j : rec.lo.w, keep ? rec.lo.x : rec.hi.y, keep ? rec.lo.y : rec.hi.z,
                        keep ? rec.hi.x : rec.hi.w);
@@ -198,20 +267,20 @@ __device__ __forceinline__ uint32_t probe_pairs(const uint32_t *col, const uint4
 }
 
 // Membership tests through the hashed edge set: one 32-byte bucket load per
-// pair in the common case, all P loads issued together.  HINT (behind the
-// filter): the filter rules out most pairs; the set is far larger than the
+// pair in the common case, all P loads issued together.  kPmFilter (behind
+// the filter): the filter rules out most pairs; the set is far larger than the
 // L2 and a bucket is rarely read twice, so buckets are read evict-first,
 // which keeps the filter, lists and hub slot records resident.  With HUB,
 // the ends' rank-table entries come first (one 8-byte load per vertex, all
 // together), and a pair of two hubs is answered by one bit of the hubs'
 // adjacency bitmap, loaded beside the other pairs' filter words.
-template <int P, bool HINT, bool HUB>
+template <int P, int PM, bool HUB>
 __device__ __forceinline__ uint32_t probe_hash(const DevGraph &g, const uint32_t (&a)[P], const uint32_t (&b)[P]) {
     uint32_t bk[P];
     uint32_t found = 0, pending = (1u << P) - 1u;
     if (g.filter) {   // warp-uniform: only pairs the filter cannot rule out go to the set
         uint32_t hubpair = 0, bit[P];
-        if (HINT && HUB && g.hub_rank) {   // warp-uniform
+        if (PM == kPmFilter && HUB && g.hub_rank) {   // warp-uniform
             uint2 ea[P], eb[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) {
@@ -247,7 +316,7 @@ __device__ __forceinline__ uint32_t probe_hash(const DevGraph &g, const uint32_t
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             if (pending >> p & 1u) {
-                const Sector e = HINT ? ld8_first(g.hash + 2 * (uint64_t)bk[p]) : ld8(g.hash + 2 * (uint64_t)bk[p]);
+                const Sector e = ld8s<PM>(g.hash + 2 * (uint64_t)bk[p]);
                 const uint64_t key = edge_key(a[p], b[p]);
                 const uint32_t lo = (uint32_t)key, hi = (uint32_t)(key >> 32);
                 const bool hit = (e.lo.x == lo && e.lo.y == hi) || (e.lo.z == lo && e.lo.w == hi) ||
@@ -271,20 +340,20 @@ struct Sample {
     int cls;
 };
 
-template <int RNG, bool HASH, bool HINT = false>
+template <int RNG, bool HASH, int PM = kPmPlain>
 __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
     const Words2 x01 = sample_words2<RNG>(seed, 0, s, 0);
-    const VertexPick pv = draw_vertex<HINT, RNG>(g, 0, g.vert, seed, s, 6, x01.x[0], x01.x[1]);   // x6: level
+    const VertexPick pv = draw_vertex<PM, RNG>(g, 0, g.vert, seed, s, 6, x01.x[0], x01.x[1]);   // x6: level
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
     const Words2 x23 = sample_words2<RNG>(seed, 0, s, 1);
-    const Pick pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, x23.x[0], x23.x[1]);
+    const Pick pu = draw_sigma<PM>(g.slot, g.vert, vr.x, vr.y, vr.z, x23.x[0], x23.x[1]);
     const Words2 x45 = sample_words2<RNG>(seed, 0, s, 2);
     const uint32_t jw = skip1((uint32_t)word_index(x45.x[0], vr.y - 1), pu.pos);
-    const uint32_t w = ld1(g.col + vr.x + jw);
+    const uint32_t w = ldc<PM>(g.col + vr.x + jw);
     const uint32_t jr = skip1((uint32_t)word_index(x45.x[1], pu.deg - 1), pu.twin);
-    const uint32_t r = ld1(g.col + pu.off + jr);
+    const uint32_t r = ldc<PM>(g.col + pu.off + jr);
     out.v[0] = v; out.v[1] = pu.id; out.v[2] = w; out.v[3] = r; out.v[4] = 0;
     if (r == pu.id || r == w) {
         out.cls = 0;
@@ -294,7 +363,7 @@ __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t 
     const uint32_t A[3] = {v, pu.id, w}, B[3] = {r, w, r};
     uint32_t f;
     if (HASH) {
-        f = probe_hash<3, HINT, kHubProbes[0]>(g, A, B);
+        f = probe_hash<3, PM, kHubProbes[0]>(g, A, B);
     } else {
         const uint4 ur = make_uint4(pu.off, pu.deg, 0u, 0u), wr = ld4(g.vert + w), rr = ld4(g.vert + r);
         const uint4 ra[3] = {vr, ur, wr}, rb[3] = {rr, wr, rr};
@@ -306,22 +375,22 @@ __device__ __forceinline__ Sample sample_moss4(const DevGraph &g, const uint8_t 
     return out;
 }
 
-template <int RNG, bool HASH, bool HINT = false>
+template <int RNG, bool HASH, int PM = kPmPlain>
 __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
     const Words2 x01 = sample_words2<RNG>(seed, 1, s, 0);
-    const VertexPick pv = draw_vertex<HINT, RNG>(g, 1, g.vert, seed, s, 7, x01.x[0], x01.x[1]);   // x7: level
+    const VertexPick pv = draw_vertex<PM, RNG>(g, 1, g.vert, seed, s, 7, x01.x[0], x01.x[1]);   // x7: level
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
     const Words2 x23 = sample_words2<RNG>(seed, 1, s, 1);
-    const Pick pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, x23.x[0], x23.x[1]);
+    const Pick pu = draw_sigma<PM>(g.slot, g.vert, vr.x, vr.y, vr.z, x23.x[0], x23.x[1]);
     const Words2 x45 = sample_words2<RNG>(seed, 1, s, 2);
     const uint32_t jw = skip1((uint32_t)word_index(x45.x[0], vr.y - 1), pu.pos);
     const uint32_t jr = skip2((uint32_t)word_index(x45.x[1], vr.y - 2), pu.pos, jw);
-    const uint32_t w = ld1(g.col + vr.x + jw);
-    const uint32_t r = ld1(g.col + vr.x + jr);
+    const uint32_t w = ldc<PM>(g.col + vr.x + jw);
+    const uint32_t r = ldc<PM>(g.col + vr.x + jr);
     const uint32_t jt = skip1((uint32_t)word_index(sample_word<RNG>(seed, 1, s, 6), pu.deg - 1), pu.twin);
-    const uint32_t t = ld1(g.col + pu.off + jt);
+    const uint32_t t = ldc<PM>(g.col + pu.off + jt);
     out.v[0] = v; out.v[1] = pu.id; out.v[2] = w; out.v[3] = r; out.v[4] = t;
     if (t == w || t == r) {
         out.cls = 0;
@@ -331,7 +400,7 @@ __device__ __forceinline__ Sample sample_t5(const DevGraph &g, const uint8_t *lu
     const uint32_t A[6] = {pu.id, pu.id, w, v, w, r}, B[6] = {w, r, r, t, t, t};
     uint32_t f;
     if (HASH) {
-        f = probe_hash<6, HINT, kHubProbes[1]>(g, A, B);
+        f = probe_hash<6, PM, kHubProbes[1]>(g, A, B);
     } else {
         const uint4 ur = make_uint4(pu.off, pu.deg, 0u, 0u);
         const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r), tr = ld4(g.vert + t);
@@ -370,12 +439,12 @@ __device__ __forceinline__ int min_slot(int cls, uint32_t c) {
     return kSlots;
 }
 
-template <int RNG, bool HASH, bool HINT = false>
+template <int RNG, bool HASH, int PM = kPmPlain>
 __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *lut, const uint8_t *lutc, uint64_t seed,
                                              uint64_t s) {
     Sample out;
     const Words2 x01 = sample_words2<RNG>(seed, 3, s, 0);
-    const VertexPick pv = draw_vertex<HINT, RNG>(g, 3, g.mvert, seed, s, 6, x01.x[0], x01.x[1]);   // x6: level
+    const VertexPick pv = draw_vertex<PM, RNG>(g, 3, g.mvert, seed, s, 6, x01.x[0], x01.x[1]);   // x6: level
     const uint32_t v = pv.v;
     const uint4 mv = pv.rec;                           // {off, d_v, Gamma-check_v}
     const uint64_t Gv = ((uint64_t)mv.w << 32) | mv.z;
@@ -390,7 +459,7 @@ __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *l
     uint32_t u;
     Sector pk;
     pk.hi.w = kSlotHub;
-    if (mv.w == 0) pk = ld8_first(g.mpick + 2 * (uint64_t)(mv.x + j));
+    if (mv.w == 0) pk = ld8p<PM>(g.mpick + 2 * (uint64_t)(mv.x + j));
     if (pk.hi.w != kSlotHub) {
         const bool keep = y < pk.lo.x;
         const uint32_t dd = keep ? pk.lo.w : pk.hi.z;
@@ -398,8 +467,9 @@ __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *l
         sb = make_uint4(keep ? pk.lo.z : pk.hi.y, keep ? (pk.hi.w & 0xffffu) : (pk.hi.w >> 16), dd & 0xffffu,
                         dd >> 16);
     } else {
-        Sector ms = ld8(g.mslot + 2 * (uint64_t)(mv.x + j));
-        if (!(y < (((uint64_t)ms.lo.y << 32) | ms.lo.x))) ms = ld8(g.mslot + 2 * (uint64_t)(mv.x + ms.lo.z));
+        Sector ms = ld8s<PM == kPmFilter ? kPmPlain : PM>(g.mslot + 2 * (uint64_t)(mv.x + j));
+        if (!(y < (((uint64_t)ms.lo.y << 32) | ms.lo.x)))
+            ms = ld8s<PM == kPmFilter ? kPmPlain : PM>(g.mslot + 2 * (uint64_t)(mv.x + ms.lo.z));
         sb = ms.hi;
         u = ms.lo.w;
     }
@@ -416,7 +486,7 @@ __device__ __forceinline__ Sample sample_min(const DevGraph &g, const uint8_t *l
     const uint32_t A[3] = {v, u, w}, B[3] = {r, w, r};
     uint32_t f;
     if (HASH) {
-        f = probe_hash<3, HINT, kHubProbes[3]>(g, A, B);
+        f = probe_hash<3, PM, kHubProbes[3]>(g, A, B);
     } else {
         const uint4 vr = make_uint4(mv.x, mv.y, 0u, 0u), ur = make_uint4(sb.x, sb.y, 0u, 0u);
         const uint4 wr = ld4(g.vert + w), rr = ld4(g.vert + r);
@@ -481,11 +551,11 @@ __device__ __noinline__ void path5_fallback(const uint32_t *acc, const uint64_t 
 // STAGE 3.
 constexpr int kDeferred = 254;
 
-template <int RNG, bool HASH, int STAGE, bool HINT = false>
+template <int RNG, bool HASH, int STAGE, int PM = kPmPlain>
 __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t *lut, uint64_t seed, uint64_t s) {
     Sample out;
     const Words2 x01 = sample_words2<RNG>(seed, 2, s, 0);
-    const VertexPick pv = draw_vertex<HINT, RNG>(g, 2, g.vert, seed, s, 14, x01.x[0], x01.x[1]);   // x14: level
+    const VertexPick pv = draw_vertex<PM, RNG>(g, 2, g.vert, seed, s, 14, x01.x[0], x01.x[1]);   // x14: level
     const uint32_t v = pv.v;
     const uint4 vr = pv.rec;
     Pick pu, pw;
@@ -493,8 +563,8 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
     if (STAGE == 0 || STAGE == 3) {
         const Words2 x45 = sample_words2<RNG>(seed, 2, s, 2);
         const Words2 x67 = sample_words2<RNG>(seed, 2, s, 3);
-        pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, x45.x[0], x45.x[1]);
-        pw = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, x67.x[0], x67.x[1]);
+        pu = draw_sigma<PM>(g.slot, g.vert, vr.x, vr.y, vr.z, x45.x[0], x45.x[1]);
+        pw = draw_sigma<PM>(g.slot, g.vert, vr.x, vr.y, vr.z, x67.x[0], x67.x[1]);
         collide = pu.pos == pw.pos;
         if (STAGE == 0 && collide) {
             out.cls = kDeferred;
@@ -504,8 +574,8 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
     if (STAGE == 1 || (STAGE == 3 && collide)) {
         const Words2 x89 = sample_words2<RNG>(seed, 2, s, 4);
         const Words2 x1011 = sample_words2<RNG>(seed, 2, s, 5);
-        pu = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, x89.x[0], x89.x[1]);
-        pw = draw_sigma(g.slot, g.vert, vr.x, vr.y, vr.z, x1011.x[0], x1011.x[1]);
+        pu = draw_sigma<PM>(g.slot, g.vert, vr.x, vr.y, vr.z, x89.x[0], x89.x[1]);
+        pw = draw_sigma<PM>(g.slot, g.vert, vr.x, vr.y, vr.z, x1011.x[0], x1011.x[1]);
         collide = pu.pos == pw.pos;
         if (STAGE == 1 && collide) {
             out.cls = kDeferred;
@@ -521,8 +591,8 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
     }
     const uint32_t u = pu.id, w = pw.id;
     const Words2 x23 = sample_words2<RNG>(seed, 2, s, 1);
-    const uint32_t r = ld1(g.col + pu.off + skip1((uint32_t)word_index(x23.x[0], pu.deg - 1), pu.twin));
-    const uint32_t t = ld1(g.col + pw.off + skip1((uint32_t)word_index(x23.x[1], pw.deg - 1), pw.twin));
+    const uint32_t r = ldc<PM>(g.col + pu.off + skip1((uint32_t)word_index(x23.x[0], pu.deg - 1), pu.twin));
+    const uint32_t t = ldc<PM>(g.col + pw.off + skip1((uint32_t)word_index(x23.x[1], pw.deg - 1), pw.twin));
     out.v[0] = v; out.v[1] = u; out.v[2] = w; out.v[3] = r; out.v[4] = t;
     if (t == u || r == w || t == r) {
         out.cls = 0;
@@ -532,7 +602,7 @@ __device__ __forceinline__ Sample sample_path5(const DevGraph &g, const uint8_t 
     const uint32_t A[6] = {v, v, u, u, w, r}, B[6] = {r, t, w, t, r, t};
     uint32_t f;
     if (HASH) {
-        f = probe_hash<6, HINT, kHubProbes[2]>(g, A, B);
+        f = probe_hash<6, PM, kHubProbes[2]>(g, A, B);
     } else {
         const uint4 ur = make_uint4(pu.off, pu.deg, 0u, 0u), wr = make_uint4(pw.off, pw.deg, 0u, 0u);
         const uint4 rr = ld4(g.vert + r), tr = ld4(g.vert + t);
@@ -567,7 +637,7 @@ constexpr int defer_min_blocks() { return STAGE == 1 ? 5 : 4; }
 template <int STAGE, int RNG>
 constexpr int defer_bound_blocks() { return RNG == kRngPhilox ? 4 : defer_min_blocks<STAGE>(); }
 
-template <int METHOD, bool RECORD, bool HASH, bool HINT, int RNG>
+template <int METHOD, bool RECORD, bool HASH, int PM, int RNG>
 __global__ void __launch_bounds__(kThreads, min_blocks<METHOD, RNG>()) k_sample(DevGraph g, uint64_t first, uint64_t count, uint64_t seed,
                                                      uint64_t *partials, uint8_t *classes, uint32_t *verts) {
     __shared__ uint8_t lut[kLut];
@@ -591,10 +661,10 @@ __global__ void __launch_bounds__(kThreads, min_blocks<METHOD, RNG>()) k_sample(
         if (i < count) {
             const uint64_t s = first + i;
             Sample sm;
-            if (METHOD == 0) sm = sample_moss4<RNG, HASH, HINT>(g, lut, seed, s);
-            else if (METHOD == 1) sm = sample_t5<RNG, HASH, HINT>(g, lut, seed, s);
-            else if (METHOD == 2) sm = sample_path5<RNG, HASH, 0, HINT>(g, lut, seed, s);
-            else sm = sample_min<RNG, HASH, HINT>(g, lut, lutc, seed, s);
+            if (METHOD == 0) sm = sample_moss4<RNG, HASH, PM>(g, lut, seed, s);
+            else if (METHOD == 1) sm = sample_t5<RNG, HASH, PM>(g, lut, seed, s);
+            else if (METHOD == 2) sm = sample_path5<RNG, HASH, 0, PM>(g, lut, seed, s);
+            else sm = sample_min<RNG, HASH, PM>(g, lut, lutc, seed, s);
             deferred = METHOD == 2 && sm.cls == kDeferred;
             if (!deferred) {
                 cls = METHOD == 3 ? min_slot(sm.cls, sm.v[4]) : sm.cls;
@@ -637,7 +707,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<METHOD, RNG>()) k_sample(
 // launched with no more blocks than STAGE 1, adds into STAGE 1's rows.
 constexpr uint32_t kDeferList = 1024 + 32;   // a window's ids plus the carry-over
 
-template <bool RECORD, bool HASH, int STAGE, bool HINT, int RNG>
+template <bool RECORD, bool HASH, int STAGE, int PM, int RNG>
 __global__ void __launch_bounds__(kThreads, defer_bound_blocks<STAGE, RNG>())
     k_sample_deferred(DevGraph g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
                       uint8_t *classes, uint32_t *verts) {
@@ -659,7 +729,7 @@ __global__ void __launch_bounds__(kThreads, defer_bound_blocks<STAGE, RNG>())
         uint64_t i = 0;
         if ((uint32_t)lane < cnt) {
             i = lst[k0 + lane];   // < count: only drawn ids are flagged
-            const Sample sm = sample_path5<RNG, HASH, STAGE, HINT>(g, lut, seed, first + i);
+            const Sample sm = sample_path5<RNG, HASH, STAGE, PM>(g, lut, seed, first + i);
             again = STAGE == 1 && sm.cls == kDeferred;
             if (!again) {
                 cls = sm.cls;
@@ -743,6 +813,8 @@ constexpr int kBatchBlocks = 4;   // resident blocks per SM (Path-5 bound)
 
 // the count slot of sample s of a method: its class, or for MOSS-4Min its
 // (class, c) slot
+// (plain loads for every graph: a second, streaming body per method in the
+// persistent batch kernel cost 12% on the 512-graph batch)
 template <bool HASH, int RNG>
 __device__ __forceinline__ int sample_any(const DevGraph &g, const uint8_t *lut4, const uint8_t *lut5,
                                           const uint8_t *lutc, uint32_t method, uint64_t seed, uint64_t s) {
@@ -855,15 +927,30 @@ __global__ void k_reduce(const uint64_t *partials, int blocks, uint64_t *out, in
     }
 }
 
+// the probe variant of a launch: 0 list search, 1 hashed set, 2 filter in
+// front of it, 3 hashed set with two-level vertex tables (kPmStream)
+int probe_variant(int method, const DevGraph &g) {
+    if (!g.hash) return 0;
+    if (g.filter) return 2;
+    return g.nheavy[method] != 0 && g.nheavy[method] <= kStreamHeavy ? 3 : 1;
+}
+
 template <int M, bool R, int RNG>
 cudaError_t launch_one_rng(const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
                            int blocks, uint8_t *classes, uint32_t *verts, cudaStream_t s) {
-    if (g.hash && g.filter)
-        k_sample<M, R, true, true, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-    else if (g.hash)
-        k_sample<M, R, true, false, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-    else
-        k_sample<M, R, false, false, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    switch (probe_variant(M, g)) {
+        case 2:
+            k_sample<M, R, true, kPmFilter, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+            break;
+        case 3:
+            k_sample<M, R, true, kPmStream, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+            break;
+        case 1:
+            k_sample<M, R, true, kPmPlain, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+            break;
+        default:
+            k_sample<M, R, false, kPmPlain, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    }
     return cudaGetLastError();
 }
 
@@ -884,25 +971,29 @@ void upload_luts(const uint8_t *lut4, const uint8_t *lut5, const uint8_t *lutc) 
 }
 
 // resident blocks per SM of each sampler variant (probe 0 search, 1 hash, 2
-// filter; + 3 under Philox words) on each device, 0 until queried
-constexpr int kVariants = 6;
+// filter, 3 hash with two-level tables; + 4 under Philox words) on each
+// device, 0 until queried
+constexpr int kProbeVariants = 4;
+constexpr int kVariants = 2 * kProbeVariants;
 std::atomic<int> g_sample_per_sm[64][kMethods][kVariants];
 
 template <int M, int RNG>
-cudaError_t occupancy3(int *per) {
+cudaError_t occupancy_probe(int *per) {
     cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], k_sample<M, false, false, false, RNG>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], k_sample<M, false, false, kPmPlain, RNG>, kThreads, 0);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], k_sample<M, false, true, false, RNG>, kThreads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], k_sample<M, false, true, kPmPlain, RNG>, kThreads, 0);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[2], k_sample<M, false, true, true, RNG>, kThreads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[2], k_sample<M, false, true, kPmFilter, RNG>, kThreads, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[3], k_sample<M, false, true, kPmStream, RNG>, kThreads, 0);
     return e;
 }
 
 template <int M>
-cudaError_t occupancy6(int (&per)[kVariants]) {
-    cudaError_t e = occupancy3<M, kRngSplitMix>(per);
-    if (e == cudaSuccess) e = occupancy3<M, kRngPhilox>(per + 3);
+cudaError_t occupancy_all(int (&per)[kVariants]) {
+    cudaError_t e = occupancy_probe<M, kRngSplitMix>(per);
+    if (e == cudaSuccess) e = occupancy_probe<M, kRngPhilox>(per + kProbeVariants);
     return e;
 }
 
@@ -913,12 +1004,12 @@ int sample_per_sm(int method, int device, int variant) {
         const int c = g_sample_per_sm[device][method][variant].load(std::memory_order_relaxed);
         if (c > 0) return c;
     }
-    int per[kVariants] = {1, 1, 1, 1, 1, 1};
+    int per[kVariants] = {1, 1, 1, 1, 1, 1, 1, 1};
     cudaError_t e;
-    if (method == 0) e = occupancy6<0>(per);
-    else if (method == 1) e = occupancy6<1>(per);
-    else if (method == 2) e = occupancy6<2>(per);
-    else e = occupancy6<3>(per);
+    if (method == 0) e = occupancy_all<0>(per);
+    else if (method == 1) e = occupancy_all<1>(per);
+    else if (method == 2) e = occupancy_all<2>(per);
+    else e = occupancy_all<3>(per);
     for (int v = 0; v < kVariants; ++v) {
         if (e != cudaSuccess || per[v] < 1) per[v] = 1;
         if (cached && e == cudaSuccess) g_sample_per_sm[device][method][v].store(per[v], std::memory_order_relaxed);
@@ -934,7 +1025,7 @@ int sample_blocks(int method, int device) {
 
 int sample_launch_blocks(int method, int device, const DevGraph &g) {
     return device_sms(device) *
-           sample_per_sm(method, device, (g.hash ? (g.filter ? 2 : 1) : 0) + (g.rng == kRngPhilox ? 3 : 0));
+           sample_per_sm(method, device, probe_variant(method, g) + (g.rng == kRngPhilox ? kProbeVariants : 0));
 }
 
 namespace {
@@ -959,15 +1050,22 @@ template <int STAGE, int RNG>
 cudaError_t launch_deferred_rng(const DevGraph &g, uint64_t first, uint64_t count, uint64_t seed, uint64_t *partials,
                                 int blocks, uint8_t *classes, uint32_t *verts, cudaStream_t s) {
     const bool rec = classes != nullptr;
-    if (g.hash && g.filter) {
-        if (rec) k_sample_deferred<true, true, STAGE, true, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-        else k_sample_deferred<false, true, STAGE, true, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-    } else if (g.hash) {
-        if (rec) k_sample_deferred<true, true, STAGE, false, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-        else k_sample_deferred<false, true, STAGE, false, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-    } else {
-        if (rec) k_sample_deferred<true, false, STAGE, false, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
-        else k_sample_deferred<false, false, STAGE, false, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+    switch (probe_variant(2, g)) {
+        case 2:
+            if (rec) k_sample_deferred<true, true, STAGE, kPmFilter, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+            else k_sample_deferred<false, true, STAGE, kPmFilter, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+            break;
+        case 3:
+            if (rec) k_sample_deferred<true, true, STAGE, kPmStream, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+            else k_sample_deferred<false, true, STAGE, kPmStream, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+            break;
+        case 1:
+            if (rec) k_sample_deferred<true, true, STAGE, kPmPlain, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+            else k_sample_deferred<false, true, STAGE, kPmPlain, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+            break;
+        default:
+            if (rec) k_sample_deferred<true, false, STAGE, kPmPlain, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
+            else k_sample_deferred<false, false, STAGE, kPmPlain, RNG><<<blocks, kThreads, 0, s>>>(g, first, count, seed, partials, classes, verts);
     }
     return cudaGetLastError();
 }

@@ -139,8 +139,13 @@ __global__ void __launch_bounds__(kTableThreads) k_slots(uint32_t n, uint4 *vert
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     Totals t = {};
-    for (uint64_t v = (uint64_t)blockIdx.x * wpb + warp; v < n; v += (uint64_t)gridDim.x * wpb) {
-        const uint4 vr = vert[v];
+    const uint64_t stride = (uint64_t)gridDim.x * wpb;
+    uint64_t v = (uint64_t)blockIdx.x * wpb + warp;
+    uint4 next = v < n ? vert[v] : make_uint4(0u, 0u, 0u, 0u);
+    for (; v < n; v += stride) {
+        // the next vertex's record is loaded while this list is scanned
+        const uint4 vr = next;
+        if (v + stride < n) next = vert[v + stride];
         const uint32_t o = vr.x, d = vr.y;
         if (d > kLongList) continue;   // k_slots_long
         uint64_t run = 0, qsum = 0;
@@ -371,8 +376,13 @@ __global__ void __launch_bounds__(kTableThreads) k_sigma_alias(uint32_t n, const
     uint64_t *pre = s_pre[warp];
     uint32_t *idx = s_idx[warp];
     const uint32_t below = (1u << lane) - 1u;
-    for (uint64_t v = (uint64_t)blockIdx.x * wpb + warp; v < n; v += (uint64_t)gridDim.x * wpb) {
-        const uint4 vr = vert[v];
+    const uint64_t stride = (uint64_t)gridDim.x * wpb;
+    uint64_t v = (uint64_t)blockIdx.x * wpb + warp;
+    uint4 next = v < n ? vert[v] : make_uint4(0u, 0u, 0u, 0u);
+    for (; v < n; v += stride) {
+        // the next list's record is loaded while this one is built
+        const uint4 vr = next;
+        if (v + stride < n) next = vert[v + stride];
         const uint32_t o = vr.x, d = vr.y, S = vr.z;
         if (d == 0 || (d > kLongList && S != 0)) continue;   // long lists: k_sigma_alias_long
         uint32_t *slot32 = reinterpret_cast<uint32_t *>(slot);
@@ -652,20 +662,36 @@ __global__ void __launch_bounds__(kSeedThreads) k_level_count(uint32_t n, const 
     if (W == 0) return;
     const u128 cut = heavy_cut(W, split);
     const uint64_t base = (uint64_t)blockIdx.x * kSeedChunk;
-    SeedAgg acc;
-    acc.nl = acc.nh = 0;
-    acc.D = acc.E = 0;
+    // each thread's count and weight over its rounds, then one block sum
+    uint32_t nh = 0;
+    u128 E = 0;
     for (int r = 0; r < kSeedRounds; ++r) {
         const uint64_t j = base + (uint64_t)r * kSeedThreads + threadIdx.x;
-        const bool heavy = j < n && T.w[j] >= cut;
-        uint32_t xl, xh;
-        u128 xD, xE;
-        SeedAgg t;
-        block_scan4(false, heavy, 0, heavy ? T.w[j] : 0, xl, xh, xD, xE, t);
-        acc.nh += t.nh;
-        acc.E += t.E;
+        if (j < n) {
+            const u128 w = T.w[j];
+            if (w >= cut) {
+                ++nh;
+                E += w;
+            }
+        }
     }
-    if (threadIdx.x == 0) T.agg[blockIdx.x] = acc;
+    __shared__ uint32_t s_h[kSeedThreads / kWarp];
+    __shared__ u128 s_E[kSeedThreads / kWarp];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) nh += __shfl_down_sync(0xffffffffu, nh, d);
+    E = warp_sum128(E);
+    if (lane == 0) { s_h[warp] = nh; s_E[warp] = E; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SeedAgg acc;
+        acc.nl = 0;
+        acc.nh = 0;
+        acc.D = 0;
+        acc.E = 0;
+        for (int k = 0; k < kSeedThreads / kWarp; ++k) { acc.nh += s_h[k]; acc.E += s_E[k]; }
+        T.agg[blockIdx.x] = acc;
+    }
 }
 
 // exclusive offsets of the chunks (one block per table) and the level record
@@ -733,18 +759,27 @@ __global__ void __launch_bounds__(kSeedThreads) k_level_place(uint32_t n, const 
     const u128 cut = heavy_cut(W, split);
     const uint32_t nh = tot->level[T.which].nh;
     uint32_t before = T.agg[blockIdx.x].nh;   // heavies in earlier chunks
+    __shared__ uint32_t s_w[2][kSeedThreads / kWarp];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int r = 0; r < kSeedRounds; ++r) {
         const uint64_t j = base + (uint64_t)r * kSeedThreads + threadIdx.x;
         const bool heavy = j < n && T.w[j] >= cut;
-        uint32_t xl, xh;
-        u128 xD, xE;
-        SeedAgg t;
-        block_scan4(false, heavy, 0, 0, xl, xh, xD, xE, t);
+        // rank among the round's heavies: a ballot per warp, the warps'
+        // counts through shared memory (double-buffered: one barrier a round)
+        const uint32_t b = __ballot_sync(0xffffffffu, heavy);
+        if (lane == 0) s_w[r & 1][warp] = __popc(b);
+        __syncthreads();
+        uint32_t xh = __popc(b & ((1u << lane) - 1u)), total = 0;
+        for (int k = 0; k < kSeedThreads / kWarp; ++k) {
+            const uint32_t c = s_w[r & 1][k];
+            if (k < warp) xh += c;
+            total += c;
+        }
         if (j < n) {
             const uint32_t hb = before + xh;   // heavies before j
             T.perm[heavy ? hb : nh + ((uint32_t)j - hb)] = (uint32_t)j;
         }
-        before += t.nh;
+        before += total;
     }
 }
 
