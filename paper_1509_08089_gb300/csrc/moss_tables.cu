@@ -581,40 +581,45 @@ __device__ __forceinline__ void seed_item(const SeedTask &T, uint64_t j, uint32_
     }
 }
 
-// exclusive block scan of (lights, heavies, D, E); returns the block totals
-__device__ __forceinline__ void block_scan4(bool light, bool heavy, u128 D, u128 E, uint32_t &xl, uint32_t &xh,
-                                            u128 &xD, u128 &xE, SeedAgg &tot) {
+// exclusive block scan of per-thread counts (lights, heavies) and sums
+// (deficits D, excesses E); returns the block totals
+__device__ __forceinline__ void block_scan_counts(uint32_t cl, uint32_t ch, u128 D, u128 E, uint32_t &xl,
+                                                  uint32_t &xh, u128 &xD, u128 &xE, SeedAgg &tot) {
     __shared__ uint32_t s_l[kSeedThreads / kWarp], s_h[kSeedThreads / kWarp];
     __shared__ u128 s_D[kSeedThreads / kWarp], s_E[kSeedThreads / kWarp];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t below = (1u << lane) - 1u;
-    const uint32_t lm = __ballot_sync(0xffffffffu, light), hm = __ballot_sync(0xffffffffu, heavy);
+    uint32_t il = cl, ih = ch;
+#pragma unroll
+    for (int d = 1; d < kWarp; d <<= 1) {
+        const uint32_t a = __shfl_up_sync(0xffffffffu, il, d), b = __shfl_up_sync(0xffffffffu, ih, d);
+        if (lane >= d) { il += a; ih += b; }
+    }
     const u128 Di = warp_incl_scan128(D, lane), Ei = warp_incl_scan128(E, lane);
     if (lane == 31) {
-        s_l[warp] = __popc(lm);
-        s_h[warp] = __popc(hm);
+        s_l[warp] = il;
+        s_h[warp] = ih;
         s_D[warp] = Di;
         s_E[warp] = Ei;
     }
     __syncthreads();
     uint32_t wl = 0, wh = 0;
     u128 wD = 0, wE = 0;
-    for (int k = 0; k < warp; ++k) {
-        wl += s_l[k];
-        wh += s_h[k];
-        wD += s_D[k];
-        wE += s_E[k];
-    }
     tot.nl = tot.nh = 0;
     tot.D = tot.E = 0;
     for (int k = 0; k < kSeedThreads / kWarp; ++k) {
+        if (k < warp) {
+            wl += s_l[k];
+            wh += s_h[k];
+            wD += s_D[k];
+            wE += s_E[k];
+        }
         tot.nl += s_l[k];
         tot.nh += s_h[k];
         tot.D += s_D[k];
         tot.E += s_E[k];
     }
-    xl = wl + __popc(lm & below);
-    xh = wh + __popc(hm & below);
+    xl = wl + il - cl;
+    xh = wh + ih - ch;
     xD = wD + Di - D;
     xE = wE + Ei - E;
     __syncthreads();
@@ -794,23 +799,23 @@ __global__ void __launch_bounds__(kSeedThreads) k_seed_count(uint32_t n, const D
     if (W == 0) return;
     const uint32_t m = task_items(T, tot, n), b0 = task_base(T, tot);
     const uint64_t base = (uint64_t)blockIdx.x * kSeedChunk;
-    SeedAgg acc;
-    acc.nl = acc.nh = 0;
-    acc.D = acc.E = 0;
+    // each thread's counts and deficit/excess sums, then one block sum
+    uint32_t cl = 0, ch = 0;
+    u128 sD = 0, sE = 0;
     for (int r = 0; r < kSeedRounds; ++r) {
         bool light, heavy;
         u128 D, E;
         seed_item(T, base + (uint64_t)r * kSeedThreads + threadIdx.x, m, b0, W, light, heavy, D, E);
-        uint32_t xl, xh;
-        u128 xD, xE;
-        SeedAgg t;
-        block_scan4(light, heavy, D, E, xl, xh, xD, xE, t);
-        acc.nl += t.nl;
-        acc.nh += t.nh;
-        acc.D += t.D;
-        acc.E += t.E;
+        cl += light;
+        ch += heavy;
+        sD += D;
+        sE += E;
     }
-    if (threadIdx.x == 0) T.agg[blockIdx.x] = acc;
+    uint32_t xl, xh;
+    u128 xD, xE;
+    SeedAgg t;
+    block_scan_counts(cl, ch, sD, sE, xl, xh, xD, xE, t);
+    if (threadIdx.x == 0) T.agg[blockIdx.x] = t;
 }
 
 // phase 2: exclusive scan of the chunk aggregates (one block per level)
@@ -879,30 +884,43 @@ __global__ void __launch_bounds__(kSeedThreads) k_seed_place(uint32_t n, const D
     const u128 W = task_total(T, tot);
     if (W == 0) return;
     const uint32_t m = task_items(T, tot, n), b0 = task_base(T, tot);
-    const uint64_t base = (uint64_t)blockIdx.x * kSeedChunk;
-    SeedAgg off = T.agg[blockIdx.x];
+    // thread t takes kSeedRounds consecutive items of the chunk: its counts
+    // and sums, one block scan of them, then the items again in order
+    const uint64_t first = (uint64_t)blockIdx.x * kSeedChunk + (uint64_t)threadIdx.x * kSeedRounds;
+    uint32_t cl = 0, ch = 0;
+    u128 sD = 0, sE = 0;
     for (int r = 0; r < kSeedRounds; ++r) {
-        const uint64_t j = base + (uint64_t)r * kSeedThreads + threadIdx.x;
+        bool light, heavy;
+        u128 D, E;
+        seed_item(T, first + r, m, b0, W, light, heavy, D, E);
+        cl += light;
+        ch += heavy;
+        sD += D;
+        sE += E;
+    }
+    uint32_t xl, xh;
+    u128 xD, xE;
+    SeedAgg t;
+    block_scan_counts(cl, ch, sD, sE, xl, xh, xD, xE, t);
+    const SeedAgg off = T.agg[blockIdx.x];
+    uint32_t rl = off.nl + xl, rh = off.nh + xh;
+    u128 A = off.D + xD, P = off.E + xE;
+    for (int r = 0; r < kSeedRounds; ++r) {
+        const uint64_t j = first + r;
         bool light, heavy;
         u128 D, E;
         seed_item(T, j, m, b0, W, light, heavy, D, E);
-        uint32_t xl, xh;
-        u128 xD, xE;
-        SeedAgg t;
-        block_scan4(light, heavy, D, E, xl, xh, xD, xE, t);
         if (light) {
-            const uint32_t rnk = off.nl + xl;
-            T.idx[rnk] = (uint32_t)j;
-            T.pre[rnk] = off.D + xD;                       // exclusive A_i
+            T.idx[rl] = (uint32_t)j;
+            T.pre[rl] = A;                                 // exclusive A_i
+            ++rl;
+            A += D;
         } else if (heavy) {
-            const uint32_t rnk = off.nh + xh;
-            T.idx[m - 1 - rnk] = (uint32_t)j;
-            T.pre[m - 1 - rnk] = off.E + xE + E;           // inclusive P_k
+            P += E;
+            T.idx[m - 1 - rh] = (uint32_t)j;
+            T.pre[m - 1 - rh] = P;                         // inclusive P_k
+            ++rh;
         }
-        off.nl += t.nl;
-        off.nh += t.nh;
-        off.D += t.D;
-        off.E += t.E;
     }
 }
 
