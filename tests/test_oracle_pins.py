@@ -368,3 +368,19 @@ def test_identities_on_power_law_graph():
     n5 = g.esu(5).astype(np.int64)
     t2 = table2()
     assert g.Lambda4 == sum(t2[i][2] * int(n5[i]) for i in range(1, 22))
+
+
+def test_default_vertex_splits():
+    """The default level split: one level below 2^14 vertices, split 12 up to
+    2^20, split 20 from there; the MOSS-4Min table one level below 2^20."""
+    assert [oracle.default_split(n) for n in (1, (1 << 14) - 1, 1 << 14, (1 << 20) - 1, 1 << 20)] == \
+        [oracle.ONE_LEVEL, oracle.ONE_LEVEL, oracle.VSPLIT_MID, oracle.VSPLIT_MID, oracle.VSPLIT]
+    assert [oracle.default_split_min(n) for n in (1 << 14, (1 << 20) - 1, 1 << 20)] == \
+        [oracle.ONE_LEVEL, oracle.ONE_LEVEL, oracle.VSPLIT]
+    rp, col = synth.chung_lu(1 << 14, 2.2, 8.0, 200.0, seed=3)
+    g = oracle.OracleGraph(rp, col)
+    assert (g.vsplit, g.vsplit_min) == (oracle.VSPLIT_MID, oracle.ONE_LEVEL)
+    assert all(g.vertex_table(l)["nh"] > 0 for l in range(3))
+    g.build_min()
+    assert g.vertex_table(3)["nh"] == 0
+    assert oracle.OracleGraph(rp, col, vsplit=9).vsplit_min == 9
