@@ -36,7 +36,7 @@ namespace {
 constexpr int kWarp = 32;
 constexpr int kTableThreads = 256;
 constexpr uint32_t kLongList = 256;   // longer lists get a block each in the alias passes
-constexpr int kUnroll = 4;            // chunks of 32 slots per round in k_slots
+constexpr int kUnroll = 2;            // chunks of 32 slots per round in k_slots
 constexpr int kLongThreads = 256;
 
 // ------------------------------------------------------------ vertices ---
@@ -134,11 +134,14 @@ __device__ __forceinline__ void vertex_weights(uint64_t v, uint32_t d, uint64_t 
     t.dmax = d > t.dmax ? d : t.dmax;
 }
 
-__global__ void __launch_bounds__(kTableThreads) k_slots(uint32_t n, uint4 *vert, uint32_t *acc, uint64_t *sq,
+__global__ void __launch_bounds__(kTableThreads, 6) k_slots(uint32_t n, uint4 *vert, uint32_t *acc, uint64_t *sq,
                                                         u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    Totals t = {};
+    // each warp's share of the totals in shared memory, added by its lane 0
+    // (held in registers it took the kernel to 80 and three blocks per SM)
+    __shared__ Totals sh[kTableThreads / kWarp];
+    if (lane == 0) sh[warp] = Totals{};
     const uint64_t stride = (uint64_t)gridDim.x * wpb;
     uint64_t v = (uint64_t)blockIdx.x * wpb + warp;
     uint4 next = v < n ? vert[v] : make_uint4(0u, 0u, 0u, 0u);
@@ -172,11 +175,9 @@ __global__ void __launch_bounds__(kTableThreads) k_slots(uint32_t n, uint4 *vert
                 qsum += __shfl_sync(0xffffffffu, incl2, 31);
             }
         }
-        if (lane == 0) vertex_weights(v, d, run, qsum, vert, gam0, gam1, gam2, t);
+        if (lane == 0) vertex_weights(v, d, run, qsum, vert, gam0, gam1, gam2, sh[warp]);
     }
-    // block reduction of the totals (lane 0 of each warp holds its share)
-    __shared__ Totals sh[kTableThreads / kWarp];
-    if (lane == 0) sh[warp] = t;
+    // block reduction of the totals
     __syncthreads();
     if (threadIdx.x == 0) {
         Totals b = {};
