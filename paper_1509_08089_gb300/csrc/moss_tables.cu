@@ -191,7 +191,8 @@ __global__ void __launch_bounds__(kTableThreads, 6) k_slots(uint32_t n, uint4 *v
 __global__ void __launch_bounds__(kLongThreads) k_slots_long(uint32_t n, uint4 *vert, uint32_t *acc, uint64_t *sq,
                                                             u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials) {
     __shared__ uint64_t s_w[kLongThreads / kWarp], s_q[kLongThreads / kWarp];
-    Totals t = {};
+    __shared__ Totals t;   // the block's share, added by thread 0
+    if (threadIdx.x == 0) t = Totals{};
     for_each_vertex<kLongThreads>(n, vert, [](uint4 vr) { return vr.y > kLongList; }, [&](uint32_t v) {
         const uint4 vr = vert[v];
         const uint32_t o = vr.x, d = vr.y;
