@@ -94,13 +94,13 @@ def parse():
 def _oracle_worker(args):
     """One process of the CPU baseline: build the oracle's tables for the
     workload, then draw its share of samples of each sub-method."""
-    workload, k, seed, shares, rng = args
+    workload, k, seed, shares, rng, vsplit = args
     sys.path.insert(0, ROOT)
     import oracle
     import synth
     rp, col = synth.workload(workload)
     t0 = time.perf_counter()
-    g = oracle.OracleGraph(rp, col)
+    g = oracle.OracleGraph(rp, col, vsplit=vsplit)
     if any(m == oracle.MOSS4MIN for m, _, _ in shares):
         g.build_min()
     t1 = time.perf_counter()
@@ -114,12 +114,12 @@ def sub_methods(k, mix=False):
     return ([0, 3] if mix else [0]) if k == 4 else [1, 2]
 
 
-def oracle_pass(pool, cores, workload, k, seed, per_worker, mix=False, rng=0):
+def oracle_pass(pool, cores, workload, k, seed, per_worker, mix=False, rng=0, vsplit=None):
     methods = sub_methods(k, mix)
     jobs = []
     for w in range(cores):
         shares = [(m, w * per_worker // len(methods), per_worker // len(methods)) for m in methods]
-        jobs.append((workload, k, seed, shares, rng))
+        jobs.append((workload, k, seed, shares, rng, vsplit))
     t0 = time.perf_counter()
     res = list(pool.map(_oracle_worker, jobs))
     wall = time.perf_counter() - t0
@@ -139,22 +139,25 @@ def oracle_rate(build, sample_wall, samples, budget):
 def bench_config(args, rp, world: int, workload: str | None = None) -> dict:
     """The `config` object of a line; both arms print the same one."""
     wl = workload or describe(args.workload, args.k, args.mode == "min")[1]
-    return {"workload": wl, "budget_per_gpu": args.budget, "seed": args.seed,
-            "probe": resolved_probe(args.probe, rp), "rng": args.rng,
-            "l2": "GPU arm: flushed (512 MB write) before every timed step; CPU oracle: not applicable",
-            "parallelism": f"replicas x{world}"}
+    cfg = {"workload": wl, "budget_per_gpu": args.budget, "seed": args.seed,
+           "probe": resolved_probe(args.probe, rp), "rng": args.rng,
+           "l2": "GPU arm: flushed (512 MB write) before every timed step; CPU oracle: not applicable",
+           "parallelism": f"replicas x{world}"}
+    if args.vertex_split >= 0:
+        cfg["vertex_split"] = args.vertex_split
+    return cfg
 
 
 RNG_IDS = {"splitmix64": 0, "philox4x32": 1}   # the same numbering on both sides
 
 
-def calibrate_per_worker(workload, k, seed, seconds, mix=False, rng=0):
+def calibrate_per_worker(workload, k, seed, seconds, mix=False, rng=0, vsplit=None):
     """Samples per worker process for about `seconds` of sampling, and the
     oracle's sampling rate on one core (samples/s) measured on the way."""
     import oracle
     import synth
     rp, col = synth.workload(workload)
-    g = oracle.OracleGraph(rp, col)
+    g = oracle.OracleGraph(rp, col, vsplit=vsplit)
     methods = sub_methods(k, mix)
     if mix:
         g.build_min()
@@ -189,13 +192,14 @@ def run_reference(args):
     rp, _col = synth.workload(args.workload)
     cores = os.cpu_count() or 1
     rng = RNG_IDS[args.rng]
-    per_worker, single = calibrate_per_worker(args.workload, args.k, args.seed, 4.0, mix, rng)
+    vsplit = args.vertex_split if args.vertex_split >= 0 else None
+    per_worker, single = calibrate_per_worker(args.workload, args.k, args.seed, 4.0, mix, rng, vsplit)
     with make_pool(cores) as pool:
         for _ in range(args.warmup):
-            oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker, mix, rng)
+            oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker, mix, rng, vsplit)
         walls, counts = [], []
         for _ in range(args.steps):
-            b, sw, n, wall = oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker, mix, rng)
+            b, sw, n, wall = oracle_pass(pool, cores, args.workload, args.k, args.seed, per_worker, mix, rng, vsplit)
             walls.append(wall)
             counts.append(n)
     samples = counts[0]
@@ -294,7 +298,26 @@ def resolved_probe(name: str, row_ptr) -> str:
     return "filter" if b * 32 > (64 << 20) else "hash"
 
 
-def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False, two_level: bool = False) -> int:
+def default_vertex_splits(n: int) -> tuple[int, int]:
+    """The library's default level splits of a graph of n vertices: of the
+    vertex tables of Gamma, Gamma^(1), Gamma^(2), and of the MOSS-4Min
+    table (64: one level)."""
+    if n >= 1 << 20:
+        return 20, 20
+    return (12, 64) if n >= 1 << 14 else (64, 64)
+
+
+def two_levels(args, n: int) -> tuple[bool, bool]:
+    """Whether the build splits the vertex tables (and the MOSS-4Min table)
+    into two levels under the run's vertex split."""
+    if args.vertex_split >= 0:
+        return args.vertex_split < 64, args.vertex_split < 64
+    main, mn = default_vertex_splits(n)
+    return main < 64, mn < 64
+
+
+def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False, two_level: bool = False,
+                      two_level_min: bool | None = None) -> int:
     """Kernels of one step: load 7 (vertices, owners, slot weights, short and
     long slot scans, twins, totals); build 8 (two sigma alias passes, the
     alias-half fill, four alias phases of the vertex tables, edge hash), 3
@@ -309,7 +332,8 @@ def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False, tw
     finalize."""
     from paper_1509_08089_gb300.dist import sub_budgets
     split = 3 if two_level else 0
-    n = 7 + 8 + split + (7 if filtered else 0) + ((12 + split) if mix else 0) + 1
+    split_min = split if two_level_min is None else (3 if two_level_min else 0)
+    n = 7 + 8 + split + (7 if filtered else 0) + ((12 + split_min) if mix else 0) + 1
     for m, K in sub_budgets(k, budget, mix):
         n += 4 * -(-K // DEFER_CHUNK) if m == 2 else 2
     return n
@@ -613,7 +637,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": d2h},
         "roofline": roof,
         "clocks": clk,
-        "gpu_launches": launches_per_step(k, args.budget, mix, probe_name == "filter", len(rp) - 1 >= 1 << 20)
+        "gpu_launches": launches_per_step(k, args.budget, mix, probe_name == "filter", *two_levels(args, len(rp) - 1))
         * args.steps,
         "wall_s_timed": t_wall,
         "step_ms": step_ms,

@@ -52,6 +52,18 @@ def test_launches_per_step(k, budget, mix, filtered, two, expected):
     assert bench.launches_per_step(k, budget, mix, filtered, two) == expected
 
 
+def test_launches_follow_the_default_splits():
+    # 1M-edge graph (n = 100,000): two-level vertex tables, one-level MOSS-4Min table
+    assert bench.default_vertex_splits(100_000) == (12, 64)
+    assert bench.default_vertex_splits(4_000_000) == (20, 20)
+    assert bench.default_vertex_splits(2_000) == (64, 64)
+    assert bench.launches_per_step(4, 100_000_000, True, False, True, False) == 16 + 3 + 12 + 2 + 2
+    args = type("A", (), {"vertex_split": -1})()
+    assert bench.two_levels(args, 100_000) == (True, False)
+    args.vertex_split = 64
+    assert bench.two_levels(args, 100_000) == (False, False)
+
+
 def test_resolved_probe_follows_the_hash_size():
     import numpy as np
     small = np.array([0, 1_000_000], dtype=np.int64)     # 2^19 buckets of 32 B: 16 MiB
@@ -59,3 +71,9 @@ def test_resolved_probe_follows_the_hash_size():
     assert bench.resolved_probe("auto", small) == "hash"
     assert bench.resolved_probe("auto", large) == "filter"
     assert bench.resolved_probe("search", large) == "search"
+
+
+def test_default_splits_match_the_oracle():
+    import oracle
+    for n in (100, (1 << 14) - 1, 1 << 14, 100_000, (1 << 20) - 1, 1 << 20, 4_000_000):
+        assert bench.default_vertex_splits(n) == (oracle.default_split(n), oracle.default_split_min(n)), n
