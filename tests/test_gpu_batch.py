@@ -230,3 +230,30 @@ def test_every_tuner_setting_leaves_results_unchanged(fleet):
     finally:
         for g in filt + srch:
             g.close()
+
+
+def test_batch_on_two_level_graphs():
+    """A graph of 2^14 vertices or more has two-level vertex tables by
+    default; its solo launches run the L1-streaming sampler instances and the
+    batch kernel the plain ones.  Both must give the oracle's counts."""
+    csrs = [synth.chung_lu(20_000, 2.2, 10.0, 800.0, seed=77), synth.chung_lu(1_500, 2.5, 6.0, 120.0, seed=78)]
+    graphs = [moss.Graph(rp, col) for rp, col in csrs]
+    try:
+        assert moss.moss_vertex_levels(graphs[0].handle, 1)[0] > 0
+        picks = [(0, 5, 60_001, 91), (0, 4, 40_003, 92), (1, 5, 20_001, 93)]
+        with moss.Batch() as batch:
+            for gi, k, budget, seed in picks:
+                batch.add(graphs[gi], k, budget, seed)
+            res = batch.run()
+        for (gi, k, budget, seed), r in zip(picks, res):
+            same(r, graphs[gi].estimate(k, budget, seed))
+            og = oracle.OracleGraph(*csrs[gi])
+            if k == 4:
+                assert np.array_equal(r["hits"][0], og.run(oracle.MOSS4, seed, budget))
+            else:
+                K1, K2 = budget // 2, budget - budget // 2
+                assert np.array_equal(r["hits"][0], og.run(oracle.T5, seed, K1))
+                assert np.array_equal(r["hits"][1], og.run(oracle.PATH5, seed, K2))
+    finally:
+        for g in graphs:
+            g.close()
