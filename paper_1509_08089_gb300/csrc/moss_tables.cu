@@ -36,7 +36,7 @@ namespace {
 constexpr int kWarp = 32;
 constexpr int kTableThreads = 256;
 constexpr uint32_t kLongList = 256;   // longer lists get a block each in the alias passes
-constexpr int kUnroll = 2;            // chunks of 32 slots per round in k_slots
+constexpr int kUnroll = 1;            // chunks of 32 slots per round in k_slots
 constexpr int kLongThreads = 256;
 
 // ------------------------------------------------------------ vertices ---
@@ -111,9 +111,8 @@ struct Totals {
 
 // S_v, the vertex weights Gamma_v = (d-1) S_v, Gamma^(1)_v = (d-1)(d-2) S_v,
 // Gamma^(2)_v = S_v^2 - Q_v, and v's share of the totals
-__device__ __forceinline__ void vertex_weights(uint64_t v, uint32_t d, uint64_t S, uint64_t Q, uint4 *vert,
-                                               u128 *gam0, u128 *gam1, u128 *gam2, Totals &t) {
-    vert[v].z = (uint32_t)S;
+__device__ __forceinline__ void vertex_weights(uint64_t v, uint32_t d, uint64_t S, uint64_t Q, u128 *gam0,
+                                               u128 *gam1, u128 *gam2, Totals &t) {
     const u128 g0 = d >= 1 ? (u128)(d - 1) * S : 0;
     const u128 g1 = d >= 2 ? (u128)(d - 1) * (d - 2) * S : 0;
     const u128 g2 = (u128)S * S - Q;
@@ -134,14 +133,10 @@ __device__ __forceinline__ void vertex_weights(uint64_t v, uint32_t d, uint64_t 
     t.dmax = d > t.dmax ? d : t.dmax;
 }
 
-__global__ void __launch_bounds__(kTableThreads, 6) k_slots(uint32_t n, uint4 *vert, uint32_t *acc, uint64_t *sq,
-                                                        u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials) {
+__global__ void __launch_bounds__(kTableThreads, 8) k_slots(uint32_t n, uint4 *vert, uint32_t *acc, uint64_t *sq,
+                                                           u128 *gam2) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    // each warp's share of the totals in shared memory, added by its lane 0
-    // (held in registers it took the kernel to 80 and three blocks per SM)
-    __shared__ Totals sh[kTableThreads / kWarp];
-    if (lane == 0) sh[warp] = Totals{};
     const uint64_t stride = (uint64_t)gridDim.x * wpb;
     uint64_t v = (uint64_t)blockIdx.x * wpb + warp;
     uint4 next = v < n ? vert[v] : make_uint4(0u, 0u, 0u, 0u);
@@ -175,24 +170,18 @@ __global__ void __launch_bounds__(kTableThreads, 6) k_slots(uint32_t n, uint4 *v
                 qsum += __shfl_sync(0xffffffffu, incl2, 31);
             }
         }
-        if (lane == 0) vertex_weights(v, d, run, qsum, vert, gam0, gam1, gam2, sh[warp]);
-    }
-    // block reduction of the totals
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        Totals b = {};
-        for (int w = 0; w < wpb; ++w) b.add(sh[w]);
-        b.store(partials + (uint64_t)blockIdx.x * 6);
+        if (lane == 0) {   // S_v, and Q_v until k_vertex_weights turns it into Gamma^(2)_v
+            vert[v].z = (uint32_t)run;
+            gam2[v] = qsum;
+        }
     }
 }
 
 // lists longer than kLongList: a block per list scans NT x 4 entries a round
 // (each thread 4 consecutive ones, then a block scan of the thread sums)
 __global__ void __launch_bounds__(kLongThreads) k_slots_long(uint32_t n, uint4 *vert, uint32_t *acc, uint64_t *sq,
-                                                            u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials) {
+                                                            u128 *gam2) {
     __shared__ uint64_t s_w[kLongThreads / kWarp], s_q[kLongThreads / kWarp];
-    __shared__ Totals t;   // the block's share, added by thread 0
-    if (threadIdx.x == 0) t = Totals{};
     for_each_vertex<kLongThreads>(n, vert, [](uint4 vr) { return vr.y > kLongList; }, [&](uint32_t v) {
         const uint4 vr = vert[v];
         const uint32_t o = vr.x, d = vr.y;
@@ -223,10 +212,45 @@ __global__ void __launch_bounds__(kLongThreads) k_slots_long(uint32_t n, uint4 *
             run += tw;
             qsum += tq;
         }
-        if (threadIdx.x == 0) vertex_weights(v, d, run, qsum, vert, gam0, gam1, gam2, t);
+        if (threadIdx.x == 0) {   // S_v, and Q_v until k_vertex_weights turns it into Gamma^(2)_v
+            vert[v].z = (uint32_t)run;
+            gam2[v] = qsum;
+        }
         __syncthreads();
     });
-    if (threadIdx.x == 0) t.store(partials + (uint64_t)blockIdx.x * 6);
+}
+
+// Gamma_v, Gamma^(1)_v, Gamma^(2)_v from d_v, S_v and Q_v (left in gam2 by
+// the list scans), one thread per vertex, and each block's share of the
+// exact totals (the 128-bit arithmetic of a vertex on one lane each, instead
+// of on the first lane of a warp per list)
+__global__ void __launch_bounds__(kTableThreads) k_vertex_weights(uint32_t n, const uint4 *__restrict__ vert,
+                                                                  u128 *gam0, u128 *gam1, u128 *gam2, u128 *partials) {
+    Totals t = {};
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 r = vert[v];
+        vertex_weights(v, r.y, r.z, (uint64_t)gam2[v], gam0, gam1, gam2, t);
+    }
+    __shared__ Totals sh[kTableThreads / kWarp];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) {
+        Totals o;
+        o.g0 = shfl_down_u128(t.g0, k);
+        o.g1 = shfl_down_u128(t.g1, k);
+        o.g2 = shfl_down_u128(t.g2, k);
+        o.l3 = shfl_down_u128(t.l3, k);
+        o.l4 = shfl_down_u128(t.l4, k);
+        o.dmax = __shfl_down_sync(0xffffffffu, t.dmax, k);
+        t.add(o);
+    }
+    if (lane == 0) sh[warp] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Totals b = {};
+        for (int w = 0; w < kTableThreads / kWarp; ++w) b.add(sh[w]);
+        b.store(partials + (uint64_t)blockIdx.x * 6);
+    }
 }
 
 // One block of kTotalsThreads: each thread adds a strided share of the rows,
@@ -1154,7 +1178,7 @@ cudaError_t launch_vertices(const void *row_ptr, int is64, uint32_t n, uint64_t 
 }
 
 static unsigned long_blocks(uint32_t n);
-int slot_partial_rows(uint32_t n) { return table_blocks(n) + (int)long_blocks(n); }
+int slot_partial_rows(uint32_t n) { return table_blocks(n); }   // k_vertex_weights' rows
 
 static unsigned long_blocks(uint32_t n) {
     const int sms = current_sms();
@@ -1188,14 +1212,17 @@ cudaError_t launch_slots(uint32_t n, uint64_t nnz, const uint32_t *col, uint4 *v
     cudaStream_t ts = forked ? aux->a[0] : s, ls = forked ? aux->a[1] : s;
     if (nnz) k_twin<<<flat_blocks(nnz), 256, 0, ts>>>(n, nnz, vert, col, owner, slot, flags);
     cudaError_t et = cudaGetLastError();
-    k_slots_long<<<long_blocks(n), kLongThreads, 0, ls>>>(n, vert, acc, sq, gam0, gam1, gam2,
-                                                          partials + (uint64_t)blocks * 6);
+    k_slots_long<<<long_blocks(n), kLongThreads, 0, ls>>>(n, vert, acc, sq, gam2);
     cudaError_t el = cudaGetLastError();
-    k_slots<<<blocks, kTableThreads, 0, s>>>(n, vert, acc, sq, gam0, gam1, gam2, partials);
+    k_slots<<<blocks, kTableThreads, 0, s>>>(n, vert, acc, sq, gam2);
     e = cudaGetLastError();
     if (forked) {
         const cudaError_t ej = aux->join(s);
         if (e == cudaSuccess) e = ej;
+    }
+    if (e == cudaSuccess && et == cudaSuccess && el == cudaSuccess) {
+        k_vertex_weights<<<blocks, kTableThreads, 0, s>>>(n, vert, gam0, gam1, gam2, partials);
+        e = cudaGetLastError();
     }
     return e != cudaSuccess ? e : (et != cudaSuccess ? et : el);
 }
