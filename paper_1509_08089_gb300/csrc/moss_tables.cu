@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kTableThreads, 8) k_slots(uint32_t n, uint4 *v
                 if (base + u * kWarp >= d) break;   // warp-uniform
                 const uint32_t i = base + u * kWarp + lane;
                 const uint64_t w2 = (uint64_t)w[u] * w[u];
-                const uint64_t incl = warp_incl_scan64(w[u], lane);
+                const uint64_t incl = warp_incl_scan32(w[u], lane);   // S_v < 2^32
                 const uint64_t incl2 = warp_incl_scan64(w2, lane);
                 if (i < d) {
                     acc[o + i] = (uint32_t)(run + incl - w[u]);
