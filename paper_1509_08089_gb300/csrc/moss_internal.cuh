@@ -201,15 +201,6 @@ __device__ __forceinline__ uint64_t word_index(uint64_t x, uint64_t m) { return 
 // ------------------------------------------------------------ warp scans --
 __device__ __forceinline__ uint64_t shfl_up64(uint64_t v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
 
-__device__ __forceinline__ uint32_t warp_incl_scan32(uint32_t v, int lane) {
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, v, d);
-        if (lane >= d) v += t;
-    }
-    return v;
-}
-
 __device__ __forceinline__ uint64_t warp_incl_scan64(uint64_t v, int lane) {
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {

@@ -133,6 +133,15 @@ __device__ __forceinline__ void vertex_weights(uint64_t v, uint32_t d, uint64_t 
     t.dmax = d > t.dmax ? d : t.dmax;
 }
 
+__device__ __forceinline__ uint32_t warp_incl_scan32(uint32_t v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += t;
+    }
+    return v;
+}
+
 __global__ void __launch_bounds__(kTableThreads, 8) k_slots(uint32_t n, uint4 *vert, uint32_t *acc, uint64_t *sq,
                                                            u128 *gam2) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
