@@ -318,8 +318,8 @@ def two_levels(args, n: int) -> tuple[bool, bool]:
 
 def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False, two_level: bool = False,
                       two_level_min: bool | None = None) -> int:
-    """Kernels of one step: load 7 (vertices, owners, slot weights, short and
-    long slot scans, twins, totals); build 8 (two sigma alias passes, the
+    """Kernels of one step: load 8 (vertices, owners, slot weights, short and
+    long slot scans, twins, vertex weights, totals); build 8 (two sigma alias passes, the
     alias-half fill, four alias phases of the vertex tables, edge hash), 3
     more (the level split) for two-level vertex tables, 7 more behind the
     edge filter (the filter, and the hubs' degree histogram, degree cut,
@@ -333,7 +333,7 @@ def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False, tw
     from paper_1509_08089_gb300.dist import sub_budgets
     split = 3 if two_level else 0
     split_min = split if two_level_min is None else (3 if two_level_min else 0)
-    n = 7 + 8 + split + (7 if filtered else 0) + ((12 + split_min) if mix else 0) + 1
+    n = 8 + 8 + split + (7 if filtered else 0) + ((12 + split_min) if mix else 0) + 1
     for m, K in sub_budgets(k, budget, mix):
         n += 4 * -(-K // DEFER_CHUNK) if m == 2 else 2
     return n

@@ -38,14 +38,14 @@ def test_reference_arm_json_line():
 
 
 @pytest.mark.parametrize("k,budget,mix,filtered,two,expected", [
-    # load 7 + build 8 + finalize 1; T-5: sampler + reduce; Path-5: main, two redraw stages, reduce per chunk
-    (5, 100_000_000, False, False, False, 16 + 2 + 4),
+    # load 8 + build 8 + finalize 1; T-5: sampler + reduce; Path-5: main, two redraw stages, reduce per chunk
+    (5, 100_000_000, False, False, False, 17 + 2 + 4),
     # the edge filter and its 6 hub kernels, two-level vertex tables 3 split
     # kernels; 5e8 Path-5 ids: 8 chunks of 2^26
-    (5, 1_000_000_000, False, True, True, 16 + 7 + 3 + 2 + 4 * 8),
-    (4, 100_000_000, False, False, False, 16 + 2),
-    (4, 100_000_000, True, False, False, 16 + 12 + 2 + 2),    # MOSS-4 + MOSS-4Min with its 12 table kernels
-    (4, 100_000_000, True, False, True, 16 + 3 + 15 + 2 + 2),
+    (5, 1_000_000_000, False, True, True, 17 + 7 + 3 + 2 + 4 * 8),
+    (4, 100_000_000, False, False, False, 17 + 2),
+    (4, 100_000_000, True, False, False, 17 + 12 + 2 + 2),    # MOSS-4 + MOSS-4Min with its 12 table kernels
+    (4, 100_000_000, True, False, True, 17 + 3 + 15 + 2 + 2),
 ])
 def test_launches_per_step(k, budget, mix, filtered, two, expected):
     assert bench.DEFER_CHUNK == 1 << 26
@@ -57,7 +57,7 @@ def test_launches_follow_the_default_splits():
     assert bench.default_vertex_splits(100_000) == (12, 64)
     assert bench.default_vertex_splits(4_000_000) == (20, 20)
     assert bench.default_vertex_splits(2_000) == (64, 64)
-    assert bench.launches_per_step(4, 100_000_000, True, False, True, False) == 16 + 3 + 12 + 2 + 2
+    assert bench.launches_per_step(4, 100_000_000, True, False, True, False) == 17 + 3 + 12 + 2 + 2
     args = type("A", (), {"vertex_split": -1})()
     assert bench.two_levels(args, 100_000) == (True, False)
     args.vertex_split = 64
