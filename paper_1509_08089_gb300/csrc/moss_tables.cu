@@ -660,10 +660,8 @@ __device__ __forceinline__ void block_scan_counts(uint32_t cl, uint32_t ch, u128
     __syncthreads();
 }
 
-// floor(thr 2^64 / W) for thr <= W, saturated (binary long division)
-__device__ __forceinline__ uint64_t quantize64(u128 thr, u128 W) {
-    if (W == 0) return 0;
-    if (thr >= W) return ~0ULL;
+// floor(thr 2^64 / W) for thr < W by binary long division
+__device__ __noinline__ uint64_t quantize64_long(u128 thr, u128 W) {
     uint64_t qq = 0;
     u128 r = thr;
     for (int i = 0; i < 64; ++i) {
@@ -673,6 +671,69 @@ __device__ __forceinline__ uint64_t quantize64(u128 thr, u128 W) {
         if (carry || r >= W) { r -= W; qq |= 1; }
     }
     return qq;
+}
+
+__device__ __forceinline__ double u128_to_double(u128 x) {
+    return (double)(uint64_t)(x >> 64) * 18446744073709551616.0 + (double)(uint64_t)x;
+}
+
+// thr 2^64 - q W as a signed 192-bit number: (hi, lo), hi's sign its sign
+__device__ __forceinline__ void quantize_rem(u128 thr, u128 W, uint64_t q, int64_t &hi, u128 &lo) {
+    const u128 p0 = (u128)q * (uint64_t)W, p1 = (u128)q * (uint64_t)(W >> 64);
+    const u128 blo = p0 + (p1 << 64);
+    const uint64_t bhi = (uint64_t)(p1 >> 64) + (blo < p0 ? 1u : 0u);
+    const u128 alo = (u128)(uint64_t)thr << 64;
+    const uint64_t ahi = (uint64_t)(thr >> 64);
+    lo = alo - blo;
+    hi = (int64_t)(ahi - bhi - (alo < blo ? 1u : 0u));
+}
+
+// floor(thr 2^64 / W) for thr <= W, saturated: a double estimate (53 good
+// bits), one correction from the exact remainder, then at most a few unit
+// steps -- the long division when they do not settle
+__device__ __forceinline__ uint64_t quantize64(u128 thr, u128 W) {
+    if (W == 0) return 0;
+    if (thr >= W) return ~0ULL;
+    const double dw = u128_to_double(W);
+    const double est = u128_to_double(thr) / dw * 18446744073709551616.0;
+    uint64_t q = est >= 18446744073709549568.0 ? ~0ULL : (uint64_t)est;
+    int64_t hi;
+    u128 lo;
+    quantize_rem(thr, W, q, hi, lo);
+    // the remainder is a few thousand W at most: its quotient by W in
+    // doubles, from its magnitude (the two halves of a negative one would
+    // cancel in a double)
+    double rem;
+    if (hi < 0) {
+        const u128 nlo = ~lo + 1;
+        const uint64_t nhi = ~(uint64_t)hi + (nlo == 0 ? 1u : 0u);
+        rem = -((double)nhi * 340282366920938463463374607431768211456.0 + u128_to_double(nlo));
+    } else {
+        rem = (double)hi * 340282366920938463463374607431768211456.0 + u128_to_double(lo);
+    }
+    const double delta = rem / dw;
+    if (delta > -1e6 && delta < 1e6) {
+        const int64_t step = (int64_t)floor(delta);
+        if (step < 0) q = (uint64_t)(-step) > q ? 0 : q - (uint64_t)(-step);
+        else q = (uint64_t)step > ~q ? ~0ULL : q + (uint64_t)step;
+        quantize_rem(thr, W, q, hi, lo);
+        for (int it = 0; it < 4; ++it) {
+            if (hi < 0) {   // remainder below 0: one W too many
+                --q;
+                const u128 nlo = lo + W;
+                hi += nlo < lo ? 1 : 0;
+                lo = nlo;
+            } else if (hi > 0 || lo >= W) {   // at least W left
+                ++q;
+                const u128 nlo = lo - W;
+                hi -= nlo > lo ? 1 : 0;
+                lo = nlo;
+            } else {
+                return q;
+            }
+        }
+    }
+    return quantize64_long(thr, W);
 }
 
 // ---- the split into levels (per table): heavy iff w_v >= ceil(W / 2^split)
