@@ -197,17 +197,21 @@ __device__ void block_alias(uint32_t d, T W, Weight weight, uint32_t *idx, T *pr
 // Calls body(v) for every vertex v < n whose record passes pred, one vertex at
 // a time for the whole block (body is block-cooperative).  Blocks take chunks
 // of CH <= NT vertices and test a chunk's records in parallel, so a block
-// touches n / gridDim records in coalesced loads rather than one by one; a
-// small CH spreads frequent qualifying vertices over more blocks.
+// touches n / gridDim records rather than one by one; a small CH spreads
+// frequent qualifying vertices over more blocks.  Chunk c holds the vertices
+// c + j C (j < CH, C = ceil(n / CH) chunks): vertices that are close in id
+// fall into different chunks, so a graph whose long lists sit together (one
+// loaded in degree order) still spreads them over the blocks.
 template <int NT, int CH = NT, typename Pred, typename Body>
 __device__ void for_each_vertex(uint32_t n, const uint4 *rec, Pred pred, Body body) {
     static_assert(CH <= NT, "chunk larger than the block");
     __shared__ uint32_t found[CH];
     __shared__ uint32_t nfound;
-    for (uint64_t v0 = (uint64_t)blockIdx.x * CH; v0 < n; v0 += (uint64_t)gridDim.x * CH) {
+    const uint64_t chunks = ((uint64_t)n + CH - 1) / CH;
+    for (uint64_t c = blockIdx.x; c < chunks; c += gridDim.x) {
         if (threadIdx.x == 0) nfound = 0;
         __syncthreads();
-        const uint64_t v = v0 + threadIdx.x;
+        const uint64_t v = c + (uint64_t)threadIdx.x * chunks;
         if (threadIdx.x < CH && v < n && pred(rec[v])) found[atomicAdd(&nfound, 1u)] = (uint32_t)v;
         __syncthreads();
         const uint32_t cnt = nfound;
