@@ -84,6 +84,9 @@ def parse():
                    help="word generator of the samples (both sides of the comparison use it)")
     p.add_argument("--vertex-split", type=int, default=-1,
                    help="vertex-table level split of the workload's graph (0..64; default: the library's)")
+    p.add_argument("--vertex-order", default="auto", choices=["auto", "input", "degree"],
+                   help="internal vertex order of the loads: auto (degree order when the sampling tables "
+                        "exceed the L2, else the input ids), the input ids, or degree order")
     p.add_argument("--probe", default="auto", choices=["auto", "hash", "filter", "search"],
                    help="induced-edge tests: auto (filtered set when the set exceeds 64 MiB, else the set), "
                         "hashed edge set, set behind a Bloom filter, or sorted-list search")
@@ -136,11 +139,11 @@ def oracle_rate(build, sample_wall, samples, budget):
     return budget / (build + budget / rate), rate
 
 
-def bench_config(args, rp, world: int, workload: str | None = None) -> dict:
+def bench_config(args, rp, world: int, workload: str | None = None, order: str = "input") -> dict:
     """The `config` object of a line; both arms print the same one."""
     wl = workload or describe(args.workload, args.k, args.mode == "min")[1]
     cfg = {"workload": wl, "budget_per_gpu": args.budget, "seed": args.seed,
-           "probe": resolved_probe(args.probe, rp), "rng": args.rng,
+           "probe": resolved_probe(args.probe, rp), "rng": args.rng, "vertex_order": order,
            "l2": "GPU arm: flushed (512 MB write) before every timed step; CPU oracle: not applicable",
            "parallelism": f"replicas x{world}"}
     if args.vertex_split >= 0:
@@ -206,13 +209,16 @@ def run_reference(args):
     wall = statistics.median(walls)
     v = samples / wall
     split = "T-5/Path-5" if args.k == 5 else ("MOSS-4/MOSS-4Min" if mix else "MOSS-4")
+    order = resolved_order(args.vertex_order, rp, resolved_probe(args.probe, rp), sub_methods(args.k, mix),
+                           GB300_L2_BYTES)
     sample = (f"{samples} of the workload's {args.budget} samples per step ({split} split evenly) over {cores} "
-              f"processes, each building the oracle's tables of the graph; value = samples / measured step time")
+              f"processes, each building the oracle's tables of the graph (input ids); value = samples / "
+              f"measured step time")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall, "samples_per_step": samples,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": bench_config(args, rp, args.gpus),
+        "config": bench_config(args, rp, args.gpus, order=order),
         "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle", "sample": sample,
                          "single_core_sampling_rate": single},
         "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -298,6 +304,27 @@ def resolved_probe(name: str, row_ptr) -> str:
     return "filter" if b * 32 > (64 << 20) else "hash"
 
 
+def resolved_order(name: str, row_ptr, probe: str, methods, l2_bytes: int) -> str:
+    """The vertex order --vertex-order auto picks: the graph loaded in degree
+    order when the tables a sampling call reads exceed the L2 (their records
+    then come from HBM, and grouping the heavy vertices puts the hot ones in
+    fewer lines), else the input ids (an L2-resident graph gains nothing
+    that pays for the renumbering)."""
+    if name != "auto":
+        return name
+    return "degree" if sampler_tables_bytes(row_ptr, probe, methods) > l2_bytes else "input"
+
+
+ORDER_IDS = {"input": 0, "degree": 1}
+GB300_L2_BYTES = 135_528_448   # the device's L2 (cudaDevAttrL2CacheSize); the CPU arm has no device to ask
+
+
+def data_key(workload: str, order: str) -> str:
+    """Name of a workload's sector-model and DRAM-capture files: the degree
+    order has its own (the layout of the renumbered graph)."""
+    return workload + ("_degree" if order == "degree" else "")
+
+
 def default_vertex_splits(n: int) -> tuple[int, int]:
     """The library's default level splits of a graph of n vertices: of the
     vertex tables of Gamma, Gamma^(1), Gamma^(2), and of the MOSS-4Min
@@ -317,9 +344,10 @@ def two_levels(args, n: int) -> tuple[bool, bool]:
 
 
 def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False, two_level: bool = False,
-                      two_level_min: bool | None = None) -> int:
+                      two_level_min: bool | None = None, ordered: bool = False) -> int:
     """Kernels of one step: load 8 (vertices, owners, slot weights, short and
-    long slot scans, twins, vertex weights, totals); build 8 (two sigma alias passes, the
+    long slot scans, twins, vertex weights, totals), 4 more in degree order
+    (key counts, their scan, the placement, the lists); build 8 (two sigma alias passes, the
     alias-half fill, four alias phases of the vertex tables, edge hash), 3
     more (the level split) for two-level vertex tables, 7 more behind the
     edge filter (the filter, and the hubs' degree histogram, degree cut,
@@ -333,7 +361,7 @@ def launches_per_step(k: int, budget: int, mix: bool, filtered: bool = False, tw
     from paper_1509_08089_gb300.dist import sub_budgets
     split = 3 if two_level else 0
     split_min = split if two_level_min is None else (3 if two_level_min else 0)
-    n = 8 + 8 + split + (7 if filtered else 0) + ((12 + split_min) if mix else 0) + 1
+    n = 8 + (4 if ordered else 0) + 8 + split + (7 if filtered else 0) + ((12 + split_min) if mix else 0) + 1
     for m, K in sub_budgets(k, budget, mix):
         n += 4 * -(-K // DEFER_CHUNK) if m == 2 else 2
     return n
@@ -528,8 +556,11 @@ def run_gpu(args):
 
     rng = RNG_IDS[args.rng]
 
-    def step(src_rp, src_col, seed, kk=k, budget=args.budget):
-        h = moss.moss_graph_load_csr(src_rp, src_col, device=dev, stream=stream)
+    methods_main = [m for m, _ in sub_budgets(k, args.budget, mix)]
+    order_main = resolved_order(args.vertex_order, rp, resolved_probe(args.probe, rp), methods_main, l2_bytes)
+
+    def step(src_rp, src_col, seed, kk=k, budget=args.budget, order=order_main):
+        h = moss.moss_graph_load_csr(src_rp, src_col, device=dev, stream=stream, order=ORDER_IDS[order])
         try:
             moss.moss_set_probe(h, probe)
             moss.moss_set_rng(h, rng)
@@ -613,7 +644,7 @@ def run_gpu(args):
     # ---- the dominant sampling call alone (the same call as inside the step)
     peaks = peaks_file()
     probe_name = resolved_probe(args.probe, rp)
-    h = moss.moss_graph_load_csr(rp_d, col_d, device=dev, stream=stream)
+    h = moss.moss_graph_load_csr(rp_d, col_d, device=dev, stream=stream, order=ORDER_IDS[order_main])
     try:
         moss.moss_set_probe(h, probe)
         moss.moss_set_rng(h, rng)
@@ -625,20 +656,20 @@ def run_gpu(args):
         moss.moss_graph_free(h)
     gather = (moss.moss_gather_rate(64 << 20, dev, stream) * 32.0 / 1e9,
               moss.moss_gather_rate(4 << 30, dev, stream) * 32.0 / 1e9)
-    roof = roofline(args.workload, rp, probe_name, times, [m for m, _ in sub_budgets(k, args.budget, mix)],
-                    l2_bytes, gather, peaks)
+    roof = roofline(data_key(args.workload, order_main), rp, probe_name, times, methods_main, l2_bytes, gather,
+                    peaks)
 
     out = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": bench_config(args, rp, world, WORKLOAD),
+        "config": bench_config(args, rp, world, WORKLOAD, order_main),
         "e2e": {"value": samples_per_step / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": roof,
         "clocks": clk,
-        "gpu_launches": launches_per_step(k, args.budget, mix, probe_name == "filter", *two_levels(args, len(rp) - 1))
-        * args.steps,
+        "gpu_launches": launches_per_step(k, args.budget, mix, probe_name == "filter", *two_levels(args, len(rp) - 1),
+                                          ordered=order_main == "degree") * args.steps,
         "wall_s_timed": t_wall,
         "step_ms": step_ms,
     }
@@ -650,15 +681,16 @@ def run_gpu(args):
         rp3_d = torch.from_numpy(rp3.view(np.int64)).to(f"cuda:{dev}")
         col3_d = torch.from_numpy(col3.view(np.int32)).to(f"cuda:{dev}")
         B3 = 1_000_000_000
+        p3 = resolved_probe(args.probe, rp3)
+        o3 = resolved_order(args.vertex_order, rp3, p3, [1, 2], l2_bytes)
         for i in range(args.warmup):
-            step(rp3_d, col3_d, args.seed + i, budget=B3)
+            step(rp3_d, col3_d, args.seed + i, budget=B3, order=o3)
         torch.cuda.synchronize()
         c3 = Clocks(dev)
         c3.start()
-        ms3, _ = timed_steps(rp3_d, col3_d, args.steps, args.seed + 100, budget=B3)
+        ms3, _ = timed_steps(rp3_d, col3_d, args.steps, args.seed + 100, budget=B3, order=o3)
         clk3 = c3.stop()
-        p3 = resolved_probe(args.probe, rp3)
-        h = moss.moss_graph_load_csr(rp3_d, col3_d, device=dev, stream=stream)
+        h = moss.moss_graph_load_csr(rp3_d, col3_d, device=dev, stream=stream, order=ORDER_IDS[o3])
         try:
             moss.moss_set_probe(h, probe)
             moss.moss_set_rng(h, rng)
@@ -672,10 +704,11 @@ def run_gpu(args):
             "metric": "5-node samples/s at 34M edges", "value": B3 / (m3 / 1000.0), "unit": "samples/s",
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": m3, "step_ms": ms3,
             "config": {"workload": describe("cl_n4m", 5)[1], "budget": B3, "seed": args.seed, "probe": p3,
-                       "rng": args.rng,
+                       "rng": args.rng, "vertex_order": o3,
                        "l2": "flushed (512 MB write) before every timed step; tables larger than the L2"},
-            "roofline": roofline("cl_n4m", rp3, p3, t3, [1, 2], l2_bytes, gather, peaks),
-            "clocks": clk3, "gpu_launches": launches_per_step(5, B3, False, p3 == "filter", True) * args.steps}
+            "roofline": roofline(data_key("cl_n4m", o3), rp3, p3, t3, [1, 2], l2_bytes, gather, peaks),
+            "clocks": clk3,
+            "gpu_launches": launches_per_step(5, B3, False, p3 == "filter", True, ordered=o3 == "degree") * args.steps}
         out["batched"] = measure_batched(moss, torch, [f.result() for f in futures["batched"]],
                                          batch_specs(args.graphs)[1], args.steps, args.warmup, stream, rng)
         out["served"] = measure_served(moss, [f.result() for f in futures["served"]], args.rate,
@@ -942,7 +975,10 @@ def run_call(args):
     l2_flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     out = {}
     vsplit = args.vertex_split if args.vertex_split >= 0 else None
-    with moss.Graph(rp, col, stream=stream, k_mask=kmask, probe=probe, rng=RNG_IDS[args.rng], vsplit=vsplit) as g:
+    order = resolved_order(args.vertex_order, rp, resolved_probe(args.probe, rp), methods,
+                           torch.cuda.get_device_properties(0).L2_cache_size)
+    with moss.Graph(rp, col, stream=stream, k_mask=kmask, probe=probe, rng=RNG_IDS[args.rng], vsplit=vsplit,
+                    order=ORDER_IDS[order]) as g:
         buf = torch.zeros(22, dtype=torch.int64, device="cuda")
         for m in methods:
             for c in counts:
@@ -958,7 +994,8 @@ def run_call(args):
                         ms.append(a.elapsed_time(b))
                 out[f"{NAMES[m]}@{c}"] = {"ms": statistics.median(ms), "samples_per_s": c / statistics.median(ms) * 1e3}
     print(json.dumps({"metric": "samples/s of one sampling call", "workload": describe(args.workload, 5)[1],
-                      "probe": resolved_probe(args.probe, rp), "rng": args.rng, "steps": args.steps,
+                      "probe": resolved_probe(args.probe, rp), "rng": args.rng, "vertex_order": order,
+                      "steps": args.steps,
                       "warmup": args.warmup, "calls": out}), flush=True)
 
 

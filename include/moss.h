@@ -138,6 +138,31 @@ typedef struct {
 int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *col,
                         uint32_t n, uint64_t nnz, int device, void *stream, moss_graph **out);
 
+/* moss_graph_load_csr with a choice of internal vertex order.
+ *   MOSS_ORDER_INPUT  : the input ids (moss_graph_load_csr).
+ *   MOSS_ORDER_DEGREE : the vertices renumbered on the device before the
+ *     initialization pass, by key(d_v) descending, then input id ascending;
+ *     key(d) = d for d < 16, else 16 + 4 (L - 5) + ((d >> (L - 3)) & 3), L
+ *     the bit length of d (quarter-octave classes).  Each list stays sorted
+ *     in the new ids.  The samplers read records in proportion to degree
+ *     (Sec. 4.1.3, 5.1.4), so grouping the heavy vertices puts the hot
+ *     records of a heavy-tailed graph in fewer cache lines.
+ * Estimates, counts and variances are those of the renumbered graph, which
+ * is isomorphic to the input; every quantity of Sec. 2 and Table 1 is
+ * invariant under relabelling, but the draws of a seed differ from those of
+ * the input order.  moss_sample_records reports input ids; the tables of
+ * moss_table_export hold internal ids, and MOSS_TABLE_ORDER gives the input
+ * id of each internal vertex.  Input rules and errors as
+ * moss_graph_load_csr; the renumbering needs about 13.2 n bytes of scratch
+ * during the call (plus 4 nnz when col is not device memory of `device`) and
+ * keeps 4 n bytes for the id map.
+ * MOSS_EINVAL for another order. */
+#define MOSS_ORDER_INPUT  0
+#define MOSS_ORDER_DEGREE 1
+int moss_graph_load_csr_order(const void *row_ptr, int row_ptr_is_64, const uint32_t *col,
+                              uint32_t n, uint64_t nnz, int order, int device, void *stream,
+                              moss_graph **out);
+
 /* Sampling tables (Sec. 4.1.3 WeightRandomVertex, Sec. 5.1.4): the per-list
  * alias tables of sigma^(v) (eq. 1), the vertex alias tables of pi (k_mask
  * bit 4) and rho^(1), rho^(2) (k_mask bit 5) from the exact weights computed
@@ -234,8 +259,9 @@ int moss_sample_counts_noalloc(moss_graph *g, int method, uint64_t first, uint64
 
 /* Per-sample records of samples first..first+count-1 (for verification):
  * classes_dev (device, count uint8: 0 = collision, else class) and, when not
- * NULL, verts_dev (device, 5*count uint32: v,u,w,r,t in draw order; t = 0
- * for MOSS-4; MOSS-4Min: v,u,w,r,c(s), c(s) = 0 outside classes 3, 5, 6).
+ * NULL, verts_dev (device, 5*count uint32: v,u,w,r,t in draw order, as input
+ * ids; t = 0 for MOSS-4; MOSS-4Min: v,u,w,r,c(s), c(s) = 0 outside classes
+ * 3, 5, 6).
  * Asynchronous on stream. */
 int moss_sample_records(moss_graph *g, int method, uint64_t first, uint64_t count, uint64_t seed,
                         void *stream, uint8_t *classes_dev, uint32_t *verts_dev);
@@ -473,6 +499,9 @@ int moss_graph_stats(const moss_graph *g, moss_stats *out);
  *   MOSS_TABLE_HUB_BITS  ceil(H^2 / 32) x uint32: bit i H + j (word / 32, bit
  *                        % 32) set iff hubs i and j are adjacent; edge probes
  *                        between two hubs are answered from these bits
+ * and always:
+ *   MOSS_TABLE_ORDER     n x uint32: the input id of each internal vertex
+ *                        (the identity under MOSS_ORDER_INPUT)
  * bytes must equal the table size.  Synchronous. */
 #define MOSS_TABLE_VERT   0
 #define MOSS_TABLE_SLOT   1
@@ -488,6 +517,7 @@ int moss_graph_stats(const moss_graph *g, moss_stats *out);
 #define MOSS_TABLE_MIN_PICK  15
 #define MOSS_TABLE_HUB_LIST  16
 #define MOSS_TABLE_HUB_BITS  17
+#define MOSS_TABLE_ORDER     18
 int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t bytes);
 
 void moss_graph_free(moss_graph *g);

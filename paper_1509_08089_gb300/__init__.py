@@ -36,6 +36,8 @@ TABLE_FILTER = 14
 TABLE_MIN_PICK = 15
 TABLE_HUB_LIST = 16
 TABLE_HUB_BITS = 17
+TABLE_ORDER = 18
+ORDER_INPUT, ORDER_DEGREE = 0, 1
 
 
 class moss_stats(ctypes.Structure):
@@ -99,6 +101,8 @@ def load():
     sig = {
         "moss_graph_load_csr": ([_vp, ctypes.c_int, _vp, ctypes.c_uint32, _u64, ctypes.c_int, _vp,
                                  ctypes.POINTER(_vp)], ctypes.c_int),
+        "moss_graph_load_csr_order": ([_vp, ctypes.c_int, _vp, ctypes.c_uint32, _u64, ctypes.c_int, ctypes.c_int,
+                                       _vp, ctypes.POINTER(_vp)], ctypes.c_int),
         "moss_build_tables": ([_vp, ctypes.c_uint, _vp], ctypes.c_int),
         "moss_set_probe": ([_vp, ctypes.c_int], ctypes.c_int),
         "moss_set_rng": ([_vp, ctypes.c_int], ctypes.c_int),
@@ -225,8 +229,11 @@ def moss_last_error_detail() -> str:
     return load().moss_last_error_detail().decode()
 
 
-def moss_graph_load_csr(row_ptr, col, n: int | None = None, device: int = 0, stream=None) -> int:
-    """Copy a CSR graph (host or device arrays) to the device; returns the handle."""
+def moss_graph_load_csr(row_ptr, col, n: int | None = None, device: int = 0, stream=None,
+                        order: int = ORDER_INPUT) -> int:
+    """Copy a CSR graph (host or device arrays) to the device; returns the
+    handle.  order: ORDER_INPUT keeps the input ids, ORDER_DEGREE renumbers
+    the vertices by degree key (moss_graph_load_csr_order)."""
     lib = load()
     is64 = int(getattr(row_ptr, "dtype", None) in (np.uint64, np.int64) or str(getattr(row_ptr, "dtype", "")) in
                ("torch.int64", "torch.uint64"))
@@ -234,9 +241,14 @@ def moss_graph_load_csr(row_ptr, col, n: int | None = None, device: int = 0, str
         n = len(row_ptr) - 1
     nnz = len(col)
     out = _vp()
-    _check(lib.moss_graph_load_csr(_ptr(row_ptr), is64, _ptr(col) if nnz else None, n, nnz, device,
-                                   _stream(stream, device), ctypes.byref(out)))
+    _check(lib.moss_graph_load_csr_order(_ptr(row_ptr), is64, _ptr(col) if nnz else None, n, nnz, order, device,
+                                         _stream(stream, device), ctypes.byref(out)))
     return out.value
+
+
+def moss_graph_load_csr_order(row_ptr, col, order: int, n: int | None = None, device: int = 0, stream=None) -> int:
+    """moss_graph_load_csr with the internal vertex order (ORDER_INPUT, ORDER_DEGREE)."""
+    return moss_graph_load_csr(row_ptr, col, n=n, device=device, stream=stream, order=order)
 
 
 def moss_build_tables(g: int, k_mask: int = (1 << 4) | (1 << 5), stream=None):
@@ -592,10 +604,12 @@ class Graph:
     """Owning wrapper: load, build, sample, free."""
 
     def __init__(self, row_ptr, col, device: int = 0, stream=None, k_mask: int = (1 << 4) | (1 << 5),
-                 probe: int = PROBE_AUTO, rng: int = RNG_SPLITMIX64, vsplit: int | None = None):
+                 probe: int = PROBE_AUTO, rng: int = RNG_SPLITMIX64, vsplit: int | None = None,
+                 order: int = ORDER_INPUT):
         """vsplit: heavy level of the vertex tables (0..63, VERTEX_ONE_LEVEL;
-        None: the library's default for the graph's size)."""
-        self.handle = moss_graph_load_csr(row_ptr, col, device=device, stream=stream)
+        None: the library's default for the graph's size).  order:
+        ORDER_INPUT or ORDER_DEGREE (the vertices renumbered by degree key)."""
+        self.handle = moss_graph_load_csr(row_ptr, col, device=device, stream=stream, order=order)
         self.device = device
         moss_set_probe(self.handle, probe)
         moss_set_rng(self.handle, rng)

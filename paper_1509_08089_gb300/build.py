@@ -18,8 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libmoss.so")
 SOURCES = ["moss_capi.cu", "moss_tables.cu", "moss_min.cu", "moss_sample.cu", "moss_finalize.cu", "moss_noalloc.cu",
-           "moss_batch.cu", "moss_server.cu", "moss_measure.cu"]
-HEADERS = ["moss_internal.cuh", os.path.join("..", "..", "include", "moss.h")]
+           "moss_batch.cu", "moss_server.cu", "moss_measure.cu", "moss_order.cu"]
+HEADERS = ["moss_internal.cuh", "moss_alias.cuh", "moss_order.cuh", os.path.join("..", "..", "include", "moss.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

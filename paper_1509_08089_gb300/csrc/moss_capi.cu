@@ -10,6 +10,7 @@
 
 #include "../../include/moss.h"
 #include "moss_internal.cuh"
+#include "moss_order.cuh"
 
 using namespace moss;
 
@@ -228,6 +229,7 @@ struct moss_graph {
     uint2 *hub_rank = nullptr;
     uint32_t *hub_bits = nullptr;
     uint32_t *hub_list = nullptr;
+    uint32_t *order = nullptr;   // input id of each internal vertex (MOSS_ORDER_DEGREE), else null
     moss_result res_host{};      // host staging of the result
     uint32_t flags_host[2] = {0, 0};
 };
@@ -406,8 +408,15 @@ const char *moss_strerror(int status) {
 
 int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *col, uint32_t n, uint64_t nnz,
                         int device, void *stream, moss_graph **out) {
+    return moss_graph_load_csr_order(row_ptr, row_ptr_is_64, col, n, nnz, MOSS_ORDER_INPUT, device, stream, out);
+}
+
+int moss_graph_load_csr_order(const void *row_ptr, int row_ptr_is_64, const uint32_t *col, uint32_t n, uint64_t nnz,
+                              int order, int device, void *stream, moss_graph **out) {
     if (!out) return fail(MOSS_EINVAL, "out is NULL");
     *out = nullptr;
+    if (order != MOSS_ORDER_INPUT && order != MOSS_ORDER_DEGREE) return fail(MOSS_EINVAL, "order %d", order);
+    const bool ordered = order == MOSS_ORDER_DEGREE;
     if (!row_ptr) return fail(MOSS_EINVAL, "row_ptr is NULL");
     if (nnz > 0 && !col) return fail(MOSS_EINVAL, "col is NULL with nnz > 0");
     if (n == 0) return fail(MOSS_EINVAL, "graph has no vertex");
@@ -430,6 +439,7 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
     g->vsplit_min = n >= (1u << 20) ? MOSS_VERTEX_SPLIT_DEFAULT : MOSS_VERTEX_ONE_LEVEL;
     g->nnz = nnz;
     void *rp_dev = nullptr;
+    void *oscratch = nullptr;   // renumbering scratch (released before return)
     const size_t rp_bytes = (size_t)(n + 1ULL) * (row_ptr_is_64 ? 8 : 4);
     cudaError_t e = cudaSuccess;
     int blocks = table_blocks(n);
@@ -473,12 +483,41 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
             g->flags = c.take<uint32_t>(2);
             g->defer = c.take<uint32_t>(kDeferChunk / 32);
             rp_dev = c.take<uint8_t>(rp_bytes);
+            if (ordered) g->order = c.take<uint32_t>(n);
         }
     }
     STEP(cudaMemcpyAsync(rp_dev, row_ptr, rp_bytes, cudaMemcpyDefault, s), "copying row_ptr");
-    if (nnz) STEP(cudaMemcpyAsync(g->col, col, nnz * sizeof(uint32_t), cudaMemcpyDefault, s), "copying col");
     STEP(cudaMemsetAsync(g->flags, 0, 2 * sizeof(uint32_t), s), "clearing status");
-    STEP(launch_vertices(rp_dev, row_ptr_is_64, n, nnz, g->vert, g->flags, s), "vertex kernel");
+    if (ordered) {
+        // the input lists are read in place when they are device memory of
+        // this device, else copied beside the scratch first
+        bool direct = false;
+        if (nnz) {
+            cudaPointerAttributes pa;
+            if (cudaPointerGetAttributes(&pa, col) == cudaSuccess)
+                direct = pa.type == cudaMemoryTypeDevice && pa.device == device;
+            else
+                cudaGetLastError();
+        }
+        const uint64_t ob = (order_scratch_bytes(n) + 255) & ~255ull;
+        STEP(pool_alloc(device, &oscratch, ob + (direct ? 0 : nnz * sizeof(uint32_t)), s), "allocating order scratch");
+        const uint32_t *src = col;
+        if (nnz && !direct) {
+            uint32_t *copy = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(oscratch) + ob);
+            STEP(cudaMemcpyAsync(copy, col, nnz * sizeof(uint32_t), cudaMemcpyDefault, s), "copying col");
+            src = copy;
+        }
+        uint32_t *rp_new = nullptr;
+        STEP(launch_degree_order(rp_dev, row_ptr_is_64, src, n, nnz, g->order, g->col, oscratch, &rp_new, g->flags, s),
+             "ordering kernels");
+        STEP(launch_vertices(rp_new, 0, n, nnz, g->vert, g->flags, s), "vertex kernel");
+        void *done = oscratch;
+        oscratch = nullptr;
+        STEP(cudaFreeAsync(done, s), "releasing order scratch");
+    } else {
+        if (nnz) STEP(cudaMemcpyAsync(g->col, col, nnz * sizeof(uint32_t), cudaMemcpyDefault, s), "copying col");
+        STEP(launch_vertices(rp_dev, row_ptr_is_64, n, nnz, g->vert, g->flags, s), "vertex kernel");
+    }
     {
         u128 *tp = reinterpret_cast<u128 *>(g->partials + (uint64_t)prow * kSlots);
         STEP(launch_slots(n, nnz, g->col, g->vert, g->slot, g->acc, g->owner, g->sq, g->gam[0], g->gam[1], g->gam[2],
@@ -500,6 +539,7 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
     *out = g;
     return MOSS_OK;
 fail_out:
+    if (oscratch) cudaFreeAsync(oscratch, s);
     release(g);
     return rc;
 }
@@ -727,8 +767,13 @@ int moss_sample_records(moss_graph *g, int method, uint64_t first, uint64_t coun
                         uint8_t *classes_dev, uint32_t *verts_dev) {
     if (!g || !classes_dev) return fail(MOSS_EINVAL, "NULL argument");
     DeviceGuard dg(g->device);
-    return sample_into(g, method, first, count, seed, static_cast<cudaStream_t>(stream), g->counts, classes_dev,
-                       verts_dev);
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int rc = sample_into(g, method, first, count, seed, s, g->counts, classes_dev, verts_dev);
+    if (rc || !g->order || !verts_dev) return rc;
+    // vertex words of the records back to input ids (MOSS-4 and MOSS-4Min: the first four)
+    MOSS_CUDA(launch_map_records(verts_dev, count, method == 1 || method == 2 ? 5 : 4, g->order, g->n, s),
+              "record id map");
+    return MOSS_OK;
 }
 
 static int finalize_from_device(moss_graph *g, int k, const uint64_t K[2], cudaStream_t s, moss_result *out) {
@@ -891,6 +936,16 @@ int moss_table_export(const moss_graph *g, int table, void *host_dst, uint64_t b
         const uint64_t h = hub_capacity(g->n);
         src = table == MOSS_TABLE_HUB_LIST ? static_cast<const void *>(g->hub_list) : g->hub_bits;
         need = table == MOSS_TABLE_HUB_LIST ? h * 4 : (h * h + 31) / 32 * 4;
+    } else if (table == MOSS_TABLE_ORDER) {
+        need = (uint64_t)g->n * 4;
+        if (bytes != need) return fail(MOSS_EINVAL, "table %d has %llu bytes, got %llu", table,
+                                       (unsigned long long)need, (unsigned long long)bytes);
+        if (!g->order) {   // input order: the identity
+            uint32_t *dst = static_cast<uint32_t *>(host_dst);
+            for (uint32_t i = 0; i < g->n; ++i) dst[i] = i;
+            return MOSS_OK;
+        }
+        src = g->order;
     } else if ((table >= MOSS_TABLE_MIN_SEED && table <= MOSS_TABLE_MIN_LIST) || table == MOSS_TABLE_MIN_PICK) {
         if (!(g->built >> 5 & 1u)) return fail(MOSS_ESTATE, "MOSS-4Min tables not built");
         switch (table) {

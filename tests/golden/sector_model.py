@@ -29,8 +29,10 @@ per-sample figure used by the roofline ("achieved" = figure x 32 B x samples
 / kernel time).
 
     python tests/golden/sector_model.py [workload] [samples]
-writes tests/golden/sectors_<workload>.json.  Calls only the oracle and the
-shared input generator.
+writes tests/golden/sectors_<workload>.json; a workload name ending in
+"_degree" is that workload renumbered as a MOSS_ORDER_DEGREE load renumbers
+it (tests/helpers.degree_order).  Calls only the oracle, the shared input
+generator and that test helper.
 """
 from __future__ import annotations
 
@@ -383,7 +385,12 @@ class Replay:
 
 
 def model(workload: str, samples: int = 4000, seed: int = 42) -> dict:
-    rp, col = synth.workload(workload)
+    if workload.endswith("_degree"):
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from helpers import degree_order
+        _, rp, col = degree_order(*synth.workload(workload[: -len("_degree")]))
+    else:
+        rp, col = synth.workload(workload)
     out = {"workload": workload, "samples": samples, "seed": seed,
            "layout": ("32 B vertex alias records with the alias's vertex record, 32 B slot records with the "
                       "alias's pick and both picks' neighbour list and twin, 16 B vertex records, "

@@ -189,3 +189,37 @@ def close_estimates(r, o, og, k):
         for i in range(1, n):
             for l in range(2):
                 assert abs(r["lam"][l][i] - o["lam"][l][i]) <= 1e-9
+
+
+def order_key(deg) -> np.ndarray:
+    """Degree key of MOSS_ORDER_DEGREE: d below 16, else quarter-octave
+    classes 16 + 4 (L - 5) + the two bits below the leading one (L = bit
+    length of d)."""
+    d = np.asarray(deg, dtype=np.int64)
+    L = np.zeros_like(d)
+    nz = d > 0
+    L[nz] = np.floor(np.log2(d[nz])).astype(np.int64) + 1
+    # exact bit length (the float log can be off by one next to a power of two)
+    L[nz & ((1 << np.maximum(L - 1, 0)) > d)] -= 1
+    L[nz & ((1 << L) <= d)] += 1
+    sh = np.maximum(L - 3, 0)
+    return np.where(d < 16, d, 16 + 4 * (L - 5) + ((d >> sh) & 3))
+
+
+def degree_order(rp, col):
+    """The graph renumbered as a MOSS_ORDER_DEGREE load does: internal vertex
+    i is input vertex order[i], sorted by key descending, then input id;
+    returns (order, row_ptr, col) of the renumbered graph, lists ascending."""
+    rp = np.asarray(rp, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    n = len(rp) - 1
+    deg = np.diff(rp)
+    order = np.argsort(-order_key(deg), kind="stable")
+    inv = np.empty(n, dtype=np.int64)
+    inv[order] = np.arange(n)
+    nrp = np.zeros(n + 1, dtype=np.uint64)
+    nrp[1:] = np.cumsum(deg[order])
+    nrow = inv[np.repeat(np.arange(n), deg)]
+    ncol = inv[col]
+    idx = np.lexsort((ncol, nrow))
+    return order.astype(np.uint32), nrp, ncol[idx].astype(np.uint32)

@@ -77,3 +77,21 @@ def test_default_splits_match_the_oracle():
     import oracle
     for n in (100, (1 << 14) - 1, 1 << 14, 100_000, (1 << 20) - 1, 1 << 20, 4_000_000):
         assert bench.default_vertex_splits(n) == (oracle.default_split(n), oracle.default_split_min(n)), n
+
+
+def test_vertex_order_follows_the_table_size():
+    """auto: degree order exactly when the sampling tables exceed the L2."""
+    import numpy as np
+    l2 = bench.GB300_L2_BYTES
+    small = np.zeros(100_001, dtype=np.uint64)
+    small[-1] = 2_000_000
+    large = np.zeros(4_000_001, dtype=np.uint64)
+    large[-1] = 68_000_000
+    assert bench.resolved_order("auto", small, "hash", [1, 2], l2) == "input"
+    assert bench.resolved_order("auto", large, "filter", [1, 2], l2) == "degree"
+    assert bench.resolved_order("input", large, "filter", [1, 2], l2) == "input"
+    assert bench.resolved_order("degree", small, "hash", [1, 2], l2) == "degree"
+    assert bench.data_key("cl_n4m", "degree") == "cl_n4m_degree" and bench.data_key("cl_n4m", "input") == "cl_n4m"
+    # four more kernels per step in degree order: key counts, their scan, placement, lists
+    base = bench.launches_per_step(5, 1_000_000_000, False, True, True)
+    assert bench.launches_per_step(5, 1_000_000_000, False, True, True, ordered=True) == base + 4

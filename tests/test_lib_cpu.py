@@ -55,6 +55,8 @@ def test_argument_checks_before_device():
     assert lib.moss_graph_load_csr(rp.ctypes.data, 1, col.ctypes.data, 2, 3, 0, None,
                                    ctypes.byref(out)) == moss.MOSS_EGRAPH
     assert b"odd" in lib.moss_last_error_detail()
+    assert lib.moss_graph_load_csr_order(rp.ctypes.data, 1, col.ctypes.data, 2, 2, 2, 0, None,
+                                         ctypes.byref(out)) == moss.MOSS_EINVAL
     r = moss.moss_result()
     assert lib.moss_sample_estimate(None, 4, 10, 1, None, ctypes.byref(r)) == moss.MOSS_EINVAL
     assert lib.moss_build_tables(None, 16, None) == moss.MOSS_EINVAL
