@@ -153,7 +153,7 @@ int moss_graph_load_csr(const void *row_ptr, int row_ptr_is_64, const uint32_t *
  * the input order.  moss_sample_records reports input ids; the tables of
  * moss_table_export hold internal ids, and MOSS_TABLE_ORDER gives the input
  * id of each internal vertex.  Input rules and errors as
- * moss_graph_load_csr; the renumbering needs about 13.2 n bytes of scratch
+ * moss_graph_load_csr; the renumbering needs about 9.2 n bytes of scratch
  * during the call (plus 4 nnz when col is not device memory of `device`) and
  * keeps 4 n bytes for the id map.
  * MOSS_EINVAL for another order. */
