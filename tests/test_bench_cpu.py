@@ -35,6 +35,8 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+    # the GPU line's config keys, with the order --vertex-order auto resolves to (an L2-sized graph: input ids)
+    assert d["config"]["vertex_order"] == "input" and d["config"]["probe"] == "hash"
 
 
 @pytest.mark.parametrize("k,budget,mix,filtered,two,expected", [
