@@ -33,11 +33,12 @@
 //   k_order_lists   in internal order, so the renumbered lists are written
 //                   in order (written scattered by list, in input order, the
 //                   pass took 2.35 ms against 1.93 on the 34M-edge graph):
-//                   the lists of degree 32 or more a warp each, longer than
-//                   32 by a count over the 128 key slots and a placing pass
-//                   in input order; the rest by tiles of 32, G lanes per
-//                   list (G a power of two <= 32, the tile's longest), by
-//                   rank counting on the renumbered ids.
+//                   the lists of degree 32 or more a warp each: up to 128
+//                   entries ranked in registers (four a lane, one pass),
+//                   longer lists by a count over the 128 key slots and a
+//                   placing pass in input order; the rest by tiles of 32,
+//                   G lanes per list (G a power of two <= 32, the tile's
+//                   longest), by rank counting on the renumbered ids.
 #include "../../include/moss.h"
 #include "moss_internal.cuh"
 #include "moss_order.cuh"
@@ -237,8 +238,9 @@ __global__ void __launch_bounds__(kOrderThreads) k_order_place(const IdxT *rp, u
 }
 
 // One renumbered list on the whole warp: its d input entries at col_in[a..],
-// written at col_out[o..] in internal-id order; up to 32 entries by rank
-// counting, longer lists by key counts (h: the warp's 128 counters).
+// written at col_out[o..] in internal-id order; up to 128 entries by rank
+// counting (one entry a lane, or up to four in registers), longer lists by
+// key counts (h: the warp's 128 counters).
 __device__ __forceinline__ void list_on_warp(uint32_t d, uint64_t a, uint64_t o, uint32_t n, uint64_t nnz,
                                              const uint32_t *__restrict__ col_in, const uint32_t *__restrict__ inv,
                                              const uint8_t *__restrict__ slot_of, uint32_t *col_out, uint32_t *h,
@@ -264,6 +266,49 @@ __device__ __forceinline__ void list_on_warp(uint32_t d, uint64_t a, uint64_t o,
             rank += ((uint32_t)j < d && xj < x) ? 1u : 0u;
         }
         if ((uint32_t)lane < d && o + rank < nnz) col_out[o + rank] = x;
+        return;
+    }
+    if (d <= 4 * 32) {   // up to four entries a lane, ranked against all d in registers
+        const int rounds = (int)((d + 31) / 32);
+        uint32_t u[4], x[4], rank[4];
+        uint32_t last = 0;   // the entry before this round's first
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint32_t idx = (uint32_t)(r * 32 + lane);
+            u[r] = 0;
+            x[r] = 0xffffffffu;
+            rank[r] = 0;
+            if (r < rounds) {
+                if (idx < d) {
+                    u[r] = col_in[a + idx];
+                    if (u[r] < n) {
+                        x[r] = inv[u[r]];
+                    } else {
+                        err |= kErrRange;
+                        x[r] = n;
+                    }
+                }
+                const uint32_t up = __shfl_up_sync(kFull, u[r], 1);
+                const uint32_t prev = lane ? up : last;
+                if (idx < d && idx > 0 && prev >= u[r]) err |= kErrOrder;
+                last = __shfl_sync(kFull, u[r], 31);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (q >= rounds) break;
+            for (int j = 0; j < 32; ++j) {
+                const uint32_t xs = __shfl_sync(kFull, x[q], j);
+                const bool in = (uint32_t)(q * 32 + j) < d;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) rank[r] += (in && xs < x[r]) ? 1u : 0u;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint32_t idx = (uint32_t)(r * 32 + lane);
+            if (idx < d && o + rank[r] < nnz) col_out[o + rank[r]] = x[r];
+        }
         return;
     }
     for (int k = lane; k < kOrderKeys; k += 32) h[k] = 0;
@@ -332,7 +377,7 @@ __device__ __forceinline__ void list_on_warp(uint32_t d, uint64_t a, uint64_t o,
 constexpr int kLongKeySlot = kOrderKeys - 1 - 19;   // first slot of the keys below 20
 
 template <typename IdxT>
-__global__ void __launch_bounds__(kOrderThreads) k_order_lists(const IdxT *rp, uint32_t n, uint64_t nnz,
+__global__ void __launch_bounds__(kOrderThreads, 8) k_order_lists(const IdxT *rp, uint32_t n, uint64_t nnz,
                                                                const uint32_t *__restrict__ order,
                                                                const uint32_t *__restrict__ rp_out,
                                                                const uint32_t *__restrict__ col_in,
